@@ -1,0 +1,477 @@
+"""Pins of the FP64 oracle against facts fixed outside the oracle itself.
+
+Each test ties one oracle function to the paper's definitions or to mathematics that a
+plausible mistake (a dropped term, a wrong exponent, a swapped pre-factor, a transposed
+index) would violate:
+  * hand-derived closed forms of d_beta and a hand-worked KL sweep (tests/golden/);
+  * continuity of d_beta at beta -> 1 and beta -> 0, homogeneity d(cx|cy) = c^beta d(x|y);
+  * N = 2 CP block updates equal the textbook matrix beta-NMF multiplicative updates;
+  * exact fixed points (data equal to the model leave the blocks unchanged);
+  * brute-force joint surrogate G(Theta | Theta~) of Appendices A/B: tightness at the
+    reference, majorization elsewhere, and every block update being the block argmin;
+  * monotone decrease per block (B-CoMM) and per outer iteration (J-CoMM);
+  * first J-CoMM block == first B-CoMM block; KL closed-form denominator;
+  * Tucker with a superdiagonal core reduces to CP; Tucker with identity factors maps the
+    core to the data; Tucker N = 2 core update equals the tri-factor matrix update;
+  * the COO oracle equals the dense oracle on the densified tensor; the stable permutation
+    equals a brute-force stable sort.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+BETAS = [0.0, 0.5, 1.0, 1.5]
+
+
+def textbook_gamma(beta):
+    # Fevotte & Idier (2011) MM exponent for beta-NMF
+    return 1.0 / (2.0 - beta) if beta < 1 else 1.0
+
+
+# ----------------------------------------------------------------------------- d_beta
+
+def test_dbeta_golden_closed_forms():
+    rows = [l.split("#")[0].split() for l in open(os.path.join(GOLDEN, "dbeta_closed_forms.txt"))]
+    rows = [r for r in rows if r]
+    assert len(rows) >= 8
+    for b, x, y, want in rows:
+        got = oracle.dbeta(float(x), float(y), float(b))
+        assert got == pytest.approx(float(want), rel=1e-13, abs=1e-14), (b, x, y)
+
+
+def test_dbeta_continuity_and_homogeneity():
+    g = np.random.default_rng(3)
+    for _ in range(20):
+        x, y = g.uniform(0.2, 5.0, size=2)
+        kl = oracle.dbeta(x, y, 1.0)
+        assert oracle.dbeta(x, y, 1.0 + 1e-7) == pytest.approx(kl, rel=1e-5)
+        assert oracle.dbeta(x, y, 1.0 - 1e-7) == pytest.approx(kl, rel=1e-5)
+        is_ = oracle.dbeta(x, y, 0.0)
+        assert oracle.dbeta(x, y, 1e-7) == pytest.approx(is_, rel=1e-5)
+        for b in [0.0, 0.5, 1.0, 1.5, 2.0]:
+            c = 3.7
+            assert oracle.dbeta(c * x, c * y, b) == pytest.approx(c ** b * oracle.dbeta(x, y, b), rel=1e-12)
+            assert oracle.dbeta(x, y, b) >= 0.0
+            assert abs(oracle.dbeta(x, x, b)) < 1e-14
+
+
+def test_gamma_values():
+    assert oracle.gamma(0.0) == 0.5
+    assert oracle.gamma(0.5) == pytest.approx(2.0 / 3.0)
+    assert oracle.gamma(1.0) == 1.0
+    assert oracle.gamma(1.5) == 1.0
+
+
+# ------------------------------------------------------------------- hand-worked sweep
+
+def test_hand_worked_kl_sweep():
+    want = {}
+    for line in open(os.path.join(GOLDEN, "cp_2x2_kl_hand.txt")):
+        if line.startswith("#") or line.startswith("key"):
+            continue
+        k, v = line.split()
+        want[k] = float(v)
+    X = np.array([[1.0, 2.0], [3.0, 4.0]])
+    A = [np.ones((2, 1)), np.ones((2, 1))]
+    new, F = oracle.cp_mu_sweep(X, A, beta=1.0)
+    assert new[0][:, 0] == pytest.approx([want["A1_0"], want["A1_1"]], rel=1e-14)
+    assert new[1][:, 0] == pytest.approx([want["A2_0"], want["A2_1"]], rel=1e-14)
+    assert F == pytest.approx(want["F_in"], rel=1e-13)
+
+
+# ------------------------------------------------------------- N = 2: textbook beta-NMF
+
+@pytest.mark.parametrize("beta", BETAS)
+def test_cp_n2_is_textbook_beta_nmf(beta):
+    g = np.random.default_rng(11)
+    X = g.gamma(2.0, 1.0, size=(9, 7))
+    W = g.uniform(0.2, 1.0, size=(9, 3))
+    H = g.uniform(0.2, 1.0, size=(7, 3))
+    gm = textbook_gamma(beta)
+    V = W @ H.T
+    W_tb = W * (((X * V ** (beta - 2)) @ H) / ((V ** (beta - 1)) @ H)) ** gm
+    V = W_tb @ H.T
+    H_tb = H * (((X * V ** (beta - 2)).T @ W_tb) / ((V ** (beta - 1)).T @ W_tb)) ** gm
+    new, _ = oracle.cp_mu_sweep(X, [W, H], beta)
+    np.testing.assert_allclose(new[0], W_tb, rtol=1e-12)
+    np.testing.assert_allclose(new[1], H_tb, rtol=1e-12)
+
+
+# -------------------------------------------------------------------- fixed points
+
+@pytest.mark.parametrize("beta", BETAS)
+@pytest.mark.parametrize("dims", [(5, 4, 3), (4, 3, 3, 2)])
+def test_cp_fixed_point(beta, dims):
+    X, A = synth.cp_dense(dims, 3, seed=5, kind="exact")
+    X = oracle.cp_full(dims, A)  # exact model in FP64
+    new, _ = oracle.cp_mu_sweep(X, A, beta)
+    for a, b in zip(new, A):
+        np.testing.assert_allclose(a, b, rtol=1e-11)
+    new, _ = oracle.cp_jcomm_outer(X, A, beta, L=2)
+    for a, b in zip(new, A):
+        np.testing.assert_allclose(a, b, rtol=1e-11)
+
+
+@pytest.mark.parametrize("beta", BETAS)
+def test_tucker_fixed_point(beta):
+    dims, J = (5, 4, 3), (2, 3, 2)
+    _, G, A = synth.tucker_dense(dims, J, seed=2, kind="exact")
+    X = oracle.tucker_full(dims, G, A)
+    G1, A1, _ = oracle.tucker_mu_sweep(X, G, A, beta)
+    np.testing.assert_allclose(G1, G, rtol=1e-11)
+    for a, b in zip(A1, A):
+        np.testing.assert_allclose(a, b, rtol=1e-11)
+    G2, A2, _ = oracle.tucker_jcomm_outer(X, G, A, beta, L=2)
+    np.testing.assert_allclose(G2, G, rtol=1e-11)
+    for a, b in zip(A2, A):
+        np.testing.assert_allclose(a, b, rtol=1e-11)
+
+
+# --------------------------------------------- brute-force joint surrogate (App. A, B)
+
+def _d_beta_np(x, y, beta):
+    if beta == 1.0:
+        with np.errstate(divide="ignore", invalid="ignore"):
+            xl = np.where(x > 0, x * np.log(np.where(x > 0, x, 1.0) / y), 0.0)
+        return xl - x + y
+    if beta == 0.0:
+        return x / y - np.log(x / y) - 1.0
+    return (x ** beta + (beta - 1) * y ** beta - beta * x * y ** (beta - 1)) / (beta * (beta - 1))
+
+
+def _cp_contribs(A):
+    """z_{i,r} = prod_n A^(n)_{i_n r} by broadcasting; shape dims + (R,)."""
+    N = len(A)
+    z = 1.0
+    for n, a in enumerate(A):
+        shape = [1] * N + [a.shape[1]]
+        shape[n] = a.shape[0]
+        z = z * a.reshape(shape)
+    return z
+
+
+def _tucker_contribs(G, A):
+    """z_{i,j} = G_j prod_n A^(n)_{i_n j_n}; shape dims + core dims."""
+    N = len(A)
+    z = G.reshape((1,) * N + G.shape)
+    for n, a in enumerate(A):
+        shape = [1] * (2 * N)
+        shape[n] = a.shape[0]
+        shape[N + n] = a.shape[1]
+        z = z * a.reshape(shape)
+    return z
+
+
+def _surrogate(X, z, zt, beta):
+    """G(Theta | Theta~) = sum_i G_i, z / zt: contributions at Theta / Theta~ with the
+    component axes trailing X's axes."""
+    ax = tuple(range(X.ndim, z.ndim))
+    Xt = zt.sum(axis=ax)
+    lam = zt / Xt.reshape(Xt.shape + (1,) * len(ax))
+    xe = X.reshape(X.shape + (1,) * len(ax))
+    if beta >= 1.0:
+        return float((lam * _d_beta_np(xe, z / lam, beta)).sum())
+    Xh = z.sum(axis=ax)
+    convex = (lam * xe / (1.0 - beta) * (z / lam) ** (beta - 1.0)).sum(axis=ax)
+    if beta == 0.0:
+        concave = np.log(Xt) + (Xh - Xt) / Xt
+        const = -np.log(X) - 1.0
+    else:
+        concave = Xt ** beta / beta + Xt ** (beta - 1.0) * (Xh - Xt)
+        const = X ** beta / (beta * (beta - 1.0))
+    return float((convex + concave + const).sum())
+
+
+def _assert_block_argmin(Gfun, block, rel=1e-12, deltas=(1e-2, 1e-3)):
+    base = Gfun(block)
+    flat = block.reshape(-1)
+    for t in range(flat.size):
+        for d in deltas:
+            for s in (1 + d, 1 - d):
+                pert = flat.copy()
+                pert[t] *= s
+                val = Gfun(pert.reshape(block.shape))
+                assert val >= base - rel * abs(base), (t, d, s, val - base)
+
+
+@pytest.mark.parametrize("beta", BETAS)
+def test_cp_surrogate_tight_and_majorizes(beta):
+    g = np.random.default_rng(21)
+    dims, R = (4, 3, 5), 3
+    X = g.gamma(3.0, 1.0, size=dims) + 0.05
+    At = [g.uniform(0.2, 1.0, size=(d, R)) for d in dims]
+    zt = _cp_contribs(At)
+    F_t = oracle.cp_objective(X, At, beta)
+    assert _surrogate(X, zt, zt, beta) == pytest.approx(F_t, rel=1e-12)
+    for _ in range(10):
+        A = [a * g.uniform(0.3, 3.0, size=a.shape) for a in At]
+        assert _surrogate(X, _cp_contribs(A), zt, beta) >= oracle.cp_objective(X, A, beta) * (1 - 1e-12)
+
+
+@pytest.mark.parametrize("beta", BETAS)
+def test_cp_jcomm_blocks_are_surrogate_argmins(beta):
+    g = np.random.default_rng(22)
+    dims, R, L = (4, 3, 5), 2, 2
+    X = g.gamma(3.0, 1.0, size=dims) + 0.05
+    At = [g.uniform(0.2, 1.0, size=(d, R)) for d in dims]
+    zt = _cp_contribs(At)
+    for k in range(L * len(dims)):
+        A, _ = oracle.cp_jcomm_outer(X, At, beta, L=L, max_blocks=k + 1)
+        n = k % len(dims)
+
+        def Gfun(blk, A=A, n=n):
+            B = list(A)
+            B[n] = blk
+            return _surrogate(X, _cp_contribs(B), zt, beta)
+
+        _assert_block_argmin(Gfun, A[n])
+    # outer monotonicity (Theorem "Monotonic decrease across outer iterations")
+    A = At
+    F_prev = math.inf
+    for _ in range(6):
+        A, F = oracle.cp_jcomm_outer(X, A, beta, L=L)
+        assert F <= F_prev * (1 + 1e-13)
+        F_prev = F
+
+
+@pytest.mark.parametrize("beta", BETAS)
+def test_cp_block_updates_are_block_argmins_and_monotone(beta):
+    g = np.random.default_rng(23)
+    dims, R = (4, 5, 3), 3
+    X = g.gamma(3.0, 1.0, size=dims) + 0.05
+    A = [g.uniform(0.2, 1.0, size=(d, R)) for d in dims]
+    F = oracle.cp_objective(X, A, beta)
+    for sweep in range(2):
+        for n in range(len(dims)):
+            zt = _cp_contribs(A)
+            new, _, _ = oracle.cp_block_update(X, A, n, beta)
+
+            def Gfun(blk, A=A, n=n, zt=zt):
+                B = list(A)
+                B[n] = blk
+                return _surrogate(X, _cp_contribs(B), zt, beta)
+
+            _assert_block_argmin(Gfun, new[n])
+            F_new = oracle.cp_objective(X, new, beta)
+            assert F_new <= F * (1 + 1e-13)
+            A, F = new, F_new
+
+
+@pytest.mark.parametrize("beta", BETAS)
+def test_tucker_jcomm_blocks_are_surrogate_argmins(beta):
+    g = np.random.default_rng(24)
+    dims, J, L = (4, 3, 3), (2, 2, 2), 2
+    X = g.gamma(3.0, 1.0, size=dims) + 0.05
+    Gt = g.uniform(0.2, 1.0, size=J)
+    At = [g.uniform(0.2, 1.0, size=(d, j)) for d, j in zip(dims, J)]
+    zt = _tucker_contribs(Gt, At)
+    assert _surrogate(X, zt, zt, beta) == pytest.approx(oracle.tucker_objective(X, Gt, At, beta), rel=1e-12)
+    nb = len(dims) + 1
+    for k in range(L * nb):
+        G, A, _ = oracle.tucker_jcomm_outer(X, Gt, At, beta, L=L, max_blocks=k + 1)
+        b = k % nb
+        if b == 0:
+            def Gfun(blk, A=A):
+                return _surrogate(X, _tucker_contribs(blk, A), zt, beta)
+            _assert_block_argmin(Gfun, G)
+        else:
+            n = b - 1
+
+            def Gfun(blk, A=A, G=G, n=n):
+                B = list(A)
+                B[n] = blk
+                return _surrogate(X, _tucker_contribs(G, B), zt, beta)
+
+            _assert_block_argmin(Gfun, A[n])
+
+
+@pytest.mark.parametrize("beta", BETAS)
+def test_tucker_block_updates_are_block_argmins_and_monotone(beta):
+    g = np.random.default_rng(25)
+    dims, J = (4, 3, 3), (2, 2, 2)
+    X = g.gamma(3.0, 1.0, size=dims) + 0.05
+    G0 = g.uniform(0.2, 1.0, size=J)
+    A0 = [g.uniform(0.2, 1.0, size=(d, j)) for d, j in zip(dims, J)]
+    nb = len(dims) + 1
+    prevG, prevA = G0, A0
+    F_prev = oracle.tucker_objective(X, G0, A0, beta)
+    for k in range(nb):
+        G, A, _ = oracle.tucker_mu_sweep(X, G0, A0, beta, max_blocks=k + 1)
+        zt = _tucker_contribs(prevG, prevA)
+        if k == 0:
+            _assert_block_argmin(lambda blk: _surrogate(X, _tucker_contribs(blk, A), zt, beta), G)
+        else:
+            n = k - 1
+
+            def Gfun(blk, A=A, G=G, n=n):
+                B = list(A)
+                B[n] = blk
+                return _surrogate(X, _tucker_contribs(G, B), zt, beta)
+
+            _assert_block_argmin(Gfun, A[n])
+        F = oracle.tucker_objective(X, G, A, beta)
+        assert F <= F_prev * (1 + 1e-13)
+        prevG, prevA, F_prev = G, A, F
+
+
+# ------------------------------------------------------------------ structural pins
+
+@pytest.mark.parametrize("beta", BETAS)
+def test_first_jcomm_block_equals_first_bcomm_block(beta):
+    X, _ = synth.cp_dense((6, 5, 4), 3, seed=7, kind="gamma_noise")
+    A = synth.init_factors((6, 5, 4), 3, seed=8)
+    j, _ = oracle.cp_jcomm_outer(X, A, beta, L=1, max_blocks=1)
+    b, _, _ = oracle.cp_block_update(X, A, 0, beta)
+    np.testing.assert_allclose(j[0], b[0], rtol=1e-13)
+    _, G, At = synth.tucker_dense((5, 4, 3), (2, 2, 2), seed=3)
+    G0, A0 = synth.init_tucker((5, 4, 3), (2, 2, 2), seed=4)
+    Xt = synth.tucker_dense((5, 4, 3), (2, 2, 2), seed=3)[0]
+    Gj, _, _ = oracle.tucker_jcomm_outer(Xt, G0, A0, beta, L=1, max_blocks=1)
+    Gb, _, _ = oracle.tucker_mu_sweep(Xt, G0, A0, beta, max_blocks=1)
+    np.testing.assert_allclose(Gj, Gb, rtol=1e-13)
+
+
+def test_kl_denominator_is_product_of_colsums():
+    X, _ = synth.cp_dense((6, 5, 4), 3, seed=9)
+    A = synth.init_factors((6, 5, 4), 3, seed=10)
+    for n in range(3):
+        _, _, den = oracle.cp_block_update(X, A, n, 1.0)
+        cs = np.prod([A[m].sum(axis=0) for m in range(3) if m != n], axis=0)
+        np.testing.assert_allclose(den, np.broadcast_to(cs, den.shape), rtol=1e-13)
+
+
+@pytest.mark.parametrize("beta", BETAS)
+def test_scaling_commutes_with_sweep(beta):
+    X, _ = synth.cp_dense((6, 5, 4), 3, seed=12, kind="gamma_noise")
+    A = synth.init_factors((6, 5, 4), 3, seed=13)
+    c = 2.5
+    ref, _ = oracle.cp_mu_sweep(X, A, beta)
+    sc, _ = oracle.cp_mu_sweep(c * X, [c * A[0], A[1], A[2]], beta)
+    np.testing.assert_allclose(sc[0], c * ref[0], rtol=1e-12)
+    np.testing.assert_allclose(sc[1], ref[1], rtol=1e-12)
+    np.testing.assert_allclose(sc[2], ref[2], rtol=1e-12)
+
+
+@pytest.mark.parametrize("beta", [0.5, 1.5])
+def test_mode_permutation_permutes_numden(beta):
+    X, _ = synth.cp_dense((6, 5, 4), 3, seed=14, kind="gamma_noise")
+    A = synth.init_factors((6, 5, 4), 3, seed=15)
+    perm = (2, 0, 1)
+    Xp = np.transpose(X, perm)
+    Ap = [A[p] for p in perm]
+    for n in range(3):
+        _, num, den = oracle.cp_block_update(X, A, n, beta)
+        q = perm.index(n)
+        _, nump, denp = oracle.cp_block_update(Xp, Ap, q, beta)
+        np.testing.assert_allclose(nump, num, rtol=1e-12)
+        np.testing.assert_allclose(denp, den, rtol=1e-12)
+
+
+def test_tucker_superdiagonal_core_reduces_to_cp():
+    g = np.random.default_rng(31)
+    dims, R = (5, 4, 3), 3
+    A = [g.uniform(0.2, 1.0, size=(d, R)) for d in dims]
+    gvec = g.uniform(0.5, 2.0, size=R)
+    G = np.zeros((R, R, R))
+    for r in range(R):
+        G[r, r, r] = gvec[r]
+    A_cp = [A[0] * gvec, A[1], A[2]]
+    np.testing.assert_allclose(oracle.tucker_full(dims, G, A), oracle.cp_full(dims, A_cp), rtol=1e-13)
+    T = g.gamma(2.0, 1.0, size=dims)
+    for n in range(3):
+        tk = oracle.tucker_factor_contr(T, G, A, n)
+        cp = oracle.cp_contr(T, A, n) * gvec
+        np.testing.assert_allclose(tk, cp, rtol=1e-13)
+    core = oracle.tucker_core_contr(T, A, (R, R, R))
+    c1 = oracle.cp_contr(T, A, 0)
+    for r in range(R):
+        assert core[r, r, r] == pytest.approx((c1[:, r] * A[0][:, r]).sum(), rel=1e-13)
+
+
+@pytest.mark.parametrize("beta", BETAS)
+def test_tucker_identity_factors_core_block(beta):
+    g = np.random.default_rng(32)
+    dims = (3, 4, 2)
+    X = g.gamma(2.0, 1.0, size=dims) + 0.1
+    G = g.uniform(0.5, 2.0, size=dims)
+    A = [np.eye(d) for d in dims]
+    G1, _, _ = oracle.tucker_mu_sweep(X, G, A, beta, max_blocks=1)
+    gm = textbook_gamma(beta)
+    np.testing.assert_allclose(G1, G ** (1 - gm) * X ** gm, rtol=1e-12)
+
+
+@pytest.mark.parametrize("beta", BETAS)
+def test_tucker_n2_core_update_is_trifactor_update(beta):
+    g = np.random.default_rng(33)
+    X = g.gamma(2.0, 1.0, size=(6, 5)) + 0.1
+    G = g.uniform(0.3, 1.0, size=(2, 3))
+    A1 = g.uniform(0.3, 1.0, size=(6, 2))
+    A2 = g.uniform(0.3, 1.0, size=(5, 3))
+    V = A1 @ G @ A2.T
+    gm = textbook_gamma(beta)
+    G_tb = G * ((A1.T @ (X * V ** (beta - 2)) @ A2) / (A1.T @ (V ** (beta - 1)) @ A2)) ** gm
+    G1, _, _ = oracle.tucker_mu_sweep(X, G, [A1, A2], beta, max_blocks=1)
+    np.testing.assert_allclose(G1, G_tb, rtol=1e-12)
+    # and the next block (factor 1) is the matrix MU with basis G A2^T
+    G2, A, _ = oracle.tucker_mu_sweep(X, G, [A1, A2], beta, max_blocks=2)
+    H = (G_tb @ A2.T).T
+    V = A1 @ H.T
+    A1_tb = A1 * (((X * V ** (beta - 2)) @ H) / ((V ** (beta - 1)) @ H)) ** gm
+    np.testing.assert_allclose(A[0], A1_tb, rtol=1e-12)
+
+
+def test_tucker_partial_tensor_definition():
+    g = np.random.default_rng(34)
+    dims, J = (3, 4, 2), (2, 3, 2)
+    G = g.uniform(0.2, 1.0, size=J)
+    A = [g.uniform(0.2, 1.0, size=(d, j)) for d, j in zip(dims, J)]
+    full = oracle.tucker_full(dims, G, A)
+    for n in range(3):
+        Bn = oracle.tucker_partial(dims, G, A, n)  # J_n x prod_{m!=n} I_m
+        rest = [dims[m] for m in range(3) if m != n]
+        rec = np.tensordot(A[n], Bn.reshape((J[n],) + tuple(rest)), axes=(1, 0))
+        rec = np.moveaxis(rec, 0, n)
+        np.testing.assert_allclose(rec, full, rtol=1e-13)
+
+
+# ------------------------------------------------------------------------------ COO
+
+def test_coo_oracle_equals_dense_oracle():
+    g = np.random.default_rng(41)
+    dims, R = (5, 4, 6, 3), 3
+    X = np.where(g.uniform(size=dims) < 0.3, 1.0 + g.geometric(0.3, size=dims) - 1.0, 0.0)
+    idx, vals = synth.coo_from_dense(X)
+    A = [g.uniform(0.2, 1.0, size=(d, R)) for d in dims]
+    assert oracle.coo_kl_objective(dims, idx, vals, A) == pytest.approx(oracle.cp_objective(X, A, 1.0), rel=1e-12)
+    s1, F1 = oracle.coo_kl_jcomm_outer(dims, idx, vals, A, L=2)
+    d1, G1 = oracle.cp_jcomm_outer(X, A, 1.0, L=2)
+    assert F1 == pytest.approx(G1, rel=1e-12)
+    for a, b in zip(s1, d1):
+        np.testing.assert_allclose(a, b, rtol=1e-11)
+    s2, F2 = oracle.coo_kl_mu_sweep(dims, idx, vals, A)
+    d2, G2 = oracle.cp_mu_sweep(X, A, 1.0)
+    assert F2 == pytest.approx(G2, rel=1e-12)
+    for a, b in zip(s2, d2):
+        np.testing.assert_allclose(a, b, rtol=1e-11)
+
+
+def test_stable_perm_is_stable_sort():
+    g = np.random.default_rng(42)
+    keys = g.integers(0, 17, size=500).astype(np.int32)
+    perm = oracle.stable_perm(keys, 17)
+    brute = sorted(range(len(keys)), key=lambda e: keys[e])  # Python's sort is stable
+    assert perm.tolist() == brute
+
+
+def test_objective_beta0_floor():
+    X = np.array([[0.0, 2.0], [1.0, 3.0]])
+    A = [np.ones((2, 1)), np.ones((2, 1))]
+    f = oracle.cp_objective(X, A, 0.0, eps_x=1e-3)
+    want = sum(oracle.dbeta(max(x, 1e-3), 1.0, 0.0) for x in X.ravel())
+    assert f == pytest.approx(want, rel=1e-14)

@@ -1,0 +1,350 @@
+"""Throughput benchmark of the J-CoMM / B-CoMM hot path on one GB300.
+
+Workload (one "step" = one J-CoMM outer iteration, L = 1, over the whole tensor):
+dense 3-way CP, 512 x 512 x 512 FP32 (537 MB, larger than the 129 MB L2, so no flush is
+needed between steps), rank R = 32, beta = 1, data = CP model with Gamma(2,1) factors
+times i.i.d. Gamma(10, 0.1) noise, init U(0.1, 1).  Secondary figures on the same tensor:
+B-CoMM sweeps/s, and the time for each method to reach F*(1 + 1e-4), F* being the lowest
+objective of a long FP32 B-CoMM run from the same init.
+
+Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|tf32]
+        python bench.py --impl reference ...   (the FP64 CPU oracle on a bounded sample)
+Prints one JSON line on rank 0.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "J-CoMM time-to-1e-4 rel objective vs FP32 block-MU; sweeps/s; served p99"
+DIMS = (512, 512, 512)
+RANK = 32
+BETA = 1.0
+WORKLOAD = ("dense CP 512x512x512 FP32, R=32, beta=1 (KL), J-CoMM outer iteration (L=1); "
+            "Gamma(2,1) factors x Gamma(10,0.1) noise, U(0.1,1) init")
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=50)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ntf", choices=["ntf", "reference"])
+    p.add_argument("--precision", default="fp32", choices=["fp32", "tf32"])
+    p.add_argument("--no-ttt", action="store_true", help="skip the time-to-target runs")
+    p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    return p.parse_args()
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for k, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(k)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------ CPU oracle
+def oracle_step_sample(X, A, cores):
+    """Times the FP64 oracle on a bounded sample of one J-CoMM outer iteration at beta = 1:
+    the numerator/denominator rows of `rows` sampled indices per mode, scaled to the full
+    iteration.  Returns (seconds per full step estimate, description)."""
+    import oracle
+    rows_per_mode = max(4, 2 * cores)
+    total = 0.0
+    spent = 0.0
+    for n in range(3):
+        rows = np.linspace(0, DIMS[n] - 1, rows_per_mode).astype(np.int64)
+        t0 = time.perf_counter()
+        oracle.cp_numden_rows(X, A, A, A, n, rows, BETA)
+        dt = time.perf_counter() - t0
+        spent += dt
+        total += dt * DIMS[n] / rows_per_mode
+    desc = ("FP64 oracle (ntfo_cp_numden_rows, OpenMP) on %d sampled rows per mode of one outer iteration, "
+            "scaled by I_n/rows; %.1f s of CPU work" % (rows_per_mode, spent))
+    return total, desc
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import synth
+    cores = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    X, _ = synth.cp_dense(DIMS, RANK, seed=0, kind="gamma_noise")
+    A = synth.init_factors(DIMS, RANK, seed=1)
+    per = []
+    desc = ""
+    for s in range(args.warmup + args.steps):
+        sec, desc = oracle_step_sample(X, A, cores)
+        if s >= args.warmup:
+            per.append(sec)
+    sec = sum(per) / len(per)
+    v = 1.0 / sec
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "sweeps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": "bounded row sample, see cpu_baseline"},
+            "cpu_baseline": {"value": v, "unit": "sweeps/s", "cores": cores, "kind": "oracle", "sample": desc},
+            "e2e": {"value": v, "unit": "sweeps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------------ GPU arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+    import paper_2602_14683_gb300 as ntf
+    import synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ctx = ntf.default_context(local)
+    peaks, peak_src = load_peaks()
+
+    # inputs: every rank solves its own replica (independent problems: weak scaling)
+    X_np, _ = synth.cp_dense(DIMS, RANK, seed=rank, kind="gamma_noise")
+    A_np = synth.init_factors(DIMS, RANK, seed=1000 + rank)
+    X = torch.tensor(X_np, dtype=torch.float32, device=dev)
+    A0 = [torch.tensor(a, dtype=torch.float32, device=dev) for a in A_np]
+    stream = torch.cuda.current_stream(dev)
+    prec = args.precision
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        return max_over_ranks(e0.elapsed_time(e1) / 1e3)
+
+    # ---------------- headline: J-CoMM outer iterations, inputs resident in HBM -------------
+    A = [a.clone() for a in A0]
+    obj = torch.zeros(1, dtype=torch.float64, device=dev)
+
+    def jstep():
+        ntf.jcomm_outer(X, BETA, A, objective=obj, ctx=ctx, precision=prec)
+
+    for _ in range(args.warmup):
+        jstep()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    ctx.set_pass_timing(True)
+    ctx.pass_timing()
+    l0 = ctx.launches
+    t_j = timed(jstep, args.steps, 0)
+    launches = ctx.launches - l0
+    pass_ms, pass_n = ctx.pass_timing()
+    ctx.set_pass_timing(False)
+    clk = clocks.stop()
+
+    # ---------------- B-CoMM sweeps on the same tensor ----------------
+    B = [a.clone() for a in A0]
+
+    def bstep():
+        ntf.cp_mu_sweep(X, BETA, B, objective=obj, ctx=ctx, precision=prec)
+
+    t_b = timed(bstep, max(5, args.steps // 2), args.warmup)
+    b_rate = world * max(5, args.steps // 2) / t_b
+
+    # ---------------- end to end: host buffers, copies inside the timed region -------------
+    Xh = torch.empty(X.shape, dtype=torch.float32).pin_memory()
+    Xh.copy_(X)
+    Ah = [a.cpu().pin_memory() for a in A0]
+    Ahost_out = [torch.empty_like(a).pin_memory() for a in Ah]
+    obj_h = torch.zeros(1, dtype=torch.float64).pin_memory()
+    Xe = torch.empty_like(X)
+    Ae = [torch.empty_like(a) for a in A0]
+
+    def estep():
+        Xe.copy_(Xh, non_blocking=True)
+        for d, h in zip(Ae, Ah):
+            d.copy_(h, non_blocking=True)
+        ntf.jcomm_outer(Xe, BETA, Ae, objective=obj, ctx=ctx, precision=prec)
+        for h, d in zip(Ahost_out, Ae):
+            h.copy_(d, non_blocking=True)
+        obj_h.copy_(obj, non_blocking=True)
+
+    e_steps = max(5, args.steps // 5)
+    t_e = timed(estep, e_steps, min(args.warmup, 3))
+    h2d = X.numel() * 4 + sum(a.numel() * 4 for a in A0)
+    d2h = sum(a.numel() * 4 for a in A0) + 8
+
+    # ---------------- time to F*(1 + 1e-4) ----------------
+    ttt = None
+    if not args.no_ttt:
+        n_ref, n_run = 600, 200
+        Fs = torch.zeros(n_ref, dtype=torch.float64, device=dev)
+        R_ = [a.clone() for a in A0]
+        for t in range(n_ref):
+            ntf.cp_mu_sweep(X, BETA, R_, objective=Fs[t:t + 1], ctx=ctx, precision="fp32")
+        fstar = float(Fs.min().item())
+        target = fstar * (1 + 1e-4)
+        res = {}
+        for name, fn, p in (("jcomm", ntf.jcomm_outer, prec), ("block_mu_fp32", ntf.cp_mu_sweep, "fp32")):
+            Fr = torch.zeros(n_run, dtype=torch.float64, device=dev)
+            C_ = [a.clone() for a in A0]
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for t in range(n_run):
+                fn(X, BETA, C_, objective=Fr[t:t + 1], ctx=ctx, precision=p)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            per = e0.elapsed_time(e1) / 1e3 / n_run
+            F = Fr.cpu().numpy()
+            hit = np.nonzero(F <= target)[0]
+            res[name] = {"iters": int(hit[0]) if hit.size else None,
+                         "seconds": float(hit[0] * per) if hit.size else None,
+                         "s_per_iter": per}
+        ttt = {"target": "F*(1+1e-4)", "F_star": fstar, "F_star_from": "%d FP32 B-CoMM sweeps" % n_ref, **res}
+
+    # ---------------- roofline of the dominant kernel (the fused pass) ----------------
+    entries = DIMS[0] * DIMS[1] * DIMS[2]
+    # J-CoMM at beta = 1: one fused pass per outer iteration; per entry 2R flops rebuild
+    # Xtilde, 2R contract P against the last factor (modes 1 and 2), 2R against the
+    # row Khatri-Rao product (mode 3); 4 bytes of X read.
+    flops_per_launch = entries * 6 * RANK
+    bytes_per_launch = entries * 4
+    avg_pass = pass_ms / 1e3 / max(pass_n, 1)
+    if prec == "fp32":
+        sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+        peak = sm_count * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": flops_per_launch / avg_pass / 1e12, "peak": peak, "unit": "TFLOP/s",
+                "peak_source": "FP32 FMA pipe: %d SMs x 128 lanes x 2 flop x %.0f MHz (derived)" %
+                               (sm_count, peaks.get("sm_max_mhz", 2070.0)),
+                "hbm_achieved_gbs": bytes_per_launch / avg_pass / 1e9}
+    else:
+        peak = peaks["bf16_tflops"] / 2.0
+        roof = {"bound": "tensor", "achieved": flops_per_launch / avg_pass / 1e12, "peak": peak, "unit": "TFLOP/s",
+                "peak_source": "%s bf16 burst / 2 (TF32 = half the BF16 dense rate)" % peak_src,
+                "hbm_achieved_gbs": bytes_per_launch / avg_pass / 1e9, "hbm_peak_gbs": peaks["hbm_gbs"]}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    roof["pass_ms_avg"] = avg_pass * 1e3
+    roof["pass_launches"] = pass_n
+
+    # ---------------- CPU oracle baseline (rank 0, N = 1 only) ----------------
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cores = os.cpu_count() or 1
+        sec, desc = oracle_step_sample(X_np, A_np, cores)
+        cpu = {"value": 1.0 / sec, "unit": "sweeps/s", "cores": cores, "kind": "oracle", "sample": desc}
+
+    value = world * args.steps / t_j
+    line = {
+        "metric": METRIC, "value": value, "unit": "sweeps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_j / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "precision": prec, "method": "J-CoMM L=1",
+                   "l2": "inputs larger than L2 (537 MB tensor), no flush", "parallelism": "replicas"},
+        "block_mu_sweeps_per_s": b_rate,
+        "time_to_target": ttt,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": world * e_steps / t_e, "unit": "sweeps/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,158 @@
+/*
+ * ntf.h -- C ABI of libntf: GB300 (sm_103a) kernels for the unfolding-free
+ * beta-divergence majorization-minimization updates of nonnegative CP and Tucker
+ * decompositions (Leplat, arXiv 2602.14683).
+ *
+ * Conventions shared by every call
+ *   - Pointers are DEVICE pointers unless the name ends in _host or the comment says
+ *     "host".  Arrays of pointers (factors, COO coordinates) are host arrays whose
+ *     elements are device pointers.
+ *   - Tensors are row-major (C order, last mode fastest).  A factor A^(n) is I_n x R
+ *     (CP) or I_n x J_n (Tucker), row-major FP32.  The Tucker core is J_1 x ... x J_N
+ *     row-major FP32.
+ *   - The caller owns X, the factors, the core and every output buffer.  The context
+ *     owns all workspaces (padded factor copies, partial sums, Tucker partial tensors,
+ *     COO permutations); it grows them on demand with cudaMalloc, so the first call at
+ *     a new size allocates.
+ *   - Every call is asynchronous on `stream` (a cudaStream_t passed as void*; NULL is
+ *     the legacy default stream).  Factors are updated in place when the call's work on
+ *     the stream completes.  Objective outputs are FP64 device scalars written on the
+ *     same stream.
+ *   - Return value: NTF_OK (0) or a negative ntf_status.  On error nothing has been
+ *     launched that modifies caller buffers, except NTF_ERR_CUDA (a launch failed; the
+ *     caller's buffers are in an unspecified state).  ntf_last_error(ctx) returns a
+ *     message for the last error on that context; it stays valid until the next call.
+ *   - beta must lie in [0, 2) (the range of Remark "Exponent gamma(beta)"), else
+ *     NTF_ERR_BETA.  Ranks and core dimensions must lie in 1..64, else
+ *     NTF_ERR_UNSUPPORTED.  Dense kernels accept order N = 3 (other orders return
+ *     NTF_ERR_UNSUPPORTED); COO accepts 2 <= N <= 8.
+ *   - Data must be nonnegative and finite; factors and core must be >= eps on entry
+ *     (Assumption "Positivity safeguard").  These are preconditions, not checked on the
+ *     device.  At beta = 0 the data are floored at eps_x (Remark "The case beta = 0").
+ *   - A context is used by one host thread at a time.
+ */
+#ifndef NTF_H
+#define NTF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ntf_ctx ntf_ctx;
+
+typedef enum {
+    NTF_OK = 0,
+    NTF_ERR_ARG = -1,         /* null pointer, bad enum, inconsistent sizes */
+    NTF_ERR_BETA = -2,        /* beta outside [0, 2) or not finite */
+    NTF_ERR_SHAPE = -3,       /* dims <= 0, nnz out of range, core dims > tensor dims */
+    NTF_ERR_OOM = -4,         /* workspace allocation failed */
+    NTF_ERR_NONFINITE = -5,   /* reserved for host-side input checks */
+    NTF_ERR_TIMEOUT = -6,     /* a bounded device-side wait ran out (serving loop) */
+    NTF_ERR_CUDA = -7,        /* a CUDA runtime call or launch failed */
+    NTF_ERR_UNSUPPORTED = -8  /* valid request outside what the kernels implement */
+} ntf_status;
+
+enum { NTF_DENSE = 0, NTF_COO = 1 };
+enum { NTF_CP = 0, NTF_TUCKER = 1 };
+/* Arithmetic of the contraction tiles.  FP32: CUDA-core FP32 FMA.  TF32: tcgen05
+ * tensor cores, TF32 operands, FP32 accumulation (dense CP only).  The beta-powers are
+ * always FP32 and the objective is accumulated in FP64. */
+enum { NTF_PREC_FP32 = 0, NTF_PREC_TF32 = 1 };
+
+typedef struct {
+    int order;                 /* N */
+    const int64_t *dims;       /* host array [N], each >= 1 */
+    int kind;                  /* NTF_DENSE or NTF_COO */
+    const float *values;       /* dense: prod(dims) values; COO: nnz values */
+    const int32_t *const *idx; /* COO only: host array of N device arrays of nnz coords */
+    int64_t nnz;               /* COO only: number of stored entries (unique coords) */
+} ntf_tensor;
+
+typedef struct {
+    double eps;    /* floor on every parameter and on Xhat inside the powers (1e-12) */
+    double eps_x;  /* data floor used only at beta = 0 (1e-12) */
+    int inner_L;   /* J-CoMM inner sweeps per outer iteration, >= 1 (1) */
+    int precision; /* NTF_PREC_FP32 (default) or NTF_PREC_TF32 */
+} ntf_opts;
+
+/* Fills *o with the defaults shown above. */
+void ntf_opts_default(ntf_opts *o);
+
+/* Creates a context bound to CUDA device `device`.  Returns NTF_ERR_CUDA if the device
+ * cannot be used. */
+int ntf_ctx_create(ntf_ctx **ctx, int device);
+/* Frees the context's workspaces.  Waits for its in-flight work (device sync). */
+void ntf_ctx_destroy(ntf_ctx *ctx);
+/* Last error message of this context (static storage inside ctx, never NULL). */
+const char *ntf_last_error(const ntf_ctx *ctx);
+/* Number of kernels this context has launched since creation (for accounting). */
+int64_t ntf_launch_count(const ntf_ctx *ctx);
+/* Profiling of the fused passes (the kernels that read X).  While enabled, every such
+ * launch is bracketed by a pair of CUDA events recorded on the launch's own stream.
+ * ntf_pass_timing waits for the recorded events, returns their summed elapsed time in
+ * milliseconds and the number of bracketed launches, and clears the record.  Not for use
+ * during stream capture. */
+int ntf_set_pass_timing(ntf_ctx *ctx, int enable);
+int ntf_pass_timing(ntf_ctx *ctx, double *total_ms, int64_t *launches);
+
+/* One B-CoMM sweep for CP (Algorithm 1; Theorem "CP block multiplicative update";
+ * CPContr of Section 6.1): for n = 1..N in order, rebuild Xhat from the current
+ * factors, P = X*Xhat^(beta-2), Q = Xhat^(beta-1), Num^(n) = CPContr^(n)(P; A),
+ * Den^(n) = CPContr^(n)(Q; A) (at beta = 1 the closed form prod_{m!=n} colsum A^(m),
+ * Section 6.3), A^(n) <- max(A^(n) * (Num/Den)^gamma(beta), eps).
+ *   factors:       host array of N device pointers, A^(n) is I_n x rank, updated in place
+ *   objective_dev: device double or NULL; receives D_beta(X, Xhat) of the INCOMING
+ *                  iterate (before this sweep).
+ * Dense (N = 3) and COO (beta = 1 only, else NTF_ERR_UNSUPPORTED) tensors. */
+int ntf_cp_mu_sweep(ntf_ctx *ctx, const ntf_tensor *X, float beta, int rank,
+                    float *const *factors, const ntf_opts *opts, double *objective_dev,
+                    void *stream);
+
+/* One block-MM sweep for Tucker (Theorem "Tucker block multiplicative updates";
+ * Appendix C.2, eqs. (block_core_num_den), (block_Bn), (block_factor_num/den)): the
+ * core first, then factors 1..N, each block rebuilt from the current blocks, followed
+ * by the eps clip.
+ *   core_dims: host array [N] of J_n; core: device J_1 x ... x J_N, updated in place
+ *   factors:   host array of N device pointers, A^(n) is I_n x J_n, updated in place
+ *   objective_dev: device double or NULL; D_beta of the incoming iterate.
+ * Dense N = 3 only. */
+int ntf_tucker_mu_sweep(ntf_ctx *ctx, const ntf_tensor *X, float beta, const int64_t *core_dims,
+                        float *core, float *const *factors, const ntf_opts *opts,
+                        double *objective_dev, void *stream);
+
+/* One J-CoMM outer iteration (Algorithm 2; Section 5.3; Appendix C.3): the reference is
+ * the incoming iterate, Ptilde = X*Xtilde^(beta-2) and Qtilde = Xtilde^(beta-1) are
+ * fixed for opts->inner_L inner sweeps; every inner block update uses chi1 of the
+ * other current blocks for the numerator and chi2 for the denominator, the reference
+ * block as pre-factor, then the eps clip.  Reference tensors are recomputed from the
+ * reference factors inside each pass (never stored).
+ *   model: NTF_CP (rank_or_0 = R, core arguments NULL) or NTF_TUCKER (rank_or_0 = 0)
+ *   objective_ref_dev: device double or NULL; receives D_beta at the reference.
+ * CP dense N = 3 (any beta), CP COO (beta = 1), Tucker dense N = 3 (any beta). */
+int ntf_jcomm_outer(ntf_ctx *ctx, int model, const ntf_tensor *X, float beta, int rank_or_0,
+                    const int64_t *core_dims_or_null, float *core_or_null, float *const *factors,
+                    const ntf_opts *opts, double *objective_ref_dev, void *stream);
+
+/* D_beta(X, Xhat) = sum_i d_beta(X_i | max(Xhat_i, eps)) (Section 3.2, Definition
+ * "beta-divergence") in FP64, written to *out_dev.  Per-entry terms use stable forms
+ * in FP32 (log1p/expm1) and are summed in FP64.  For COO (beta = 1 only) the unstored
+ * entries contribute prod_n colsum(A^(n)) in closed form. */
+int ntf_beta_div(ntf_ctx *ctx, int model, const ntf_tensor *X, float beta, int rank_or_0,
+                 const int64_t *core_dims_or_null, const float *core_or_null,
+                 const float *const *factors, const ntf_opts *opts, double *out_dev,
+                 void *stream);
+
+/* Stable permutation of 0..nnz-1 by key (a COO coordinate array), bit-identical to a
+ * stable sort: equal keys keep their input order.  keys: device int32 [nnz] with values
+ * in [0, key_range); perm_out: device int32 [nnz].  Used internally to order COO
+ * entries per mode; exposed for testing. */
+int ntf_coo_stable_perm(ntf_ctx *ctx, const int32_t *keys, int64_t nnz, int64_t key_range,
+                        int32_t *perm_out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NTF_H */

@@ -1,0 +1,10 @@
+"""paper_2602_14683_gb300 -- GB300 (sm_103a) kernels for unfolding-free beta-divergence
+majorization-minimization of nonnegative CP and Tucker decompositions (arXiv 2602.14683).
+
+The computation lives in libntf.so (C ABI declared in include/ntf.h); this package is its
+thin Python binding.  Build the library with ``paper_2602_14683_gb300.build.build()``.
+"""
+from ._lib import (  # noqa: F401
+    Context, Coo, NtfError, beta_div, coo_stable_perm, cp_mu_sweep, default_context, jcomm_outer,
+    make_opts, raw_library, tucker_mu_sweep, LIB_PATH, EXPORTED,
+)

@@ -1,0 +1,260 @@
+"""ctypes binding of libntf (include/ntf.h).  Argument marshalling only: every step of
+the computation runs in the library's CUDA kernels.  Tensors are torch CUDA tensors
+(float32 data/factors/core, int32 COO coordinates, float64 objective scalars); PyTorch
+provides device memory and streams.
+
+If the library has not been built this module raises at import: there is no fallback.
+"""
+import ctypes as C
+import os
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libntf.so")
+
+NTF_OK = 0
+STATUS = {0: "NTF_OK", -1: "NTF_ERR_ARG", -2: "NTF_ERR_BETA", -3: "NTF_ERR_SHAPE", -4: "NTF_ERR_OOM",
+          -5: "NTF_ERR_NONFINITE", -6: "NTF_ERR_TIMEOUT", -7: "NTF_ERR_CUDA", -8: "NTF_ERR_UNSUPPORTED"}
+NTF_DENSE, NTF_COO = 0, 1
+NTF_CP, NTF_TUCKER = 0, 1
+NTF_PREC_FP32, NTF_PREC_TF32 = 0, 1
+PRECISIONS = {"fp32": NTF_PREC_FP32, "tf32": NTF_PREC_TF32}
+
+
+class NtfError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (STATUS.get(code, "?"), code, msg))
+        self.code = code
+
+
+class Tensor(C.Structure):
+    _fields_ = [("order", C.c_int), ("dims", C.POINTER(C.c_int64)), ("kind", C.c_int),
+                ("values", C.c_void_p), ("idx", C.POINTER(C.c_void_p)), ("nnz", C.c_int64)]
+
+
+class Opts(C.Structure):
+    _fields_ = [("eps", C.c_double), ("eps_x", C.c_double), ("inner_L", C.c_int), ("precision", C.c_int)]
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError("libntf.so is not built (%s); run paper_2602_14683_gb300.build.build()" % LIB_PATH)
+
+_lib = C.CDLL(LIB_PATH)
+_P = C.c_void_p
+_sig = {
+    "ntf_opts_default": (None, [C.POINTER(Opts)]),
+    "ntf_ctx_create": (C.c_int, [C.POINTER(_P), C.c_int]),
+    "ntf_ctx_destroy": (None, [_P]),
+    "ntf_last_error": (C.c_char_p, [_P]),
+    "ntf_launch_count": (C.c_int64, [_P]),
+    "ntf_set_pass_timing": (C.c_int, [_P, C.c_int]),
+    "ntf_pass_timing": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
+    "ntf_cp_mu_sweep": (C.c_int, [_P, C.POINTER(Tensor), C.c_float, C.c_int, C.POINTER(_P), C.POINTER(Opts), _P, _P]),
+    "ntf_tucker_mu_sweep": (C.c_int, [_P, C.POINTER(Tensor), C.c_float, C.POINTER(C.c_int64), _P, C.POINTER(_P),
+                                      C.POINTER(Opts), _P, _P]),
+    "ntf_jcomm_outer": (C.c_int, [_P, C.c_int, C.POINTER(Tensor), C.c_float, C.c_int, C.POINTER(C.c_int64), _P,
+                                  C.POINTER(_P), C.POINTER(Opts), _P, _P]),
+    "ntf_beta_div": (C.c_int, [_P, C.c_int, C.POINTER(Tensor), C.c_float, C.c_int, C.POINTER(C.c_int64), _P,
+                               C.POINTER(_P), C.POINTER(Opts), _P, _P]),
+    "ntf_coo_stable_perm": (C.c_int, [_P, _P, C.c_int64, C.c_int64, _P, _P]),
+}
+for _name, (_res, _args) in _sig.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+EXPORTED = tuple(_sig)
+
+
+class Context:
+    """Owns an ntf_ctx (workspaces) bound to one CUDA device."""
+
+    def __init__(self, device=0):
+        h = _P()
+        rc = _lib.ntf_ctx_create(C.byref(h), int(device))
+        if rc != NTF_OK:
+            raise NtfError(rc, "ntf_ctx_create(device=%d) failed" % device)
+        self.h = h
+        self.device = int(device)
+
+    def close(self):
+        if self.h:
+            _lib.ntf_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def launches(self):
+        return int(_lib.ntf_launch_count(self.h))
+
+    def set_pass_timing(self, enable=True):
+        self.check(_lib.ntf_set_pass_timing(self.h, 1 if enable else 0))
+
+    def pass_timing(self):
+        """(total milliseconds, number of fused-pass launches) since the last query."""
+        ms = C.c_double()
+        n = C.c_int64()
+        self.check(_lib.ntf_pass_timing(self.h, C.byref(ms), C.byref(n)))
+        return ms.value, n.value
+
+    def check(self, rc):
+        if rc != NTF_OK:
+            raise NtfError(rc, _lib.ntf_last_error(self.h).decode(errors="replace"))
+
+
+_contexts = {}
+
+
+def default_context(device=None):
+    if device is None:
+        device = torch.cuda.current_device()
+    if device not in _contexts:
+        _contexts[device] = Context(device)
+    return _contexts[device]
+
+
+class Coo:
+    """COO tensor: `idx` is a list of N int32 CUDA tensors (nnz each), `values` float32."""
+
+    def __init__(self, shape, idx, values):
+        self.shape = tuple(int(s) for s in shape)
+        self.idx = [i.contiguous() for i in idx]
+        self.values = values.contiguous()
+        self.nnz = int(values.numel())
+
+
+def _check_dev(t, dtype, name):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if t.dtype != dtype:
+        raise TypeError("%s must be %s, got %s" % (name, dtype, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+
+
+class _Desc:
+    """Keeps the C descriptor and the arrays it points to alive for one call."""
+
+    def __init__(self, X):
+        if isinstance(X, Coo):
+            _check_dev(X.values, torch.float32, "values")
+            for i in X.idx:
+                _check_dev(i, torch.int32, "COO coordinates")
+            self.dims = (C.c_int64 * len(X.shape))(*X.shape)
+            self.idx = (C.c_void_p * len(X.idx))(*[i.data_ptr() for i in X.idx])
+            self.t = Tensor(len(X.shape), self.dims, NTF_COO, X.values.data_ptr(), self.idx, X.nnz)
+        else:
+            _check_dev(X, torch.float32, "X")
+            self.dims = (C.c_int64 * X.dim())(*X.shape)
+            self.idx = None
+            self.t = Tensor(X.dim(), self.dims, NTF_DENSE, X.data_ptr(), None, 0)
+
+
+def _ptrs(tensors, name):
+    for t in tensors:
+        _check_dev(t, torch.float32, name)
+    return (C.c_void_p * len(tensors))(*[t.data_ptr() for t in tensors])
+
+
+def make_opts(eps=1e-12, eps_x=1e-12, inner_L=1, precision="fp32"):
+    o = Opts()
+    _lib.ntf_opts_default(C.byref(o))
+    o.eps, o.eps_x, o.inner_L = float(eps), float(eps_x), int(inner_L)
+    o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    return o
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _out_ptr(t):
+    if t is None:
+        return None
+    _check_dev(t, torch.float64, "objective")
+    return t.data_ptr()
+
+
+def cp_mu_sweep(X, beta, factors, objective=None, ctx=None, stream=None, **opts):
+    """One B-CoMM sweep (Algorithm 1); factors updated in place.  `objective` (float64
+    CUDA tensor, 1 element) receives D_beta of the incoming iterate."""
+    ctx = ctx or default_context()
+    d = _Desc(X)
+    fp = _ptrs(factors, "factors")
+    o = make_opts(**opts)
+    rank = int(factors[0].shape[1])
+    ctx.check(_lib.ntf_cp_mu_sweep(ctx.h, C.byref(d.t), float(beta), rank, fp, C.byref(o),
+                                   _out_ptr(objective), _stream(stream)))
+
+
+def tucker_mu_sweep(X, beta, core, factors, objective=None, ctx=None, stream=None, **opts):
+    """One Tucker block-MM sweep (core, then factors); blocks updated in place."""
+    ctx = ctx or default_context()
+    d = _Desc(X)
+    _check_dev(core, torch.float32, "core")
+    cd = (C.c_int64 * core.dim())(*core.shape)
+    fp = _ptrs(factors, "factors")
+    o = make_opts(**opts)
+    ctx.check(_lib.ntf_tucker_mu_sweep(ctx.h, C.byref(d.t), float(beta), cd, core.data_ptr(), fp, C.byref(o),
+                                       _out_ptr(objective), _stream(stream)))
+
+
+def jcomm_outer(X, beta, factors, core=None, objective=None, ctx=None, stream=None, **opts):
+    """One J-CoMM outer iteration (Algorithm 2) for CP (core=None) or Tucker; blocks
+    updated in place.  `objective` receives D_beta at the reference (incoming) iterate."""
+    ctx = ctx or default_context()
+    d = _Desc(X)
+    fp = _ptrs(factors, "factors")
+    o = make_opts(**opts)
+    if core is None:
+        rc = _lib.ntf_jcomm_outer(ctx.h, NTF_CP, C.byref(d.t), float(beta), int(factors[0].shape[1]), None, None,
+                                  fp, C.byref(o), _out_ptr(objective), _stream(stream))
+    else:
+        _check_dev(core, torch.float32, "core")
+        cd = (C.c_int64 * core.dim())(*core.shape)
+        rc = _lib.ntf_jcomm_outer(ctx.h, NTF_TUCKER, C.byref(d.t), float(beta), 0, cd, core.data_ptr(), fp,
+                                  C.byref(o), _out_ptr(objective), _stream(stream))
+    ctx.check(rc)
+
+
+def beta_div(X, beta, factors, core=None, out=None, ctx=None, stream=None, **opts):
+    """D_beta(X, Xhat) in FP64; returns a 1-element float64 CUDA tensor (written on the
+    stream, not synchronised)."""
+    ctx = ctx or default_context()
+    d = _Desc(X)
+    fp = _ptrs(factors, "factors")
+    o = make_opts(**opts)
+    if out is None:
+        out = torch.empty(1, dtype=torch.float64, device=factors[0].device)
+    if core is None:
+        rc = _lib.ntf_beta_div(ctx.h, NTF_CP, C.byref(d.t), float(beta), int(factors[0].shape[1]), None, None, fp,
+                               C.byref(o), _out_ptr(out), _stream(stream))
+    else:
+        _check_dev(core, torch.float32, "core")
+        cd = (C.c_int64 * core.dim())(*core.shape)
+        rc = _lib.ntf_beta_div(ctx.h, NTF_TUCKER, C.byref(d.t), float(beta), 0, cd, core.data_ptr(), fp,
+                               C.byref(o), _out_ptr(out), _stream(stream))
+    ctx.check(rc)
+    return out
+
+
+def coo_stable_perm(keys, key_range, ctx=None, stream=None):
+    """Stable permutation (int32) ordering `keys` (int32 CUDA tensor)."""
+    ctx = ctx or default_context()
+    _check_dev(keys, torch.int32, "keys")
+    out = torch.empty_like(keys)
+    ctx.check(_lib.ntf_coo_stable_perm(ctx.h, keys.data_ptr(), keys.numel(), int(key_range), out.data_ptr(),
+                                       _stream(stream)))
+    return out
+
+
+def raw_library():
+    """The loaded ctypes CDLL (for ABI-level tests)."""
+    return _lib

@@ -1,0 +1,9 @@
+// Instantiations of the fused FP32 CP pass for rank padding RP = 32 (compiled in its own
+// translation unit so the library builds in parallel).
+#include "cp3_fp32.cuh"
+
+namespace ntf {
+cudaError_t cp3_launch_fp32_r32(const Cp3Plan &p, const Cp3Args &a, int ms, int den, cudaStream_t s) {
+    return fp32::launch_rp<32>(p, a, ms, den, s);
+}
+}  // namespace ntf

@@ -1,0 +1,142 @@
+// Small kernels around the fused passes: factor padding, closed-form KL denominators,
+// the partial-sum reduction fused with the multiplicative update (and the chi
+// transforms of the new block), and the FP64 objective reduction.
+#include "ntf_internal.h"
+
+namespace ntf {
+
+__global__ void pad_kernel(const float *src, int rows, int R, float *dst, int RP) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)rows * RP) return;
+    int i = (int)(t / RP), r = (int)(t % RP);
+    dst[t] = r < R ? src[(int64_t)i * R + r] : 0.0f;
+}
+
+__global__ void unpad_kernel(const float *src, int rows, int R, int RP, float *dst) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)rows * R) return;
+    int i = (int)(t / R), r = (int)(t % R);
+    dst[t] = src[(int64_t)i * RP + r];
+}
+
+cudaError_t pad_factor(const float *src, int rows, int R, float *dst, int RP, cudaStream_t s) {
+    int64_t n = (int64_t)rows * RP;
+    pad_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(src, rows, R, dst, RP);
+    return cudaGetLastError();
+}
+
+cudaError_t unpad_factor(const float *src, int rows, int R, int RP, float *dst, cudaStream_t s) {
+    int64_t n = (int64_t)rows * R;
+    unpad_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(src, rows, R, RP, dst);
+    return cudaGetLastError();
+}
+
+__global__ void copy_kernel(const float *src, float *dst, int64_t n) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) dst[t] = src[t];
+}
+
+cudaError_t copy_f32(const float *src, float *dst, int64_t n, cudaStream_t s) {
+    copy_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(src, dst, n);
+    return cudaGetLastError();
+}
+
+// Den^(n)_{i r} at beta = 1 (Q == 1, Section 6.3): prod_{m != n} colsum(F^(m))_r.
+// One warp per rank column; FP64 sums in a fixed lane/stride order.
+struct ColsumArgs {
+    const float *f[8];
+    int rows[8];
+    int nf, RP;
+    float *out;
+};
+
+__global__ void colsum_prod_kernel(ColsumArgs c) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r = blockIdx.x * (blockDim.x >> 5) + warp;
+    if (r >= c.RP) return;
+    double prod = 1.0;
+    for (int m = 0; m < c.nf; ++m) {
+        double s = 0.0;
+        for (int i = lane; i < c.rows[m]; i += 32) s += (double)c.f[m][(int64_t)i * c.RP + r];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        prod *= s;
+    }
+    if (lane == 0) c.out[r] = (float)prod;
+}
+
+cudaError_t colsum_prod(int nf, const float *const *f, const int *rows, int RP, float *out,
+                        cudaStream_t s) {
+    ColsumArgs c{};
+    if (nf > 8) return cudaErrorInvalidValue;
+    for (int m = 0; m < nf; ++m) {
+        c.f[m] = f[m];
+        c.rows[m] = rows[m];
+    }
+    c.nf = nf;
+    c.RP = RP;
+    c.out = out;
+    colsum_prod_kernel<<<(RP + 7) / 8, 256, 0, s>>>(c);
+    return cudaGetLastError();
+}
+
+// Multiplicative update with the eps-constrained minimiser (Theorem "CP block
+// multiplicative update"; Section 5.3 "CP inner update" with pre = reference block):
+//   out = max(pre * (Num / Den)^gamma, eps)
+__global__ void mu_epilogue_kernel(MuEpiArgs e) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)e.rows * e.RP) return;
+    const int r = (int)(t % e.RP);
+    if (r >= e.R) {
+        e.out[t] = 0.0f;
+        if (e.chi1_out) e.chi1_out[t] = 0.0f;
+        if (e.chi2_out) e.chi2_out[t] = 0.0f;
+        return;
+    }
+    const int64_t stride = (int64_t)e.rows * e.RP;
+    float num = 0.0f, den = 0.0f;
+    for (int p = 0; p < e.n_parts; ++p) num += e.pn[p * stride + t];
+    if (e.den_closed) {
+        den = e.den_closed[r];
+    } else {
+        for (int p = 0; p < e.n_parts; ++p) den += e.pd[p * stride + t];
+    }
+    const float ratio = __fdiv_rn(num, den);
+    float m;
+    if (e.gamma == 1.0f) m = ratio;
+    else if (e.gamma == 0.5f) m = sqrtf(ratio);
+    else m = powf(ratio, e.gamma);
+    const float v = fmaxf(e.pre[t] * m, e.eps);
+    e.out[t] = v;
+    if (e.chi1_out) e.chi1_out[t] = chi1_f(e.beta, v, e.ref[t]);
+    if (e.chi2_out) e.chi2_out[t] = chi2_f(e.beta, v, e.ref[t]);
+}
+
+cudaError_t mu_epilogue(const MuEpiArgs &e, cudaStream_t s) {
+    int64_t n = (int64_t)e.rows * e.RP;
+    mu_epilogue_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(e);
+    return cudaGetLastError();
+}
+
+// Fixed-order FP64 sum of per-CTA objective partials (one CTA; lane-strided then tree).
+__global__ void reduce_obj_kernel(const double *parts, int n, double *out) {
+    __shared__ double sh[32];
+    double s = 0.0;
+    for (int t = threadIdx.x; t < n; t += blockDim.x) s += parts[t];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+        *out = t;
+    }
+}
+
+cudaError_t reduce_objective(const double *parts, int n, double, double *out, cudaStream_t s) {
+    reduce_obj_kernel<<<1, 256, 0, s>>>(parts, n, out);
+    return cudaGetLastError();
+}
+
+}  // namespace ntf

@@ -1,0 +1,525 @@
+// C ABI of libntf: argument validation, workspaces and the orchestration of the fused
+// passes for B-CoMM (Algorithm 1), J-CoMM (Algorithm 2) and the objective.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <vector>
+#include <string>
+
+#include "../../include/ntf.h"
+#include "ntf_internal.h"
+#include "ntf_tucker.h"
+#include "ntf_coo.h"
+
+struct ntf_ctx {
+    int device = 0;
+    int num_sms = 0;
+    char err[512] = {0};
+    int64_t launches = 0;
+    std::map<std::string, std::pair<void *, size_t>> ws;
+    // pass timing (profiling only)
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;  // pairs: ev[2k] start, ev[2k+1] stop
+    size_t ev_used = 0;           // pairs in use
+};
+
+namespace {
+
+int fail(ntf_ctx *c, int code, const char *fmt, ...) {
+    if (c) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(c->err, sizeof(c->err), fmt, ap);
+        va_end(ap);
+    }
+    return code;
+}
+
+#define NTF_CUDA(call)                                                                       \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return fail(ctx, NTF_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));  \
+        ++ctx->launches;                                                                     \
+    } while (0)
+
+void *ws_get(ntf_ctx *c, const std::string &name, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    auto &e = c->ws[name];
+    if (e.first && e.second >= bytes) return e.first;
+    if (e.first) cudaFree(e.first);
+    e = {nullptr, 0};
+    void *p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    e = {p, bytes};
+    return p;
+}
+
+int rank_pad(int R) { return R <= 8 ? 8 : R <= 16 ? 16 : R <= 32 ? 32 : 64; }
+
+ntf_opts resolve_opts(const ntf_opts *o) {
+    ntf_opts d;
+    ntf_opts_default(&d);
+    return o ? *o : d;
+}
+
+int check_common(ntf_ctx *ctx, const ntf_tensor *X, float beta, const ntf_opts &o) {
+    if (!ctx) return NTF_ERR_ARG;
+    if (!X || !X->dims) return fail(ctx, NTF_ERR_ARG, "tensor descriptor or dims is NULL");
+    if (!(beta >= 0.0f && beta < 2.0f))
+        return fail(ctx, NTF_ERR_BETA, "beta = %g outside [0, 2)", (double)beta);
+    if (!(o.eps > 0.0) || !(o.eps_x > 0.0)) return fail(ctx, NTF_ERR_ARG, "eps and eps_x must be > 0");
+    if (o.inner_L < 1) return fail(ctx, NTF_ERR_ARG, "inner_L must be >= 1");
+    if (o.precision != NTF_PREC_FP32 && o.precision != NTF_PREC_TF32)
+        return fail(ctx, NTF_ERR_ARG, "unknown precision %d", o.precision);
+    if (X->kind != NTF_DENSE && X->kind != NTF_COO) return fail(ctx, NTF_ERR_ARG, "unknown tensor kind");
+    if (X->order < 2 || X->order > 8) return fail(ctx, NTF_ERR_UNSUPPORTED, "order %d not in 2..8", X->order);
+    for (int n = 0; n < X->order; ++n)
+        if (X->dims[n] < 1 || X->dims[n] > (int64_t)0x7fffffff)
+            return fail(ctx, NTF_ERR_SHAPE, "dims[%d] = %lld out of range", n, (long long)X->dims[n]);
+    if (!X->values) return fail(ctx, NTF_ERR_ARG, "tensor values pointer is NULL");
+    if (X->kind == NTF_DENSE && X->order != 3)
+        return fail(ctx, NTF_ERR_UNSUPPORTED, "dense kernels implement order 3, got %d", X->order);
+    if (X->kind == NTF_COO) {
+        if (!X->idx) return fail(ctx, NTF_ERR_ARG, "COO coordinate array is NULL");
+        for (int n = 0; n < X->order; ++n)
+            if (!X->idx[n]) return fail(ctx, NTF_ERR_ARG, "COO coordinates of mode %d are NULL", n);
+        if (X->nnz < 0 || X->nnz > (int64_t)0x7fffffff)
+            return fail(ctx, NTF_ERR_SHAPE, "nnz = %lld out of range", (long long)X->nnz);
+    }
+    return NTF_OK;
+}
+
+int check_factors(ntf_ctx *ctx, const ntf_tensor *X, int rank, const float *const *factors) {
+    if (rank < 1 || rank > 64) return fail(ctx, NTF_ERR_UNSUPPORTED, "rank %d not in 1..64", rank);
+    if (!factors) return fail(ctx, NTF_ERR_ARG, "factor array is NULL");
+    for (int n = 0; n < X->order; ++n)
+        if (!factors[n]) return fail(ctx, NTF_ERR_ARG, "factor %d is NULL", n);
+    return NTF_OK;
+}
+
+// ------------------------------------------------------------------ dense CP state
+struct CpDense {
+    int I, J, K, R, RP;
+    ntf::Cp3Plan plan;
+    float *F[3];   // current (padded)
+    float *Ft[3];  // reference (padded)
+    float *C1[3], *C2[3];
+    float *pn[3], *pd[3];
+    double *obj;
+    float *denc;
+};
+
+int cp_dense_setup(ntf_ctx *ctx, const ntf_tensor *X, int R, bool jcomm, bool need_den, CpDense &s) {
+    s.I = (int)X->dims[0];
+    s.J = (int)X->dims[1];
+    s.K = (int)X->dims[2];
+    s.R = R;
+    s.RP = rank_pad(R);
+    s.plan = ntf::cp3_plan(s.I, s.J, s.K, s.RP, ctx->num_sms);
+    const int dims[3] = {s.I, s.J, s.K};
+    const int parts[3] = {s.plan.parts1, s.plan.parts2, s.plan.parts3};
+    for (int n = 0; n < 3; ++n) {
+        size_t fb = sizeof(float) * (size_t)dims[n] * s.RP;
+        s.F[n] = (float *)ws_get(ctx, "cpF" + std::to_string(n), fb);
+        s.Ft[n] = jcomm ? (float *)ws_get(ctx, "cpFt" + std::to_string(n), fb) : nullptr;
+        s.C1[n] = jcomm ? (float *)ws_get(ctx, "cpC1" + std::to_string(n), fb) : nullptr;
+        s.C2[n] = jcomm ? (float *)ws_get(ctx, "cpC2" + std::to_string(n), fb) : nullptr;
+        size_t pb = sizeof(float) * (size_t)parts[n] * dims[n] * s.RP;
+        s.pn[n] = (float *)ws_get(ctx, "cpPn" + std::to_string(n), pb);
+        s.pd[n] = need_den ? (float *)ws_get(ctx, "cpPd" + std::to_string(n), pb) : nullptr;
+        if (!s.F[n] || !s.pn[n] || (jcomm && (!s.Ft[n] || !s.C1[n] || !s.C2[n])) || (need_den && !s.pd[n]))
+            return fail(ctx, NTF_ERR_OOM, "workspace allocation failed");
+    }
+    s.obj = (double *)ws_get(ctx, "cpObj", sizeof(double) * (size_t)s.plan.grid);
+    s.denc = (float *)ws_get(ctx, "cpDenc", sizeof(float) * 64);
+    if (!s.obj || !s.denc) return fail(ctx, NTF_ERR_OOM, "workspace allocation failed");
+    return NTF_OK;
+}
+
+ntf::Cp3Args cp_args(const ntf_tensor *X, const CpDense &s, const ntf_opts &o, float beta) {
+    ntf::Cp3Args a{};
+    a.X = X->values;
+    a.I = s.I;
+    a.J = s.J;
+    a.K = s.K;
+    a.bkind = ntf::beta_kind(beta);
+    a.beta = beta;
+    a.eps = (float)o.eps;
+    a.eps_x = (float)o.eps_x;
+    a.n_jt = s.plan.n_jt;
+    a.n_kb = s.plan.n_kb;
+    a.n_is = s.plan.n_is;
+    a.vec16 = (s.K % 4 == 0) && ((reinterpret_cast<uintptr_t>(X->values) & 15) == 0);
+    a.p1n = s.pn[0];
+    a.p1d = s.pd[0];
+    a.p2n = s.pn[1];
+    a.p2d = s.pd[1];
+    a.p3n = s.pn[2];
+    a.p3d = s.pd[2];
+    a.obj = s.obj;
+    return a;
+}
+
+// Brackets a fused-pass launch with timing events when profiling is enabled.
+struct PassTimer {
+    ntf_ctx *c;
+    cudaStream_t st;
+    cudaEvent_t stop = nullptr;
+    PassTimer(ntf_ctx *c_, cudaStream_t s) : c(c_), st(s) {
+        if (!c->timing) return;
+        if (c->ev_used * 2 + 2 > c->ev.size()) {
+            cudaEvent_t a, b;
+            if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return;
+            c->ev.push_back(a);
+            c->ev.push_back(b);
+        }
+        cudaEventRecord(c->ev[c->ev_used * 2], st);
+        stop = c->ev[c->ev_used * 2 + 1];
+        ++c->ev_used;
+    }
+    ~PassTimer() {
+        if (stop) cudaEventRecord(stop, st);
+    }
+};
+
+int launch_pass(ntf_ctx *ctx, const CpDense &s, const ntf::Cp3Args &a, int ms, int den, int precision,
+                cudaStream_t st) {
+    PassTimer t(ctx, st);
+    if (precision == NTF_PREC_TF32 && ntf::cp3_tc_supported(s.RP, ms, den)) {
+        NTF_CUDA(ntf::cp3_tc_launch(s.plan, a, ms, den, st));
+    } else {
+        NTF_CUDA(ntf::cp3_launch(s.plan, a, ms, den, st));
+    }
+    return NTF_OK;
+}
+
+int cp_dense_mu_sweep(ntf_ctx *ctx, const ntf_tensor *X, float beta, int R, float *const *factors,
+                      const ntf_opts &o, double *objective_dev, cudaStream_t st) {
+    const int bk = ntf::beta_kind(beta);
+    const int den = bk != ntf::BK_KL;
+    CpDense s{};
+    int rc = cp_dense_setup(ctx, X, R, false, den, s);
+    if (rc) return rc;
+    const int dims[3] = {s.I, s.J, s.K};
+    const int parts[3] = {s.plan.parts1, s.plan.parts2, s.plan.parts3};
+    for (int n = 0; n < 3; ++n) NTF_CUDA(ntf::pad_factor(factors[n], dims[n], R, s.F[n], s.RP, st));
+    ntf::Cp3Args a = cp_args(X, s, o, beta);
+    const float gam = ntf::mu_gamma(beta);
+    for (int n = 0; n < 3; ++n) {
+        for (int m = 0; m < 3; ++m) a.rec[m] = a.num[m] = a.den[m] = s.F[m];
+        int ms = (n == 0 ? ntf::PM_M1 : n == 1 ? ntf::PM_M2 : ntf::PM_M3);
+        if (n == 0 && objective_dev) ms |= ntf::PM_OBJ;
+        rc = launch_pass(ctx, s, a, ms, den, o.precision, st);
+        if (rc) return rc;
+        if (!den) {
+            const float *f[2];
+            int rows[2], c = 0;
+            for (int m = 0; m < 3; ++m)
+                if (m != n) { f[c] = s.F[m]; rows[c] = dims[m]; ++c; }
+            NTF_CUDA(ntf::colsum_prod(2, f, rows, s.RP, s.denc, st));
+        }
+        ntf::MuEpiArgs e{};
+        e.pn = s.pn[n];
+        e.pd = s.pd[n];
+        e.n_parts = parts[n];
+        e.rows = dims[n];
+        e.RP = s.RP;
+        e.R = R;
+        e.den_closed = den ? nullptr : s.denc;
+        e.pre = s.F[n];
+        e.out = s.F[n];
+        e.beta = beta;
+        e.gamma = gam;
+        e.eps = (float)o.eps;
+        NTF_CUDA(ntf::mu_epilogue(e, st));
+    }
+    if (objective_dev) NTF_CUDA(ntf::reduce_objective(s.obj, s.plan.grid, 0.0, objective_dev, st));
+    for (int n = 0; n < 3; ++n) NTF_CUDA(ntf::unpad_factor(s.F[n], dims[n], R, s.RP, factors[n], st));
+    return NTF_OK;
+}
+
+int cp_dense_jcomm(ntf_ctx *ctx, const ntf_tensor *X, float beta, int R, float *const *factors,
+                   const ntf_opts &o, double *objective_dev, cudaStream_t st) {
+    const int bk = ntf::beta_kind(beta);
+    const bool kl = bk == ntf::BK_KL;
+    CpDense s{};
+    int rc = cp_dense_setup(ctx, X, R, true, !kl, s);
+    if (rc) return rc;
+    const int dims[3] = {s.I, s.J, s.K};
+    const int parts[3] = {s.plan.parts1, s.plan.parts2, s.plan.parts3};
+    for (int n = 0; n < 3; ++n) {
+        NTF_CUDA(ntf::pad_factor(factors[n], dims[n], R, s.F[n], s.RP, st));
+        NTF_CUDA(ntf::copy_f32(s.F[n], s.Ft[n], (int64_t)dims[n] * s.RP, st));
+    }
+    ntf::Cp3Args a = cp_args(X, s, o, beta);
+    const float gam = ntf::mu_gamma(beta);
+    if (kl) {
+        // beta = 1: chi1(Z, Zt) = Zt, so every Num_J^(n) depends on the reference only and
+        // one pass over X yields all three numerators (and D_beta at the reference);
+        // Qtilde == 1 makes each Den_J^(n) the product of column sums of the other
+        // current blocks (chi2(Z, Zt) = Z at beta = 1).
+        for (int m = 0; m < 3; ++m) a.rec[m] = a.num[m] = a.den[m] = s.Ft[m];
+        rc = launch_pass(ctx, s, a, ntf::PM_M1 | ntf::PM_M2 | ntf::PM_M3 | ntf::PM_OBJ, 0, o.precision, st);
+        if (rc) return rc;
+        for (int l = 0; l < o.inner_L; ++l) {
+            for (int n = 0; n < 3; ++n) {
+                const float *f[2];
+                int rows[2], c = 0;
+                for (int m = 0; m < 3; ++m)
+                    if (m != n) { f[c] = s.F[m]; rows[c] = dims[m]; ++c; }
+                NTF_CUDA(ntf::colsum_prod(2, f, rows, s.RP, s.denc, st));
+                ntf::MuEpiArgs e{};
+                e.pn = s.pn[n];
+                e.n_parts = parts[n];
+                e.rows = dims[n];
+                e.RP = s.RP;
+                e.R = R;
+                e.den_closed = s.denc;
+                e.pre = s.Ft[n];
+                e.out = s.F[n];
+                e.beta = beta;
+                e.gamma = gam;
+                e.eps = (float)o.eps;
+                NTF_CUDA(ntf::mu_epilogue(e, st));
+            }
+        }
+    } else {
+        for (int n = 0; n < 3; ++n) {
+            NTF_CUDA(ntf::copy_f32(s.Ft[n], s.C1[n], (int64_t)dims[n] * s.RP, st));
+            NTF_CUDA(ntf::copy_f32(s.Ft[n], s.C2[n], (int64_t)dims[n] * s.RP, st));
+        }
+        for (int l = 0; l < o.inner_L; ++l) {
+            for (int n = 0; n < 3; ++n) {
+                for (int m = 0; m < 3; ++m) {
+                    a.rec[m] = s.Ft[m];
+                    a.num[m] = s.C1[m];
+                    a.den[m] = s.C2[m];
+                }
+                int ms = (n == 0 ? ntf::PM_M1 : n == 1 ? ntf::PM_M2 : ntf::PM_M3);
+                if (l == 0 && n == 0) ms |= ntf::PM_OBJ;
+                rc = launch_pass(ctx, s, a, ms, 1, o.precision, st);
+                if (rc) return rc;
+                ntf::MuEpiArgs e{};
+                e.pn = s.pn[n];
+                e.pd = s.pd[n];
+                e.n_parts = parts[n];
+                e.rows = dims[n];
+                e.RP = s.RP;
+                e.R = R;
+                e.pre = s.Ft[n];
+                e.out = s.F[n];
+                e.ref = s.Ft[n];
+                e.chi1_out = s.C1[n];
+                e.chi2_out = s.C2[n];
+                e.beta = beta;
+                e.gamma = gam;
+                e.eps = (float)o.eps;
+                NTF_CUDA(ntf::mu_epilogue(e, st));
+            }
+        }
+    }
+    if (objective_dev) NTF_CUDA(ntf::reduce_objective(s.obj, s.plan.grid, 0.0, objective_dev, st));
+    for (int n = 0; n < 3; ++n) NTF_CUDA(ntf::unpad_factor(s.F[n], dims[n], R, s.RP, factors[n], st));
+    return NTF_OK;
+}
+
+int cp_dense_beta_div(ntf_ctx *ctx, const ntf_tensor *X, float beta, int R, const float *const *factors,
+                      const ntf_opts &o, double *out_dev, cudaStream_t st) {
+    CpDense s{};
+    int rc = cp_dense_setup(ctx, X, R, false, false, s);
+    if (rc) return rc;
+    const int dims[3] = {s.I, s.J, s.K};
+    for (int n = 0; n < 3; ++n) NTF_CUDA(ntf::pad_factor(factors[n], dims[n], R, s.F[n], s.RP, st));
+    ntf::Cp3Args a = cp_args(X, s, o, beta);
+    for (int m = 0; m < 3; ++m) a.rec[m] = a.num[m] = a.den[m] = s.F[m];
+    {
+        PassTimer t(ctx, st);
+        NTF_CUDA(ntf::cp3_launch(s.plan, a, ntf::PM_OBJ, 0, st));
+    }
+    NTF_CUDA(ntf::reduce_objective(s.obj, s.plan.grid, 0.0, out_dev, st));
+    return NTF_OK;
+}
+
+}  // namespace
+
+// =================================================================================== ABI
+
+extern "C" {
+
+void ntf_opts_default(ntf_opts *o) {
+    if (!o) return;
+    o->eps = 1e-12;
+    o->eps_x = 1e-12;
+    o->inner_L = 1;
+    o->precision = NTF_PREC_FP32;
+}
+
+int ntf_ctx_create(ntf_ctx **out, int device) {
+    if (!out) return NTF_ERR_ARG;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+        cudaGetLastError();
+        return NTF_ERR_CUDA;
+    }
+    if (cudaSetDevice(device) != cudaSuccess) return NTF_ERR_CUDA;
+    ntf_ctx *c = new ntf_ctx();
+    c->device = device;
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (c->num_sms <= 0) c->num_sms = 1;
+    *out = c;
+    return NTF_OK;
+}
+
+void ntf_ctx_destroy(ntf_ctx *c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    for (auto &kv : c->ws)
+        if (kv.second.first) cudaFree(kv.second.first);
+    for (auto e : c->ev) cudaEventDestroy(e);
+    ntf::tucker_release(c);
+    ntf::coo_release(c);
+    delete c;
+}
+
+const char *ntf_last_error(const ntf_ctx *c) { return c ? c->err : "null context"; }
+
+int64_t ntf_launch_count(const ntf_ctx *c) { return c ? c->launches : 0; }
+
+int ntf_set_pass_timing(ntf_ctx *c, int enable) {
+    if (!c) return NTF_ERR_ARG;
+    c->timing = enable != 0;
+    return NTF_OK;
+}
+
+int ntf_pass_timing(ntf_ctx *c, double *total_ms, int64_t *launches) {
+    if (!c || !total_ms || !launches) return NTF_ERR_ARG;
+    cudaSetDevice(c->device);
+    double t = 0.0;
+    for (size_t k = 0; k < c->ev_used; ++k) {
+        float ms = 0.0f;
+        if (cudaEventSynchronize(c->ev[2 * k + 1]) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, c->ev[2 * k], c->ev[2 * k + 1]) != cudaSuccess) {
+            cudaGetLastError();
+            c->ev_used = 0;
+            return fail(c, NTF_ERR_CUDA, "pass timing events failed");
+        }
+        t += ms;
+    }
+    *total_ms = t;
+    *launches = (int64_t)c->ev_used;
+    c->ev_used = 0;
+    return NTF_OK;
+}
+
+int ntf_cp_mu_sweep(ntf_ctx *ctx, const ntf_tensor *X, float beta, int rank, float *const *factors,
+                    const ntf_opts *opts, double *objective_dev, void *stream) {
+    ntf_opts o = resolve_opts(opts);
+    int rc = check_common(ctx, X, beta, o);
+    if (rc) return rc;
+    rc = check_factors(ctx, X, rank, factors);
+    if (rc) return rc;
+    cudaSetDevice(ctx->device);
+    ctx->err[0] = 0;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (X->kind == NTF_COO) {
+        if (ntf::beta_kind(beta) != ntf::BK_KL)
+            return fail(ctx, NTF_ERR_UNSUPPORTED, "COO tensors are implemented for beta = 1 only");
+        return ntf::coo_kl_sweep(ctx, X, rank, factors, o, objective_dev, st, /*jcomm=*/false);
+    }
+    return cp_dense_mu_sweep(ctx, X, beta, rank, factors, o, objective_dev, st);
+}
+
+int ntf_tucker_mu_sweep(ntf_ctx *ctx, const ntf_tensor *X, float beta, const int64_t *core_dims, float *core,
+                        float *const *factors, const ntf_opts *opts, double *objective_dev, void *stream) {
+    ntf_opts o = resolve_opts(opts);
+    int rc = check_common(ctx, X, beta, o);
+    if (rc) return rc;
+    if (X->kind != NTF_DENSE) return fail(ctx, NTF_ERR_UNSUPPORTED, "Tucker is implemented for dense tensors");
+    cudaSetDevice(ctx->device);
+    ctx->err[0] = 0;
+    return ntf::tucker_run(ctx, X, beta, core_dims, core, factors, o, objective_dev, (cudaStream_t)stream,
+                           /*jcomm=*/false);
+}
+
+int ntf_jcomm_outer(ntf_ctx *ctx, int model, const ntf_tensor *X, float beta, int rank_or_0,
+                    const int64_t *core_dims_or_null, float *core_or_null, float *const *factors,
+                    const ntf_opts *opts, double *objective_ref_dev, void *stream) {
+    ntf_opts o = resolve_opts(opts);
+    int rc = check_common(ctx, X, beta, o);
+    if (rc) return rc;
+    cudaSetDevice(ctx->device);
+    ctx->err[0] = 0;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (model == NTF_CP) {
+        rc = check_factors(ctx, X, rank_or_0, factors);
+        if (rc) return rc;
+        if (X->kind == NTF_COO) {
+            if (ntf::beta_kind(beta) != ntf::BK_KL)
+                return fail(ctx, NTF_ERR_UNSUPPORTED, "COO tensors are implemented for beta = 1 only");
+            return ntf::coo_kl_sweep(ctx, X, rank_or_0, factors, o, objective_ref_dev, st, /*jcomm=*/true);
+        }
+        return cp_dense_jcomm(ctx, X, beta, rank_or_0, factors, o, objective_ref_dev, st);
+    }
+    if (model == NTF_TUCKER) {
+        if (X->kind != NTF_DENSE) return fail(ctx, NTF_ERR_UNSUPPORTED, "Tucker is implemented for dense tensors");
+        return ntf::tucker_run(ctx, X, beta, core_dims_or_null, core_or_null, factors, o, objective_ref_dev, st,
+                               /*jcomm=*/true);
+    }
+    return fail(ctx, NTF_ERR_ARG, "unknown model %d", model);
+}
+
+int ntf_beta_div(ntf_ctx *ctx, int model, const ntf_tensor *X, float beta, int rank_or_0,
+                 const int64_t *core_dims_or_null, const float *core_or_null, const float *const *factors,
+                 const ntf_opts *opts, double *out_dev, void *stream) {
+    ntf_opts o = resolve_opts(opts);
+    int rc = check_common(ctx, X, beta, o);
+    if (rc) return rc;
+    if (!out_dev) return fail(ctx, NTF_ERR_ARG, "out_dev is NULL");
+    cudaSetDevice(ctx->device);
+    ctx->err[0] = 0;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (model == NTF_CP) {
+        rc = check_factors(ctx, X, rank_or_0, factors);
+        if (rc) return rc;
+        if (X->kind == NTF_COO) {
+            if (ntf::beta_kind(beta) != ntf::BK_KL)
+                return fail(ctx, NTF_ERR_UNSUPPORTED, "COO tensors are implemented for beta = 1 only");
+            return ntf::coo_kl_objective(ctx, X, rank_or_0, factors, o, out_dev, st);
+        }
+        return cp_dense_beta_div(ctx, X, beta, rank_or_0, factors, o, out_dev, st);
+    }
+    if (model == NTF_TUCKER) {
+        if (X->kind != NTF_DENSE) return fail(ctx, NTF_ERR_UNSUPPORTED, "Tucker is implemented for dense tensors");
+        return ntf::tucker_beta_div(ctx, X, beta, core_dims_or_null, core_or_null, factors, o, out_dev, st);
+    }
+    return fail(ctx, NTF_ERR_ARG, "unknown model %d", model);
+}
+
+int ntf_coo_stable_perm(ntf_ctx *ctx, const int32_t *keys, int64_t nnz, int64_t key_range, int32_t *perm_out,
+                        void *stream) {
+    if (!ctx) return NTF_ERR_ARG;
+    if ((!keys || !perm_out) && nnz > 0) return fail(ctx, NTF_ERR_ARG, "keys or perm_out is NULL");
+    if (nnz < 0 || nnz > (int64_t)0x7fffffff) return fail(ctx, NTF_ERR_SHAPE, "nnz out of range");
+    if (key_range < 1 || key_range > (int64_t)0x7fffffff) return fail(ctx, NTF_ERR_SHAPE, "key_range out of range");
+    cudaSetDevice(ctx->device);
+    ctx->err[0] = 0;
+    return ntf::coo_stable_perm(ctx, keys, nnz, key_range, perm_out, (cudaStream_t)stream);
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------ helpers for other units
+namespace ntf {
+void *ctx_ws(ntf_ctx *c, const char *name, size_t bytes) { return ws_get(c, name, bytes); }
+int ctx_fail(ntf_ctx *c, int code, const char *msg) { return fail(c, code, "%s", msg); }
+void ctx_count(ntf_ctx *c, int n) { c->launches += n; }
+int ctx_num_sms(const ntf_ctx *c) { return c->num_sms; }
+}  // namespace ntf

@@ -1,0 +1,178 @@
+// Internal declarations shared by the libntf translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ntf {
+
+// ---------------------------------------------------------------------------------
+// beta specialisations of the powers P = X*Y^(beta-2), Q = Y^(beta-1) (Section 4.1):
+// the four values used by the workloads get a single-MUFU form, any other beta goes
+// through powf.
+// ---------------------------------------------------------------------------------
+enum BetaKind : int { BK_IS = 0, BK_HALF = 1, BK_KL = 2, BK_THREEHALF = 3, BK_GEN = 4 };
+
+inline int beta_kind(float b) {
+    if (b == 0.0f) return BK_IS;
+    if (b == 0.5f) return BK_HALF;
+    if (b == 1.0f) return BK_KL;
+    if (b == 1.5f) return BK_THREEHALF;
+    return BK_GEN;
+}
+
+// gamma(beta) of Remark "Exponent gamma(beta)".
+inline float mu_gamma(float b) { return b < 1.0f ? 1.0f / (2.0f - b) : 1.0f; }
+
+#ifdef __CUDACC__
+// y: clipped reconstruction max(Xhat, eps) > 0; x: data (already floored at beta = 0).
+__device__ __forceinline__ void pq_powers(int bk, float beta, float x, float y, float &P, float &Q) {
+    switch (bk) {
+        case BK_IS: {
+            float r = __frcp_rn(y);
+            Q = r;
+            P = x * r * r;
+            break;
+        }
+        case BK_HALF: {
+            float s = rsqrtf(y);
+            Q = s;
+            P = x * s * s * s;
+            break;
+        }
+        case BK_KL: {
+            P = __fdiv_rn(x, y);
+            Q = 1.0f;
+            break;
+        }
+        case BK_THREEHALF: {
+            float s = rsqrtf(y);
+            Q = y * s;
+            P = x * s;
+            break;
+        }
+        default: {
+            Q = powf(y, beta - 1.0f);
+            P = x * powf(y, beta - 2.0f);
+            break;
+        }
+    }
+}
+
+// d_beta(x|y) (Section 3.2) in FP32.  Near x = y the terms of the definition cancel,
+// so there the divergence is written through log1p/expm1 of the ratio:
+//   KL : x (t - log1p t),  t = y/x - 1
+//   IS : s - log1p s,      s = x/y - 1
+//   else: x^b ((b-1) expm1(b L) - b expm1((b-1) L)) / (b (b-1)),  L = log1p(y/x - 1)
+// Far from x = y (ratio outside [1e-4, 1e4]) the ratio minus one loses the small
+// operand to rounding, and the definition itself has no cancellation; it is used there.
+__device__ __forceinline__ float dbeta_stable(int bk, float beta, float x, float y) {
+    if (bk == BK_IS) {
+        const float u = __fdiv_rn(x, y);
+        if (u > 1e-4f && u < 1e4f) {
+            const float s = u - 1.0f;
+            return s - log1pf(s);
+        }
+        return u - (logf(x) - logf(y)) - 1.0f;
+    }
+    if (!(x > 0.0f)) return bk == BK_KL ? y : powf(y, beta) / beta;
+    const float r = __fdiv_rn(y, x);
+    const bool near = r > 1e-4f && r < 1e4f;
+    if (bk == BK_KL) {
+        if (near) {
+            const float t = r - 1.0f;
+            return x * (t - log1pf(t));
+        }
+        return x * (logf(x) - logf(y)) - x + y;
+    }
+    if (near) {
+        const float L = log1pf(r - 1.0f);
+        const float e1 = expm1f(beta * L), e2 = expm1f((beta - 1.0f) * L);
+        return powf(x, beta) * ((beta - 1.0f) * e1 - beta * e2) / (beta * (beta - 1.0f));
+    }
+    return (powf(x, beta) + (beta - 1.0f) * powf(y, beta) - beta * x * powf(y, beta - 1.0f)) /
+           (beta * (beta - 1.0f));
+}
+
+// Transforms chi1, chi2 of Section 5.3 on one entry (z: current, zt: reference).
+__device__ __forceinline__ float chi1_f(float beta, float z, float zt) {
+    if (beta == 1.0f) return zt;
+    return powf(zt, 2.0f - beta) * powf(z, beta - 1.0f);
+}
+__device__ __forceinline__ float chi2_f(float beta, float z, float zt) {
+    if (beta < 1.0f) return z;
+    if (beta == 1.0f) return z;
+    return powf(z, beta) * powf(zt, 1.0f - beta);
+}
+#endif
+
+// ---------------------------------------------------------------------------------
+// Dense 3-way CP pass (the fused reconstruct -> powers -> contract kernel)
+// ---------------------------------------------------------------------------------
+enum PassMode : int { PM_M1 = 1, PM_M2 = 2, PM_M3 = 4, PM_OBJ = 8 };
+
+struct Cp3Args {
+    const float *X;
+    int I, J, K;
+    const float *rec[3];  // factors that rebuild Xhat, padded [I_n][RP]
+    const float *num[3];  // factors of the numerator contraction
+    const float *den[3];  // factors of the denominator contraction
+    // Optional explicit row factors [I*J][RP] (Tucker partial tensors): when rrow is set,
+    // GEMM1 uses rrow[i*J + j] instead of rec[0][i] * rec[1][j]; nrow / drow replace
+    // num[0][i] * num[1][j] and den[0][i] * den[1][j] in the mode-3 contraction.
+    const float *rrow, *nrow, *drow;
+    int bkind;
+    float beta, eps, eps_x;
+    int n_jt, n_kb, n_is;  // grid decomposition: row tiles x column blocks x slab splits
+    int vec16;             // 1: K % 4 == 0 and X 16-byte aligned (16-byte async copies)
+    float *p1n, *p1d;      // mode-1 partials [n_jt*n_kb][I][RP]
+    float *p2n, *p2d;      // mode-2 partials [n_kb*n_is][J][RP]
+    float *p3n, *p3d;      // mode-3 partials [n_jt*n_is][K][RP]
+    double *obj;           // per-CTA objective partials [grid]
+};
+
+struct Cp3Plan {
+    int RP, TJ, KB;
+    int n_jt, n_kb, n_is;
+    int grid;
+    int parts1, parts2, parts3;
+};
+
+Cp3Plan cp3_plan(int I, int J, int K, int RP, int num_sms);
+// Launches one pass.  mode_set: OR of PassMode; den: 1 when the denominator partials are
+// needed (beta != 1).  Returns a cudaError_t.
+cudaError_t cp3_launch(const Cp3Plan &plan, const Cp3Args &a, int mode_set, int den,
+                       cudaStream_t s);
+
+// Tensor-core (tcgen05, TF32) variant of the same pass; same partial layouts.
+bool cp3_tc_supported(int RP, int mode_set, int den);
+cudaError_t cp3_tc_launch(const Cp3Plan &plan, const Cp3Args &a, int mode_set, int den,
+                          cudaStream_t s);
+
+// ---------------------------------------------------------------------------------
+// Small kernels (epilogue.cu)
+// ---------------------------------------------------------------------------------
+cudaError_t pad_factor(const float *src, int rows, int R, float *dst, int RP, cudaStream_t s);
+cudaError_t unpad_factor(const float *src, int rows, int R, int RP, float *dst, cudaStream_t s);
+// out[r] = prod over the given factors of colsum(f)[r] (FP64 sums), r < RP.
+cudaError_t colsum_prod(int nf, const float *const *f, const int *rows, int RP, float *out,
+                        cudaStream_t s);
+// Reduce partial sums (fixed order) and apply the multiplicative update:
+//   out = max(pre * (sum pn / D)^gamma, eps), D = sum pd or den_closed[r];
+// optionally chi1_out = chi1(out, ref), chi2_out = chi2(out, ref).  Columns r >= R -> 0.
+struct MuEpiArgs {
+    const float *pn, *pd;
+    int n_parts, rows, RP, R;
+    const float *den_closed;
+    const float *pre;
+    float *out;
+    const float *ref;
+    float *chi1_out, *chi2_out;
+    float beta, gamma, eps;
+};
+cudaError_t mu_epilogue(const MuEpiArgs &e, cudaStream_t s);
+cudaError_t reduce_objective(const double *parts, int n, double add_const_unused, double *out,
+                             cudaStream_t s);
+cudaError_t copy_f32(const float *src, float *dst, int64_t n, cudaStream_t s);
+
+}  // namespace ntf

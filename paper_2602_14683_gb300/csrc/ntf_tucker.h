@@ -1,0 +1,17 @@
+// Internal: dense 3-way Tucker block MM and J-CoMM (tucker.cu).
+#pragma once
+#include "../../include/ntf.h"
+#include "ntf_internal.h"
+
+namespace ntf {
+void *ctx_ws(ntf_ctx *c, const char *name, size_t bytes);
+int ctx_fail(ntf_ctx *c, int code, const char *msg);
+void ctx_count(ntf_ctx *c, int n);
+int ctx_num_sms(const ntf_ctx *c);
+
+int tucker_run(ntf_ctx *ctx, const ntf_tensor *X, float beta, const int64_t *core_dims, float *core,
+               float *const *factors, const ntf_opts &o, double *objective_dev, cudaStream_t st, bool jcomm);
+int tucker_beta_div(ntf_ctx *ctx, const ntf_tensor *X, float beta, const int64_t *core_dims, const float *core,
+                    const float *const *factors, const ntf_opts &o, double *out_dev, cudaStream_t st);
+void tucker_release(ntf_ctx *ctx);
+}  // namespace ntf

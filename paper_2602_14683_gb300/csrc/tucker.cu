@@ -1,0 +1,695 @@
+// Dense 3-way Tucker: block MM (Theorem "Tucker block multiplicative updates",
+// Appendix C.2) and J-CoMM (Algorithm 2, Appendix C.3).
+//
+// Every block update reads X once through a fused pass:
+//   * Xhat rows come from the mode-3 partial tensor B3[i][j][c] = sum_{a,b} G[a,b,c]
+//     A1[i,a] A2[j,b] (eq. (block_Bn) for n = 3), materialised as an I1*I2 x J3 matrix
+//     (20 MB at 400^3, J = 32) by two small GEMMs, and the columns of A3:
+//     Xhat[i,j,k] = sum_c B3[i,j,c] A3[k,c].
+//   * Core and modes 1, 2: the "rows" pass writes W[i,j,c] = sum_k P[i,j,k] A3n[k,c] (and
+//     Wd with Q and A3d).  The remaining sums of eqs. (block_core_num_den),
+//     (block_factor_num/den) are then small GEMMs over W:
+//       Num1[i,a]   = sum_{j,c} W[i,j,c] H[j,a,c],    H[j,a,c]   = sum_b G[a,b,c] A2[j,b]
+//       Num2[j,b]   = sum_{i,c} W[i,j,c] GA1[i,b,c],  GA1[i,b,c] = sum_a A1[i,a] G[a,b,c]
+//       Pcore[a,b,c] = sum_i A1[i,a] sum_j A2[j,b] W[i,j,c]
+//   * Mode 3: the CP pass in mode 3 with explicit rows, Num3[k,c] = sum_{i,j} P B3n[i,j,c].
+// J-CoMM uses the reference blocks to rebuild Xtilde and chi1 / chi2 transforms of the
+// current blocks (and of the core) on the numerator / denominator side; since W depends
+// on the third factor only, one rows pass serves the core and modes 1 and 2 of an inner
+// sweep, so an inner sweep reads X twice instead of four times.
+#include <string>
+
+#include "cp3_fp32.cuh"
+#include "ntf_tucker.h"
+
+namespace ntf {
+
+// ----------------------------------------------------------------------------------
+// Strided batched GEMM with a two-level reduction index (FP32 FMA, FP64 carry):
+//   C[bt][m][n] = sum_{k1 < K1, k2 < K2} A(bt, m, k1, k2) * B(bt, k1, k2, n)
+// ----------------------------------------------------------------------------------
+struct Gemm {
+    const float *A, *B;
+    float *C;
+    int M, N, K1, K2, batch;
+    int64_t sab, sam, sak1, sak2;
+    int64_t sbb, sbk1, sbk2, sbn;
+    int64_t scb, scm, scn;
+};
+
+constexpr int GT = 64;   // output tile edge
+constexpr int GK = 16;   // reduction chunk
+constexpr int GCARRY = 16;  // chunks summed in FP32 before the FP64 carry
+
+__global__ void __launch_bounds__(256) gemm2k_kernel(const Gemm g) {
+    __shared__ float As[GK][GT + 4];
+    __shared__ float Bs[GK][GT + 4];
+    const int bt = blockIdx.z;
+    const int m0 = blockIdx.y * GT, n0 = blockIdx.x * GT;
+    const int tid = threadIdx.x, tm = tid / 16, tn = tid % 16;
+    const int64_t K = (int64_t)g.K1 * g.K2;
+    float acc[4][4];
+    double tot[4][4];
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) acc[x][y] = 0.0f, tot[x][y] = 0.0;
+    const float *A = g.A + bt * g.sab;
+    const float *B = g.B + bt * g.sbb;
+    int chunk = 0;
+    for (int64_t k0 = 0; k0 < K; k0 += GK) {
+        for (int t = tid; t < GK * GT; t += 256) {
+            const int kk = t / GT, mm = t % GT;
+            const int64_t k = k0 + kk;
+            float va = 0.0f, vb = 0.0f;
+            if (k < K) {
+                const int64_t k1 = k / g.K2, k2 = k % g.K2;
+                if (m0 + mm < g.M) va = A[(m0 + mm) * g.sam + k1 * g.sak1 + k2 * g.sak2];
+                if (n0 + mm < g.N) vb = B[k1 * g.sbk1 + k2 * g.sbk2 + (n0 + mm) * g.sbn];
+            }
+            As[kk][mm] = va;
+            Bs[kk][mm] = vb;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < GK; ++kk) {
+            float a[4], b[4];
+#pragma unroll
+            for (int x = 0; x < 4; ++x) a[x] = As[kk][tm + 16 * x];
+#pragma unroll
+            for (int y = 0; y < 4; ++y) b[y] = Bs[kk][tn + 16 * y];
+#pragma unroll
+            for (int x = 0; x < 4; ++x)
+#pragma unroll
+                for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(a[x], b[y], acc[x][y]);
+        }
+        __syncthreads();
+        if (++chunk == GCARRY) {
+            chunk = 0;
+#pragma unroll
+            for (int x = 0; x < 4; ++x)
+#pragma unroll
+                for (int y = 0; y < 4; ++y) tot[x][y] += (double)acc[x][y], acc[x][y] = 0.0f;
+        }
+    }
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) {
+            const int m = m0 + tm + 16 * x, n = n0 + tn + 16 * y;
+            if (m < g.M && n < g.N) g.C[bt * g.scb + m * g.scm + n * g.scn] = (float)(tot[x][y] + (double)acc[x][y]);
+        }
+}
+
+static cudaError_t gemm(const Gemm &g, cudaStream_t s) {
+    dim3 grid((g.N + GT - 1) / GT, (g.M + GT - 1) / GT, g.batch);
+    gemm2k_kernel<<<grid, 256, 0, s>>>(g);
+    return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------------
+// Rows pass: W[i][j][c] = sum_k P[i,j,k] Cn[k,c], Wd with Q and Cd, over all k.
+// Xhat[i,j,k] = sum_c Rrow[i*J+j][c] Crec[k][c].  One CTA owns a tile of TJ rows j and a
+// range of slabs i; column chunks of the third factors are staged with the X tile.
+// ----------------------------------------------------------------------------------
+struct RowsArgs {
+    Cp3Args a;      // X, sizes, bkind/beta/eps, rrow, rec[2] (= Crec), num[2], den[2], obj
+    float *Wn, *Wd; // [I*J][RP]
+    int n_is;
+};
+
+template <int RP, bool DEN, bool OBJ>
+__global__ void __launch_bounds__(fp32::NT, 1) tucker_rows_kernel(const RowsArgs ra) {
+    using namespace fp32;
+    using G = Geo<RP>;
+    constexpr int TJ = G::TJ, RW = G::RW, RG = G::RG, RS = G::RS, TT = G::TT;
+    const Cp3Args &a = ra.a;
+    extern __shared__ __align__(16) float sm[];
+    float *xs0 = sm;                          // 2 x TJ x XS
+    float *ps = xs0 + 2 * TJ * XS;            // TJ x XS
+    float *qs = ps + TJ * XS;                 // TJ x XS (DEN)
+    float *rrT = qs + (DEN ? TJ * XS : 0);    // RP x TT
+    float *ct0 = rrT + RP * TT;               // 2 x RP x KC  (Crec chunk, permuted)
+    float *cn0 = ct0 + 2 * RP * KC;           // 2 x KC x RS
+    float *cd0 = cn0 + 2 * KC * RS;           // 2 x KC x RS (DEN)
+    double *dred = reinterpret_cast<double *>(cd0 + (DEN ? 2 * KC * RS : 0));
+
+    const int tid = threadIdx.x, tr = tid >> 3, tc = tid & 7;
+    const int is = blockIdx.x % ra.n_is, jt = blockIdx.x / ra.n_is;
+    const int i0 = (int)((int64_t)is * a.I / ra.n_is), i1 = (int)((int64_t)(is + 1) * a.I / ra.n_is);
+    const int j0 = jt * TJ, J = a.J, K = a.K;
+    const int nch = (K + KC - 1) / KC;
+
+    auto stage = [&](int buf, int i, int q) {
+        const int kc = q * KC;
+        load_x_tile<TJ>(a, xs0 + buf * TJ * XS, i, j0, kc);
+        float *ct = ct0 + buf * RP * KC;
+        for (int t = tid; t < RP * KC; t += NT) {
+            const int r = t / KC, c = t % KC, k = kc + c;
+            const bool v = k < K;
+            cp_async4(ct + r * KC + (c & 7) * 4 + (c >> 3), v ? a.rec[2] + (int64_t)k * RP + r : a.rec[2], v ? 4 : 0);
+        }
+        float *cn = cn0 + buf * KC * RS;
+        float *cd = cd0 + buf * KC * RS;
+        for (int t = tid; t < KC * (RP / 4); t += NT) {
+            const int c = t / (RP / 4), seg = t % (RP / 4), k = kc + c;
+            const bool v = k < K;
+            cp_async16(cn + c * RS + seg * 4, v ? a.num[2] + (int64_t)k * RP + seg * 4 : a.num[2], v ? 16 : 0);
+            if (DEN) cp_async16(cd + c * RS + seg * 4, v ? a.den[2] + (int64_t)k * RP + seg * 4 : a.den[2], v ? 16 : 0);
+        }
+    };
+
+    double obj_acc = 0.0;
+    const int total = (i1 - i0) * nch;
+    if (total > 0) stage(0, i0, 0);
+    cp_async_commit();
+    int buf = 0;
+    float W[RW][RG], Wd[RW][RG];
+    for (int it = 0; it < total; ++it) {
+        const int i = i0 + it / nch, q = it % nch;
+        if (q == 0) {
+            const int64_t rb = (int64_t)i * J + j0;
+            for (int t = tid; t < TJ * RP; t += NT) {
+                const int row = t / RP, r = t % RP;
+                rrT[r * TT + row] = (j0 + row < J) ? __ldg(a.rrow + (rb + row) * RP + r) : 0.0f;
+            }
+#pragma unroll
+            for (int x = 0; x < RW; ++x)
+#pragma unroll
+                for (int y = 0; y < RG; ++y) W[x][y] = Wd[x][y] = 0.0f;
+        }
+        if (it + 1 < total) stage(buf ^ 1, i0 + (it + 1) / nch, (it + 1) % nch);
+        cp_async_commit();
+        cp_async_wait<1>();
+        __syncthreads();
+        const float *xs = xs0 + buf * TJ * XS;
+        const float *ct = ct0 + buf * RP * KC;
+        const float *cn = cn0 + buf * KC * RS;
+        const float *cd = cd0 + buf * KC * RS;
+        const int kc = q * KC;
+
+        float xh[RW][4];
+#pragma unroll
+        for (int x = 0; x < RW; ++x)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) xh[x][c] = 0.0f;
+#pragma unroll 8
+        for (int r = 0; r < RP; ++r) {
+            float rv[RW], cb[4];
+            VecLd<RW>::ld(rrT + r * TT + tr * RW, rv);
+            VecLd<4>::ld(ct + r * KC + tc * 4, cb);
+#pragma unroll
+            for (int x = 0; x < RW; ++x)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) xh[x][c] = fmaf(rv[x], cb[c], xh[x][c]);
+        }
+        float objf = 0.0f;
+#pragma unroll
+        for (int x = 0; x < RW; ++x) {
+            const int row = tr * RW + x;
+            const bool rv = (j0 + row) < J;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int col = tc + 8 * c;
+                const bool v = rv && (kc + col) < K;
+                float xv = xs[row * XS + col];
+                if (a.bkind == BK_IS) xv = fmaxf(xv, a.eps_x);
+                const float y = fmaxf(xh[x][c], a.eps);
+                float P, Q;
+                pq_powers(a.bkind, a.beta, xv, y, P, Q);
+                if (!v) { P = 0.0f; Q = 0.0f; }
+                if (OBJ && v) objf += dbeta_stable(a.bkind, a.beta, xv, y);
+                ps[row * XS + col] = P;
+                if (DEN) qs[row * XS + col] = Q;
+            }
+        }
+        if (OBJ) obj_acc += (double)objf;
+        __syncthreads();
+#pragma unroll 2
+        for (int c4 = 0; c4 < KC / 4; ++c4) {
+            float p[RW][4], qv[RW][4];
+#pragma unroll
+            for (int x = 0; x < RW; ++x) {
+                VecLd<4>::ld(ps + (tr * RW + x) * XS + c4 * 4, p[x]);
+                if (DEN) VecLd<4>::ld(qs + (tr * RW + x) * XS + c4 * 4, qv[x]);
+            }
+#pragma unroll
+            for (int cq = 0; cq < 4; ++cq) {
+                float cv[RG], dv[RG];
+                VecLd<RG>::ld(cn + (c4 * 4 + cq) * RS + tc * RG, cv);
+                if (DEN) VecLd<RG>::ld(cd + (c4 * 4 + cq) * RS + tc * RG, dv);
+#pragma unroll
+                for (int x = 0; x < RW; ++x)
+#pragma unroll
+                    for (int y = 0; y < RG; ++y) {
+                        W[x][y] = fmaf(p[x][cq], cv[y], W[x][y]);
+                        if (DEN) Wd[x][y] = fmaf(qv[x][cq], dv[y], Wd[x][y]);
+                    }
+            }
+        }
+        if (q == nch - 1) {
+            const int64_t rb = (int64_t)i * J + j0;
+#pragma unroll
+            for (int x = 0; x < RW; ++x) {
+                const int row = tr * RW + x;
+                if (j0 + row < J) {
+#pragma unroll
+                    for (int y = 0; y < RG; ++y) {
+                        ra.Wn[(rb + row) * RP + tc * RG + y] = W[x][y];
+                        if (DEN) ra.Wd[(rb + row) * RP + tc * RG + y] = Wd[x][y];
+                    }
+                }
+            }
+        }
+        __syncthreads();  // buffers of this iteration are restaged two iterations later
+        buf ^= 1;
+    }
+    cp_async_wait<0>();
+    if (OBJ) {
+        double v = obj_acc;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        __syncthreads();
+        if ((tid & 31) == 0) dred[tid >> 5] = v;
+        __syncthreads();
+        if (tid == 0) {
+            double t = 0.0;
+            for (int w = 0; w < NT / 32; ++w) t += dred[w];
+            a.obj[blockIdx.x] = t;
+        }
+    }
+}
+
+template <int RP, bool DEN, bool OBJ>
+static cudaError_t rows_launch_t(const RowsArgs &ra, int grid, cudaStream_t s) {
+    using namespace fp32;
+    using G = Geo<RP>;
+    const size_t floats = 2 * G::TJ * XS + G::TJ * XS + (DEN ? G::TJ * XS : 0) + RP * G::TT + 2 * RP * KC +
+                          2 * KC * G::RS + (DEN ? 2 * KC * G::RS : 0) + 2 * 32;
+    const size_t bytes = floats * sizeof(float);
+    auto k = tucker_rows_kernel<RP, DEN, OBJ>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    k<<<grid, NT, bytes, s>>>(ra);
+    return cudaGetLastError();
+}
+
+template <int RP>
+static cudaError_t rows_launch_rp(const RowsArgs &ra, int grid, bool obj, cudaStream_t s) {
+    return obj ? rows_launch_t<RP, true, true>(ra, grid, s) : rows_launch_t<RP, true, false>(ra, grid, s);
+}
+
+static cudaError_t rows_launch(int RP, const RowsArgs &ra, int grid, bool obj, cudaStream_t s) {
+    switch (RP) {
+        case 8: return rows_launch_rp<8>(ra, grid, obj, s);
+        case 16: return rows_launch_rp<16>(ra, grid, obj, s);
+        case 32: return rows_launch_rp<32>(ra, grid, obj, s);
+        case 64: return rows_launch_rp<64>(ra, grid, obj, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// ----------------------------------------------------------------------------------
+// small elementwise kernels
+// ----------------------------------------------------------------------------------
+__global__ void mu_plain_kernel(const float *pre, const float *num, const float *den, int64_t n, float gamma,
+                                float eps, float *out) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const float ratio = __fdiv_rn(num[t], den[t]);
+    const float m = gamma == 1.0f ? ratio : (gamma == 0.5f ? sqrtf(ratio) : powf(ratio, gamma));
+    out[t] = fmaxf(pre[t] * m, eps);
+}
+
+__global__ void chi_kernel(const float *z, const float *zt, int64_t n, float beta, float *c1, float *c2) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    c1[t] = chi1_f(beta, z[t], zt[t]);
+    c2[t] = chi2_f(beta, z[t], zt[t]);
+}
+
+__global__ void pad_cols_kernel(const float *src, int rows, int cols, int ld, float *dst) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)rows * ld) return;
+    const int i = (int)(t / ld), c = (int)(t % ld);
+    dst[t] = c < cols ? src[(int64_t)i * cols + c] : 0.0f;
+}
+
+__global__ void unpad_cols_kernel(const float *src, int rows, int cols, int ld, float *dst) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)rows * cols) return;
+    const int i = (int)(t / cols), c = (int)(t % cols);
+    dst[t] = src[(int64_t)i * ld + c];
+}
+
+static unsigned nblk(int64_t n) { return (unsigned)((n + 255) / 256); }
+
+// ----------------------------------------------------------------------------------
+// orchestration
+// ----------------------------------------------------------------------------------
+namespace {
+
+struct Blocks {  // one Tucker parameter set on the device (A3 padded to RP columns)
+    float *G, *A1, *A2, *A3p;
+};
+
+struct TuckerWs {
+    int I1, I2, I3, J1, J2, J3, RP;
+    float *Brec, *Bn, *Bd;  // [I1*I2][RP]
+    float *GA1, *H;         // [I1][J2*J3], [I2][J1*J3]
+    float *Wn, *Wd;         // [I1*I2][RP]
+    float *Y;               // [I1][J2*J3]
+    float *num, *den;       // max(I_n*J_n, J1*J2*J3)
+    float *pn3, *pd3;       // mode-3 partials
+    double *obj;
+    Cp3Plan plan3;
+    int rows_grid, rows_is;
+    Blocks cur, ref, t1, t2;  // current, reference, chi1 and chi2 transforms
+};
+
+#define TK(call)                                                                   \
+    do {                                                                           \
+        cudaError_t e_ = (call);                                                   \
+        if (e_ != cudaSuccess) return ctx_fail(ctx, NTF_ERR_CUDA, cudaGetErrorString(e_)); \
+        ctx_count(ctx, 1);                                                         \
+    } while (0)
+
+int rank_pad(int R) { return R <= 8 ? 8 : R <= 16 ? 16 : R <= 32 ? 32 : 64; }
+
+float *wsf(ntf_ctx *ctx, const char *name, int64_t n, bool &ok) {
+    float *p = (float *)ctx_ws(ctx, name, sizeof(float) * (size_t)(n > 0 ? n : 1));
+    if (!p) ok = false;
+    return p;
+}
+
+// B3[i][j][c] = sum_b A2[j,b] sum_a A1[i,a] G[a,b,c], padded to RP columns (pad kept 0)
+int build_b3(ntf_ctx *ctx, TuckerWs &w, const Blocks &b, float *out, cudaStream_t st) {
+    TK(cudaMemsetAsync(out, 0, sizeof(float) * (size_t)w.I1 * w.I2 * w.RP, st));
+    Gemm g{};
+    g.A = b.A1; g.B = b.G; g.C = w.GA1;
+    g.M = w.I1; g.N = w.J2 * w.J3; g.K1 = w.J1; g.K2 = 1; g.batch = 1;
+    g.sam = w.J1; g.sak1 = 1; g.sbk1 = (int64_t)w.J2 * w.J3; g.sbn = 1; g.scm = (int64_t)w.J2 * w.J3; g.scn = 1;
+    TK(gemm(g, st));
+    Gemm h{};
+    h.A = b.A2; h.B = w.GA1; h.C = out;
+    h.M = w.I2; h.N = w.J3; h.K1 = w.J2; h.K2 = 1; h.batch = w.I1;
+    h.sab = 0; h.sam = w.J2; h.sak1 = 1;
+    h.sbb = (int64_t)w.J2 * w.J3; h.sbk1 = w.J3; h.sbn = 1;
+    h.scb = (int64_t)w.I2 * w.RP; h.scm = w.RP; h.scn = 1;
+    TK(gemm(h, st));
+    return NTF_OK;
+}
+
+Cp3Args base_args(const ntf_tensor *X, const TuckerWs &w, const ntf_opts &o, float beta) {
+    Cp3Args a{};
+    a.X = X->values;
+    a.I = w.I1; a.J = w.I2; a.K = w.I3;
+    a.bkind = beta_kind(beta);
+    a.beta = beta;
+    a.eps = (float)o.eps;
+    a.eps_x = (float)o.eps_x;
+    a.vec16 = (w.I3 % 4 == 0) && ((reinterpret_cast<uintptr_t>(X->values) & 15) == 0);
+    a.obj = w.obj;
+    return a;
+}
+
+// W (and Wd) from P, Q with third-factor columns n3 / d3; Xhat from rrow, A3rec.
+int rows_pass(ntf_ctx *ctx, TuckerWs &w, const ntf_tensor *X, const ntf_opts &o, float beta, const float *rrow,
+              const float *a3rec, const float *n3, const float *d3, bool obj, cudaStream_t st) {
+    RowsArgs ra{};
+    ra.a = base_args(X, w, o, beta);
+    ra.a.rrow = rrow;
+    ra.a.rec[2] = a3rec;
+    ra.a.num[2] = n3;
+    ra.a.den[2] = d3;
+    ra.Wn = w.Wn;
+    ra.Wd = w.Wd;
+    ra.n_is = w.rows_is;
+    TK(rows_launch(w.RP, ra, w.rows_grid, obj, st));
+    return NTF_OK;
+}
+
+// Num1 / Num2 / Pcore from W with the (possibly transformed) blocks b
+int contract_from_w(ntf_ctx *ctx, TuckerWs &w, int block, const Blocks &b, const float *W, float *out,
+                    cudaStream_t st) {
+    if (block == 0) {  // core: Y[i][b][c] = sum_j A2[j,b] W[i,j,c]; Pcore = sum_i A1[i,a] Y[i]
+        Gemm g{};
+        g.A = b.A2; g.B = W; g.C = w.Y;
+        g.M = w.J2; g.N = w.J3; g.K1 = w.I2; g.K2 = 1; g.batch = w.I1;
+        g.sam = 1; g.sak1 = w.J2;
+        g.sbb = (int64_t)w.I2 * w.RP; g.sbk1 = w.RP; g.sbn = 1;
+        g.scb = (int64_t)w.J2 * w.J3; g.scm = w.J3; g.scn = 1;
+        TK(gemm(g, st));
+        Gemm h{};
+        h.A = b.A1; h.B = w.Y; h.C = out;
+        h.M = w.J1; h.N = w.J2 * w.J3; h.K1 = w.I1; h.K2 = 1; h.batch = 1;
+        h.sam = 1; h.sak1 = w.J1; h.sbk1 = (int64_t)w.J2 * w.J3; h.sbn = 1;
+        h.scm = (int64_t)w.J2 * w.J3; h.scn = 1;
+        TK(gemm(h, st));
+    } else if (block == 1) {  // H[j][a][c] = sum_b A2[j,b] G[a,b,c]; Num1 = sum_{j,c} W H
+        Gemm g{};
+        g.A = b.A2; g.B = b.G; g.C = w.H;
+        g.M = w.I2; g.N = w.J3; g.K1 = w.J2; g.K2 = 1; g.batch = w.J1;
+        g.sam = w.J2; g.sak1 = 1;
+        g.sbb = (int64_t)w.J2 * w.J3; g.sbk1 = w.J3; g.sbn = 1;
+        g.scb = w.J3; g.scm = (int64_t)w.J1 * w.J3; g.scn = 1;
+        TK(gemm(g, st));
+        Gemm h{};
+        h.A = W; h.B = w.H; h.C = out;
+        h.M = w.I1; h.N = w.J1; h.K1 = w.I2; h.K2 = w.J3; h.batch = 1;
+        h.sam = (int64_t)w.I2 * w.RP; h.sak1 = w.RP; h.sak2 = 1;
+        h.sbk1 = (int64_t)w.J1 * w.J3; h.sbk2 = 1; h.sbn = w.J3;
+        h.scm = w.J1; h.scn = 1;
+        TK(gemm(h, st));
+    } else {  // GA1[i][b][c] = sum_a A1[i,a] G[a,b,c]; Num2 = sum_{i,c} W GA1
+        Gemm g{};
+        g.A = b.A1; g.B = b.G; g.C = w.GA1;
+        g.M = w.I1; g.N = w.J2 * w.J3; g.K1 = w.J1; g.K2 = 1; g.batch = 1;
+        g.sam = w.J1; g.sak1 = 1; g.sbk1 = (int64_t)w.J2 * w.J3; g.sbn = 1; g.scm = (int64_t)w.J2 * w.J3; g.scn = 1;
+        TK(gemm(g, st));
+        Gemm h{};
+        h.A = W; h.B = w.GA1; h.C = out;
+        h.M = w.I2; h.N = w.J2; h.K1 = w.I1; h.K2 = w.J3; h.batch = 1;
+        h.sam = w.RP; h.sak1 = (int64_t)w.I2 * w.RP; h.sak2 = 1;
+        h.sbk1 = (int64_t)w.J2 * w.J3; h.sbk2 = 1; h.sbn = w.J3;
+        h.scm = w.J2; h.scn = 1;
+        TK(gemm(h, st));
+    }
+    return NTF_OK;
+}
+
+int setup(ntf_ctx *ctx, const ntf_tensor *X, const int64_t *core_dims, bool jcomm, TuckerWs &w) {
+    w.I1 = (int)X->dims[0]; w.I2 = (int)X->dims[1]; w.I3 = (int)X->dims[2];
+    w.J1 = (int)core_dims[0]; w.J2 = (int)core_dims[1]; w.J3 = (int)core_dims[2];
+    w.RP = rank_pad(w.J3);
+    const int64_t IJ = (int64_t)w.I1 * w.I2, Jc = (int64_t)w.J1 * w.J2 * w.J3;
+    bool ok = true;
+    w.Brec = wsf(ctx, "tkBrec", IJ * w.RP, ok);
+    w.Bn = jcomm ? wsf(ctx, "tkBn", IJ * w.RP, ok) : w.Brec;
+    w.Bd = jcomm ? wsf(ctx, "tkBd", IJ * w.RP, ok) : w.Brec;
+    w.GA1 = wsf(ctx, "tkGA1", (int64_t)w.I1 * w.J2 * w.J3, ok);
+    w.H = wsf(ctx, "tkH", (int64_t)w.I2 * w.J1 * w.J3, ok);
+    w.Wn = wsf(ctx, "tkWn", IJ * w.RP, ok);
+    w.Wd = wsf(ctx, "tkWd", IJ * w.RP, ok);
+    w.Y = wsf(ctx, "tkY", (int64_t)w.I1 * w.J2 * w.J3, ok);
+    int64_t mx = Jc;
+    const int64_t In[3] = {w.I1, w.I2, w.I3}, Jn[3] = {w.J1, w.J2, w.J3};
+    for (int n = 0; n < 3; ++n) mx = mx > In[n] * Jn[n] ? mx : In[n] * Jn[n];
+    w.num = wsf(ctx, "tkNum", mx, ok);
+    w.den = wsf(ctx, "tkDen", mx, ok);
+    w.plan3 = cp3_plan(w.I1, w.I2, w.I3, w.RP, ctx_num_sms(ctx));
+    w.pn3 = wsf(ctx, "tkPn3", (int64_t)w.plan3.parts3 * w.I3 * w.RP, ok);
+    w.pd3 = wsf(ctx, "tkPd3", (int64_t)w.plan3.parts3 * w.I3 * w.RP, ok);
+    // rows pass grid: row tiles x slab splits, about one wave per SM
+    const int TJ = (w.RP == 64) ? 64 : 128;
+    const int n_jt = (w.I2 + TJ - 1) / TJ;
+    int is = (ctx_num_sms(ctx) + n_jt - 1) / n_jt;
+    if (is > w.I1) is = w.I1;
+    w.rows_is = is;
+    w.rows_grid = n_jt * is;
+    int gmax = w.rows_grid > w.plan3.grid ? w.rows_grid : w.plan3.grid;
+    w.obj = (double *)ctx_ws(ctx, "tkObj", sizeof(double) * (size_t)gmax);
+    if (!w.obj) ok = false;
+    const char *names[4][4] = {{"tkG", "tkA1", "tkA2", "tkA3"}, {"tkGt", "tkA1t", "tkA2t", "tkA3t"},
+                               {"tkG1", "tkA11", "tkA21", "tkA31"}, {"tkG2", "tkA12", "tkA22", "tkA32"}};
+    Blocks *bs[4] = {&w.cur, &w.ref, &w.t1, &w.t2};
+    for (int q = 0; q < (jcomm ? 4 : 1); ++q) {
+        bs[q]->G = wsf(ctx, names[q][0], Jc, ok);
+        bs[q]->A1 = wsf(ctx, names[q][1], (int64_t)w.I1 * w.J1, ok);
+        bs[q]->A2 = wsf(ctx, names[q][2], (int64_t)w.I2 * w.J2, ok);
+        bs[q]->A3p = wsf(ctx, names[q][3], (int64_t)w.I3 * w.RP, ok);
+    }
+    if (!ok) return ctx_fail(ctx, NTF_ERR_OOM, "Tucker workspace allocation failed");
+    return NTF_OK;
+}
+
+int load_blocks(ntf_ctx *ctx, TuckerWs &w, const float *core, const float *const *A, Blocks &b, cudaStream_t st) {
+    const int64_t Jc = (int64_t)w.J1 * w.J2 * w.J3;
+    TK(cudaMemcpyAsync(b.G, core, sizeof(float) * Jc, cudaMemcpyDeviceToDevice, st));
+    TK(cudaMemcpyAsync(b.A1, A[0], sizeof(float) * w.I1 * w.J1, cudaMemcpyDeviceToDevice, st));
+    TK(cudaMemcpyAsync(b.A2, A[1], sizeof(float) * w.I2 * w.J2, cudaMemcpyDeviceToDevice, st));
+    pad_cols_kernel<<<nblk((int64_t)w.I3 * w.RP), 256, 0, st>>>(A[2], w.I3, w.J3, w.RP, b.A3p);
+    TK(cudaGetLastError());
+    return NTF_OK;
+}
+
+int copy_blocks(ntf_ctx *ctx, TuckerWs &w, const Blocks &s, Blocks &d, cudaStream_t st) {
+    const int64_t Jc = (int64_t)w.J1 * w.J2 * w.J3;
+    TK(cudaMemcpyAsync(d.G, s.G, sizeof(float) * Jc, cudaMemcpyDeviceToDevice, st));
+    TK(cudaMemcpyAsync(d.A1, s.A1, sizeof(float) * w.I1 * w.J1, cudaMemcpyDeviceToDevice, st));
+    TK(cudaMemcpyAsync(d.A2, s.A2, sizeof(float) * w.I2 * w.J2, cudaMemcpyDeviceToDevice, st));
+    TK(cudaMemcpyAsync(d.A3p, s.A3p, sizeof(float) * w.I3 * w.RP, cudaMemcpyDeviceToDevice, st));
+    return NTF_OK;
+}
+
+// block update: out = max(pre * (num/den)^gamma, eps), with chi transforms when jcomm
+int apply_mu(ntf_ctx *ctx, TuckerWs &w, const float *pre, float *out, int64_t n, float beta, float eps,
+             const float *ref, float *c1, float *c2, cudaStream_t st) {
+    mu_plain_kernel<<<nblk(n), 256, 0, st>>>(pre, w.num, w.den, n, mu_gamma(beta), eps, out);
+    TK(cudaGetLastError());
+    if (c1) {
+        chi_kernel<<<nblk(n), 256, 0, st>>>(out, ref, n, beta, c1, c2);
+        TK(cudaGetLastError());
+    }
+    return NTF_OK;
+}
+
+int mode3_pass(ntf_ctx *ctx, TuckerWs &w, const ntf_tensor *X, const ntf_opts &o, float beta, const float *rrow,
+               const float *a3rec, const float *nrow, const float *drow, bool obj, cudaStream_t st) {
+    Cp3Args a = base_args(X, w, o, beta);
+    a.rrow = rrow;
+    a.nrow = nrow;
+    a.drow = drow;
+    for (int m = 0; m < 3; ++m) a.rec[m] = a.num[m] = a.den[m] = a3rec;
+    a.n_jt = w.plan3.n_jt;
+    a.n_kb = w.plan3.n_kb;
+    a.n_is = w.plan3.n_is;
+    a.p3n = w.pn3;
+    a.p3d = w.pd3;
+    TK(cp3_launch(w.plan3, a, PM_M3 | (obj ? 0 : 0), 1, st));
+    return NTF_OK;
+}
+
+}  // namespace
+
+int tucker_run(ntf_ctx *ctx, const ntf_tensor *X, float beta, const int64_t *core_dims, float *core,
+               float *const *factors, const ntf_opts &o, double *objective_dev, cudaStream_t st, bool jcomm) {
+    if (!core_dims || !core || !factors) return ctx_fail(ctx, NTF_ERR_ARG, "core_dims, core and factors are required");
+    if (X->order != 3) return ctx_fail(ctx, NTF_ERR_UNSUPPORTED, "Tucker kernels implement order 3");
+    for (int n = 0; n < 3; ++n) {
+        if (!factors[n]) return ctx_fail(ctx, NTF_ERR_ARG, "factor is NULL");
+        if (core_dims[n] < 1 || core_dims[n] > 64)
+            return ctx_fail(ctx, NTF_ERR_UNSUPPORTED, "core dimensions must lie in 1..64");
+        if (core_dims[n] > X->dims[n]) return ctx_fail(ctx, NTF_ERR_SHAPE, "core dimension exceeds tensor dimension");
+    }
+    TuckerWs w{};
+    int rc = setup(ctx, X, core_dims, jcomm, w);
+    if (rc) return rc;
+    const float eps = (float)o.eps;
+    const int64_t Jc = (int64_t)w.J1 * w.J2 * w.J3;
+    const int64_t n1 = (int64_t)w.I1 * w.J1, n2 = (int64_t)w.I2 * w.J2, n3p = (int64_t)w.I3 * w.RP;
+    rc = load_blocks(ctx, w, core, factors, w.cur, st);
+    if (rc) return rc;
+    const Cp3Args probe = base_args(X, w, o, beta);
+    (void)probe;
+
+    if (!jcomm) {
+        // ---- core block (the pass also yields D_beta of the incoming iterate) ----
+        if ((rc = build_b3(ctx, w, w.cur, w.Brec, st))) return rc;
+        if ((rc = rows_pass(ctx, w, X, o, beta, w.Brec, w.cur.A3p, w.cur.A3p, w.cur.A3p, objective_dev != nullptr, st)))
+            return rc;
+        if (objective_dev) TK(reduce_objective(w.obj, w.rows_grid, 0.0, objective_dev, st));
+        if ((rc = contract_from_w(ctx, w, 0, w.cur, w.Wn, w.num, st))) return rc;
+        if ((rc = contract_from_w(ctx, w, 0, w.cur, w.Wd, w.den, st))) return rc;
+        if ((rc = apply_mu(ctx, w, w.cur.G, w.cur.G, Jc, beta, eps, nullptr, nullptr, nullptr, st))) return rc;
+        // ---- modes 1 and 2 ----
+        for (int blk = 1; blk <= 2; ++blk) {
+            if ((rc = build_b3(ctx, w, w.cur, w.Brec, st))) return rc;
+            if ((rc = rows_pass(ctx, w, X, o, beta, w.Brec, w.cur.A3p, w.cur.A3p, w.cur.A3p, false, st))) return rc;
+            if ((rc = contract_from_w(ctx, w, blk, w.cur, w.Wn, w.num, st))) return rc;
+            if ((rc = contract_from_w(ctx, w, blk, w.cur, w.Wd, w.den, st))) return rc;
+            float *A = blk == 1 ? w.cur.A1 : w.cur.A2;
+            if ((rc = apply_mu(ctx, w, A, A, blk == 1 ? n1 : n2, beta, eps, nullptr, nullptr, nullptr, st))) return rc;
+        }
+        // ---- mode 3 ----
+        if ((rc = build_b3(ctx, w, w.cur, w.Brec, st))) return rc;
+        if ((rc = mode3_pass(ctx, w, X, o, beta, w.Brec, w.cur.A3p, w.Brec, w.Brec, false, st))) return rc;
+        MuEpiArgs e{};
+        e.pn = w.pn3; e.pd = w.pd3; e.n_parts = w.plan3.parts3; e.rows = w.I3; e.RP = w.RP; e.R = w.J3;
+        e.pre = w.cur.A3p; e.out = w.cur.A3p; e.beta = beta; e.gamma = mu_gamma(beta); e.eps = eps;
+        TK(mu_epilogue(e, st));
+    } else {
+        if ((rc = copy_blocks(ctx, w, w.cur, w.ref, st))) return rc;
+        if ((rc = copy_blocks(ctx, w, w.cur, w.t1, st))) return rc;
+        if ((rc = copy_blocks(ctx, w, w.cur, w.t2, st))) return rc;
+        // Xtilde rows from the reference, fixed for the whole outer iteration
+        if ((rc = build_b3(ctx, w, w.ref, w.Brec, st))) return rc;
+        for (int l = 0; l < o.inner_L; ++l) {
+            // W from Ptilde with chi1(A3), Wd from Qtilde with chi2(A3): A3 changes only at the
+            // end of the sweep, so one pass serves the core and modes 1 and 2
+            const bool obj = (l == 0) && objective_dev;
+            if ((rc = rows_pass(ctx, w, X, o, beta, w.Brec, w.ref.A3p, w.t1.A3p, w.t2.A3p, obj, st))) return rc;
+            if (obj) TK(reduce_objective(w.obj, w.rows_grid, 0.0, objective_dev, st));
+            // core: Num with A_(1) of modes 1, 2 (and W), Den with A_(2)
+            if ((rc = contract_from_w(ctx, w, 0, w.t1, w.Wn, w.num, st))) return rc;
+            if ((rc = contract_from_w(ctx, w, 0, w.t2, w.Wd, w.den, st))) return rc;
+            if ((rc = apply_mu(ctx, w, w.ref.G, w.cur.G, Jc, beta, eps, w.ref.G, w.t1.G, w.t2.G, st))) return rc;
+            for (int blk = 1; blk <= 2; ++blk) {
+                if ((rc = contract_from_w(ctx, w, blk, w.t1, w.Wn, w.num, st))) return rc;
+                if ((rc = contract_from_w(ctx, w, blk, w.t2, w.Wd, w.den, st))) return rc;
+                float *A = blk == 1 ? w.cur.A1 : w.cur.A2;
+                const float *At = blk == 1 ? w.ref.A1 : w.ref.A2;
+                float *c1 = blk == 1 ? w.t1.A1 : w.t1.A2;
+                float *c2 = blk == 1 ? w.t2.A1 : w.t2.A2;
+                if ((rc = apply_mu(ctx, w, At, A, blk == 1 ? n1 : n2, beta, eps, At, c1, c2, st))) return rc;
+            }
+            // mode 3: rows of the transformed partial tensors
+            if ((rc = build_b3(ctx, w, w.t1, w.Bn, st))) return rc;
+            if ((rc = build_b3(ctx, w, w.t2, w.Bd, st))) return rc;
+            if ((rc = mode3_pass(ctx, w, X, o, beta, w.Brec, w.ref.A3p, w.Bn, w.Bd, false, st))) return rc;
+            MuEpiArgs e{};
+            e.pn = w.pn3; e.pd = w.pd3; e.n_parts = w.plan3.parts3; e.rows = w.I3; e.RP = w.RP; e.R = w.J3;
+            e.pre = w.ref.A3p; e.out = w.cur.A3p; e.ref = w.ref.A3p; e.chi1_out = w.t1.A3p; e.chi2_out = w.t2.A3p;
+            e.beta = beta; e.gamma = mu_gamma(beta); e.eps = eps;
+            TK(mu_epilogue(e, st));
+        }
+    }
+    // write back
+    TK(cudaMemcpyAsync(core, w.cur.G, sizeof(float) * Jc, cudaMemcpyDeviceToDevice, st));
+    TK(cudaMemcpyAsync(factors[0], w.cur.A1, sizeof(float) * n1, cudaMemcpyDeviceToDevice, st));
+    TK(cudaMemcpyAsync(factors[1], w.cur.A2, sizeof(float) * n2, cudaMemcpyDeviceToDevice, st));
+    unpad_cols_kernel<<<nblk((int64_t)w.I3 * w.J3), 256, 0, st>>>(w.cur.A3p, w.I3, w.J3, w.RP, factors[2]);
+    TK(cudaGetLastError());
+    (void)n3p;
+    return NTF_OK;
+}
+
+int tucker_beta_div(ntf_ctx *ctx, const ntf_tensor *X, float beta, const int64_t *core_dims, const float *core,
+                    const float *const *factors, const ntf_opts &o, double *out_dev, cudaStream_t st) {
+    if (!core_dims || !core || !factors) return ctx_fail(ctx, NTF_ERR_ARG, "core_dims, core and factors are required");
+    if (X->order != 3) return ctx_fail(ctx, NTF_ERR_UNSUPPORTED, "Tucker kernels implement order 3");
+    for (int n = 0; n < 3; ++n) {
+        if (!factors[n]) return ctx_fail(ctx, NTF_ERR_ARG, "factor is NULL");
+        if (core_dims[n] < 1 || core_dims[n] > 64)
+            return ctx_fail(ctx, NTF_ERR_UNSUPPORTED, "core dimensions must lie in 1..64");
+        if (core_dims[n] > X->dims[n]) return ctx_fail(ctx, NTF_ERR_SHAPE, "core dimension exceeds tensor dimension");
+    }
+    TuckerWs w{};
+    int rc = setup(ctx, X, core_dims, false, w);
+    if (rc) return rc;
+    if ((rc = load_blocks(ctx, w, core, factors, w.cur, st))) return rc;
+    if ((rc = build_b3(ctx, w, w.cur, w.Brec, st))) return rc;
+    Cp3Args a = base_args(X, w, o, beta);
+    a.rrow = w.Brec;
+    for (int m = 0; m < 3; ++m) a.rec[m] = a.num[m] = a.den[m] = w.cur.A3p;
+    a.n_jt = w.plan3.n_jt;
+    a.n_kb = w.plan3.n_kb;
+    a.n_is = w.plan3.n_is;
+    TK(cp3_launch(w.plan3, a, PM_OBJ, 0, st));
+    TK(reduce_objective(w.obj, w.plan3.grid, 0.0, out_dev, st));
+    return NTF_OK;
+}
+
+void tucker_release(ntf_ctx *) {}
+
+}  // namespace ntf

@@ -96,6 +96,12 @@ int64_t ntf_launch_count(const ntf_ctx *ctx);
  * during stream capture. */
 int ntf_set_pass_timing(ntf_ctx *ctx, int enable);
 int ntf_pass_timing(ntf_ctx *ctx, double *total_ms, int64_t *launches);
+/* Device-side status of the context's kernels.  Kernels whose waits are bounded (the
+ * tensor-core passes wait on TMA and MMA completion barriers) set a status word in device
+ * memory instead of hanging when a wait runs out.  This call synchronizes `stream`, reads
+ * and clears that word, and returns NTF_OK or NTF_ERR_TIMEOUT (the results of the calls
+ * since the last check are then invalid). */
+int ntf_device_status(ntf_ctx *ctx, void *stream);
 
 /* One B-CoMM sweep for CP (Algorithm 1; Theorem "CP block multiplicative update";
  * CPContr of Section 6.1): for n = 1..N in order, rebuild Xhat from the current

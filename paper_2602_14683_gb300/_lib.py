@@ -50,6 +50,7 @@ _sig = {
     "ntf_launch_count": (C.c_int64, [_P]),
     "ntf_set_pass_timing": (C.c_int, [_P, C.c_int]),
     "ntf_pass_timing": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
+    "ntf_device_status": (C.c_int, [_P, _P]),
     "ntf_cp_mu_sweep": (C.c_int, [_P, C.POINTER(Tensor), C.c_float, C.c_int, C.POINTER(_P), C.POINTER(Opts), _P, _P]),
     "ntf_tucker_mu_sweep": (C.c_int, [_P, C.POINTER(Tensor), C.c_float, C.POINTER(C.c_int64), _P, C.POINTER(_P),
                                       C.POINTER(Opts), _P, _P]),
@@ -102,6 +103,11 @@ class Context:
         n = C.c_int64()
         self.check(_lib.ntf_pass_timing(self.h, C.byref(ms), C.byref(n)))
         return ms.value, n.value
+
+    def device_status(self, stream=None):
+        """Synchronizes the stream and raises NtfError(NTF_ERR_TIMEOUT) if a bounded
+        device-side wait gave up since the last check."""
+        self.check(_lib.ntf_device_status(self.h, _stream(stream)))
 
     def check(self, rc):
         if rc != NTF_OK:

@@ -13,11 +13,12 @@ cudaError_t cp3_launch_fp32_r64(const Cp3Plan &, const Cp3Args &, int, int, cuda
 // the split minimises waves * (ceil(I / n_is) + c0), where c0 = 4 slab-equivalents is
 // the per-CTA cost of staging factor blocks and writing partial sums; ties go to fewer
 // CTAs.
-Cp3Plan cp3_plan(int I, int J, int K, int RP, int num_sms) {
+Cp3Plan cp3_plan(int I, int J, int K, int RP, int num_sms, int kb) {
     Cp3Plan p{};
+    p.tc = kb == 128;
     p.RP = RP;
     p.TJ = (RP == 64) ? 64 : 128;
-    p.KB = 64;
+    p.KB = kb;
     p.n_jt = (J + p.TJ - 1) / p.TJ;
     p.n_kb = (K + p.KB - 1) / p.KB;
     const int base = p.n_jt * p.n_kb;

@@ -1,0 +1,626 @@
+// Fused dense 3-way CP pass on the 5th-generation tensor cores (tcgen05, sm_103a).
+//
+// Same computation and partial-sum layouts as the FP32 pass (CPContr^(n) of P and Q,
+// Section 6.1; Theorem "CP block multiplicative update"; Xhat never stored).  A CTA of
+// 256 threads owns a tile of 128 rows j, a block of 128 columns k and a range of slabs i,
+// walked as a sequence of 64-column chunks (two per slab).  Thread (warp w, lane l) owns
+// tile row 32 (w % 4) + l (its TMEM lane) and the column half w / 4 of each chunk.
+//
+// Per chunk n (slab i, columns k0 + 64 q):
+//   TMA       X chunk (128 x 64 FP32) into a 2- or 3-stage ring, issued that far ahead;
+//   GEMM1     Xhat = R C^T on 3xTF32 (hi/lo parts rounded to nearest; hi*hi + hi*lo +
+//             lo*hi), M128 N64 K32, into one of two TMEM buffers, issued one chunk ahead;
+//   epilogue  Xhat from TMEM (tcgen05.ld), X from shared memory, P = X Y^(beta-2),
+//             Q = Y^(beta-1) (Y = max(Xhat, eps)) and the objective terms in FP32
+//             registers; P, Q stored once as BF16 tiles [rows][64 cols];
+//   GEMM2     rows: W[j][r] += sum_k P[j][k] Cn[k][r]   (A = P K-major, B = Cn^T)
+//             cols: N3^T[r][k] += sum_j KRn^T[r][j] P[j][k]  (A = KRn^T with the rank
+//             padded to M = 128, B = the same P tile read MN-major),
+//             BF16 operands, FP32 accumulation in TMEM, overlapping the next epilogue.
+// At each slab boundary mode 1 reduces sum_j W[j][r] Bn[j][r] (shuffle reduce-scatter)
+// and mode 2 accumulates An[i][r] W[j][r] per row.  One thread issues TMA and MMAs;
+// completion is tracked with mbarriers whose waits are bounded: on timeout the kernel sets
+// the context's status word, waits (bounded) for its copies and MMAs, frees its TMEM and
+// returns.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include "ntf_internal.h"
+
+namespace ntf {
+namespace tc {
+
+constexpr int NT = 256;
+constexpr int ROWS = 128;  // tile rows
+constexpr int KBLK = 128;  // columns per CTA block
+constexpr int CH = 64;     // columns per chunk
+constexpr int RP = 32;
+
+struct Layout {
+    int x, p, q, r, rl, c, cl, cnt, cdt, knt, kdt, misc, total;
+    int ns;  // X stages
+    int np;  // P / Q buffers
+};
+
+// 1024-aligned regions.  The column contraction reads KRn^T as an M = 128 operand whose
+// rows 32..127 are padding: those rows only feed accumulator rows that are never read, so
+// only the 32 real rows are stored (two 4 KB K-atoms) and the padding reads fall on the
+// 16 KB that follow (the Crec / R tiles), which stay inside the allocation.
+__host__ __device__ constexpr int layout_bytes(bool rows, bool m3, bool den, int ns, int np) {
+    return ns * 32768 + np * 16384 * (den ? 2 : 1) + 4 * 16384 + (rows ? 8192 : 0) + ((rows && den) ? 8192 : 0) +
+           (m3 ? 8192 : 0) + ((m3 && den) ? 8192 : 0) + 4096 + 1024;
+}
+
+__host__ __device__ constexpr Layout make_layout(bool rows, bool m3, bool den) {
+    Layout L{};
+    constexpr int kMax = 232448;  // opt-in shared memory per CTA
+    L.ns = 2;
+    L.np = 1;
+    if (layout_bytes(rows, m3, den, 2, 2) <= kMax) L.np = 2;
+    if (layout_bytes(rows, m3, den, 3, L.np) <= kMax) L.ns = 3;
+    int o = 0;
+    L.x = o; o += L.ns * 32768;
+    L.p = o; o += L.np * 16384;
+    L.q = o; o += den ? L.np * 16384 : 0;
+    L.knt = o; o += m3 ? 8192 : 0;            // padding rows read the C tiles below
+    L.c = o; o += 16384;
+    L.cl = o; o += 16384;
+    L.kdt = o; o += (m3 && den) ? 8192 : 0;   // padding rows read the R tiles below
+    L.r = o; o += 16384;
+    L.rl = o; o += 16384;
+    L.cnt = o; o += rows ? 8192 : 0;
+    L.cdt = o; o += (rows && den) ? 8192 : 0;
+    L.misc = o; o += 4096;
+    L.total = o + 1024;  // alignment slack of the dynamic base
+    return L;
+}
+
+__device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor, 128-byte swizzle: lbo = stride between 128-byte atoms
+// along the contiguous dimension (MN-major only), sbo = stride between 8-row groups
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo = 16, uint32_t sbo = 1024) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFF);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+// instruction descriptors (D = F32, M = 128): TF32 K-major; BF16 with B K- or MN-major
+__device__ __forceinline__ uint32_t idesc_tf32(int N) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+__device__ __forceinline__ uint32_t idesc_bf16(int N, bool b_mn) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((b_mn ? 1u : 0u) << 16) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(128 >> 4) << 24);
+}
+__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+                 :: "r"(d), "l"(a), "l"(b), "r"(id), "r"(acc));
+}
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                 :: "r"(d), "l"(a), "l"(b), "r"(id), "r"(acc));
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" :: "r"(bar) : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t addr, float *v) {
+    uint32_t r[32];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+                   "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+                   "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                 : "r"(addr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+    for (int c = 0; c < 32; ++c) v[c] = __uint_as_float(r[c]);
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t addr, float *v) {
+    uint32_t r[16];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                 : "r"(addr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+    for (int c = 0; c < 16; ++c) v[c] = __uint_as_float(r[c]);
+}
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+constexpr int WAIT_LIMIT = 1 << 26;  // polls (seconds at worst) before a wait gives up
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
+    for (int it = 0; it < WAIT_LIMIT; ++it) {
+        uint32_t ok;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(ok) : "r"(bar), "r"(phase) : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ float tf32_rna(float v) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(r) : "f"(v));
+    return __uint_as_float(r);
+}
+
+// element offsets inside 128-byte swizzled atoms (8-row period)
+__device__ __forceinline__ int swf(int row, int k) { return row * 32 + ((((k >> 2) ^ (row & 7)) << 2) | (k & 3)); }
+__device__ __forceinline__ int swh(int row, int k) { return row * 64 + ((((k >> 3) ^ (row & 7)) << 3) | (k & 7)); }
+
+__device__ __forceinline__ void tma_2d(const CUtensorMap *map, uint32_t dst, uint32_t bar, int x, int y) {
+    asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n"
+                 :: "r"(dst), "l"(map), "r"(x), "r"(y), "r"(bar) : "memory");
+}
+__device__ __forceinline__ void expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" :: "r"(bar), "r"(bytes) : "memory");
+}
+
+// P and Q with a compile-time beta class; P and Q are stored in BF16, so single-MUFU forms
+template <int BK>
+__device__ __forceinline__ void pq_fast(float beta, float x, float y, float &P, float &Q) {
+    if (BK == BK_IS) {
+        const float r = __fdividef(1.0f, y);
+        Q = r;
+        P = x * r * r;
+    } else if (BK == BK_HALF) {
+        const float s = rsqrtf(y);
+        Q = s;
+        P = x * s * s * s;
+    } else if (BK == BK_KL) {
+        P = __fdividef(x, y);
+        Q = 1.0f;
+    } else if (BK == BK_THREEHALF) {
+        const float s = rsqrtf(y);
+        Q = y * s;
+        P = x * s;
+    } else {
+        Q = __powf(y, beta - 1.0f);
+        P = __fdividef(x * Q, y);
+    }
+}
+
+// sum over the 32 lanes of v[k] for k < 16: afterwards lane l < 16 holds the sum for k = l
+__device__ __forceinline__ float reduce_scatter16(float v[16]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 8; k >= 1; k >>= 1) {
+        const bool upper = (lane & k) != 0;
+#pragma unroll
+        for (int q = 0; q < k; ++q) {
+            const float send = upper ? v[q] : v[q + k];
+            const float keep = upper ? v[q + k] : v[q];
+            v[q] = keep + __shfl_xor_sync(0xffffffffu, send, k);
+        }
+    }
+    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 16);
+}
+
+template <int MS, int BK>
+__global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUtensorMap xmap, const Cp3Args a) {
+    constexpr bool DEN = BK != BK_KL;
+    constexpr bool M1 = (MS & PM_M1) != 0, M2 = (MS & PM_M2) != 0, M3 = (MS & PM_M3) != 0;
+    constexpr bool OBJ = (MS & PM_OBJ) != 0, RW = M1 || M2;
+    constexpr Layout L = make_layout(RW, M3, DEN);
+    constexpr int NP = L.np, NS = L.ns;
+    extern __shared__ __align__(1024) uint8_t smraw[];
+    uint8_t *sm = (uint8_t *)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
+    const float *Xs = (const float *)(sm + L.x);
+    __nv_bfloat16 *Ps = (__nv_bfloat16 *)(sm + L.p);
+    __nv_bfloat16 *Qs = (__nv_bfloat16 *)(sm + L.q);
+    float *Rs = (float *)(sm + L.r);
+    float *Rl = (float *)(sm + L.rl);
+    float *Cs = (float *)(sm + L.c);
+    float *Cl = (float *)(sm + L.cl);
+    __nv_bfloat16 *CnT = (__nv_bfloat16 *)(sm + L.cnt);
+    __nv_bfloat16 *CdT = (__nv_bfloat16 *)(sm + L.cdt);
+    __nv_bfloat16 *KnT = (__nv_bfloat16 *)(sm + L.knt);
+    __nv_bfloat16 *KdT = (__nv_bfloat16 *)(sm + L.kdt);
+    uint64_t *bar_x = (uint64_t *)(sm + L.misc);  // [NS]
+    uint64_t *bar_g1 = bar_x + 3;                  // [2]
+    uint64_t *bar_g2 = bar_x + 5;                  // [2]
+    uint32_t *tslot = (uint32_t *)(bar_x + 7);
+    float *red = (float *)(sm + L.misc + 64);          // [4 quarters][32] (+[4][32] DEN)
+    double *dred = (double *)(sm + L.misc + 64 + 1024);  // [8]
+    float *srow = (float *)(sm + L.misc + 2048);          // [3 slabs][rec0, num0, den0][32]
+
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int quarter = warp & 3, half = warp >> 2;
+    const int row = 32 * quarter + lane;  // tile row = TMEM lane
+    int b = blockIdx.x;
+    const int is = b % a.n_is;
+    b /= a.n_is;
+    const int kb = b % a.n_kb;
+    const int jt = b / a.n_kb;
+    const int i0 = (int)((int64_t)is * a.I / a.n_is);
+    const int i1 = (int)((int64_t)(is + 1) * a.I / a.n_is);
+    const int J = a.J, K = a.K;
+    const int j0 = jt * ROWS, k0 = kb * KBLK;
+    const int j = j0 + row;
+    const bool jv = j < J;
+    const int NC = 2 * (i1 - i0);
+    const int r0 = 16 * half;  // this thread's rank slice for slab operands and folds
+
+    // ---- per-CTA constants ---------------------------------------------------------------
+    float brec[16], bn[16], bd[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+        brec[r] = jv ? __ldg(a.rec[1] + (int64_t)j * RP + r0 + r) : 0.0f;
+        bn[r] = (jv && (M1 || M3)) ? __ldg(a.num[1] + (int64_t)j * RP + r0 + r) : 0.0f;
+        bd[r] = (jv && (M1 || M3) && DEN) ? __ldg(a.den[1] + (int64_t)j * RP + r0 + r) : 0.0f;
+    }
+    {
+        // Crec block (hi / lo), TF32 K-major [128 cols][32 rank]; thread: column `row`, rank slice r0
+        const int kc = k0 + row;
+        const bool kv = kc < K;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float h[4], l[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float v = kv ? __ldg(a.rec[2] + (int64_t)kc * RP + r0 + 4 * q + e) : 0.0f;
+                h[e] = tf32_rna(v);
+                l[e] = tf32_rna(v - h[e]);
+            }
+            *reinterpret_cast<float4 *>(Cs + swf(row, r0 + 4 * q)) = make_float4(h[0], h[1], h[2], h[3]);
+            *reinterpret_cast<float4 *>(Cl + swf(row, r0 + 4 * q)) = make_float4(l[0], l[1], l[2], l[3]);
+        }
+        if (RW) {
+            // Cn^T, Cd^T: BF16 [32 rank][128 cols] as two 64-column atoms; thread: column `row`
+#pragma unroll
+            for (int r = 0; r < 16; ++r) {
+                const int rr = r0 + r;
+                CnT[(row >> 6) * 2048 + swh(rr, row & 63)] =
+                    __float2bfloat16_rn(kv ? __ldg(a.num[2] + (int64_t)kc * RP + rr) : 0.0f);
+                if (DEN)
+                    CdT[(row >> 6) * 2048 + swh(rr, row & 63)] =
+                        __float2bfloat16_rn(kv ? __ldg(a.den[2] + (int64_t)kc * RP + rr) : 0.0f);
+            }
+        }
+    }
+    if (t == 0) {
+        for (int q = 0; q < 7; ++q) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" :: "r"(su32(bar_x + q)));
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
+    }
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;\n" :: "r"(su32(tslot)));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tslot;
+    const uint32_t lane_off = (uint32_t)(32 * quarter) << 16;
+    const uint32_t t_d1 = tmem;          // 2 x 64 columns
+    const uint32_t t_w = tmem + 128;     // 32
+    const uint32_t t_wd = tmem + 160;    // 32
+    const uint32_t t_n3 = tmem + 256;    // 128
+    const uint32_t t_n3d = tmem + 384;   // 128
+
+    // the first-mode factor rows of slab i (reconstruction, numerator, denominator) are
+    // staged once in shared memory, in a ring of three slabs
+    auto stage_rows = [&](int i) {
+        if (t < 96) {
+            const int f = t >> 5, r = t & 31;
+            const float *src = f == 0 ? a.rec[0] : f == 1 ? a.num[0] : a.den[0];
+            srow[(i % 3) * 96 + t] = (f == 2 && !DEN) ? 0.0f : __ldg(src + (int64_t)i * RP + r);
+        }
+    };
+    auto slab_rows = [&](int i) {  // R (hi/lo) for slab i: thread writes row `row`, rank slice r0
+        const float *ar = srow + (i % 3) * 96 + r0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float h[4], l[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float v = ar[4 * q + e] * brec[4 * q + e];
+                h[e] = tf32_rna(v);
+                l[e] = tf32_rna(v - h[e]);
+            }
+            *reinterpret_cast<float4 *>(Rs + swf(row, r0 + 4 * q)) = make_float4(h[0], h[1], h[2], h[3]);
+            *reinterpret_cast<float4 *>(Rl + swf(row, r0 + 4 * q)) = make_float4(l[0], l[1], l[2], l[3]);
+        }
+    };
+    auto slab_kr = [&](int i) {  // KRn^T / KRd^T rows r0..r0+15, column `row` (tile row)
+        const float *an = srow + (i % 3) * 96 + 32 + r0, *ad = an + 32;
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+            const int rr = r0 + r;
+            KnT[(row >> 6) * 2048 + swh(rr, row & 63)] = __float2bfloat16_rn(an[r] * bn[r]);
+            if (DEN) KdT[(row >> 6) * 2048 + swh(rr, row & 63)] = __float2bfloat16_rn(ad[r] * bd[r]);
+        }
+    };
+    auto issue_x = [&](int n) {  // TMA of chunk n into stage n % NS
+        const int i = i0 + (n >> 1), q = n & 1;
+        const uint32_t bar = su32(bar_x + (n % NS));
+        const uint32_t dst = su32(Xs) + (n % NS) * 32768;
+        expect_tx(bar, 32768);
+        tma_2d(&xmap, dst, bar, k0 + CH * q, i * J + j0);
+        tma_2d(&xmap, dst + 16384, bar, k0 + CH * q + 32, i * J + j0);
+    };
+    auto issue_g1 = [&](int n) {  // GEMM1 of chunk n (3xTF32) into D1[n % 2]
+        const int q = n & 1;
+        const uint32_t d = t_d1 + 64 * (n & 1);
+        const uint32_t id = idesc_tf32(CH);
+        const uint32_t cb = su32(Cs) + q * 8192, cbl = su32(Cl) + q * 8192;
+#pragma unroll
+        for (int s = 0; s < 4; ++s) mma_tf32(d, sdesc(su32(Rl) + s * 32), sdesc(cb + s * 32), id, s > 0);
+#pragma unroll
+        for (int s = 0; s < 4; ++s) mma_tf32(d, sdesc(su32(Rs) + s * 32), sdesc(cbl + s * 32), id, 1);
+#pragma unroll
+        for (int s = 0; s < 4; ++s) mma_tf32(d, sdesc(su32(Rs) + s * 32), sdesc(cb + s * 32), id, 1);
+        mma_commit(su32(bar_g1 + (n & 1)));
+    };
+    auto issue_g2 = [&](int n) {  // contractions of chunk n from P[n % NP]
+        const int q = n & 1;
+        const uint32_t pb = su32(Ps) + (n % NP) * 16384, qb = su32(Qs) + (n % NP) * 16384;
+        if (RW) {
+            const uint32_t id = idesc_bf16(RP, false);
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+                mma_bf16(t_w, sdesc(pb + s * 32), sdesc(su32(CnT) + q * 4096 + s * 32), id, (q > 0 || s > 0) ? 1u : 0u);
+                if (DEN) mma_bf16(t_wd, sdesc(qb + s * 32), sdesc(su32(CdT) + q * 4096 + s * 32), id, (q > 0 || s > 0) ? 1u : 0u);
+            }
+        }
+        if (M3) {
+            const uint32_t id = idesc_bf16(CH, true);
+#pragma unroll
+            for (int s = 0; s < 8; ++s) {
+                const uint32_t ao = (s >> 2) * 4096 + (s & 3) * 32;
+                const uint32_t acc = (n >= 2 || s > 0) ? 1u : 0u;
+                mma_bf16(t_n3 + 64 * q, sdesc(su32(KnT) + ao), sdesc(pb + s * 2048, 16384, 1024), id, acc);
+                if (DEN) mma_bf16(t_n3d + 64 * q, sdesc(su32(KdT) + ao), sdesc(qb + s * 2048, 16384, 1024), id, acc);
+            }
+        }
+        mma_commit(su32(bar_g2 + (n % NP)));
+    };
+
+    float acc2[16], acc2d[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) acc2[r] = acc2d[r] = 0.0f;
+    double obj_acc = 0.0;
+    bool ok = true;
+
+    auto fold = [&](int i) {  // modes 1 and 2 from W of slab i (GEMM2 complete)
+        float w[16], wd[16];
+#pragma unroll
+        for (int r = 0; r < 16; ++r) w[r] = wd[r] = 0.0f;
+        if (ok) {
+            tmem_ld16(t_w + lane_off + r0, w);
+            if (DEN) tmem_ld16(t_wd + lane_off + r0, wd);
+        }
+        if (M2) {
+            const float *an = srow + (i % 3) * 96 + 32 + r0, *ad = an + 32;
+#pragma unroll
+            for (int r = 0; r < 16; ++r) {
+                acc2[r] = fmaf(an[r], w[r], acc2[r]);
+                if (DEN) acc2d[r] = fmaf(ad[r], wd[r], acc2d[r]);
+            }
+        }
+        if (M1) {
+#pragma unroll
+            for (int r = 0; r < 16; ++r) {
+                w[r] *= bn[r];
+                if (DEN) wd[r] *= bd[r];
+            }
+            const float s = reduce_scatter16(w);
+            const float sd = DEN ? reduce_scatter16(wd) : 0.0f;
+            if (lane < 16) {
+                red[quarter * 32 + r0 + lane] = s;
+                if (DEN) red[128 + quarter * 32 + r0 + lane] = sd;
+            }
+            __syncthreads();
+            if (t < RP && ok) {
+                const int64_t slot = ((int64_t)(jt * a.n_kb + kb) * a.I + i) * RP + t;
+                a.p1n[slot] = red[t] + red[32 + t] + red[64 + t] + red[96 + t];
+                if (DEN) a.p1d[slot] = red[128 + t] + red[160 + t] + red[192 + t] + red[224 + t];
+            }
+            __syncthreads();
+        }
+    };
+
+    // ---- prologue --------------------------------------------------------------------------
+    if (NC > 0) {
+        if (t == 0)
+            for (int q = 0; q < NS - 1 && q < NC; ++q) issue_x(q);
+        stage_rows(i0);
+        if (i0 + 1 < i1) stage_rows(i0 + 1);
+        __syncthreads();
+        slab_rows(i0);
+        if (M3) slab_kr(i0);
+        fence_async_smem();
+        __syncthreads();
+        if (t == 0) {
+            fence_after();
+            issue_g1(0);
+        }
+    }
+
+    // ---- chunk loop ------------------------------------------------------------------------
+    for (int n = 0; n < NC && ok; ++n) {
+        const int i = i0 + (n >> 1), q = n & 1;
+        if (q == 0 && n > 0) {
+            // slab boundary: previous slab's contractions done -> fold W, refresh KRn^T
+            if (!mbar_wait(su32(bar_g2 + ((n - 1) % NP)), ((n - 1) / NP) & 1)) ok = false;
+            ok = __all_sync(0xffffffffu, ok);
+            fence_after();
+            if (RW) fold(i - 1);
+            if (M3 && ok) slab_kr(i);
+        }
+        if (q == 0 && n > 0 && i + 1 < i1) stage_rows(i + 1);
+        if (ok && !mbar_wait(su32(bar_g1 + (n & 1)), (n >> 1) & 1)) ok = false;
+        ok = __all_sync(0xffffffffu, ok);
+        if (q == 1 && n + 1 < NC) {
+            // next chunk opens slab i + 1: its GEMM1 needs the next R (this chunk's GEMM1 is done)
+            slab_rows(i + 1);
+            fence_async_smem();
+            ok = __syncthreads_and(ok ? 1 : 0) != 0;
+        }
+        if (t == 0 && ok && n + 1 < NC) {
+            fence_after();
+            issue_g1(n + 1);
+        }
+        if (n >= NP && ok && !mbar_wait(su32(bar_g2 + (n % NP)), ((n - NP) / NP) & 1)) ok = false;
+        if (ok && !mbar_wait(su32(bar_x + (n % NS)), (n / NS) & 1)) ok = false;
+        ok = __all_sync(0xffffffffu, ok);
+        fence_after();
+        // ---- epilogue of chunk n: 32 columns of row `row` ---------------------------------
+        if (ok) {
+            float xh[32];
+            tmem_ld32(t_d1 + 64 * (n & 1) + lane_off + 32 * half, xh);
+            const float *xa = Xs + (n % NS) * 8192 + half * 4096;
+            __nv_bfloat16 *pa = Ps + (n % NP) * 8192;
+            __nv_bfloat16 *qa = Qs + (n % NP) * 8192;
+            const int kc = k0 + CH * q + 32 * half;
+            float objf = 0.0f;
+#pragma unroll
+            for (int g = 0; g < 4; ++g) {
+                const float4 x0 = *reinterpret_cast<const float4 *>(xa + swf(row, 8 * g));
+                const float4 x1 = *reinterpret_cast<const float4 *>(xa + swf(row, 8 * g + 4));
+                const float xv[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+                float pv[8], qv[8];
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    const bool v = jv && (kc + 8 * g + c) < K;
+                    float x = xv[c];
+                    if (BK == BK_IS) x = fmaxf(x, a.eps_x);
+                    const float y = fmaxf(xh[8 * g + c], a.eps);
+                    float P, Q;
+                    pq_fast<BK>(a.beta, x, y, P, Q);
+                    if (OBJ && v) objf += dbeta_stable(BK, a.beta, x, y);
+                    pv[c] = v ? P : 0.0f;
+                    qv[c] = v ? Q : 0.0f;
+                }
+                const int kk = 32 * half + 8 * g;
+                __nv_bfloat162 h0 = __floats2bfloat162_rn(pv[0], pv[1]), h1 = __floats2bfloat162_rn(pv[2], pv[3]);
+                __nv_bfloat162 h2 = __floats2bfloat162_rn(pv[4], pv[5]), h3 = __floats2bfloat162_rn(pv[6], pv[7]);
+                uint4 u;
+                u.x = *reinterpret_cast<uint32_t *>(&h0); u.y = *reinterpret_cast<uint32_t *>(&h1);
+                u.z = *reinterpret_cast<uint32_t *>(&h2); u.w = *reinterpret_cast<uint32_t *>(&h3);
+                *reinterpret_cast<uint4 *>(pa + swh(row, kk)) = u;
+                if (DEN) {
+                    h0 = __floats2bfloat162_rn(qv[0], qv[1]); h1 = __floats2bfloat162_rn(qv[2], qv[3]);
+                    h2 = __floats2bfloat162_rn(qv[4], qv[5]); h3 = __floats2bfloat162_rn(qv[6], qv[7]);
+                    u.x = *reinterpret_cast<uint32_t *>(&h0); u.y = *reinterpret_cast<uint32_t *>(&h1);
+                    u.z = *reinterpret_cast<uint32_t *>(&h2); u.w = *reinterpret_cast<uint32_t *>(&h3);
+                    *reinterpret_cast<uint4 *>(qa + swh(row, kk)) = u;
+                }
+            }
+            if (OBJ) obj_acc += (double)objf;
+        }
+        fence_async_smem();
+        fence_before();
+        ok = __syncthreads_and(ok ? 1 : 0) != 0;
+        if (t == 0 && ok) {
+            fence_after();
+            if (n + NS - 1 < NC) issue_x(n + NS - 1);
+            issue_g2(n);
+        }
+    }
+    // ---- last slab's fold, CTA outputs -----------------------------------------------------
+    if (NC > 0) {
+        if (ok && !mbar_wait(su32(bar_g2 + ((NC - 1) % NP)), ((NC - 1) / NP) & 1)) ok = false;
+        ok = __all_sync(0xffffffffu, ok);
+        fence_after();
+        if (RW) fold(i1 - 1);
+        ok = __syncthreads_and(ok ? 1 : 0) != 0;
+    }
+    if (M2 && jv) {
+        const int64_t base = ((int64_t)(kb * a.n_is + is) * J + j) * RP + r0;
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+            a.p2n[base + r] = acc2[r];
+            if (DEN) a.p2d[base + r] = acc2d[r];
+        }
+    }
+    if (M3 && quarter == 0) {
+        // N3^T lanes 0..31 = rank r = lane; this warp pair covers columns 64 half .. +63
+        const int64_t base = (int64_t)(jt * a.n_is + is) * K;
+#pragma unroll 1
+        for (int g = 0; g < 2; ++g) {
+            float v[32], vd[32];
+            const bool have = ok && NC > 0;
+            if (have) {
+                tmem_ld32(t_n3 + 64 * half + 32 * g, v);
+                if (DEN) tmem_ld32(t_n3d + 64 * half + 32 * g, vd);
+            }
+#pragma unroll
+            for (int c = 0; c < 32; ++c) {
+                const int kc = k0 + 64 * half + 32 * g + c;
+                if (kc < K) {
+                    a.p3n[(base + kc) * RP + lane] = have ? v[c] : 0.0f;
+                    if (DEN) a.p3d[(base + kc) * RP + lane] = have ? vd[c] : 0.0f;
+                }
+            }
+        }
+    }
+    if (OBJ) {
+        double v = obj_acc;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) dred[warp] = v;
+        __syncthreads();
+        if (t == 0) {
+            double s = 0.0;
+            for (int w = 0; w < NT / 32; ++w) s += dred[w];
+            a.obj[blockIdx.x] = s;
+        }
+    }
+    if (!ok && t == 0) {
+        // bounded waits for anything still in flight before the CTA's TMEM and smem go
+        for (int q = 0; q < NS; ++q) {
+            mbar_wait(su32(bar_x + q), 0);
+            mbar_wait(su32(bar_x + q), 1);
+        }
+        mbar_wait(su32(bar_g2), 0);
+        if (a.err) atomicExch(a.err, 1);
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;\n" :: "r"(tmem));
+    }
+}
+
+cudaError_t launch_x_map(const Cp3Args &a, CUtensorMap *map);
+
+template <int MS, int BK>
+cudaError_t launch_t(const Cp3Plan &p, const Cp3Args &a, cudaStream_t s) {
+    constexpr Layout L = make_layout((MS & (PM_M1 | PM_M2)) != 0, (MS & PM_M3) != 0, BK != BK_KL);
+    CUtensorMap map;
+    cudaError_t e = launch_x_map(a, &map);
+    if (e != cudaSuccess) return e;
+    auto k = cp3_pass_tc<MS, BK>;
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total);
+    if (e != cudaSuccess) return e;
+    k<<<p.grid, NT, L.total, s>>>(map, a);
+    return cudaGetLastError();
+}
+
+template <int BK>
+cudaError_t launch_bk(const Cp3Plan &p, const Cp3Args &a, int ms, cudaStream_t s) {
+    switch (ms) {
+        case PM_M1: return launch_t<PM_M1, BK>(p, a, s);
+        case PM_M1 | PM_OBJ: return launch_t<PM_M1 | PM_OBJ, BK>(p, a, s);
+        case PM_M2: return launch_t<PM_M2, BK>(p, a, s);
+        case PM_M3: return launch_t<PM_M3, BK>(p, a, s);
+        case PM_M1 | PM_M2 | PM_M3 | PM_OBJ:
+            if (BK == BK_KL) return launch_t<PM_M1 | PM_M2 | PM_M3 | PM_OBJ, BK_KL>(p, a, s);
+            return cudaErrorInvalidValue;
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace tc
+}  // namespace ntf

@@ -1,0 +1,8 @@
+// Tensor-core pass instantiations for one beta class (compiled in parallel).
+#include "cp3_tc.cuh"
+
+namespace ntf {
+cudaError_t cp3_tc_launch_bk2(const Cp3Plan &p, const Cp3Args &a, int ms, cudaStream_t s) {
+    return tc::launch_bk<2>(p, a, ms, s);
+}
+}  // namespace ntf

@@ -23,6 +23,7 @@ struct ntf_ctx {
     bool timing = false;
     std::vector<cudaEvent_t> ev;  // pairs: ev[2k] start, ev[2k+1] stop
     size_t ev_used = 0;           // pairs in use
+    int *status = nullptr;        // device status word (bounded waits that gave up)
 };
 
 namespace {
@@ -115,13 +116,17 @@ struct CpDense {
     float *denc;
 };
 
-int cp_dense_setup(ntf_ctx *ctx, const ntf_tensor *X, int R, bool jcomm, bool need_den, CpDense &s) {
+int cp_dense_setup(ntf_ctx *ctx, const ntf_tensor *X, int R, bool jcomm, bool need_den, int precision,
+                   CpDense &s) {
     s.I = (int)X->dims[0];
     s.J = (int)X->dims[1];
     s.K = (int)X->dims[2];
     s.R = R;
     s.RP = rank_pad(R);
-    s.plan = ntf::cp3_plan(s.I, s.J, s.K, s.RP, ctx->num_sms);
+    // tensor-core passes where the request asks for them and the shapes allow (rank padded
+    // to 32, rows of X 16-byte aligned for TMA); FP32 CUDA-core passes otherwise
+    const bool tc = precision == NTF_PREC_TF32 && ntf::cp3_tc_eligible(s.RP, s.K, X->values);
+    s.plan = ntf::cp3_plan(s.I, s.J, s.K, s.RP, ctx->num_sms, tc ? 128 : 64);
     const int dims[3] = {s.I, s.J, s.K};
     const int parts[3] = {s.plan.parts1, s.plan.parts2, s.plan.parts3};
     for (int n = 0; n < 3; ++n) {
@@ -163,6 +168,7 @@ ntf::Cp3Args cp_args(const ntf_tensor *X, const CpDense &s, const ntf_opts &o, f
     a.p3n = s.pn[2];
     a.p3d = s.pd[2];
     a.obj = s.obj;
+    a.err = nullptr;
     return a;
 }
 
@@ -188,13 +194,16 @@ struct PassTimer {
     }
 };
 
-int launch_pass(ntf_ctx *ctx, const CpDense &s, const ntf::Cp3Args &a, int ms, int den, int precision,
-                cudaStream_t st) {
+int launch_pass(ntf_ctx *ctx, const CpDense &s, const ntf::Cp3Args &a_in, int ms, int den, cudaStream_t st) {
     PassTimer t(ctx, st);
-    if (precision == NTF_PREC_TF32 && ntf::cp3_tc_supported(s.RP, ms, den)) {
+    if (s.plan.tc) {
+        if (!ntf::cp3_tc_supported(ms, den))
+            return fail(ctx, NTF_ERR_UNSUPPORTED, "pass variant %d/%d has no tensor-core kernel", ms, den);
+        ntf::Cp3Args a = a_in;
+        a.err = ctx->status;
         NTF_CUDA(ntf::cp3_tc_launch(s.plan, a, ms, den, st));
     } else {
-        NTF_CUDA(ntf::cp3_launch(s.plan, a, ms, den, st));
+        NTF_CUDA(ntf::cp3_launch(s.plan, a_in, ms, den, st));
     }
     return NTF_OK;
 }
@@ -204,7 +213,7 @@ int cp_dense_mu_sweep(ntf_ctx *ctx, const ntf_tensor *X, float beta, int R, floa
     const int bk = ntf::beta_kind(beta);
     const int den = bk != ntf::BK_KL;
     CpDense s{};
-    int rc = cp_dense_setup(ctx, X, R, false, den, s);
+    int rc = cp_dense_setup(ctx, X, R, false, den, o.precision, s);
     if (rc) return rc;
     const int dims[3] = {s.I, s.J, s.K};
     const int parts[3] = {s.plan.parts1, s.plan.parts2, s.plan.parts3};
@@ -215,7 +224,7 @@ int cp_dense_mu_sweep(ntf_ctx *ctx, const ntf_tensor *X, float beta, int R, floa
         for (int m = 0; m < 3; ++m) a.rec[m] = a.num[m] = a.den[m] = s.F[m];
         int ms = (n == 0 ? ntf::PM_M1 : n == 1 ? ntf::PM_M2 : ntf::PM_M3);
         if (n == 0 && objective_dev) ms |= ntf::PM_OBJ;
-        rc = launch_pass(ctx, s, a, ms, den, o.precision, st);
+        rc = launch_pass(ctx, s, a, ms, den, st);
         if (rc) return rc;
         if (!den) {
             const float *f[2];
@@ -249,7 +258,7 @@ int cp_dense_jcomm(ntf_ctx *ctx, const ntf_tensor *X, float beta, int R, float *
     const int bk = ntf::beta_kind(beta);
     const bool kl = bk == ntf::BK_KL;
     CpDense s{};
-    int rc = cp_dense_setup(ctx, X, R, true, !kl, s);
+    int rc = cp_dense_setup(ctx, X, R, true, !kl, o.precision, s);
     if (rc) return rc;
     const int dims[3] = {s.I, s.J, s.K};
     const int parts[3] = {s.plan.parts1, s.plan.parts2, s.plan.parts3};
@@ -265,7 +274,7 @@ int cp_dense_jcomm(ntf_ctx *ctx, const ntf_tensor *X, float beta, int R, float *
         // Qtilde == 1 makes each Den_J^(n) the product of column sums of the other
         // current blocks (chi2(Z, Zt) = Z at beta = 1).
         for (int m = 0; m < 3; ++m) a.rec[m] = a.num[m] = a.den[m] = s.Ft[m];
-        rc = launch_pass(ctx, s, a, ntf::PM_M1 | ntf::PM_M2 | ntf::PM_M3 | ntf::PM_OBJ, 0, o.precision, st);
+        rc = launch_pass(ctx, s, a, ntf::PM_M1 | ntf::PM_M2 | ntf::PM_M3 | ntf::PM_OBJ, 0, st);
         if (rc) return rc;
         for (int l = 0; l < o.inner_L; ++l) {
             for (int n = 0; n < 3; ++n) {
@@ -303,7 +312,7 @@ int cp_dense_jcomm(ntf_ctx *ctx, const ntf_tensor *X, float beta, int R, float *
                 }
                 int ms = (n == 0 ? ntf::PM_M1 : n == 1 ? ntf::PM_M2 : ntf::PM_M3);
                 if (l == 0 && n == 0) ms |= ntf::PM_OBJ;
-                rc = launch_pass(ctx, s, a, ms, 1, o.precision, st);
+                rc = launch_pass(ctx, s, a, ms, 1, st);
                 if (rc) return rc;
                 ntf::MuEpiArgs e{};
                 e.pn = s.pn[n];
@@ -332,7 +341,7 @@ int cp_dense_jcomm(ntf_ctx *ctx, const ntf_tensor *X, float beta, int R, float *
 int cp_dense_beta_div(ntf_ctx *ctx, const ntf_tensor *X, float beta, int R, const float *const *factors,
                       const ntf_opts &o, double *out_dev, cudaStream_t st) {
     CpDense s{};
-    int rc = cp_dense_setup(ctx, X, R, false, false, s);
+    int rc = cp_dense_setup(ctx, X, R, false, false, NTF_PREC_FP32, s);
     if (rc) return rc;
     const int dims[3] = {s.I, s.J, s.K};
     for (int n = 0; n < 3; ++n) NTF_CUDA(ntf::pad_factor(factors[n], dims[n], R, s.F[n], s.RP, st));
@@ -373,6 +382,11 @@ int ntf_ctx_create(ntf_ctx **out, int device) {
     c->device = device;
     cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
     if (c->num_sms <= 0) c->num_sms = 1;
+    if (cudaMalloc(&c->status, sizeof(int)) != cudaSuccess || cudaMemset(c->status, 0, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return NTF_ERR_CUDA;
+    }
     *out = c;
     return NTF_OK;
 }
@@ -384,6 +398,7 @@ void ntf_ctx_destroy(ntf_ctx *c) {
     for (auto &kv : c->ws)
         if (kv.second.first) cudaFree(kv.second.first);
     for (auto e : c->ev) cudaEventDestroy(e);
+    if (c->status) cudaFree(c->status);
     ntf::tucker_release(c);
     ntf::coo_release(c);
     delete c;
@@ -396,6 +411,22 @@ int64_t ntf_launch_count(const ntf_ctx *c) { return c ? c->launches : 0; }
 int ntf_set_pass_timing(ntf_ctx *c, int enable) {
     if (!c) return NTF_ERR_ARG;
     c->timing = enable != 0;
+    return NTF_OK;
+}
+
+int ntf_device_status(ntf_ctx *c, void *stream) {
+    if (!c) return NTF_ERR_ARG;
+    cudaSetDevice(c->device);
+    int h = 0;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(&h, c->status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return fail(c, NTF_ERR_CUDA, "reading the device status failed: %s", cudaGetErrorString(cudaGetLastError()));
+    if (h) {
+        cudaMemsetAsync(c->status, 0, sizeof(int), st);
+        cudaStreamSynchronize(st);
+        return fail(c, NTF_ERR_TIMEOUT, "a bounded device-side wait ran out (status %d)", h);
+    }
     return NTF_OK;
 }
 

@@ -129,23 +129,29 @@ struct Cp3Args {
     float *p2n, *p2d;      // mode-2 partials [n_kb*n_is][J][RP]
     float *p3n, *p3d;      // mode-3 partials [n_jt*n_is][K][RP]
     double *obj;           // per-CTA objective partials [grid]
+    int *err;              // device status word: set non-zero when a bounded wait gives up
 };
 
 struct Cp3Plan {
+    int tc;  // 1: tensor-core (tcgen05) pass, else FP32 CUDA-core pass
     int RP, TJ, KB;
     int n_jt, n_kb, n_is;
     int grid;
     int parts1, parts2, parts3;
 };
 
-Cp3Plan cp3_plan(int I, int J, int K, int RP, int num_sms);
+// kb: columns per CTA block (64 for the FP32 pass, 128 for the tensor-core pass)
+Cp3Plan cp3_plan(int I, int J, int K, int RP, int num_sms, int kb = 64);
 // Launches one pass.  mode_set: OR of PassMode; den: 1 when the denominator partials are
 // needed (beta != 1).  Returns a cudaError_t.
 cudaError_t cp3_launch(const Cp3Plan &plan, const Cp3Args &a, int mode_set, int den,
                        cudaStream_t s);
 
-// Tensor-core (tcgen05, TF32) variant of the same pass; same partial layouts.
-bool cp3_tc_supported(int RP, int mode_set, int den);
+// Tensor-core (tcgen05) variant of the same pass (plan with kb = 128): TF32 reconstruction
+// GEMM, BF16 contraction GEMMs, FP32 accumulation; same partial-sum layouts.
+// Eligible when RP == 32, K % 4 == 0 and X is 16-byte aligned.
+bool cp3_tc_eligible(int RP, int K, const float *X);
+bool cp3_tc_supported(int mode_set, int den);
 cudaError_t cp3_tc_launch(const Cp3Plan &plan, const Cp3Args &a, int mode_set, int den,
                           cudaStream_t s);
 

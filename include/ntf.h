@@ -157,6 +157,29 @@ int ntf_beta_div(ntf_ctx *ctx, int model, const ntf_tensor *X, float beta, int r
 int ntf_coo_stable_perm(ntf_ctx *ctx, const int32_t *keys, int64_t nnz, int64_t key_range,
                         int32_t *perm_out, void *stream);
 
+/* Allocation-free objective for dense CP tensors.  The paper has no counterpart: this is a
+ * service for callers that cannot allocate device memory when they call -- code running
+ * while a CUDA graph is being captured, or a process whose device memory is reserved up
+ * front by another allocator or a fixed budget.  The other entry points grow workspaces
+ * with cudaMalloc; this one allocates nothing.  It computes the same value as
+ * ntf_beta_div(ctx, NTF_CP, X, beta, rank, NULL, NULL, factors, opts, out_dev, stream)
+ * with opts = {eps, eps_x}, on the current device, asynchronously on `stream`.
+ *   - Scratch: a file-scope device array of NTF_NOALLOC_SCRATCH_BYTES that every GPU
+ *     loading the library holds until the process exits.  It must fit the padded factor
+ *     copies and one FP64 partial per CTA: about (I_1 + I_2 + I_3) * 32 * 4 bytes at
+ *     rank <= 32; larger problems return NTF_ERR_UNSUPPORTED before any work is queued.
+ *   - The first call on a device looks up the array's device address (one
+ *     cudaGetSymbolAddress with that device current); make that first call before any
+ *     stream capture.
+ *   - Every call on a device shares the same array and each call overwrites what it uses.
+ *     Calls whose GPU work overlaps (different streams, or concurrent host threads) race;
+ *     order them on one stream or synchronize between them.
+ *   - Dense order-3 tensors only; other arguments and errors as ntf_beta_div.  No
+ *     context, so no message: the return code is the only error report. */
+#define NTF_NOALLOC_SCRATCH_BYTES (4u << 20)
+int ntf_cp_beta_div_noalloc(const ntf_tensor *X, float beta, int rank, const float *const *factors,
+                            double eps, double eps_x, double *out_dev, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

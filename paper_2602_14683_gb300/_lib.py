@@ -59,6 +59,8 @@ _sig = {
     "ntf_beta_div": (C.c_int, [_P, C.c_int, C.POINTER(Tensor), C.c_float, C.c_int, C.POINTER(C.c_int64), _P,
                                C.POINTER(_P), C.POINTER(Opts), _P, _P]),
     "ntf_coo_stable_perm": (C.c_int, [_P, _P, C.c_int64, C.c_int64, _P, _P]),
+    "ntf_cp_beta_div_noalloc": (C.c_int, [C.POINTER(Tensor), C.c_float, C.c_int, C.POINTER(_P), C.c_double,
+                                          C.c_double, _P, _P]),
 }
 for _name, (_res, _args) in _sig.items():
     _f = getattr(_lib, _name)
@@ -259,6 +261,15 @@ def coo_stable_perm(keys, key_range, ctx=None, stream=None):
     ctx.check(_lib.ntf_coo_stable_perm(ctx.h, keys.data_ptr(), keys.numel(), int(key_range), out.data_ptr(),
                                        _stream(stream)))
     return out
+
+
+def cp_beta_div_noalloc(X, beta, factors, out, eps=1e-12, eps_x=1e-12, stream=None):
+    """Allocation-free dense CP objective (ntf_cp_beta_div_noalloc); `out` is a 1-element
+    float64 CUDA tensor owned by the caller.  Returns the C status code."""
+    d = _Desc(X)
+    fp = _ptrs(factors, "factors")
+    return _lib.ntf_cp_beta_div_noalloc(C.byref(d.t), float(beta), int(factors[0].shape[1]), fp, float(eps),
+                                        float(eps_x), _out_ptr(out), _stream(stream))
 
 
 def raw_library():

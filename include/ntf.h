@@ -34,6 +34,7 @@
 #ifndef NTF_H
 #define NTF_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -156,6 +157,56 @@ int ntf_beta_div(ntf_ctx *ctx, int model, const ntf_tensor *X, float beta, int r
  * entries per mode; exposed for testing. */
 int ntf_coo_stable_perm(ntf_ctx *ctx, const int32_t *keys, int64_t nnz, int64_t key_range,
                         int32_t *perm_out, void *stream);
+
+/* ---------------------------------------------------------------------------------
+ * Continuous-batching server for many small dense 3-way jobs (CP or Tucker).
+ * The server owns `slots` execution slots (a context and a stream each) and a scheduler
+ * thread.  Submitted jobs queue FIFO; the head is admitted into a free slot when its
+ * estimated workspace fits the device-memory budget (a job larger than the budget runs
+ * alone).  An admitted job runs one iteration eagerly, then one iteration of its method is
+ * captured as a CUDA graph and replayed; after each iteration the FP64 objective of the
+ * iteration's incoming iterate (Section 3.2) is read into pinned host memory and the job
+ * stops when |F_{t-1} - F_t| / F_{t-1} <= rtol or after max_iters iterations.  Jobs in
+ * different slots run concurrently.  A job's result does not depend on what else runs.
+ * The caller owns X, factors and core (device memory) and must keep them alive and
+ * untouched until the job's result has been polled; factors and core are updated in
+ * place.  Server functions are thread-safe; each job uses the device of the server.
+ * --------------------------------------------------------------------------------- */
+typedef struct ntf_server ntf_server;
+
+typedef struct {
+    int model;             /* NTF_CP or NTF_TUCKER */
+    int method;            /* 0: J-CoMM (Algorithm 2) with inner_L = 1; 1: block MM */
+    int precision;         /* NTF_PREC_FP32 or NTF_PREC_TF32 (CP, rank padded to 32) */
+    int64_t dims[3];       /* I_1, I_2, I_3 */
+    int rank;              /* CP rank (1..64) */
+    int64_t core_dims[3];  /* Tucker core dimensions (1..64 each) */
+    float beta;            /* in [0, 2) */
+    double eps;            /* parameter floor; <= 0 selects 1e-12 */
+    double rtol;           /* relative objective change that stops the job */
+    int max_iters;         /* iteration cap, >= 1 */
+    const float *X;        /* device, dense row-major */
+    float *factors[3];     /* device, I_n x rank (CP) or I_n x J_n (Tucker), in place */
+    float *core;           /* device, Tucker core (NULL for CP), in place */
+} ntf_job;
+
+typedef struct {
+    int64_t id;            /* id returned by ntf_server_submit */
+    int status;            /* NTF_OK or the failing call's status */
+    int iterations;        /* iterations run */
+    double objective;      /* D_beta of the incoming iterate of the last iteration */
+    double t_submit, t_admit, t_done; /* host steady-clock seconds */
+} ntf_result;
+
+/* mem_budget_bytes = 0 selects half of the device memory free at creation. */
+int ntf_server_create(ntf_server **server, int device, int slots, size_t mem_budget_bytes);
+/* Queues a copy of *job; returns at once.  id_out (may be NULL) receives the job id. */
+int ntf_server_submit(ntf_server *server, const ntf_job *job, int64_t *id_out);
+/* Moves up to max_results completed results into out and returns how many; with
+ * wait_all != 0 it first waits until every submitted job has completed. */
+int ntf_server_poll(ntf_server *server, ntf_result *out, int max_results, int wait_all);
+/* Stops the scheduler (queued jobs are dropped), waits for running work, frees slots. */
+void ntf_server_destroy(ntf_server *server);
 
 /* Allocation-free objective for dense CP tensors.  The paper has no counterpart: this is a
  * service for callers that cannot allocate device memory when they call -- code running

@@ -33,6 +33,18 @@ class Tensor(C.Structure):
                 ("values", C.c_void_p), ("idx", C.POINTER(C.c_void_p)), ("nnz", C.c_int64)]
 
 
+class Job(C.Structure):
+    _fields_ = [("model", C.c_int), ("method", C.c_int), ("precision", C.c_int), ("dims", C.c_int64 * 3),
+                ("rank", C.c_int), ("core_dims", C.c_int64 * 3), ("beta", C.c_float), ("eps", C.c_double),
+                ("rtol", C.c_double), ("max_iters", C.c_int), ("X", C.c_void_p), ("factors", C.c_void_p * 3),
+                ("core", C.c_void_p)]
+
+
+class Result(C.Structure):
+    _fields_ = [("id", C.c_int64), ("status", C.c_int), ("iterations", C.c_int), ("objective", C.c_double),
+                ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_done", C.c_double)]
+
+
 class Opts(C.Structure):
     _fields_ = [("eps", C.c_double), ("eps_x", C.c_double), ("inner_L", C.c_int), ("precision", C.c_int)]
 
@@ -59,6 +71,10 @@ _sig = {
     "ntf_beta_div": (C.c_int, [_P, C.c_int, C.POINTER(Tensor), C.c_float, C.c_int, C.POINTER(C.c_int64), _P,
                                C.POINTER(_P), C.POINTER(Opts), _P, _P]),
     "ntf_coo_stable_perm": (C.c_int, [_P, _P, C.c_int64, C.c_int64, _P, _P]),
+    "ntf_server_create": (C.c_int, [C.POINTER(_P), C.c_int, C.c_int, C.c_size_t]),
+    "ntf_server_submit": (C.c_int, [_P, C.POINTER(Job), C.POINTER(C.c_int64)]),
+    "ntf_server_poll": (C.c_int, [_P, C.POINTER(Result), C.c_int, C.c_int]),
+    "ntf_server_destroy": (None, [_P]),
     "ntf_cp_beta_div_noalloc": (C.c_int, [C.POINTER(Tensor), C.c_float, C.c_int, C.POINTER(_P), C.c_double,
                                           C.c_double, _P, _P]),
 }
@@ -270,6 +286,70 @@ def cp_beta_div_noalloc(X, beta, factors, out, eps=1e-12, eps_x=1e-12, stream=No
     fp = _ptrs(factors, "factors")
     return _lib.ntf_cp_beta_div_noalloc(C.byref(d.t), float(beta), int(factors[0].shape[1]), fp, float(eps),
                                         float(eps_x), _out_ptr(out), _stream(stream))
+
+
+class Server:
+    """Continuous-batching server (ntf_server_*): submit jobs made of CUDA tensors, poll
+    results.  Keeps every submitted job's tensors alive until its result is polled."""
+
+    def __init__(self, device=0, slots=8, mem_budget_bytes=0):
+        h = _P()
+        rc = _lib.ntf_server_create(C.byref(h), int(device), int(slots), int(mem_budget_bytes))
+        if rc != NTF_OK:
+            raise NtfError(rc, "ntf_server_create failed")
+        self.h = h
+        self._live = {}
+
+    def submit(self, X, beta, factors, core=None, method="jcomm", rtol=1e-6, max_iters=200, precision="fp32",
+               eps=1e-12):
+        _check_dev(X, torch.float32, "X")
+        for f in factors:
+            _check_dev(f, torch.float32, "factors")
+        j = Job()
+        j.model = NTF_CP if core is None else NTF_TUCKER
+        j.method = {"jcomm": 0, "block": 1}[method]
+        j.precision = PRECISIONS[precision]
+        for n in range(3):
+            j.dims[n] = X.shape[n]
+        if core is None:
+            j.rank = factors[0].shape[1]
+        else:
+            _check_dev(core, torch.float32, "core")
+            for n in range(3):
+                j.core_dims[n] = core.shape[n]
+            j.core = core.data_ptr()
+        j.beta, j.eps, j.rtol, j.max_iters = float(beta), float(eps), float(rtol), int(max_iters)
+        j.X = X.data_ptr()
+        for n in range(3):
+            j.factors[n] = factors[n].data_ptr()
+        jid = C.c_int64()
+        rc = _lib.ntf_server_submit(self.h, C.byref(j), C.byref(jid))
+        if rc != NTF_OK:
+            raise NtfError(rc, "ntf_server_submit failed")
+        self._live[jid.value] = (X, factors, core)
+        return jid.value
+
+    def poll(self, wait_all=False, max_results=4096):
+        buf = (Result * max_results)()
+        n = _lib.ntf_server_poll(self.h, buf, max_results, 1 if wait_all else 0)
+        out = []
+        for q in range(n):
+            r = buf[q]
+            self._live.pop(r.id, None)
+            out.append(dict(id=r.id, status=r.status, iterations=r.iterations, objective=r.objective,
+                            t_submit=r.t_submit, t_admit=r.t_admit, t_done=r.t_done))
+        return out
+
+    def close(self):
+        if self.h:
+            _lib.ntf_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def raw_library():

@@ -1,0 +1,319 @@
+// Continuous-batching server for many small factorization jobs.
+//
+// A server owns `slots` execution slots, each an ntf context (its own workspaces) and a
+// CUDA stream.  Jobs wait in a FIFO queue; a scheduler thread admits the head of the queue
+// into a free slot when the slot's estimated workspace fits the device-memory budget, runs
+// one eager iteration (which sizes the workspaces and yields the first objective), then
+// captures one iteration of the job's method as a CUDA graph and replays it.  After each
+// iteration the FP64 objective is copied to pinned host memory and an event is recorded;
+// the scheduler polls the events of all active slots, applies the stopping test
+// |F_{t-1} - F_t| / F_{t-1} <= rtol (or the iteration cap) and either replays the graph
+// again or completes the job and frees the slot for the next admission.  Jobs in
+// different slots overlap on the device through their streams.  A job's kernels, launch
+// shapes and reduction orders depend only on its own shapes, so its result is the same
+// whether it runs alone or among others.
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "../../include/ntf.h"
+#include "ntf_internal.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+double now_s() { return std::chrono::duration<double>(Clock::now().time_since_epoch()).count(); }
+
+struct Slot {
+    ntf_ctx *ctx = nullptr;
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    double *F_dev = nullptr;
+    double *F_host = nullptr;  // pinned
+    cudaGraphExec_t exec = nullptr;
+    bool busy = false;
+    ntf_job job{};
+    int64_t id = -1;
+    int iters = 0;
+    double F_prev = 0.0, F_last = 0.0;
+    double t_submit = 0.0, t_admit = 0.0;
+    size_t bytes = 0;
+};
+
+struct Pending {
+    ntf_job job;
+    int64_t id;
+    double t_submit;
+};
+
+int rank_pad(int R) { return R <= 8 ? 8 : R <= 16 ? 16 : R <= 32 ? 32 : 64; }
+
+// workspace bytes a job's context grows to (padded blocks, partial sums, Tucker partial
+// tensors); an estimate used for admission, not an allocation
+size_t estimate_bytes(const ntf_job &j, int sms) {
+    const int64_t I = j.dims[0], J = j.dims[1], K = j.dims[2];
+    size_t b = 0;
+    if (j.model == NTF_CP) {
+        const int RP = rank_pad(j.rank);
+        const ntf::Cp3Plan p = ntf::cp3_plan((int)I, (int)J, (int)K, RP, sms, 64);
+        b += 4 * sizeof(float) * (size_t)(I + J + K) * RP;
+        b += 2 * sizeof(float) * ((size_t)p.parts1 * I + (size_t)p.parts2 * J + (size_t)p.parts3 * K) * RP;
+        b += sizeof(double) * (size_t)p.grid;
+    } else {
+        const int RP = rank_pad((int)j.core_dims[2]);
+        const int64_t Jc = j.core_dims[0] * j.core_dims[1] * j.core_dims[2];
+        b += 5 * sizeof(float) * (size_t)(I * J) * RP;  // B3 rec / num / den, W, Wd
+        b += 4 * sizeof(float) * (size_t)(4 * Jc + I * j.core_dims[0] + J * j.core_dims[1] + K * RP);
+        b += 3 * sizeof(float) * (size_t)(I * j.core_dims[1] * j.core_dims[2]);
+        const ntf::Cp3Plan p = ntf::cp3_plan((int)I, (int)J, (int)K, RP, sms, 64);
+        b += 2 * sizeof(float) * (size_t)p.parts3 * K * RP + sizeof(double) * (size_t)p.grid * 4;
+    }
+    return b + (1u << 20);
+}
+
+}  // namespace
+
+struct ntf_server {
+    int device = 0, sms = 1;
+    size_t budget = 0, used = 0;
+    std::vector<Slot> slots;
+    std::deque<Pending> pending;
+    std::vector<ntf_result> done;
+    int64_t next_id = 0;
+    int active = 0;
+    std::mutex mu;
+    std::condition_variable cv, cv_done;
+    std::thread worker;
+    bool stop = false;
+};
+
+namespace {
+
+int run_step(Slot &s, cudaStream_t st) {
+    const ntf_job &j = s.job;
+    ntf_opts o;
+    ntf_opts_default(&o);
+    o.precision = j.precision;
+    o.eps = j.eps > 0 ? j.eps : o.eps;
+    ntf_tensor X{};
+    X.order = 3;
+    X.dims = j.dims;
+    X.kind = NTF_DENSE;
+    X.values = j.X;
+    float *const *f = j.factors;
+    if (j.method == 1) {
+        if (j.model == NTF_CP) return ntf_cp_mu_sweep(s.ctx, &X, j.beta, j.rank, f, &o, s.F_dev, st);
+        return ntf_tucker_mu_sweep(s.ctx, &X, j.beta, j.core_dims, j.core, f, &o, s.F_dev, st);
+    }
+    if (j.model == NTF_CP) return ntf_jcomm_outer(s.ctx, NTF_CP, &X, j.beta, j.rank, nullptr, nullptr, f, &o, s.F_dev, st);
+    return ntf_jcomm_outer(s.ctx, NTF_TUCKER, &X, j.beta, 0, j.core_dims, j.core, f, &o, s.F_dev, st);
+}
+
+void finish(ntf_server *sv, Slot &s, int status) {
+    ntf_result r{};
+    r.id = s.id;
+    r.status = status;
+    r.iterations = s.iters;
+    r.objective = s.F_last;
+    r.t_submit = s.t_submit;
+    r.t_admit = s.t_admit;
+    r.t_done = now_s();
+    if (s.exec) {
+        cudaGraphExecDestroy(s.exec);
+        s.exec = nullptr;
+    }
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->done.push_back(r);
+        sv->used -= s.bytes;
+        --sv->active;
+    }
+    s.busy = false;
+    sv->cv_done.notify_all();
+}
+
+// first (eager) iteration, then capture of one iteration as a graph
+int admit(Slot &s) {
+    int rc = run_step(s, s.st);
+    if (rc) return rc;
+    if (cudaMemcpyAsync(s.F_host, s.F_dev, sizeof(double), cudaMemcpyDeviceToHost, s.st) != cudaSuccess) return NTF_ERR_CUDA;
+    if (cudaEventRecord(s.ev, s.st) != cudaSuccess) return NTF_ERR_CUDA;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(s.st, cudaStreamCaptureModeRelaxed) != cudaSuccess) return NTF_ERR_CUDA;
+    rc = run_step(s, s.st);
+    if (cudaMemcpyAsync(s.F_host, s.F_dev, sizeof(double), cudaMemcpyDeviceToHost, s.st) != cudaSuccess) rc = NTF_ERR_CUDA;
+    cudaError_t e = cudaStreamEndCapture(s.st, &g);
+    if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess || !g) return NTF_ERR_CUDA;
+    e = cudaGraphInstantiate(&s.exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return NTF_ERR_CUDA;
+    s.iters = 0;
+    return NTF_OK;
+}
+
+void worker_loop(ntf_server *sv) {
+    cudaSetDevice(sv->device);
+    for (;;) {
+        // admissions (FIFO: the head waits until a slot and the memory budget allow it)
+        for (;;) {
+            Pending p;
+            int slot = -1;
+            {
+                std::unique_lock<std::mutex> lk(sv->mu);
+                if (sv->stop) return;
+                if (sv->pending.empty()) break;
+                const size_t need = estimate_bytes(sv->pending.front().job, sv->sms);
+                for (size_t q = 0; q < sv->slots.size(); ++q)
+                    if (!sv->slots[q].busy) { slot = (int)q; break; }
+                if (slot < 0 || (sv->used + need > sv->budget && sv->active > 0)) break;
+                p = sv->pending.front();
+                sv->pending.pop_front();
+                sv->used += need;
+                ++sv->active;
+                sv->slots[slot].bytes = need;
+            }
+            Slot &s = sv->slots[slot];
+            s.busy = true;
+            s.job = p.job;
+            s.id = p.id;
+            s.t_submit = p.t_submit;
+            s.t_admit = now_s();
+            s.F_prev = s.F_last = 0.0;
+            s.iters = 0;
+            const int rc = admit(s);
+            if (rc) finish(sv, s, rc);
+        }
+        // progress of active slots
+        bool any = false;
+        for (auto &s : sv->slots) {
+            if (!s.busy) continue;
+            any = true;
+            const cudaError_t q = cudaEventQuery(s.ev);
+            if (q == cudaErrorNotReady) continue;
+            if (q != cudaSuccess) {
+                cudaGetLastError();
+                finish(sv, s, NTF_ERR_CUDA);
+                continue;
+            }
+            // one more iteration completed: F_host holds the objective of its incoming iterate
+            ++s.iters;
+            s.F_prev = s.F_last;
+            s.F_last = *s.F_host;
+            const bool conv = s.iters > 1 && s.F_prev > 0.0 && (s.F_prev - s.F_last) / s.F_prev <= s.job.rtol &&
+                              (s.F_last - s.F_prev) / s.F_prev <= s.job.rtol;
+            if (conv || s.iters >= s.job.max_iters) {
+                finish(sv, s, NTF_OK);
+                continue;
+            }
+            if (cudaGraphLaunch(s.exec, s.st) != cudaSuccess || cudaEventRecord(s.ev, s.st) != cudaSuccess) {
+                cudaGetLastError();
+                finish(sv, s, NTF_ERR_CUDA);
+            }
+        }
+        if (!any) {
+            std::unique_lock<std::mutex> lk(sv->mu);
+            sv->cv.wait_for(lk, std::chrono::milliseconds(2), [&] { return sv->stop || !sv->pending.empty(); });
+            if (sv->stop) return;
+        } else {
+            std::this_thread::yield();
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int ntf_server_create(ntf_server **out, int device, int slots, size_t mem_budget_bytes) {
+    if (!out || slots < 1 || slots > 256) return NTF_ERR_ARG;
+    *out = nullptr;
+    if (cudaSetDevice(device) != cudaSuccess) {
+        cudaGetLastError();
+        return NTF_ERR_CUDA;
+    }
+    ntf_server *sv = new ntf_server();
+    sv->device = device;
+    cudaDeviceGetAttribute(&sv->sms, cudaDevAttrMultiProcessorCount, device);
+    if (sv->sms < 1) sv->sms = 1;
+    if (mem_budget_bytes == 0) {
+        size_t fr = 0, tot = 0;
+        cudaMemGetInfo(&fr, &tot);
+        mem_budget_bytes = fr / 2;
+    }
+    sv->budget = mem_budget_bytes;
+    sv->slots.resize(slots);
+    for (auto &s : sv->slots) {
+        if (ntf_ctx_create(&s.ctx, device) != NTF_OK || cudaStreamCreateWithFlags(&s.st, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming) != cudaSuccess ||
+            cudaMalloc(&s.F_dev, sizeof(double)) != cudaSuccess ||
+            cudaMallocHost(&s.F_host, sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            ntf_server_destroy(sv);
+            return NTF_ERR_CUDA;
+        }
+    }
+    sv->worker = std::thread(worker_loop, sv);
+    *out = sv;
+    return NTF_OK;
+}
+
+int ntf_server_submit(ntf_server *sv, const ntf_job *job, int64_t *id_out) {
+    if (!sv || !job) return NTF_ERR_ARG;
+    if (job->model != NTF_CP && job->model != NTF_TUCKER) return NTF_ERR_ARG;
+    if (!job->X || !job->factors[0] || !job->factors[1] || !job->factors[2]) return NTF_ERR_ARG;
+    if (job->model == NTF_TUCKER && !job->core) return NTF_ERR_ARG;
+    if (!(job->beta >= 0.0f && job->beta < 2.0f)) return NTF_ERR_BETA;
+    if (job->max_iters < 1 || job->method < 0 || job->method > 1) return NTF_ERR_ARG;
+    for (int n = 0; n < 3; ++n)
+        if (job->dims[n] < 1) return NTF_ERR_SHAPE;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    const int64_t id = sv->next_id++;
+    sv->pending.push_back({*job, id, now_s()});
+    if (id_out) *id_out = id;
+    sv->cv.notify_all();
+    return NTF_OK;
+}
+
+int ntf_server_poll(ntf_server *sv, ntf_result *out, int max_results, int wait_all) {
+    if (!sv || (!out && max_results > 0)) return NTF_ERR_ARG;
+    std::unique_lock<std::mutex> lk(sv->mu);
+    if (wait_all) sv->cv_done.wait(lk, [&] { return sv->pending.empty() && sv->active == 0; });
+    int n = 0;
+    while (n < max_results && !sv->done.empty()) {
+        out[n++] = sv->done.front();
+        sv->done.erase(sv->done.begin());
+    }
+    return n;
+}
+
+void ntf_server_destroy(ntf_server *sv) {
+    if (!sv) return;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->stop = true;
+    }
+    sv->cv.notify_all();
+    if (sv->worker.joinable()) sv->worker.join();
+    cudaSetDevice(sv->device);
+    for (auto &s : sv->slots) {
+        if (s.st) cudaStreamSynchronize(s.st);
+        if (s.exec) cudaGraphExecDestroy(s.exec);
+        if (s.ev) cudaEventDestroy(s.ev);
+        if (s.st) cudaStreamDestroy(s.st);
+        if (s.F_dev) cudaFree(s.F_dev);
+        if (s.F_host) cudaFreeHost(s.F_host);
+        if (s.ctx) ntf_ctx_destroy(s.ctx);
+    }
+    delete sv;
+}
+
+}  // extern "C"

@@ -178,3 +178,29 @@ def job_data(job):
     X, _, _ = tucker_dense(job["dims"], job["core"], seed=job["seed"])
     G0, A0 = init_tucker(job["dims"], job["core"], seed=job["seed"] + 1)
     return X, G0, A0
+
+
+def job_data_torch(job, device="cuda"):
+    """Same recipe as job_data, drawn on the device with a seeded torch generator (used to
+    feed the serving benchmark without host-side generation of large jobs)."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(job["seed"]))
+    dims = job["dims"]
+    if job["model"] == "cp":
+        R = job["rank"]
+        A = [torch.rand((d, R), generator=g, device=device) * 0.9 + 0.1 for d in dims]
+        M = torch.einsum("ir,jr,kr->ijk", *A)
+        M *= 10.0 / M.mean()
+        X = torch.poisson(M, generator=g).float()
+        A0 = [torch.rand((d, R), generator=g, device=device) * 0.9 + 0.1 for d in dims]
+        return X.contiguous(), None, [a.contiguous() for a in A0]
+    J = job["core"]
+    core = torch.distributions.Gamma(torch.full(tuple(J), 2.0, device=device), 1.0).sample()
+    A = [torch.rand((d, j), generator=g, device=device) * 2.0 for d, j in zip(dims, J)]
+    M = torch.einsum("abc,ia,jb,kc->ijk", core, *A)
+    M *= 10.0 / M.mean()
+    X = torch.poisson(M, generator=g).float()
+    G0 = torch.rand(tuple(J), generator=g, device=device) * 0.9 + 0.1
+    A0 = [torch.rand((d, j), generator=g, device=device) * 0.9 + 0.1 for d, j in zip(dims, J)]
+    return X.contiguous(), G0.contiguous(), [a.contiguous() for a in A0]

@@ -1,10 +1,14 @@
 // Fused dense 3-way CP pass on the 5th-generation tensor cores (tcgen05, sm_103a).
 //
 // Same computation and partial-sum layouts as the FP32 pass (CPContr^(n) of P and Q,
-// Section 6.1; Theorem "CP block multiplicative update"; Xhat never stored).  A CTA of
-// 256 threads owns a tile of 128 rows j, a block of 128 columns k and a range of slabs i,
-// walked as a sequence of 64-column chunks (two per slab).  Thread (warp w, lane l) owns
-// tile row 32 (w % 4) + l (its TMEM lane) and the column half w / 4 of each chunk.
+// Section 6.1; Theorem "CP block multiplicative update"; Xhat never stored).  A CTA owns a
+// tile of 128 rows j, a block of 128 columns k and a range of slabs i, walked as a sequence
+// of 64-column chunks (two per slab).  Warps are specialised: warp 8 issues every TMA copy
+// and MMA, in chunk order, driven by mbarriers; warps 0..7 are the epilogue, thread
+// (warp w, lane l) owning tile row 32 (w % 4) + l (its TMEM lane) and the column half w / 4
+// of each chunk.  The epilogue warps signal per warp when an X stage, an X-hat buffer, a P
+// tile or the next slab's R operand is free / ready; nothing waits on a block-wide barrier
+// in the steady state.
 //
 // Per chunk n (slab i, columns k0 + 64 q):
 //   TMA       X chunk (128 x 64 FP32) into a 2- or 3-stage ring, issued that far ahead;
@@ -18,21 +22,24 @@
 //             padded to M = 128, B = the same P tile read MN-major),
 //             BF16 operands, FP32 accumulation in TMEM, overlapping the next epilogue.
 // At each slab boundary mode 1 reduces sum_j W[j][r] Bn[j][r] (shuffle reduce-scatter)
-// and mode 2 accumulates An[i][r] W[j][r] per row.  One thread issues TMA and MMAs;
-// completion is tracked with mbarriers whose waits are bounded: on timeout the kernel sets
-// the context's status word, waits (bounded) for its copies and MMAs, frees its TMEM and
-// returns.
+// and mode 2 accumulates An[i][r] W[j][r] per row.  Every wait on an mbarrier is bounded;
+// a wait that runs out raises a shared abort flag that ends the other waits at once; the
+// kernel then sets the context's status word, waits (bounded) for its copies and MMAs,
+// frees its TMEM and returns.
 #pragma once
 
 #include <cuda.h>
 #include <cuda_bf16.h>
+
+#include <type_traits>
 
 #include "ntf_internal.h"
 
 namespace ntf {
 namespace tc {
 
-constexpr int NT = 256;
+constexpr int EW = 256;  // epilogue threads (warps 0..7)
+constexpr int NT = EW + 32;  // + one issuer warp
 constexpr int ROWS = 128;  // tile rows
 constexpr int KBLK = 128;  // columns per CTA block
 constexpr int CH = 64;     // columns per chunk
@@ -165,28 +172,71 @@ __device__ __forceinline__ void expect_tx(uint32_t bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" :: "r"(bar), "r"(bytes) : "memory");
 }
 
-// P and Q with a compile-time beta class; P and Q are stored in BF16, so single-MUFU forms
-template <int BK>
-__device__ __forceinline__ void pq_fast(float beta, float x, float y, float &P, float &Q) {
-    if (BK == BK_IS) {
-        const float r = __fdividef(1.0f, y);
+// Hardware approximate transcendentals (single MUFU instructions, denormals flushed).
+__device__ __forceinline__ float mufu_rcp(float x) { float r; asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x)); return r; }
+__device__ __forceinline__ float mufu_rsqrt(float x) { float r; asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x)); return r; }
+__device__ __forceinline__ float mufu_sqrt(float x) { float r; asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x)); return r; }
+__device__ __forceinline__ float mufu_lg2(float x) { float r; asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x)); return r; }
+__device__ __forceinline__ float mufu_ex2(float x) { float r; asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x)); return r; }
+
+// One entry of the epilogue: P, Q (stored in BF16) and, with OBJ, the terms of d_beta(x|y)
+// (Section 3.2) split so that the per-entry work is a few MUFU / FMA instructions:
+//   KL : d = ln2 * x (lg2 x - lg2 y) + (y - x)          -> o1 += x (lg2 x - lg2 y), o2 += y - x
+//   IS : d = u - ln2 lg2 u - 1, u = x / y                -> o1 += lg2 u,            o2 += u - 1
+//   1/2: d = -4 (sqrt x - y / 2 sqrt y - x / 2 sqrt y)  -> o2 += d
+//   3/2: d = (x sqrt x + y sqrt y / 2 - 3 x sqrt y / 2) / (3/4)  -> o2 += d
+//   else: beta (beta - 1) d with ex2 / lg2                -> o2 += beta (beta - 1) d
+// The chunk's objective is o1 * ln2 + o2 (KL), o2 - o1 * ln2 (IS), o2 / (beta (beta - 1))
+// for the general class and o2 for 1/2, 3/2.  These
+// are the definition evaluated directly: where x ~ y its terms cancel, which costs about
+// u_fp32 * x^beta / d relative accuracy per entry (the FP32 path keeps log1p / expm1 forms).
+template <int BK, bool OBJ>
+__device__ __forceinline__ void point(float beta, float x, float y, float &P, float &Q, float &o1, float &o2) {
+    if (BK == BK_KL) {
+        P = x * mufu_rcp(y);
+        Q = 1.0f;
+        if (OBJ) {
+            o1 = fmaf(x, mufu_lg2(fmaxf(x, 1e-30f)) - mufu_lg2(y), o1);
+            o2 += y - x;
+        }
+    } else if (BK == BK_IS) {
+        const float r = mufu_rcp(y);
         Q = r;
         P = x * r * r;
+        if (OBJ) {
+            const float u = x * r;
+            o1 += mufu_lg2(u);
+            o2 += u - 1.0f;
+        }
     } else if (BK == BK_HALF) {
-        const float s = rsqrtf(y);
-        Q = s;
-        P = x * s * s * s;
-    } else if (BK == BK_KL) {
-        P = __fdividef(x, y);
-        Q = 1.0f;
+        const float sr = mufu_rsqrt(y);
+        Q = sr;
+        P = x * sr * sr * sr;
+        if (OBJ) o2 += -4.0f * (mufu_sqrt(x) - 0.5f * y * sr - 0.5f * x * sr);
     } else if (BK == BK_THREEHALF) {
-        const float s = rsqrtf(y);
-        Q = y * s;
-        P = x * s;
+        const float sr = mufu_rsqrt(y), sy = y * sr;
+        Q = sy;
+        P = x * sr;
+        if (OBJ) o2 += (x * mufu_sqrt(x) + 0.5f * y * sy - 1.5f * x * sy) * (1.0f / 0.75f);
     } else {
-        Q = __powf(y, beta - 1.0f);
-        P = __fdividef(x * Q, y);
+        const float ly = mufu_lg2(y);
+        Q = mufu_ex2((beta - 1.0f) * ly);
+        P = x * Q * mufu_rcp(y);
+        if (OBJ) {
+            const float yb = mufu_ex2(beta * ly);
+            const float xb = x > 0.0f ? mufu_ex2(beta * mufu_lg2(x)) : 0.0f;
+            o2 += xb + (beta - 1.0f) * yb - beta * x * Q;
+        }
     }
+}
+
+template <int BK>
+__device__ __forceinline__ float obj_combine(float beta, float o1, float o2) {
+    const float ln2 = 0.6931471805599453f;
+    if (BK == BK_KL) return fmaf(o1, ln2, o2);
+    if (BK == BK_IS) return fmaf(-o1, ln2, o2);
+    if (BK == BK_GEN) return o2 / (beta * (beta - 1.0f));
+    return o2;
 }
 
 // sum over the 32 lanes of v[k] for k < 16: afterwards lane l < 16 holds the sum for k = l
@@ -225,17 +275,21 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
     __nv_bfloat16 *CdT = (__nv_bfloat16 *)(sm + L.cdt);
     __nv_bfloat16 *KnT = (__nv_bfloat16 *)(sm + L.knt);
     __nv_bfloat16 *KdT = (__nv_bfloat16 *)(sm + L.kdt);
-    uint64_t *bar_x = (uint64_t *)(sm + L.misc);  // [NS]
-    uint64_t *bar_g1 = bar_x + 3;                  // [2]
-    uint64_t *bar_g2 = bar_x + 5;                  // [2]
-    uint32_t *tslot = (uint32_t *)(bar_x + 7);
-    float *red = (float *)(sm + L.misc + 64);          // [4 quarters][32] (+[4][32] DEN)
-    double *dred = (double *)(sm + L.misc + 64 + 1024);  // [8]
+    // mbarriers: X stage full / empty, X-hat buffer full / empty, P tile full, contractions
+    // done, next slab's R written
+    uint64_t *bars = (uint64_t *)(sm + L.misc);
+    uint64_t *x_full = bars, *x_empty = bars + 3, *g1_full = bars + 6, *d1_empty = bars + 8;
+    uint64_t *p_full = bars + 10, *g2_done = bars + 12, *r_full = bars + 14;
+    uint32_t *tslot = (uint32_t *)(sm + L.misc + 128);
+    volatile int *abort_flag = (volatile int *)(sm + L.misc + 136);
+    float *red = (float *)(sm + L.misc + 192);            // [4 quarters][32] (+[4][32] DEN)
+    double *dred = (double *)(sm + L.misc + 192 + 1024);  // [8]
     float *srow = (float *)(sm + L.misc + 2048);          // [3 slabs][rec0, num0, den0][32]
 
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    const int quarter = warp & 3, half = warp >> 2;
-    const int row = 32 * quarter + lane;  // tile row = TMEM lane
+    const bool issuer = warp == EW / 32;
+    const int quarter = warp & 3, half = (warp >> 2) & 1;
+    const int row = 32 * quarter + lane;  // tile row = TMEM lane (epilogue warps)
     int b = blockIdx.x;
     const int is = b % a.n_is;
     b /= a.n_is;
@@ -246,11 +300,29 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
     const int J = a.J, K = a.K;
     const int j0 = jt * ROWS, k0 = kb * KBLK;
     const int j = j0 + row;
-    const bool jv = j < J;
+    const bool jv = !issuer && j < J;
     const int NC = 2 * (i1 - i0);
-    const int r0 = 16 * half;  // this thread's rank slice for slab operands and folds
+    const int r0 = 16 * half;
 
-    // ---- per-CTA constants ---------------------------------------------------------------
+    auto wait = [&](uint64_t *bar, uint32_t phase) -> bool {
+        const uint32_t ba = su32(bar);
+        for (int it = 0; it < WAIT_LIMIT; ++it) {
+            uint32_t done;
+            asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                         : "=r"(done) : "r"(ba), "r"(phase) : "memory");
+            if (done) return true;
+            if (*abort_flag) return false;
+        }
+        *abort_flag = 1;
+        return false;
+    };
+    auto arrive = [&](uint64_t *bar) {  // one arrival per warp, after the warp's accesses
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" :: "r"(su32(bar)) : "memory");
+    };
+    auto epi_sync = [&]() { asm volatile("bar.sync 1, %0;\n" :: "n"(EW) : "memory"); };
+
+    // ---- per-CTA constants (epilogue threads) ----------------------------------------------
     float brec[16], bn[16], bd[16];
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
@@ -258,8 +330,7 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
         bn[r] = (jv && (M1 || M3)) ? __ldg(a.num[1] + (int64_t)j * RP + r0 + r) : 0.0f;
         bd[r] = (jv && (M1 || M3) && DEN) ? __ldg(a.den[1] + (int64_t)j * RP + r0 + r) : 0.0f;
     }
-    {
-        // Crec block (hi / lo), TF32 K-major [128 cols][32 rank]; thread: column `row`, rank slice r0
+    if (!issuer) {
         const int kc = k0 + row;
         const bool kv = kc < K;
 #pragma unroll
@@ -275,7 +346,6 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
             *reinterpret_cast<float4 *>(Cl + swf(row, r0 + 4 * q)) = make_float4(l[0], l[1], l[2], l[3]);
         }
         if (RW) {
-            // Cn^T, Cd^T: BF16 [32 rank][128 cols] as two 64-column atoms; thread: column `row`
 #pragma unroll
             for (int r = 0; r < 16; ++r) {
                 const int rr = r0 + r;
@@ -287,36 +357,14 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
             }
         }
     }
-    if (t == 0) {
-        for (int q = 0; q < 7; ++q) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" :: "r"(su32(bar_x + q)));
-        asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
-    }
-    __syncthreads();
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;\n" :: "r"(su32(tslot)));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
-    }
-    fence_before();
-    __syncthreads();
-    fence_after();
-    const uint32_t tmem = *tslot;
-    const uint32_t lane_off = (uint32_t)(32 * quarter) << 16;
-    const uint32_t t_d1 = tmem;          // 2 x 64 columns
-    const uint32_t t_w = tmem + 128;     // 32
-    const uint32_t t_wd = tmem + 160;    // 32
-    const uint32_t t_n3 = tmem + 256;    // 128
-    const uint32_t t_n3d = tmem + 384;   // 128
-
-    // the first-mode factor rows of slab i (reconstruction, numerator, denominator) are
-    // staged once in shared memory, in a ring of three slabs
-    auto stage_rows = [&](int i) {
+    auto stage_rows = [&](int i) {  // factor rows of slab i for R / KR / folds, ring of 3
         if (t < 96) {
             const int f = t >> 5, r = t & 31;
             const float *src = f == 0 ? a.rec[0] : f == 1 ? a.num[0] : a.den[0];
             srow[(i % 3) * 96 + t] = (f == 2 && !DEN) ? 0.0f : __ldg(src + (int64_t)i * RP + r);
         }
     };
-    auto slab_rows = [&](int i) {  // R (hi/lo) for slab i: thread writes row `row`, rank slice r0
+    auto slab_rows = [&](int i) {  // R (hi/lo) of slab i: row `row`, rank slice r0
         const float *ar = srow + (i % 3) * 96 + r0;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -331,7 +379,7 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
             *reinterpret_cast<float4 *>(Rl + swf(row, r0 + 4 * q)) = make_float4(l[0], l[1], l[2], l[3]);
         }
     };
-    auto slab_kr = [&](int i) {  // KRn^T / KRd^T rows r0..r0+15, column `row` (tile row)
+    auto slab_kr = [&](int i) {  // KRn^T / KRd^T rows r0..r0+15, column `row`
         const float *an = srow + (i % 3) * 96 + 32 + r0, *ad = an + 32;
 #pragma unroll
         for (int r = 0; r < 16; ++r) {
@@ -340,254 +388,306 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
             if (DEN) KdT[(row >> 6) * 2048 + swh(rr, row & 63)] = __float2bfloat16_rn(ad[r] * bd[r]);
         }
     };
-    auto issue_x = [&](int n) {  // TMA of chunk n into stage n % NS
-        const int i = i0 + (n >> 1), q = n & 1;
-        const uint32_t bar = su32(bar_x + (n % NS));
-        const uint32_t dst = su32(Xs) + (n % NS) * 32768;
-        expect_tx(bar, 32768);
-        tma_2d(&xmap, dst, bar, k0 + CH * q, i * J + j0);
-        tma_2d(&xmap, dst + 16384, bar, k0 + CH * q + 32, i * J + j0);
-    };
-    auto issue_g1 = [&](int n) {  // GEMM1 of chunk n (3xTF32) into D1[n % 2]
-        const int q = n & 1;
-        const uint32_t d = t_d1 + 64 * (n & 1);
-        const uint32_t id = idesc_tf32(CH);
-        const uint32_t cb = su32(Cs) + q * 8192, cbl = su32(Cl) + q * 8192;
-#pragma unroll
-        for (int s = 0; s < 4; ++s) mma_tf32(d, sdesc(su32(Rl) + s * 32), sdesc(cb + s * 32), id, s > 0);
-#pragma unroll
-        for (int s = 0; s < 4; ++s) mma_tf32(d, sdesc(su32(Rs) + s * 32), sdesc(cbl + s * 32), id, 1);
-#pragma unroll
-        for (int s = 0; s < 4; ++s) mma_tf32(d, sdesc(su32(Rs) + s * 32), sdesc(cb + s * 32), id, 1);
-        mma_commit(su32(bar_g1 + (n & 1)));
-    };
-    auto issue_g2 = [&](int n) {  // contractions of chunk n from P[n % NP]
-        const int q = n & 1;
-        const uint32_t pb = su32(Ps) + (n % NP) * 16384, qb = su32(Qs) + (n % NP) * 16384;
-        if (RW) {
-            const uint32_t id = idesc_bf16(RP, false);
-#pragma unroll
-            for (int s = 0; s < 4; ++s) {
-                mma_bf16(t_w, sdesc(pb + s * 32), sdesc(su32(CnT) + q * 4096 + s * 32), id, (q > 0 || s > 0) ? 1u : 0u);
-                if (DEN) mma_bf16(t_wd, sdesc(qb + s * 32), sdesc(su32(CdT) + q * 4096 + s * 32), id, (q > 0 || s > 0) ? 1u : 0u);
-            }
+    if (t == EW) {
+        for (int q = 0; q < 15; ++q) {
+            const uint32_t cnt = (q >= 3 && q < 6) || (q >= 8 && q < 12) || q == 14 ? EW / 32 : 1;
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" :: "r"(su32(bars + q)), "r"(cnt));
         }
-        if (M3) {
-            const uint32_t id = idesc_bf16(CH, true);
-#pragma unroll
-            for (int s = 0; s < 8; ++s) {
-                const uint32_t ao = (s >> 2) * 4096 + (s & 3) * 32;
-                const uint32_t acc = (n >= 2 || s > 0) ? 1u : 0u;
-                mma_bf16(t_n3 + 64 * q, sdesc(su32(KnT) + ao), sdesc(pb + s * 2048, 16384, 1024), id, acc);
-                if (DEN) mma_bf16(t_n3d + 64 * q, sdesc(su32(KdT) + ao), sdesc(qb + s * 2048, 16384, 1024), id, acc);
-            }
-        }
-        mma_commit(su32(bar_g2 + (n % NP)));
-    };
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
+        *abort_flag = 0;
+    }
+    if (NC > 0) {
+        stage_rows(i0);
+        if (i0 + 1 < i1) stage_rows(i0 + 1);
+    }
+    __syncthreads();
+    if (issuer) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;\n" :: "r"(su32(tslot)));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
+    } else if (NC > 0) {
+        slab_rows(i0);
+        if (M3) slab_kr(i0);
+    }
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tslot;
+    const uint32_t lane_off = (uint32_t)(32 * quarter) << 16;
+    const uint32_t t_d1 = tmem, t_w = tmem + 128, t_wd = tmem + 160, t_n3 = tmem + 256, t_n3d = tmem + 384;
 
     float acc2[16], acc2d[16];
 #pragma unroll
     for (int r = 0; r < 16; ++r) acc2[r] = acc2d[r] = 0.0f;
     double obj_acc = 0.0;
-    bool ok = true;
 
-    auto fold = [&](int i) {  // modes 1 and 2 from W of slab i (GEMM2 complete)
-        float w[16], wd[16];
+    if (issuer) {
+        // ---- issuer warp: TMA of X, GEMM1, contractions, in chunk order ---------------------
+        if (lane == 0 && NC > 0) {
+            auto issue_x = [&](int n) {
+                const int i = i0 + (n >> 1), q = n & 1;
+                const uint32_t bar = su32(x_full + (n % NS));
+                const uint32_t dst = su32(Xs) + (n % NS) * 32768;
+                expect_tx(bar, 32768);
+                tma_2d(&xmap, dst, bar, k0 + CH * q, i * J + j0);
+                tma_2d(&xmap, dst + 16384, bar, k0 + CH * q + 32, i * J + j0);
+            };
+            auto issue_g1 = [&](int n) {
+                const int q = n & 1;
+                const uint32_t d = t_d1 + 64 * (n & 1);
+                const uint32_t id = idesc_tf32(CH);
+                const uint32_t cb = su32(Cs) + q * 8192, cbl = su32(Cl) + q * 8192;
 #pragma unroll
-        for (int r = 0; r < 16; ++r) w[r] = wd[r] = 0.0f;
-        if (ok) {
-            tmem_ld16(t_w + lane_off + r0, w);
-            if (DEN) tmem_ld16(t_wd + lane_off + r0, wd);
-        }
-        if (M2) {
-            const float *an = srow + (i % 3) * 96 + 32 + r0, *ad = an + 32;
+                for (int s = 0; s < 4; ++s) mma_tf32(d, sdesc(su32(Rl) + s * 32), sdesc(cb + s * 32), id, s > 0);
 #pragma unroll
-            for (int r = 0; r < 16; ++r) {
-                acc2[r] = fmaf(an[r], w[r], acc2[r]);
-                if (DEN) acc2d[r] = fmaf(ad[r], wd[r], acc2d[r]);
-            }
-        }
-        if (M1) {
+                for (int s = 0; s < 4; ++s) mma_tf32(d, sdesc(su32(Rs) + s * 32), sdesc(cbl + s * 32), id, 1);
 #pragma unroll
-            for (int r = 0; r < 16; ++r) {
-                w[r] *= bn[r];
-                if (DEN) wd[r] *= bd[r];
-            }
-            const float s = reduce_scatter16(w);
-            const float sd = DEN ? reduce_scatter16(wd) : 0.0f;
-            if (lane < 16) {
-                red[quarter * 32 + r0 + lane] = s;
-                if (DEN) red[128 + quarter * 32 + r0 + lane] = sd;
-            }
-            __syncthreads();
-            if (t < RP && ok) {
-                const int64_t slot = ((int64_t)(jt * a.n_kb + kb) * a.I + i) * RP + t;
-                a.p1n[slot] = red[t] + red[32 + t] + red[64 + t] + red[96 + t];
-                if (DEN) a.p1d[slot] = red[128 + t] + red[160 + t] + red[192 + t] + red[224 + t];
-            }
-            __syncthreads();
-        }
-    };
-
-    // ---- prologue --------------------------------------------------------------------------
-    if (NC > 0) {
-        if (t == 0)
-            for (int q = 0; q < NS - 1 && q < NC; ++q) issue_x(q);
-        stage_rows(i0);
-        if (i0 + 1 < i1) stage_rows(i0 + 1);
-        __syncthreads();
-        slab_rows(i0);
-        if (M3) slab_kr(i0);
-        fence_async_smem();
-        __syncthreads();
-        if (t == 0) {
+                for (int s = 0; s < 4; ++s) mma_tf32(d, sdesc(su32(Rs) + s * 32), sdesc(cb + s * 32), id, 1);
+                mma_commit(su32(g1_full + (n & 1)));
+            };
+            auto issue_g2 = [&](int n) {
+                const int q = n & 1;
+                const uint32_t pb = su32(Ps) + (n % NP) * 16384, qb = su32(Qs) + (n % NP) * 16384;
+                if (RW) {
+                    const uint32_t id = idesc_bf16(RP, false);
+#pragma unroll
+                    for (int s = 0; s < 4; ++s) {
+                        const uint32_t acc = (q > 0 || s > 0) ? 1u : 0u;
+                        mma_bf16(t_w, sdesc(pb + s * 32), sdesc(su32(CnT) + q * 4096 + s * 32), id, acc);
+                        if (DEN) mma_bf16(t_wd, sdesc(qb + s * 32), sdesc(su32(CdT) + q * 4096 + s * 32), id, acc);
+                    }
+                }
+                if (M3) {
+                    const uint32_t id = idesc_bf16(CH, true);
+#pragma unroll
+                    for (int s = 0; s < 8; ++s) {
+                        const uint32_t ao = (s >> 2) * 4096 + (s & 3) * 32;
+                        const uint32_t acc = (n >= 2 || s > 0) ? 1u : 0u;
+                        mma_bf16(t_n3 + 64 * q, sdesc(su32(KnT) + ao), sdesc(pb + s * 2048, 16384, 1024), id, acc);
+                        if (DEN) mma_bf16(t_n3d + 64 * q, sdesc(su32(KdT) + ao), sdesc(qb + s * 2048, 16384, 1024), id, acc);
+                    }
+                }
+                mma_commit(su32(g2_done + (n % NP)));
+            };
+            for (int c = 0; c < NS && c < NC; ++c) issue_x(c);
             fence_after();
             issue_g1(0);
+            for (int n = 0; n < NC && !*abort_flag; ++n) {
+                const int m = n + 1;
+                if (m < NC) {
+                    bool ok = true;
+                    if (m >= 2) ok = wait(d1_empty + (m & 1), ((m >> 1) - 1) & 1);
+                    if (ok && (m & 1) == 0) ok = wait(r_full, ((m >> 1) - 1) & 1);
+                    if (!ok) break;
+                    fence_after();
+                    issue_g1(m);
+                }
+                if (n + NS < NC) {
+                    if (!wait(x_empty + (n % NS), (n / NS) & 1)) break;
+                    issue_x(n + NS);
+                }
+                if (!wait(p_full + (n % NP), (n / NP) & 1)) break;
+                fence_after();
+                issue_g2(n);
+            }
         }
-    }
-
-    // ---- chunk loop ------------------------------------------------------------------------
-    for (int n = 0; n < NC && ok; ++n) {
-        const int i = i0 + (n >> 1), q = n & 1;
-        if (q == 0 && n > 0) {
-            // slab boundary: previous slab's contractions done -> fold W, refresh KRn^T
-            if (!mbar_wait(su32(bar_g2 + ((n - 1) % NP)), ((n - 1) / NP) & 1)) ok = false;
-            ok = __all_sync(0xffffffffu, ok);
+        __syncwarp();
+    } else {
+        // ---- epilogue warps ---------------------------------------------------------------
+        auto fold = [&](int i) {  // modes 1 and 2 from W of slab i (contractions complete)
+            float w[16], wd[16];
+#pragma unroll
+            for (int r = 0; r < 16; ++r) w[r] = wd[r] = 0.0f;
+            if (!__any_sync(0xffffffffu, *abort_flag != 0)) {  // warp-uniform before tcgen05.ld
+                tmem_ld16(t_w + lane_off + r0, w);
+                if (DEN) tmem_ld16(t_wd + lane_off + r0, wd);
+            }
+            if (M2) {
+                const float *an = srow + (i % 3) * 96 + 32 + r0, *ad = an + 32;
+#pragma unroll
+                for (int r = 0; r < 16; ++r) {
+                    acc2[r] = fmaf(an[r], w[r], acc2[r]);
+                    if (DEN) acc2d[r] = fmaf(ad[r], wd[r], acc2d[r]);
+                }
+            }
+            if (M1) {
+#pragma unroll
+                for (int r = 0; r < 16; ++r) {
+                    w[r] *= bn[r];
+                    if (DEN) wd[r] *= bd[r];
+                }
+                const float sr = reduce_scatter16(w);
+                const float sd = DEN ? reduce_scatter16(wd) : 0.0f;
+                if (lane < 16) {
+                    red[quarter * 32 + r0 + lane] = sr;
+                    if (DEN) red[128 + quarter * 32 + r0 + lane] = sd;
+                }
+                epi_sync();
+                if (t < RP && !*abort_flag) {
+                    const int64_t slot = ((int64_t)(jt * a.n_kb + kb) * a.I + i) * RP + t;
+                    a.p1n[slot] = red[t] + red[32 + t] + red[64 + t] + red[96 + t];
+                    if (DEN) a.p1d[slot] = red[128 + t] + red[160 + t] + red[192 + t] + red[224 + t];
+                }
+                epi_sync();
+            }
+        };
+        for (int n = 0; n < NC; ++n) {
+            const int i = i0 + (n >> 1), q = n & 1;
+            if (q == 0 && n > 0) {
+                // slab boundary: rows of slab i + 1 staged for the next R; previous slab's
+                // contractions complete -> fold W, refresh KRn^T for slab i
+                if (i + 1 < i1) stage_rows(i + 1);
+                wait(g2_done + ((n - 1) % NP), ((n - 1) / NP) & 1);
+                fence_after();
+                epi_sync();  // staged rows visible to all epilogue warps
+                if (RW) fold(i - 1);
+                if (M3) slab_kr(i);
+            } else if (n >= NP) {
+                wait(g2_done + (n % NP), ((n - NP) / NP) & 1);  // P tile n % NP free again
+            }
+            wait(g1_full + (n & 1), (n >> 1) & 1);
+            wait(x_full + (n % NS), (n / NS) & 1);
             fence_after();
-            if (RW) fold(i - 1);
-            if (M3 && ok) slab_kr(i);
-        }
-        if (q == 0 && n > 0 && i + 1 < i1) stage_rows(i + 1);
-        if (ok && !mbar_wait(su32(bar_g1 + (n & 1)), (n >> 1) & 1)) ok = false;
-        ok = __all_sync(0xffffffffu, ok);
-        if (q == 1 && n + 1 < NC) {
-            // next chunk opens slab i + 1: its GEMM1 needs the next R (this chunk's GEMM1 is done)
-            slab_rows(i + 1);
-            fence_async_smem();
-            ok = __syncthreads_and(ok ? 1 : 0) != 0;
-        }
-        if (t == 0 && ok && n + 1 < NC) {
-            fence_after();
-            issue_g1(n + 1);
-        }
-        if (n >= NP && ok && !mbar_wait(su32(bar_g2 + (n % NP)), ((n - NP) / NP) & 1)) ok = false;
-        if (ok && !mbar_wait(su32(bar_x + (n % NS)), (n / NS) & 1)) ok = false;
-        ok = __all_sync(0xffffffffu, ok);
-        fence_after();
-        // ---- epilogue of chunk n: 32 columns of row `row` ---------------------------------
-        if (ok) {
             float xh[32];
-            tmem_ld32(t_d1 + 64 * (n & 1) + lane_off + 32 * half, xh);
-            const float *xa = Xs + (n % NS) * 8192 + half * 4096;
+            if (!__any_sync(0xffffffffu, *abort_flag != 0)) tmem_ld32(t_d1 + 64 * (n & 1) + lane_off + 32 * half, xh);
+            else {
+#pragma unroll
+                for (int c = 0; c < 32; ++c) xh[c] = 0.0f;
+            }
+            fence_before();
+            arrive(d1_empty + (n & 1));
+            if (q == 1 && n + 1 < NC) {
+                // this chunk's GEMM1 is complete, so R can take slab i + 1 (needed by GEMM1 of
+                // the next chunk, which the issuer starts once every warp has arrived)
+                slab_rows(i + 1);
+                fence_async_smem();
+                arrive(r_full);
+            }
+            float xv[32];
+            {
+                const float *xa = Xs + (n % NS) * 8192 + half * 4096;
+#pragma unroll
+                for (int g = 0; g < 8; ++g) {
+                    const float4 v = *reinterpret_cast<const float4 *>(xa + swf(row, 4 * g));
+                    xv[4 * g] = v.x; xv[4 * g + 1] = v.y; xv[4 * g + 2] = v.z; xv[4 * g + 3] = v.w;
+                }
+            }
+            arrive(x_empty + (n % NS));
             __nv_bfloat16 *pa = Ps + (n % NP) * 8192;
             __nv_bfloat16 *qa = Qs + (n % NP) * 8192;
             const int kc = k0 + CH * q + 32 * half;
-            float objf = 0.0f;
+            float o1 = 0.0f, o2 = 0.0f;
+            // full 32-column strip of a valid row: no per-entry masks
+            auto body = [&](auto full_tag) {
+                constexpr bool FULL = decltype(full_tag)::value;
 #pragma unroll
-            for (int g = 0; g < 4; ++g) {
-                const float4 x0 = *reinterpret_cast<const float4 *>(xa + swf(row, 8 * g));
-                const float4 x1 = *reinterpret_cast<const float4 *>(xa + swf(row, 8 * g + 4));
-                const float xv[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
-                float pv[8], qv[8];
+                for (int g = 0; g < 4; ++g) {
+                    float pv[8], qv[8];
 #pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    const bool v = jv && (kc + 8 * g + c) < K;
-                    float x = xv[c];
-                    if (BK == BK_IS) x = fmaxf(x, a.eps_x);
-                    const float y = fmaxf(xh[8 * g + c], a.eps);
-                    float P, Q;
-                    pq_fast<BK>(a.beta, x, y, P, Q);
-                    if (OBJ && v) objf += dbeta_stable(BK, a.beta, x, y);
-                    pv[c] = v ? P : 0.0f;
-                    qv[c] = v ? Q : 0.0f;
-                }
-                const int kk = 32 * half + 8 * g;
-                __nv_bfloat162 h0 = __floats2bfloat162_rn(pv[0], pv[1]), h1 = __floats2bfloat162_rn(pv[2], pv[3]);
-                __nv_bfloat162 h2 = __floats2bfloat162_rn(pv[4], pv[5]), h3 = __floats2bfloat162_rn(pv[6], pv[7]);
-                uint4 u;
-                u.x = *reinterpret_cast<uint32_t *>(&h0); u.y = *reinterpret_cast<uint32_t *>(&h1);
-                u.z = *reinterpret_cast<uint32_t *>(&h2); u.w = *reinterpret_cast<uint32_t *>(&h3);
-                *reinterpret_cast<uint4 *>(pa + swh(row, kk)) = u;
-                if (DEN) {
-                    h0 = __floats2bfloat162_rn(qv[0], qv[1]); h1 = __floats2bfloat162_rn(qv[2], qv[3]);
-                    h2 = __floats2bfloat162_rn(qv[4], qv[5]); h3 = __floats2bfloat162_rn(qv[6], qv[7]);
+                    for (int c = 0; c < 8; ++c) {
+                        float x = xv[8 * g + c];
+                        if (BK == BK_IS) x = fmaxf(x, a.eps_x);
+                        const float y = fmaxf(xh[8 * g + c], a.eps);
+                        if (FULL) {
+                            point<BK, OBJ>(a.beta, x, y, pv[c], qv[c], o1, o2);
+                        } else {
+                            float P, Q, e1 = 0.0f, e2 = 0.0f;
+                            point<BK, OBJ>(a.beta, x, y, P, Q, e1, e2);
+                            const bool v = jv && (kc + 8 * g + c) < K;
+                            pv[c] = v ? P : 0.0f;
+                            qv[c] = v ? Q : 0.0f;
+                            if (OBJ && v) { o1 += e1; o2 += e2; }
+                        }
+                    }
+                    const int kk = 32 * half + 8 * g;
+                    __nv_bfloat162 h0 = __floats2bfloat162_rn(pv[0], pv[1]), h1 = __floats2bfloat162_rn(pv[2], pv[3]);
+                    __nv_bfloat162 h2 = __floats2bfloat162_rn(pv[4], pv[5]), h3 = __floats2bfloat162_rn(pv[6], pv[7]);
+                    uint4 u;
                     u.x = *reinterpret_cast<uint32_t *>(&h0); u.y = *reinterpret_cast<uint32_t *>(&h1);
                     u.z = *reinterpret_cast<uint32_t *>(&h2); u.w = *reinterpret_cast<uint32_t *>(&h3);
-                    *reinterpret_cast<uint4 *>(qa + swh(row, kk)) = u;
+                    *reinterpret_cast<uint4 *>(pa + swh(row, kk)) = u;
+                    if (DEN) {
+                        h0 = __floats2bfloat162_rn(qv[0], qv[1]); h1 = __floats2bfloat162_rn(qv[2], qv[3]);
+                        h2 = __floats2bfloat162_rn(qv[4], qv[5]); h3 = __floats2bfloat162_rn(qv[6], qv[7]);
+                        u.x = *reinterpret_cast<uint32_t *>(&h0); u.y = *reinterpret_cast<uint32_t *>(&h1);
+                        u.z = *reinterpret_cast<uint32_t *>(&h2); u.w = *reinterpret_cast<uint32_t *>(&h3);
+                        *reinterpret_cast<uint4 *>(qa + swh(row, kk)) = u;
+                    }
                 }
-            }
+            };
+            if (jv && kc + 32 <= K) body(std::true_type{});
+            else body(std::false_type{});
+            const float objf = OBJ ? obj_combine<BK>(a.beta, o1, o2) : 0.0f;
             if (OBJ) obj_acc += (double)objf;
+            fence_async_smem();
+            arrive(p_full + (n % NP));
         }
-        fence_async_smem();
-        fence_before();
-        ok = __syncthreads_and(ok ? 1 : 0) != 0;
-        if (t == 0 && ok) {
+        if (NC > 0) {
+            wait(g2_done + ((NC - 1) % NP), ((NC - 1) / NP) & 1);
             fence_after();
-            if (n + NS - 1 < NC) issue_x(n + NS - 1);
-            issue_g2(n);
+            if (RW) fold(i1 - 1);
         }
-    }
-    // ---- last slab's fold, CTA outputs -----------------------------------------------------
-    if (NC > 0) {
-        if (ok && !mbar_wait(su32(bar_g2 + ((NC - 1) % NP)), ((NC - 1) / NP) & 1)) ok = false;
-        ok = __all_sync(0xffffffffu, ok);
-        fence_after();
-        if (RW) fold(i1 - 1);
-        ok = __syncthreads_and(ok ? 1 : 0) != 0;
-    }
-    if (M2 && jv) {
-        const int64_t base = ((int64_t)(kb * a.n_is + is) * J + j) * RP + r0;
+        // ---- CTA outputs ------------------------------------------------------------------
+        const bool good = !__any_sync(0xffffffffu, *abort_flag != 0);
+        if (M2 && jv) {
+            const int64_t base = ((int64_t)(kb * a.n_is + is) * J + j) * RP + r0;
 #pragma unroll
-        for (int r = 0; r < 16; ++r) {
-            a.p2n[base + r] = acc2[r];
-            if (DEN) a.p2d[base + r] = acc2d[r];
-        }
-    }
-    if (M3 && quarter == 0) {
-        // N3^T lanes 0..31 = rank r = lane; this warp pair covers columns 64 half .. +63
-        const int64_t base = (int64_t)(jt * a.n_is + is) * K;
-#pragma unroll 1
-        for (int g = 0; g < 2; ++g) {
-            float v[32], vd[32];
-            const bool have = ok && NC > 0;
-            if (have) {
-                tmem_ld32(t_n3 + 64 * half + 32 * g, v);
-                if (DEN) tmem_ld32(t_n3d + 64 * half + 32 * g, vd);
+            for (int r = 0; r < 16; ++r) {
+                a.p2n[base + r] = acc2[r];
+                if (DEN) a.p2d[base + r] = acc2d[r];
             }
+        }
+        if (M3 && quarter == 0) {
+            const int64_t base = (int64_t)(jt * a.n_is + is) * K;
+#pragma unroll 1
+            for (int g = 0; g < 2; ++g) {
+                float v[32], vd[32];
+                const bool have = good && NC > 0;
+                if (have) {
+                    tmem_ld32(t_n3 + 64 * half + 32 * g, v);
+                    if (DEN) tmem_ld32(t_n3d + 64 * half + 32 * g, vd);
+                }
 #pragma unroll
-            for (int c = 0; c < 32; ++c) {
-                const int kc = k0 + 64 * half + 32 * g + c;
-                if (kc < K) {
-                    a.p3n[(base + kc) * RP + lane] = have ? v[c] : 0.0f;
-                    if (DEN) a.p3d[(base + kc) * RP + lane] = have ? vd[c] : 0.0f;
+                for (int c = 0; c < 32; ++c) {
+                    const int kc = k0 + 64 * half + 32 * g + c;
+                    if (kc < K) {
+                        a.p3n[(base + kc) * RP + lane] = have ? v[c] : 0.0f;
+                        if (DEN) a.p3d[(base + kc) * RP + lane] = have ? vd[c] : 0.0f;
+                    }
                 }
             }
         }
-    }
-    if (OBJ) {
-        double v = obj_acc;
+        if (OBJ) {
+            double v = obj_acc;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) dred[warp] = v;
-        __syncthreads();
-        if (t == 0) {
-            double s = 0.0;
-            for (int w = 0; w < NT / 32; ++w) s += dred[w];
-            a.obj[blockIdx.x] = s;
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) dred[warp] = v;
+            epi_sync();
+            if (t == 0) {
+                double s2 = 0.0;
+                for (int w = 0; w < EW / 32; ++w) s2 += dred[w];
+                a.obj[blockIdx.x] = s2;
+            }
         }
-    }
-    if (!ok && t == 0) {
-        // bounded waits for anything still in flight before the CTA's TMEM and smem go
-        for (int q = 0; q < NS; ++q) {
-            mbar_wait(su32(bar_x + q), 0);
-            mbar_wait(su32(bar_x + q), 1);
-        }
-        mbar_wait(su32(bar_g2), 0);
-        if (a.err) atomicExch(a.err, 1);
     }
     fence_before();
     __syncthreads();
-    if (warp == 0) {
+    if (*abort_flag && t == EW) {
+        // bounded waits (without the abort shortcut) for copies and MMAs still in flight
+        for (int q = 0; q < 15; ++q) {
+            for (int ph = 0; ph < 2; ++ph) {
+                for (int it = 0; it < (1 << 20); ++it) {
+                    uint32_t done;
+                    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                                 : "=r"(done) : "r"(su32(bars + q)), "r"(ph) : "memory");
+                    if (done) break;
+                }
+            }
+        }
+        if (a.err) atomicExch(a.err, 1);
+    }
+    __syncthreads();
+    if (issuer) {
         fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;\n" :: "r"(tmem));
     }

@@ -9,6 +9,9 @@ about u_bf16 * sqrt(sum w^2) / sum w ~ u_bf16 / sqrt(n_eff); with at least a few
 effective terms per output here that is below 2e-4, and the ratio Num/Den of one block
 update inherits it.  The bar below (TOL_TC = 1e-3 on each factor after one sweep, 2e-4 on
 the objective, which only sees the TF32 reconstruction) leaves a factor ~5 of margin.
+The objective on this path evaluates the definition of d_beta directly with single-MUFU
+logarithms / roots: near x = y its terms cancel, costing about u_fp32 * x^beta / d per
+entry, well inside 2e-4 on the noisy data used here.
 """
 import numpy as np
 import pytest

@@ -37,7 +37,7 @@ Cp3Plan cp3_plan(int I, int J, int K, int RP, int num_sms, int kb) {
     }
     p.n_is = best;
     p.grid = base * best;
-    p.parts1 = p.n_jt * p.n_kb;
+    p.parts1 = p.n_jt * p.n_kb * (p.tc ? 4 : 1);  // tensor-core pass: one per 32-row quarter
     p.parts2 = p.n_kb * p.n_is;
     p.parts3 = p.n_jt * p.n_is;
     return p;

@@ -3,12 +3,14 @@
 // Same computation and partial-sum layouts as the FP32 pass (CPContr^(n) of P and Q,
 // Section 6.1; Theorem "CP block multiplicative update"; Xhat never stored).  A CTA owns a
 // tile of 128 rows j, a block of 128 columns k and a range of slabs i, walked as a sequence
-// of 64-column chunks (two per slab).  Warps are specialised: warp 8 issues every TMA copy
-// and MMA, in chunk order, driven by mbarriers; warps 0..7 are the epilogue, thread
-// (warp w, lane l) owning tile row 32 (w % 4) + l (its TMEM lane) and the column half w / 4
-// of each chunk.  The epilogue warps signal per warp when an X stage, an X-hat buffer, a P
-// tile or the next slab's R operand is free / ready; nothing waits on a block-wide barrier
-// in the steady state.
+// of 64-column chunks (two per slab).  Warps are specialised: warp 4 CG + 1 streams X
+// chunks into a shared-memory ring by TMA (and PF chunks further ahead into L2 by bulk
+// prefetch); warp 4 CG issues every MMA, in chunk order; warps 0..4 CG - 1 are the epilogue,
+// thread (warp w, lane l) owning tile row 32 (w % 4) + l (its TMEM lane), the column group
+// w / 4 (64 / CG columns) of each chunk and the rank slice w / 4 (32 / CG ranks) of the
+// row-side constants and folds.  The epilogue warps signal per warp, on mbarriers, when an
+// X stage, an X-hat buffer, a P tile or the next slab's R operand is free / ready; the only
+// block-wide wait is one named barrier per slab.
 //
 // Per chunk n (slab i, columns k0 + 64 q):
 //   TMA       X chunk (128 x 64 FP32) into a 2- or 3-stage ring, issued that far ahead;
@@ -21,8 +23,10 @@
 //             cols: N3^T[r][k] += sum_j KRn^T[r][j] P[j][k]  (A = KRn^T with the rank
 //             padded to M = 128, B = the same P tile read MN-major),
 //             BF16 operands, FP32 accumulation in TMEM, overlapping the next epilogue.
-// At each slab boundary mode 1 reduces sum_j W[j][r] Bn[j][r] (shuffle reduce-scatter)
-// and mode 2 accumulates An[i][r] W[j][r] per row.  Every wait on an mbarrier is bounded;
+// W and KRn^T are double-buffered per slab: during the second chunk of slab i, mode 1
+// reduces sum_j W[j][r] Bn[j][r] of slab i - 1 over each warp's 32 rows (shuffle
+// reduce-scatter; one partial per 32-row quarter, summed in fixed order later) and mode 2
+// accumulates An[i-1][r] W[j][r] per row, while the contractions of slab i proceed.  Every wait on an mbarrier is bounded;
 // a wait that runs out raises a shared abort flag that ends the other waits at once; the
 // kernel then sets the context's status word, waits (bounded) for its copies and MMAs,
 // frees its TMEM and returns.
@@ -38,26 +42,32 @@
 namespace ntf {
 namespace tc {
 
-constexpr int EW = 256;  // epilogue threads (warps 0..7)
-constexpr int NT = EW + 32;  // + one issuer warp
 constexpr int ROWS = 128;  // tile rows
 constexpr int KBLK = 128;  // columns per CTA block
 constexpr int CH = 64;     // columns per chunk
 constexpr int RP = 32;
+constexpr int CG = 4;      // column groups per chunk (epilogue warps = 4 CG)
+constexpr int CW = CH / CG;  // columns per epilogue thread and chunk
+constexpr int RS = RP / CG;  // ranks per epilogue thread in the row-side work
+constexpr int EW = 128 * CG;  // epilogue threads
+constexpr int NT = EW + 64;   // + the MMA issuer warp + the TMA producer warp
+constexpr int PF = 6;         // X chunks prefetched into L2 ahead of the shared-memory ring
+static_assert(CW % 8 == 0 && RS % 4 == 0 && 32 % CW == 0, "column groups");
 
 struct Layout {
     int x, p, q, r, rl, c, cl, cnt, cdt, knt, kdt, misc, total;
     int ns;  // X stages
     int np;  // P / Q buffers
+    int nk;  // KRn^T / KRd^T buffers (2: slab i + 1's is written while slab i's is read)
 };
 
 // 1024-aligned regions.  The column contraction reads KRn^T as an M = 128 operand whose
 // rows 32..127 are padding: those rows only feed accumulator rows that are never read, so
-// only the 32 real rows are stored (two 4 KB K-atoms) and the padding reads fall on the
-// 16 KB that follow (the Crec / R tiles), which stay inside the allocation.
-__host__ __device__ constexpr int layout_bytes(bool rows, bool m3, bool den, int ns, int np) {
+// only the 32 real rows are stored (two 4 KB K-atoms per buffer) and the padding reads fall
+// on the 16 KB that follow (the Crec / R tiles), which stay inside the allocation.
+__host__ __device__ constexpr int layout_bytes(bool rows, bool m3, bool den, int ns, int np, int nk) {
     return ns * 32768 + np * 16384 * (den ? 2 : 1) + 4 * 16384 + (rows ? 8192 : 0) + ((rows && den) ? 8192 : 0) +
-           (m3 ? 8192 : 0) + ((m3 && den) ? 8192 : 0) + 4096 + 1024;
+           (m3 ? nk * 8192 : 0) + ((m3 && den) ? nk * 8192 : 0) + 4096 + 1024;
 }
 
 __host__ __device__ constexpr Layout make_layout(bool rows, bool m3, bool den) {
@@ -65,16 +75,18 @@ __host__ __device__ constexpr Layout make_layout(bool rows, bool m3, bool den) {
     constexpr int kMax = 232448;  // opt-in shared memory per CTA
     L.ns = 2;
     L.np = 1;
-    if (layout_bytes(rows, m3, den, 2, 2) <= kMax) L.np = 2;
-    if (layout_bytes(rows, m3, den, 3, L.np) <= kMax) L.ns = 3;
+    L.nk = 1;
+    if (layout_bytes(rows, m3, den, 2, 2, 1) <= kMax) L.np = 2;
+    if (layout_bytes(rows, m3, den, 2, L.np, 2) <= kMax) L.nk = 2;
+    if (layout_bytes(rows, m3, den, 3, L.np, L.nk) <= kMax) L.ns = 3;
     int o = 0;
     L.x = o; o += L.ns * 32768;
     L.p = o; o += L.np * 16384;
     L.q = o; o += den ? L.np * 16384 : 0;
-    L.knt = o; o += m3 ? 8192 : 0;            // padding rows read the C tiles below
+    L.knt = o; o += m3 ? L.nk * 8192 : 0;            // padding rows read the C tiles below
     L.c = o; o += 16384;
     L.cl = o; o += 16384;
-    L.kdt = o; o += (m3 && den) ? 8192 : 0;   // padding rows read the R tiles below
+    L.kdt = o; o += (m3 && den) ? L.nk * 8192 : 0;   // padding rows read the R tiles below
     L.r = o; o += 16384;
     L.rl = o; o += 16384;
     L.cnt = o; o += rows ? 8192 : 0;
@@ -138,6 +150,21 @@ __device__ __forceinline__ void tmem_ld16(uint32_t addr, float *v) {
 #pragma unroll
     for (int c = 0; c < 16; ++c) v[c] = __uint_as_float(r[c]);
 }
+__device__ __forceinline__ void tmem_ld8(uint32_t addr, float *v) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(addr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+    for (int c = 0; c < 8; ++c) v[c] = __uint_as_float(r[c]);
+}
+template <int N>
+__device__ __forceinline__ void tmem_ld(uint32_t addr, float *v) {
+    if (N == 32) tmem_ld32(addr, v);
+    else if (N == 16) tmem_ld16(addr, v);
+    else tmem_ld8(addr, v);
+}
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
@@ -167,6 +194,9 @@ __device__ __forceinline__ int swh(int row, int k) { return row * 64 + ((((k >> 
 __device__ __forceinline__ void tma_2d(const CUtensorMap *map, uint32_t dst, uint32_t bar, int x, int y) {
     asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n"
                  :: "r"(dst), "l"(map), "r"(x), "r"(y), "r"(bar) : "memory");
+}
+__device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap *map, int x, int y) {
+    asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];\n" :: "l"(map), "r"(x), "r"(y) : "memory");
 }
 __device__ __forceinline__ void expect_tx(uint32_t bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" :: "r"(bar), "r"(bytes) : "memory");
@@ -239,11 +269,12 @@ __device__ __forceinline__ float obj_combine(float beta, float o1, float o2) {
     return o2;
 }
 
-// sum over the 32 lanes of v[k] for k < 16: afterwards lane l < 16 holds the sum for k = l
-__device__ __forceinline__ float reduce_scatter16(float v[16]) {
+// sum over the 32 lanes of v[k] for k < N: afterwards lane l holds the sum for k = l % N
+template <int N>
+__device__ __forceinline__ float reduce_scatter(float v[N]) {
     const int lane = threadIdx.x & 31;
 #pragma unroll
-    for (int k = 8; k >= 1; k >>= 1) {
+    for (int k = N / 2; k >= 1; k >>= 1) {
         const bool upper = (lane & k) != 0;
 #pragma unroll
         for (int q = 0; q < k; ++q) {
@@ -252,7 +283,10 @@ __device__ __forceinline__ float reduce_scatter16(float v[16]) {
             v[q] = keep + __shfl_xor_sync(0xffffffffu, send, k);
         }
     }
-    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 16);
+    float s = v[0];
+#pragma unroll
+    for (int o = N; o < 32; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
 }
 
 template <int MS, int BK>
@@ -261,7 +295,7 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
     constexpr bool M1 = (MS & PM_M1) != 0, M2 = (MS & PM_M2) != 0, M3 = (MS & PM_M3) != 0;
     constexpr bool OBJ = (MS & PM_OBJ) != 0, RW = M1 || M2;
     constexpr Layout L = make_layout(RW, M3, DEN);
-    constexpr int NP = L.np, NS = L.ns;
+    constexpr int NP = L.np, NS = L.ns, NK = L.nk;
     extern __shared__ __align__(1024) uint8_t smraw[];
     uint8_t *sm = (uint8_t *)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
     const float *Xs = (const float *)(sm + L.x);
@@ -282,13 +316,12 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
     uint64_t *p_full = bars + 10, *g2_done = bars + 12, *r_full = bars + 14;
     uint32_t *tslot = (uint32_t *)(sm + L.misc + 128);
     volatile int *abort_flag = (volatile int *)(sm + L.misc + 136);
-    float *red = (float *)(sm + L.misc + 192);            // [4 quarters][32] (+[4][32] DEN)
-    double *dred = (double *)(sm + L.misc + 192 + 1024);  // [8]
-    float *srow = (float *)(sm + L.misc + 2048);          // [3 slabs][rec0, num0, den0][32]
+    double *dred = (double *)(sm + L.misc + 192 + 1024);  // [EW / 32]
+    float *srow = (float *)(sm + L.misc + 2048);          // [4 slabs][rec0, num0, den0][32]
 
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    const bool issuer = warp == EW / 32;
-    const int quarter = warp & 3, half = (warp >> 2) & 1;
+    const bool issuer = warp == EW / 32, producer = warp == EW / 32 + 1, epi = warp < EW / 32;
+    const int quarter = warp & 3, cg = warp >> 2;
     const int row = 32 * quarter + lane;  // tile row = TMEM lane (epilogue warps)
     int b = blockIdx.x;
     const int is = b % a.n_is;
@@ -300,9 +333,9 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
     const int J = a.J, K = a.K;
     const int j0 = jt * ROWS, k0 = kb * KBLK;
     const int j = j0 + row;
-    const bool jv = !issuer && j < J;
+    const bool jv = epi && j < J;
     const int NC = 2 * (i1 - i0);
-    const int r0 = 16 * half;
+    const int r0 = RS * cg;
 
     auto wait = [&](uint64_t *bar, uint32_t phase) -> bool {
         const uint32_t ba = su32(bar);
@@ -323,18 +356,18 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
     auto epi_sync = [&]() { asm volatile("bar.sync 1, %0;\n" :: "n"(EW) : "memory"); };
 
     // ---- per-CTA constants (epilogue threads) ----------------------------------------------
-    float brec[16], bn[16], bd[16];
+    float brec[RS], bn[RS], bd[RS];
 #pragma unroll
-    for (int r = 0; r < 16; ++r) {
+    for (int r = 0; r < RS; ++r) {
         brec[r] = jv ? __ldg(a.rec[1] + (int64_t)j * RP + r0 + r) : 0.0f;
         bn[r] = (jv && (M1 || M3)) ? __ldg(a.num[1] + (int64_t)j * RP + r0 + r) : 0.0f;
         bd[r] = (jv && (M1 || M3) && DEN) ? __ldg(a.den[1] + (int64_t)j * RP + r0 + r) : 0.0f;
     }
-    if (!issuer) {
+    if (epi) {
         const int kc = k0 + row;
         const bool kv = kc < K;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < RS / 4; ++q) {
             float h[4], l[4];
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
@@ -347,7 +380,7 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
         }
         if (RW) {
 #pragma unroll
-            for (int r = 0; r < 16; ++r) {
+            for (int r = 0; r < RS; ++r) {
                 const int rr = r0 + r;
                 CnT[(row >> 6) * 2048 + swh(rr, row & 63)] =
                     __float2bfloat16_rn(kv ? __ldg(a.num[2] + (int64_t)kc * RP + rr) : 0.0f);
@@ -357,17 +390,24 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
             }
         }
     }
-    auto stage_rows = [&](int i) {  // factor rows of slab i for R / KR / folds, ring of 3
-        if (t < 96) {
-            const int f = t >> 5, r = t & 31;
-            const float *src = f == 0 ? a.rec[0] : f == 1 ? a.num[0] : a.den[0];
-            srow[(i % 3) * 96 + t] = (f == 2 && !DEN) ? 0.0f : __ldg(src + (int64_t)i * RP + r);
-        }
+    // Factor rows of slab i for R / KR / folds, in a ring of 4: slot (i + 2) % 4 is written at
+    // the start of slab i, after the barrier there, and its previous slab (i - 2) was last
+    // read by the fold during slab i - 1, before every warp reached that barrier; the first
+    // reader of slab i + 2 (R during slab i + 1) comes after the barrier of slab i + 1.
+    // Slabs i0 .. i0 + 2 are staged before the loop; at the start of slab i (after its
+    // barrier) threads 0..95 store slab i + 2 from a register loaded a slab earlier.
+    auto row_val = [&](int i) -> float {  // thread t < 96: entry t of slab i's staged rows
+        const int f = t >> 5, r = t & 31;
+        const float *src = f == 0 ? a.rec[0] : f == 1 ? a.num[0] : a.den[0];
+        return (f == 2 && !DEN) ? 0.0f : __ldg(src + (int64_t)i * RP + r);
+    };
+    auto stage_rows = [&](int i) {
+        if (t < 96) srow[(i & 3) * 96 + t] = row_val(i);
     };
     auto slab_rows = [&](int i) {  // R (hi/lo) of slab i: row `row`, rank slice r0
-        const float *ar = srow + (i % 3) * 96 + r0;
+        const float *ar = srow + (i & 3) * 96 + r0;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < RS / 4; ++q) {
             float h[4], l[4];
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
@@ -379,13 +419,14 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
             *reinterpret_cast<float4 *>(Rl + swf(row, r0 + 4 * q)) = make_float4(l[0], l[1], l[2], l[3]);
         }
     };
-    auto slab_kr = [&](int i) {  // KRn^T / KRd^T rows r0..r0+15, column `row`
-        const float *an = srow + (i % 3) * 96 + 32 + r0, *ad = an + 32;
+    auto slab_kr = [&](int i) {  // KRn^T / KRd^T of slab i: rows r0.. r0 + RS - 1, column `row`
+        const float *an = srow + (i & 3) * 96 + 32 + r0, *ad = an + 32;
+        __nv_bfloat16 *kn = KnT + ((i - i0) % NK) * 4096, *kd = KdT + ((i - i0) % NK) * 4096;
 #pragma unroll
-        for (int r = 0; r < 16; ++r) {
+        for (int r = 0; r < RS; ++r) {
             const int rr = r0 + r;
-            KnT[(row >> 6) * 2048 + swh(rr, row & 63)] = __float2bfloat16_rn(an[r] * bn[r]);
-            if (DEN) KdT[(row >> 6) * 2048 + swh(rr, row & 63)] = __float2bfloat16_rn(ad[r] * bd[r]);
+            kn[(row >> 6) * 2048 + swh(rr, row & 63)] = __float2bfloat16_rn(an[r] * bn[r]);
+            if (DEN) kd[(row >> 6) * 2048 + swh(rr, row & 63)] = __float2bfloat16_rn(ad[r] * bd[r]);
         }
     };
     if (t == EW) {
@@ -396,15 +437,16 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
         *abort_flag = 0;
     }
+    float rnext = 0.0f;  // slab i0 + 3's staged-row entry (threads t < 96)
     if (NC > 0) {
-        stage_rows(i0);
-        if (i0 + 1 < i1) stage_rows(i0 + 1);
+        for (int i = i0; i < i0 + 3 && i < i1; ++i) stage_rows(i);
+        if (t < 96 && i0 + 3 < i1) rnext = row_val(i0 + 3);
     }
     __syncthreads();
     if (issuer) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;\n" :: "r"(su32(tslot)));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
-    } else if (NC > 0) {
+    } else if (epi && NC > 0) {
         slab_rows(i0);
         if (M3) slab_kr(i0);
     }
@@ -414,24 +456,39 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
     fence_after();
     const uint32_t tmem = *tslot;
     const uint32_t lane_off = (uint32_t)(32 * quarter) << 16;
+    // TMEM columns: X-hat [2][64] | W, Wd of even / odd slabs [2][32 + 32] | N3 [128] | N3d [128]
     const uint32_t t_d1 = tmem, t_w = tmem + 128, t_wd = tmem + 160, t_n3 = tmem + 256, t_n3d = tmem + 384;
 
-    float acc2[16], acc2d[16];
+    float acc2[RS], acc2d[RS];
 #pragma unroll
-    for (int r = 0; r < 16; ++r) acc2[r] = acc2d[r] = 0.0f;
+    for (int r = 0; r < RS; ++r) acc2[r] = acc2d[r] = 0.0f;
     double obj_acc = 0.0;
 
-    if (issuer) {
-        // ---- issuer warp: TMA of X, GEMM1, contractions, in chunk order ---------------------
+    if (producer) {
+        // ---- producer warp: X chunks into the shared-memory ring, PF chunks ahead into L2 ----
         if (lane == 0 && NC > 0) {
-            auto issue_x = [&](int n) {
+            auto prefetch_x = [&](int n) {
+                const int i = i0 + (n >> 1), x = k0 + CH * (n & 1);
+                // only boxes that start inside the tensor (a ragged block's last chunk may not)
+                if (x < K) tma_prefetch_2d(&xmap, x, i * J + j0);
+                if (x + 32 < K) tma_prefetch_2d(&xmap, x + 32, i * J + j0);
+            };
+            for (int c = NS; c < NS + PF && c < NC; ++c) prefetch_x(c);
+            for (int n = 0; n < NC; ++n) {
+                if (n >= NS && !wait(x_empty + (n % NS), ((n - NS) / NS) & 1)) break;
                 const int i = i0 + (n >> 1), q = n & 1;
                 const uint32_t bar = su32(x_full + (n % NS));
                 const uint32_t dst = su32(Xs) + (n % NS) * 32768;
                 expect_tx(bar, 32768);
                 tma_2d(&xmap, dst, bar, k0 + CH * q, i * J + j0);
                 tma_2d(&xmap, dst + 16384, bar, k0 + CH * q + 32, i * J + j0);
-            };
+                if (n >= NS && n + PF < NC) prefetch_x(n + PF);
+            }
+        }
+        __syncwarp();
+    } else if (issuer) {
+        // ---- issuer warp: GEMM1 and the contractions, in chunk order ----------------------
+        if (lane == 0 && NC > 0) {
             auto issue_g1 = [&](int n) {
                 const int q = n & 1;
                 const uint32_t d = t_d1 + 64 * (n & 1);
@@ -446,15 +503,16 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
                 mma_commit(su32(g1_full + (n & 1)));
             };
             auto issue_g2 = [&](int n) {
-                const int q = n & 1;
+                const int q = n & 1, sb = (n >> 1) & 1;
+                const uint32_t kn = su32(KnT) + ((n >> 1) % NK) * 8192, kd = su32(KdT) + ((n >> 1) % NK) * 8192;
                 const uint32_t pb = su32(Ps) + (n % NP) * 16384, qb = su32(Qs) + (n % NP) * 16384;
                 if (RW) {
                     const uint32_t id = idesc_bf16(RP, false);
 #pragma unroll
                     for (int s = 0; s < 4; ++s) {
                         const uint32_t acc = (q > 0 || s > 0) ? 1u : 0u;
-                        mma_bf16(t_w, sdesc(pb + s * 32), sdesc(su32(CnT) + q * 4096 + s * 32), id, acc);
-                        if (DEN) mma_bf16(t_wd, sdesc(qb + s * 32), sdesc(su32(CdT) + q * 4096 + s * 32), id, acc);
+                        mma_bf16(t_w + 64 * sb, sdesc(pb + s * 32), sdesc(su32(CnT) + q * 4096 + s * 32), id, acc);
+                        if (DEN) mma_bf16(t_wd + 64 * sb, sdesc(qb + s * 32), sdesc(su32(CdT) + q * 4096 + s * 32), id, acc);
                     }
                 }
                 if (M3) {
@@ -463,13 +521,12 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
                     for (int s = 0; s < 8; ++s) {
                         const uint32_t ao = (s >> 2) * 4096 + (s & 3) * 32;
                         const uint32_t acc = (n >= 2 || s > 0) ? 1u : 0u;
-                        mma_bf16(t_n3 + 64 * q, sdesc(su32(KnT) + ao), sdesc(pb + s * 2048, 16384, 1024), id, acc);
-                        if (DEN) mma_bf16(t_n3d + 64 * q, sdesc(su32(KdT) + ao), sdesc(qb + s * 2048, 16384, 1024), id, acc);
+                        mma_bf16(t_n3 + 64 * q, sdesc(kn + ao), sdesc(pb + s * 2048, 16384, 1024), id, acc);
+                        if (DEN) mma_bf16(t_n3d + 64 * q, sdesc(kd + ao), sdesc(qb + s * 2048, 16384, 1024), id, acc);
                     }
                 }
                 mma_commit(su32(g2_done + (n % NP)));
             };
-            for (int c = 0; c < NS && c < NC; ++c) issue_x(c);
             fence_after();
             issue_g1(0);
             for (int n = 0; n < NC && !*abort_flag; ++n) {
@@ -482,10 +539,6 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
                     fence_after();
                     issue_g1(m);
                 }
-                if (n + NS < NC) {
-                    if (!wait(x_empty + (n % NS), (n / NS) & 1)) break;
-                    issue_x(n + NS);
-                }
                 if (!wait(p_full + (n % NP), (n / NP) & 1)) break;
                 fence_after();
                 issue_g2(n);
@@ -494,65 +547,73 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
         __syncwarp();
     } else {
         // ---- epilogue warps ---------------------------------------------------------------
-        auto fold = [&](int i) {  // modes 1 and 2 from W of slab i (contractions complete)
-            float w[16], wd[16];
+        auto fold = [&](int i) {  // modes 1 and 2 from W of slab i (its contractions complete)
+            const uint32_t wb = 64 * ((i - i0) & 1);
+            float w[RS], wd[RS];
 #pragma unroll
-            for (int r = 0; r < 16; ++r) w[r] = wd[r] = 0.0f;
+            for (int r = 0; r < RS; ++r) w[r] = wd[r] = 0.0f;
             if (!__any_sync(0xffffffffu, *abort_flag != 0)) {  // warp-uniform before tcgen05.ld
-                tmem_ld16(t_w + lane_off + r0, w);
-                if (DEN) tmem_ld16(t_wd + lane_off + r0, wd);
+                tmem_ld<RS>(t_w + wb + lane_off + r0, w);
+                if (DEN) tmem_ld<RS>(t_wd + wb + lane_off + r0, wd);
             }
             if (M2) {
-                const float *an = srow + (i % 3) * 96 + 32 + r0, *ad = an + 32;
+                const float *an = srow + (i & 3) * 96 + 32 + r0, *ad = an + 32;
 #pragma unroll
-                for (int r = 0; r < 16; ++r) {
+                for (int r = 0; r < RS; ++r) {
                     acc2[r] = fmaf(an[r], w[r], acc2[r]);
                     if (DEN) acc2d[r] = fmaf(ad[r], wd[r], acc2d[r]);
                 }
             }
             if (M1) {
 #pragma unroll
-                for (int r = 0; r < 16; ++r) {
+                for (int r = 0; r < RS; ++r) {
                     w[r] *= bn[r];
                     if (DEN) wd[r] *= bd[r];
                 }
-                const float sr = reduce_scatter16(w);
-                const float sd = DEN ? reduce_scatter16(wd) : 0.0f;
-                if (lane < 16) {
-                    red[quarter * 32 + r0 + lane] = sr;
-                    if (DEN) red[128 + quarter * 32 + r0 + lane] = sd;
+                // one partial per warp (its 32 rows of the tile), summed later in fixed order
+                const float sr = reduce_scatter<RS>(w);
+                const float sd = DEN ? reduce_scatter<RS>(wd) : 0.0f;
+                if (lane < RS && !*abort_flag) {
+                    const int64_t slot = (((int64_t)(jt * a.n_kb + kb) * 4 + quarter) * a.I + i) * RP + r0 + lane;
+                    a.p1n[slot] = sr;
+                    if (DEN) a.p1d[slot] = sd;
                 }
-                epi_sync();
-                if (t < RP && !*abort_flag) {
-                    const int64_t slot = ((int64_t)(jt * a.n_kb + kb) * a.I + i) * RP + t;
-                    a.p1n[slot] = red[t] + red[32 + t] + red[64 + t] + red[96 + t];
-                    if (DEN) a.p1d[slot] = red[128 + t] + red[160 + t] + red[192 + t] + red[224 + t];
-                }
-                epi_sync();
             }
         };
         for (int n = 0; n < NC; ++n) {
             const int i = i0 + (n >> 1), q = n & 1;
+            if (n >= NP) wait(g2_done + (n % NP), ((n - NP) / NP) & 1);  // P tile n % NP free again
             if (q == 0 && n > 0) {
-                // slab boundary: rows of slab i + 1 staged for the next R; previous slab's
-                // contractions complete -> fold W, refresh KRn^T for slab i
-                if (i + 1 < i1) stage_rows(i + 1);
-                wait(g2_done + ((n - 1) % NP), ((n - 1) / NP) & 1);
+                // slab boundary: rows of slab i + 2 staged; KRn^T of slab i written into the
+                // buffer last read by the contractions of slab i - NK, which are complete (the
+                // wait above covers chunk n - 1 or n - 2, and MMAs complete in order)
+                if (M3 && NK == 1 && NP == 2) {
+                    wait(g2_done + ((n - 1) % NP), ((n - 1) / NP) & 1);
+                }
                 fence_after();
-                epi_sync();  // staged rows visible to all epilogue warps
-                if (RW) fold(i - 1);
+                epi_sync();  // rows of slab i + 1 (stored at the previous boundary) visible
+                if (t < 96 && i + 2 < i1) {
+                    srow[((i + 2) & 3) * 96 + t] = rnext;
+                    if (i + 3 < i1) rnext = row_val(i + 3);
+                }
                 if (M3) slab_kr(i);
-            } else if (n >= NP) {
-                wait(g2_done + (n % NP), ((n - NP) / NP) & 1);  // P tile n % NP free again
+            }
+            if (RW && q == 1 && n >= 3) {
+                // fold slab i - 1: its last contraction (chunk n - 2) is complete, as the
+                // P-tile wait above covers chunk n - NP >= n - 2; W of slab i - 1 is rewritten
+                // by slab i + 1, whose contractions start only after this chunk's P tile
+                fence_after();
+                fold(i - 1);
+                fence_before();
             }
             wait(g1_full + (n & 1), (n >> 1) & 1);
             wait(x_full + (n % NS), (n / NS) & 1);
             fence_after();
-            float xh[32];
-            if (!__any_sync(0xffffffffu, *abort_flag != 0)) tmem_ld32(t_d1 + 64 * (n & 1) + lane_off + 32 * half, xh);
+            float xh[CW];
+            if (!__any_sync(0xffffffffu, *abort_flag != 0)) tmem_ld<CW>(t_d1 + 64 * (n & 1) + lane_off + CW * cg, xh);
             else {
 #pragma unroll
-                for (int c = 0; c < 32; ++c) xh[c] = 0.0f;
+                for (int c = 0; c < CW; ++c) xh[c] = 0.0f;
             }
             fence_before();
             arrive(d1_empty + (n & 1));
@@ -563,25 +624,27 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
                 fence_async_smem();
                 arrive(r_full);
             }
-            float xv[32];
+            float xv[CW];
             {
-                const float *xa = Xs + (n % NS) * 8192 + half * 4096;
+                // the X stage holds two 128 x 32 halves; this group's columns lie in one
+                const float *xa = Xs + (n % NS) * 8192 + ((CW * cg) >> 5) * 4096;
+                const int xc = (CW * cg) & 31;
 #pragma unroll
-                for (int g = 0; g < 8; ++g) {
-                    const float4 v = *reinterpret_cast<const float4 *>(xa + swf(row, 4 * g));
+                for (int g = 0; g < CW / 4; ++g) {
+                    const float4 v = *reinterpret_cast<const float4 *>(xa + swf(row, xc + 4 * g));
                     xv[4 * g] = v.x; xv[4 * g + 1] = v.y; xv[4 * g + 2] = v.z; xv[4 * g + 3] = v.w;
                 }
             }
             arrive(x_empty + (n % NS));
             __nv_bfloat16 *pa = Ps + (n % NP) * 8192;
             __nv_bfloat16 *qa = Qs + (n % NP) * 8192;
-            const int kc = k0 + CH * q + 32 * half;
+            const int kc = k0 + CH * q + CW * cg;
             float o1 = 0.0f, o2 = 0.0f;
             // full 32-column strip of a valid row: no per-entry masks
             auto body = [&](auto full_tag) {
                 constexpr bool FULL = decltype(full_tag)::value;
 #pragma unroll
-                for (int g = 0; g < 4; ++g) {
+                for (int g = 0; g < CW / 8; ++g) {
                     float pv[8], qv[8];
 #pragma unroll
                     for (int c = 0; c < 8; ++c) {
@@ -599,7 +662,7 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
                             if (OBJ && v) { o1 += e1; o2 += e2; }
                         }
                     }
-                    const int kk = 32 * half + 8 * g;
+                    const int kk = CW * cg + 8 * g;
                     __nv_bfloat162 h0 = __floats2bfloat162_rn(pv[0], pv[1]), h1 = __floats2bfloat162_rn(pv[2], pv[3]);
                     __nv_bfloat162 h2 = __floats2bfloat162_rn(pv[4], pv[5]), h3 = __floats2bfloat162_rn(pv[6], pv[7]);
                     uint4 u;
@@ -615,7 +678,7 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
                     }
                 }
             };
-            if (jv && kc + 32 <= K) body(std::true_type{});
+            if (jv && kc + CW <= K) body(std::true_type{});
             else body(std::false_type{});
             const float objf = OBJ ? obj_combine<BK>(a.beta, o1, o2) : 0.0f;
             if (OBJ) obj_acc += (double)objf;
@@ -632,7 +695,7 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
         if (M2 && jv) {
             const int64_t base = ((int64_t)(kb * a.n_is + is) * J + j) * RP + r0;
 #pragma unroll
-            for (int r = 0; r < 16; ++r) {
+            for (int r = 0; r < RS; ++r) {
                 a.p2n[base + r] = acc2[r];
                 if (DEN) a.p2d[base + r] = acc2d[r];
             }
@@ -640,16 +703,17 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
         if (M3 && quarter == 0) {
             const int64_t base = (int64_t)(jt * a.n_is + is) * K;
 #pragma unroll 1
-            for (int g = 0; g < 2; ++g) {
+            for (int g = 0; g < KBLK / (32 * CG); ++g) {
                 float v[32], vd[32];
                 const bool have = good && NC > 0;
+                const int cb = (KBLK / CG) * cg + 32 * g;
                 if (have) {
-                    tmem_ld32(t_n3 + 64 * half + 32 * g, v);
-                    if (DEN) tmem_ld32(t_n3d + 64 * half + 32 * g, vd);
+                    tmem_ld32(t_n3 + cb, v);
+                    if (DEN) tmem_ld32(t_n3d + cb, vd);
                 }
 #pragma unroll
                 for (int c = 0; c < 32; ++c) {
-                    const int kc = k0 + 64 * half + 32 * g + c;
+                    const int kc = k0 + cb + c;
                     if (kc < K) {
                         a.p3n[(base + kc) * RP + lane] = have ? v[c] : 0.0f;
                         if (DEN) a.p3d[(base + kc) * RP + lane] = have ? vd[c] : 0.0f;

@@ -125,7 +125,7 @@ struct Cp3Args {
     float beta, eps, eps_x;
     int n_jt, n_kb, n_is;  // grid decomposition: row tiles x column blocks x slab splits
     int vec16;             // 1: K % 4 == 0 and X 16-byte aligned (16-byte async copies)
-    float *p1n, *p1d;      // mode-1 partials [n_jt*n_kb][I][RP]
+    float *p1n, *p1d;      // mode-1 partials [parts1][I][RP] (parts1 = n_jt*n_kb, x4 on tensor cores)
     float *p2n, *p2d;      // mode-2 partials [n_kb*n_is][J][RP]
     float *p3n, *p3d;      // mode-3 partials [n_jt*n_is][K][RP]
     double *obj;           // per-CTA objective partials [grid]

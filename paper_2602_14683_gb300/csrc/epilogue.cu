@@ -124,6 +124,121 @@ cudaError_t mu_epilogue(const MuEpiArgs &e, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// Fixed-order FP64 sum over the G row groups of a [G][RP] block of per-thread partials.
+__device__ __forceinline__ double group_sum(double *sh, double v, int RP, int t) {
+    sh[t] = v;
+    __syncthreads();
+    double tot = 0.0;
+    if (t < RP)
+        for (int g = 0; g < (int)blockDim.x / RP; ++g) tot += sh[g * RP + t];
+    __syncthreads();
+    return tot;
+}
+
+__global__ void prep_kernel(PrepArgs p) {
+    __shared__ double sh[256];
+    int b = blockIdx.x, m = 0;
+    while (m < 2 && b >= row_blocks(p.rows[m], p.RP)) {
+        b -= row_blocks(p.rows[m], p.RP);
+        ++m;
+    }
+    const int RP = p.RP, G = blockDim.x / RP, t = threadIdx.x, r = t % RP, g = t / RP;
+    const int rows = p.rows[m], rpb = rows_per_block(rows, RP);
+    const int ibeg = b * rpb, iend = min(rows, ibeg + rpb);
+    double cs = 0.0;
+    for (int i = ibeg + g; i < iend; i += G) {
+        const float v = r < p.R ? p.src[m][(int64_t)i * p.R + r] : 0.0f;
+        const int64_t o = (int64_t)i * RP + r;
+        p.F[m][o] = v;
+        if (p.Ft[m]) p.Ft[m][o] = v;
+        if (p.C1[m]) p.C1[m][o] = v;
+        if (p.C2[m]) p.C2[m][o] = v;
+        cs += (double)v;
+    }
+    if (p.cs[m]) {
+        const double tot = group_sum(sh, cs, RP, t);
+        if (t < RP) p.cs[m][(int64_t)b * RP + t] = tot;
+    }
+}
+
+cudaError_t prep_factors(const PrepArgs &p, cudaStream_t s) {
+    int blocks = 0;
+    for (int m = 0; m < 3; ++m) blocks += row_blocks(p.rows[m], p.RP);
+    prep_kernel<<<blocks, 256, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+__global__ void mode_update_kernel(UpdArgs u) {
+    __shared__ double sh[256];
+    __shared__ float den_s[64];
+    const MuEpiArgs &e = u.e;
+    const int RP = e.RP, G = blockDim.x / RP, t = threadIdx.x, r = t % RP, g = t / RP;
+    if (u.obj_out && blockIdx.x == 0) {  // same order as reduce_obj_kernel
+        double v = 0.0;
+        for (int k = t; k < u.obj_n; k += blockDim.x) v += u.obj_parts[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((t & 31) == 0) sh[t >> 5] = v;
+        __syncthreads();
+        if (t == 0) {
+            double tot = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += sh[w];
+            *u.obj_out = tot;
+        }
+        __syncthreads();
+    }
+    if (u.n_cs > 0) {
+        if (t < RP) {
+            double prod = 1.0;
+            for (int k = 0; k < u.n_cs; ++k) {
+                double sum = 0.0;
+                for (int b = 0; b < u.cs_nb[k]; ++b) sum += u.cs_in[k][(int64_t)b * RP + t];
+                prod *= sum;
+            }
+            den_s[t] = (float)prod;
+        }
+        __syncthreads();
+    }
+    const int rpb = rows_per_block(e.rows, RP);
+    const int ibeg = blockIdx.x * rpb, iend = min(e.rows, ibeg + rpb);
+    const int64_t stride = (int64_t)e.rows * RP;
+    double cs = 0.0;
+    for (int i = ibeg + g; i < iend; i += G) {
+        const int64_t o = (int64_t)i * RP + r;
+        float v = 0.0f, c1 = 0.0f, c2 = 0.0f;
+        if (r < e.R) {
+            float num = 0.0f, den = 0.0f;
+            for (int p = 0; p < e.n_parts; ++p) num += e.pn[p * stride + o];
+            if (u.n_cs > 0) den = den_s[r];
+            else if (e.den_closed) den = e.den_closed[r];
+            else
+                for (int p = 0; p < e.n_parts; ++p) den += e.pd[p * stride + o];
+            const float ratio = __fdiv_rn(num, den);
+            float m;
+            if (e.gamma == 1.0f) m = ratio;
+            else if (e.gamma == 0.5f) m = sqrtf(ratio);
+            else m = powf(ratio, e.gamma);
+            v = fmaxf(e.pre[o] * m, e.eps);
+            if (e.chi1_out) c1 = chi1_f(e.beta, v, e.ref[o]);
+            if (e.chi2_out) c2 = chi2_f(e.beta, v, e.ref[o]);
+            if (u.user_out) u.user_out[(int64_t)i * e.R + r] = v;
+        }
+        e.out[o] = v;
+        if (e.chi1_out) e.chi1_out[o] = c1;
+        if (e.chi2_out) e.chi2_out[o] = c2;
+        cs += (double)v;
+    }
+    if (u.cs_out) {
+        const double tot = group_sum(sh, cs, RP, t);
+        if (t < RP) u.cs_out[(int64_t)blockIdx.x * RP + t] = tot;
+    }
+}
+
+cudaError_t mode_update(const UpdArgs &u, cudaStream_t s) {
+    mode_update_kernel<<<row_blocks(u.e.rows, u.e.RP), 256, 0, s>>>(u);
+    return cudaGetLastError();
+}
+
 // Fixed-order FP64 sum of per-CTA objective partials (one CTA; lane-strided then tree).
 __global__ void reduce_obj_kernel(const double *parts, int n, double *out) {
     __shared__ double sh[32];

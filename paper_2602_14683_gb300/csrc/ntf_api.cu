@@ -114,6 +114,7 @@ struct CpDense {
     float *pn[3], *pd[3];
     double *obj;
     float *denc;
+    double *cs[3];  // FP64 column-sum partials of F[n] ([row block][RP]), closed-form KL Den
 };
 
 int cp_dense_setup(ntf_ctx *ctx, const ntf_tensor *X, int R, bool jcomm, bool need_den, int precision,
@@ -144,6 +145,11 @@ int cp_dense_setup(ntf_ctx *ctx, const ntf_tensor *X, int R, bool jcomm, bool ne
     s.obj = (double *)ws_get(ctx, "cpObj", sizeof(double) * (size_t)s.plan.grid);
     s.denc = (float *)ws_get(ctx, "cpDenc", sizeof(float) * 64);
     if (!s.obj || !s.denc) return fail(ctx, NTF_ERR_OOM, "workspace allocation failed");
+    for (int n = 0; n < 3; ++n) {
+        s.cs[n] = (double *)ws_get(ctx, "cpCs" + std::to_string(n),
+                                   sizeof(double) * (size_t)ntf::row_blocks(dims[n], s.RP) * s.RP);
+        if (!s.cs[n]) return fail(ctx, NTF_ERR_OOM, "workspace allocation failed");
+    }
     return NTF_OK;
 }
 
@@ -208,6 +214,56 @@ int launch_pass(ntf_ctx *ctx, const CpDense &s, const ntf::Cp3Args &a_in, int ms
     return NTF_OK;
 }
 
+// Padded working copies of the user's factors (and reference / chi copies) in one launch.
+ntf::PrepArgs prep_args(const CpDense &s, float *const *factors, bool ref, bool chi, bool colsums) {
+    ntf::PrepArgs p{};
+    const int dims[3] = {s.I, s.J, s.K};
+    for (int n = 0; n < 3; ++n) {
+        p.src[n] = factors[n];
+        p.rows[n] = dims[n];
+        p.F[n] = s.F[n];
+        p.Ft[n] = ref ? s.Ft[n] : nullptr;
+        p.C1[n] = chi ? s.C1[n] : nullptr;
+        p.C2[n] = chi ? s.C2[n] : nullptr;
+        p.cs[n] = colsums ? s.cs[n] : nullptr;
+    }
+    p.R = s.R;
+    p.RP = s.RP;
+    return p;
+}
+
+// Update of mode n from its partial sums; closed-form KL denominators from the other two
+// factors' column-sum partials when `closed`; the result also goes unpadded to `user`.
+ntf::UpdArgs upd_args(const CpDense &s, int n, float beta, const ntf_opts &o, bool closed, const float *pre,
+                      float *user) {
+    const int dims[3] = {s.I, s.J, s.K};
+    const int parts[3] = {s.plan.parts1, s.plan.parts2, s.plan.parts3};
+    ntf::UpdArgs u{};
+    ntf::MuEpiArgs &e = u.e;
+    e.pn = s.pn[n];
+    e.pd = closed ? nullptr : s.pd[n];
+    e.n_parts = parts[n];
+    e.rows = dims[n];
+    e.RP = s.RP;
+    e.R = s.R;
+    e.pre = pre;
+    e.out = s.F[n];
+    e.beta = beta;
+    e.gamma = ntf::mu_gamma(beta);
+    e.eps = (float)o.eps;
+    if (closed) {
+        for (int m = 0; m < 3; ++m)
+            if (m != n) {
+                u.cs_in[u.n_cs] = s.cs[m];
+                u.cs_nb[u.n_cs] = ntf::row_blocks(dims[m], s.RP);
+                ++u.n_cs;
+            }
+        u.cs_out = s.cs[n];
+    }
+    u.user_out = user;
+    return u;
+}
+
 int cp_dense_mu_sweep(ntf_ctx *ctx, const ntf_tensor *X, float beta, int R, float *const *factors,
                       const ntf_opts &o, double *objective_dev, cudaStream_t st) {
     const int bk = ntf::beta_kind(beta);
@@ -215,41 +271,22 @@ int cp_dense_mu_sweep(ntf_ctx *ctx, const ntf_tensor *X, float beta, int R, floa
     CpDense s{};
     int rc = cp_dense_setup(ctx, X, R, false, den, o.precision, s);
     if (rc) return rc;
-    const int dims[3] = {s.I, s.J, s.K};
-    const int parts[3] = {s.plan.parts1, s.plan.parts2, s.plan.parts3};
-    for (int n = 0; n < 3; ++n) NTF_CUDA(ntf::pad_factor(factors[n], dims[n], R, s.F[n], s.RP, st));
+    NTF_CUDA(ntf::prep_factors(prep_args(s, factors, false, false, !den), st));
     ntf::Cp3Args a = cp_args(X, s, o, beta);
-    const float gam = ntf::mu_gamma(beta);
     for (int n = 0; n < 3; ++n) {
         for (int m = 0; m < 3; ++m) a.rec[m] = a.num[m] = a.den[m] = s.F[m];
         int ms = (n == 0 ? ntf::PM_M1 : n == 1 ? ntf::PM_M2 : ntf::PM_M3);
         if (n == 0 && objective_dev) ms |= ntf::PM_OBJ;
         rc = launch_pass(ctx, s, a, ms, den, st);
         if (rc) return rc;
-        if (!den) {
-            const float *f[2];
-            int rows[2], c = 0;
-            for (int m = 0; m < 3; ++m)
-                if (m != n) { f[c] = s.F[m]; rows[c] = dims[m]; ++c; }
-            NTF_CUDA(ntf::colsum_prod(2, f, rows, s.RP, s.denc, st));
+        ntf::UpdArgs u = upd_args(s, n, beta, o, !den, s.F[n], factors[n]);
+        if (n == 0 && objective_dev) {
+            u.obj_parts = s.obj;
+            u.obj_n = s.plan.grid;
+            u.obj_out = objective_dev;
         }
-        ntf::MuEpiArgs e{};
-        e.pn = s.pn[n];
-        e.pd = s.pd[n];
-        e.n_parts = parts[n];
-        e.rows = dims[n];
-        e.RP = s.RP;
-        e.R = R;
-        e.den_closed = den ? nullptr : s.denc;
-        e.pre = s.F[n];
-        e.out = s.F[n];
-        e.beta = beta;
-        e.gamma = gam;
-        e.eps = (float)o.eps;
-        NTF_CUDA(ntf::mu_epilogue(e, st));
+        NTF_CUDA(ntf::mode_update(u, st));
     }
-    if (objective_dev) NTF_CUDA(ntf::reduce_objective(s.obj, s.plan.grid, 0.0, objective_dev, st));
-    for (int n = 0; n < 3; ++n) NTF_CUDA(ntf::unpad_factor(s.F[n], dims[n], R, s.RP, factors[n], st));
     return NTF_OK;
 }
 
@@ -260,14 +297,22 @@ int cp_dense_jcomm(ntf_ctx *ctx, const ntf_tensor *X, float beta, int R, float *
     CpDense s{};
     int rc = cp_dense_setup(ctx, X, R, true, !kl, o.precision, s);
     if (rc) return rc;
-    const int dims[3] = {s.I, s.J, s.K};
-    const int parts[3] = {s.plan.parts1, s.plan.parts2, s.plan.parts3};
-    for (int n = 0; n < 3; ++n) {
-        NTF_CUDA(ntf::pad_factor(factors[n], dims[n], R, s.F[n], s.RP, st));
-        NTF_CUDA(ntf::copy_f32(s.F[n], s.Ft[n], (int64_t)dims[n] * s.RP, st));
-    }
+    NTF_CUDA(ntf::prep_factors(prep_args(s, factors, true, !kl, kl), st));
     ntf::Cp3Args a = cp_args(X, s, o, beta);
-    const float gam = ntf::mu_gamma(beta);
+    auto update = [&](int l, int n) {
+        ntf::UpdArgs u = upd_args(s, n, beta, o, kl, s.Ft[n], l == o.inner_L - 1 ? factors[n] : nullptr);
+        if (!kl) {
+            u.e.ref = s.Ft[n];
+            u.e.chi1_out = s.C1[n];
+            u.e.chi2_out = s.C2[n];
+        }
+        if (l == 0 && n == 0 && objective_dev) {  // D_beta at the reference, from the first pass
+            u.obj_parts = s.obj;
+            u.obj_n = s.plan.grid;
+            u.obj_out = objective_dev;
+        }
+        return ntf::mode_update(u, st);
+    };
     if (kl) {
         // beta = 1: chi1(Z, Zt) = Zt, so every Num_J^(n) depends on the reference only and
         // one pass over X yields all three numerators (and D_beta at the reference);
@@ -276,33 +321,9 @@ int cp_dense_jcomm(ntf_ctx *ctx, const ntf_tensor *X, float beta, int R, float *
         for (int m = 0; m < 3; ++m) a.rec[m] = a.num[m] = a.den[m] = s.Ft[m];
         rc = launch_pass(ctx, s, a, ntf::PM_M1 | ntf::PM_M2 | ntf::PM_M3 | ntf::PM_OBJ, 0, st);
         if (rc) return rc;
-        for (int l = 0; l < o.inner_L; ++l) {
-            for (int n = 0; n < 3; ++n) {
-                const float *f[2];
-                int rows[2], c = 0;
-                for (int m = 0; m < 3; ++m)
-                    if (m != n) { f[c] = s.F[m]; rows[c] = dims[m]; ++c; }
-                NTF_CUDA(ntf::colsum_prod(2, f, rows, s.RP, s.denc, st));
-                ntf::MuEpiArgs e{};
-                e.pn = s.pn[n];
-                e.n_parts = parts[n];
-                e.rows = dims[n];
-                e.RP = s.RP;
-                e.R = R;
-                e.den_closed = s.denc;
-                e.pre = s.Ft[n];
-                e.out = s.F[n];
-                e.beta = beta;
-                e.gamma = gam;
-                e.eps = (float)o.eps;
-                NTF_CUDA(ntf::mu_epilogue(e, st));
-            }
-        }
+        for (int l = 0; l < o.inner_L; ++l)
+            for (int n = 0; n < 3; ++n) NTF_CUDA(update(l, n));
     } else {
-        for (int n = 0; n < 3; ++n) {
-            NTF_CUDA(ntf::copy_f32(s.Ft[n], s.C1[n], (int64_t)dims[n] * s.RP, st));
-            NTF_CUDA(ntf::copy_f32(s.Ft[n], s.C2[n], (int64_t)dims[n] * s.RP, st));
-        }
         for (int l = 0; l < o.inner_L; ++l) {
             for (int n = 0; n < 3; ++n) {
                 for (int m = 0; m < 3; ++m) {
@@ -314,27 +335,10 @@ int cp_dense_jcomm(ntf_ctx *ctx, const ntf_tensor *X, float beta, int R, float *
                 if (l == 0 && n == 0) ms |= ntf::PM_OBJ;
                 rc = launch_pass(ctx, s, a, ms, 1, st);
                 if (rc) return rc;
-                ntf::MuEpiArgs e{};
-                e.pn = s.pn[n];
-                e.pd = s.pd[n];
-                e.n_parts = parts[n];
-                e.rows = dims[n];
-                e.RP = s.RP;
-                e.R = R;
-                e.pre = s.Ft[n];
-                e.out = s.F[n];
-                e.ref = s.Ft[n];
-                e.chi1_out = s.C1[n];
-                e.chi2_out = s.C2[n];
-                e.beta = beta;
-                e.gamma = gam;
-                e.eps = (float)o.eps;
-                NTF_CUDA(ntf::mu_epilogue(e, st));
+                NTF_CUDA(update(l, n));
             }
         }
     }
-    if (objective_dev) NTF_CUDA(ntf::reduce_objective(s.obj, s.plan.grid, 0.0, objective_dev, st));
-    for (int n = 0; n < 3; ++n) NTF_CUDA(ntf::unpad_factor(s.F[n], dims[n], R, s.RP, factors[n], st));
     return NTF_OK;
 }
 

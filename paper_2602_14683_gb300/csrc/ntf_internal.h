@@ -177,6 +177,46 @@ struct MuEpiArgs {
     float beta, gamma, eps;
 };
 cudaError_t mu_epilogue(const MuEpiArgs &e, cudaStream_t s);
+
+// Row blocking shared by prep_factors and mode_update: blocks of rows_per_block(rows, RP)
+// rows (a multiple of 256 / RP, at most 512 blocks), column-sum partials [block][RP] in FP64.
+__host__ __device__ inline int rows_per_block(int rows, int RP) {
+    const int G = 256 / RP;
+    const int per = (rows + 512 * G - 1) / (512 * G);
+    return G * (per > 0 ? per : 1);
+}
+__host__ __device__ inline int row_blocks(int rows, int RP) { return (rows + rows_per_block(rows, RP) - 1) / rows_per_block(rows, RP); }
+
+// One launch over the three factors: F[m] = padded copy of src[m] (rows x R -> rows x RP,
+// zero columns r >= R), optional extra copies into Ft / C1 / C2, and optional FP64
+// column-sum partials cs[m][block][RP] of the padded rows.
+struct PrepArgs {
+    const float *src[3];
+    int rows[3];
+    int R, RP;
+    float *F[3], *Ft[3], *C1[3], *C2[3];
+    double *cs[3];
+};
+cudaError_t prep_factors(const PrepArgs &p, cudaStream_t s);
+
+// Multiplicative update of one padded factor in row blocks (same arithmetic as mu_epilogue):
+//   out = max(pre * (sum_p pn / D)^gamma, eps), D = sum_p pd, den_closed[r], or, with cs_in,
+//   prod_k sum_b cs_in[k][b][r] (the closed-form KL denominator from column-sum partials);
+// optional chi1 / chi2 outputs, an unpadded copy user_out (rows x R), FP64 column-sum
+// partials of the result cs_out[block][RP], and (block 0) the fixed-order FP64 sum of
+// obj_n objective partials into *obj_out.
+struct UpdArgs {
+    MuEpiArgs e;
+    const double *cs_in[2];
+    int cs_nb[2];
+    int n_cs;
+    double *cs_out;
+    float *user_out;
+    const double *obj_parts;
+    int obj_n;
+    double *obj_out;
+};
+cudaError_t mode_update(const UpdArgs &u, cudaStream_t s);
 cudaError_t reduce_objective(const double *parts, int n, double add_const_unused, double *out,
                              cudaStream_t s);
 cudaError_t copy_f32(const float *src, float *dst, int64_t n, cudaStream_t s);

@@ -60,10 +60,22 @@ size_t estimate_bytes(const ntf_job &j, int sms) {
     size_t b = 0;
     if (j.model == NTF_CP) {
         const int RP = rank_pad(j.rank);
-        const ntf::Cp3Plan p = ntf::cp3_plan((int)I, (int)J, (int)K, RP, sms, 64);
+        // the tensor-core plan (128-column blocks, four mode-1 partials per row tile) where
+        // the job asks for it, else the FP32 plan; the larger of the two when either may run
+        const ntf::Cp3Plan p32 = ntf::cp3_plan((int)I, (int)J, (int)K, RP, sms, 64);
+        size_t parts = (size_t)p32.parts1 * I + (size_t)p32.parts2 * J + (size_t)p32.parts3 * K;
+        int grid = p32.grid;
+        if (j.precision == NTF_PREC_TF32 && RP == 32) {
+            const ntf::Cp3Plan ptc = ntf::cp3_plan((int)I, (int)J, (int)K, RP, sms, 128);
+            const size_t pt = (size_t)ptc.parts1 * I + (size_t)ptc.parts2 * J + (size_t)ptc.parts3 * K;
+            parts = pt > parts ? pt : parts;
+            grid = ptc.grid > grid ? ptc.grid : grid;
+        }
         b += 4 * sizeof(float) * (size_t)(I + J + K) * RP;
-        b += 2 * sizeof(float) * ((size_t)p.parts1 * I + (size_t)p.parts2 * J + (size_t)p.parts3 * K) * RP;
-        b += sizeof(double) * (size_t)p.grid;
+        b += 2 * sizeof(float) * parts * RP;
+        b += sizeof(double) * (size_t)grid;
+        b += sizeof(double) * (size_t)(ntf::row_blocks((int)I, RP) + ntf::row_blocks((int)J, RP) +
+                                       ntf::row_blocks((int)K, RP)) * RP;
     } else {
         const int RP = rank_pad((int)j.core_dims[2]);
         const int64_t Jc = j.core_dims[0] * j.core_dims[1] * j.core_dims[2];

@@ -7,7 +7,7 @@ times i.i.d. Gamma(10, 0.1) noise, init U(0.1, 1).  Secondary figures on the sam
 B-CoMM sweeps/s, and the time for each method to reach F*(1 + 1e-4), F* being the lowest
 objective of a long FP32 B-CoMM run from the same init.
 
-Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|tf32]
+Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|tf32|3xtf32]
         python bench.py --impl reference ...   (the FP64 CPU oracle on a bounded sample)
 Prints one JSON line on rank 0.
 """
@@ -39,7 +39,7 @@ def parse():
     p.add_argument("--steps", type=int, default=50)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ntf", choices=["ntf", "reference"])
-    p.add_argument("--precision", default="tf32", choices=["fp32", "tf32"])
+    p.add_argument("--precision", default="tf32", choices=["fp32", "tf32", "3xtf32"])
     p.add_argument("--no-ttt", action="store_true", help="skip the time-to-target runs")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     p.add_argument("--serve-jobs", type=int, default=48,
@@ -323,7 +323,8 @@ def main():
         # incoming iterate; F* is the lowest objective any run reaches
         n_run = 1000
         runs = {}
-        for name, fn, p in (("jcomm_" + prec, ntf.jcomm_outer, prec), ("block_mu_fp32", ntf.cp_mu_sweep, "fp32"),
+        for name, fn, p in (("jcomm_" + prec, ntf.jcomm_outer, prec), ("jcomm_3xtf32", ntf.jcomm_outer, "3xtf32"),
+                            ("jcomm_fp32", ntf.jcomm_outer, "fp32"), ("block_mu_fp32", ntf.cp_mu_sweep, "fp32"),
                             ("block_mu_" + prec, ntf.cp_mu_sweep, prec)):
             if name in runs:
                 continue

@@ -57,10 +57,13 @@ typedef enum {
 
 enum { NTF_DENSE = 0, NTF_COO = 1 };
 enum { NTF_CP = 0, NTF_TUCKER = 1 };
-/* Arithmetic of the contraction tiles.  FP32: CUDA-core FP32 FMA.  TF32: tcgen05
- * tensor cores, TF32 operands, FP32 accumulation (dense CP only).  The beta-powers are
- * always FP32 and the objective is accumulated in FP64. */
-enum { NTF_PREC_FP32 = 0, NTF_PREC_TF32 = 1 };
+/* Arithmetic of the contraction tiles.  FP32: CUDA-core FP32 FMA.  TF32: tcgen05 tensor
+ * cores (dense CP, rank padded to 32): the reconstruction Xhat on TF32 operands rounded to
+ * nearest (one MMA pass), the Num / Den contractions on BF16 operands, FP32 accumulation.
+ * 3XTF32: the same, with the reconstruction split into high and low TF32 parts (three MMA
+ * passes, about FP32 accuracy for Xhat and the objective).  The beta-powers are always
+ * FP32 and the objective is accumulated in FP64. */
+enum { NTF_PREC_FP32 = 0, NTF_PREC_TF32 = 1, NTF_PREC_3XTF32 = 2 };
 
 typedef struct {
     int order;                 /* N */
@@ -75,7 +78,7 @@ typedef struct {
     double eps;    /* floor on every parameter and on Xhat inside the powers (1e-12) */
     double eps_x;  /* data floor used only at beta = 0 (1e-12) */
     int inner_L;   /* J-CoMM inner sweeps per outer iteration, >= 1 (1) */
-    int precision; /* NTF_PREC_FP32 (default) or NTF_PREC_TF32 */
+    int precision; /* NTF_PREC_FP32 (default), NTF_PREC_TF32 or NTF_PREC_3XTF32 */
 } ntf_opts;
 
 /* Fills *o with the defaults shown above. */
@@ -177,7 +180,7 @@ typedef struct ntf_server ntf_server;
 typedef struct {
     int model;             /* NTF_CP or NTF_TUCKER */
     int method;            /* 0: J-CoMM (Algorithm 2) with inner_L = 1; 1: block MM */
-    int precision;         /* NTF_PREC_FP32 or NTF_PREC_TF32 (CP, rank padded to 32) */
+    int precision;         /* NTF_PREC_FP32, NTF_PREC_TF32 or NTF_PREC_3XTF32 (CP only) */
     int64_t dims[3];       /* I_1, I_2, I_3 */
     int rank;              /* CP rank (1..64) */
     int64_t core_dims[3];  /* Tucker core dimensions (1..64 each) */

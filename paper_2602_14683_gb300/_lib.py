@@ -18,8 +18,8 @@ STATUS = {0: "NTF_OK", -1: "NTF_ERR_ARG", -2: "NTF_ERR_BETA", -3: "NTF_ERR_SHAPE
           -5: "NTF_ERR_NONFINITE", -6: "NTF_ERR_TIMEOUT", -7: "NTF_ERR_CUDA", -8: "NTF_ERR_UNSUPPORTED"}
 NTF_DENSE, NTF_COO = 0, 1
 NTF_CP, NTF_TUCKER = 0, 1
-NTF_PREC_FP32, NTF_PREC_TF32 = 0, 1
-PRECISIONS = {"fp32": NTF_PREC_FP32, "tf32": NTF_PREC_TF32}
+NTF_PREC_FP32, NTF_PREC_TF32, NTF_PREC_3XTF32 = 0, 1, 2
+PRECISIONS = {"fp32": NTF_PREC_FP32, "tf32": NTF_PREC_TF32, "3xtf32": NTF_PREC_3XTF32}
 
 
 class NtfError(RuntimeError):

@@ -14,8 +14,9 @@
 //
 // Per chunk n (slab i, columns k0 + 64 q):
 //   TMA       X chunk (128 x 64 FP32) into a 2- or 3-stage ring, issued that far ahead;
-//   GEMM1     Xhat = R C^T on 3xTF32 (hi/lo parts rounded to nearest; hi*hi + hi*lo +
-//             lo*hi), M128 N64 K32, into one of two TMEM buffers, issued one chunk ahead;
+//   GEMM1     Xhat = R C^T on TF32 operands rounded to nearest, M128 N64 K32, into one of
+//             two TMEM buffers, issued one chunk ahead; with S3 the operands are split into
+//             hi / lo TF32 parts and GEMM1 is hi*lo + lo*hi + hi*hi (about FP32 accuracy);
 //   epilogue  Xhat from TMEM (tcgen05.ld), X from shared memory, P = X Y^(beta-2),
 //             Q = Y^(beta-1) (Y = max(Xhat, eps)) and the objective terms in FP32
 //             registers; P, Q stored once as BF16 tiles [rows][64 cols];
@@ -65,30 +66,30 @@ struct Layout {
 // rows 32..127 are padding: those rows only feed accumulator rows that are never read, so
 // only the 32 real rows are stored (two 4 KB K-atoms per buffer) and the padding reads fall
 // on the 16 KB that follow (the Crec / R tiles), which stay inside the allocation.
-__host__ __device__ constexpr int layout_bytes(bool rows, bool m3, bool den, int ns, int np, int nk) {
-    return ns * 32768 + np * 16384 * (den ? 2 : 1) + 4 * 16384 + (rows ? 8192 : 0) + ((rows && den) ? 8192 : 0) +
-           (m3 ? nk * 8192 : 0) + ((m3 && den) ? nk * 8192 : 0) + 4096 + 1024;
+__host__ __device__ constexpr int layout_bytes(bool rows, bool m3, bool den, bool s3, int ns, int np, int nk) {
+    return ns * 32768 + np * 16384 * (den ? 2 : 1) + (s3 ? 4 : 2) * 16384 + (rows ? 8192 : 0) +
+           ((rows && den) ? 8192 : 0) + (m3 ? nk * 8192 : 0) + ((m3 && den) ? nk * 8192 : 0) + 4096 + 1024;
 }
 
-__host__ __device__ constexpr Layout make_layout(bool rows, bool m3, bool den) {
+__host__ __device__ constexpr Layout make_layout(bool rows, bool m3, bool den, bool s3) {
     Layout L{};
     constexpr int kMax = 232448;  // opt-in shared memory per CTA
     L.ns = 2;
     L.np = 1;
     L.nk = 1;
-    if (layout_bytes(rows, m3, den, 2, 2, 1) <= kMax) L.np = 2;
-    if (layout_bytes(rows, m3, den, 2, L.np, 2) <= kMax) L.nk = 2;
-    if (layout_bytes(rows, m3, den, 3, L.np, L.nk) <= kMax) L.ns = 3;
+    if (layout_bytes(rows, m3, den, s3, 2, 2, 1) <= kMax) L.np = 2;
+    if (layout_bytes(rows, m3, den, s3, 2, L.np, 2) <= kMax) L.nk = 2;
+    if (layout_bytes(rows, m3, den, s3, 3, L.np, L.nk) <= kMax) L.ns = 3;
     int o = 0;
     L.x = o; o += L.ns * 32768;
     L.p = o; o += L.np * 16384;
     L.q = o; o += den ? L.np * 16384 : 0;
     L.knt = o; o += m3 ? L.nk * 8192 : 0;            // padding rows read the C tiles below
     L.c = o; o += 16384;
-    L.cl = o; o += 16384;
+    L.cl = o; o += s3 ? 16384 : 0;
     L.kdt = o; o += (m3 && den) ? L.nk * 8192 : 0;   // padding rows read the R tiles below
     L.r = o; o += 16384;
-    L.rl = o; o += 16384;
+    L.rl = o; o += s3 ? 16384 : 0;
     L.cnt = o; o += rows ? 8192 : 0;
     L.cdt = o; o += (rows && den) ? 8192 : 0;
     L.misc = o; o += 4096;
@@ -211,7 +212,7 @@ __device__ __forceinline__ float mufu_ex2(float x) { float r; asm("ex2.approx.ft
 
 // One entry of the epilogue: P, Q (stored in BF16) and, with OBJ, the terms of d_beta(x|y)
 // (Section 3.2) split so that the per-entry work is a few MUFU / FMA instructions:
-//   KL : d = ln2 * x (lg2 x - lg2 y) + (y - x)          -> o1 += x (lg2 x - lg2 y), o2 += y - x
+//   KL : d = ln2 * x lg2 P + (y - x), P = x / y          -> o1 += x lg2 P,          o2 += y - x
 //   IS : d = u - ln2 lg2 u - 1, u = x / y                -> o1 += lg2 u,            o2 += u - 1
 //   1/2: d = -4 (sqrt x - y / 2 sqrt y - x / 2 sqrt y)  -> o2 += d
 //   3/2: d = (x sqrt x + y sqrt y / 2 - 3 x sqrt y / 2) / (3/4)  -> o2 += d
@@ -225,8 +226,8 @@ __device__ __forceinline__ void point(float beta, float x, float y, float &P, fl
     if (BK == BK_KL) {
         P = x * mufu_rcp(y);
         Q = 1.0f;
-        if (OBJ) {
-            o1 = fmaf(x, mufu_lg2(fmaxf(x, 1e-30f)) - mufu_lg2(y), o1);
+        if (OBJ) {  // x log(x / y) = x log P; the floor only keeps 0 * log 0 at 0
+            o1 = fmaf(x, mufu_lg2(fmaxf(P, 1e-30f)), o1);
             o2 += y - x;
         }
     } else if (BK == BK_IS) {
@@ -289,12 +290,12 @@ __device__ __forceinline__ float reduce_scatter(float v[N]) {
     return s;
 }
 
-template <int MS, int BK>
+template <int MS, int BK, bool S3>
 __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUtensorMap xmap, const Cp3Args a) {
     constexpr bool DEN = BK != BK_KL;
     constexpr bool M1 = (MS & PM_M1) != 0, M2 = (MS & PM_M2) != 0, M3 = (MS & PM_M3) != 0;
     constexpr bool OBJ = (MS & PM_OBJ) != 0, RW = M1 || M2;
-    constexpr Layout L = make_layout(RW, M3, DEN);
+    constexpr Layout L = make_layout(RW, M3, DEN, S3);
     constexpr int NP = L.np, NS = L.ns, NK = L.nk;
     extern __shared__ __align__(1024) uint8_t smraw[];
     uint8_t *sm = (uint8_t *)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
@@ -373,10 +374,10 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
             for (int e = 0; e < 4; ++e) {
                 const float v = kv ? __ldg(a.rec[2] + (int64_t)kc * RP + r0 + 4 * q + e) : 0.0f;
                 h[e] = tf32_rna(v);
-                l[e] = tf32_rna(v - h[e]);
+                l[e] = S3 ? tf32_rna(v - h[e]) : 0.0f;
             }
             *reinterpret_cast<float4 *>(Cs + swf(row, r0 + 4 * q)) = make_float4(h[0], h[1], h[2], h[3]);
-            *reinterpret_cast<float4 *>(Cl + swf(row, r0 + 4 * q)) = make_float4(l[0], l[1], l[2], l[3]);
+            if (S3) *reinterpret_cast<float4 *>(Cl + swf(row, r0 + 4 * q)) = make_float4(l[0], l[1], l[2], l[3]);
         }
         if (RW) {
 #pragma unroll
@@ -413,10 +414,10 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
             for (int e = 0; e < 4; ++e) {
                 const float v = ar[4 * q + e] * brec[4 * q + e];
                 h[e] = tf32_rna(v);
-                l[e] = tf32_rna(v - h[e]);
+                l[e] = S3 ? tf32_rna(v - h[e]) : 0.0f;
             }
             *reinterpret_cast<float4 *>(Rs + swf(row, r0 + 4 * q)) = make_float4(h[0], h[1], h[2], h[3]);
-            *reinterpret_cast<float4 *>(Rl + swf(row, r0 + 4 * q)) = make_float4(l[0], l[1], l[2], l[3]);
+            if (S3) *reinterpret_cast<float4 *>(Rl + swf(row, r0 + 4 * q)) = make_float4(l[0], l[1], l[2], l[3]);
         }
     };
     auto slab_kr = [&](int i) {  // KRn^T / KRd^T of slab i: rows r0.. r0 + RS - 1, column `row`
@@ -494,12 +495,14 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
                 const uint32_t d = t_d1 + 64 * (n & 1);
                 const uint32_t id = idesc_tf32(CH);
                 const uint32_t cb = su32(Cs) + q * 8192, cbl = su32(Cl) + q * 8192;
+                if (S3) {
 #pragma unroll
-                for (int s = 0; s < 4; ++s) mma_tf32(d, sdesc(su32(Rl) + s * 32), sdesc(cb + s * 32), id, s > 0);
+                    for (int s = 0; s < 4; ++s) mma_tf32(d, sdesc(su32(Rl) + s * 32), sdesc(cb + s * 32), id, s > 0);
 #pragma unroll
-                for (int s = 0; s < 4; ++s) mma_tf32(d, sdesc(su32(Rs) + s * 32), sdesc(cbl + s * 32), id, 1);
+                    for (int s = 0; s < 4; ++s) mma_tf32(d, sdesc(su32(Rs) + s * 32), sdesc(cbl + s * 32), id, 1);
+                }
 #pragma unroll
-                for (int s = 0; s < 4; ++s) mma_tf32(d, sdesc(su32(Rs) + s * 32), sdesc(cb + s * 32), id, 1);
+                for (int s = 0; s < 4; ++s) mma_tf32(d, sdesc(su32(Rs) + s * 32), sdesc(cb + s * 32), id, S3 || s > 0);
                 mma_commit(su32(g1_full + (n & 1)));
             };
             auto issue_g2 = [&](int n) {
@@ -759,28 +762,28 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
 
 cudaError_t launch_x_map(const Cp3Args &a, CUtensorMap *map);
 
-template <int MS, int BK>
+template <int MS, int BK, bool S3>
 cudaError_t launch_t(const Cp3Plan &p, const Cp3Args &a, cudaStream_t s) {
-    constexpr Layout L = make_layout((MS & (PM_M1 | PM_M2)) != 0, (MS & PM_M3) != 0, BK != BK_KL);
+    constexpr Layout L = make_layout((MS & (PM_M1 | PM_M2)) != 0, (MS & PM_M3) != 0, BK != BK_KL, S3);
     CUtensorMap map;
     cudaError_t e = launch_x_map(a, &map);
     if (e != cudaSuccess) return e;
-    auto k = cp3_pass_tc<MS, BK>;
+    auto k = cp3_pass_tc<MS, BK, S3>;
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total);
     if (e != cudaSuccess) return e;
     k<<<p.grid, NT, L.total, s>>>(map, a);
     return cudaGetLastError();
 }
 
-template <int BK>
+template <int BK, bool S3>
 cudaError_t launch_bk(const Cp3Plan &p, const Cp3Args &a, int ms, cudaStream_t s) {
     switch (ms) {
-        case PM_M1: return launch_t<PM_M1, BK>(p, a, s);
-        case PM_M1 | PM_OBJ: return launch_t<PM_M1 | PM_OBJ, BK>(p, a, s);
-        case PM_M2: return launch_t<PM_M2, BK>(p, a, s);
-        case PM_M3: return launch_t<PM_M3, BK>(p, a, s);
+        case PM_M1: return launch_t<PM_M1, BK, S3>(p, a, s);
+        case PM_M1 | PM_OBJ: return launch_t<PM_M1 | PM_OBJ, BK, S3>(p, a, s);
+        case PM_M2: return launch_t<PM_M2, BK, S3>(p, a, s);
+        case PM_M3: return launch_t<PM_M3, BK, S3>(p, a, s);
         case PM_M1 | PM_M2 | PM_M3 | PM_OBJ:
-            if (BK == BK_KL) return launch_t<PM_M1 | PM_M2 | PM_M3 | PM_OBJ, BK_KL>(p, a, s);
+            if (BK == BK_KL) return launch_t<PM_M1 | PM_M2 | PM_M3 | PM_OBJ, BK_KL, S3>(p, a, s);
             return cudaErrorInvalidValue;
         default: return cudaErrorInvalidValue;
     }

@@ -3,6 +3,6 @@
 
 namespace ntf {
 cudaError_t cp3_tc_launch_bk0(const Cp3Plan &p, const Cp3Args &a, int ms, cudaStream_t s) {
-    return tc::launch_bk<0>(p, a, ms, s);
+    return p.s3 ? tc::launch_bk<0, true>(p, a, ms, s) : tc::launch_bk<0, false>(p, a, ms, s);
 }
 }  // namespace ntf

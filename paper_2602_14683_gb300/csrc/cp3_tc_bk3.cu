@@ -3,6 +3,6 @@
 
 namespace ntf {
 cudaError_t cp3_tc_launch_bk3(const Cp3Plan &p, const Cp3Args &a, int ms, cudaStream_t s) {
-    return tc::launch_bk<3>(p, a, ms, s);
+    return p.s3 ? tc::launch_bk<3, true>(p, a, ms, s) : tc::launch_bk<3, false>(p, a, ms, s);
 }
 }  // namespace ntf

@@ -76,7 +76,7 @@ int check_common(ntf_ctx *ctx, const ntf_tensor *X, float beta, const ntf_opts &
         return fail(ctx, NTF_ERR_BETA, "beta = %g outside [0, 2)", (double)beta);
     if (!(o.eps > 0.0) || !(o.eps_x > 0.0)) return fail(ctx, NTF_ERR_ARG, "eps and eps_x must be > 0");
     if (o.inner_L < 1) return fail(ctx, NTF_ERR_ARG, "inner_L must be >= 1");
-    if (o.precision != NTF_PREC_FP32 && o.precision != NTF_PREC_TF32)
+    if (o.precision != NTF_PREC_FP32 && o.precision != NTF_PREC_TF32 && o.precision != NTF_PREC_3XTF32)
         return fail(ctx, NTF_ERR_ARG, "unknown precision %d", o.precision);
     if (X->kind != NTF_DENSE && X->kind != NTF_COO) return fail(ctx, NTF_ERR_ARG, "unknown tensor kind");
     if (X->order < 2 || X->order > 8) return fail(ctx, NTF_ERR_UNSUPPORTED, "order %d not in 2..8", X->order);
@@ -126,8 +126,9 @@ int cp_dense_setup(ntf_ctx *ctx, const ntf_tensor *X, int R, bool jcomm, bool ne
     s.RP = rank_pad(R);
     // tensor-core passes where the request asks for them and the shapes allow (rank padded
     // to 32, rows of X 16-byte aligned for TMA); FP32 CUDA-core passes otherwise
-    const bool tc = precision == NTF_PREC_TF32 && ntf::cp3_tc_eligible(s.RP, s.K, X->values);
+    const bool tc = precision != NTF_PREC_FP32 && ntf::cp3_tc_eligible(s.RP, s.K, X->values);
     s.plan = ntf::cp3_plan(s.I, s.J, s.K, s.RP, ctx->num_sms, tc ? 128 : 64);
+    s.plan.s3 = tc && precision == NTF_PREC_3XTF32;
     const int dims[3] = {s.I, s.J, s.K};
     const int parts[3] = {s.plan.parts1, s.plan.parts2, s.plan.parts3};
     for (int n = 0; n < 3; ++n) {

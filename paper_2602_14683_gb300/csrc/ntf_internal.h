@@ -134,6 +134,7 @@ struct Cp3Args {
 
 struct Cp3Plan {
     int tc;  // 1: tensor-core (tcgen05) pass, else FP32 CUDA-core pass
+    int s3;  // tensor-core pass: reconstruction on split (hi / lo) TF32 operands
     int RP, TJ, KB;
     int n_jt, n_kb, n_is;
     int grid;

@@ -65,7 +65,7 @@ size_t estimate_bytes(const ntf_job &j, int sms) {
         const ntf::Cp3Plan p32 = ntf::cp3_plan((int)I, (int)J, (int)K, RP, sms, 64);
         size_t parts = (size_t)p32.parts1 * I + (size_t)p32.parts2 * J + (size_t)p32.parts3 * K;
         int grid = p32.grid;
-        if (j.precision == NTF_PREC_TF32 && RP == 32) {
+        if (j.precision != NTF_PREC_FP32 && RP == 32) {
             const ntf::Cp3Plan ptc = ntf::cp3_plan((int)I, (int)J, (int)K, RP, sms, 128);
             const size_t pt = (size_t)ptc.parts1 * I + (size_t)ptc.parts2 * J + (size_t)ptc.parts3 * K;
             parts = pt > parts ? pt : parts;

@@ -319,27 +319,40 @@ def main():
     # ---------------- time to F*(1 + 1e-4) ----------------
     ttt = None
     if not args.no_ttt:
-        # every method runs n iterations from the same init, recording the objective of each
-        # incoming iterate; F* is the lowest objective any run reaches
-        n_run = 1000
-        runs = {}
-        for name, fn, p in (("jcomm_" + prec, ntf.jcomm_outer, prec), ("jcomm_3xtf32", ntf.jcomm_outer, "3xtf32"),
-                            ("jcomm_fp32", ntf.jcomm_outer, "fp32"), ("block_mu_fp32", ntf.cp_mu_sweep, "fp32"),
-                            ("block_mu_" + prec, ntf.cp_mu_sweep, prec)):
-            if name in runs:
-                continue
-            Fr = torch.zeros(n_run, dtype=torch.float64, device=dev)
+        # F* = lowest FP64 objective of 1000 FP32 block-MU sweeps from the shared init; every
+        # other method runs from the same init until its objective first reaches F*(1+1e-4)
+        # or an iteration cap, recording the objective of each incoming iterate on the device
+        # (checked every 100 iterations)
+        n_ref = 1000
+        def run_until(fn, p, n_max, target):
+            Fr = torch.zeros(n_max, dtype=torch.float64, device=dev)
+            W_ = [a.clone() for a in A0]
+            for _ in range(3):  # untimed: workspaces sized for this method and precision
+                fn(X, BETA, W_, objective=Fr[:1], ctx=ctx, precision=p)
             C_ = [a.clone() for a in A0]
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            for t in range(n_run):
-                fn(X, BETA, C_, objective=Fr[t:t + 1], ctx=ctx, precision=p)
+            t = 0
+            while t < n_max:
+                for _ in range(min(100, n_max - t)):
+                    fn(X, BETA, C_, objective=Fr[t:t + 1], ctx=ctx, precision=p)
+                    t += 1
+                if target is not None and float(Fr[:t].min()) <= target:
+                    break
             e1.record(stream)
             torch.cuda.synchronize()
-            runs[name] = (Fr.cpu().numpy(), e0.elapsed_time(e1) / 1e3 / n_run)
-        fstar = min(float(F.min()) for F, _ in runs.values())
+            return Fr[:t].cpu().numpy(), e0.elapsed_time(e1) / 1e3 / t
+        F_ref, per_ref = run_until(ntf.cp_mu_sweep, "fp32", n_ref, None)
+        fstar = float(F_ref.min())
         target = fstar * (1 + 1e-4)
+        runs = {"block_mu_fp32": (F_ref, per_ref)}
+        for name, fn, p, cap in (("jcomm_" + prec, ntf.jcomm_outer, prec, 5000),
+                                 ("jcomm_3xtf32", ntf.jcomm_outer, "3xtf32", 5000),
+                                 ("block_mu_" + prec, ntf.cp_mu_sweep, prec, 2000),
+                                 ("jcomm_fp32", ntf.jcomm_outer, "fp32", 2000)):
+            if name not in runs:
+                runs[name] = run_until(fn, p, cap, target)
         res = {}
         for name, (F, per) in runs.items():
             hit = np.nonzero(F <= target)[0]
@@ -347,12 +360,12 @@ def main():
             conv = np.nonzero(rel <= 1e-4)[0]
             res[name] = {"iters": int(hit[0]) if hit.size else None,
                          "seconds": float(hit[0] * per) if hit.size else None,
-                         "s_per_iter": per,
+                         "s_per_iter": per, "iters_run": int(F.size),
                          "iters_rel_change_1e-4": int(conv[0]) + 1 if conv.size else None,
                          "seconds_rel_change_1e-4": float((conv[0] + 1) * per) if conv.size else None,
                          "final_rel_gap": float(F[-1] / fstar - 1.0)}
         ttt = {"target": "F*(1+1e-4)", "F_star": fstar,
-               "F_star_from": "lowest objective of %d iterations of each method" % n_run, **res}
+               "F_star_from": "lowest objective of %d FP32 block-MU sweeps" % n_ref, **res}
 
     # ---------------- roofline of the dominant kernel (the fused pass) ----------------
     entries = DIMS[0] * DIMS[1] * DIMS[2]

@@ -210,6 +210,33 @@ __device__ __forceinline__ float mufu_sqrt(float x) { float r; asm("sqrt.approx.
 __device__ __forceinline__ float mufu_lg2(float x) { float r; asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x)); return r; }
 __device__ __forceinline__ float mufu_ex2(float x) { float r; asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x)); return r; }
 
+// Packed pairs of FP32 values (one FMA-pipe instruction for both lanes of the pair).
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+    float2 r;
+    asm("{\n .reg .b64 a, b, d;\n mov.b64 a, {%2, %3};\n mov.b64 b, {%4, %5};\n mul.rn.ftz.f32x2 d, a, b;\n"
+        " mov.b64 {%0, %1}, d;\n}\n" : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+    float2 r;
+    asm("{\n .reg .b64 a, b, c, d;\n mov.b64 a, {%2, %3};\n mov.b64 b, {%4, %5};\n mov.b64 c, {%6, %7};\n"
+        " fma.rn.ftz.f32x2 d, a, b, c;\n mov.b64 {%0, %1}, d;\n}\n"
+        : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return r;
+}
+__device__ __forceinline__ float2 add2(float2 a, float2 b) {
+    float2 r;
+    asm("{\n .reg .b64 a, b, d;\n mov.b64 a, {%2, %3};\n mov.b64 b, {%4, %5};\n add.rn.ftz.f32x2 d, a, b;\n"
+        " mov.b64 {%0, %1}, d;\n}\n" : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+    float2 r;
+    asm("{\n .reg .b64 a, b, d;\n mov.b64 a, {%2, %3};\n mov.b64 b, {%4, %5};\n sub.rn.ftz.f32x2 d, a, b;\n"
+        " mov.b64 {%0, %1}, d;\n}\n" : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+
 // One entry of the epilogue: P, Q (stored in BF16) and, with OBJ, the terms of d_beta(x|y)
 // (Section 3.2) split so that the per-entry work is a few MUFU / FMA instructions:
 //   KL : d = ln2 * x lg2 P + (y - x), P = x / y          -> o1 += x lg2 P,          o2 += y - x
@@ -310,11 +337,14 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
     __nv_bfloat16 *CdT = (__nv_bfloat16 *)(sm + L.cdt);
     __nv_bfloat16 *KnT = (__nv_bfloat16 *)(sm + L.knt);
     __nv_bfloat16 *KdT = (__nv_bfloat16 *)(sm + L.kdt);
-    // mbarriers: X stage full / empty, X-hat buffer full / empty, P tile full, contractions
-    // done, next slab's R written
+    // mbarriers, per ring slot s = chunk % NS: chunk_ready (X stage landed and X-hat computed:
+    // the TMA bytes plus the GEMM1 commit), inputs_free (every epilogue warp has read the X
+    // stage and the X-hat buffer); per P buffer: p_full, g2_done (its contractions complete);
+    // r_full (R holds the next slab)
     uint64_t *bars = (uint64_t *)(sm + L.misc);
-    uint64_t *x_full = bars, *x_empty = bars + 3, *g1_full = bars + 6, *d1_empty = bars + 8;
-    uint64_t *p_full = bars + 10, *g2_done = bars + 12, *r_full = bars + 14;
+    uint64_t *chunk_ready = bars, *inputs_free = bars + 4, *p_full = bars + 8, *g2_done = bars + 10;
+    uint64_t *r_full = bars + 12;
+    constexpr int NBAR = 13;
     uint32_t *tslot = (uint32_t *)(sm + L.misc + 128);
     volatile int *abort_flag = (volatile int *)(sm + L.misc + 136);
     double *dred = (double *)(sm + L.misc + 192 + 1024);  // [EW / 32]
@@ -431,8 +461,8 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
         }
     };
     if (t == EW) {
-        for (int q = 0; q < 15; ++q) {
-            const uint32_t cnt = (q >= 3 && q < 6) || (q >= 8 && q < 12) || q == 14 ? EW / 32 : 1;
+        for (int q = 0; q < NBAR; ++q) {
+            const uint32_t cnt = q < 4 ? 2 : q < 10 || q == 12 ? EW / 32 : 1;
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" :: "r"(su32(bars + q)), "r"(cnt));
         }
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
@@ -475,15 +505,22 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
                 if (x + 32 < K) tma_prefetch_2d(&xmap, x + 32, i * J + j0);
             };
             for (int c = NS; c < NS + PF && c < NC; ++c) prefetch_x(c);
+            int xs = 0;        // ring slot of chunk n
+            uint32_t xph = 0;  // parity of its phase, (n / NS) & 1
             for (int n = 0; n < NC; ++n) {
-                if (n >= NS && !wait(x_empty + (n % NS), ((n - NS) / NS) & 1)) break;
+                // chunk n - NS used this slot with the other parity
+                if (n >= NS && !wait(inputs_free + xs, xph ^ 1)) break;
                 const int i = i0 + (n >> 1), q = n & 1;
-                const uint32_t bar = su32(x_full + (n % NS));
-                const uint32_t dst = su32(Xs) + (n % NS) * 32768;
+                const uint32_t bar = su32(chunk_ready + xs);
+                const uint32_t dst = su32(Xs) + xs * 32768;
                 expect_tx(bar, 32768);
                 tma_2d(&xmap, dst, bar, k0 + CH * q, i * J + j0);
                 tma_2d(&xmap, dst + 16384, bar, k0 + CH * q + 32, i * J + j0);
                 if (n >= NS && n + PF < NC) prefetch_x(n + PF);
+                if (++xs == NS) {
+                    xs = 0;
+                    xph ^= 1;
+                }
             }
         }
         __syncwarp();
@@ -503,7 +540,7 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
                 }
 #pragma unroll
                 for (int s = 0; s < 4; ++s) mma_tf32(d, sdesc(su32(Rs) + s * 32), sdesc(cb + s * 32), id, S3 || s > 0);
-                mma_commit(su32(g1_full + (n & 1)));
+                mma_commit(su32(chunk_ready + n % NS));
             };
             auto issue_g2 = [&](int n) {
                 const int q = n & 1, sb = (n >> 1) & 1;
@@ -536,7 +573,8 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
                 const int m = n + 1;
                 if (m < NC) {
                     bool ok = true;
-                    if (m >= 2) ok = wait(d1_empty + (m & 1), ((m >> 1) - 1) & 1);
+                    // X-hat buffer m & 1 was last read by chunk m - 2
+                    if (m >= 2) ok = wait(inputs_free + (m - 2) % NS, ((m - 2) / NS) & 1);
                     if (ok && (m & 1) == 0) ok = wait(r_full, ((m >> 1) - 1) & 1);
                     if (!ok) break;
                     fence_after();
@@ -583,9 +621,18 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
                 }
             }
         };
+        // shared-memory offsets of this thread's X and P / Q entries within a stage / tile
+        int xo[CW / 4], po[CW / 8];
+#pragma unroll
+        for (int g = 0; g < CW / 4; ++g) xo[g] = ((CW * cg) >> 5) * 4096 + swf(row, ((CW * cg) & 31) + 4 * g);
+#pragma unroll
+        for (int g = 0; g < CW / 8; ++g) po[g] = swh(row, CW * cg + 8 * g);
+        int xs = 0;        // ring slot of chunk n
+        uint32_t xph = 0;  // parity of its phase, (n / NS) & 1
         for (int n = 0; n < NC; ++n) {
             const int i = i0 + (n >> 1), q = n & 1;
-            if (n >= NP) wait(g2_done + (n % NP), ((n - NP) / NP) & 1);  // P tile n % NP free again
+            const int pb = NP == 2 ? q : 0;
+            if (n >= NP) wait(g2_done + pb, ((n - NP) / NP) & 1);  // P tile pb free again
             if (q == 0 && n > 0) {
                 // slab boundary: rows of slab i + 2 staged; KRn^T of slab i written into the
                 // buffer last read by the contractions of slab i - NK, which are complete (the
@@ -609,17 +656,30 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
                 fold(i - 1);
                 fence_before();
             }
-            wait(g1_full + (n & 1), (n >> 1) & 1);
-            wait(x_full + (n % NS), (n / NS) & 1);
+            const bool ready = __all_sync(0xffffffffu, wait(chunk_ready + xs, xph));
             fence_after();
-            float xh[CW];
-            if (!__any_sync(0xffffffffu, *abort_flag != 0)) tmem_ld<CW>(t_d1 + 64 * (n & 1) + lane_off + CW * cg, xh);
-            else {
+            float xh[CW], xv[CW];
+            if (ready) {  // warp-uniform before tcgen05.ld
+                tmem_ld<CW>(t_d1 + 64 * q + lane_off + CW * cg, xh);
+            } else {
 #pragma unroll
                 for (int c = 0; c < CW; ++c) xh[c] = 0.0f;
             }
+            {
+                // the X stage holds two 128 x 32 halves; this group's columns lie in one
+                const float *xa = Xs + xs * 8192;
+#pragma unroll
+                for (int g = 0; g < CW / 4; ++g) {
+                    const float4 v = *reinterpret_cast<const float4 *>(xa + xo[g]);
+                    xv[4 * g] = v.x; xv[4 * g + 1] = v.y; xv[4 * g + 2] = v.z; xv[4 * g + 3] = v.w;
+                }
+            }
             fence_before();
-            arrive(d1_empty + (n & 1));
+            arrive(inputs_free + xs);
+            if (++xs == NS) {
+                xs = 0;
+                xph ^= 1;
+            }
             if (q == 1 && n + 1 < NC) {
                 // this chunk's GEMM1 is complete, so R can take slab i + 1 (needed by GEMM1 of
                 // the next chunk, which the issuer starts once every warp has arrived)
@@ -627,28 +687,33 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
                 fence_async_smem();
                 arrive(r_full);
             }
-            float xv[CW];
-            {
-                // the X stage holds two 128 x 32 halves; this group's columns lie in one
-                const float *xa = Xs + (n % NS) * 8192 + ((CW * cg) >> 5) * 4096;
-                const int xc = (CW * cg) & 31;
-#pragma unroll
-                for (int g = 0; g < CW / 4; ++g) {
-                    const float4 v = *reinterpret_cast<const float4 *>(xa + swf(row, xc + 4 * g));
-                    xv[4 * g] = v.x; xv[4 * g + 1] = v.y; xv[4 * g + 2] = v.z; xv[4 * g + 3] = v.w;
-                }
-            }
-            arrive(x_empty + (n % NS));
-            __nv_bfloat16 *pa = Ps + (n % NP) * 8192;
-            __nv_bfloat16 *qa = Qs + (n % NP) * 8192;
+            __nv_bfloat16 *pa = Ps + pb * 8192;
+            __nv_bfloat16 *qa = Qs + pb * 8192;
             const int kc = k0 + CH * q + CW * cg;
             float o1 = 0.0f, o2 = 0.0f;
-            // full 32-column strip of a valid row: no per-entry masks
+            float2 u1 = make_float2(0.0f, 0.0f), u2 = make_float2(0.0f, 0.0f);  // packed KL sums
+            // full strip of a valid row: no per-entry masks
             auto body = [&](auto full_tag) {
                 constexpr bool FULL = decltype(full_tag)::value;
 #pragma unroll
                 for (int g = 0; g < CW / 8; ++g) {
                     float pv[8], qv[8];
+                    if (FULL && BK == BK_KL) {
+                        // the KL point function on pairs of entries
+#pragma unroll
+                        for (int c = 0; c < 8; c += 2) {
+                            const float2 x2 = make_float2(xv[8 * g + c], xv[8 * g + c + 1]);
+                            const float2 y2 = make_float2(fmaxf(xh[8 * g + c], a.eps), fmaxf(xh[8 * g + c + 1], a.eps));
+                            const float2 P2 = mul2(x2, make_float2(mufu_rcp(y2.x), mufu_rcp(y2.y)));
+                            pv[c] = P2.x;
+                            pv[c + 1] = P2.y;
+                            if (OBJ) {
+                                const float2 l2 = make_float2(mufu_lg2(fmaxf(P2.x, 1e-30f)), mufu_lg2(fmaxf(P2.y, 1e-30f)));
+                                u1 = fma2(x2, l2, u1);
+                                u2 = add2(u2, sub2(y2, x2));
+                            }
+                        }
+                    } else
 #pragma unroll
                     for (int c = 0; c < 8; ++c) {
                         float x = xv[8 * g + c];
@@ -665,31 +730,34 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
                             if (OBJ && v) { o1 += e1; o2 += e2; }
                         }
                     }
-                    const int kk = CW * cg + 8 * g;
                     __nv_bfloat162 h0 = __floats2bfloat162_rn(pv[0], pv[1]), h1 = __floats2bfloat162_rn(pv[2], pv[3]);
                     __nv_bfloat162 h2 = __floats2bfloat162_rn(pv[4], pv[5]), h3 = __floats2bfloat162_rn(pv[6], pv[7]);
                     uint4 u;
                     u.x = *reinterpret_cast<uint32_t *>(&h0); u.y = *reinterpret_cast<uint32_t *>(&h1);
                     u.z = *reinterpret_cast<uint32_t *>(&h2); u.w = *reinterpret_cast<uint32_t *>(&h3);
-                    *reinterpret_cast<uint4 *>(pa + swh(row, kk)) = u;
+                    *reinterpret_cast<uint4 *>(pa + po[g]) = u;
                     if (DEN) {
                         h0 = __floats2bfloat162_rn(qv[0], qv[1]); h1 = __floats2bfloat162_rn(qv[2], qv[3]);
                         h2 = __floats2bfloat162_rn(qv[4], qv[5]); h3 = __floats2bfloat162_rn(qv[6], qv[7]);
                         u.x = *reinterpret_cast<uint32_t *>(&h0); u.y = *reinterpret_cast<uint32_t *>(&h1);
                         u.z = *reinterpret_cast<uint32_t *>(&h2); u.w = *reinterpret_cast<uint32_t *>(&h3);
-                        *reinterpret_cast<uint4 *>(qa + swh(row, kk)) = u;
+                        *reinterpret_cast<uint4 *>(qa + po[g]) = u;
                     }
                 }
             };
             if (jv && kc + CW <= K) body(std::true_type{});
             else body(std::false_type{});
+            if (BK == BK_KL) {
+                o1 += u1.x + u1.y;
+                o2 += u2.x + u2.y;
+            }
             const float objf = OBJ ? obj_combine<BK>(a.beta, o1, o2) : 0.0f;
             if (OBJ) obj_acc += (double)objf;
             fence_async_smem();
-            arrive(p_full + (n % NP));
+            arrive(p_full + pb);
         }
         if (NC > 0) {
-            wait(g2_done + ((NC - 1) % NP), ((NC - 1) / NP) & 1);
+            wait(g2_done + (NC - 1) % NP, ((NC - 1) / NP) & 1);
             fence_after();
             if (RW) fold(i1 - 1);
         }
@@ -741,7 +809,7 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
     __syncthreads();
     if (*abort_flag && t == EW) {
         // bounded waits (without the abort shortcut) for copies and MMAs still in flight
-        for (int q = 0; q < 15; ++q) {
+        for (int q = 0; q < NBAR; ++q) {
             for (int ph = 0; ph < 2; ++ph) {
                 for (int it = 0; it < (1 << 20); ++it) {
                     uint32_t done;

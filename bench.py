@@ -46,7 +46,47 @@ def parse():
                    help="jobs of the serving-mix measurement in the default run (0: skip)")
     p.add_argument("--serve", action="store_true", help="print only the serving-mix line")
     p.add_argument("--slots", type=int, default=16)
+    p.add_argument("--profile-n", type=int, default=0,
+                   help="profiling driver: three J-CoMM steps and three block-MU sweeps on an n^3, "
+                        "R = 32, beta = 1 tensor at --precision, then exit (no measurement)")
     return p.parse_args()
+
+
+# DRAM bytes (read + write) per tensor entry of the timed tensor-core pass (all numerators +
+# objective, TF32 reconstruction), from the ncu capture summarised in
+# profiles/cp3_pass_tc_cp384_r32_beta1_tf32.md; valid only for the kernel sources it was taken on
+TC_CAPTURE = {
+    "sources": {"paper_2602_14683_gb300/csrc/cp3_tc.cuh": "a2e9ee5cd8c2ef70a63652ad518975caca0067635bc1d3cc1b4ae92e4a78fb29",
+                "paper_2602_14683_gb300/csrc/cp3_tc.cu": "f0c1d697e022d9ea88a203d90bdc95881740869dd753f03242113a9c49949ae3"},
+    "bytes_per_entry": (228.187392e6 + 4.641536e6) / 384 ** 3,
+}
+
+
+def tc_traffic(entries):
+    import hashlib
+    here = os.path.dirname(os.path.abspath(__file__))
+    for rel, digest in TC_CAPTURE["sources"].items():
+        with open(os.path.join(here, rel), "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest() != digest:
+                return None  # the kernel changed since the counters were taken
+    return TC_CAPTURE["bytes_per_entry"] * entries
+
+
+def profile_case(n, prec):
+    """Small, fixed launch sequence for ncu captures (one GPU, a few hundred MB)."""
+    import torch
+    import paper_2602_14683_gb300 as ntf
+    g = torch.Generator(device="cuda").manual_seed(0)
+    X = torch.rand((n, n, n), device="cuda", generator=g) * 10 + 0.1
+    A = [torch.rand((n, 32), device="cuda", generator=g) * 0.9 + 0.1 for _ in range(3)]
+    obj = torch.zeros(1, dtype=torch.float64, device="cuda")
+    for _ in range(3):
+        ntf.jcomm_outer(X, 1.0, A, objective=obj, precision=prec)
+        ntf.cp_mu_sweep(X, 1.0, A, objective=obj, precision=prec)
+    torch.cuda.synchronize()
+    ntf.default_context().device_status()
+    print("profile case n=%d precision=%s objective %.6e" % (n, prec, obj.item()))
+    return 0
 
 
 def run_serving(ntf, n_jobs, slots, seed=0, max_iters=200, rtol=1e-6):
@@ -207,6 +247,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_n > 0:
+        return profile_case(args.profile_n, args.precision)
 
     import torch
     import torch.distributed as dist
@@ -389,7 +431,7 @@ def main():
                 "unit": "GB/s", "peak_source": "%s HBM copy bandwidth" % peak_src,
                 "tensor_tflops_algorithmic": flops_per_launch / avg_pass / 1e12}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
+    roof["traffic"] = tc_traffic(entries) if prec == "tf32" else None
     roof["pass_ms_avg"] = avg_pass * 1e3
     roof["pass_launches"] = pass_n
 

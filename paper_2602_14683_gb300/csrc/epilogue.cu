@@ -188,15 +188,24 @@ __global__ void mode_update_kernel(UpdArgs u) {
         __syncthreads();
     }
     if (u.n_cs > 0) {
-        if (t < RP) {
-            double prod = 1.0;
-            for (int k = 0; k < u.n_cs; ++k) {
-                double sum = 0.0;
-                for (int b = 0; b < u.cs_nb[k]; ++b) sum += u.cs_in[k][(int64_t)b * RP + t];
-                prod *= sum;
+        // each factor's column sums: thread (g, r) adds blocks g, g + G, ..., then the G
+        // group sums are added in order (fixed order, the same in every block)
+        double prod = 1.0;
+        for (int k = 0; k < u.n_cs; ++k) {
+            double sum = 0.0;
+            for (int b0 = g; b0 < u.cs_nb[k]; b0 += 8 * G) {  // eight loads in flight
+                double v[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int b = b0 + q * G;
+                    v[q] = b < u.cs_nb[k] ? u.cs_in[k][(int64_t)b * RP + r] : 0.0;
+                }
+#pragma unroll
+                for (int q = 0; q < 8; ++q) sum += v[q];
             }
-            den_s[t] = (float)prod;
+            prod *= group_sum(sh, sum, RP, t);
         }
+        if (t < RP) den_s[t] = (float)prod;
         __syncthreads();
     }
     const int rpb = rows_per_block(e.rows, RP);
@@ -207,12 +216,27 @@ __global__ void mode_update_kernel(UpdArgs u) {
         const int64_t o = (int64_t)i * RP + r;
         float v = 0.0f, c1 = 0.0f, c2 = 0.0f;
         if (r < e.R) {
-            float num = 0.0f, den = 0.0f;
-            for (int p = 0; p < e.n_parts; ++p) num += e.pn[p * stride + o];
+            // partials in batches of 16 loads in flight, each batch added as a fixed tree and
+            // the batch sums in order (a fixed order for every run)
+            auto psum = [&](const float *src) {
+                float acc = 0.0f;
+                for (int p0 = 0; p0 < e.n_parts; p0 += 16) {
+                    float v[16];
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) v[k] = p0 + k < e.n_parts ? src[(int64_t)(p0 + k) * stride + o] : 0.0f;
+#pragma unroll
+                    for (int w = 8; w >= 1; w >>= 1)
+#pragma unroll
+                        for (int k = 0; k < w; ++k) v[k] += v[k + w];
+                    acc += v[0];
+                }
+                return acc;
+            };
+            const float num = psum(e.pn);
+            float den;
             if (u.n_cs > 0) den = den_s[r];
             else if (e.den_closed) den = e.den_closed[r];
-            else
-                for (int p = 0; p < e.n_parts; ++p) den += e.pd[p * stride + o];
+            else den = psum(e.pd);
             const float ratio = __fdiv_rn(num, den);
             float m;
             if (e.gamma == 1.0f) m = ratio;

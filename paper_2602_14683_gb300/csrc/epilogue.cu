@@ -190,21 +190,24 @@ __global__ void mode_update_kernel(UpdArgs u) {
     if (u.n_cs > 0) {
         // each factor's column sums: thread (g, r) adds blocks g, g + G, ..., then the G
         // group sums are added in order (fixed order, the same in every block)
-        double prod = 1.0;
-        for (int k = 0; k < u.n_cs; ++k) {
-            double sum = 0.0;
-            for (int b0 = g; b0 < u.cs_nb[k]; b0 += 8 * G) {  // eight loads in flight
-                double v[8];
+        // the loads of both factors' first eight blocks are issued together
+        double sum[2] = {0.0, 0.0};
+        for (int b0 = g; b0 < u.cs_nb[0] || (u.n_cs > 1 && b0 < u.cs_nb[1]); b0 += 8 * G) {
+            double v[2][8];
+#pragma unroll
+            for (int k = 0; k < 2; ++k)
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
                     const int b = b0 + q * G;
-                    v[q] = b < u.cs_nb[k] ? u.cs_in[k][(int64_t)b * RP + r] : 0.0;
+                    v[k][q] = (k < u.n_cs && b < u.cs_nb[k]) ? u.cs_in[k][(int64_t)b * RP + r] : 0.0;
                 }
 #pragma unroll
-                for (int q = 0; q < 8; ++q) sum += v[q];
-            }
-            prod *= group_sum(sh, sum, RP, t);
+            for (int k = 0; k < 2; ++k)
+#pragma unroll
+                for (int q = 0; q < 8; ++q) sum[k] += v[k][q];
         }
+        double prod = 1.0;
+        for (int k = 0; k < u.n_cs; ++k) prod *= group_sum(sh, sum[k], RP, t);
         if (t < RP) den_s[t] = (float)prod;
         __syncthreads();
     }
@@ -216,19 +219,25 @@ __global__ void mode_update_kernel(UpdArgs u) {
         const int64_t o = (int64_t)i * RP + r;
         float v = 0.0f, c1 = 0.0f, c2 = 0.0f;
         if (r < e.R) {
-            // partials in batches of 16 loads in flight, each batch added as a fixed tree and
-            // the batch sums in order (a fixed order for every run)
+            // partials in batches of 16, each batch added as a fixed tree and the batch sums
+            // in order (a fixed order for every run); two batches (32 loads) are in flight at
+            // once
             auto psum = [&](const float *src) {
                 float acc = 0.0f;
-                for (int p0 = 0; p0 < e.n_parts; p0 += 16) {
-                    float v[16];
+                for (int p0 = 0; p0 < e.n_parts; p0 += 32) {
+                    float v[32];
 #pragma unroll
-                    for (int k = 0; k < 16; ++k) v[k] = p0 + k < e.n_parts ? src[(int64_t)(p0 + k) * stride + o] : 0.0f;
+                    for (int k = 0; k < 32; ++k) v[k] = p0 + k < e.n_parts ? src[(int64_t)(p0 + k) * stride + o] : 0.0f;
 #pragma unroll
-                    for (int w = 8; w >= 1; w >>= 1)
+                    for (int b = 0; b < 2; ++b) {
+                        if (p0 + 16 * b >= e.n_parts) break;
+                        float *w16 = v + 16 * b;
 #pragma unroll
-                        for (int k = 0; k < w; ++k) v[k] += v[k + w];
-                    acc += v[0];
+                        for (int w = 8; w >= 1; w >>= 1)
+#pragma unroll
+                            for (int k = 0; k < w; ++k) w16[k] += w16[k + w];
+                        acc += w16[0];
+                    }
                 }
                 return acc;
             };

@@ -17,6 +17,7 @@
 // current blocks (and of the core) on the numerator / denominator side; since W depends
 // on the third factor only, one rows pass serves the core and modes 1 and 2 of an inner
 // sweep, so an inner sweep reads X twice instead of four times.
+#include <algorithm>
 #include <string>
 
 #include "cp3_fp32.cuh"
@@ -27,6 +28,9 @@ namespace ntf {
 // ----------------------------------------------------------------------------------
 // Strided batched GEMM with a two-level reduction index (FP32 FMA, FP64 carry):
 //   C[bt][m][n] = sum_{k1 < K1, k2 < K2} A(bt, m, k1, k2) * B(bt, k1, k2, n)
+// The reduction index k = k1 * K2 + k2 may be split into `splits` contiguous ranges, one
+// CTA per (tile, batch, range); each range's FP64 sum goes to `part`, and the ranges are
+// then added in order by a second kernel (a fixed order for every run).
 // ----------------------------------------------------------------------------------
 struct Gemm {
     const float *A, *B;
@@ -35,6 +39,8 @@ struct Gemm {
     int64_t sab, sam, sak1, sak2;
     int64_t sbb, sbk1, sbk2, sbn;
     int64_t scb, scm, scn;
+    int splits, kchunks;  // reduction ranges and GK-chunks per range (set by gemm())
+    double *part;         // [splits][batch][M][N] when splits > 1
 };
 
 constexpr int GT = 64;   // output tile edge
@@ -44,10 +50,11 @@ constexpr int GCARRY = 16;  // chunks summed in FP32 before the FP64 carry
 __global__ void __launch_bounds__(256) gemm2k_kernel(const Gemm g) {
     __shared__ float As[GK][GT + 4];
     __shared__ float Bs[GK][GT + 4];
-    const int bt = blockIdx.z;
+    const int bt = blockIdx.z % g.batch, sp = blockIdx.z / g.batch;
     const int m0 = blockIdx.y * GT, n0 = blockIdx.x * GT;
     const int tid = threadIdx.x, tm = tid / 16, tn = tid % 16;
-    const int64_t K = (int64_t)g.K1 * g.K2;
+    const int K = g.K1 * g.K2;
+    const int kbeg = sp * g.kchunks * GK, kend = min(K, kbeg + g.kchunks * GK);
     float acc[4][4];
     double tot[4][4];
 #pragma unroll
@@ -57,13 +64,13 @@ __global__ void __launch_bounds__(256) gemm2k_kernel(const Gemm g) {
     const float *A = g.A + bt * g.sab;
     const float *B = g.B + bt * g.sbb;
     int chunk = 0;
-    for (int64_t k0 = 0; k0 < K; k0 += GK) {
+    for (int k0 = kbeg; k0 < kend; k0 += GK) {
         for (int t = tid; t < GK * GT; t += 256) {
             const int kk = t / GT, mm = t % GT;
-            const int64_t k = k0 + kk;
+            const int k = k0 + kk;
             float va = 0.0f, vb = 0.0f;
-            if (k < K) {
-                const int64_t k1 = k / g.K2, k2 = k % g.K2;
+            if (k < kend) {
+                const int k1 = g.K2 == 1 ? k : k / g.K2, k2 = k - k1 * g.K2;
                 if (m0 + mm < g.M) va = A[(m0 + mm) * g.sam + k1 * g.sak1 + k2 * g.sak2];
                 if (n0 + mm < g.N) vb = B[k1 * g.sbk1 + k2 * g.sbk2 + (n0 + mm) * g.sbn];
             }
@@ -97,14 +104,50 @@ __global__ void __launch_bounds__(256) gemm2k_kernel(const Gemm g) {
 #pragma unroll
         for (int y = 0; y < 4; ++y) {
             const int m = m0 + tm + 16 * x, n = n0 + tn + 16 * y;
-            if (m < g.M && n < g.N) g.C[bt * g.scb + m * g.scm + n * g.scn] = (float)(tot[x][y] + (double)acc[x][y]);
+            if (m < g.M && n < g.N) {
+                const double v = tot[x][y] + (double)acc[x][y];
+                if (g.splits > 1) g.part[(((int64_t)sp * g.batch + bt) * g.M + m) * g.N + n] = v;
+                else g.C[bt * g.scb + m * g.scm + n * g.scn] = (float)v;
+            }
         }
 }
 
-static cudaError_t gemm(const Gemm &g, cudaStream_t s) {
-    dim3 grid((g.N + GT - 1) / GT, (g.M + GT - 1) / GT, g.batch);
+// C = sum over the reduction ranges, in range order
+__global__ void gemm_split_sum_kernel(const Gemm g) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t mn = (int64_t)g.M * g.N, total = mn * g.batch;
+    if (t >= total) return;
+    double v = 0.0;
+    for (int sp = 0; sp < g.splits; ++sp) v += g.part[(int64_t)sp * total + t];
+    const int bt = (int)(t / mn), m = (int)((t % mn) / g.N), n = (int)(t % g.N);
+    g.C[bt * g.scb + m * g.scm + n * g.scn] = (float)v;
+}
+
+// Splits the reduction when the output tiles alone would leave most SMs idle: about two
+// CTAs per SM, at least four GK-chunks per range.
+static int gemm(ntf_ctx *ctx, Gemm g, cudaStream_t s) {
+    const int tiles = ((g.N + GT - 1) / GT) * ((g.M + GT - 1) / GT) * g.batch;
+    const int nchunks = (g.K1 * g.K2 + GK - 1) / GK;
+    int splits = (2 * ctx_num_sms(ctx) + tiles - 1) / tiles;
+    splits = std::max(1, std::min(splits, nchunks / 4));
+    g.kchunks = (nchunks + splits - 1) / splits;
+    g.splits = (nchunks + g.kchunks - 1) / g.kchunks;
+    if (g.splits > 1) {
+        g.part = (double *)ctx_ws(ctx, "gemm_split", sizeof(double) * (size_t)g.splits * g.batch * g.M * g.N);
+        if (!g.part) return ctx_fail(ctx, NTF_ERR_OOM, "workspace allocation failed");
+    }
+    dim3 grid((g.N + GT - 1) / GT, (g.M + GT - 1) / GT, g.batch * g.splits);
     gemm2k_kernel<<<grid, 256, 0, s>>>(g);
-    return cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && g.splits > 1) {
+        const int64_t total = (int64_t)g.M * g.N * g.batch;
+        gemm_split_sum_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(g);
+        e = cudaGetLastError();
+        ctx_count(ctx, 1);
+    }
+    if (e != cudaSuccess) return ctx_fail(ctx, NTF_ERR_CUDA, cudaGetErrorString(e));
+    ctx_count(ctx, 1);
+    return NTF_OK;
 }
 
 // ----------------------------------------------------------------------------------
@@ -389,14 +432,14 @@ int build_b3(ntf_ctx *ctx, TuckerWs &w, const Blocks &b, float *out, cudaStream_
     g.A = b.A1; g.B = b.G; g.C = w.GA1;
     g.M = w.I1; g.N = w.J2 * w.J3; g.K1 = w.J1; g.K2 = 1; g.batch = 1;
     g.sam = w.J1; g.sak1 = 1; g.sbk1 = (int64_t)w.J2 * w.J3; g.sbn = 1; g.scm = (int64_t)w.J2 * w.J3; g.scn = 1;
-    TK(gemm(g, st));
+    { const int rc_ = gemm(ctx, g, st); if (rc_) return rc_; }
     Gemm h{};
     h.A = b.A2; h.B = w.GA1; h.C = out;
     h.M = w.I2; h.N = w.J3; h.K1 = w.J2; h.K2 = 1; h.batch = w.I1;
     h.sab = 0; h.sam = w.J2; h.sak1 = 1;
     h.sbb = (int64_t)w.J2 * w.J3; h.sbk1 = w.J3; h.sbn = 1;
     h.scb = (int64_t)w.I2 * w.RP; h.scm = w.RP; h.scn = 1;
-    TK(gemm(h, st));
+    { const int rc_ = gemm(ctx, h, st); if (rc_) return rc_; }
     return NTF_OK;
 }
 
@@ -439,13 +482,13 @@ int contract_from_w(ntf_ctx *ctx, TuckerWs &w, int block, const Blocks &b, const
         g.sam = 1; g.sak1 = w.J2;
         g.sbb = (int64_t)w.I2 * w.RP; g.sbk1 = w.RP; g.sbn = 1;
         g.scb = (int64_t)w.J2 * w.J3; g.scm = w.J3; g.scn = 1;
-        TK(gemm(g, st));
+        { const int rc_ = gemm(ctx, g, st); if (rc_) return rc_; }
         Gemm h{};
         h.A = b.A1; h.B = w.Y; h.C = out;
         h.M = w.J1; h.N = w.J2 * w.J3; h.K1 = w.I1; h.K2 = 1; h.batch = 1;
         h.sam = 1; h.sak1 = w.J1; h.sbk1 = (int64_t)w.J2 * w.J3; h.sbn = 1;
         h.scm = (int64_t)w.J2 * w.J3; h.scn = 1;
-        TK(gemm(h, st));
+        { const int rc_ = gemm(ctx, h, st); if (rc_) return rc_; }
     } else if (block == 1) {  // H[j][a][c] = sum_b A2[j,b] G[a,b,c]; Num1 = sum_{j,c} W H
         Gemm g{};
         g.A = b.A2; g.B = b.G; g.C = w.H;
@@ -453,27 +496,27 @@ int contract_from_w(ntf_ctx *ctx, TuckerWs &w, int block, const Blocks &b, const
         g.sam = w.J2; g.sak1 = 1;
         g.sbb = (int64_t)w.J2 * w.J3; g.sbk1 = w.J3; g.sbn = 1;
         g.scb = w.J3; g.scm = (int64_t)w.J1 * w.J3; g.scn = 1;
-        TK(gemm(g, st));
+        { const int rc_ = gemm(ctx, g, st); if (rc_) return rc_; }
         Gemm h{};
         h.A = W; h.B = w.H; h.C = out;
         h.M = w.I1; h.N = w.J1; h.K1 = w.I2; h.K2 = w.J3; h.batch = 1;
         h.sam = (int64_t)w.I2 * w.RP; h.sak1 = w.RP; h.sak2 = 1;
         h.sbk1 = (int64_t)w.J1 * w.J3; h.sbk2 = 1; h.sbn = w.J3;
         h.scm = w.J1; h.scn = 1;
-        TK(gemm(h, st));
+        { const int rc_ = gemm(ctx, h, st); if (rc_) return rc_; }
     } else {  // GA1[i][b][c] = sum_a A1[i,a] G[a,b,c]; Num2 = sum_{i,c} W GA1
         Gemm g{};
         g.A = b.A1; g.B = b.G; g.C = w.GA1;
         g.M = w.I1; g.N = w.J2 * w.J3; g.K1 = w.J1; g.K2 = 1; g.batch = 1;
         g.sam = w.J1; g.sak1 = 1; g.sbk1 = (int64_t)w.J2 * w.J3; g.sbn = 1; g.scm = (int64_t)w.J2 * w.J3; g.scn = 1;
-        TK(gemm(g, st));
+        { const int rc_ = gemm(ctx, g, st); if (rc_) return rc_; }
         Gemm h{};
         h.A = W; h.B = w.GA1; h.C = out;
         h.M = w.I2; h.N = w.J2; h.K1 = w.I1; h.K2 = w.J3; h.batch = 1;
         h.sam = w.RP; h.sak1 = (int64_t)w.I2 * w.RP; h.sak2 = 1;
         h.sbk1 = (int64_t)w.J2 * w.J3; h.sbk2 = 1; h.sbn = w.J3;
         h.scm = w.J2; h.scn = 1;
-        TK(gemm(h, st));
+        { const int rc_ = gemm(ctx, h, st); if (rc_) return rc_; }
     }
     return NTF_OK;
 }

@@ -166,11 +166,13 @@ int ntf_coo_stable_perm(ntf_ctx *ctx, const int32_t *keys, int64_t nnz, int64_t 
  * The server owns `slots` execution slots (a context and a stream each) and a scheduler
  * thread.  Submitted jobs queue FIFO; the head is admitted into a free slot when its
  * estimated workspace fits the device-memory budget (a job larger than the budget runs
- * alone).  An admitted job runs one iteration eagerly, then one iteration of its method is
- * captured as a CUDA graph and replayed; after each iteration the FP64 objective of the
- * iteration's incoming iterate (Section 3.2) is read into pinned host memory and the job
- * stops when |F_{t-1} - F_t| / F_{t-1} <= rtol or after max_iters iterations.  Jobs in
- * different slots run concurrently.  A job's result does not depend on what else runs.
+ * alone).  An admitted job runs one iteration eagerly (sizing its slot's workspaces), then
+ * the rest of the job as one CUDA graph launch: a conditional WHILE node over one captured
+ * iteration of its method followed by a one-thread kernel that applies the stopping test on
+ * the device to the FP64 objective of the iteration's incoming iterate (Section 3.2): stop
+ * when |F_{t-1} - F_t| / F_{t-1} <= rtol or after max_iters iterations.  No host round trip
+ * happens between iterations.  Jobs in different slots run concurrently.  A job's result
+ * does not depend on what else runs.
  * The caller owns X, factors and core (device memory) and must keep them alive and
  * untouched until the job's result has been polled; factors and core are updated in
  * place.  Server functions are thread-safe; each job uses the device of the server.

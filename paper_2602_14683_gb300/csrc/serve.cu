@@ -3,13 +3,14 @@
 // A server owns `slots` execution slots, each an ntf context (its own workspaces) and a
 // CUDA stream.  Jobs wait in a FIFO queue; a scheduler thread admits the head of the queue
 // into a free slot when the slot's estimated workspace fits the device-memory budget, runs
-// one eager iteration (which sizes the workspaces and yields the first objective), then
-// captures one iteration of the job's method as a CUDA graph and replays it.  After each
-// iteration the FP64 objective is copied to pinned host memory and an event is recorded;
-// the scheduler polls the events of all active slots, applies the stopping test
-// |F_{t-1} - F_t| / F_{t-1} <= rtol (or the iteration cap) and either replays the graph
-// again or completes the job and frees the slot for the next admission.  Jobs in
-// different slots overlap on the device through their streams.  A job's kernels, launch
+// one eager iteration (which sizes the workspaces) followed by a one-thread kernel that
+// applies the stopping test to its objective, and then launches the rest of the job as ONE
+// CUDA graph: a conditional WHILE node whose body is one captured iteration of the job's
+// method plus the same stopping-test kernel, which clears the loop condition when
+// |F_{t-1} - F_t| / F_{t-1} <= rtol or the iteration cap is reached.  The whole solve thus
+// runs on the device without a host round trip per iteration; the host only sees the job's
+// final state (iterations, last objective), copied to pinned memory behind an event.  Jobs
+// in different slots overlap on the device through their streams.  A job's kernels, launch
 // shapes and reduction orders depend only on its own shapes, so its result is the same
 // whether it runs alone or among others.
 #include <chrono>
@@ -29,21 +30,43 @@ using Clock = std::chrono::steady_clock;
 
 double now_s() { return std::chrono::duration<double>(Clock::now().time_since_epoch()).count(); }
 
+// Stopping state of one job, updated on the device after every iteration.
+struct JobState {
+    double F_prev, F_last;  // objectives of the last two iterations' incoming iterates
+    double rtol;
+    int iters, max_iters, done, pad;
+};
+
 struct Slot {
     ntf_ctx *ctx = nullptr;
     cudaStream_t st = nullptr;
     cudaEvent_t ev = nullptr;
     double *F_dev = nullptr;
-    double *F_host = nullptr;  // pinned
+    JobState *S_dev = nullptr;
+    JobState *S_host = nullptr;  // pinned
     cudaGraphExec_t exec = nullptr;
     bool busy = false;
     ntf_job job{};
     int64_t id = -1;
-    int iters = 0;
-    double F_prev = 0.0, F_last = 0.0;
     double t_submit = 0.0, t_admit = 0.0;
     size_t bytes = 0;
 };
+
+// One more iteration done: its incoming iterate's objective is *F.  Same test as a host
+// loop would apply: stop when t > 1 and |F_{t-1} - F_t| / F_{t-1} <= rtol, or t = max_iters.
+__device__ void job_step(JobState *s, const double *F) {
+    s->iters += 1;
+    s->F_prev = s->F_last;
+    s->F_last = *F;
+    const double a = s->F_prev, b = s->F_last;
+    const bool conv = s->iters > 1 && a > 0.0 && (a - b) / a <= s->rtol && (b - a) / a <= s->rtol;
+    s->done = (conv || s->iters >= s->max_iters) ? 1 : 0;
+}
+__global__ void job_check_kernel(JobState *s, const double *F) { job_step(s, F); }
+__global__ void job_check_loop_kernel(JobState *s, const double *F, cudaGraphConditionalHandle h) {
+    job_step(s, F);
+    cudaGraphSetConditional(h, s->done ? 0u : 1u);
+}
 
 struct Pending {
     ntf_job job;
@@ -130,8 +153,8 @@ void finish(ntf_server *sv, Slot &s, int status) {
     ntf_result r{};
     r.id = s.id;
     r.status = status;
-    r.iterations = s.iters;
-    r.objective = s.F_last;
+    r.iterations = status == NTF_OK ? s.S_host->iters : 0;
+    r.objective = status == NTF_OK ? s.S_host->F_last : 0.0;
     r.t_submit = s.t_submit;
     r.t_admit = s.t_admit;
     r.t_done = now_s();
@@ -149,26 +172,57 @@ void finish(ntf_server *sv, Slot &s, int status) {
     sv->cv_done.notify_all();
 }
 
-// first (eager) iteration, then capture of one iteration as a graph
+// First (eager) iteration and its stopping test, then the remaining iterations as one
+// graph launch (WHILE node over one captured iteration + the stopping test), then the
+// job's final state to pinned memory and the slot's event.
 int admit(Slot &s) {
+    JobState init{};
+    init.rtol = s.job.rtol;
+    init.max_iters = s.job.max_iters;
+    *s.S_host = init;
+    if (cudaMemcpyAsync(s.S_dev, s.S_host, sizeof(JobState), cudaMemcpyHostToDevice, s.st) != cudaSuccess)
+        return NTF_ERR_CUDA;
     int rc = run_step(s, s.st);
     if (rc) return rc;
-    if (cudaMemcpyAsync(s.F_host, s.F_dev, sizeof(double), cudaMemcpyDeviceToHost, s.st) != cudaSuccess) return NTF_ERR_CUDA;
-    if (cudaEventRecord(s.ev, s.st) != cudaSuccess) return NTF_ERR_CUDA;
-    cudaGraph_t g = nullptr;
-    if (cudaStreamBeginCapture(s.st, cudaStreamCaptureModeRelaxed) != cudaSuccess) return NTF_ERR_CUDA;
-    rc = run_step(s, s.st);
-    if (cudaMemcpyAsync(s.F_host, s.F_dev, sizeof(double), cudaMemcpyDeviceToHost, s.st) != cudaSuccess) rc = NTF_ERR_CUDA;
-    cudaError_t e = cudaStreamEndCapture(s.st, &g);
-    if (rc) {
-        if (g) cudaGraphDestroy(g);
-        return rc;
+    job_check_kernel<<<1, 1, 0, s.st>>>(s.S_dev, s.F_dev);
+    if (cudaGetLastError() != cudaSuccess) return NTF_ERR_CUDA;
+    if (s.job.max_iters > 1) {
+        cudaGraph_t g = nullptr;
+        if (cudaGraphCreate(&g, 0) != cudaSuccess) return NTF_ERR_CUDA;
+        auto bail = [&](int code) {
+            cudaGraphDestroy(g);
+            return code;
+        };
+        cudaGraphConditionalHandle h;
+        if (cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) != cudaSuccess)
+            return bail(NTF_ERR_CUDA);
+        cudaGraphNodeParams cp{};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t node;
+        if (cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp) != cudaSuccess) return bail(NTF_ERR_CUDA);
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        if (cudaStreamBeginCaptureToGraph(s.st, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) != cudaSuccess)
+            return bail(NTF_ERR_CUDA);
+        rc = run_step(s, s.st);
+        if (!rc) {
+            job_check_loop_kernel<<<1, 1, 0, s.st>>>(s.S_dev, s.F_dev, h);
+            if (cudaGetLastError() != cudaSuccess) rc = NTF_ERR_CUDA;
+        }
+        cudaGraph_t captured = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(s.st, &captured);
+        if (rc) return bail(rc);
+        if (e != cudaSuccess) return bail(NTF_ERR_CUDA);
+        const cudaError_t ei = cudaGraphInstantiate(&s.exec, g, 0);
+        cudaGraphDestroy(g);
+        if (ei != cudaSuccess) return NTF_ERR_CUDA;
+        if (cudaGraphLaunch(s.exec, s.st) != cudaSuccess) return NTF_ERR_CUDA;
     }
-    if (e != cudaSuccess || !g) return NTF_ERR_CUDA;
-    e = cudaGraphInstantiate(&s.exec, g, 0);
-    cudaGraphDestroy(g);
-    if (e != cudaSuccess) return NTF_ERR_CUDA;
-    s.iters = 0;
+    if (cudaMemcpyAsync(s.S_host, s.S_dev, sizeof(JobState), cudaMemcpyDeviceToHost, s.st) != cudaSuccess)
+        return NTF_ERR_CUDA;
+    if (cudaEventRecord(s.ev, s.st) != cudaSuccess) return NTF_ERR_CUDA;
     return NTF_OK;
 }
 
@@ -199,12 +253,10 @@ void worker_loop(ntf_server *sv) {
             s.id = p.id;
             s.t_submit = p.t_submit;
             s.t_admit = now_s();
-            s.F_prev = s.F_last = 0.0;
-            s.iters = 0;
             const int rc = admit(s);
             if (rc) finish(sv, s, rc);
         }
-        // progress of active slots
+        // completion of active slots (each runs its whole job as one graph launch)
         bool any = false;
         for (auto &s : sv->slots) {
             if (!s.busy) continue;
@@ -216,20 +268,7 @@ void worker_loop(ntf_server *sv) {
                 finish(sv, s, NTF_ERR_CUDA);
                 continue;
             }
-            // one more iteration completed: F_host holds the objective of its incoming iterate
-            ++s.iters;
-            s.F_prev = s.F_last;
-            s.F_last = *s.F_host;
-            const bool conv = s.iters > 1 && s.F_prev > 0.0 && (s.F_prev - s.F_last) / s.F_prev <= s.job.rtol &&
-                              (s.F_last - s.F_prev) / s.F_prev <= s.job.rtol;
-            if (conv || s.iters >= s.job.max_iters) {
-                finish(sv, s, NTF_OK);
-                continue;
-            }
-            if (cudaGraphLaunch(s.exec, s.st) != cudaSuccess || cudaEventRecord(s.ev, s.st) != cudaSuccess) {
-                cudaGetLastError();
-                finish(sv, s, NTF_ERR_CUDA);
-            }
+            finish(sv, s, NTF_OK);
         }
         if (!any) {
             std::unique_lock<std::mutex> lk(sv->mu);
@@ -267,7 +306,8 @@ int ntf_server_create(ntf_server **out, int device, int slots, size_t mem_budget
         if (ntf_ctx_create(&s.ctx, device) != NTF_OK || cudaStreamCreateWithFlags(&s.st, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming) != cudaSuccess ||
             cudaMalloc(&s.F_dev, sizeof(double)) != cudaSuccess ||
-            cudaMallocHost(&s.F_host, sizeof(double)) != cudaSuccess) {
+            cudaMalloc(&s.S_dev, sizeof(JobState)) != cudaSuccess ||
+            cudaMallocHost(&s.S_host, sizeof(JobState)) != cudaSuccess) {
             cudaGetLastError();
             ntf_server_destroy(sv);
             return NTF_ERR_CUDA;
@@ -322,7 +362,8 @@ void ntf_server_destroy(ntf_server *sv) {
         if (s.ev) cudaEventDestroy(s.ev);
         if (s.st) cudaStreamDestroy(s.st);
         if (s.F_dev) cudaFree(s.F_dev);
-        if (s.F_host) cudaFreeHost(s.F_host);
+        if (s.S_dev) cudaFree(s.S_dev);
+        if (s.S_host) cudaFreeHost(s.S_host);
         if (s.ctx) ntf_ctx_destroy(s.ctx);
     }
     delete sv;

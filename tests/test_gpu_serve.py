@@ -88,3 +88,32 @@ def test_server_rejects_bad_jobs_and_empty_poll():
         srv.submit(X, 2.5, A)
     assert srv.poll(wait_all=True) == []
     srv.close()
+
+
+def test_iteration_caps_match_alone():
+    """A job capped at 1 or 2 iterations (no WHILE loop / one loop pass) stops exactly
+    where the alone loop does."""
+    ntf = _ntf()
+    import torch
+    rtol = 1e-12
+    jobs = _jobs(4, seed=9)
+    srv = ntf.Server(slots=2)
+    for cap in (1, 2, 3):
+        alone = [_alone(ntf, j, d, rtol, cap) for j, d in jobs]
+        torch.cuda.synchronize()
+        mixed = {}
+        for q, (j, (X, G, A)) in enumerate(jobs):
+            Xd = dev(X)
+            Ad = [dev(a) for a in A]
+            Gd = dev(G) if G is not None else None
+            mixed[srv.submit(Xd, j["beta"], Ad, core=Gd, rtol=rtol, max_iters=cap)] = (q, Ad, Gd)
+        res = srv.poll(wait_all=True)
+        assert len(res) == len(jobs)
+        for r in res:
+            q, Ad, Gd = mixed[r["id"]]
+            A1, G1, iters, F = alone[q]
+            assert r["status"] == 0 and r["iterations"] == iters == cap, (cap, q, r, iters)
+            assert abs(r["objective"] - F) <= 1e-6 * abs(F)
+            for n in range(3):
+                assert rel_fro(host(Ad[n]), host(A1[n])) <= 1e-6, (cap, q, n)
+    srv.close()

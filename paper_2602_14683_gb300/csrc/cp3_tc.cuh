@@ -391,8 +391,18 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
 #pragma unroll
     for (int r = 0; r < RS; ++r) {
         brec[r] = jv ? __ldg(a.rec[1] + (int64_t)j * RP + r0 + r) : 0.0f;
-        bn[r] = (jv && (M1 || M3)) ? __ldg(a.num[1] + (int64_t)j * RP + r0 + r) : 0.0f;
-        bd[r] = (jv && (M1 || M3) && DEN) ? __ldg(a.den[1] + (int64_t)j * RP + r0 + r) : 0.0f;
+        bn[r] = (jv && M1) ? __ldg(a.num[1] + (int64_t)j * RP + r0 + r) : 0.0f;
+        bd[r] = (jv && M1 && DEN) ? __ldg(a.den[1] + (int64_t)j * RP + r0 + r) : 0.0f;
+    }
+    // KRn^T / KRd^T side (mode 3): epilogue thread t owns rank t % 32 and the eight tile rows
+    // 8 (t / 32) .. 8 (t / 32) + 7, so that a slab's KR tile is one 16-byte store per thread
+    const int kr_r = t & 31, kr_j = 8 * (t >> 5);
+    float bk[8], bkd[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        const bool v = M3 && epi && j0 + kr_j + e < J;
+        bk[e] = v ? __ldg(a.num[1] + (int64_t)(j0 + kr_j + e) * RP + kr_r) : 0.0f;
+        bkd[e] = (v && DEN) ? __ldg(a.den[1] + (int64_t)(j0 + kr_j + e) * RP + kr_r) : 0.0f;
     }
     if (epi) {
         const int kc = k0 + row;
@@ -450,15 +460,19 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
             if (S3) *reinterpret_cast<float4 *>(Rl + swf(row, r0 + 4 * q)) = make_float4(l[0], l[1], l[2], l[3]);
         }
     };
-    auto slab_kr = [&](int i) {  // KRn^T / KRd^T of slab i: rows r0.. r0 + RS - 1, column `row`
-        const float *an = srow + (i & 3) * 96 + 32 + r0, *ad = an + 32;
-        __nv_bfloat16 *kn = KnT + ((i - i0) % NK) * 4096, *kd = KdT + ((i - i0) % NK) * 4096;
-#pragma unroll
-        for (int r = 0; r < RS; ++r) {
-            const int rr = r0 + r;
-            kn[(row >> 6) * 2048 + swh(rr, row & 63)] = __float2bfloat16_rn(an[r] * bn[r]);
-            if (DEN) kd[(row >> 6) * 2048 + swh(rr, row & 63)] = __float2bfloat16_rn(ad[r] * bd[r]);
-        }
+    auto pack8 = [](const float *v, float s) {  // eight BF16 values s * v[e] as one uint4
+        __nv_bfloat162 h0 = __floats2bfloat162_rn(s * v[0], s * v[1]), h1 = __floats2bfloat162_rn(s * v[2], s * v[3]);
+        __nv_bfloat162 h2 = __floats2bfloat162_rn(s * v[4], s * v[5]), h3 = __floats2bfloat162_rn(s * v[6], s * v[7]);
+        uint4 u;
+        u.x = *reinterpret_cast<uint32_t *>(&h0); u.y = *reinterpret_cast<uint32_t *>(&h1);
+        u.z = *reinterpret_cast<uint32_t *>(&h2); u.w = *reinterpret_cast<uint32_t *>(&h3);
+        return u;
+    };
+    auto slab_kr = [&](int i) {  // KRn^T / KRd^T of slab i: row kr_r, columns kr_j .. kr_j + 7
+        const float *an = srow + (i & 3) * 96 + 32;
+        const int off = (kr_j >> 6) * 2048 + swh(kr_r, kr_j & 63);
+        *reinterpret_cast<uint4 *>(KnT + ((i - i0) % NK) * 4096 + off) = pack8(bk, an[kr_r]);
+        if (DEN) *reinterpret_cast<uint4 *>(KdT + ((i - i0) % NK) * 4096 + off) = pack8(bkd, an[32 + kr_r]);
     };
     if (t == EW) {
         for (int q = 0; q < NBAR; ++q) {

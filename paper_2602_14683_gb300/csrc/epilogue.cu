@@ -100,13 +100,21 @@ __global__ void mu_epilogue_kernel(MuEpiArgs e) {
         return;
     }
     const int64_t stride = (int64_t)e.rows * e.RP;
-    float num = 0.0f, den = 0.0f;
-    for (int p = 0; p < e.n_parts; ++p) num += e.pn[p * stride + t];
-    if (e.den_closed) {
-        den = e.den_closed[r];
-    } else {
-        for (int p = 0; p < e.n_parts; ++p) den += e.pd[p * stride + t];
-    }
+    // partial sums added in part order; sixteen loads are issued before their adds
+    auto psum = [&](const float *src) {
+        float acc = 0.0f;
+        for (int p0 = 0; p0 < e.n_parts; p0 += 16) {
+            float v[16];
+#pragma unroll
+            for (int k = 0; k < 16; ++k) v[k] = p0 + k < e.n_parts ? src[(p0 + k) * stride + t] : 0.0f;
+#pragma unroll
+            for (int k = 0; k < 16; ++k)
+                if (p0 + k < e.n_parts) acc += v[k];
+        }
+        return acc;
+    };
+    const float num = psum(e.pn);
+    const float den = e.den_closed ? e.den_closed[r] : psum(e.pd);
     const float ratio = __fdiv_rn(num, den);
     float m;
     if (e.gamma == 1.0f) m = ratio;

@@ -147,12 +147,15 @@ def run_serving(ntf, n_jobs, slots, seed=0, max_iters=200, rtol=1e-6):
                    "Poisson-noised low-rank data at mean 10, J-CoMM L=1, stop at 1e-6 rel change or 200 its"}
 
 
-def run_tucker_c3(ntf, ctx, peaks, iters=10, n=400, J=32, beta=1.5, seed=3):
+def run_tucker_c3(ntf, ctx, peaks, iters=10, n=400, J=32, beta=1.5, seed=3, precisions=("fp32", "tf32", "3xtf32")):
     """Dense Tucker 400 x 400 x 400, core 32 x 32 x 32, beta = 3/2: Gamma(2,1) core and
     factors, model rescaled to mean 10, Poisson noise (drawn on the device, seeded); init
-    U(0.1, 1).  Times block-MM sweeps (core, then modes 1..3) and J-CoMM outer iterations
-    (L = 1), FP32 CUDA-core path.  Roofline: per block of a sweep, one pass over X with
-    2J flops for Xhat and 2J for each of the two contractions (P and Q) per entry."""
+    U(0.1, 1).  For each precision, times block-MM sweeps (core, then modes 1..3) and J-CoMM
+    outer iterations (L = 1), and reports the objective after the timed sweeps relative to
+    the FP32 CUDA-core path's.  Roofline per sweep: four passes over X (4 bytes per entry
+    each; FP32 path: 2J flops for Xhat and 2J for each of the P and Q contractions per
+    entry, against the derived FP32 FMA peak; tensor-core path: the bytes against the HBM
+    copy bandwidth)."""
     import torch
     torch.manual_seed(seed)
     dev = torch.device("cuda", torch.cuda.current_device())
@@ -166,34 +169,49 @@ def run_tucker_c3(ntf, ctx, peaks, iters=10, n=400, J=32, beta=1.5, seed=3):
     G0 = torch.rand((J, J, J), device=dev, generator=g) * 0.9 + 0.1
     A0 = [torch.rand((n, J), device=dev, generator=g) * 0.9 + 0.1 for _ in range(3)]
     obj = torch.zeros(1, dtype=torch.float64, device=dev)
-    out = {"workload": "dense Tucker %dx%dx%d, core %dx%dx%d, beta=%g, FP32 CUDA cores" % (n, n, n, J, J, J, beta)}
-    for name in ("block_mm", "jcomm"):
-        Gc, Ac = G0.clone(), [a.clone() for a in A0]
-
-        def step():
-            if name == "jcomm":
-                ntf.jcomm_outer(X, beta, Ac, core=Gc, objective=obj, ctx=ctx)
-            else:
-                ntf.tucker_mu_sweep(X, beta, Gc, Ac, objective=obj, ctx=ctx)
-        for _ in range(3):
-            step()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(iters):
-            step()
-        e1.record()
-        torch.cuda.synchronize()
-        out[name + "_ms"] = e0.elapsed_time(e1) / max(iters, 1)
     entries = n ** 3
-    # block MM: four blocks, each one pass over X (Xhat 2J, Num and Den contractions 2J each)
-    flops = 4 * entries * 6 * J
-    sec = out["block_mm_ms"] / 1e3
     fp32_peak = torch.cuda.get_device_properties(dev).multi_processor_count * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) / 1e6
-    out["roofline"] = {"bound": "alu", "achieved": flops / sec / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
-                       "frac": flops / sec / 1e12 / fp32_peak, "of": "block-MM sweep, algorithmic FLOPs (4 passes x 6J "
-                       "per entry) over sweep time, against the derived FP32 FMA peak",
-                       "hbm_gbs": 4 * entries * 4 / sec / 1e9}
+    out = {"workload": "dense Tucker %dx%dx%d, core %dx%dx%d, beta=%g" % (n, n, n, J, J, J, beta)}
+    for prec in precisions:
+        res = {}
+        for name in ("block_mm", "jcomm"):
+            Gc, Ac = G0.clone(), [a.clone() for a in A0]
+
+            def step():
+                if name == "jcomm":
+                    ntf.jcomm_outer(X, beta, Ac, core=Gc, objective=obj, ctx=ctx, precision=prec)
+                else:
+                    ntf.tucker_mu_sweep(X, beta, Gc, Ac, objective=obj, ctx=ctx, precision=prec)
+            for _ in range(3):
+                step()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(iters):
+                step()
+            e1.record()
+            torch.cuda.synchronize()
+            res[name + "_ms"] = e0.elapsed_time(e1) / max(iters, 1)
+            res[name + "_objective"] = obj.item()
+        sec = res["block_mm_ms"] / 1e3
+        if prec == "fp32":
+            flops = 4 * entries * 6 * J
+            res["roofline"] = {"bound": "alu", "achieved": flops / sec / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
+                               "frac": flops / sec / 1e12 / fp32_peak,
+                               "of": "block-MM sweep: 4 passes x 6J flops per entry over the sweep time, derived FP32 FMA peak"}
+        else:
+            byt = 4 * entries * 4
+            res["roofline"] = {"bound": "hbm", "achieved": byt / sec / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                               "frac": byt / sec / 1e9 / peaks["hbm_gbs"],
+                               "of": "block-MM sweep: 4 passes x 4 bytes per entry over the sweep time (small GEMMs and "
+                                     "W sums included), measured HBM copy bandwidth"}
+        out[prec] = res
+    if "fp32" in out:
+        for prec in precisions:
+            if prec != "fp32":
+                for name in ("block_mm", "jcomm"):
+                    f0 = out["fp32"][name + "_objective"]
+                    out[prec][name + "_objective_rel_diff_vs_fp32"] = abs(out[prec][name + "_objective"] - f0) / f0
     return out
 
 
@@ -302,7 +320,7 @@ def oracle_step_sample(X, A, cores, budget_s):
     that the sample takes about `budget_s` seconds of CPU time (at most every row, i.e. the
     whole iteration).  Returns (seconds per full step estimate, description)."""
     import oracle
-    probe = 4
+    probe = min(min(DIMS), 2 * cores)  # rows run in parallel: probe with every core busy
     t0 = time.perf_counter()
     for n in range(3):
         oracle.cp_numden_rows(X, A, A, A, n, np.arange(probe, dtype=np.int64), BETA)
@@ -365,7 +383,7 @@ def main():
         import paper_2602_14683_gb300 as ntf
         ctx, peaks = ntf.default_context(), load_peaks()[0]
         if args.profile_case == "tucker":
-            r = run_tucker_c3(ntf, ctx, peaks, iters=0)
+            r = run_tucker_c3(ntf, ctx, peaks, iters=0, precisions=(args.precision,))
         else:
             r = run_coo_c4(ntf, ctx, peaks, iters=0)
         print("profile case", args.profile_case, "done")

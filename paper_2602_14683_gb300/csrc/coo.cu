@@ -207,40 +207,176 @@ __global__ void __launch_bounds__(256) coo_pass_kernel(const CooPassArgs a) {
     if (a.obj && lane == 0) a.obj[u] = (double)objf;
 }
 
-// Num[i][r] = sum of the unit partials of row i (units of a row are consecutive)
-__global__ void coo_row_reduce_kernel(const float *part, const int32_t *row_units, int rows, int RP, float *num) {
-    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (int64_t)rows * RP) return;
-    const int i = (int)(t / RP), r = (int)(t % RP);
-    float s = 0.0f;
-    for (int u = row_units[i]; u < row_units[i + 1]; ++u) s += part[(int64_t)u * RP + r];
-    num[t] = s;
-}
-
-// objective: sum of stored-entry terms (fixed order) + sum_r prod_n colsum(A^(n))_r
-__global__ void coo_obj_finish_kernel(const double *parts, int n, const float *const *F, const int *rows, int N,
-                                      int R, int RP, double *out) {
-    __shared__ double sh[32];
-    double s = 0.0;
-    for (int t = threadIdx.x; t < n; t += blockDim.x) s += parts[t];
-    // dense part: each of the first R threads handles one rank column
-    if (threadIdx.x < R) {
-        double prod = 1.0;
-        for (int m = 0; m < N; ++m) {
-            double c = 0.0;
-            for (int i = 0; i < rows[m]; ++i) c += (double)F[m][(int64_t)i * RP + threadIdx.x];
-            prod *= c;
+// Rank 32: one warp per unit; eight lanes per stored entry, four entries of the unit at a
+// time (lane group g = lane / 8 takes entries g, g + 4, ...), lane l holding ranks
+// 4 (l % 8) .. 4 (l % 8) + 3.  Each factor row other than mode n's is then one 128-byte
+// gather per entry (eight 16-byte loads that share a line), the unit's own mode-n row is
+// read once, Xhat = sum_r z[r] A^(n)[i_n, r] is a three-step shuffle within the group,
+// p = x / max(Xhat, eps) and the lane adds p z[r] for its ranks.  At the end of the unit
+// the four groups are added (two shuffle steps, a fixed order).  The reconstruction and
+// the numerator use the same factors (beta = 1: block MM, and J-CoMM at the reference).
+template <int NMAX>  // order N <= NMAX
+__global__ void __launch_bounds__(256) coo_pass32_kernel(const CooPassArgs a) {
+    const int lane = threadIdx.x & 31, grp = lane >> 3, sub = lane & 7;
+    const int u = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (u >= a.n_units) return;  // warp-uniform
+    const int beg = a.unit_beg[u], end = a.unit_end[u];
+    const int64_t in = (int64_t)__ldg(a.sidx + (int64_t)a.n * a.nnz + beg) * 32;
+    const float4 an = __ldg(reinterpret_cast<const float4 *>(a.rec[a.n] + in) + sub);
+    float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    float objf = 0.0f;
+    // coordinates and value of this group's entry in the next round, loaded one round ahead
+    int nid[NMAX];
+    float nx = 0.0f;
+    auto load_round = [&](int t0) {
+        const int t = t0 + grp;
+        const bool v = t < end;
+#pragma unroll
+        for (int m = 0; m < NMAX; ++m) nid[m] = (v && m < a.N && m != a.n) ? __ldg(a.sidx + (int64_t)m * a.nnz + t) : 0;
+        nx = v ? __ldg(a.sval + t) : 0.0f;
+    };
+    load_round(beg);
+    for (int t0 = beg; t0 < end; t0 += 4) {
+        const bool v = t0 + grp < end;
+        int id[NMAX];
+#pragma unroll
+        for (int m = 0; m < NMAX; ++m) id[m] = nid[m];
+        const float x = nx;
+        if (t0 + 4 < end) load_round(t0 + 4);
+        float4 z = make_float4(1.0f, 1.0f, 1.0f, 1.0f);
+#pragma unroll
+        for (int m = 0; m < NMAX; ++m) {
+            if (m >= a.N || m == a.n) continue;
+            const float4 f = __ldg(reinterpret_cast<const float4 *>(a.rec[m] + (int64_t)id[m] * 32) + sub);
+            z.x *= f.x; z.y *= f.y; z.z *= f.z; z.w *= f.w;
         }
-        s += prod;
+        float s = fmaf(z.x, an.x, fmaf(z.y, an.y, fmaf(z.z, an.z, z.w * an.w)));
+        s += __shfl_xor_sync(0xffffffffu, s, 1);
+        s += __shfl_xor_sync(0xffffffffu, s, 2);
+        s += __shfl_xor_sync(0xffffffffu, s, 4);
+        const float y = fmaxf(s, a.eps);
+        const float p = v ? __fdiv_rn(x, y) : 0.0f;
+        acc.x = fmaf(p, z.x, acc.x); acc.y = fmaf(p, z.y, acc.y);
+        acc.z = fmaf(p, z.z, acc.z); acc.w = fmaf(p, z.w, acc.w);
+        if (a.obj && v && sub == 0 && x > 0.0f) {
+            // x log(x / y) - x, the stored-entry part of d_1 (the + y part is summed in closed form)
+            const float rr = __fdiv_rn(y, x);
+            float d;
+            if (rr > 1e-4f && rr < 1e4f) {
+                const float tt = rr - 1.0f;
+                d = x * (tt - log1pf(tt)) - y;
+            } else {
+                d = x * (logf(x) - logf(y)) - x;
+            }
+            objf += d;
+        }
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    for (int k = 8; k <= 16; k <<= 1) {
+        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, k);
+        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, k);
+        acc.z += __shfl_xor_sync(0xffffffffu, acc.z, k);
+        acc.w += __shfl_xor_sync(0xffffffffu, acc.w, k);
+    }
+    if (lane < 8) reinterpret_cast<float4 *>(a.part + (int64_t)u * 32)[sub] = acc;
+    if (a.obj) {
+        double o = (double)objf;
+#pragma unroll
+        for (int k = 16; k >= 1; k >>= 1) o += __shfl_xor_sync(0xffffffffu, o, k);
+        if (lane == 0) a.obj[u] = o;
+    }
+}
+
+// Num[i][r] = sum of the unit partials of row i (units of a row are consecutive), in two
+// fixed-order levels: groups of up to GROUP consecutive units of one row, then the groups of
+// a row.  Loads are issued sixteen at a time before their adds.
+constexpr int GROUP = 32;
+
+template <typename T>
+__device__ __forceinline__ T ordered_sum16(const T *src, int64_t stride, int n) {
+    T acc = 0;
+    for (int p0 = 0; p0 < n; p0 += 16) {
+        T v[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) v[k] = p0 + k < n ? src[(int64_t)(p0 + k) * stride] : T(0);
+#pragma unroll
+        for (int k = 0; k < 16; ++k)
+            if (p0 + k < n) acc += v[k];
+    }
+    return acc;
+}
+
+__global__ void coo_group_reduce_kernel(const float *part, const int32_t *group_beg, int n_groups, int RP, float *gpart) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)n_groups * RP) return;
+    const int g = (int)(t / RP), r = (int)(t % RP);
+    const int b = group_beg[g];
+    gpart[t] = ordered_sum16(part + (int64_t)b * RP + r, RP, group_beg[g + 1] - b);
+}
+
+__global__ void coo_row_reduce_kernel(const float *gpart, const int32_t *row_groups, int rows, int RP, float *num) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)rows * RP) return;
+    const int i = (int)(t / RP), r = (int)(t % RP);
+    const int g = row_groups[i];
+    num[t] = ordered_sum16(gpart + (int64_t)g * RP + r, RP, row_groups[i + 1] - g);
+}
+
+// objective: sum of stored-entry terms + sum_r prod_n colsum(A^(n))_r (Section 6.3), one
+// CTA of 1024 threads in a fixed order: thread (s, r) sums the rows i = s mod 32 of rank r
+// for each factor, the 32 slices are added in order, and the products over ranks r < R
+// are added in rank order after the stored-entry partials.
+__global__ void __launch_bounds__(1024) coo_obj_finish_kernel(const double *parts, int n, const float *const *F,
+                                                              const int *rows, int N, int R, int RP, double *out) {
+    __shared__ double sh[1024];
+    __shared__ double prod[64];
+    const int t = threadIdx.x, r = t % 32, sl = t / 32;
+    // stored-entry partials
+    double s = 0.0;
+    for (int k0 = t; k0 < n; k0 += 8 * 1024) {
+        double v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] = k0 + 1024 * k < n ? parts[k0 + 1024 * k] : 0.0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) s += v[k];
+    }
+    sh[t] = s;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
-        *out = t;
+    for (int w = 512; w >= 1; w >>= 1) {
+        if (t < w) sh[t] += sh[t + w];
+        __syncthreads();
+    }
+    const double stored = sh[0];
+    __syncthreads();
+    // dense part, 32 ranks at a time
+    for (int rb = 0; rb < RP; rb += 32) {
+        double pr = 1.0;
+        for (int m = 0; m < N; ++m) {
+            double c = 0.0;
+            const float *f = F[m] + rb + r;
+            for (int i0 = sl; i0 < rows[m]; i0 += 8 * 32) {
+                float v[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) v[k] = i0 + 32 * k < rows[m] ? f[(int64_t)(i0 + 32 * k) * RP] : 0.0f;
+#pragma unroll
+                for (int k = 0; k < 8; ++k) c += (double)v[k];
+            }
+            sh[t] = c;
+            __syncthreads();
+            if (sl == 0) {
+                double cs = 0.0;
+                for (int q = 0; q < 32; ++q) cs += sh[q * 32 + r];
+                pr *= cs;
+            }
+            __syncthreads();
+        }
+        if (sl == 0) prod[rb + r] = pr;
+    }
+    __syncthreads();
+    if (t == 0) {
+        double tot = stored;
+        for (int q = 0; q < R; ++q) tot += prod[q];
+        *out = tot;
     }
 }
 
@@ -249,8 +385,9 @@ namespace {
 
 struct ModeData {
     int32_t *perm = nullptr, *sidx = nullptr, *unit_beg = nullptr, *unit_end = nullptr, *row_units = nullptr;
+    int32_t *group_beg = nullptr, *row_groups = nullptr;  // unit groups of one row, GROUP units at most
     float *sval = nullptr;
-    int n_units = 0;
+    int n_units = 0, n_groups = 0;
 };
 
 struct CooCache {
@@ -261,7 +398,7 @@ struct CooCache {
     const void *idx[8] = {nullptr};
     const void *vals = nullptr;
     ModeData md[8];
-    int max_units = 0;
+    int max_units = 0, max_groups = 0;
 };
 
 std::mutex g_mu;
@@ -330,12 +467,26 @@ int build_cache(ntf_ctx *ctx, const ntf_tensor *X, CooCache &c, cudaStream_t st)
             }
         }
         ru[X->dims[n]] = (int32_t)ub.size();
+        std::vector<int32_t> gb, rg(ru.size());
+        for (int64_t i = 0; i < X->dims[n]; ++i) {
+            rg[i] = (int32_t)gb.size();
+            for (int u = ru[i]; u < ru[i + 1]; u += GROUP) gb.push_back(u);
+        }
+        rg[X->dims[n]] = (int32_t)gb.size();
+        gb.push_back((int32_t)ub.size());
+        d.n_groups = (int)gb.size() - 1;
+        c.max_groups = d.n_groups > c.max_groups ? d.n_groups : c.max_groups;
         d.n_units = (int)ub.size();
         c.max_units = d.n_units > c.max_units ? d.n_units : c.max_units;
         d.unit_beg = (int32_t *)ctx_ws(ctx, ("cooUb" + tag).c_str(), sizeof(int32_t) * (ub.size() + 1));
         d.unit_end = (int32_t *)ctx_ws(ctx, ("cooUe" + tag).c_str(), sizeof(int32_t) * (ub.size() + 1));
         d.row_units = (int32_t *)ctx_ws(ctx, ("cooRu" + tag).c_str(), sizeof(int32_t) * ru.size());
-        if (!d.unit_beg || !d.unit_end || !d.row_units) return ctx_fail(ctx, NTF_ERR_OOM, "COO workspace allocation failed");
+        d.group_beg = (int32_t *)ctx_ws(ctx, ("cooGb" + tag).c_str(), sizeof(int32_t) * gb.size());
+        d.row_groups = (int32_t *)ctx_ws(ctx, ("cooRg" + tag).c_str(), sizeof(int32_t) * rg.size());
+        if (!d.unit_beg || !d.unit_end || !d.row_units || !d.group_beg || !d.row_groups)
+            return ctx_fail(ctx, NTF_ERR_OOM, "COO workspace allocation failed");
+        CK(cudaMemcpyAsync(d.group_beg, gb.data(), sizeof(int32_t) * gb.size(), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(d.row_groups, rg.data(), sizeof(int32_t) * rg.size(), cudaMemcpyHostToDevice, st));
         if (!ub.empty()) {
             CK(cudaMemcpyAsync(d.unit_beg, ub.data(), sizeof(int32_t) * ub.size(), cudaMemcpyHostToDevice, st));
             CK(cudaMemcpyAsync(d.unit_end, ue.data(), sizeof(int32_t) * ue.size(), cudaMemcpyHostToDevice, st));
@@ -379,10 +530,28 @@ int launch_coo_pass(ntf_ctx *ctx, const CooCache &c, int n, int RP, const float 
     a.part = part;
     a.obj = obj;
     const unsigned grid = (unsigned)((d.n_units + 7) / 8);
-    if (RP == 32) coo_pass_kernel<1><<<grid, 256, 0, st>>>(a);
+    bool same = true;  // the rank-32 kernel reads one set of factors for both roles
+    for (int m = 0; m < c.N; ++m) same = same && rec[m] == num[m];
+    if (RP == 32 && same && c.N <= 4) coo_pass32_kernel<4><<<grid, 256, 0, st>>>(a);
+    else if (RP == 32 && same) coo_pass32_kernel<8><<<grid, 256, 0, st>>>(a);
+    else if (RP == 32) coo_pass_kernel<1><<<grid, 256, 0, st>>>(a);
     else coo_pass_kernel<2><<<grid, 256, 0, st>>>(a);
     CK(cudaGetLastError());
     ctx_count(ctx, 1);
+    return NTF_OK;
+}
+
+// Num^(n) rows from the unit partials: group sums, then row sums (both in a fixed order)
+int row_sums(ntf_ctx *ctx, const CooCache &c, int n, int RP, const float *part, float *gpart, float *out,
+             cudaStream_t st) {
+    const ModeData &d = c.md[n];
+    if (d.n_groups > 0) {
+        coo_group_reduce_kernel<<<nb((int64_t)d.n_groups * RP), 256, 0, st>>>(part, d.group_beg, d.n_groups, RP, gpart);
+        CK(cudaGetLastError());
+    }
+    coo_row_reduce_kernel<<<nb(c.dims[n] * RP), 256, 0, st>>>(gpart, d.row_groups, (int)c.dims[n], RP, out);
+    CK(cudaGetLastError());
+    ctx_count(ctx, d.n_groups > 0 ? 2 : 1);
     return NTF_OK;
 }
 
@@ -406,7 +575,9 @@ int coo_kl_sweep(ntf_ctx *ctx, const ntf_tensor *X, int R, float *const *factors
         ctx_count(ctx, jcomm ? 2 : 1);
     }
     float *part = (float *)ctx_ws(ctx, "cooPart", sizeof(float) * (size_t)(c->max_units + 1) * RP);
+    float *gpart = (float *)ctx_ws(ctx, "cooGpart", sizeof(float) * (size_t)(c->max_groups + 1) * RP);
     double *objp = (double *)ctx_ws(ctx, "cooObjP", sizeof(double) * (size_t)(c->max_units + 1));
+    if (!gpart) return ctx_fail(ctx, NTF_ERR_OOM, "COO workspace allocation failed");
     int64_t maxdim = 1;
     for (int m = 0; m < N; ++m) maxdim = X->dims[m] > maxdim ? X->dims[m] : maxdim;
     float *num = (float *)ctx_ws(ctx, "cooNum", sizeof(float) * (size_t)maxdim * RP);
@@ -432,13 +603,12 @@ int coo_kl_sweep(ntf_ctx *ctx, const ntf_tensor *X, int R, float *const *factors
                 int rows[8];
                 for (int m = 0; m < N; ++m) rows[m] = (int)X->dims[m];
                 CK(cudaMemcpyAsync(frows, rows, sizeof(int) * N, cudaMemcpyHostToDevice, st));
-                coo_obj_finish_kernel<<<1, 256, 0, st>>>(objp, c->md[0].n_units, fptr, frows, N, R, RP, objective_dev);
+                coo_obj_finish_kernel<<<1, 1024, 0, st>>>(objp, c->md[0].n_units, fptr, frows, N, R, RP, objective_dev);
                 CK(cudaGetLastError());
                 ctx_count(ctx, 1);
             }
-            coo_row_reduce_kernel<<<nb(X->dims[n] * RP), 256, 0, st>>>(part, c->md[n].row_units, (int)X->dims[n], RP, buf);
-            CK(cudaGetLastError());
-            ctx_count(ctx, 1);
+            rc = row_sums(ctx, *c, n, RP, part, gpart, buf, st);
+            if (rc) return rc;
             jnum.push_back(buf);
         }
     }
@@ -456,13 +626,12 @@ int coo_kl_sweep(ntf_ctx *ctx, const ntf_tensor *X, int R, float *const *factors
                     int rows[8];
                     for (int m = 0; m < N; ++m) rows[m] = (int)X->dims[m];
                     CK(cudaMemcpyAsync(frows, rows, sizeof(int) * N, cudaMemcpyHostToDevice, st));
-                    coo_obj_finish_kernel<<<1, 256, 0, st>>>(objp, c->md[0].n_units, fptr, frows, N, R, RP, objective_dev);
+                    coo_obj_finish_kernel<<<1, 1024, 0, st>>>(objp, c->md[0].n_units, fptr, frows, N, R, RP, objective_dev);
                     CK(cudaGetLastError());
                     ctx_count(ctx, 1);
                 }
-                coo_row_reduce_kernel<<<nb(X->dims[n] * RP), 256, 0, st>>>(part, c->md[n].row_units, (int)X->dims[n], RP, num);
-                CK(cudaGetLastError());
-                ctx_count(ctx, 1);
+                rc = row_sums(ctx, *c, n, RP, part, gpart, num, st);
+                if (rc) return rc;
                 nrows = num;
             }
             // Den^(n)_{i r} = prod_{m != n} colsum(A^(m))_r (current blocks; chi2(Z, Zt) = Z)
@@ -521,7 +690,7 @@ int coo_kl_objective(ntf_ctx *ctx, const ntf_tensor *X, int R, const float *cons
     int rows[8];
     for (int m = 0; m < N; ++m) rows[m] = (int)X->dims[m];
     CK(cudaMemcpyAsync(frows, rows, sizeof(int) * N, cudaMemcpyHostToDevice, st));
-    coo_obj_finish_kernel<<<1, 256, 0, st>>>(objp, c->md[0].n_units, fptr, frows, N, R, RP, out_dev);
+    coo_obj_finish_kernel<<<1, 1024, 0, st>>>(objp, c->md[0].n_units, fptr, frows, N, R, RP, out_dev);
     CK(cudaGetLastError());
     ctx_count(ctx, 1);
     return NTF_OK;

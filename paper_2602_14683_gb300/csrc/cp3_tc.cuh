@@ -31,6 +31,13 @@
 // a wait that runs out raises a shared abort flag that ends the other waits at once; the
 // kernel then sets the context's status word, waits (bounded) for its copies and MMAs,
 // frees its TMEM and returns.
+//
+// With RX (explicit rows: the Tucker passes of Appendix C), the GEMM1 rows of slab i are
+// rrow[i*J + j] (the mode-3 partial tensor B^(3) of eq. (block_Bn)) instead of A_i (.) B_j,
+// the column contraction's operand is nrow[i*J + j] (and drow) instead of A_i (.) B_j, and
+// the rows contraction W[j][r] of each slab is written out ([column block][I*J][RP]
+// partials, summed over the column blocks afterwards) instead of being folded into modes
+// 1 and 2.  Row values are loaded from global memory two chunks before they are staged.
 #pragma once
 
 #include <cuda.h>
@@ -317,7 +324,7 @@ __device__ __forceinline__ float reduce_scatter(float v[N]) {
     return s;
 }
 
-template <int MS, int BK, bool S3>
+template <int MS, int BK, bool S3, bool RX>
 __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUtensorMap xmap, const Cp3Args a) {
     constexpr bool DEN = BK != BK_KL;
     constexpr bool M1 = (MS & PM_M1) != 0, M2 = (MS & PM_M2) != 0, M3 = (MS & PM_M3) != 0;
@@ -390,9 +397,9 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
     float brec[RS], bn[RS], bd[RS];
 #pragma unroll
     for (int r = 0; r < RS; ++r) {
-        brec[r] = jv ? __ldg(a.rec[1] + (int64_t)j * RP + r0 + r) : 0.0f;
-        bn[r] = (jv && M1) ? __ldg(a.num[1] + (int64_t)j * RP + r0 + r) : 0.0f;
-        bd[r] = (jv && M1 && DEN) ? __ldg(a.den[1] + (int64_t)j * RP + r0 + r) : 0.0f;
+        brec[r] = (jv && !RX) ? __ldg(a.rec[1] + (int64_t)j * RP + r0 + r) : 0.0f;
+        bn[r] = (jv && M1 && !RX) ? __ldg(a.num[1] + (int64_t)j * RP + r0 + r) : 0.0f;
+        bd[r] = (jv && M1 && DEN && !RX) ? __ldg(a.den[1] + (int64_t)j * RP + r0 + r) : 0.0f;
     }
     // KRn^T / KRd^T side (mode 3): epilogue thread t owns rank t % 32 and the eight tile rows
     // 8 (t / 32) .. 8 (t / 32) + 7, so that a slab's KR tile is one 16-byte store per thread
@@ -400,7 +407,7 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
     float bk[8], bkd[8];
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
-        const bool v = M3 && epi && j0 + kr_j + e < J;
+        const bool v = M3 && !RX && epi && j0 + kr_j + e < J;
         bk[e] = v ? __ldg(a.num[1] + (int64_t)(j0 + kr_j + e) * RP + kr_r) : 0.0f;
         bkd[e] = (v && DEN) ? __ldg(a.den[1] + (int64_t)(j0 + kr_j + e) * RP + kr_r) : 0.0f;
     }
@@ -443,7 +450,26 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
         return (f == 2 && !DEN) ? 0.0f : __ldg(src + (int64_t)i * RP + r);
     };
     auto stage_rows = [&](int i) {
-        if (t < 96) srow[(i & 3) * 96 + t] = row_val(i);
+        if (t < 96 && !RX) srow[(i & 3) * 96 + t] = row_val(i);
+    };
+    // RX: this thread's entries of the next slabs' explicit rows, loaded ahead
+    float rx[RS], kx[8], kxd[8];
+    auto rx_load = [&](int i) {  // GEMM1 rows of slab i: row `row`, rank slice r0
+#pragma unroll
+        for (int q = 0; q < RS / 4; ++q) {
+            const float4 v = jv ? __ldg(reinterpret_cast<const float4 *>(a.rrow + ((int64_t)i * J + j) * RP + r0) + q)
+                                : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            rx[4 * q] = v.x; rx[4 * q + 1] = v.y; rx[4 * q + 2] = v.z; rx[4 * q + 3] = v.w;
+        }
+    };
+    auto kx_load = [&](int i) {  // column-contraction rows of slab i: rank kr_r, rows kr_j ..
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const bool v = epi && j0 + kr_j + e < J;
+            const int64_t o = ((int64_t)i * J + j0 + kr_j + e) * RP + kr_r;
+            kx[e] = v ? __ldg(a.nrow + o) : 0.0f;
+            kxd[e] = (v && DEN) ? __ldg(a.drow + o) : 0.0f;
+        }
     };
     auto slab_rows = [&](int i) {  // R (hi/lo) of slab i: row `row`, rank slice r0
         const float *ar = srow + (i & 3) * 96 + r0;
@@ -452,7 +478,7 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
             float h[4], l[4];
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-                const float v = ar[4 * q + e] * brec[4 * q + e];
+                const float v = RX ? rx[4 * q + e] : ar[4 * q + e] * brec[4 * q + e];
                 h[e] = tf32_rna(v);
                 l[e] = S3 ? tf32_rna(v - h[e]) : 0.0f;
             }
@@ -471,8 +497,9 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
     auto slab_kr = [&](int i) {  // KRn^T / KRd^T of slab i: row kr_r, columns kr_j .. kr_j + 7
         const float *an = srow + (i & 3) * 96 + 32;
         const int off = (kr_j >> 6) * 2048 + swh(kr_r, kr_j & 63);
-        *reinterpret_cast<uint4 *>(KnT + ((i - i0) % NK) * 4096 + off) = pack8(bk, an[kr_r]);
-        if (DEN) *reinterpret_cast<uint4 *>(KdT + ((i - i0) % NK) * 4096 + off) = pack8(bkd, an[32 + kr_r]);
+        *reinterpret_cast<uint4 *>(KnT + ((i - i0) % NK) * 4096 + off) = RX ? pack8(kx, 1.0f) : pack8(bk, an[kr_r]);
+        if (DEN)
+            *reinterpret_cast<uint4 *>(KdT + ((i - i0) % NK) * 4096 + off) = RX ? pack8(kxd, 1.0f) : pack8(bkd, an[32 + kr_r]);
     };
     if (t == EW) {
         for (int q = 0; q < NBAR; ++q) {
@@ -485,15 +512,21 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
     float rnext = 0.0f;  // slab i0 + 3's staged-row entry (threads t < 96)
     if (NC > 0) {
         for (int i = i0; i < i0 + 3 && i < i1; ++i) stage_rows(i);
-        if (t < 96 && i0 + 3 < i1) rnext = row_val(i0 + 3);
+        if (t < 96 && i0 + 3 < i1 && !RX) rnext = row_val(i0 + 3);
     }
     __syncthreads();
     if (issuer) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;\n" :: "r"(su32(tslot)));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
     } else if (epi && NC > 0) {
+        if (RX) rx_load(i0);
         slab_rows(i0);
-        if (M3) slab_kr(i0);
+        if (RX && i0 + 1 < i1) rx_load(i0 + 1);
+        if (M3) {
+            if (RX) kx_load(i0);
+            slab_kr(i0);
+            if (RX && i0 + 1 < i1) kx_load(i0 + 1);
+        }
     }
     fence_async_smem();
     fence_before();
@@ -611,6 +644,19 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
                 tmem_ld<RS>(t_w + wb + lane_off + r0, w);
                 if (DEN) tmem_ld<RS>(t_wd + wb + lane_off + r0, wd);
             }
+            if (RX) {  // W rows of slab i for this column block: [kb][i * J + j][RP] partials
+                if (jv && !*abort_flag) {
+                    const int64_t o = (((int64_t)kb * a.I + i) * J + j) * RP + r0;
+#pragma unroll
+                    for (int q = 0; q < RS / 4; ++q) {
+                        reinterpret_cast<float4 *>(a.p1n + o)[q] = make_float4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+                        if (DEN)
+                            reinterpret_cast<float4 *>(a.p1d + o)[q] =
+                                make_float4(wd[4 * q], wd[4 * q + 1], wd[4 * q + 2], wd[4 * q + 3]);
+                    }
+                }
+                return;
+            }
             if (M2) {
                 const float *an = srow + (i & 3) * 96 + 32 + r0, *ad = an + 32;
 #pragma unroll
@@ -657,10 +703,13 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
                 fence_after();
                 epi_sync();  // rows of slab i + 1 (stored at the previous boundary) visible
                 if (t < 96 && i + 2 < i1) {
-                    srow[((i + 2) & 3) * 96 + t] = rnext;
-                    if (i + 3 < i1) rnext = row_val(i + 3);
+                    if (!RX) srow[((i + 2) & 3) * 96 + t] = rnext;
+                    if (i + 3 < i1 && !RX) rnext = row_val(i + 3);
                 }
-                if (M3) slab_kr(i);
+                if (M3) {
+                    slab_kr(i);
+                    if (RX && i + 1 < i1) kx_load(i + 1);
+                }
             }
             if (RW && q == 1 && n >= 3) {
                 // fold slab i - 1: its last contraction (chunk n - 2) is complete, as the
@@ -698,6 +747,7 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
                 // this chunk's GEMM1 is complete, so R can take slab i + 1 (needed by GEMM1 of
                 // the next chunk, which the issuer starts once every warp has arrived)
                 slab_rows(i + 1);
+                if (RX && i + 2 < i1) rx_load(i + 2);
                 fence_async_smem();
                 arrive(r_full);
             }
@@ -777,7 +827,7 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
         }
         // ---- CTA outputs ------------------------------------------------------------------
         const bool good = !__any_sync(0xffffffffu, *abort_flag != 0);
-        if (M2 && jv) {
+        if (M2 && jv && !RX) {
             const int64_t base = ((int64_t)(kb * a.n_is + is) * J + j) * RP + r0;
 #pragma unroll
             for (int r = 0; r < RS; ++r) {
@@ -844,13 +894,13 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
 
 cudaError_t launch_x_map(const Cp3Args &a, CUtensorMap *map);
 
-template <int MS, int BK, bool S3>
+template <int MS, int BK, bool S3, bool RX>
 cudaError_t launch_t(const Cp3Plan &p, const Cp3Args &a, cudaStream_t s) {
     constexpr Layout L = make_layout((MS & (PM_M1 | PM_M2)) != 0, (MS & PM_M3) != 0, BK != BK_KL, S3);
     CUtensorMap map;
     cudaError_t e = launch_x_map(a, &map);
     if (e != cudaSuccess) return e;
-    auto k = cp3_pass_tc<MS, BK, S3>;
+    auto k = cp3_pass_tc<MS, BK, S3, RX>;
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total);
     if (e != cudaSuccess) return e;
     k<<<p.grid, NT, L.total, s>>>(map, a);
@@ -859,13 +909,25 @@ cudaError_t launch_t(const Cp3Plan &p, const Cp3Args &a, cudaStream_t s) {
 
 template <int BK, bool S3>
 cudaError_t launch_bk(const Cp3Plan &p, const Cp3Args &a, int ms, cudaStream_t s) {
+    if (a.rrow) {  // explicit rows (Tucker): W rows out, or the column contraction
+        if constexpr (BK == BK_KL) {
+            return cudaErrorInvalidValue;
+        } else {
+            switch (ms) {
+                case PM_M1 | PM_M2: return launch_t<PM_M1 | PM_M2, BK, S3, true>(p, a, s);
+                case PM_M1 | PM_M2 | PM_OBJ: return launch_t<PM_M1 | PM_M2 | PM_OBJ, BK, S3, true>(p, a, s);
+                case PM_M3: return launch_t<PM_M3, BK, S3, true>(p, a, s);
+                default: return cudaErrorInvalidValue;
+            }
+        }
+    }
     switch (ms) {
-        case PM_M1: return launch_t<PM_M1, BK, S3>(p, a, s);
-        case PM_M1 | PM_OBJ: return launch_t<PM_M1 | PM_OBJ, BK, S3>(p, a, s);
-        case PM_M2: return launch_t<PM_M2, BK, S3>(p, a, s);
-        case PM_M3: return launch_t<PM_M3, BK, S3>(p, a, s);
+        case PM_M1: return launch_t<PM_M1, BK, S3, false>(p, a, s);
+        case PM_M1 | PM_OBJ: return launch_t<PM_M1 | PM_OBJ, BK, S3, false>(p, a, s);
+        case PM_M2: return launch_t<PM_M2, BK, S3, false>(p, a, s);
+        case PM_M3: return launch_t<PM_M3, BK, S3, false>(p, a, s);
         case PM_M1 | PM_M2 | PM_M3 | PM_OBJ:
-            if (BK == BK_KL) return launch_t<PM_M1 | PM_M2 | PM_M3 | PM_OBJ, BK_KL, S3>(p, a, s);
+            if (BK == BK_KL) return launch_t<PM_M1 | PM_M2 | PM_M3 | PM_OBJ, BK_KL, S3, false>(p, a, s);
             return cudaErrorInvalidValue;
         default: return cudaErrorInvalidValue;
     }

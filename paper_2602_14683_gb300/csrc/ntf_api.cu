@@ -558,4 +558,5 @@ void *ctx_ws(ntf_ctx *c, const char *name, size_t bytes) { return ws_get(c, name
 int ctx_fail(ntf_ctx *c, int code, const char *msg) { return fail(c, code, "%s", msg); }
 void ctx_count(ntf_ctx *c, int n) { c->launches += n; }
 int ctx_num_sms(const ntf_ctx *c) { return c->num_sms; }
+int *ctx_status(ntf_ctx *c) { return c->status; }
 }  // namespace ntf

@@ -60,7 +60,8 @@ __device__ __forceinline__ void pq_powers(int bk, float beta, float x, float y, 
 }
 
 // d_beta(x|y) (Section 3.2) in FP32.  Near x = y the terms of the definition cancel,
-// so there the divergence is written through log1p/expm1 of the ratio:
+// so there the divergence is written through exact factorisations (beta = 1/2, 3/2, see
+// below) or through log1p/expm1 of the ratio:
 //   KL : x (t - log1p t),  t = y/x - 1
 //   IS : s - log1p s,      s = x/y - 1
 //   else: x^b ((b-1) expm1(b L) - b expm1((b-1) L)) / (b (b-1)),  L = log1p(y/x - 1)
@@ -76,6 +77,13 @@ __device__ __forceinline__ float dbeta_stable(int bk, float beta, float x, float
         return u - (logf(x) - logf(y)) - 1.0f;
     }
     if (!(x > 0.0f)) return bk == BK_KL ? y : powf(y, beta) / beta;
+    if (bk == BK_THREEHALF || bk == BK_HALF) {
+        // exact factorisations in t = sqrt(y / x), free of cancellation:
+        //   beta = 3/2: d = (2/3) x^(3/2) (t - 1)^2 (t + 2);   beta = 1/2: d = 2 x^(1/2) (t - 1)^2 / t
+        const float t = sqrtf(__fdiv_rn(y, x)), sx = sqrtf(x), e = t - 1.0f;
+        if (bk == BK_THREEHALF) return (2.0f / 3.0f) * x * sx * e * e * (t + 2.0f);
+        return 2.0f * sx * e * __fdiv_rn(e, t);
+    }
     const float r = __fdiv_rn(y, x);
     const bool near = r > 1e-4f && r < 1e4f;
     if (bk == BK_KL) {
@@ -152,7 +160,9 @@ cudaError_t cp3_launch(const Cp3Plan &plan, const Cp3Args &a, int mode_set, int 
 // GEMM, BF16 contraction GEMMs, FP32 accumulation; same partial-sum layouts.
 // Eligible when RP == 32, K % 4 == 0 and X is 16-byte aligned.
 bool cp3_tc_eligible(int RP, int K, const float *X);
-bool cp3_tc_supported(int mode_set, int den);
+// rx: explicit rows (Tucker): modes M1 | M2 (W rows out, optionally with the objective) or
+// M3, and only with the denominator side (beta != 1).
+bool cp3_tc_supported(int mode_set, int den, bool rx = false);
 cudaError_t cp3_tc_launch(const Cp3Plan &plan, const Cp3Args &a, int mode_set, int den,
                           cudaStream_t s);
 

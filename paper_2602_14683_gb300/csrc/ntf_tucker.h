@@ -8,6 +8,7 @@ void *ctx_ws(ntf_ctx *c, const char *name, size_t bytes);
 int ctx_fail(ntf_ctx *c, int code, const char *msg);
 void ctx_count(ntf_ctx *c, int n);
 int ctx_num_sms(const ntf_ctx *c);
+int *ctx_status(ntf_ctx *c);  // device status word of the bounded-wait kernels
 
 int tucker_run(ntf_ctx *ctx, const ntf_tensor *X, float beta, const int64_t *core_dims, float *core,
                float *const *factors, const ntf_opts &o, double *objective_dev, cudaStream_t st, bool jcomm);

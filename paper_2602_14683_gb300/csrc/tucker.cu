@@ -355,6 +355,22 @@ static cudaError_t rows_launch(int RP, const RowsArgs &ra, int grid, bool obj, c
 // ----------------------------------------------------------------------------------
 // small elementwise kernels
 // ----------------------------------------------------------------------------------
+// out[t] = sum over the parts of parts[p][t], in part order (loads issued eight at a time)
+__global__ void sum_parts_kernel(const float *parts, int n_parts, int64_t n, float *out) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    float acc = 0.0f;
+    for (int p0 = 0; p0 < n_parts; p0 += 8) {
+        float v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] = p0 + k < n_parts ? parts[(int64_t)(p0 + k) * n + t] : 0.0f;
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            if (p0 + k < n_parts) acc += v[k];
+    }
+    out[t] = acc;
+}
+
 __global__ void mu_plain_kernel(const float *pre, const float *num, const float *den, int64_t n, float gamma,
                                 float eps, float *out) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -407,6 +423,12 @@ struct TuckerWs {
     double *obj;
     Cp3Plan plan3;
     int rows_grid, rows_is;
+    // tensor-core passes (TF32 / 3xTF32 reconstruction, BF16 contractions): plan, W partials
+    // per 128-column block [n_kb][I1*I2][RP], and the partial counts of the passes in use
+    bool tc;
+    Cp3Plan tplan;
+    float *Wpn, *Wpd;
+    int parts3, obj_n;
     Blocks cur, ref, t1, t2;  // current, reference, chi1 and chi2 transforms
 };
 
@@ -459,6 +481,27 @@ Cp3Args base_args(const ntf_tensor *X, const TuckerWs &w, const ntf_opts &o, flo
 // W (and Wd) from P, Q with third-factor columns n3 / d3; Xhat from rrow, A3rec.
 int rows_pass(ntf_ctx *ctx, TuckerWs &w, const ntf_tensor *X, const ntf_opts &o, float beta, const float *rrow,
               const float *a3rec, const float *n3, const float *d3, bool obj, cudaStream_t st) {
+    if (w.tc) {
+        Cp3Args a = base_args(X, w, o, beta);
+        a.rrow = rrow;
+        a.rec[2] = a3rec;
+        a.num[2] = n3;
+        a.den[2] = d3;
+        a.n_jt = w.tplan.n_jt;
+        a.n_kb = w.tplan.n_kb;
+        a.n_is = w.tplan.n_is;
+        a.p1n = w.Wpn;
+        a.p1d = w.Wpd;
+        a.err = ctx_status(ctx);
+        TK(cp3_tc_launch(w.tplan, a, PM_M1 | PM_M2 | (obj ? PM_OBJ : 0), 1, st));
+        // W = sum over the column blocks, in block order
+        const int64_t n = (int64_t)w.I1 * w.I2 * w.RP;
+        sum_parts_kernel<<<nblk(n), 256, 0, st>>>(w.Wpn, w.tplan.n_kb, n, w.Wn);
+        TK(cudaGetLastError());
+        sum_parts_kernel<<<nblk(n), 256, 0, st>>>(w.Wpd, w.tplan.n_kb, n, w.Wd);
+        TK(cudaGetLastError());
+        return NTF_OK;
+    }
     RowsArgs ra{};
     ra.a = base_args(X, w, o, beta);
     ra.a.rrow = rrow;
@@ -521,7 +564,8 @@ int contract_from_w(ntf_ctx *ctx, TuckerWs &w, int block, const Blocks &b, const
     return NTF_OK;
 }
 
-int setup(ntf_ctx *ctx, const ntf_tensor *X, const int64_t *core_dims, bool jcomm, TuckerWs &w) {
+int setup(ntf_ctx *ctx, const ntf_tensor *X, const int64_t *core_dims, bool jcomm, TuckerWs &w, const ntf_opts &o,
+          float beta) {
     w.I1 = (int)X->dims[0]; w.I2 = (int)X->dims[1]; w.I3 = (int)X->dims[2];
     w.J1 = (int)core_dims[0]; w.J2 = (int)core_dims[1]; w.J3 = (int)core_dims[2];
     w.RP = rank_pad(w.J3);
@@ -541,8 +585,20 @@ int setup(ntf_ctx *ctx, const ntf_tensor *X, const int64_t *core_dims, bool jcom
     w.num = wsf(ctx, "tkNum", mx, ok);
     w.den = wsf(ctx, "tkDen", mx, ok);
     w.plan3 = cp3_plan(w.I1, w.I2, w.I3, w.RP, ctx_num_sms(ctx));
-    w.pn3 = wsf(ctx, "tkPn3", (int64_t)w.plan3.parts3 * w.I3 * w.RP, ok);
-    w.pd3 = wsf(ctx, "tkPd3", (int64_t)w.plan3.parts3 * w.I3 * w.RP, ok);
+    // tensor cores when asked for and the shapes fit them: third core dimension 17..32
+    // (rank padded to 32), a 16-byte aligned X with I3 % 4 == 0, and beta != 1 (the
+    // explicit-rows kernels carry the denominator side)
+    w.tc = o.precision != NTF_PREC_FP32 && beta_kind(beta) != BK_KL &&
+           cp3_tc_eligible(w.RP, w.I3, X->values) && (int64_t)w.I1 * w.I2 < (1ll << 31);
+    if (w.tc) {
+        w.tplan = cp3_plan(w.I1, w.I2, w.I3, w.RP, ctx_num_sms(ctx), 128);
+        w.tplan.s3 = o.precision == NTF_PREC_3XTF32;
+        w.Wpn = wsf(ctx, "tkWpn", (int64_t)w.tplan.n_kb * IJ * w.RP, ok);
+        w.Wpd = wsf(ctx, "tkWpd", (int64_t)w.tplan.n_kb * IJ * w.RP, ok);
+    }
+    w.parts3 = w.tc ? w.tplan.parts3 : w.plan3.parts3;
+    w.pn3 = wsf(ctx, "tkPn3", (int64_t)w.parts3 * w.I3 * w.RP, ok);
+    w.pd3 = wsf(ctx, "tkPd3", (int64_t)w.parts3 * w.I3 * w.RP, ok);
     // rows pass grid: row tiles x slab splits, about one wave per SM
     const int TJ = (w.RP == 64) ? 64 : 128;
     const int n_jt = (w.I2 + TJ - 1) / TJ;
@@ -550,7 +606,8 @@ int setup(ntf_ctx *ctx, const ntf_tensor *X, const int64_t *core_dims, bool jcom
     if (is > w.I1) is = w.I1;
     w.rows_is = is;
     w.rows_grid = n_jt * is;
-    int gmax = w.rows_grid > w.plan3.grid ? w.rows_grid : w.plan3.grid;
+    w.obj_n = w.tc ? w.tplan.grid : w.rows_grid;
+    int gmax = std::max(std::max(w.rows_grid, w.plan3.grid), w.tc ? w.tplan.grid : 0);
     w.obj = (double *)ctx_ws(ctx, "tkObj", sizeof(double) * (size_t)gmax);
     if (!w.obj) ok = false;
     const char *names[4][4] = {{"tkG", "tkA1", "tkA2", "tkA3"}, {"tkGt", "tkA1t", "tkA2t", "tkA3t"},
@@ -604,6 +661,16 @@ int mode3_pass(ntf_ctx *ctx, TuckerWs &w, const ntf_tensor *X, const ntf_opts &o
     a.nrow = nrow;
     a.drow = drow;
     for (int m = 0; m < 3; ++m) a.rec[m] = a.num[m] = a.den[m] = a3rec;
+    if (w.tc) {
+        a.n_jt = w.tplan.n_jt;
+        a.n_kb = w.tplan.n_kb;
+        a.n_is = w.tplan.n_is;
+        a.p3n = w.pn3;
+        a.p3d = w.pd3;
+        a.err = ctx_status(ctx);
+        TK(cp3_tc_launch(w.tplan, a, PM_M3, 1, st));
+        return NTF_OK;
+    }
     a.n_jt = w.plan3.n_jt;
     a.n_kb = w.plan3.n_kb;
     a.n_is = w.plan3.n_is;
@@ -626,7 +693,7 @@ int tucker_run(ntf_ctx *ctx, const ntf_tensor *X, float beta, const int64_t *cor
         if (core_dims[n] > X->dims[n]) return ctx_fail(ctx, NTF_ERR_SHAPE, "core dimension exceeds tensor dimension");
     }
     TuckerWs w{};
-    int rc = setup(ctx, X, core_dims, jcomm, w);
+    int rc = setup(ctx, X, core_dims, jcomm, w, o, beta);
     if (rc) return rc;
     const float eps = (float)o.eps;
     const int64_t Jc = (int64_t)w.J1 * w.J2 * w.J3;
@@ -641,7 +708,7 @@ int tucker_run(ntf_ctx *ctx, const ntf_tensor *X, float beta, const int64_t *cor
         if ((rc = build_b3(ctx, w, w.cur, w.Brec, st))) return rc;
         if ((rc = rows_pass(ctx, w, X, o, beta, w.Brec, w.cur.A3p, w.cur.A3p, w.cur.A3p, objective_dev != nullptr, st)))
             return rc;
-        if (objective_dev) TK(reduce_objective(w.obj, w.rows_grid, 0.0, objective_dev, st));
+        if (objective_dev) TK(reduce_objective(w.obj, w.obj_n, 0.0, objective_dev, st));
         if ((rc = contract_from_w(ctx, w, 0, w.cur, w.Wn, w.num, st))) return rc;
         if ((rc = contract_from_w(ctx, w, 0, w.cur, w.Wd, w.den, st))) return rc;
         if ((rc = apply_mu(ctx, w, w.cur.G, w.cur.G, Jc, beta, eps, nullptr, nullptr, nullptr, st))) return rc;
@@ -658,7 +725,7 @@ int tucker_run(ntf_ctx *ctx, const ntf_tensor *X, float beta, const int64_t *cor
         if ((rc = build_b3(ctx, w, w.cur, w.Brec, st))) return rc;
         if ((rc = mode3_pass(ctx, w, X, o, beta, w.Brec, w.cur.A3p, w.Brec, w.Brec, false, st))) return rc;
         MuEpiArgs e{};
-        e.pn = w.pn3; e.pd = w.pd3; e.n_parts = w.plan3.parts3; e.rows = w.I3; e.RP = w.RP; e.R = w.J3;
+        e.pn = w.pn3; e.pd = w.pd3; e.n_parts = w.parts3; e.rows = w.I3; e.RP = w.RP; e.R = w.J3;
         e.pre = w.cur.A3p; e.out = w.cur.A3p; e.beta = beta; e.gamma = mu_gamma(beta); e.eps = eps;
         TK(mu_epilogue(e, st));
     } else {
@@ -672,7 +739,7 @@ int tucker_run(ntf_ctx *ctx, const ntf_tensor *X, float beta, const int64_t *cor
             // end of the sweep, so one pass serves the core and modes 1 and 2
             const bool obj = (l == 0) && objective_dev;
             if ((rc = rows_pass(ctx, w, X, o, beta, w.Brec, w.ref.A3p, w.t1.A3p, w.t2.A3p, obj, st))) return rc;
-            if (obj) TK(reduce_objective(w.obj, w.rows_grid, 0.0, objective_dev, st));
+            if (obj) TK(reduce_objective(w.obj, w.obj_n, 0.0, objective_dev, st));
             // core: Num with A_(1) of modes 1, 2 (and W), Den with A_(2)
             if ((rc = contract_from_w(ctx, w, 0, w.t1, w.Wn, w.num, st))) return rc;
             if ((rc = contract_from_w(ctx, w, 0, w.t2, w.Wd, w.den, st))) return rc;
@@ -691,7 +758,7 @@ int tucker_run(ntf_ctx *ctx, const ntf_tensor *X, float beta, const int64_t *cor
             if ((rc = build_b3(ctx, w, w.t2, w.Bd, st))) return rc;
             if ((rc = mode3_pass(ctx, w, X, o, beta, w.Brec, w.ref.A3p, w.Bn, w.Bd, false, st))) return rc;
             MuEpiArgs e{};
-            e.pn = w.pn3; e.pd = w.pd3; e.n_parts = w.plan3.parts3; e.rows = w.I3; e.RP = w.RP; e.R = w.J3;
+            e.pn = w.pn3; e.pd = w.pd3; e.n_parts = w.parts3; e.rows = w.I3; e.RP = w.RP; e.R = w.J3;
             e.pre = w.ref.A3p; e.out = w.cur.A3p; e.ref = w.ref.A3p; e.chi1_out = w.t1.A3p; e.chi2_out = w.t2.A3p;
             e.beta = beta; e.gamma = mu_gamma(beta); e.eps = eps;
             TK(mu_epilogue(e, st));
@@ -718,7 +785,7 @@ int tucker_beta_div(ntf_ctx *ctx, const ntf_tensor *X, float beta, const int64_t
         if (core_dims[n] > X->dims[n]) return ctx_fail(ctx, NTF_ERR_SHAPE, "core dimension exceeds tensor dimension");
     }
     TuckerWs w{};
-    int rc = setup(ctx, X, core_dims, false, w);
+    int rc = setup(ctx, X, core_dims, false, w, o, beta);
     if (rc) return rc;
     if ((rc = load_blocks(ctx, w, core, factors, w.cur, st))) return rc;
     if ((rc = build_b3(ctx, w, w.cur, w.Brec, st))) return rc;

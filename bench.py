@@ -448,7 +448,7 @@ def main():
     obj = torch.zeros(1, dtype=torch.float64, device=dev)
 
     def jstep():
-        ntf.jcomm_outer(X, BETA, A, objective=obj, ctx=ctx, precision=prec)
+        ntf.jcomm_outer(X, BETA, A, objective=obj, ctx=ctx, precision=prec, autotune=True)
 
     for _ in range(args.warmup):
         jstep()
@@ -468,7 +468,7 @@ def main():
     B = [a.clone() for a in A0]
 
     def bstep():
-        ntf.cp_mu_sweep(X, BETA, B, objective=obj, ctx=ctx, precision=prec)
+        ntf.cp_mu_sweep(X, BETA, B, objective=obj, ctx=ctx, precision=prec, autotune=True)
 
     t_b = timed(bstep, max(5, args.steps // 2), args.warmup)
     b_rate = world * max(5, args.steps // 2) / t_b
@@ -486,7 +486,7 @@ def main():
         Xe.copy_(Xh, non_blocking=True)
         for d, h in zip(Ae, Ah):
             d.copy_(h, non_blocking=True)
-        ntf.jcomm_outer(Xe, BETA, Ae, objective=obj, ctx=ctx, precision=prec)
+        ntf.jcomm_outer(Xe, BETA, Ae, objective=obj, ctx=ctx, precision=prec, autotune=True)
         for h, d in zip(Ahost_out, Ae):
             h.copy_(d, non_blocking=True)
         obj_h.copy_(obj, non_blocking=True)
@@ -510,7 +510,7 @@ def main():
             Fr = torch.zeros(n_max, dtype=torch.float64, device=dev)
             W_ = [a.clone() for a in A0]
             for _ in range(3):  # untimed: workspaces sized for this method and precision
-                fn(X, BETA, W_, objective=Fr[:1], ctx=ctx, precision=p)
+                fn(X, BETA, W_, objective=Fr[:1], ctx=ctx, precision=p, autotune=True)
             C_ = [a.clone() for a in A0]
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -518,7 +518,7 @@ def main():
             t = 0
             while t < n_max:
                 for _ in range(min(100, n_max - t)):
-                    fn(X, BETA, C_, objective=Fr[t:t + 1], ctx=ctx, precision=p)
+                    fn(X, BETA, C_, objective=Fr[t:t + 1], ctx=ctx, precision=p, autotune=True)
                     t += 1
                 if target is not None and float(Fr[:t].min()) <= target:
                     break
@@ -595,7 +595,7 @@ def main():
         "metric": METRIC, "value": value, "unit": "sweeps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_j / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "precision": prec, "method": "J-CoMM L=1",
+        "config": {"workload": WORKLOAD, "precision": prec, "method": "J-CoMM L=1", "plan": "autotuned slab split",
                    "l2": "inputs larger than L2 (537 MB tensor), no flush", "parallelism": "replicas"},
         "block_mu_sweeps_per_s": b_rate,
         "time_to_target": ttt,

@@ -79,6 +79,15 @@ typedef struct {
     double eps_x;  /* data floor used only at beta = 0 (1e-12) */
     int inner_L;   /* J-CoMM inner sweeps per outer iteration, >= 1 (1) */
     int precision; /* NTF_PREC_FP32 (default), NTF_PREC_TF32 or NTF_PREC_3XTF32 */
+    int autotune;  /* dense CP: 1 = pick the pass's slab split by timing (0).  On the first call
+                      for a given shape, rank padding, precision, beta class and pass variant in
+                      this process, the call times the pass it is about to run under a few grid
+                      plans (about one to four waves of CTAs, plus the cost model's choice) on its
+                      own stream, synchronizing that stream, and keeps the fastest in a
+                      process-wide table that every later call and context reuses.  The split
+                      sets the order of the partial sums, so results may differ from a run with
+                      another table in the last bits.  Ignored (cost-model plan, nothing cached)
+                      while the stream is being captured. */
 } ntf_opts;
 
 /* Fills *o with the defaults shown above. */

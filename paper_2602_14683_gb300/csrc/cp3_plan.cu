@@ -13,7 +13,7 @@ cudaError_t cp3_launch_fp32_r64(const Cp3Plan &, const Cp3Args &, int, int, cuda
 // the split minimises waves * (ceil(I / n_is) + c0), where c0 = 4 slab-equivalents is
 // the per-CTA cost of staging factor blocks and writing partial sums; ties go to fewer
 // CTAs.
-Cp3Plan cp3_plan(int I, int J, int K, int RP, int num_sms, int kb) {
+Cp3Plan cp3_plan(int I, int J, int K, int RP, int num_sms, int kb, int force_is) {
     Cp3Plan p{};
     p.tc = kb == 128;
     p.RP = RP;
@@ -35,6 +35,7 @@ Cp3Plan cp3_plan(int I, int J, int K, int RP, int num_sms, int kb) {
             best = n;
         }
     }
+    if (force_is > 0) best = force_is < I ? force_is : I;
     p.n_is = best;
     p.grid = base * best;
     p.parts1 = p.n_jt * p.n_kb * (p.tc ? 4 : 1);  // tensor-core pass: one per 32-row quarter

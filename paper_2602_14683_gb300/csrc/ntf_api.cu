@@ -4,7 +4,10 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <map>
+#include <mutex>
+#include <tuple>
 #include <vector>
 #include <string>
 
@@ -108,6 +111,8 @@ int check_factors(ntf_ctx *ctx, const ntf_tensor *X, int rank, const float *cons
 struct CpDense {
     int I, J, K, R, RP;
     ntf::Cp3Plan plan;
+    bool tc;
+    std::vector<int> tune;  // slab splits to time (empty: plan fixed)
     float *F[3];   // current (padded)
     float *Ft[3];  // reference (padded)
     float *C1[3], *C2[3];
@@ -117,8 +122,35 @@ struct CpDense {
     double *cs[3];  // FP64 column-sum partials of F[n] ([row block][RP]), closed-form KL Den
 };
 
+// ------------------------------------------------------------------ autotuner
+// Process-wide table of timed slab splits for the dense CP pass, keyed by device, shape,
+// rank padding, tensor-core use, split TF32, beta class and the pass variant timed.
+struct TuneKey {
+    int dev, I, J, K, RP, tc, s3, bk, ms;
+    bool operator<(const TuneKey &o) const {
+        return std::tie(dev, I, J, K, RP, tc, s3, bk, ms) < std::tie(o.dev, o.I, o.J, o.K, o.RP, o.tc, o.s3, o.bk, o.ms);
+    }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, int> g_tuned;
+
+// candidate slab splits: the cost model's, and the splits whose grids come closest to 1..4
+// waves of one CTA per SM from below and above
+std::vector<int> tune_candidates(const ntf::Cp3Plan &model, int I, int sms) {
+    const int base = model.n_jt * model.n_kb;
+    std::vector<int> c = {model.n_is};
+    for (int w = 1; w <= 4; ++w) {
+        const int lo = std::max(1, (w * sms) / base), hi = std::max(1, (w * sms + base - 1) / base);
+        if (lo <= I) c.push_back(lo);
+        if (hi <= I) c.push_back(hi);
+    }
+    std::sort(c.begin(), c.end());
+    c.erase(std::unique(c.begin(), c.end()), c.end());
+    return c;
+}
+
 int cp_dense_setup(ntf_ctx *ctx, const ntf_tensor *X, int R, bool jcomm, bool need_den, int precision,
-                   CpDense &s) {
+                   CpDense &s, const ntf_opts *tune_opts = nullptr, int tune_bk = 0, int tune_ms = 0) {
     s.I = (int)X->dims[0];
     s.J = (int)X->dims[1];
     s.K = (int)X->dims[2];
@@ -127,10 +159,27 @@ int cp_dense_setup(ntf_ctx *ctx, const ntf_tensor *X, int R, bool jcomm, bool ne
     // tensor-core passes where the request asks for them and the shapes allow (rank padded
     // to 32, rows of X 16-byte aligned for TMA); FP32 CUDA-core passes otherwise
     const bool tc = precision != NTF_PREC_FP32 && ntf::cp3_tc_eligible(s.RP, s.K, X->values);
+    s.tc = tc;
     s.plan = ntf::cp3_plan(s.I, s.J, s.K, s.RP, ctx->num_sms, tc ? 128 : 64);
     s.plan.s3 = tc && precision == NTF_PREC_3XTF32;
+    s.tune.clear();
+    ntf::Cp3Plan sizing = s.plan;  // the plan with the most partial sums among those that may run
+    if (tune_opts && tune_opts->autotune) {
+        const TuneKey key{ctx->device, s.I, s.J, s.K, s.RP, tc, s.plan.s3, tune_bk, tune_ms};
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tuned.find(key);
+        if (it != g_tuned.end()) {
+            const int s3 = s.plan.s3;
+            s.plan = ntf::cp3_plan(s.I, s.J, s.K, s.RP, ctx->num_sms, tc ? 128 : 64, it->second);
+            s.plan.s3 = s3;
+            sizing = s.plan;
+        } else {
+            s.tune = tune_candidates(s.plan, s.I, ctx->num_sms);
+            sizing = ntf::cp3_plan(s.I, s.J, s.K, s.RP, ctx->num_sms, tc ? 128 : 64, s.tune.back());
+        }
+    }
     const int dims[3] = {s.I, s.J, s.K};
-    const int parts[3] = {s.plan.parts1, s.plan.parts2, s.plan.parts3};
+    const int parts[3] = {sizing.parts1, std::max(sizing.parts2, s.plan.parts2), std::max(sizing.parts3, s.plan.parts3)};
     for (int n = 0; n < 3; ++n) {
         size_t fb = sizeof(float) * (size_t)dims[n] * s.RP;
         s.F[n] = (float *)ws_get(ctx, "cpF" + std::to_string(n), fb);
@@ -143,7 +192,7 @@ int cp_dense_setup(ntf_ctx *ctx, const ntf_tensor *X, int R, bool jcomm, bool ne
         if (!s.F[n] || !s.pn[n] || (jcomm && (!s.Ft[n] || !s.C1[n] || !s.C2[n])) || (need_den && !s.pd[n]))
             return fail(ctx, NTF_ERR_OOM, "workspace allocation failed");
     }
-    s.obj = (double *)ws_get(ctx, "cpObj", sizeof(double) * (size_t)s.plan.grid);
+    s.obj = (double *)ws_get(ctx, "cpObj", sizeof(double) * (size_t)std::max(s.plan.grid, sizing.grid));
     s.denc = (float *)ws_get(ctx, "cpDenc", sizeof(float) * 64);
     if (!s.obj || !s.denc) return fail(ctx, NTF_ERR_OOM, "workspace allocation failed");
     for (int n = 0; n < 3; ++n) {
@@ -265,15 +314,74 @@ ntf::UpdArgs upd_args(const CpDense &s, int n, float beta, const ntf_opts &o, bo
     return u;
 }
 
+// Times the pass variant `ms` (factors as in `a`) under each candidate slab split, keeps the
+// fastest for this key and switches s.plan to it.  The timing launches write only the
+// partial-sum workspaces, which the real passes overwrite.
+int tune_plan(ntf_ctx *ctx, const ntf_tensor *X, CpDense &s, const ntf_opts &o, float beta, ntf::Cp3Args a, int ms,
+              int den, cudaStream_t st) {
+    if (s.tune.empty()) return NTF_OK;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    NTF_CUDA(cudaStreamIsCapturing(st, &cap));
+    if (cap != cudaStreamCaptureStatusNone) {
+        s.tune.clear();  // cost-model plan; nothing is timed or cached during capture
+        return NTF_OK;
+    }
+    cudaEvent_t e0, e1;
+    NTF_CUDA(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(ctx, NTF_ERR_CUDA, "event creation failed");
+    }
+    const ntf::Cp3Plan model = s.plan;
+    int best = model.n_is, rc = NTF_OK;
+    float best_ms = 0.0f;
+    for (int n_is : s.tune) {
+        s.plan = ntf::cp3_plan(s.I, s.J, s.K, s.RP, ctx->num_sms, model.KB, n_is);
+        s.plan.s3 = model.s3;
+        a.n_jt = s.plan.n_jt;
+        a.n_kb = s.plan.n_kb;
+        a.n_is = s.plan.n_is;
+        float t = 0.0f;
+        if ((rc = launch_pass(ctx, s, a, ms, den, st))) break;  // untimed: caches, clocks
+        if (cudaEventRecord(e0, st) != cudaSuccess) { rc = NTF_ERR_CUDA; break; }
+        for (int r = 0; r < 2 && !rc; ++r) rc = launch_pass(ctx, s, a, ms, den, st);
+        if (rc) break;
+        if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) {
+            rc = NTF_ERR_CUDA;
+            break;
+        }
+        if (best_ms == 0.0f || t < best_ms) {
+            best_ms = t;
+            best = n_is;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc == NTF_ERR_CUDA ? fail(ctx, rc, "autotuning launch failed") : rc;
+    s.plan = ntf::cp3_plan(s.I, s.J, s.K, s.RP, ctx->num_sms, model.KB, best);
+    s.plan.s3 = model.s3;
+    s.tune.clear();
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned[TuneKey{ctx->device, s.I, s.J, s.K, s.RP, s.tc, s.plan.s3, ntf::beta_kind(beta), ms}] = best;
+    return NTF_OK;
+}
+
 int cp_dense_mu_sweep(ntf_ctx *ctx, const ntf_tensor *X, float beta, int R, float *const *factors,
                       const ntf_opts &o, double *objective_dev, cudaStream_t st) {
     const int bk = ntf::beta_kind(beta);
     const int den = bk != ntf::BK_KL;
     CpDense s{};
-    int rc = cp_dense_setup(ctx, X, R, false, den, o.precision, s);
+    const int tune_ms = ntf::PM_M1 | (objective_dev ? ntf::PM_OBJ : 0);
+    int rc = cp_dense_setup(ctx, X, R, false, den, o.precision, s, &o, bk, tune_ms);
     if (rc) return rc;
     NTF_CUDA(ntf::prep_factors(prep_args(s, factors, false, false, !den), st));
     ntf::Cp3Args a = cp_args(X, s, o, beta);
+    if (!s.tune.empty()) {
+        for (int m = 0; m < 3; ++m) a.rec[m] = a.num[m] = a.den[m] = s.F[m];
+        if ((rc = tune_plan(ctx, X, s, o, beta, a, tune_ms, den, st))) return rc;
+        a = cp_args(X, s, o, beta);
+    }
     for (int n = 0; n < 3; ++n) {
         for (int m = 0; m < 3; ++m) a.rec[m] = a.num[m] = a.den[m] = s.F[m];
         int ms = (n == 0 ? ntf::PM_M1 : n == 1 ? ntf::PM_M2 : ntf::PM_M3);
@@ -296,10 +404,20 @@ int cp_dense_jcomm(ntf_ctx *ctx, const ntf_tensor *X, float beta, int R, float *
     const int bk = ntf::beta_kind(beta);
     const bool kl = bk == ntf::BK_KL;
     CpDense s{};
-    int rc = cp_dense_setup(ctx, X, R, true, !kl, o.precision, s);
+    const int tune_ms = kl ? (ntf::PM_M1 | ntf::PM_M2 | ntf::PM_M3 | ntf::PM_OBJ) : (ntf::PM_M1 | ntf::PM_OBJ);
+    int rc = cp_dense_setup(ctx, X, R, true, !kl, o.precision, s, &o, bk, tune_ms);
     if (rc) return rc;
     NTF_CUDA(ntf::prep_factors(prep_args(s, factors, true, !kl, kl), st));
     ntf::Cp3Args a = cp_args(X, s, o, beta);
+    if (!s.tune.empty()) {
+        for (int m = 0; m < 3; ++m) {
+            a.rec[m] = s.Ft[m];
+            a.num[m] = kl ? s.Ft[m] : s.C1[m];
+            a.den[m] = kl ? s.Ft[m] : s.C2[m];
+        }
+        if ((rc = tune_plan(ctx, X, s, o, beta, a, tune_ms, kl ? 0 : 1, st))) return rc;
+        a = cp_args(X, s, o, beta);
+    }
     auto update = [&](int l, int n) {
         ntf::UpdArgs u = upd_args(s, n, beta, o, kl, s.Ft[n], l == o.inner_L - 1 ? factors[n] : nullptr);
         if (!kl) {
@@ -372,6 +490,7 @@ void ntf_opts_default(ntf_opts *o) {
     o->eps_x = 1e-12;
     o->inner_L = 1;
     o->precision = NTF_PREC_FP32;
+    o->autotune = 0;
 }
 
 int ntf_ctx_create(ntf_ctx **out, int device) {

@@ -29,8 +29,10 @@ namespace ntf {
 // Strided batched GEMM with a two-level reduction index (FP32 FMA, FP64 carry):
 //   C[bt][m][n] = sum_{k1 < K1, k2 < K2} A(bt, m, k1, k2) * B(bt, k1, k2, n)
 // The reduction index k = k1 * K2 + k2 may be split into `splits` contiguous ranges, one
-// CTA per (tile, batch, range); each range's FP64 sum goes to `part`, and the ranges are
-// then added in order by a second kernel (a fixed order for every run).
+// CTA per (tile, batch, range); each range's sum goes to `part` (FP32), and the ranges are
+// then added in order, in FP64, by a second kernel (a fixed order for every run).  Within a
+// range, products are summed in FP32 over blocks of GCARRY * GK terms and the blocks in
+// FP64; a range of one block never touches FP64 (a slow pipe on this part).
 // ----------------------------------------------------------------------------------
 struct Gemm {
     const float *A, *B;
@@ -40,7 +42,7 @@ struct Gemm {
     int64_t sbb, sbk1, sbk2, sbn;
     int64_t scb, scm, scn;
     int splits, kchunks;  // reduction ranges and GK-chunks per range (set by gemm())
-    double *part;         // [splits][batch][M][N] when splits > 1
+    float *part;          // [splits][batch][M][N] when splits > 1
 };
 
 constexpr int GT = 64;   // output tile edge
@@ -55,6 +57,7 @@ __global__ void __launch_bounds__(256) gemm2k_kernel(const Gemm g) {
     const int tid = threadIdx.x, tm = tid / 16, tn = tid % 16;
     const int K = g.K1 * g.K2;
     const int kbeg = sp * g.kchunks * GK, kend = min(K, kbeg + g.kchunks * GK);
+    const bool carry = (kend - kbeg + GK - 1) / GK > GCARRY;  // more than one FP32 block
     float acc[4][4];
     double tot[4][4];
 #pragma unroll
@@ -91,7 +94,7 @@ __global__ void __launch_bounds__(256) gemm2k_kernel(const Gemm g) {
                 for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(a[x], b[y], acc[x][y]);
         }
         __syncthreads();
-        if (++chunk == GCARRY) {
+        if (carry && ++chunk == GCARRY) {
             chunk = 0;
 #pragma unroll
             for (int x = 0; x < 4; ++x)
@@ -105,9 +108,9 @@ __global__ void __launch_bounds__(256) gemm2k_kernel(const Gemm g) {
         for (int y = 0; y < 4; ++y) {
             const int m = m0 + tm + 16 * x, n = n0 + tn + 16 * y;
             if (m < g.M && n < g.N) {
-                const double v = tot[x][y] + (double)acc[x][y];
+                const float v = carry ? (float)(tot[x][y] + (double)acc[x][y]) : acc[x][y];
                 if (g.splits > 1) g.part[(((int64_t)sp * g.batch + bt) * g.M + m) * g.N + n] = v;
-                else g.C[bt * g.scb + m * g.scm + n * g.scn] = (float)v;
+                else g.C[bt * g.scb + m * g.scm + n * g.scn] = v;
             }
         }
 }
@@ -118,7 +121,7 @@ __global__ void gemm_split_sum_kernel(const Gemm g) {
     const int64_t mn = (int64_t)g.M * g.N, total = mn * g.batch;
     if (t >= total) return;
     double v = 0.0;
-    for (int sp = 0; sp < g.splits; ++sp) v += g.part[(int64_t)sp * total + t];
+    for (int sp = 0; sp < g.splits; ++sp) v += (double)g.part[(int64_t)sp * total + t];
     const int bt = (int)(t / mn), m = (int)((t % mn) / g.N), n = (int)(t % g.N);
     g.C[bt * g.scb + m * g.scm + n * g.scn] = (float)v;
 }
@@ -133,7 +136,7 @@ static int gemm(ntf_ctx *ctx, Gemm g, cudaStream_t s) {
     g.kchunks = (nchunks + splits - 1) / splits;
     g.splits = (nchunks + g.kchunks - 1) / g.kchunks;
     if (g.splits > 1) {
-        g.part = (double *)ctx_ws(ctx, "gemm_split", sizeof(double) * (size_t)g.splits * g.batch * g.M * g.N);
+        g.part = (float *)ctx_ws(ctx, "gemm_split", sizeof(float) * (size_t)g.splits * g.batch * g.M * g.N);
         if (!g.part) return ctx_fail(ctx, NTF_ERR_OOM, "workspace allocation failed");
     }
     dim3 grid((g.N + GT - 1) / GT, (g.M + GT - 1) / GT, g.batch * g.splits);

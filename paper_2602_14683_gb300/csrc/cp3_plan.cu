@@ -15,7 +15,7 @@ cudaError_t cp3_launch_fp32_r64(const Cp3Plan &, const Cp3Args &, int, int, cuda
 // CTAs.
 Cp3Plan cp3_plan(int I, int J, int K, int RP, int num_sms, int kb, int force_is) {
     Cp3Plan p{};
-    p.tc = kb == 128;
+    p.tc = kb >= 128;
     p.RP = RP;
     p.TJ = (RP == 64) ? 64 : 128;
     p.KB = kb;

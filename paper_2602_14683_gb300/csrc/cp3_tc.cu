@@ -62,7 +62,7 @@ bool cp3_tc_supported(int ms, int den, bool rx) {
 }
 
 cudaError_t cp3_tc_launch(const Cp3Plan &p, const Cp3Args &a, int ms, int den, cudaStream_t s) {
-    if (!p.tc || p.RP != 32 || p.KB != tc::KBLK) return cudaErrorInvalidValue;
+    if (!p.tc || p.RP != 32 || (p.KB != tc::KBLK && p.KB != 2 * tc::KBLK)) return cudaErrorInvalidValue;
     if ((a.bkind == BK_KL) != (den == 0)) return cudaErrorInvalidValue;
     switch (a.bkind) {
         case 0: return cp3_tc_launch_bk0(p, a, ms, s);

@@ -51,7 +51,7 @@ namespace ntf {
 namespace tc {
 
 constexpr int ROWS = 128;  // tile rows
-constexpr int KBLK = 128;  // columns per CTA block
+constexpr int KBLK = 128;  // columns per CTA block (256 for the KL / single-TF32 variants)
 constexpr int CH = 64;     // columns per chunk
 constexpr int RP = 32;
 constexpr int CG = 4;      // column groups per chunk (epilogue warps = 4 CG)
@@ -73,32 +73,35 @@ struct Layout {
 // rows 32..127 are padding: those rows only feed accumulator rows that are never read, so
 // only the 32 real rows are stored (two 4 KB K-atoms per buffer) and the padding reads fall
 // on the 16 KB that follow (the Crec / R tiles), which stay inside the allocation.
-__host__ __device__ constexpr int layout_bytes(bool rows, bool m3, bool den, bool s3, int ns, int np, int nk) {
-    return ns * 32768 + np * 16384 * (den ? 2 : 1) + (s3 ? 4 : 2) * 16384 + (rows ? 8192 : 0) +
-           ((rows && den) ? 8192 : 0) + (m3 ? nk * 8192 : 0) + ((m3 && den) ? nk * 8192 : 0) + 4096 + 1024;
+// kb: columns per CTA block; the C tile is kb x 32 TF32 (128 bytes a column) and the
+// contraction's C^T operand 32 x kb BF16
+__host__ __device__ constexpr int layout_bytes(bool rows, bool m3, bool den, bool s3, int ns, int np, int nk, int kb) {
+    return ns * 32768 + np * 16384 * (den ? 2 : 1) + (s3 ? 2 : 1) * kb * 128 + (s3 ? 2 : 1) * 16384 +
+           (rows ? kb * 64 : 0) + ((rows && den) ? kb * 64 : 0) + (m3 ? nk * 8192 : 0) + ((m3 && den) ? nk * 8192 : 0) +
+           4096 + 1024;
 }
 
-__host__ __device__ constexpr Layout make_layout(bool rows, bool m3, bool den, bool s3) {
+__host__ __device__ constexpr Layout make_layout(bool rows, bool m3, bool den, bool s3, int kb) {
     Layout L{};
     constexpr int kMax = 232448;  // opt-in shared memory per CTA
     L.ns = 2;
     L.np = 1;
     L.nk = 1;
-    if (layout_bytes(rows, m3, den, s3, 2, 2, 1) <= kMax) L.np = 2;
-    if (layout_bytes(rows, m3, den, s3, 2, L.np, 2) <= kMax) L.nk = 2;
-    if (layout_bytes(rows, m3, den, s3, 3, L.np, L.nk) <= kMax) L.ns = 3;
+    if (layout_bytes(rows, m3, den, s3, 2, 2, 1, kb) <= kMax) L.np = 2;
+    if (layout_bytes(rows, m3, den, s3, 2, L.np, 2, kb) <= kMax) L.nk = 2;
+    if (layout_bytes(rows, m3, den, s3, 3, L.np, L.nk, kb) <= kMax) L.ns = 3;
     int o = 0;
     L.x = o; o += L.ns * 32768;
     L.p = o; o += L.np * 16384;
     L.q = o; o += den ? L.np * 16384 : 0;
     L.knt = o; o += m3 ? L.nk * 8192 : 0;            // padding rows read the C tiles below
-    L.c = o; o += 16384;
-    L.cl = o; o += s3 ? 16384 : 0;
+    L.c = o; o += kb * 128;
+    L.cl = o; o += s3 ? kb * 128 : 0;
     L.kdt = o; o += (m3 && den) ? L.nk * 8192 : 0;   // padding rows read the R tiles below
     L.r = o; o += 16384;
     L.rl = o; o += s3 ? 16384 : 0;
-    L.cnt = o; o += rows ? 8192 : 0;
-    L.cdt = o; o += (rows && den) ? 8192 : 0;
+    L.cnt = o; o += rows ? kb * 64 : 0;
+    L.cdt = o; o += (rows && den) ? kb * 64 : 0;
     L.misc = o; o += 4096;
     L.total = o + 1024;  // alignment slack of the dynamic base
     return L;
@@ -324,12 +327,14 @@ __device__ __forceinline__ float reduce_scatter(float v[N]) {
     return s;
 }
 
-template <int MS, int BK, bool S3, bool RX>
+template <int MS, int BK, bool S3, bool RX, int KB>
 __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUtensorMap xmap, const Cp3Args a) {
     constexpr bool DEN = BK != BK_KL;
     constexpr bool M1 = (MS & PM_M1) != 0, M2 = (MS & PM_M2) != 0, M3 = (MS & PM_M3) != 0;
     constexpr bool OBJ = (MS & PM_OBJ) != 0, RW = M1 || M2;
-    constexpr Layout L = make_layout(RW, M3, DEN, S3);
+    constexpr int CPS = KB / CH;  // chunks per slab
+    static_assert(KB == 128 || (KB == 256 && !DEN && !S3 && !RX), "256-column blocks: KL, single TF32");
+    constexpr Layout L = make_layout(RW, M3, DEN, S3, KB);
     constexpr int NP = L.np, NS = L.ns, NK = L.nk;
     extern __shared__ __align__(1024) uint8_t smraw[];
     uint8_t *sm = (uint8_t *)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
@@ -369,10 +374,10 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
     const int i0 = (int)((int64_t)is * a.I / a.n_is);
     const int i1 = (int)((int64_t)(is + 1) * a.I / a.n_is);
     const int J = a.J, K = a.K;
-    const int j0 = jt * ROWS, k0 = kb * KBLK;
+    const int j0 = jt * ROWS, k0 = kb * KB;
     const int j = j0 + row;
     const bool jv = epi && j < J;
-    const int NC = 2 * (i1 - i0);
+    const int NC = CPS * (i1 - i0);
     const int r0 = RS * cg;
 
     auto wait = [&](uint64_t *bar, uint32_t phase) -> bool {
@@ -412,29 +417,32 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
         bkd[e] = (v && DEN) ? __ldg(a.den[1] + (int64_t)(j0 + kr_j + e) * RP + kr_r) : 0.0f;
     }
     if (epi) {
-        const int kc = k0 + row;
-        const bool kv = kc < K;
+#pragma unroll 1
+        for (int cc = row; cc < KB; cc += ROWS) {  // block column cc
+            const int kc = k0 + cc;
+            const bool kv = kc < K;
 #pragma unroll
-        for (int q = 0; q < RS / 4; ++q) {
-            float h[4], l[4];
+            for (int q = 0; q < RS / 4; ++q) {
+                float h[4], l[4];
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const float v = kv ? __ldg(a.rec[2] + (int64_t)kc * RP + r0 + 4 * q + e) : 0.0f;
-                h[e] = tf32_rna(v);
-                l[e] = S3 ? tf32_rna(v - h[e]) : 0.0f;
+                for (int e = 0; e < 4; ++e) {
+                    const float v = kv ? __ldg(a.rec[2] + (int64_t)kc * RP + r0 + 4 * q + e) : 0.0f;
+                    h[e] = tf32_rna(v);
+                    l[e] = S3 ? tf32_rna(v - h[e]) : 0.0f;
+                }
+                *reinterpret_cast<float4 *>(Cs + swf(cc, r0 + 4 * q)) = make_float4(h[0], h[1], h[2], h[3]);
+                if (S3) *reinterpret_cast<float4 *>(Cl + swf(cc, r0 + 4 * q)) = make_float4(l[0], l[1], l[2], l[3]);
             }
-            *reinterpret_cast<float4 *>(Cs + swf(row, r0 + 4 * q)) = make_float4(h[0], h[1], h[2], h[3]);
-            if (S3) *reinterpret_cast<float4 *>(Cl + swf(row, r0 + 4 * q)) = make_float4(l[0], l[1], l[2], l[3]);
-        }
-        if (RW) {
+            if (RW) {
 #pragma unroll
-            for (int r = 0; r < RS; ++r) {
-                const int rr = r0 + r;
-                CnT[(row >> 6) * 2048 + swh(rr, row & 63)] =
-                    __float2bfloat16_rn(kv ? __ldg(a.num[2] + (int64_t)kc * RP + rr) : 0.0f);
-                if (DEN)
-                    CdT[(row >> 6) * 2048 + swh(rr, row & 63)] =
-                        __float2bfloat16_rn(kv ? __ldg(a.den[2] + (int64_t)kc * RP + rr) : 0.0f);
+                for (int r = 0; r < RS; ++r) {
+                    const int rr = r0 + r;
+                    CnT[(cc >> 6) * 2048 + swh(rr, cc & 63)] =
+                        __float2bfloat16_rn(kv ? __ldg(a.num[2] + (int64_t)kc * RP + rr) : 0.0f);
+                    if (DEN)
+                        CdT[(cc >> 6) * 2048 + swh(rr, cc & 63)] =
+                            __float2bfloat16_rn(kv ? __ldg(a.den[2] + (int64_t)kc * RP + rr) : 0.0f);
+                }
             }
         }
     }
@@ -546,7 +554,7 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
         // ---- producer warp: X chunks into the shared-memory ring, PF chunks ahead into L2 ----
         if (lane == 0 && NC > 0) {
             auto prefetch_x = [&](int n) {
-                const int i = i0 + (n >> 1), x = k0 + CH * (n & 1);
+                const int i = i0 + n / CPS, x = k0 + CH * (n % CPS);
                 // only boxes that start inside the tensor (a ragged block's last chunk may not)
                 if (x < K) tma_prefetch_2d(&xmap, x, i * J + j0);
                 if (x + 32 < K) tma_prefetch_2d(&xmap, x + 32, i * J + j0);
@@ -557,7 +565,7 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
             for (int n = 0; n < NC; ++n) {
                 // chunk n - NS used this slot with the other parity
                 if (n >= NS && !wait(inputs_free + xs, xph ^ 1)) break;
-                const int i = i0 + (n >> 1), q = n & 1;
+                const int i = i0 + n / CPS, q = n % CPS;
                 const uint32_t bar = su32(chunk_ready + xs);
                 const uint32_t dst = su32(Xs) + xs * 32768;
                 expect_tx(bar, 32768);
@@ -575,7 +583,7 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
         // ---- issuer warp: GEMM1 and the contractions, in chunk order ----------------------
         if (lane == 0 && NC > 0) {
             auto issue_g1 = [&](int n) {
-                const int q = n & 1;
+                const int q = n % CPS;
                 const uint32_t d = t_d1 + 64 * (n & 1);
                 const uint32_t id = idesc_tf32(CH);
                 const uint32_t cb = su32(Cs) + q * 8192, cbl = su32(Cl) + q * 8192;
@@ -590,8 +598,8 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
                 mma_commit(su32(chunk_ready + n % NS));
             };
             auto issue_g2 = [&](int n) {
-                const int q = n & 1, sb = (n >> 1) & 1;
-                const uint32_t kn = su32(KnT) + ((n >> 1) % NK) * 8192, kd = su32(KdT) + ((n >> 1) % NK) * 8192;
+                const int q = n % CPS, sb = (n / CPS) & 1;
+                const uint32_t kn = su32(KnT) + ((n / CPS) % NK) * 8192, kd = su32(KdT) + ((n / CPS) % NK) * 8192;
                 const uint32_t pb = su32(Ps) + (n % NP) * 16384, qb = su32(Qs) + (n % NP) * 16384;
                 if (RW) {
                     const uint32_t id = idesc_bf16(RP, false);
@@ -607,7 +615,7 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
 #pragma unroll
                     for (int s = 0; s < 8; ++s) {
                         const uint32_t ao = (s >> 2) * 4096 + (s & 3) * 32;
-                        const uint32_t acc = (n >= 2 || s > 0) ? 1u : 0u;
+                        const uint32_t acc = (n >= CPS || s > 0) ? 1u : 0u;
                         mma_bf16(t_n3 + 64 * q, sdesc(kn + ao), sdesc(pb + s * 2048, 16384, 1024), id, acc);
                         if (DEN) mma_bf16(t_n3d + 64 * q, sdesc(kd + ao), sdesc(qb + s * 2048, 16384, 1024), id, acc);
                     }
@@ -622,7 +630,7 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
                     bool ok = true;
                     // X-hat buffer m & 1 was last read by chunk m - 2
                     if (m >= 2) ok = wait(inputs_free + (m - 2) % NS, ((m - 2) / NS) & 1);
-                    if (ok && (m & 1) == 0) ok = wait(r_full, ((m >> 1) - 1) & 1);
+                    if (ok && m % CPS == 0) ok = wait(r_full, (m / CPS - 1) & 1);
                     if (!ok) break;
                     fence_after();
                     issue_g1(m);
@@ -690,8 +698,8 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
         int xs = 0;        // ring slot of chunk n
         uint32_t xph = 0;  // parity of its phase, (n / NS) & 1
         for (int n = 0; n < NC; ++n) {
-            const int i = i0 + (n >> 1), q = n & 1;
-            const int pb = NP == 2 ? q : 0;
+            const int i = i0 + n / CPS, q = n % CPS;
+            const int pb = n % NP;
             if (n >= NP) wait(g2_done + pb, ((n - NP) / NP) & 1);  // P tile pb free again
             if (q == 0 && n > 0) {
                 // slab boundary: rows of slab i + 2 staged; KRn^T of slab i written into the
@@ -711,7 +719,7 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
                     if (RX && i + 1 < i1) kx_load(i + 1);
                 }
             }
-            if (RW && q == 1 && n >= 3) {
+            if (RW && q == 1 && n > CPS) {
                 // fold slab i - 1: its last contraction (chunk n - 2) is complete, as the
                 // P-tile wait above covers chunk n - NP >= n - 2; W of slab i - 1 is rewritten
                 // by slab i + 1, whose contractions start only after this chunk's P tile
@@ -723,7 +731,7 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
             fence_after();
             float xh[CW], xv[CW];
             if (ready) {  // warp-uniform before tcgen05.ld
-                tmem_ld<CW>(t_d1 + 64 * q + lane_off + CW * cg, xh);
+                tmem_ld<CW>(t_d1 + 64 * (n & 1) + lane_off + CW * cg, xh);
             } else {
 #pragma unroll
                 for (int c = 0; c < CW; ++c) xh[c] = 0.0f;
@@ -743,7 +751,7 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
                 xs = 0;
                 xph ^= 1;
             }
-            if (q == 1 && n + 1 < NC) {
+            if (q == CPS - 1 && n + 1 < NC) {
                 // this chunk's GEMM1 is complete, so R can take slab i + 1 (needed by GEMM1 of
                 // the next chunk, which the issuer starts once every warp has arrived)
                 slab_rows(i + 1);
@@ -838,10 +846,10 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
         if (M3 && quarter == 0) {
             const int64_t base = (int64_t)(jt * a.n_is + is) * K;
 #pragma unroll 1
-            for (int g = 0; g < KBLK / (32 * CG); ++g) {
+            for (int g = 0; g < KB / (32 * CG); ++g) {
                 float v[32], vd[32];
                 const bool have = good && NC > 0;
-                const int cb = (KBLK / CG) * cg + 32 * g;
+                const int cb = (KB / CG) * cg + 32 * g;
                 if (have) {
                     tmem_ld32(t_n3 + cb, v);
                     if (DEN) tmem_ld32(t_n3d + cb, vd);
@@ -894,13 +902,13 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
 
 cudaError_t launch_x_map(const Cp3Args &a, CUtensorMap *map);
 
-template <int MS, int BK, bool S3, bool RX>
+template <int MS, int BK, bool S3, bool RX, int KB = KBLK>
 cudaError_t launch_t(const Cp3Plan &p, const Cp3Args &a, cudaStream_t s) {
-    constexpr Layout L = make_layout((MS & (PM_M1 | PM_M2)) != 0, (MS & PM_M3) != 0, BK != BK_KL, S3);
+    constexpr Layout L = make_layout((MS & (PM_M1 | PM_M2)) != 0, (MS & PM_M3) != 0, BK != BK_KL, S3, KB);
     CUtensorMap map;
     cudaError_t e = launch_x_map(a, &map);
     if (e != cudaSuccess) return e;
-    auto k = cp3_pass_tc<MS, BK, S3, RX>;
+    auto k = cp3_pass_tc<MS, BK, S3, RX, KB>;
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total);
     if (e != cudaSuccess) return e;
     k<<<p.grid, NT, L.total, s>>>(map, a);
@@ -921,6 +929,19 @@ cudaError_t launch_bk(const Cp3Plan &p, const Cp3Args &a, int ms, cudaStream_t s
             }
         }
     }
+    if constexpr (BK == BK_KL && !S3) {
+        if (p.KB == 256) {
+            switch (ms) {
+                case PM_M1: return launch_t<PM_M1, BK, S3, false, 256>(p, a, s);
+                case PM_M1 | PM_OBJ: return launch_t<PM_M1 | PM_OBJ, BK, S3, false, 256>(p, a, s);
+                case PM_M2: return launch_t<PM_M2, BK, S3, false, 256>(p, a, s);
+                case PM_M3: return launch_t<PM_M3, BK, S3, false, 256>(p, a, s);
+                case PM_M1 | PM_M2 | PM_M3 | PM_OBJ: return launch_t<PM_M1 | PM_M2 | PM_M3 | PM_OBJ, BK, S3, false, 256>(p, a, s);
+                default: return cudaErrorInvalidValue;
+            }
+        }
+    }
+    if (p.KB != KBLK) return cudaErrorInvalidValue;
     switch (ms) {
         case PM_M1: return launch_t<PM_M1, BK, S3, false>(p, a, s);
         case PM_M1 | PM_OBJ: return launch_t<PM_M1 | PM_OBJ, BK, S3, false>(p, a, s);

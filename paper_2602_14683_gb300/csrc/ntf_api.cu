@@ -160,7 +160,10 @@ int cp_dense_setup(ntf_ctx *ctx, const ntf_tensor *X, int R, bool jcomm, bool ne
     // to 32, rows of X 16-byte aligned for TMA); FP32 CUDA-core passes otherwise
     const bool tc = precision != NTF_PREC_FP32 && ntf::cp3_tc_eligible(s.RP, s.K, X->values);
     s.tc = tc;
-    s.plan = ntf::cp3_plan(s.I, s.J, s.K, s.RP, ctx->num_sms, tc ? 128 : 64);
+    // 256-column blocks where the tensor memory allows them (KL: no denominator accumulators;
+    // single TF32: no low-part C tile)
+    const int kb = tc ? ((!need_den && precision == NTF_PREC_TF32) ? 256 : 128) : 64;
+    s.plan = ntf::cp3_plan(s.I, s.J, s.K, s.RP, ctx->num_sms, kb);
     s.plan.s3 = tc && precision == NTF_PREC_3XTF32;
     s.tune.clear();
     ntf::Cp3Plan sizing = s.plan;  // the plan with the most partial sums among those that may run
@@ -170,12 +173,12 @@ int cp_dense_setup(ntf_ctx *ctx, const ntf_tensor *X, int R, bool jcomm, bool ne
         auto it = g_tuned.find(key);
         if (it != g_tuned.end()) {
             const int s3 = s.plan.s3;
-            s.plan = ntf::cp3_plan(s.I, s.J, s.K, s.RP, ctx->num_sms, tc ? 128 : 64, it->second);
+            s.plan = ntf::cp3_plan(s.I, s.J, s.K, s.RP, ctx->num_sms, kb, it->second);
             s.plan.s3 = s3;
             sizing = s.plan;
         } else {
             s.tune = tune_candidates(s.plan, s.I, ctx->num_sms);
-            sizing = ntf::cp3_plan(s.I, s.J, s.K, s.RP, ctx->num_sms, tc ? 128 : 64, s.tune.back());
+            sizing = ntf::cp3_plan(s.I, s.J, s.K, s.RP, ctx->num_sms, kb, s.tune.back());
         }
     }
     const int dims[3] = {s.I, s.J, s.K};

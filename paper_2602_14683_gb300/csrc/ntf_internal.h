@@ -149,8 +149,8 @@ struct Cp3Plan {
     int parts1, parts2, parts3;
 };
 
-// kb: columns per CTA block (64 for the FP32 pass, 128 for the tensor-core pass); n_is > 0
-// forces the slab split instead of the cost model's choice
+// kb: columns per CTA block (64 for the FP32 pass; 128 for the tensor-core pass, 256 for its
+// KL single-TF32 variants); n_is > 0 forces the slab split instead of the cost model's choice
 Cp3Plan cp3_plan(int I, int J, int K, int RP, int num_sms, int kb = 64, int n_is = 0);
 // Launches one pass.  mode_set: OR of PassMode; den: 1 when the denominator partials are
 // needed (beta != 1).  Returns a cudaError_t.

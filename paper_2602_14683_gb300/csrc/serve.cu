@@ -89,10 +89,12 @@ size_t estimate_bytes(const ntf_job &j, int sms) {
         size_t parts = (size_t)p32.parts1 * I + (size_t)p32.parts2 * J + (size_t)p32.parts3 * K;
         int grid = p32.grid;
         if (j.precision != NTF_PREC_FP32 && RP == 32) {
-            const ntf::Cp3Plan ptc = ntf::cp3_plan((int)I, (int)J, (int)K, RP, sms, 128);
-            const size_t pt = (size_t)ptc.parts1 * I + (size_t)ptc.parts2 * J + (size_t)ptc.parts3 * K;
-            parts = pt > parts ? pt : parts;
-            grid = ptc.grid > grid ? ptc.grid : grid;
+            for (int kb = 128; kb <= 256; kb *= 2) {
+                const ntf::Cp3Plan ptc = ntf::cp3_plan((int)I, (int)J, (int)K, RP, sms, kb);
+                const size_t pt = (size_t)ptc.parts1 * I + (size_t)ptc.parts2 * J + (size_t)ptc.parts3 * K;
+                parts = pt > parts ? pt : parts;
+                grid = ptc.grid > grid ? ptc.grid : grid;
+            }
         }
         b += 4 * sizeof(float) * (size_t)(I + J + K) * RP;
         b += 2 * sizeof(float) * parts * RP;

@@ -58,12 +58,13 @@ def parse():
 
 
 # DRAM bytes (read + write) per tensor entry of the timed tensor-core pass (all numerators +
-# objective, TF32 reconstruction), from the ncu capture summarised in
-# profiles/cp3_pass_tc_cp384_r32_beta1_tf32.md; valid only for the kernel sources it was taken on
+# objective, TF32 reconstruction, 256-column blocks), from the ncu capture at 512^3 summarised
+# in profiles/cp3_pass_tc_cp512_r32_beta1_tf32.md; valid only for the kernel sources it was
+# taken on
 TC_CAPTURE = {
-    "sources": {"paper_2602_14683_gb300/csrc/cp3_tc.cuh": "a2e9ee5cd8c2ef70a63652ad518975caca0067635bc1d3cc1b4ae92e4a78fb29",
-                "paper_2602_14683_gb300/csrc/cp3_tc.cu": "f0c1d697e022d9ea88a203d90bdc95881740869dd753f03242113a9c49949ae3"},
-    "bytes_per_entry": (228.308224e6 + 3.979776e6) / 384 ** 3,
+    "sources": {"paper_2602_14683_gb300/csrc/cp3_tc.cuh": "cd4ab2a5ddb38e7c099f17e175831e29f0ffbab3846fb661b27171a4769cd8c2",
+                "paper_2602_14683_gb300/csrc/cp3_tc.cu": "304d0a78be4a25df8d7262e60a31af2b6769d3e8f48b05534b8a83c9e738e3ca"},
+    "bytes_per_entry": (540.562688e6 + 5.062144e6) / 512 ** 3,
 }
 
 

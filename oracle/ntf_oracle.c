@@ -208,6 +208,50 @@ void ntfo_cp_mu_sweep(int N, const int64_t *dims, const double *X, int R, double
         ntfo_cp_block_update(N, dims, X, R, A, n, beta, eps, eps_x, NULL, NULL);
 }
 
+/* One extrapolated B-CoMM outer iteration for CP (Section "Going beyond: Majorization-
+ * Minimization with Extrapolation", item (i)).  A holds the current iterate A^t and becomes
+ * A^(t+1); Aprev holds the previous outer iterate A^(t-1) and becomes A^t.  For n = 1..N:
+ *   D = [A^(n) - Aprev^(n)]_+ (componentwise positive part, A^(n) not yet updated),
+ *   alpha_n = min(alpha_nes, cap / (||D||_F + delta)),
+ *   Ahat = max(A^(n) + alpha_n D, eps),
+ * then the block update of Theorem "CP block multiplicative update" with Xhat rebuilt from
+ * Ahat in mode n and the current other blocks, and Ahat as the multiplicative pre-factor.
+ * F_in (may be NULL) receives the objective of the incoming iterate A^t.  Readings: the
+ * previous iterate kept for the next call is the incoming one (so that the next
+ * displacement is A^(t+1) - A^t); the cap is applied per block. */
+void ntfo_cp_mu_sweep_extrap(int N, const int64_t *dims, const double *X, int R, double *const *A,
+                             double *const *Aprev, double beta, double eps, double eps_x, double alpha_nes,
+                             double cap, double delta, double *F_in) {
+    if (F_in) *F_in = ntfo_cp_objective(N, dims, X, R, (const double *const *)A, beta, eps, eps_x);
+    double *saved[8];
+    for (int n = 0; n < N; ++n) {
+        saved[n] = (double *)malloc(sizeof(double) * dims[n] * R);
+        memcpy(saved[n], A[n], sizeof(double) * dims[n] * R);
+    }
+    for (int n = 0; n < N; ++n) {
+        const int64_t cnt = dims[n] * R;
+        double nrm2 = 0.0;
+        for (int64_t e = 0; e < cnt; ++e) {
+            const double d = A[n][e] - Aprev[n][e];
+            if (d > 0.0) nrm2 += d * d;
+        }
+        double alpha = cap / (sqrt(nrm2) + delta);
+        if (alpha_nes < alpha) alpha = alpha_nes;
+        for (int64_t e = 0; e < cnt; ++e) {
+            const double d = A[n][e] - Aprev[n][e];
+            const double v = A[n][e] + alpha * (d > 0.0 ? d : 0.0);
+            A[n][e] = v > eps ? v : eps;
+        }
+        /* block n now holds Ahat: the block update rebuilds Xhat from it and uses it as the
+         * pre-factor */
+        ntfo_cp_block_update(N, dims, X, R, A, n, beta, eps, eps_x, NULL, NULL);
+    }
+    for (int n = 0; n < N; ++n) {
+        memcpy(Aprev[n], saved[n], sizeof(double) * dims[n] * R);
+        free(saved[n]);
+    }
+}
+
 /* One outer iteration of Algorithm 2 (J-CoMM) for CP with L inner sweeps (Section 5.3,
  * "CP inner update"): the reference is the incoming iterate; Ptilde/Qtilde are formed
  * once; each inner block update uses chi1 of the other current blocks for the numerator,

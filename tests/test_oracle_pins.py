@@ -475,3 +475,72 @@ def test_objective_beta0_floor():
     f = oracle.cp_objective(X, A, 0.0, eps_x=1e-3)
     want = sum(oracle.dbeta(max(x, 1e-3), 1.0, 0.0) for x in X.ravel())
     assert f == pytest.approx(want, rel=1e-14)
+
+
+# ----------------------------------------- extrapolated B-CoMM (BMMe-style, Section "Going beyond")
+
+def test_extrap_reduces_to_bcomm_without_extrapolation():
+    """alpha = 0, or a previous iterate equal to the current one, is plain B-CoMM (exactly)."""
+    g = np.random.default_rng(31)
+    dims, R = (4, 5, 3), 3
+    X = g.gamma(3.0, 1.0, size=dims) + 0.05
+    A = [g.uniform(0.2, 1.0, size=(d, R)) for d in dims]
+    Ap = [g.uniform(0.2, 1.0, size=(d, R)) for d in dims]
+    want, Fw = oracle.cp_mu_sweep(X, A, 1.5)
+    got, prev, F = oracle.cp_mu_sweep_extrap(X, A, Ap, 1.5, alpha=0.0)
+    for n in range(3):
+        assert np.array_equal(got[n], want[n]) and np.array_equal(prev[n], A[n])
+    assert F == Fw
+    got, _, _ = oracle.cp_mu_sweep_extrap(X, A, A, 1.5, alpha=0.9)
+    for n in range(3):
+        assert np.array_equal(got[n], want[n])
+
+
+@pytest.mark.parametrize("beta", BETAS)
+def test_extrap_blocks_are_surrogate_argmins_at_the_extrapolated_point(beta):
+    """Each block of the extrapolated sweep minimises the block surrogate built at the
+    extrapolated point (Ahat in mode n, current other blocks); alpha and the cap are
+    recomputed here from their definitions."""
+    g = np.random.default_rng(32)
+    dims, R = (4, 3, 5), 2
+    X = g.gamma(3.0, 1.0, size=dims) + 0.05
+    A = [g.uniform(0.2, 1.0, size=(d, R)) for d in dims]
+    Ap = [a * g.uniform(0.5, 1.2, size=a.shape) for a in A]
+    alpha, cap, delta, eps = 0.6, 0.05, 1e-12, 1e-12
+    got, prev, _ = oracle.cp_mu_sweep_extrap(X, A, Ap, beta, alpha=alpha, cap=cap, delta=delta)
+    cur = [a.copy() for a in A]
+    for n in range(3):
+        D = np.maximum(A[n] - Ap[n], 0.0)
+        a_n = min(alpha, cap / (np.linalg.norm(D) + delta))
+        hat = np.maximum(A[n] + a_n * D, eps)
+        ref = list(cur)
+        ref[n] = hat
+        zt = _cp_contribs(ref)
+
+        def Gfun(blk, ref=ref, n=n, zt=zt):
+            B = list(ref)
+            B[n] = blk
+            return _surrogate(X, _cp_contribs(B), zt, beta)
+
+        _assert_block_argmin(Gfun, got[n])
+        cur[n] = got[n]
+    for n in range(3):
+        assert np.array_equal(prev[n], A[n])
+
+
+def test_extrap_cap_limits_the_step():
+    """With a tiny cap the extrapolated point stays within cap of the current block."""
+    g = np.random.default_rng(33)
+    dims, R = (3, 4, 5), 2
+    X = g.gamma(3.0, 1.0, size=dims) + 0.05
+    A = [g.uniform(0.2, 1.0, size=(d, R)) for d in dims]
+    # a non-uniform displacement (a pure rescaling of a block leaves the KL update unchanged)
+    Ap = [a * g.uniform(0.3, 0.9, size=a.shape) for a in A]
+    # alpha -> 0 through the cap: the sweep approaches plain B-CoMM
+    got, _, _ = oracle.cp_mu_sweep_extrap(X, A, Ap, 1.0, alpha=1.0, cap=1e-14)
+    want, _ = oracle.cp_mu_sweep(X, A, 1.0)
+    for n in range(3):
+        assert np.linalg.norm(got[n] - want[n]) / np.linalg.norm(want[n]) < 1e-10
+    # a large cap leaves alpha = alpha_nes: the first block differs from plain B-CoMM
+    got2, _, _ = oracle.cp_mu_sweep_extrap(X, A, Ap, 1.0, alpha=1.0, cap=1e9)
+    assert np.linalg.norm(got2[0] - want[0]) / np.linalg.norm(want[0]) > 1e-3

@@ -327,18 +327,21 @@ def oracle_step_sample(X, A, cores, budget_s):
         oracle.cp_numden_rows(X, A, A, A, n, np.arange(probe, dtype=np.int64), BETA)
     per_row = (time.perf_counter() - t0) / (3 * probe)
     rows_per_mode = int(min(min(DIMS), max(probe, budget_s / (3 * per_row))))
+    # when every row fits the budget, the whole iteration is repeated (at most five times)
+    reps = max(1, min(5, int(budget_s / (3 * per_row * rows_per_mode))))
     total = 0.0
     spent = 0.0
-    for n in range(3):
-        rows = np.linspace(0, DIMS[n] - 1, rows_per_mode).astype(np.int64)
-        t0 = time.perf_counter()
-        oracle.cp_numden_rows(X, A, A, A, n, rows, BETA)
-        dt = time.perf_counter() - t0
-        spent += dt
-        total += dt * DIMS[n] / rows_per_mode
+    for _ in range(reps):
+        for n in range(3):
+            rows = np.linspace(0, DIMS[n] - 1, rows_per_mode).astype(np.int64)
+            t0 = time.perf_counter()
+            oracle.cp_numden_rows(X, A, A, A, n, rows, BETA)
+            dt = time.perf_counter() - t0
+            spent += dt
+            total += dt * DIMS[n] / rows_per_mode / reps
     desc = ("FP64 oracle (ntfo_cp_numden_rows, OpenMP) on %d evenly spaced rows per mode (of %s) of one J-CoMM "
-            "outer iteration (all three numerator/denominator row sets from the reference factors), scaled by "
-            "I_n/rows; %.1f s of CPU work" % (rows_per_mode, "x".join(map(str, DIMS)), spent))
+            "outer iteration (all three numerator/denominator row sets from the reference factors), %d time(s), "
+            "scaled by I_n/rows; %.1f s of CPU work" % (rows_per_mode, "x".join(map(str, DIMS)), reps, spent))
     return total, desc
 
 
@@ -535,6 +538,19 @@ def main():
             run_until.chunk_ms = [round(min(chunks), 2), round(max(chunks), 2)]
             run_until.host_s = host
             return Fr[:t].cpu().numpy(), ev[0].elapsed_time(ev[-1]) / 1e3 / t
+        class Extrap:
+            # extrapolated B-CoMM with the Nesterov-type weights, one state per factor list
+            def __init__(self):
+                self.prev, self.w = {}, {}
+
+            def __call__(self, X, beta, A, objective=None, ctx=None, precision="tf32", autotune=False):
+                k = id(A)
+                if k not in self.prev:
+                    self.prev[k] = [a.clone() for a in A]
+                    self.w[k] = ntf.nesterov_weights()
+                ntf.cp_mu_sweep_extrap(X, beta, A, self.prev[k], next(self.w[k]), objective=objective, ctx=ctx,
+                                       precision=precision, autotune=autotune)
+
         F_ref, per_ref = run_until(ntf.cp_mu_sweep, "fp32", n_ref, None)
         fstar = float(F_ref.min())
         target = fstar * (1 + 1e-4)
@@ -543,6 +559,7 @@ def main():
         for name, fn, p, cap in (("jcomm_" + prec, ntf.jcomm_outer, prec, 5000),
                                  ("jcomm_3xtf32", ntf.jcomm_outer, "3xtf32", 5000),
                                  ("block_mu_" + prec, ntf.cp_mu_sweep, prec, 2000),
+                                 ("block_mu_extrap_" + prec, Extrap(), prec, 2000),
                                  ("jcomm_fp32", ntf.jcomm_outer, "fp32", 2000)):
             if name not in runs:
                 runs[name] = run_until(fn, p, cap, target)

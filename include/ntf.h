@@ -129,6 +129,29 @@ int ntf_cp_mu_sweep(ntf_ctx *ctx, const ntf_tensor *X, float beta, int rank,
                     float *const *factors, const ntf_opts *opts, double *objective_dev,
                     void *stream);
 
+/* One extrapolated B-CoMM sweep for dense 3-way CP (Section "Going beyond: Majorization-
+ * Minimization with Extrapolation", item (i)).  For n = 1..3: with D = [A^(n) - Aprev^(n)]_+
+ * (componentwise positive part) and alpha_n = min(alpha, cap / (||D||_F + delta)), the block
+ * is first moved to Ahat = max(A^(n) + alpha_n D, eps); Xhat is rebuilt from Ahat and the
+ * current other blocks, P and Q formed as in ntf_cp_mu_sweep, and
+ * A^(n) <- max(Ahat * (Num / Den)^gamma(beta), eps) with Num / Den the contractions against the
+ * current other blocks.
+ *   factors:       host array of 3 device pointers, A^(n) is I_n x rank: the current iterate
+ *                  A^t on entry, A^(t+1) on exit
+ *   factors_prev:  host array of 3 device pointers, same shapes: the previous iterate A^(t-1) on
+ *                  entry, overwritten with the incoming A^t (ready for the next call); pass a copy
+ *                  of factors on the first call (no displacement: a plain B-CoMM sweep)
+ *   alpha:         extrapolation weight of this outer iteration (>= 0; e.g. a Nesterov-type
+ *                  sequence chosen by the caller), the same for every block
+ *   cap, delta:    displacement cap (>= 0; INFINITY disables it) and its regulariser (> 0)
+ *   objective_dev: device double or NULL; receives D_beta of the incoming iterate A^t (one more
+ *                  pass over X when requested).
+ * Dense order-3 tensors only, else NTF_ERR_UNSUPPORTED; other arguments and errors as
+ * ntf_cp_mu_sweep. */
+int ntf_cp_mu_sweep_extrap(ntf_ctx *ctx, const ntf_tensor *X, float beta, int rank, float *const *factors,
+                           float *const *factors_prev, float alpha, float cap, float delta,
+                           const ntf_opts *opts, double *objective_dev, void *stream);
+
 /* One block-MM sweep for Tucker (Theorem "Tucker block multiplicative updates";
  * Appendix C.2, eqs. (block_core_num_den), (block_Bn), (block_factor_num/den)): the
  * core first, then factors 1..N, each block rebuilt from the current blocks, followed

@@ -5,6 +5,7 @@ The computation lives in libntf.so (C ABI declared in include/ntf.h); this packa
 thin Python binding.  Build the library with ``paper_2602_14683_gb300.build.build()``.
 """
 from ._lib import (  # noqa: F401
-    Context, Coo, NtfError, beta_div, coo_stable_perm, cp_beta_div_noalloc, cp_mu_sweep, default_context, jcomm_outer,
+    Context, Coo, NtfError, beta_div, coo_stable_perm, cp_beta_div_noalloc, cp_mu_sweep, cp_mu_sweep_extrap,
+    default_context, jcomm_outer, nesterov_weights,
     make_opts, raw_library, tucker_mu_sweep, Server, LIB_PATH, EXPORTED,
 )

@@ -65,6 +65,8 @@ _sig = {
     "ntf_pass_timing": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "ntf_device_status": (C.c_int, [_P, _P]),
     "ntf_cp_mu_sweep": (C.c_int, [_P, C.POINTER(Tensor), C.c_float, C.c_int, C.POINTER(_P), C.POINTER(Opts), _P, _P]),
+    "ntf_cp_mu_sweep_extrap": (C.c_int, [_P, C.POINTER(Tensor), C.c_float, C.c_int, C.POINTER(_P), C.POINTER(_P),
+                                         C.c_float, C.c_float, C.c_float, C.POINTER(Opts), _P, _P]),
     "ntf_tucker_mu_sweep": (C.c_int, [_P, C.POINTER(Tensor), C.c_float, C.POINTER(C.c_int64), _P, C.POINTER(_P),
                                       C.POINTER(Opts), _P, _P]),
     "ntf_jcomm_outer": (C.c_int, [_P, C.c_int, C.POINTER(Tensor), C.c_float, C.c_int, C.POINTER(C.c_int64), _P,
@@ -218,6 +220,34 @@ def cp_mu_sweep(X, beta, factors, objective=None, ctx=None, stream=None, **opts)
     rank = int(factors[0].shape[1])
     ctx.check(_lib.ntf_cp_mu_sweep(ctx.h, C.byref(d.t), float(beta), rank, fp, C.byref(o),
                                    _out_ptr(objective), _stream(stream)))
+
+
+def cp_mu_sweep_extrap(X, beta, factors, factors_prev, alpha, cap=float("inf"), delta=1e-12, objective=None,
+                       ctx=None, stream=None, **opts):
+    """One extrapolated B-CoMM sweep (dense 3-way CP): factors A^t -> A^(t+1) in place,
+    factors_prev A^(t-1) -> A^t in place; `alpha` is this iteration's extrapolation weight,
+    capped per block at cap / (||[A - Aprev]_+|| + delta).  `objective` receives D_beta of the
+    incoming iterate."""
+    ctx = ctx or default_context()
+    d = _Desc(X)
+    fp = _ptrs(factors, "factors")
+    pp = _ptrs(factors_prev, "factors_prev")
+    o = make_opts(**opts)
+    rank = int(factors[0].shape[1])
+    ctx.check(_lib.ntf_cp_mu_sweep_extrap(ctx.h, C.byref(d.t), float(beta), rank, fp, pp, float(alpha), float(cap),
+                                          float(delta), C.byref(o), _out_ptr(objective), _stream(stream)))
+
+
+def nesterov_weights():
+    """Extrapolation weights alpha_t = (a_(t-1) - 1) / a_t with a_0 = 1 and
+    a_t = (1 + sqrt(1 + 4 a_(t-1)^2)) / 2 -- the accelerated-gradient momentum sequence of
+    Beck and Teboulle (FISTA) -- for t = 1, 2, ... (alpha_1 = 0)."""
+    import math
+    a = 1.0
+    while True:
+        a_next = (1.0 + math.sqrt(1.0 + 4.0 * a * a)) / 2.0
+        yield (a - 1.0) / a_next
+        a = a_next
 
 
 def tucker_mu_sweep(X, beta, core, factors, objective=None, ctx=None, stream=None, **opts):

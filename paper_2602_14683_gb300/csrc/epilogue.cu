@@ -169,6 +169,82 @@ __global__ void prep_kernel(PrepArgs p) {
     }
 }
 
+// Extrapolation (Section "Going beyond: Majorization-Minimization with Extrapolation"):
+// for each factor, D = pad([A - Aprev]_+) and FP64 partial sums of D^2 per row block (the
+// row blocking of prep_kernel); then Aprev <- A, the incoming iterate kept for the next call.
+__global__ void extrap_prep_kernel(ExtrapArgs x) {
+    __shared__ double sh[256];
+    int b = blockIdx.x, m = 0;
+    while (m < 2 && b >= row_blocks(x.rows[m], x.RP)) {
+        b -= row_blocks(x.rows[m], x.RP);
+        ++m;
+    }
+    const int RP = x.RP, G = blockDim.x / RP, t = threadIdx.x, r = t % RP, g = t / RP;
+    const int rows = x.rows[m], rpb = rows_per_block(rows, RP);
+    const int ibeg = b * rpb, iend = min(rows, ibeg + rpb);
+    double s2 = 0.0;
+    for (int i = ibeg + g; i < iend; i += G) {
+        float d = 0.0f;
+        if (r < x.R) {
+            const int64_t o = (int64_t)i * x.R + r;
+            const float a = x.A[m][o];
+            d = fmaxf(a - x.Aprev[m][o], 0.0f);
+            x.Aprev[m][o] = a;
+        }
+        x.D[m][(int64_t)i * RP + r] = d;
+        s2 += (double)d * (double)d;
+    }
+    const double tot = group_sum(sh, s2, RP, t);
+    if (t < RP) x.nrm[m][(int64_t)b * RP + t] = tot;
+}
+
+// E = max(F + alpha_n D, eps), alpha_n = min(alpha, cap / (||D||_F + delta)); every block
+// sums the norm partials of its factor in the same order, so alpha_n is the same everywhere.
+__global__ void extrap_apply_kernel(ExtrapArgs x) {
+    __shared__ double sh[256];
+    __shared__ double alpha_s;
+    int b = blockIdx.x, m = 0;
+    while (m < 2 && b >= row_blocks(x.rows[m], x.RP)) {
+        b -= row_blocks(x.rows[m], x.RP);
+        ++m;
+    }
+    const int RP = x.RP, t = threadIdx.x;
+    {
+        // ||D||^2: thread t adds partials t, t + 256, ... in order, then a fixed tree
+        const int n = row_blocks(x.rows[m], RP) * RP;
+        double s2 = 0.0;
+        for (int k = t; k < n; k += blockDim.x) s2 += x.nrm[m][k];
+        sh[t] = s2;
+        __syncthreads();
+        for (int w = 128; w >= 1; w >>= 1) {
+            if (t < w) sh[t] += sh[t + w];
+            __syncthreads();
+        }
+        if (t == 0) {
+            const double cap = (double)x.cap / (sqrt(sh[0]) + (double)x.delta);
+            alpha_s = (double)x.alpha < cap ? (double)x.alpha : cap;
+        }
+        __syncthreads();
+    }
+    const float alpha = (float)alpha_s;
+    const int rows = x.rows[m], rpb = rows_per_block(rows, RP);
+    const int64_t beg = (int64_t)b * rpb * RP, end = (int64_t)min(rows, (b + 1) * rpb) * RP;
+    for (int64_t e = beg + t; e < end; e += blockDim.x) {
+        const int r = (int)(e % RP);
+        x.E[m][e] = r < x.R ? fmaxf(fmaf(alpha, x.D[m][e], x.F[m][e]), x.eps) : 0.0f;
+    }
+}
+
+cudaError_t extrapolate(const ExtrapArgs &x, cudaStream_t s) {
+    int blocks = 0;
+    for (int m = 0; m < 3; ++m) blocks += row_blocks(x.rows[m], x.RP);
+    extrap_prep_kernel<<<blocks, 256, 0, s>>>(x);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    extrap_apply_kernel<<<blocks, 256, 0, s>>>(x);
+    return cudaGetLastError();
+}
+
 cudaError_t prep_factors(const PrepArgs &p, cudaStream_t s) {
     int blocks = 0;
     for (int m = 0; m < 3; ++m) blocks += row_blocks(p.rows[m], p.RP);

@@ -464,6 +464,73 @@ int cp_dense_jcomm(ntf_ctx *ctx, const ntf_tensor *X, float beta, int R, float *
     return NTF_OK;
 }
 
+// Extrapolated B-CoMM sweep (Section "Going beyond: Majorization-Minimization with
+// Extrapolation", item (i)): the block of mode n is first moved to
+// Ahat = max(A + alpha_n [A - Aprev]_+, eps), Xhat is rebuilt from Ahat and the current
+// other blocks, and Ahat is the multiplicative pre-factor.  All Ahat depend only on the
+// incoming iterate, so they are formed once, before the first pass.
+int cp_dense_mu_sweep_extrap(ntf_ctx *ctx, const ntf_tensor *X, float beta, int R, float *const *factors,
+                             float *const *factors_prev, float alpha, float cap, float delta, const ntf_opts &o,
+                             double *objective_dev, cudaStream_t st) {
+    const int bk = ntf::beta_kind(beta);
+    const int den = bk != ntf::BK_KL;
+    CpDense s{};
+    // the plan (and its autotuned table entry) of the plain sweep's first pass
+    const int tune_ms = ntf::PM_M1 | (objective_dev ? ntf::PM_OBJ : 0);
+    int rc = cp_dense_setup(ctx, X, R, false, den, o.precision, s, &o, bk, tune_ms);
+    if (rc) return rc;
+    const int dims[3] = {s.I, s.J, s.K};
+    ntf::ExtrapArgs x{};
+    for (int n = 0; n < 3; ++n) {
+        const size_t fb = sizeof(float) * (size_t)dims[n] * s.RP;
+        x.A[n] = factors[n];
+        x.Aprev[n] = factors_prev[n];
+        x.F[n] = s.F[n];
+        x.D[n] = (float *)ws_get(ctx, "cpXD" + std::to_string(n), fb);
+        x.E[n] = (float *)ws_get(ctx, "cpXE" + std::to_string(n), fb);
+        x.nrm[n] = (double *)ws_get(ctx, "cpXN" + std::to_string(n),
+                                    sizeof(double) * (size_t)ntf::row_blocks(dims[n], s.RP) * s.RP);
+        x.rows[n] = dims[n];
+        if (!x.D[n] || !x.E[n] || !x.nrm[n]) return fail(ctx, NTF_ERR_OOM, "workspace allocation failed");
+    }
+    x.R = R;
+    x.RP = s.RP;
+    x.alpha = alpha;
+    x.cap = cap;
+    x.delta = delta;
+    x.eps = (float)o.eps;
+    NTF_CUDA(ntf::prep_factors(prep_args(s, factors, false, false, !den), st));
+    ntf::Cp3Args a = cp_args(X, s, o, beta);
+    if (!s.tune.empty()) {  // timed on the unextrapolated blocks, before factors_prev changes
+        for (int m = 0; m < 3; ++m) a.rec[m] = a.num[m] = a.den[m] = s.F[m];
+        if ((rc = tune_plan(ctx, X, s, o, beta, a, tune_ms, den, st))) return rc;
+        a = cp_args(X, s, o, beta);
+    }
+    NTF_CUDA(ntf::extrapolate(x, st));
+    if (objective_dev) {
+        // D_beta of the incoming iterate: a mode-1 pass from the unextrapolated blocks (its
+        // partial sums are overwritten by the first extrapolated pass)
+        for (int m = 0; m < 3; ++m) a.rec[m] = a.num[m] = a.den[m] = s.F[m];
+        rc = launch_pass(ctx, s, a, ntf::PM_M1 | ntf::PM_OBJ, den, st);
+        if (rc) return rc;
+    }
+    for (int n = 0; n < 3; ++n) {
+        for (int m = 0; m < 3; ++m) a.rec[m] = a.num[m] = a.den[m] = s.F[m];
+        a.rec[n] = x.E[n];
+        const int ms = n == 0 ? ntf::PM_M1 : n == 1 ? ntf::PM_M2 : ntf::PM_M3;
+        rc = launch_pass(ctx, s, a, ms, den, st);
+        if (rc) return rc;
+        ntf::UpdArgs u = upd_args(s, n, beta, o, !den, x.E[n], factors[n]);
+        if (n == 0 && objective_dev) {
+            u.obj_parts = s.obj;
+            u.obj_n = s.plan.grid;
+            u.obj_out = objective_dev;
+        }
+        NTF_CUDA(ntf::mode_update(u, st));
+    }
+    return NTF_OK;
+}
+
 int cp_dense_beta_div(ntf_ctx *ctx, const ntf_tensor *X, float beta, int R, const float *const *factors,
                       const ntf_opts &o, double *out_dev, cudaStream_t st) {
     CpDense s{};
@@ -593,6 +660,27 @@ int ntf_cp_mu_sweep(ntf_ctx *ctx, const ntf_tensor *X, float beta, int rank, flo
         return ntf::coo_kl_sweep(ctx, X, rank, factors, o, objective_dev, st, /*jcomm=*/false);
     }
     return cp_dense_mu_sweep(ctx, X, beta, rank, factors, o, objective_dev, st);
+}
+
+int ntf_cp_mu_sweep_extrap(ntf_ctx *ctx, const ntf_tensor *X, float beta, int rank, float *const *factors,
+                           float *const *factors_prev, float alpha, float cap, float delta, const ntf_opts *opts,
+                           double *objective_dev, void *stream) {
+    ntf_opts o = resolve_opts(opts);
+    int rc = check_common(ctx, X, beta, o);
+    if (rc) return rc;
+    rc = check_factors(ctx, X, rank, factors);
+    if (rc) return rc;
+    if (X->kind != NTF_DENSE || X->order != 3)
+        return fail(ctx, NTF_ERR_UNSUPPORTED, "extrapolated sweeps are implemented for dense order-3 tensors");
+    if (!factors_prev) return fail(ctx, NTF_ERR_ARG, "previous-iterate array is NULL");
+    for (int n = 0; n < 3; ++n)
+        if (!factors_prev[n]) return fail(ctx, NTF_ERR_ARG, "previous iterate %d is NULL", n);
+    if (!(alpha >= 0.0f) || !(cap >= 0.0f) || !(delta > 0.0f))
+        return fail(ctx, NTF_ERR_ARG, "alpha and cap must be >= 0 and delta > 0");
+    cudaSetDevice(ctx->device);
+    ctx->err[0] = 0;
+    return cp_dense_mu_sweep_extrap(ctx, X, beta, rank, factors, factors_prev, alpha, cap, delta, o, objective_dev,
+                                    (cudaStream_t)stream);
 }
 
 int ntf_tucker_mu_sweep(ntf_ctx *ctx, const ntf_tensor *X, float beta, const int64_t *core_dims, float *core,

@@ -217,6 +217,21 @@ cudaError_t prep_factors(const PrepArgs &p, cudaStream_t s);
 // optional chi1 / chi2 outputs, an unpadded copy user_out (rows x R), FP64 column-sum
 // partials of the result cs_out[block][RP], and (block 0) the fixed-order FP64 sum of
 // obj_n objective partials into *obj_out.
+// Extrapolated block MM: per factor m < 3, A / Aprev are the user's I_m x R iterate and
+// previous iterate (Aprev is overwritten with A), F the padded iterate, D / E padded
+// workspaces (displacement, extrapolated block), nrm FP64 norm partials [row block][RP].
+struct ExtrapArgs {
+    const float *A[3];
+    float *Aprev[3];
+    const float *F[3];
+    float *D[3], *E[3];
+    double *nrm[3];
+    int rows[3];
+    int R, RP;
+    float alpha, cap, delta, eps;
+};
+cudaError_t extrapolate(const ExtrapArgs &x, cudaStream_t s);
+
 struct UpdArgs {
     MuEpiArgs e;
     const double *cs_in[2];

@@ -1,0 +1,60 @@
+"""Extrapolated B-CoMM sweeps (ntf_cp_mu_sweep_extrap) against the FP64 oracle.
+
+Same bars as the plain sweeps: FP32 path 1e-5 per factor after one sweep and on the
+objective of the incoming iterate, 1e-4 on a 15-iteration objective trajectory driven by
+the Nesterov-type weights; tensor-core path 1e-3 / 2e-4.  The previous-iterate buffers must
+come back holding the incoming iterate exactly.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests._gpu_util import dev, host, obj_tensor, rel_fro
+
+pytestmark = pytest.mark.gpu
+
+
+def _ntf():
+    import paper_2602_14683_gb300 as ntf
+    return ntf
+
+
+@pytest.mark.parametrize("prec,R,tol,tol_obj", [("fp32", 12, 1e-5, 1e-5), ("tf32", 32, 1e-3, 2e-4)])
+@pytest.mark.parametrize("beta", [0.5, 1.0, 1.5])
+@pytest.mark.parametrize("cap", [float("inf"), 0.3])
+def test_extrap_sweep_parity(prec, R, tol, tol_obj, beta, cap):
+    ntf = _ntf()
+    dims = (9, 150, 200)
+    X, _ = synth.cp_dense(dims, R, seed=R + 3, kind="gamma_noise")
+    A = synth.init_factors(dims, R, seed=R + 4)
+    g = np.random.default_rng(R)
+    Ap = [a * g.uniform(0.6, 1.1, size=a.shape) for a in A]
+    Ap = [np.float32(a).astype(np.float64) for a in Ap]
+    alpha = 0.7
+    want, want_prev, Fw = oracle.cp_mu_sweep_extrap(X, A, Ap, beta, alpha=alpha, cap=cap)
+    Ad, Pd, obj = [dev(a) for a in A], [dev(a) for a in Ap], obj_tensor()
+    ntf.cp_mu_sweep_extrap(dev(X), beta, Ad, Pd, alpha, cap=cap, objective=obj, precision=prec)
+    ntf.default_context().device_status()
+    errs = [rel_fro(host(Ad[n]), want[n]) for n in range(3)]
+    assert max(errs) <= tol, errs
+    for n in range(3):
+        assert np.array_equal(host(Pd[n]), np.float32(A[n]).astype(np.float64)), n
+    assert abs(obj.item() - Fw) / Fw <= tol_obj
+
+
+def test_extrap_trajectory_nesterov():
+    ntf = _ntf()
+    dims, R = (12, 90, 70), 6
+    X, _ = synth.cp_dense(dims, R, seed=41, kind="uniform_poisson")
+    A = synth.init_factors(dims, R, seed=42)
+    P = [a.copy() for a in A]
+    Ad, Pd, Xd, obj = [dev(a) for a in A], [dev(a) for a in A], dev(X), obj_tensor()
+    weights = ntf.nesterov_weights()
+    worst = 0.0
+    for t in range(15):
+        w = next(weights)
+        A, P, Fo = oracle.cp_mu_sweep_extrap(X, A, P, 1.0, alpha=w, cap=1.0)
+        ntf.cp_mu_sweep_extrap(Xd, 1.0, Ad, Pd, w, cap=1.0, objective=obj)
+        worst = max(worst, abs(obj.item() - Fo) / Fo)
+    assert worst <= 1e-4, worst

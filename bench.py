@@ -539,17 +539,18 @@ def main():
             run_until.host_s = host
             return Fr[:t].cpu().numpy(), ev[0].elapsed_time(ev[-1]) / 1e3 / t
         class Extrap:
-            # extrapolated B-CoMM with the Nesterov-type weights, one state per factor list
-            def __init__(self):
-                self.prev, self.w = {}, {}
+            # extrapolated sweeps / outer iterations with the Nesterov-type weights, one state
+            # per factor list
+            def __init__(self, fn):
+                self.fn, self.prev, self.w = fn, {}, {}
 
             def __call__(self, X, beta, A, objective=None, ctx=None, precision="tf32", autotune=False):
                 k = id(A)
                 if k not in self.prev:
                     self.prev[k] = [a.clone() for a in A]
                     self.w[k] = ntf.nesterov_weights()
-                ntf.cp_mu_sweep_extrap(X, beta, A, self.prev[k], next(self.w[k]), objective=objective, ctx=ctx,
-                                       precision=precision, autotune=autotune)
+                self.fn(X, beta, A, self.prev[k], next(self.w[k]), objective=objective, ctx=ctx,
+                        precision=precision, autotune=autotune)
 
         F_ref, per_ref = run_until(ntf.cp_mu_sweep, "fp32", n_ref, None)
         fstar = float(F_ref.min())
@@ -559,7 +560,8 @@ def main():
         for name, fn, p, cap in (("jcomm_" + prec, ntf.jcomm_outer, prec, 5000),
                                  ("jcomm_3xtf32", ntf.jcomm_outer, "3xtf32", 5000),
                                  ("block_mu_" + prec, ntf.cp_mu_sweep, prec, 2000),
-                                 ("block_mu_extrap_" + prec, Extrap(), prec, 2000),
+                                 ("block_mu_extrap_" + prec, Extrap(ntf.cp_mu_sweep_extrap), prec, 2000),
+                                 ("jcomm_extrap_" + prec, Extrap(ntf.cp_jcomm_outer_extrap), prec, 2000),
                                  ("jcomm_fp32", ntf.jcomm_outer, "fp32", 2000)):
             if name not in runs:
                 runs[name] = run_until(fn, p, cap, target)

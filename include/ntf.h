@@ -152,6 +152,20 @@ int ntf_cp_mu_sweep_extrap(ntf_ctx *ctx, const ntf_tensor *X, float beta, int ra
                            float *const *factors_prev, float alpha, float cap, float delta,
                            const ntf_opts *opts, double *objective_dev, void *stream);
 
+/* One J-CoMM outer iteration for dense 3-way CP from an extrapolated outer reference
+ * (Section "Going beyond: Majorization-Minimization with Extrapolation", item (iii)): every
+ * block is first moved to max(A^(n) + alpha_n [A^(n) - Aprev^(n)]_+, eps) with alpha_n as in
+ * ntf_cp_mu_sweep_extrap, and the outer iteration of ntf_jcomm_outer (Algorithm 2, opts->inner_L
+ * inner sweeps) runs with that point as its reference and as the inner iterations' start.
+ * The paper gives this variant as a heuristic without a convergence result.
+ *   factors / factors_prev / alpha / cap / delta: as ntf_cp_mu_sweep_extrap
+ *   objective_dev: device double or NULL; receives D_beta of the incoming iterate A^t (one more
+ *                  pass over X when requested).
+ * Dense order-3 tensors only, else NTF_ERR_UNSUPPORTED. */
+int ntf_cp_jcomm_outer_extrap(ntf_ctx *ctx, const ntf_tensor *X, float beta, int rank, float *const *factors,
+                              float *const *factors_prev, float alpha, float cap, float delta,
+                              const ntf_opts *opts, double *objective_dev, void *stream);
+
 /* One block-MM sweep for Tucker (Theorem "Tucker block multiplicative updates";
  * Appendix C.2, eqs. (block_core_num_den), (block_Bn), (block_factor_num/den)): the
  * core first, then factors 1..N, each block rebuilt from the current blocks, followed

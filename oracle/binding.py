@@ -33,6 +33,7 @@ def _load():
             "ntfo_cp_mu_sweep": (None, [C.c_int, _P, _P, C.c_int, _P, _D, _D, _D, _P]),
             "ntfo_cp_mu_sweep_extrap": (None, [C.c_int, _P, _P, C.c_int, _P, _P, _D, _D, _D, _D, _D, _D, _P]),
             "ntfo_cp_jcomm_outer": (None, [C.c_int, _P, _P, C.c_int, _P, _D, _D, _D, C.c_int, C.c_int, _P]),
+            "ntfo_cp_jcomm_outer_extrap": (None, [C.c_int, _P, _P, C.c_int, _P, _P, _D, _D, _D, C.c_int, _D, _D, _D, _P]),
             "ntfo_cp_numden_rows": (None, [C.c_int, _P, _P, C.c_int, _P, _P, _P, C.c_int, _D, _D, _D,
                                            C.c_int, _P, _P, _P]),
             "ntfo_tucker_full": (None, [C.c_int, _P, _P, _P, _P, _P]),
@@ -180,6 +181,20 @@ def cp_jcomm_outer(X, factors, beta, L=1, eps=1e-12, eps_x=1e-12, max_blocks=-1)
     _load().ntfo_cp_jcomm_outer(X.ndim, _ptr(_dims(X.shape)), _ptr(X), fs[0].shape[1], pa.c, float(beta),
                                 float(eps), float(eps_x), int(L), int(max_blocks), _ptr(f))
     return fs, float(f[0])
+
+
+def cp_jcomm_outer_extrap(X, factors, factors_prev, beta, alpha, cap=np.inf, delta=1e-12, L=1, eps=1e-12,
+                          eps_x=1e-12):
+    """One J-CoMM outer iteration from the extrapolated reference.  Returns (new_factors,
+    new_prev, objective of the incoming iterate)."""
+    X = _f64(X)
+    fs = [_f64(a).copy() for a in factors]
+    ps = [_f64(a).copy() for a in factors_prev]
+    f = np.zeros(1)
+    pa, pp = _PtrArray(fs), _PtrArray(ps)
+    _load().ntfo_cp_jcomm_outer_extrap(X.ndim, _ptr(_dims(X.shape)), _ptr(X), fs[0].shape[1], pa.c, pp.c, float(beta),
+                                       float(eps), float(eps_x), int(L), float(alpha), float(cap), float(delta), _ptr(f))
+    return fs, ps, float(f[0])
 
 
 def cp_numden_rows(X, recon, num_f, den_f, n, rows, beta, eps=1e-12, eps_x=1e-12):

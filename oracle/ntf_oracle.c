@@ -295,6 +295,37 @@ void ntfo_cp_jcomm_outer(int N, const int64_t *dims, const double *X, int R, dou
     free(Xt); free(Pt); free(Qt);
 }
 
+/* One J-CoMM outer iteration from an extrapolated outer reference (Section "Going beyond:
+ * Majorization-Minimization with Extrapolation", item (iii)).  A holds A^t (becomes the new
+ * iterate), Aprev holds A^(t-1) (becomes A^t).  Every block is first moved to
+ *   At^(n) = max(A^(n) + alpha_n [A^(n) - Aprev^(n)]_+, eps),
+ *   alpha_n = min(alpha_nes, cap / (||[A^(n) - Aprev^(n)]_+||_F + delta)),
+ * and the outer iteration of Algorithm 2 then runs with that point as its reference (and as
+ * the inner iterations' starting point).  F_in (may be NULL) receives the objective of the
+ * incoming iterate A^t.  Readings as for ntfo_cp_mu_sweep_extrap. */
+void ntfo_cp_jcomm_outer_extrap(int N, const int64_t *dims, const double *X, int R, double *const *A,
+                                double *const *Aprev, double beta, double eps, double eps_x, int L,
+                                double alpha_nes, double cap, double delta, double *F_in) {
+    if (F_in) *F_in = ntfo_cp_objective(N, dims, X, R, (const double *const *)A, beta, eps, eps_x);
+    for (int n = 0; n < N; ++n) {
+        const int64_t cnt = dims[n] * R;
+        double nrm2 = 0.0;
+        for (int64_t e = 0; e < cnt; ++e) {
+            const double d = A[n][e] - Aprev[n][e];
+            if (d > 0.0) nrm2 += d * d;
+        }
+        double alpha = cap / (sqrt(nrm2) + delta);
+        if (alpha_nes < alpha) alpha = alpha_nes;
+        for (int64_t e = 0; e < cnt; ++e) {
+            const double a = A[n][e], d = a - Aprev[n][e];
+            const double v = a + alpha * (d > 0.0 ? d : 0.0);
+            Aprev[n][e] = a;
+            A[n][e] = v > eps ? v : eps;
+        }
+    }
+    ntfo_cp_jcomm_outer(N, dims, X, R, A, beta, eps, eps_x, L, -1, NULL);
+}
+
 /* Num^(n)/Den^(n) rows of one block update, for a few selected rows i_n only, with P and
  * Q evaluated entry by entry from the factors given (recon factors Ar for Xhat, Bn for the
  * numerator contraction, Bd for the denominator contraction).  Used to check single rows

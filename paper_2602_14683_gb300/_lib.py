@@ -67,6 +67,8 @@ _sig = {
     "ntf_cp_mu_sweep": (C.c_int, [_P, C.POINTER(Tensor), C.c_float, C.c_int, C.POINTER(_P), C.POINTER(Opts), _P, _P]),
     "ntf_cp_mu_sweep_extrap": (C.c_int, [_P, C.POINTER(Tensor), C.c_float, C.c_int, C.POINTER(_P), C.POINTER(_P),
                                          C.c_float, C.c_float, C.c_float, C.POINTER(Opts), _P, _P]),
+    "ntf_cp_jcomm_outer_extrap": (C.c_int, [_P, C.POINTER(Tensor), C.c_float, C.c_int, C.POINTER(_P), C.POINTER(_P),
+                                            C.c_float, C.c_float, C.c_float, C.POINTER(Opts), _P, _P]),
     "ntf_tucker_mu_sweep": (C.c_int, [_P, C.POINTER(Tensor), C.c_float, C.POINTER(C.c_int64), _P, C.POINTER(_P),
                                       C.POINTER(Opts), _P, _P]),
     "ntf_jcomm_outer": (C.c_int, [_P, C.c_int, C.POINTER(Tensor), C.c_float, C.c_int, C.POINTER(C.c_int64), _P,
@@ -236,6 +238,21 @@ def cp_mu_sweep_extrap(X, beta, factors, factors_prev, alpha, cap=float("inf"), 
     rank = int(factors[0].shape[1])
     ctx.check(_lib.ntf_cp_mu_sweep_extrap(ctx.h, C.byref(d.t), float(beta), rank, fp, pp, float(alpha), float(cap),
                                           float(delta), C.byref(o), _out_ptr(objective), _stream(stream)))
+
+
+def cp_jcomm_outer_extrap(X, beta, factors, factors_prev, alpha, cap=float("inf"), delta=1e-12, objective=None,
+                          ctx=None, stream=None, **opts):
+    """One J-CoMM outer iteration (dense 3-way CP) from the extrapolated reference
+    max(A + alpha_n [A - Aprev]_+, eps); factors A^t -> new iterate, factors_prev -> A^t, in
+    place.  `objective` receives D_beta of the incoming iterate."""
+    ctx = ctx or default_context()
+    d = _Desc(X)
+    fp = _ptrs(factors, "factors")
+    pp = _ptrs(factors_prev, "factors_prev")
+    o = make_opts(**opts)
+    rank = int(factors[0].shape[1])
+    ctx.check(_lib.ntf_cp_jcomm_outer_extrap(ctx.h, C.byref(d.t), float(beta), rank, fp, pp, float(alpha), float(cap),
+                                             float(delta), C.byref(o), _out_ptr(objective), _stream(stream)))
 
 
 def nesterov_weights():

@@ -227,11 +227,21 @@ __global__ void extrap_apply_kernel(ExtrapArgs x) {
         __syncthreads();
     }
     const float alpha = (float)alpha_s;
+    const int G = blockDim.x / RP, r = t % RP, g = t / RP;
     const int rows = x.rows[m], rpb = rows_per_block(rows, RP);
-    const int64_t beg = (int64_t)b * rpb * RP, end = (int64_t)min(rows, (b + 1) * rpb) * RP;
-    for (int64_t e = beg + t; e < end; e += blockDim.x) {
-        const int r = (int)(e % RP);
-        x.E[m][e] = r < x.R ? fmaxf(fmaf(alpha, x.D[m][e], x.F[m][e]), x.eps) : 0.0f;
+    const int ibeg = b * rpb, iend = min(rows, ibeg + rpb);
+    double cs = 0.0;
+    for (int i = ibeg + g; i < iend; i += G) {
+        const int64_t e = (int64_t)i * RP + r;
+        const float v = r < x.R ? fmaxf(fmaf(alpha, x.D[m][e], x.F[m][e]), x.eps) : 0.0f;
+        x.E[m][e] = v;
+        if (x.E2[m]) x.E2[m][e] = v;
+        if (x.E3[m]) x.E3[m][e] = v;
+        cs += (double)v;
+    }
+    if (x.cs[m]) {
+        const double tot = group_sum(sh, cs, RP, t);
+        if (t < RP) x.cs[m][(int64_t)b * RP + t] = tot;
     }
 }
 

@@ -402,8 +402,15 @@ int cp_dense_mu_sweep(ntf_ctx *ctx, const ntf_tensor *X, float beta, int R, floa
     return NTF_OK;
 }
 
+// Outer-reference extrapolation of J-CoMM (Section "Going beyond: Majorization-Minimization
+// with Extrapolation", item (iii)): previous iterate and weights of the caller.
+struct JExtrap {
+    float *const *prev;
+    float alpha, cap, delta;
+};
+
 int cp_dense_jcomm(ntf_ctx *ctx, const ntf_tensor *X, float beta, int R, float *const *factors,
-                   const ntf_opts &o, double *objective_dev, cudaStream_t st) {
+                   const ntf_opts &o, double *objective_dev, cudaStream_t st, const JExtrap *xe = nullptr) {
     const int bk = ntf::beta_kind(beta);
     const bool kl = bk == ntf::BK_KL;
     CpDense s{};
@@ -421,6 +428,51 @@ int cp_dense_jcomm(ntf_ctx *ctx, const ntf_tensor *X, float beta, int R, float *
         if ((rc = tune_plan(ctx, X, s, o, beta, a, tune_ms, kl ? 0 : 1, st))) return rc;
         a = cp_args(X, s, o, beta);
     }
+    double *obj_parts = s.obj;
+    if (xe) {
+        // objective of the incoming iterate, from a mode-1 pass over the unextrapolated blocks
+        // with outputs of its own; then the reference (and the starting point of the inner
+        // iterations) moves to max(A + alpha_n [A - Aprev]_+, eps), written over Ft (and the chi
+        // copies C1, C2), with the column sums of the new reference for the KL denominators
+        const int dims[3] = {s.I, s.J, s.K};
+        if (objective_dev) {
+            const size_t pb = sizeof(float) * (size_t)s.plan.parts1 * s.I * s.RP;
+            float *scr = (float *)ws_get(ctx, "cpXscr", pb);
+            float *scr2 = kl ? nullptr : (float *)ws_get(ctx, "cpXscr2", pb);
+            obj_parts = (double *)ws_get(ctx, "cpXobj", sizeof(double) * (size_t)s.plan.grid);
+            if (!scr || (!kl && !scr2) || !obj_parts) return fail(ctx, NTF_ERR_OOM, "workspace allocation failed");
+            ntf::Cp3Args ao = a;
+            for (int m = 0; m < 3; ++m) ao.rec[m] = ao.num[m] = ao.den[m] = s.F[m];
+            ao.p1n = scr;
+            ao.p1d = scr2;
+            ao.obj = obj_parts;
+            rc = launch_pass(ctx, s, ao, ntf::PM_M1 | ntf::PM_OBJ, kl ? 0 : 1, st);
+            if (rc) return rc;
+        }
+        ntf::ExtrapArgs x{};
+        for (int n = 0; n < 3; ++n) {
+            const size_t fb = sizeof(float) * (size_t)dims[n] * s.RP;
+            x.A[n] = factors[n];
+            x.Aprev[n] = xe->prev[n];
+            x.F[n] = s.F[n];
+            x.D[n] = (float *)ws_get(ctx, "cpXD" + std::to_string(n), fb);
+            x.E[n] = s.Ft[n];
+            x.E2[n] = kl ? nullptr : s.C1[n];
+            x.E3[n] = kl ? nullptr : s.C2[n];
+            x.nrm[n] = (double *)ws_get(ctx, "cpXN" + std::to_string(n),
+                                        sizeof(double) * (size_t)ntf::row_blocks(dims[n], s.RP) * s.RP);
+            x.cs[n] = kl ? s.cs[n] : nullptr;
+            x.rows[n] = dims[n];
+            if (!x.D[n] || !x.nrm[n]) return fail(ctx, NTF_ERR_OOM, "workspace allocation failed");
+        }
+        x.R = R;
+        x.RP = s.RP;
+        x.alpha = xe->alpha;
+        x.cap = xe->cap;
+        x.delta = xe->delta;
+        x.eps = (float)o.eps;
+        NTF_CUDA(ntf::extrapolate(x, st));
+    }
     auto update = [&](int l, int n) {
         ntf::UpdArgs u = upd_args(s, n, beta, o, kl, s.Ft[n], l == o.inner_L - 1 ? factors[n] : nullptr);
         if (!kl) {
@@ -428,8 +480,8 @@ int cp_dense_jcomm(ntf_ctx *ctx, const ntf_tensor *X, float beta, int R, float *
             u.e.chi1_out = s.C1[n];
             u.e.chi2_out = s.C2[n];
         }
-        if (l == 0 && n == 0 && objective_dev) {  // D_beta at the reference, from the first pass
-            u.obj_parts = s.obj;
+        if (l == 0 && n == 0 && objective_dev) {  // D_beta at the reference (incoming iterate)
+            u.obj_parts = obj_parts;
             u.obj_n = s.plan.grid;
             u.obj_out = objective_dev;
         }
@@ -681,6 +733,27 @@ int ntf_cp_mu_sweep_extrap(ntf_ctx *ctx, const ntf_tensor *X, float beta, int ra
     ctx->err[0] = 0;
     return cp_dense_mu_sweep_extrap(ctx, X, beta, rank, factors, factors_prev, alpha, cap, delta, o, objective_dev,
                                     (cudaStream_t)stream);
+}
+
+int ntf_cp_jcomm_outer_extrap(ntf_ctx *ctx, const ntf_tensor *X, float beta, int rank, float *const *factors,
+                              float *const *factors_prev, float alpha, float cap, float delta, const ntf_opts *opts,
+                              double *objective_dev, void *stream) {
+    ntf_opts o = resolve_opts(opts);
+    int rc = check_common(ctx, X, beta, o);
+    if (rc) return rc;
+    rc = check_factors(ctx, X, rank, factors);
+    if (rc) return rc;
+    if (X->kind != NTF_DENSE || X->order != 3)
+        return fail(ctx, NTF_ERR_UNSUPPORTED, "extrapolated outer iterations are implemented for dense order-3 tensors");
+    if (!factors_prev) return fail(ctx, NTF_ERR_ARG, "previous-iterate array is NULL");
+    for (int n = 0; n < 3; ++n)
+        if (!factors_prev[n]) return fail(ctx, NTF_ERR_ARG, "previous iterate %d is NULL", n);
+    if (!(alpha >= 0.0f) || !(cap >= 0.0f) || !(delta > 0.0f))
+        return fail(ctx, NTF_ERR_ARG, "alpha and cap must be >= 0 and delta > 0");
+    cudaSetDevice(ctx->device);
+    ctx->err[0] = 0;
+    const JExtrap xe{factors_prev, alpha, cap, delta};
+    return cp_dense_jcomm(ctx, X, beta, rank, factors, o, objective_dev, (cudaStream_t)stream, &xe);
 }
 
 int ntf_tucker_mu_sweep(ntf_ctx *ctx, const ntf_tensor *X, float beta, const int64_t *core_dims, float *core,

@@ -220,12 +220,16 @@ cudaError_t prep_factors(const PrepArgs &p, cudaStream_t s);
 // Extrapolated block MM: per factor m < 3, A / Aprev are the user's I_m x R iterate and
 // previous iterate (Aprev is overwritten with A), F the padded iterate, D / E padded
 // workspaces (displacement, extrapolated block), nrm FP64 norm partials [row block][RP].
+// Optional: E2 / E3 receive copies of E, cs the FP64 column-sum partials of E ([row block][RP],
+// the row blocking of prep_factors).
 struct ExtrapArgs {
     const float *A[3];
     float *Aprev[3];
     const float *F[3];
     float *D[3], *E[3];
+    float *E2[3], *E3[3];
     double *nrm[3];
+    double *cs[3];
     int rows[3];
     int R, RP;
     float alpha, cap, delta, eps;

@@ -58,3 +58,24 @@ def test_extrap_trajectory_nesterov():
         ntf.cp_mu_sweep_extrap(Xd, 1.0, Ad, Pd, w, cap=1.0, objective=obj)
         worst = max(worst, abs(obj.item() - Fo) / Fo)
     assert worst <= 1e-4, worst
+
+
+@pytest.mark.parametrize("prec,R,tol,tol_obj", [("fp32", 12, 1e-5, 1e-5), ("tf32", 32, 1e-3, 2e-4)])
+@pytest.mark.parametrize("beta", [0.5, 1.0, 1.5])
+@pytest.mark.parametrize("L", [1, 2])
+def test_jcomm_extrap_parity(prec, R, tol, tol_obj, beta, L):
+    ntf = _ntf()
+    dims = (9, 150, 200)
+    X, _ = synth.cp_dense(dims, R, seed=R + 5, kind="gamma_noise")
+    A = synth.init_factors(dims, R, seed=R + 6)
+    g = np.random.default_rng(R + 1)
+    Ap = [np.float32(a * g.uniform(0.6, 1.1, size=a.shape)).astype(np.float64) for a in A]
+    want, want_prev, Fw = oracle.cp_jcomm_outer_extrap(X, A, Ap, beta, alpha=0.7, cap=0.5, L=L)
+    Ad, Pd, obj = [dev(a) for a in A], [dev(a) for a in Ap], obj_tensor()
+    ntf.cp_jcomm_outer_extrap(dev(X), beta, Ad, Pd, 0.7, cap=0.5, objective=obj, precision=prec, inner_L=L)
+    ntf.default_context().device_status()
+    errs = [rel_fro(host(Ad[n]), want[n]) for n in range(3)]
+    assert max(errs) <= tol, errs
+    for n in range(3):
+        assert np.array_equal(host(Pd[n]), np.float32(A[n]).astype(np.float64)), n
+    assert abs(obj.item() - Fw) / Fw <= tol_obj

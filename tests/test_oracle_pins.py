@@ -544,3 +544,28 @@ def test_extrap_cap_limits_the_step():
     # a large cap leaves alpha = alpha_nes: the first block differs from plain B-CoMM
     got2, _, _ = oracle.cp_mu_sweep_extrap(X, A, Ap, 1.0, alpha=1.0, cap=1e9)
     assert np.linalg.norm(got2[0] - want[0]) / np.linalg.norm(want[0]) > 1e-3
+
+
+def test_jcomm_extrap_is_jcomm_from_the_extrapolated_reference():
+    """Outer-reference extrapolation = J-CoMM started from max(A + alpha_n [A - Aprev]_+, eps),
+    alpha_n recomputed here from its definition; alpha = 0 is plain J-CoMM exactly."""
+    g = np.random.default_rng(34)
+    dims, R = (4, 5, 3), 3
+    X = g.gamma(3.0, 1.0, size=dims) + 0.05
+    A = [g.uniform(0.2, 1.0, size=(d, R)) for d in dims]
+    Ap = [a * g.uniform(0.4, 1.2, size=a.shape) for a in A]
+    for beta in (0.5, 1.0, 1.5):
+        want, Fw = oracle.cp_jcomm_outer(X, A, beta, L=2)
+        got, prev, F = oracle.cp_jcomm_outer_extrap(X, A, Ap, beta, alpha=0.0, L=2)
+        assert all(np.array_equal(x, y) for x, y in zip(got, want)) and F == Fw
+        alpha, cap = 0.8, 0.2
+        ref = []
+        for a, p in zip(A, Ap):
+            D = np.maximum(a - p, 0.0)
+            ref.append(np.maximum(a + min(alpha, cap / (np.linalg.norm(D) + 1e-12)) * D, 1e-12))
+        want2, _ = oracle.cp_jcomm_outer(X, ref, beta, L=2)
+        got2, prev2, F2 = oracle.cp_jcomm_outer_extrap(X, A, Ap, beta, alpha=alpha, cap=cap, L=2)
+        for n in range(3):
+            assert np.allclose(got2[n], want2[n], rtol=1e-13, atol=0.0)
+            assert np.array_equal(prev2[n], A[n])
+        assert F2 == Fw

@@ -501,6 +501,80 @@ void ntfo_tucker_mu_sweep(int N, const int64_t *dims, const double *X, const int
     free(Xhat); free(P); free(Q);
 }
 
+/* Z <- max(Z + alpha [Z - Zprev]_+, eps) with alpha = min(alpha_nes, cap / (||[Z - Zprev]_+||_F
+ * + delta)) (Section "Going beyond: Majorization-Minimization with Extrapolation"). */
+static void extrap_block(int64_t cnt, double *Z, const double *Zprev, double alpha_nes, double cap, double delta,
+                         double eps) {
+    double nrm2 = 0.0;
+    for (int64_t e = 0; e < cnt; ++e) {
+        const double d = Z[e] - Zprev[e];
+        if (d > 0.0) nrm2 += d * d;
+    }
+    double alpha = cap / (sqrt(nrm2) + delta);
+    if (alpha_nes < alpha) alpha = alpha_nes;
+    for (int64_t e = 0; e < cnt; ++e) {
+        const double d = Z[e] - Zprev[e];
+        const double v = Z[e] + alpha * (d > 0.0 ? d : 0.0);
+        Z[e] = v > eps ? v : eps;
+    }
+}
+
+/* One extrapolated block-MM sweep for Tucker (Section "Going beyond: Majorization-
+ * Minimization with Extrapolation", item (ii)): the core, then factors 1..N; before its update
+ * each block is moved to its extrapolated point (the displacement from the previous outer
+ * iterate, positive part, capped weight), Xhat is rebuilt with that block and the current
+ * others, and the extrapolated block is the multiplicative pre-factor (Theorem "Tucker block
+ * multiplicative updates", Appendix C.2).  G, A: G^t, A^t in, the new iterate out; Gprev, Aprev:
+ * the previous outer iterate in, G^t, A^t out.  F_in (may be NULL): objective of the incoming
+ * iterate. */
+void ntfo_tucker_mu_sweep_extrap(int N, const int64_t *dims, const double *X, const int64_t *J, double *G,
+                                 double *const *A, double *Gprev, double *const *Aprev, double beta, double eps,
+                                 double eps_x, double alpha_nes, double cap, double delta, double *F_in) {
+    int64_t cnt = numel(N, dims), cj = numel(N, J);
+    double *Xhat = (double *)malloc(sizeof(double) * cnt);
+    double *P = (double *)malloc(sizeof(double) * cnt);
+    double *Q = (double *)malloc(sizeof(double) * cnt);
+    const double *const *Ac = (const double *const *)A;
+    if (F_in) {
+        ntfo_tucker_full(N, dims, J, G, Ac, Xhat);
+        *F_in = objective_from_full(cnt, X, Xhat, beta, eps, eps_x);
+    }
+    double *G0 = (double *)malloc(sizeof(double) * cj), *A0[NTFO_MAXN];
+    memcpy(G0, G, sizeof(double) * cj);
+    for (int n = 0; n < N; ++n) {
+        A0[n] = (double *)malloc(sizeof(double) * dims[n] * J[n]);
+        memcpy(A0[n], A[n], sizeof(double) * dims[n] * J[n]);
+    }
+    /* core block at its extrapolated point */
+    extrap_block(cj, G, Gprev, alpha_nes, cap, delta, eps);
+    ntfo_tucker_full(N, dims, J, G, Ac, Xhat);
+    powers(cnt, X, Xhat, beta, eps, eps_x, P, Q);
+    double *pc = (double *)malloc(sizeof(double) * cj), *qc = (double *)malloc(sizeof(double) * cj);
+    ntfo_tucker_core_contr(N, dims, P, J, Ac, pc);
+    ntfo_tucker_core_contr(N, dims, Q, J, Ac, qc);
+    ntfo_mu_apply(cj, G, pc, qc, beta, eps, G);
+    free(pc); free(qc);
+    /* factor blocks */
+    for (int n = 0; n < N; ++n) {
+        extrap_block(dims[n] * J[n], A[n], Aprev[n], alpha_nes, cap, delta, eps);
+        ntfo_tucker_full(N, dims, J, G, Ac, Xhat);
+        powers(cnt, X, Xhat, beta, eps, eps_x, P, Q);
+        double *num = (double *)malloc(sizeof(double) * dims[n] * J[n]);
+        double *den = (double *)malloc(sizeof(double) * dims[n] * J[n]);
+        ntfo_tucker_factor_contr(N, dims, P, J, G, Ac, n, num);
+        ntfo_tucker_factor_contr(N, dims, Q, J, G, Ac, n, den);
+        ntfo_mu_apply(dims[n] * J[n], A[n], num, den, beta, eps, A[n]);
+        free(num); free(den);
+    }
+    memcpy(Gprev, G0, sizeof(double) * cj);
+    free(G0);
+    for (int n = 0; n < N; ++n) {
+        memcpy(Aprev[n], A0[n], sizeof(double) * dims[n] * J[n]);
+        free(A0[n]);
+    }
+    free(Xhat); free(P); free(Q);
+}
+
 /* Tucker J-CoMM outer iteration (Algorithm 2; Appendix C.3): reference tensors once
  * (eq. (ref_PQ)); per inner block the transformed blocks G_(1), G_(2), A_(1), A_(2);
  * core by eqs. (jmm_core_num)/(jmm_core_den), factors by eqs. (jmm_factor_num)/

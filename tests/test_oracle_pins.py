@@ -569,3 +569,42 @@ def test_jcomm_extrap_is_jcomm_from_the_extrapolated_reference():
             assert np.allclose(got2[n], want2[n], rtol=1e-13, atol=0.0)
             assert np.array_equal(prev2[n], A[n])
         assert F2 == Fw
+
+
+def test_tucker_extrap_reduces_to_block_mm_and_blocks_are_argmins():
+    """Extrapolated Tucker sweep: alpha = 0 is the plain sweep exactly; otherwise every block
+    (core, then factors) minimises the block surrogate built at its extrapolated point."""
+    g = np.random.default_rng(35)
+    dims, J = (4, 3, 5), (2, 3, 2)
+    X = g.gamma(3.0, 1.0, size=dims) + 0.05
+    G = g.uniform(0.2, 1.0, size=J)
+    A = [g.uniform(0.2, 1.0, size=(d, j)) for d, j in zip(dims, J)]
+    Gp = G * g.uniform(0.5, 1.2, size=G.shape)
+    Ap = [a * g.uniform(0.5, 1.2, size=a.shape) for a in A]
+    Gw, Aw, Fw = oracle.tucker_mu_sweep(X, G, A, 1.5)
+    G0, A0, Gp0, Ap0, F0 = oracle.tucker_mu_sweep_extrap(X, G, A, Gp, Ap, 1.5, alpha=0.0)
+    assert np.array_equal(G0, Gw) and all(np.array_equal(x, y) for x, y in zip(A0, Aw)) and F0 == Fw
+    assert np.array_equal(Gp0, G) and all(np.array_equal(x, y) for x, y in zip(Ap0, A))
+    for beta in (0.5, 1.0, 1.5):
+        alpha, cap = 0.7, 0.3
+        Gn, An, _, _, _ = oracle.tucker_mu_sweep_extrap(X, G, A, Gp, Ap, beta, alpha=alpha, cap=cap)
+
+        def hat(z, zp):
+            D = np.maximum(z - zp, 0.0)
+            return np.maximum(z + min(alpha, cap / (np.linalg.norm(D) + 1e-12)) * D, 1e-12)
+        Gh = hat(G, Gp)
+        zt = _tucker_contribs(Gh, A)
+        _assert_block_argmin(lambda blk: _surrogate(X, _tucker_contribs(blk, A), zt, beta), Gn)
+        cur = list(A)
+        for n in range(3):
+            ref = list(cur)
+            ref[n] = hat(A[n], Ap[n])
+            zt = _tucker_contribs(Gn, ref)
+
+            def Gfun(blk, ref=ref, n=n, zt=zt):
+                B = list(ref)
+                B[n] = blk
+                return _surrogate(X, _tucker_contribs(Gn, B), zt, beta)
+
+            _assert_block_argmin(Gfun, An[n])
+            cur[n] = An[n]

@@ -262,12 +262,17 @@ cudaError_t prep_factors(const PrepArgs &p, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// One block per row block of the mode, plus (when the objective is wanted) one more block
+// that only sums the objective partials, so that this reduction is off the critical path.
+// A thread's loads of the column-sum partials and of its first row's partial sums are all
+// issued before the first barrier.
 __global__ void mode_update_kernel(UpdArgs u) {
     __shared__ double sh[256];
     __shared__ float den_s[64];
     const MuEpiArgs &e = u.e;
     const int RP = e.RP, G = blockDim.x / RP, t = threadIdx.x, r = t % RP, g = t / RP;
-    if (u.obj_out && blockIdx.x == 0) {  // same order as reduce_obj_kernel
+    const int nrb = row_blocks(e.rows, RP);
+    if ((int)blockIdx.x == nrb) {  // the objective block: same order as reduce_obj_kernel
         double v = 0.0;
         for (int k = t; k < u.obj_n; k += blockDim.x) v += u.obj_parts[k];
 #pragma unroll
@@ -279,12 +284,53 @@ __global__ void mode_update_kernel(UpdArgs u) {
             for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += sh[w];
             *u.obj_out = tot;
         }
-        __syncthreads();
+        return;
     }
+    const int rpb = rows_per_block(e.rows, RP);
+    const int ibeg = blockIdx.x * rpb, iend = min(e.rows, ibeg + rpb);
+    const int64_t stride = (int64_t)e.rows * RP;
+    // partials in batches of 16, each batch added as a fixed tree and the batch sums in order
+    // (a fixed order for every run); 32 loads are in flight at once
+    auto load32 = [&](const float *src, int64_t o, int p0, float *v) {
+#pragma unroll
+        for (int k = 0; k < 32; ++k) v[k] = p0 + k < e.n_parts ? src[(int64_t)(p0 + k) * stride + o] : 0.0f;
+    };
+    auto add32 = [&](int p0, float *v, float acc) {
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            if (p0 + 16 * b >= e.n_parts) break;
+            float *w16 = v + 16 * b;
+#pragma unroll
+            for (int w = 8; w >= 1; w >>= 1)
+#pragma unroll
+                for (int k = 0; k < w; ++k) w16[k] += w16[k + w];
+            acc += w16[0];
+        }
+        return acc;
+    };
+    auto psum = [&](const float *src, int64_t o, float *first) {  // first: loaded batch 0 or null
+        float acc = 0.0f;
+        for (int p0 = 0; p0 < e.n_parts; p0 += 32) {
+            float v[32];
+            if (p0 == 0 && first) {
+#pragma unroll
+                for (int k = 0; k < 32; ++k) v[k] = first[k];
+            } else {
+                load32(src, o, p0, v);
+            }
+            acc = add32(p0, v, acc);
+        }
+        return acc;
+    };
+    // the first row's numerator partials, loaded ahead of the column-sum phase
+    const int i_first = ibeg + g;
+    const bool pre = i_first < iend && r < e.R;
+    float first[32];
+    if (pre) load32(e.pn, (int64_t)i_first * RP + r, 0, first);
     if (u.n_cs > 0) {
         // each factor's column sums: thread (g, r) adds blocks g, g + G, ..., then the G
-        // group sums are added in order (fixed order, the same in every block)
-        // the loads of both factors' first eight blocks are issued together
+        // group sums are added in order (fixed order, the same in every block); the loads of
+        // both factors' first eight blocks are issued together
         double sum[2] = {0.0, 0.0};
         for (int b0 = g; b0 < u.cs_nb[0] || (u.n_cs > 1 && b0 < u.cs_nb[1]); b0 += 8 * G) {
             double v[2][8];
@@ -305,41 +351,16 @@ __global__ void mode_update_kernel(UpdArgs u) {
         if (t < RP) den_s[t] = (float)prod;
         __syncthreads();
     }
-    const int rpb = rows_per_block(e.rows, RP);
-    const int ibeg = blockIdx.x * rpb, iend = min(e.rows, ibeg + rpb);
-    const int64_t stride = (int64_t)e.rows * RP;
     double cs = 0.0;
     for (int i = ibeg + g; i < iend; i += G) {
         const int64_t o = (int64_t)i * RP + r;
         float v = 0.0f, c1 = 0.0f, c2 = 0.0f;
         if (r < e.R) {
-            // partials in batches of 16, each batch added as a fixed tree and the batch sums
-            // in order (a fixed order for every run); two batches (32 loads) are in flight at
-            // once
-            auto psum = [&](const float *src) {
-                float acc = 0.0f;
-                for (int p0 = 0; p0 < e.n_parts; p0 += 32) {
-                    float v[32];
-#pragma unroll
-                    for (int k = 0; k < 32; ++k) v[k] = p0 + k < e.n_parts ? src[(int64_t)(p0 + k) * stride + o] : 0.0f;
-#pragma unroll
-                    for (int b = 0; b < 2; ++b) {
-                        if (p0 + 16 * b >= e.n_parts) break;
-                        float *w16 = v + 16 * b;
-#pragma unroll
-                        for (int w = 8; w >= 1; w >>= 1)
-#pragma unroll
-                            for (int k = 0; k < w; ++k) w16[k] += w16[k + w];
-                        acc += w16[0];
-                    }
-                }
-                return acc;
-            };
-            const float num = psum(e.pn);
+            const float num = psum(e.pn, o, (pre && i == i_first) ? first : nullptr);
             float den;
             if (u.n_cs > 0) den = den_s[r];
             else if (e.den_closed) den = e.den_closed[r];
-            else den = psum(e.pd);
+            else den = psum(e.pd, o, nullptr);
             const float ratio = __fdiv_rn(num, den);
             float m;
             if (e.gamma == 1.0f) m = ratio;
@@ -362,7 +383,7 @@ __global__ void mode_update_kernel(UpdArgs u) {
 }
 
 cudaError_t mode_update(const UpdArgs &u, cudaStream_t s) {
-    mode_update_kernel<<<row_blocks(u.e.rows, u.e.RP), 256, 0, s>>>(u);
+    mode_update_kernel<<<row_blocks(u.e.rows, u.e.RP) + (u.obj_out ? 1 : 0), 256, 0, s>>>(u);
     return cudaGetLastError();
 }
 

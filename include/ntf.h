@@ -178,6 +178,23 @@ int ntf_tucker_mu_sweep(ntf_ctx *ctx, const ntf_tensor *X, float beta, const int
                         float *core, float *const *factors, const ntf_opts *opts,
                         double *objective_dev, void *stream);
 
+/* One extrapolated block-MM sweep for dense 3-way Tucker (Section "Going beyond:
+ * Majorization-Minimization with Extrapolation", item (ii)): the core, then factors 1..3;
+ * before its update each block Z is moved to max(Z + alpha_Z [Z - Zprev]_+, eps) with
+ * alpha_Z = min(alpha, cap / (||[Z - Zprev]_+||_F + delta)), the reconstruction uses that
+ * block and the current others, and it is the multiplicative pre-factor (Theorem "Tucker block
+ * multiplicative updates").
+ *   core / factors: the current iterate in, the new iterate out (as ntf_tucker_mu_sweep)
+ *   core_prev / factors_prev: the previous iterate in (same shapes), overwritten with the
+ *                  incoming iterate; pass copies of core / factors on the first call
+ *   alpha / cap / delta: as ntf_cp_mu_sweep_extrap
+ *   objective_dev: device double or NULL; receives D_beta of the incoming iterate (one more
+ *                  pass over X when requested).
+ * Dense N = 3 only. */
+int ntf_tucker_mu_sweep_extrap(ntf_ctx *ctx, const ntf_tensor *X, float beta, const int64_t *core_dims, float *core,
+                               float *const *factors, float *core_prev, float *const *factors_prev, float alpha,
+                               float cap, float delta, const ntf_opts *opts, double *objective_dev, void *stream);
+
 /* One J-CoMM outer iteration (Algorithm 2; Section 5.3; Appendix C.3): the reference is
  * the incoming iterate, Ptilde = X*Xtilde^(beta-2) and Qtilde = Xtilde^(beta-1) are
  * fixed for opts->inner_L inner sweeps; every inner block update uses chi1 of the

@@ -14,5 +14,8 @@ int tucker_run(ntf_ctx *ctx, const ntf_tensor *X, float beta, const int64_t *cor
                float *const *factors, const ntf_opts &o, double *objective_dev, cudaStream_t st, bool jcomm);
 int tucker_beta_div(ntf_ctx *ctx, const ntf_tensor *X, float beta, const int64_t *core_dims, const float *core,
                     const float *const *factors, const ntf_opts &o, double *out_dev, cudaStream_t st);
+int tucker_run_extrap(ntf_ctx *ctx, const ntf_tensor *X, float beta, const int64_t *core_dims, float *core,
+                      float *const *factors, float *core_prev, float *const *factors_prev, float alpha, float cap,
+                      float delta, const ntf_opts &o, double *objective_dev, cudaStream_t st);
 void tucker_release(ntf_ctx *ctx);
 }  // namespace ntf

@@ -374,6 +374,46 @@ __global__ void sum_parts_kernel(const float *parts, int n_parts, int64_t n, flo
     out[t] = acc;
 }
 
+// Extrapolation of one flat block (Section "Going beyond: Majorization-Minimization with
+// Extrapolation"): D = [A - Aprev]_+ and FP64 partial sums of D^2 per CTA, Aprev <- A; then
+// E = max(A + alpha D, eps), alpha = min(alpha_nes, cap / (||D||_F + delta)), every CTA
+// summing the partials in the same order.
+constexpr int XB = 64;  // CTAs of the flat extrapolation kernels
+
+__global__ void extrap_flat_prep_kernel(const float *A, float *Aprev, float *D, int64_t n, double *part) {
+    __shared__ double sh[256];
+    double s2 = 0.0;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        const float a = A[t];
+        const float d = fmaxf(a - Aprev[t], 0.0f);
+        Aprev[t] = a;
+        D[t] = d;
+        s2 += (double)d * (double)d;
+    }
+    sh[threadIdx.x] = s2;
+    __syncthreads();
+    for (int w = 128; w >= 1; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+__global__ void extrap_flat_apply_kernel(const float *A, const float *D, int64_t n, const double *part, float alpha_nes,
+                                         float cap, float delta, float eps, float *E) {
+    __shared__ float alpha_s;
+    if (threadIdx.x == 0) {
+        double s2 = 0.0;
+        for (int b = 0; b < XB; ++b) s2 += part[b];
+        const double c = (double)cap / (sqrt(s2) + (double)delta);
+        alpha_s = (float)((double)alpha_nes < c ? (double)alpha_nes : c);
+    }
+    __syncthreads();
+    const float alpha = alpha_s;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        E[t] = fmaxf(fmaf(alpha, D[t], A[t]), eps);
+}
+
 __global__ void mu_plain_kernel(const float *pre, const float *num, const float *den, int64_t n, float gamma,
                                 float eps, float *out) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -800,6 +840,93 @@ int tucker_beta_div(ntf_ctx *ctx, const ntf_tensor *X, float beta, const int64_t
     a.n_is = w.plan3.n_is;
     TK(cp3_launch(w.plan3, a, PM_OBJ, 0, st));
     TK(reduce_objective(w.obj, w.plan3.grid, 0.0, out_dev, st));
+    return NTF_OK;
+}
+
+// Extrapolated block-MM sweep for Tucker (Section "Going beyond: Majorization-Minimization
+// with Extrapolation", item (ii)): the core, then modes 1..3; each block is moved to its
+// extrapolated point just before its update (it depends only on the incoming iterate and the
+// previous one), B3 / the mode-3 reconstruction use that block and the current others, and it
+// is the multiplicative pre-factor.  The objective of the incoming iterate (when asked for)
+// comes from a rows pass over the unextrapolated blocks.
+int tucker_run_extrap(ntf_ctx *ctx, const ntf_tensor *X, float beta, const int64_t *core_dims, float *core,
+                      float *const *factors, float *core_prev, float *const *factors_prev, float alpha, float cap,
+                      float delta, const ntf_opts &o, double *objective_dev, cudaStream_t st) {
+    if (!core_dims || !core || !factors || !core_prev || !factors_prev)
+        return ctx_fail(ctx, NTF_ERR_ARG, "core_dims, core, factors and their previous iterates are required");
+    if (X->order != 3) return ctx_fail(ctx, NTF_ERR_UNSUPPORTED, "Tucker kernels implement order 3");
+    for (int n = 0; n < 3; ++n) {
+        if (!factors[n] || !factors_prev[n]) return ctx_fail(ctx, NTF_ERR_ARG, "factor is NULL");
+        if (core_dims[n] < 1 || core_dims[n] > 64)
+            return ctx_fail(ctx, NTF_ERR_UNSUPPORTED, "core dimensions must lie in 1..64");
+        if (core_dims[n] > X->dims[n]) return ctx_fail(ctx, NTF_ERR_SHAPE, "core dimension exceeds tensor dimension");
+    }
+    TuckerWs w{};
+    int rc = setup(ctx, X, core_dims, false, w, o, beta);
+    if (rc) return rc;
+    const float eps = (float)o.eps;
+    const int64_t Jc = (int64_t)w.J1 * w.J2 * w.J3;
+    const int64_t n1 = (int64_t)w.I1 * w.J1, n2 = (int64_t)w.I2 * w.J2, n3 = (int64_t)w.I3 * w.J3;
+    bool ok = true;
+    Blocks hat{};
+    hat.G = wsf(ctx, "tkXG", Jc, ok);
+    hat.A1 = wsf(ctx, "tkXA1", n1, ok);
+    hat.A2 = wsf(ctx, "tkXA2", n2, ok);
+    hat.A3p = wsf(ctx, "tkXA3", (int64_t)w.I3 * w.RP, ok);
+    float *E3 = wsf(ctx, "tkXE3", n3, ok);
+    float *D = wsf(ctx, "tkXD", std::max(std::max(Jc, n1), std::max(n2, n3)), ok);
+    double *part = (double *)ctx_ws(ctx, "tkXpart", sizeof(double) * XB);
+    if (!ok || !part) return ctx_fail(ctx, NTF_ERR_OOM, "workspace allocation failed");
+    auto extrap = [&](const float *A, float *Aprev, int64_t n, float *E) -> int {
+        extrap_flat_prep_kernel<<<XB, 256, 0, st>>>(A, Aprev, D, n, part);
+        TK(cudaGetLastError());
+        extrap_flat_apply_kernel<<<XB, 256, 0, st>>>(A, D, n, part, alpha, cap, delta, eps, E);
+        TK(cudaGetLastError());
+        return NTF_OK;
+    };
+    if ((rc = load_blocks(ctx, w, core, factors, w.cur, st))) return rc;
+    if (objective_dev) {
+        if ((rc = build_b3(ctx, w, w.cur, w.Brec, st))) return rc;
+        if ((rc = rows_pass(ctx, w, X, o, beta, w.Brec, w.cur.A3p, w.cur.A3p, w.cur.A3p, true, st))) return rc;
+        TK(reduce_objective(w.obj, w.obj_n, 0.0, objective_dev, st));
+    }
+    // core block at its extrapolated point
+    if ((rc = extrap(w.cur.G, core_prev, Jc, hat.G))) return rc;
+    Blocks b = w.cur;
+    b.G = hat.G;
+    if ((rc = build_b3(ctx, w, b, w.Brec, st))) return rc;
+    if ((rc = rows_pass(ctx, w, X, o, beta, w.Brec, w.cur.A3p, w.cur.A3p, w.cur.A3p, false, st))) return rc;
+    if ((rc = contract_from_w(ctx, w, 0, w.cur, w.Wn, w.num, st))) return rc;
+    if ((rc = contract_from_w(ctx, w, 0, w.cur, w.Wd, w.den, st))) return rc;
+    if ((rc = apply_mu(ctx, w, hat.G, w.cur.G, Jc, beta, eps, nullptr, nullptr, nullptr, st))) return rc;
+    // modes 1 and 2
+    for (int blk = 1; blk <= 2; ++blk) {
+        float *A = blk == 1 ? w.cur.A1 : w.cur.A2;
+        float *Ah = blk == 1 ? hat.A1 : hat.A2;
+        if ((rc = extrap(A, factors_prev[blk - 1], blk == 1 ? n1 : n2, Ah))) return rc;
+        b = w.cur;
+        if (blk == 1) b.A1 = Ah; else b.A2 = Ah;
+        if ((rc = build_b3(ctx, w, b, w.Brec, st))) return rc;
+        if ((rc = rows_pass(ctx, w, X, o, beta, w.Brec, w.cur.A3p, w.cur.A3p, w.cur.A3p, false, st))) return rc;
+        if ((rc = contract_from_w(ctx, w, blk, w.cur, w.Wn, w.num, st))) return rc;
+        if ((rc = contract_from_w(ctx, w, blk, w.cur, w.Wd, w.den, st))) return rc;
+        if ((rc = apply_mu(ctx, w, Ah, A, blk == 1 ? n1 : n2, beta, eps, nullptr, nullptr, nullptr, st))) return rc;
+    }
+    // mode 3: extrapolated on the unpadded block, then padded
+    if ((rc = extrap(factors[2], factors_prev[2], n3, E3))) return rc;
+    pad_cols_kernel<<<nblk((int64_t)w.I3 * w.RP), 256, 0, st>>>(E3, w.I3, w.J3, w.RP, hat.A3p);
+    TK(cudaGetLastError());
+    if ((rc = build_b3(ctx, w, w.cur, w.Brec, st))) return rc;
+    if ((rc = mode3_pass(ctx, w, X, o, beta, w.Brec, hat.A3p, w.Brec, w.Brec, false, st))) return rc;
+    MuEpiArgs e{};
+    e.pn = w.pn3; e.pd = w.pd3; e.n_parts = w.parts3; e.rows = w.I3; e.RP = w.RP; e.R = w.J3;
+    e.pre = hat.A3p; e.out = w.cur.A3p; e.beta = beta; e.gamma = mu_gamma(beta); e.eps = eps;
+    TK(mu_epilogue(e, st));
+    TK(cudaMemcpyAsync(core, w.cur.G, sizeof(float) * Jc, cudaMemcpyDeviceToDevice, st));
+    TK(cudaMemcpyAsync(factors[0], w.cur.A1, sizeof(float) * n1, cudaMemcpyDeviceToDevice, st));
+    TK(cudaMemcpyAsync(factors[1], w.cur.A2, sizeof(float) * n2, cudaMemcpyDeviceToDevice, st));
+    unpad_cols_kernel<<<nblk(n3), 256, 0, st>>>(w.cur.A3p, w.I3, w.J3, w.RP, factors[2]);
+    TK(cudaGetLastError());
     return NTF_OK;
 }
 

@@ -208,6 +208,18 @@ int ntf_jcomm_outer(ntf_ctx *ctx, int model, const ntf_tensor *X, float beta, in
                     const int64_t *core_dims_or_null, float *core_or_null, float *const *factors,
                     const ntf_opts *opts, double *objective_ref_dev, void *stream);
 
+/* One Tucker J-CoMM outer iteration (dense 3-way) from an extrapolated outer reference
+ * (Section "Going beyond: Majorization-Minimization with Extrapolation", item (iii)): the core
+ * and every factor are first moved to max(Z + alpha_Z [Z - Zprev]_+, eps) (alpha_Z as in
+ * ntf_tucker_mu_sweep_extrap), and the outer iteration of ntf_jcomm_outer (NTF_TUCKER) runs with
+ * that point as its reference.  A heuristic without a convergence result in the paper.
+ *   core / factors / core_prev / factors_prev / alpha / cap / delta: as ntf_tucker_mu_sweep_extrap
+ *   objective_dev: device double or NULL; receives D_beta of the incoming iterate. */
+int ntf_tucker_jcomm_outer_extrap(ntf_ctx *ctx, const ntf_tensor *X, float beta, const int64_t *core_dims,
+                                  float *core, float *const *factors, float *core_prev, float *const *factors_prev,
+                                  float alpha, float cap, float delta, const ntf_opts *opts, double *objective_dev,
+                                  void *stream);
+
 /* D_beta(X, Xhat) = sum_i d_beta(X_i | max(Xhat_i, eps)) (Section 3.2, Definition
  * "beta-divergence") in FP64, written to *out_dev.  Per-entry terms use stable forms
  * in FP32 (log1p/expm1) and are summed in FP64.  For COO (beta = 1 only) the unstored

@@ -31,6 +31,8 @@ def _load():
             "ntfo_cp_contr": (None, [C.c_int, _P, _P, C.c_int, _P, C.c_int, _P]),
             "ntfo_cp_block_update": (None, [C.c_int, _P, _P, C.c_int, _P, C.c_int, _D, _D, _D, _P, _P]),
             "ntfo_cp_mu_sweep": (None, [C.c_int, _P, _P, C.c_int, _P, _D, _D, _D, _P]),
+            "ntfo_tucker_jcomm_outer_extrap": (None, [C.c_int, _P, _P, _P, _P, _P, _P, _P, _D, _D, _D, C.c_int, _D, _D, _D,
+                                                      _P]),
             "ntfo_tucker_mu_sweep_extrap": (None, [C.c_int, _P, _P, _P, _P, _P, _P, _P, _D, _D, _D, _D, _D, _D, _P]),
             "ntfo_cp_mu_sweep_extrap": (None, [C.c_int, _P, _P, C.c_int, _P, _P, _D, _D, _D, _D, _D, _D, _P]),
             "ntfo_cp_jcomm_outer": (None, [C.c_int, _P, _P, C.c_int, _P, _D, _D, _D, C.c_int, C.c_int, _P]),
@@ -289,6 +291,23 @@ def tucker_mu_sweep_extrap(X, core, factors, core_prev, factors_prev, beta, alph
     _load().ntfo_tucker_mu_sweep_extrap(X.ndim, _ptr(_dims(X.shape)), _ptr(X), _ptr(_dims(G.shape)), _ptr(G), pa.c,
                                         _ptr(Gp), pp.c, float(beta), float(eps), float(eps_x), float(alpha), float(cap),
                                         float(delta), _ptr(f))
+    return G, fs, Gp, ps, float(f[0])
+
+
+def tucker_jcomm_outer_extrap(X, core, factors, core_prev, factors_prev, beta, alpha, cap=np.inf, delta=1e-12, L=1,
+                              eps=1e-12, eps_x=1e-12):
+    """One Tucker J-CoMM outer iteration from the extrapolated reference.  Returns (core,
+    factors, core_prev, factors_prev, objective of the incoming iterate)."""
+    X = _f64(X)
+    G = _f64(core).copy()
+    Gp = _f64(core_prev).copy()
+    fs = [_f64(a).copy() for a in factors]
+    ps = [_f64(a).copy() for a in factors_prev]
+    f = np.zeros(1)
+    pa, pp = _PtrArray(fs), _PtrArray(ps)
+    _load().ntfo_tucker_jcomm_outer_extrap(X.ndim, _ptr(_dims(X.shape)), _ptr(X), _ptr(_dims(G.shape)), _ptr(G), pa.c,
+                                           _ptr(Gp), pp.c, float(beta), float(eps), float(eps_x), int(L), float(alpha),
+                                           float(cap), float(delta), _ptr(f))
     return G, fs, Gp, ps, float(f[0])
 
 

@@ -634,6 +634,37 @@ void ntfo_tucker_jcomm_outer(int N, const int64_t *dims, const double *X, const 
     free(Gt); free(G1); free(G2); free(Xt); free(Pt); free(Qt);
 }
 
+/* Tucker J-CoMM outer iteration from an extrapolated outer reference (Section "Going beyond:
+ * Majorization-Minimization with Extrapolation", item (iii)): every block (core and factors)
+ * is first moved to its extrapolated point as in ntfo_tucker_mu_sweep_extrap, then the outer
+ * iteration of Algorithm 2 runs from that reference.  Gprev / Aprev become the incoming
+ * iterate; F_in (may be NULL) receives the objective of the incoming iterate. */
+void ntfo_tucker_jcomm_outer_extrap(int N, const int64_t *dims, const double *X, const int64_t *J, double *G,
+                                    double *const *A, double *Gprev, double *const *Aprev, double beta, double eps,
+                                    double eps_x, int L, double alpha_nes, double cap, double delta, double *F_in) {
+    int64_t cnt = numel(N, dims), cj = numel(N, J);
+    if (F_in) {
+        double *Xhat = (double *)malloc(sizeof(double) * cnt);
+        ntfo_tucker_full(N, dims, J, G, (const double *const *)A, Xhat);
+        *F_in = objective_from_full(cnt, X, Xhat, beta, eps, eps_x);
+        free(Xhat);
+    }
+    double *G0 = (double *)malloc(sizeof(double) * cj);
+    memcpy(G0, G, sizeof(double) * cj);
+    extrap_block(cj, G, Gprev, alpha_nes, cap, delta, eps);
+    memcpy(Gprev, G0, sizeof(double) * cj);
+    free(G0);
+    for (int n = 0; n < N; ++n) {
+        const int64_t c = dims[n] * J[n];
+        double *A0 = (double *)malloc(sizeof(double) * c);
+        memcpy(A0, A[n], sizeof(double) * c);
+        extrap_block(c, A[n], Aprev[n], alpha_nes, cap, delta, eps);
+        memcpy(Aprev[n], A0, sizeof(double) * c);
+        free(A0);
+    }
+    ntfo_tucker_jcomm_outer(N, dims, X, J, G, A, beta, eps, eps_x, L, -1, NULL);
+}
+
 /* ----------------------------------------------------------------------------------
  * Sparse COO tensors under KL (beta = 1), Section 6.3 "For sparse tensors"
  * idx is N arrays of nnz int32 coordinates; coordinates are unique.

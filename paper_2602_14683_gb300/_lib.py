@@ -69,6 +69,9 @@ _sig = {
                                          C.c_float, C.c_float, C.c_float, C.POINTER(Opts), _P, _P]),
     "ntf_cp_jcomm_outer_extrap": (C.c_int, [_P, C.POINTER(Tensor), C.c_float, C.c_int, C.POINTER(_P), C.POINTER(_P),
                                             C.c_float, C.c_float, C.c_float, C.POINTER(Opts), _P, _P]),
+    "ntf_tucker_jcomm_outer_extrap": (C.c_int, [_P, C.POINTER(Tensor), C.c_float, C.POINTER(C.c_int64), _P,
+                                                C.POINTER(_P), _P, C.POINTER(_P), C.c_float, C.c_float, C.c_float,
+                                                C.POINTER(Opts), _P, _P]),
     "ntf_tucker_mu_sweep_extrap": (C.c_int, [_P, C.POINTER(Tensor), C.c_float, C.POINTER(C.c_int64), _P, C.POINTER(_P),
                                              _P, C.POINTER(_P), C.c_float, C.c_float, C.c_float, C.POINTER(Opts), _P,
                                              _P]),
@@ -273,6 +276,23 @@ def tucker_mu_sweep_extrap(X, beta, core, factors, core_prev, factors_prev, alph
     ctx.check(_lib.ntf_tucker_mu_sweep_extrap(ctx.h, C.byref(d.t), float(beta), cd, C.c_void_p(core.data_ptr()), fp,
                                               C.c_void_p(core_prev.data_ptr()), pp, float(alpha), float(cap),
                                               float(delta), C.byref(o), _out_ptr(objective), _stream(stream)))
+
+
+def tucker_jcomm_outer_extrap(X, beta, core, factors, core_prev, factors_prev, alpha, cap=float("inf"), delta=1e-12,
+                              objective=None, ctx=None, stream=None, **opts):
+    """One Tucker J-CoMM outer iteration from the extrapolated reference: core / factors ->
+    new iterate, core_prev / factors_prev -> the incoming iterate, in place."""
+    ctx = ctx or default_context()
+    d = _Desc(X)
+    _check_dev(core, torch.float32, "core")
+    _check_dev(core_prev, torch.float32, "core_prev")
+    cd = (C.c_int64 * 3)(*core.shape)
+    fp = _ptrs(factors, "factors")
+    pp = _ptrs(factors_prev, "factors_prev")
+    o = make_opts(**opts)
+    ctx.check(_lib.ntf_tucker_jcomm_outer_extrap(ctx.h, C.byref(d.t), float(beta), cd, C.c_void_p(core.data_ptr()),
+                                                 fp, C.c_void_p(core_prev.data_ptr()), pp, float(alpha), float(cap),
+                                                 float(delta), C.byref(o), _out_ptr(objective), _stream(stream)))
 
 
 def nesterov_weights():

@@ -783,6 +783,26 @@ int ntf_tucker_mu_sweep_extrap(ntf_ctx *ctx, const ntf_tensor *X, float beta, co
                                   objective_dev, (cudaStream_t)stream);
 }
 
+int ntf_tucker_jcomm_outer_extrap(ntf_ctx *ctx, const ntf_tensor *X, float beta, const int64_t *core_dims,
+                                  float *core, float *const *factors, float *core_prev, float *const *factors_prev,
+                                  float alpha, float cap, float delta, const ntf_opts *opts, double *objective_dev,
+                                  void *stream) {
+    ntf_opts o = resolve_opts(opts);
+    int rc = check_common(ctx, X, beta, o);
+    if (rc) return rc;
+    if (X->kind != NTF_DENSE) return fail(ctx, NTF_ERR_UNSUPPORTED, "Tucker is implemented for dense tensors");
+    if (!core_prev || !factors_prev) return fail(ctx, NTF_ERR_ARG, "previous iterate is NULL");
+    for (int n = 0; n < 3 && n < X->order; ++n)
+        if (!factors_prev[n]) return fail(ctx, NTF_ERR_ARG, "previous factor %d is NULL", n);
+    if (!(alpha >= 0.0f) || !(cap >= 0.0f) || !(delta > 0.0f))
+        return fail(ctx, NTF_ERR_ARG, "alpha and cap must be >= 0 and delta > 0");
+    cudaSetDevice(ctx->device);
+    ctx->err[0] = 0;
+    const ntf::TuckerExtrap xe{core_prev, factors_prev, alpha, cap, delta};
+    return ntf::tucker_run(ctx, X, beta, core_dims, core, factors, o, objective_dev, (cudaStream_t)stream,
+                           /*jcomm=*/true, &xe);
+}
+
 int ntf_jcomm_outer(ntf_ctx *ctx, int model, const ntf_tensor *X, float beta, int rank_or_0,
                     const int64_t *core_dims_or_null, float *core_or_null, float *const *factors,
                     const ntf_opts *opts, double *objective_ref_dev, void *stream) {

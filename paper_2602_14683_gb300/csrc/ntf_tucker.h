@@ -10,8 +10,15 @@ void ctx_count(ntf_ctx *c, int n);
 int ctx_num_sms(const ntf_ctx *c);
 int *ctx_status(ntf_ctx *c);  // device status word of the bounded-wait kernels
 
+// previous iterate and weights of an outer-reference extrapolation (J-CoMM)
+struct TuckerExtrap {
+    float *core_prev;
+    float *const *factors_prev;
+    float alpha, cap, delta;
+};
 int tucker_run(ntf_ctx *ctx, const ntf_tensor *X, float beta, const int64_t *core_dims, float *core,
-               float *const *factors, const ntf_opts &o, double *objective_dev, cudaStream_t st, bool jcomm);
+               float *const *factors, const ntf_opts &o, double *objective_dev, cudaStream_t st, bool jcomm,
+               const TuckerExtrap *xe = nullptr);
 int tucker_beta_div(ntf_ctx *ctx, const ntf_tensor *X, float beta, const int64_t *core_dims, const float *core,
                     const float *const *factors, const ntf_opts &o, double *out_dev, cudaStream_t st);
 int tucker_run_extrap(ntf_ctx *ctx, const ntf_tensor *X, float beta, const int64_t *core_dims, float *core,

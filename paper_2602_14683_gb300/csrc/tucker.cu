@@ -726,7 +726,8 @@ int mode3_pass(ntf_ctx *ctx, TuckerWs &w, const ntf_tensor *X, const ntf_opts &o
 }  // namespace
 
 int tucker_run(ntf_ctx *ctx, const ntf_tensor *X, float beta, const int64_t *core_dims, float *core,
-               float *const *factors, const ntf_opts &o, double *objective_dev, cudaStream_t st, bool jcomm) {
+               float *const *factors, const ntf_opts &o, double *objective_dev, cudaStream_t st, bool jcomm,
+               const TuckerExtrap *xe) {
     if (!core_dims || !core || !factors) return ctx_fail(ctx, NTF_ERR_ARG, "core_dims, core and factors are required");
     if (X->order != 3) return ctx_fail(ctx, NTF_ERR_UNSUPPORTED, "Tucker kernels implement order 3");
     for (int n = 0; n < 3; ++n) {
@@ -743,8 +744,36 @@ int tucker_run(ntf_ctx *ctx, const ntf_tensor *X, float beta, const int64_t *cor
     const int64_t n1 = (int64_t)w.I1 * w.J1, n2 = (int64_t)w.I2 * w.J2, n3p = (int64_t)w.I3 * w.RP;
     rc = load_blocks(ctx, w, core, factors, w.cur, st);
     if (rc) return rc;
-    const Cp3Args probe = base_args(X, w, o, beta);
-    (void)probe;
+    if (xe && jcomm) {
+        // outer-reference extrapolation (Section "Going beyond: Majorization-Minimization with
+        // Extrapolation", item (iii)): the objective of the incoming iterate first, then every
+        // block moved in place to its extrapolated point, which becomes the reference
+        if (objective_dev) {
+            if ((rc = build_b3(ctx, w, w.cur, w.Brec, st))) return rc;
+            if ((rc = rows_pass(ctx, w, X, o, beta, w.Brec, w.cur.A3p, w.cur.A3p, w.cur.A3p, true, st))) return rc;
+            TK(reduce_objective(w.obj, w.obj_n, 0.0, objective_dev, st));
+            objective_dev = nullptr;
+        }
+        const int64_t n3 = (int64_t)w.I3 * w.J3;
+        bool ok = true;
+        float *E3 = wsf(ctx, "tkXE3", n3, ok);
+        float *D = wsf(ctx, "tkXD", std::max(std::max(Jc, n1), std::max(n2, n3)), ok);
+        double *part = (double *)ctx_ws(ctx, "tkXpart", sizeof(double) * XB);
+        if (!ok || !part) return ctx_fail(ctx, NTF_ERR_OOM, "workspace allocation failed");
+        auto extrap = [&](const float *A, float *Aprev, int64_t n, float *E) -> int {
+            extrap_flat_prep_kernel<<<XB, 256, 0, st>>>(A, Aprev, D, n, part);
+            TK(cudaGetLastError());
+            extrap_flat_apply_kernel<<<XB, 256, 0, st>>>(A, D, n, part, xe->alpha, xe->cap, xe->delta, eps, E);
+            TK(cudaGetLastError());
+            return NTF_OK;
+        };
+        if ((rc = extrap(w.cur.G, xe->core_prev, Jc, w.cur.G))) return rc;
+        if ((rc = extrap(w.cur.A1, xe->factors_prev[0], n1, w.cur.A1))) return rc;
+        if ((rc = extrap(w.cur.A2, xe->factors_prev[1], n2, w.cur.A2))) return rc;
+        if ((rc = extrap(factors[2], xe->factors_prev[2], n3, E3))) return rc;
+        pad_cols_kernel<<<nblk(n3p), 256, 0, st>>>(E3, w.I3, w.J3, w.RP, w.cur.A3p);
+        TK(cudaGetLastError());
+    }
 
     if (!jcomm) {
         // ---- core block (the pass also yields D_beta of the incoming iterate) ----

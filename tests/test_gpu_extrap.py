@@ -104,3 +104,25 @@ def test_tucker_extrap_sweep_parity(case, beta):
     for n in range(3):
         assert np.array_equal(host(Apd[n]), np.float32(A0[n]).astype(np.float64)), n
     assert abs(obj.item() - Fw) / Fw <= tol_obj
+
+
+@pytest.mark.parametrize("case", range(len(TUCKER_CASES)))
+@pytest.mark.parametrize("beta", [0.5, 1.5])
+@pytest.mark.parametrize("L", [1, 2])
+def test_tucker_jcomm_extrap_parity(case, beta, L):
+    ntf = _ntf()
+    dims, J, prec, tol, tol_obj = TUCKER_CASES[case]
+    X, _, _ = synth.tucker_dense(dims, J, seed=80 + case)
+    G0, A0 = synth.init_tucker(dims, J, seed=81 + case)
+    g = np.random.default_rng(case + 10)
+    Gp = np.float32(G0 * g.uniform(0.6, 1.1, size=G0.shape)).astype(np.float64)
+    Ap = [np.float32(a * g.uniform(0.6, 1.1, size=a.shape)).astype(np.float64) for a in A0]
+    Gw, Aw, _, _, Fw = oracle.tucker_jcomm_outer_extrap(X, G0, A0, Gp, Ap, beta, alpha=0.6, cap=0.4, L=L)
+    Gd, Ad, Gpd, Apd, obj = dev(G0), [dev(a) for a in A0], dev(Gp), [dev(a) for a in Ap], obj_tensor()
+    ntf.tucker_jcomm_outer_extrap(dev(X), beta, Gd, Ad, Gpd, Apd, 0.6, cap=0.4, objective=obj, precision=prec,
+                                  inner_L=L)
+    ntf.default_context().device_status()
+    errs = [rel_fro(host(Gd), Gw)] + [rel_fro(host(Ad[n]), Aw[n]) for n in range(3)]
+    assert max(errs) <= tol, errs
+    assert np.array_equal(host(Gpd), np.float32(G0).astype(np.float64))
+    assert abs(obj.item() - Fw) / Fw <= tol_obj

@@ -608,3 +608,29 @@ def test_tucker_extrap_reduces_to_block_mm_and_blocks_are_argmins():
 
             _assert_block_argmin(Gfun, An[n])
             cur[n] = An[n]
+
+
+def test_tucker_jcomm_extrap_is_jcomm_from_the_extrapolated_reference():
+    g = np.random.default_rng(36)
+    dims, J = (4, 3, 5), (2, 3, 2)
+    X = g.gamma(3.0, 1.0, size=dims) + 0.05
+    G = g.uniform(0.2, 1.0, size=J)
+    A = [g.uniform(0.2, 1.0, size=(d, j)) for d, j in zip(dims, J)]
+    Gp = G * g.uniform(0.5, 1.2, size=G.shape)
+    Ap = [a * g.uniform(0.5, 1.2, size=a.shape) for a in A]
+
+    def hat(z, zp, alpha, cap):
+        D = np.maximum(z - zp, 0.0)
+        return np.maximum(z + min(alpha, cap / (np.linalg.norm(D) + 1e-12)) * D, 1e-12)
+    for beta in (0.5, 1.0, 1.5):
+        Gw, Aw, Fw = oracle.tucker_jcomm_outer(X, G, A, beta, L=2)
+        G0, A0, Gp0, Ap0, F0 = oracle.tucker_jcomm_outer_extrap(X, G, A, Gp, Ap, beta, alpha=0.0, L=2)
+        assert np.array_equal(G0, Gw) and all(np.array_equal(x, y) for x, y in zip(A0, Aw)) and F0 == Fw
+        want_G, want_A, _ = oracle.tucker_jcomm_outer(X, hat(G, Gp, 0.7, 0.3), [hat(a, p, 0.7, 0.3) for a, p in zip(A, Ap)],
+                                                      beta, L=2)
+        G1, A1, Gp1, Ap1, F1 = oracle.tucker_jcomm_outer_extrap(X, G, A, Gp, Ap, beta, alpha=0.7, cap=0.3, L=2)
+        assert np.allclose(G1, want_G, rtol=1e-13, atol=0.0) and F1 == Fw
+        for n in range(3):
+            assert np.allclose(A1[n], want_A[n], rtol=1e-13, atol=0.0)
+            assert np.array_equal(Ap1[n], A[n])
+        assert np.array_equal(Gp1, G)

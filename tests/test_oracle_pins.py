@@ -634,3 +634,38 @@ def test_tucker_jcomm_extrap_is_jcomm_from_the_extrapolated_reference():
             assert np.allclose(A1[n], want_A[n], rtol=1e-13, atol=0.0)
             assert np.array_equal(Ap1[n], A[n])
         assert np.array_equal(Gp1, G)
+
+
+@pytest.mark.parametrize("beta", BETAS)
+def test_cp_order4_matches_brute_force_and_permutations(beta):
+    """Order 4: Num/Den of every block equal brute-force sums over all entries (written here
+    with einsum from the definitions of P, Q and CPContr), mode permutations permute them, and
+    exact data is a fixed point of both B-CoMM and J-CoMM."""
+    g = np.random.default_rng(37)
+    dims, R = (3, 4, 2, 5), 2
+    X = g.gamma(3.0, 1.0, size=dims) + 0.05
+    A = [g.uniform(0.2, 1.0, size=(d, R)) for d in dims]
+    Xh = np.einsum("ir,jr,kr,lr->ijkl", *A)
+    y = np.maximum(Xh, 1e-12)
+    Xs = np.maximum(X, 1e-12) if beta == 0.0 else X
+    P, Q = Xs * y ** (beta - 2.0), y ** (beta - 1.0)
+    subs = "ijkl"
+    for n in range(4):
+        others = [m for m in range(4) if m != n]
+        spec = "ijkl," + ",".join(subs[m] + "r" for m in others) + "->" + subs[n] + "r"
+        num_bf = np.einsum(spec, P, *[A[m] for m in others])
+        den_bf = np.einsum(spec, Q, *[A[m] for m in others])
+        _, num, den = oracle.cp_block_update(X, A, n, beta)
+        np.testing.assert_allclose(num, num_bf, rtol=1e-12)
+        np.testing.assert_allclose(den, den_bf, rtol=1e-12)
+    perm = (2, 0, 3, 1)
+    Xp, Ap = np.transpose(X, perm), [A[p] for p in perm]
+    for n in range(4):
+        _, num, den = oracle.cp_block_update(X, A, n, beta)
+        _, nump, denp = oracle.cp_block_update(Xp, Ap, perm.index(n), beta)
+        np.testing.assert_allclose(nump, num, rtol=1e-12)
+        np.testing.assert_allclose(denp, den, rtol=1e-12)
+    Xe = oracle.cp_full(dims, A)
+    for fn in (lambda: oracle.cp_mu_sweep(Xe, A, beta)[0], lambda: oracle.cp_jcomm_outer(Xe, A, beta, L=2)[0]):
+        for a, b in zip(fn(), A):
+            np.testing.assert_allclose(a, b, rtol=1e-11)

@@ -255,6 +255,79 @@ cudaError_t extrapolate(const ExtrapArgs &x, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// Order N >= 4 on the 3-way kernels: the leading modes 0..M-1 are merged into one mode whose
+// index is the row-major multi-index (last leading mode fastest -- the memory order of X),
+// with the Khatri-Rao factor KR[(i_0..i_{M-1})][r] = prod_m L_m[i_m][r].
+__global__ void kr_merge_kernel(KrArgs k) {
+    __shared__ double sh[256];
+    const int RP = k.RP, G = blockDim.x / RP, t = threadIdx.x, r = t % RP, g = t / RP;
+    const int rpb = rows_per_block(k.rows, RP);
+    const int ibeg = blockIdx.x * rpb, iend = min(k.rows, ibeg + rpb);
+    double cs = 0.0;
+    for (int i = ibeg + g; i < iend; i += G) {
+        int rem = i;
+        float v = 1.0f;
+        for (int m = k.M - 1; m >= 0; --m) {
+            const int im = rem % k.dims[m];
+            rem /= k.dims[m];
+            v *= k.L[m][(int64_t)im * RP + r];
+        }
+        if (k.out) k.out[(int64_t)i * RP + r] = v;
+        cs += (double)v;
+    }
+    if (k.cs) {
+        const double tot = group_sum(sh, cs, RP, t);
+        if (t < RP) k.cs[(int64_t)blockIdx.x * RP + t] = tot;
+    }
+}
+
+cudaError_t kr_merge(const KrArgs &k, cudaStream_t s) {
+    kr_merge_kernel<<<row_blocks(k.rows, k.RP), 256, 0, s>>>(k);
+    return cudaGetLastError();
+}
+
+// out[i_n][r] = sum over the other leading indices (row-major order) of
+//   (sum over the parts, in order, of parts[p][merged index][r]) * prod_{m != n} L_m[i_m][r]
+// -- CPContr^(n) of the merged-mode contraction, one thread per (i_n, r), FP64 accumulation.
+__global__ void kr_fold_kernel(FoldArgs f) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int RP = f.RP;
+    if (t >= (int64_t)f.dims[f.n] * RP) return;
+    const int in = (int)(t / RP), r = (int)(t % RP);
+    int64_t other = 1;
+    for (int m = 0; m < f.M; ++m)
+        if (m != f.n) other *= f.dims[m];
+    const int64_t stride = f.rows * RP;
+    double acc = 0.0;
+    for (int64_t q = 0; q < other; ++q) {
+        // the other leading indices from q (row-major over m != n), and the merged row index
+        int64_t rem = q, row = 0, mul = 1;
+        float w = 1.0f;
+        for (int m = f.M - 1; m >= 0; --m) {
+            int im;
+            if (m == f.n) {
+                im = in;
+            } else {
+                im = (int)(rem % f.dims[m]);
+                rem /= f.dims[m];
+                w *= f.L[m][(int64_t)im * RP + r];
+            }
+            row += (int64_t)im * mul;
+            mul *= f.dims[m];
+        }
+        float s = 0.0f;
+        for (int p = 0; p < f.n_parts; ++p) s += f.parts[(int64_t)p * stride + row * RP + r];
+        acc += (double)s * (double)w;
+    }
+    f.out[t] = r < f.R ? (float)acc : 0.0f;
+}
+
+cudaError_t kr_fold(const FoldArgs &f, cudaStream_t s) {
+    const int64_t n = (int64_t)f.dims[f.n] * f.RP;
+    kr_fold_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(f);
+    return cudaGetLastError();
+}
+
 cudaError_t prep_factors(const PrepArgs &p, cudaStream_t s) {
     int blocks = 0;
     for (int m = 0; m < 3; ++m) blocks += row_blocks(p.rows[m], p.RP);

@@ -87,8 +87,8 @@ int check_common(ntf_ctx *ctx, const ntf_tensor *X, float beta, const ntf_opts &
         if (X->dims[n] < 1 || X->dims[n] > (int64_t)0x7fffffff)
             return fail(ctx, NTF_ERR_SHAPE, "dims[%d] = %lld out of range", n, (long long)X->dims[n]);
     if (!X->values) return fail(ctx, NTF_ERR_ARG, "tensor values pointer is NULL");
-    if (X->kind == NTF_DENSE && X->order != 3)
-        return fail(ctx, NTF_ERR_UNSUPPORTED, "dense kernels implement order 3, got %d", X->order);
+    if (X->kind == NTF_DENSE && X->order < 3)
+        return fail(ctx, NTF_ERR_UNSUPPORTED, "dense kernels implement orders 3..8, got %d", X->order);
     if (X->kind == NTF_COO) {
         if (!X->idx) return fail(ctx, NTF_ERR_ARG, "COO coordinate array is NULL");
         for (int n = 0; n < X->order; ++n)
@@ -583,6 +583,222 @@ int cp_dense_mu_sweep_extrap(ntf_ctx *ctx, const ntf_tensor *X, float beta, int 
     return NTF_OK;
 }
 
+// ------------------------------------------------------------ dense CP of order N >= 4
+// The leading modes 0..M-1 (M = N - 2) are merged: X (row-major) is then the 3-way tensor
+// (prod_{m<M} I_m) x I_{N-2} x I_{N-1}, whose first factor is the Khatri-Rao product of the
+// leading factors.  Modes N-2 and N-1 are 3-way modes 2 and 3 of that view; a leading mode n
+// takes the view's mode-1 contraction and folds it against the other leading factors
+// (CPContr^(n) over the merged index), Section 6.1.
+struct NWay {
+    int N, M;
+    int64_t dims[8];
+    int64_t merged;
+    ntf_tensor X3;
+    int64_t dims3[3];
+    float *L[8], *Lt[8];  // padded current / reference leading factors
+    float *num, *den;     // folded Num / Den of a leading mode, [max I_n][RP]
+};
+
+int nway_setup(ntf_ctx *ctx, const ntf_tensor *X, int R, bool jcomm, bool need_den, int precision, CpDense &s,
+               NWay &w, const ntf_opts *tune_opts, int tune_bk, int tune_ms) {
+    w.N = X->order;
+    w.M = w.N - 2;
+    w.merged = 1;
+    for (int n = 0; n < w.N; ++n) w.dims[n] = X->dims[n];
+    for (int m = 0; m < w.M; ++m) w.merged *= X->dims[m];
+    if (w.merged > (int64_t)0x7fffffff) return fail(ctx, NTF_ERR_SHAPE, "product of the leading dimensions too large");
+    w.dims3[0] = w.merged;
+    w.dims3[1] = X->dims[w.N - 2];
+    w.dims3[2] = X->dims[w.N - 1];
+    w.X3 = *X;
+    w.X3.order = 3;
+    w.X3.dims = w.dims3;
+    int rc = cp_dense_setup(ctx, &w.X3, R, jcomm, need_den, precision, s, tune_opts, tune_bk, tune_ms);
+    if (rc) return rc;
+    int64_t maxI = 1;
+    for (int m = 0; m < w.M; ++m) {
+        const size_t fb = sizeof(float) * (size_t)w.dims[m] * s.RP;
+        w.L[m] = (float *)ws_get(ctx, "nwL" + std::to_string(m), fb);
+        w.Lt[m] = jcomm ? (float *)ws_get(ctx, "nwLt" + std::to_string(m), fb) : w.L[m];
+        if (!w.L[m] || !w.Lt[m]) return fail(ctx, NTF_ERR_OOM, "workspace allocation failed");
+        maxI = std::max(maxI, w.dims[m]);
+    }
+    w.num = (float *)ws_get(ctx, "nwNum", sizeof(float) * (size_t)maxI * s.RP);
+    w.den = (float *)ws_get(ctx, "nwDen", sizeof(float) * (size_t)maxI * s.RP);
+    if (!w.num || !w.den) return fail(ctx, NTF_ERR_OOM, "workspace allocation failed");
+    return NTF_OK;
+}
+
+ntf::KrArgs kr_args(const NWay &w, const CpDense &s, float *const *L, float *out, double *cs) {
+    ntf::KrArgs k{};
+    for (int m = 0; m < w.M; ++m) {
+        k.L[m] = L[m];
+        k.dims[m] = (int)w.dims[m];
+    }
+    k.M = w.M;
+    k.rows = (int)w.merged;
+    k.RP = s.RP;
+    k.out = out;
+    k.cs = cs;
+    return k;
+}
+
+// pads the trailing two factors into the view's F[1], F[2] (and, for J-CoMM, the reference
+// copies Ft[1], Ft[2]) with FP64 column-sum partials; the view's mode 1 is left to kr_merge
+int nway_prep_trailing(ntf_ctx *ctx, NWay &w, CpDense &s, float *const *factors, bool ref, cudaStream_t st) {
+    ntf::PrepArgs p{};
+    p.rows[0] = 0;  // no row blocks for the merged slot
+    for (int m = 1; m < 3; ++m) {
+        p.src[m] = factors[w.M + m - 1];
+        p.rows[m] = (int)w.dims[w.M + m - 1];
+        p.F[m] = s.F[m];
+        p.Ft[m] = ref ? s.Ft[m] : nullptr;
+        p.cs[m] = s.cs[m];
+    }
+    p.R = s.R;
+    p.RP = s.RP;
+    NTF_CUDA(ntf::prep_factors(p, st));
+    return NTF_OK;
+}
+
+// update of leading mode n from the view's mode-1 partial sums: fold, closed-form KL
+// denominator (product of the column sums of every other current factor) or folded Den, MU
+int nway_leading_update(ntf_ctx *ctx, NWay &w, CpDense &s, int n, float beta, const ntf_opts &o, bool kl,
+                        float *const *Lfold, const float *pre, float *out, float *user, cudaStream_t st) {
+    ntf::FoldArgs f{};
+    f.parts = s.pn[0];
+    f.n_parts = s.plan.parts1;
+    for (int m = 0; m < w.M; ++m) {
+        f.L[m] = Lfold[m];
+        f.dims[m] = (int)w.dims[m];
+    }
+    f.M = w.M;
+    f.n = n;
+    f.rows = (int)w.merged;
+    f.R = s.R;
+    f.RP = s.RP;
+    f.out = w.num;
+    NTF_CUDA(ntf::kr_fold(f, st));
+    ntf::MuEpiArgs e{};
+    e.pn = w.num;
+    e.n_parts = 1;
+    e.rows = (int)w.dims[n];
+    e.RP = s.RP;
+    e.R = s.R;
+    if (kl) {
+        const float *cf[8];
+        int rows[8], q = 0;
+        for (int m = 0; m < w.M; ++m)
+            if (m != n) { cf[q] = w.L[m]; rows[q] = (int)w.dims[m]; ++q; }
+        cf[q] = s.F[1]; rows[q] = (int)w.dims[w.N - 2]; ++q;
+        cf[q] = s.F[2]; rows[q] = (int)w.dims[w.N - 1]; ++q;
+        NTF_CUDA(ntf::colsum_prod(q, cf, rows, s.RP, s.denc, st));
+        e.den_closed = s.denc;
+    } else {
+        f.parts = s.pd[0];
+        f.out = w.den;
+        NTF_CUDA(ntf::kr_fold(f, st));
+        e.pd = w.den;
+    }
+    e.pre = pre;
+    e.out = out;
+    e.beta = beta;
+    e.gamma = ntf::mu_gamma(beta);
+    e.eps = (float)o.eps;
+    NTF_CUDA(ntf::mu_epilogue(e, st));
+    if (user) NTF_CUDA(ntf::unpad_factor(out, (int)w.dims[n], s.R, s.RP, user, st));
+    return NTF_OK;
+}
+
+int cp_nway_mu_sweep(ntf_ctx *ctx, const ntf_tensor *X, float beta, int R, float *const *factors, const ntf_opts &o,
+                     double *objective_dev, cudaStream_t st) {
+    const int bk = ntf::beta_kind(beta);
+    const bool kl = bk == ntf::BK_KL;
+    CpDense s{};
+    NWay w{};
+    int rc = nway_setup(ctx, X, R, false, !kl, o.precision, s, w, nullptr, 0, 0);
+    if (rc) return rc;
+    for (int m = 0; m < w.M; ++m) NTF_CUDA(ntf::pad_factor(factors[m], (int)w.dims[m], R, w.L[m], s.RP, st));
+    if ((rc = nway_prep_trailing(ctx, w, s, factors, false, st))) return rc;
+    ntf::Cp3Args a = cp_args(&w.X3, s, o, beta);
+    for (int m = 0; m < 3; ++m) a.rec[m] = a.num[m] = a.den[m] = s.F[m];
+    for (int n = 0; n < w.N; ++n) {
+        if (n <= w.M) NTF_CUDA(ntf::kr_merge(kr_args(w, s, w.L, s.F[0], s.cs[0]), st));  // current leading blocks
+        if (n < w.M) {
+            const int ms = ntf::PM_M1 | ((n == 0 && objective_dev) ? ntf::PM_OBJ : 0);
+            if ((rc = launch_pass(ctx, s, a, ms, kl ? 0 : 1, st))) return rc;
+            if (n == 0 && objective_dev) NTF_CUDA(ntf::reduce_objective(s.obj, s.plan.grid, 0.0, objective_dev, st));
+            if ((rc = nway_leading_update(ctx, w, s, n, beta, o, kl, w.L, w.L[n], w.L[n], factors[n], st))) return rc;
+        } else {
+            const int k = n - w.M + 1;  // the view's mode 2 or 3
+            if ((rc = launch_pass(ctx, s, a, k == 1 ? ntf::PM_M2 : ntf::PM_M3, kl ? 0 : 1, st))) return rc;
+            ntf::UpdArgs u = upd_args(s, k, beta, o, kl, s.F[k], factors[n]);
+            NTF_CUDA(ntf::mode_update(u, st));
+        }
+    }
+    return NTF_OK;
+}
+
+// J-CoMM at beta = 1 (Section 5.3 with chi1(Z, Zt) = Zt): one pass over X from the reference
+// gives every numerator (the leading ones by folding with the reference leading blocks);
+// Den^(n) = prod_{m != n} colsum of the current blocks.
+int cp_nway_jcomm(ntf_ctx *ctx, const ntf_tensor *X, float beta, int R, float *const *factors, const ntf_opts &o,
+                  double *objective_dev, cudaStream_t st) {
+    if (ntf::beta_kind(beta) != ntf::BK_KL)
+        return fail(ctx, NTF_ERR_UNSUPPORTED, "J-CoMM for dense orders N >= 4 is implemented at beta = 1");
+    CpDense s{};
+    NWay w{};
+    int rc = nway_setup(ctx, X, R, true, false, o.precision, s, w, nullptr, 0, 0);
+    if (rc) return rc;
+    for (int m = 0; m < w.M; ++m) {
+        NTF_CUDA(ntf::pad_factor(factors[m], (int)w.dims[m], R, w.Lt[m], s.RP, st));
+        NTF_CUDA(ntf::copy_f32(w.Lt[m], w.L[m], w.dims[m] * s.RP, st));
+    }
+    if ((rc = nway_prep_trailing(ctx, w, s, factors, true, st))) return rc;
+    NTF_CUDA(ntf::kr_merge(kr_args(w, s, w.Lt, s.Ft[0], s.cs[0]), st));
+    ntf::Cp3Args a = cp_args(&w.X3, s, o, beta);
+    for (int m = 0; m < 3; ++m) a.rec[m] = a.num[m] = a.den[m] = s.Ft[m];
+    if ((rc = launch_pass(ctx, s, a, ntf::PM_M1 | ntf::PM_M2 | ntf::PM_M3 | ntf::PM_OBJ, 0, st))) return rc;
+    if (objective_dev) NTF_CUDA(ntf::reduce_objective(s.obj, s.plan.grid, 0.0, objective_dev, st));
+    for (int l = 0; l < o.inner_L; ++l) {
+        for (int n = 0; n < w.N; ++n) {
+            float *user = l == o.inner_L - 1 ? factors[n] : nullptr;
+            if (n < w.M) {
+                // the trailing current blocks sit in the view's F[1], F[2]: until their first
+                // update they equal the reference (F = Ft after the prep copies)
+                if ((rc = nway_leading_update(ctx, w, s, n, beta, o, true, w.Lt, w.Lt[n], w.L[n], user, st)))
+                    return rc;
+            } else {
+                const int k = n - w.M + 1;
+                if (n == w.M) NTF_CUDA(ntf::kr_merge(kr_args(w, s, w.L, nullptr, s.cs[0]), st));  // current leading
+                ntf::UpdArgs u = upd_args(s, k, beta, o, true, s.Ft[k], user);
+                NTF_CUDA(ntf::mode_update(u, st));
+            }
+        }
+    }
+    return NTF_OK;
+}
+
+int cp_nway_beta_div(ntf_ctx *ctx, const ntf_tensor *X, float beta, int R, const float *const *factors,
+                     const ntf_opts &o, double *out_dev, cudaStream_t st) {
+    CpDense s{};
+    NWay w{};
+    int rc = nway_setup(ctx, X, R, false, false, NTF_PREC_FP32, s, w, nullptr, 0, 0);
+    if (rc) return rc;
+    for (int m = 0; m < w.M; ++m) NTF_CUDA(ntf::pad_factor(factors[m], (int)w.dims[m], R, w.L[m], s.RP, st));
+    NTF_CUDA(ntf::pad_factor(factors[w.N - 2], (int)w.dims[w.N - 2], R, s.F[1], s.RP, st));
+    NTF_CUDA(ntf::pad_factor(factors[w.N - 1], (int)w.dims[w.N - 1], R, s.F[2], s.RP, st));
+    NTF_CUDA(ntf::kr_merge(kr_args(w, s, w.L, s.F[0], nullptr), st));
+    ntf::Cp3Args a = cp_args(&w.X3, s, o, beta);
+    for (int m = 0; m < 3; ++m) a.rec[m] = a.num[m] = a.den[m] = s.F[m];
+    {
+        PassTimer t(ctx, st);
+        NTF_CUDA(ntf::cp3_launch(s.plan, a, ntf::PM_OBJ, 0, st));
+    }
+    NTF_CUDA(ntf::reduce_objective(s.obj, s.plan.grid, 0.0, out_dev, st));
+    return NTF_OK;
+}
+
 int cp_dense_beta_div(ntf_ctx *ctx, const ntf_tensor *X, float beta, int R, const float *const *factors,
                       const ntf_opts &o, double *out_dev, cudaStream_t st) {
     CpDense s{};
@@ -711,6 +927,7 @@ int ntf_cp_mu_sweep(ntf_ctx *ctx, const ntf_tensor *X, float beta, int rank, flo
             return fail(ctx, NTF_ERR_UNSUPPORTED, "COO tensors are implemented for beta = 1 only");
         return ntf::coo_kl_sweep(ctx, X, rank, factors, o, objective_dev, st, /*jcomm=*/false);
     }
+    if (X->order > 3) return cp_nway_mu_sweep(ctx, X, beta, rank, factors, o, objective_dev, st);
     return cp_dense_mu_sweep(ctx, X, beta, rank, factors, o, objective_dev, st);
 }
 
@@ -820,6 +1037,7 @@ int ntf_jcomm_outer(ntf_ctx *ctx, int model, const ntf_tensor *X, float beta, in
                 return fail(ctx, NTF_ERR_UNSUPPORTED, "COO tensors are implemented for beta = 1 only");
             return ntf::coo_kl_sweep(ctx, X, rank_or_0, factors, o, objective_ref_dev, st, /*jcomm=*/true);
         }
+        if (X->order > 3) return cp_nway_jcomm(ctx, X, beta, rank_or_0, factors, o, objective_ref_dev, st);
         return cp_dense_jcomm(ctx, X, beta, rank_or_0, factors, o, objective_ref_dev, st);
     }
     if (model == NTF_TUCKER) {
@@ -848,6 +1066,7 @@ int ntf_beta_div(ntf_ctx *ctx, int model, const ntf_tensor *X, float beta, int r
                 return fail(ctx, NTF_ERR_UNSUPPORTED, "COO tensors are implemented for beta = 1 only");
             return ntf::coo_kl_objective(ctx, X, rank_or_0, factors, o, out_dev, st);
         }
+        if (X->order > 3) return cp_nway_beta_div(ctx, X, beta, rank_or_0, factors, o, out_dev, st);
         return cp_dense_beta_div(ctx, X, beta, rank_or_0, factors, o, out_dev, st);
     }
     if (model == NTF_TUCKER) {

@@ -236,6 +236,27 @@ struct ExtrapArgs {
 };
 cudaError_t extrapolate(const ExtrapArgs &x, cudaStream_t s);
 
+// Order N >= 4 on the 3-way kernels (leading modes 0..M-1 merged): Khatri-Rao factor of the
+// padded leading factors L (rows = prod dims[0..M-1]) with FP64 column-sum partials, and the fold
+// of a merged-mode contraction onto leading mode n.
+struct KrArgs {
+    const float *L[8];
+    int dims[8];
+    int M, rows, RP;
+    float *out;   // KR [rows][RP] or null
+    double *cs;   // column-sum partials [row block][RP] or null
+};
+cudaError_t kr_merge(const KrArgs &k, cudaStream_t s);
+struct FoldArgs {
+    const float *parts;  // [n_parts][rows][RP]
+    int n_parts;
+    const float *L[8];
+    int dims[8];
+    int M, n, rows, R, RP;
+    float *out;          // [dims[n]][RP]
+};
+cudaError_t kr_fold(const FoldArgs &f, cudaStream_t s);
+
 struct UpdArgs {
     MuEpiArgs e;
     const double *cs_in[2];

@@ -144,9 +144,9 @@ def test_error_codes():
     with pytest.raises(ntf.NtfError) as e:
         ntf.cp_mu_sweep(X, 1.0, A65)
     assert e.value.code == -8
-    X4 = dev(np.ones((2, 3, 4, 5)))
+    X2 = dev(np.ones((4, 5)))
     with pytest.raises(ntf.NtfError) as e:
-        ntf.cp_mu_sweep(X4, 1.0, [dev(np.ones((d, 3))) for d in (2, 3, 4, 5)])
+        ntf.cp_mu_sweep(X2, 1.0, [dev(np.ones((d, 3))) for d in (4, 5)])
     assert e.value.code == -8
     with pytest.raises(ntf.NtfError) as e:
         ntf.cp_mu_sweep(X, 1.0, A, inner_L=0)

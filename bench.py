@@ -43,7 +43,7 @@ def parse():
     p.add_argument("--no-ttt", action="store_true", help="skip the time-to-target runs")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     p.add_argument("--no-other", action="store_true",
-                   help="skip the Tucker 400^3 and sparse 3.3M-nonzero measurements")
+                   help="skip the Tucker 400^3, sparse 3.3M-nonzero and 4-way CP measurements")
     p.add_argument("--serve-jobs", type=int, default=48,
                    help="jobs of the serving-mix measurement in the default run (0: skip)")
     p.add_argument("--serve", action="store_true", help="print only the serving-mix line")
@@ -251,6 +251,51 @@ def run_coo_c4(ntf, ctx, peaks, iters=20, R=32, seed=0):
                          "frac": byt / (ms / 1e3) / 1e9 / peaks["hbm_gbs"],
                          "of": "whole outer iteration (per-mode sorted copies are cached after the first call): "
                                "4 passes x 20 B/nnz streamed; factor-row gathers hit L2"}}
+
+
+def run_cp_4way(ntf, ctx, peaks, iters=20, dims=(80, 70, 60, 50), R=10, seed=5):
+    """Dense 4-way CP 80 x 70 x 60 x 50, R = 10 (the shape of the paper's synthetic CP
+    experiment): Gamma(2,1) factors x Gamma(10,0.1) noise, init U(0.1, 1).  Times B-CoMM
+    sweeps at beta in {1/2, 1, 3/2} and J-CoMM outer iterations (L = 1) at beta = 1, FP32 and
+    TF32.  The tensor (67 MB) fits in the 129 MB L2, so a 256 MB buffer is written before
+    every timed iteration and each iteration is timed alone.  Roofline: a B-CoMM sweep makes
+    4 passes over X (leading modes on the merged 3-way view), a J-CoMM iteration at beta = 1
+    one; 4 bytes per entry and pass against the HBM copy bandwidth."""
+    import torch
+    import synth
+    dev = torch.device("cuda", torch.cuda.current_device())
+    Xn, _ = synth.cp_dense(dims, R, seed=seed, kind="gamma_noise")
+    X = torch.tensor(Xn, dtype=torch.float32, device=dev)
+    A0 = [torch.tensor(a, dtype=torch.float32, device=dev) for a in synth.init_factors(dims, R, seed=seed + 1)]
+    obj = torch.zeros(1, dtype=torch.float64, device=dev)
+    flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)
+    entries = int(np.prod(dims))
+    out = {"workload": "dense 4-way CP %s, R=%d" % ("x".join(map(str, dims)), R),
+           "l2": "256 MB write between timed iterations"}
+    for prec in ("fp32", "tf32"):
+        res = {}
+        for name, beta in (("block_mu_b0.5", 0.5), ("block_mu_b1", 1.0), ("block_mu_b1.5", 1.5), ("jcomm_b1", 1.0)):
+            A = [a.clone() for a in A0]
+            fn = ntf.jcomm_outer if name.startswith("jcomm") else ntf.cp_mu_sweep
+            for _ in range(3):
+                fn(X, beta, A, objective=obj, ctx=ctx, precision=prec)
+            torch.cuda.synchronize()
+            tot = 0.0
+            for _ in range(iters):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                fn(X, beta, A, objective=obj, ctx=ctx, precision=prec)
+                e1.record()
+                torch.cuda.synchronize()
+                tot += e0.elapsed_time(e1)
+            ms = tot / iters
+            passes = 1 if name.startswith("jcomm") else len(dims)
+            gbs = passes * 4 * entries / (ms / 1e3) / 1e9
+            res[name] = {"ms": ms, "objective": obj.item(), "hbm_gbs_algorithmic": gbs,
+                         "frac_of_measured_hbm": gbs / peaks["hbm_gbs"]}
+        out[prec] = res
+    return out
 
 
 def load_peaks():
@@ -616,7 +661,8 @@ def main():
 
     other = None
     if not args.no_other:
-        other = {"tucker_c3": run_tucker_c3(ntf, ctx, peaks), "coo_c4": run_coo_c4(ntf, ctx, peaks)}
+        other = {"tucker_c3": run_tucker_c3(ntf, ctx, peaks), "coo_c4": run_coo_c4(ntf, ctx, peaks),
+                 "cp_4way": run_cp_4way(ntf, ctx, peaks)}
 
     serving = None
     if args.serve_jobs > 0:

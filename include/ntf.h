@@ -88,6 +88,11 @@ typedef struct {
                       sets the order of the partial sums, so results may differ from a run with
                       another table in the last bits.  Ignored (cost-model plan, nothing cached)
                       while the stream is being captured. */
+    int merge;     /* dense CP of order N >= 4, which runs on the 3-way passes with the modes cut
+                      into three runs of consecutive modes [0, a), [a, b), [b, N) (a run of
+                      several modes is one 3-way mode whose factor is the Khatri-Rao product of
+                      the run's blocks): 0 = the library picks the cut (0); else 16 * a + b,
+                      1 <= a < b <= N - 1 (NTF_ERR_ARG otherwise).  Ignored at N = 3. */
 } ntf_opts;
 
 /* Fills *o with the defaults shown above. */

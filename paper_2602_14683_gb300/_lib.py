@@ -47,7 +47,7 @@ class Result(C.Structure):
 
 class Opts(C.Structure):
     _fields_ = [("eps", C.c_double), ("eps_x", C.c_double), ("inner_L", C.c_int), ("precision", C.c_int),
-                ("autotune", C.c_int)]
+                ("autotune", C.c_int), ("merge", C.c_int)]
 
 
 if not os.path.exists(LIB_PATH):
@@ -197,11 +197,14 @@ def _ptrs(tensors, name):
     return (C.c_void_p * len(tensors))(*[t.data_ptr() for t in tensors])
 
 
-def make_opts(eps=1e-12, eps_x=1e-12, inner_L=1, precision="fp32", autotune=False):
+def make_opts(eps=1e-12, eps_x=1e-12, inner_L=1, precision="fp32", autotune=False, merge=None):
+    """merge: None, or (a, b) cutting the modes of an order N >= 4 tensor into the runs
+    [0, a), [a, b), [b, N) of the 3-way view."""
     o = Opts()
     _lib.ntf_opts_default(C.byref(o))
     o.eps, o.eps_x, o.inner_L = float(eps), float(eps_x), int(inner_L)
     o.autotune = 1 if autotune else 0
+    o.merge = 0 if merge is None else 16 * int(merge[0]) + int(merge[1])
     o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     return o
 

@@ -286,21 +286,30 @@ cudaError_t kr_merge(const KrArgs &k, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// out[i_n][r] = sum over the other leading indices (row-major order) of
-//   (sum over the parts, in order, of parts[p][merged index][r]) * prod_{m != n} L_m[i_m][r]
-// -- CPContr^(n) of the merged-mode contraction, one thread per (i_n, r), FP64 accumulation.
-__global__ void kr_fold_kernel(FoldArgs f) {
+// sum[row][r] = sum over the parts, in order, of parts[p][row][r] (FP32)
+__global__ void fold_parts_kernel(const float *parts, int n_parts, int64_t n, float *sum) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int RP = f.RP;
-    if (t >= (int64_t)f.dims[f.n] * RP) return;
-    const int in = (int)(t / RP), r = (int)(t % RP);
+    if (t >= n) return;
+    float v = 0.0f;
+    for (int p = 0; p < n_parts; ++p) v += parts[(int64_t)p * n + t];
+    sum[t] = v;
+}
+
+// out[i_n][r] = sum over the run's other indices (row-major order) of
+//   S[merged index][r] * prod_{m != n} L_m[i_m][r]
+// -- CPContr^(n) of the merged-mode contraction S.  One block per i_n; RP-lane group g of the
+// block takes the other-index positions q = g, g + G, ..., accumulating in FP64, and the groups'
+// sums are added in group order.
+__global__ void kr_fold_kernel(FoldArgs f, const float *S) {
+    __shared__ double sh[256];
+    const int RP = f.RP, G = blockDim.x / RP, t = threadIdx.x, r = t % RP, g = t / RP;
+    const int in = blockIdx.x;
     int64_t other = 1;
     for (int m = 0; m < f.M; ++m)
         if (m != f.n) other *= f.dims[m];
-    const int64_t stride = f.rows * RP;
     double acc = 0.0;
-    for (int64_t q = 0; q < other; ++q) {
-        // the other leading indices from q (row-major over m != n), and the merged row index
+    for (int64_t q = g; q < other; q += G) {
+        // the other indices from q (row-major over m != n), and the merged row index
         int64_t rem = q, row = 0, mul = 1;
         float w = 1.0f;
         for (int m = f.M - 1; m >= 0; --m) {
@@ -315,22 +324,29 @@ __global__ void kr_fold_kernel(FoldArgs f) {
             row += (int64_t)im * mul;
             mul *= f.dims[m];
         }
-        float s = 0.0f;
-        for (int p = 0; p < f.n_parts; ++p) s += f.parts[(int64_t)p * stride + row * RP + r];
-        acc += (double)s * (double)w;
+        acc += (double)S[row * RP + r] * (double)w;
     }
-    f.out[t] = r < f.R ? (float)acc : 0.0f;
+    const double tot = group_sum(sh, acc, RP, t);
+    if (t < RP) f.out[(int64_t)in * RP + t] = t < f.R ? (float)tot : 0.0f;
 }
 
 cudaError_t kr_fold(const FoldArgs &f, cudaStream_t s) {
-    const int64_t n = (int64_t)f.dims[f.n] * f.RP;
-    kr_fold_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(f);
+    const float *S = f.parts;
+    if (f.n_parts > 1) {
+        const int64_t n = (int64_t)f.rows * f.RP;
+        fold_parts_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(f.parts, f.n_parts, n, f.scratch);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        S = f.scratch;
+    }
+    kr_fold_kernel<<<f.dims[f.n], 256, 0, s>>>(f, S);
     return cudaGetLastError();
 }
 
 cudaError_t prep_factors(const PrepArgs &p, cudaStream_t s) {
     int blocks = 0;
     for (int m = 0; m < 3; ++m) blocks += row_blocks(p.rows[m], p.RP);
+    if (blocks == 0) return cudaSuccess;
     prep_kernel<<<blocks, 256, 0, s>>>(p);
     return cudaGetLastError();
 }

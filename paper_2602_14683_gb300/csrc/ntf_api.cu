@@ -155,10 +155,10 @@ int cp_dense_setup(ntf_ctx *ctx, const ntf_tensor *X, int R, bool jcomm, bool ne
     s.J = (int)X->dims[1];
     s.K = (int)X->dims[2];
     s.R = R;
-    s.RP = rank_pad(R);
     // tensor-core passes where the request asks for them and the shapes allow (rank padded
     // to 32, rows of X 16-byte aligned for TMA); FP32 CUDA-core passes otherwise
-    const bool tc = precision != NTF_PREC_FP32 && ntf::cp3_tc_eligible(s.RP, s.K, X->values);
+    const bool tc = precision != NTF_PREC_FP32 && R <= 32 && ntf::cp3_tc_eligible(32, s.K, X->values);
+    s.RP = tc ? 32 : rank_pad(R);
     s.tc = tc;
     // 256-column blocks where the tensor memory allows them (KL: no denominator accumulators;
     // single TF32: no low-part C tile)
@@ -584,100 +584,199 @@ int cp_dense_mu_sweep_extrap(ntf_ctx *ctx, const ntf_tensor *X, float beta, int 
 }
 
 // ------------------------------------------------------------ dense CP of order N >= 4
-// The leading modes 0..M-1 (M = N - 2) are merged: X (row-major) is then the 3-way tensor
-// (prod_{m<M} I_m) x I_{N-2} x I_{N-1}, whose first factor is the Khatri-Rao product of the
-// leading factors.  Modes N-2 and N-1 are 3-way modes 2 and 3 of that view; a leading mode n
-// takes the view's mode-1 contraction and folds it against the other leading factors
-// (CPContr^(n) over the merged index), Section 6.1.
+// The N modes are cut into three runs of consecutive modes, [0, a), [a, b), [b, N); X
+// (row-major) is then the 3-way tensor (prod of each run's dims), and a run of several modes
+// has the Khatri-Rao product of its factors (row-major over the run) as its 3-way factor.  A
+// mode alone in its run is a 3-way mode; a mode inside a longer run takes that run's 3-way
+// contraction and folds it against the run's other factors (CPContr^(n) over the merged index,
+// Section 6.1).
 struct NWay {
-    int N, M;
+    int N;
     int64_t dims[8];
-    int64_t merged;
+    int gb[3], ge[3];      // runs of modes
+    int view[8];           // run of each mode
     ntf_tensor X3;
     int64_t dims3[3];
-    float *L[8], *Lt[8];  // padded current / reference leading factors
-    float *num, *den;     // folded Num / Den of a leading mode, [max I_n][RP]
+    // padded current / reference / chi1 / chi2 blocks of each mode: the view's slot for a
+    // mode alone in its run, a buffer of its own otherwise (the slot then holds the run's
+    // Khatri-Rao product)
+    float *P[8], *Pt[8], *C1P[8], *C2P[8];
+    float *num, *den;      // folded Num / Den of a merged mode, [max I_n][RP]
+    float *sum;            // summed partials of a merged run, [max run extent][RP]
 };
 
-int nway_setup(ntf_ctx *ctx, const ntf_tensor *X, int R, bool jcomm, bool need_den, int precision, CpDense &s,
-               NWay &w, const ntf_opts *tune_opts, int tune_bk, int tune_ms) {
-    w.N = X->order;
-    w.M = w.N - 2;
-    w.merged = 1;
-    for (int n = 0; n < w.N; ++n) w.dims[n] = X->dims[n];
-    for (int m = 0; m < w.M; ++m) w.merged *= X->dims[m];
-    if (w.merged > (int64_t)0x7fffffff) return fail(ctx, NTF_ERR_SHAPE, "product of the leading dimensions too large");
-    w.dims3[0] = w.merged;
-    w.dims3[1] = X->dims[w.N - 2];
-    w.dims3[2] = X->dims[w.N - 1];
-    w.X3 = *X;
-    w.X3.order = 3;
-    w.X3.dims = w.dims3;
-    int rc = cp_dense_setup(ctx, &w.X3, R, jcomm, need_den, precision, s, tune_opts, tune_bk, tune_ms);
-    if (rc) return rc;
-    int64_t maxI = 1;
-    for (int m = 0; m < w.M; ++m) {
-        const size_t fb = sizeof(float) * (size_t)w.dims[m] * s.RP;
-        w.L[m] = (float *)ws_get(ctx, "nwL" + std::to_string(m), fb);
-        w.Lt[m] = jcomm ? (float *)ws_get(ctx, "nwLt" + std::to_string(m), fb) : w.L[m];
-        if (!w.L[m] || !w.Lt[m]) return fail(ctx, NTF_ERR_OOM, "workspace allocation failed");
-        maxI = std::max(maxI, w.dims[m]);
+bool nway_single(const NWay &w, int v) { return w.ge[v] - w.gb[v] == 1; }
+
+// Run boundaries: opts->merge when given, else the split whose padded 3-way tile work is
+// least, tensor-core eligibility (rank <= 32, last run's extent a multiple of 4) weighing 8x.
+int nway_split(ntf_ctx *ctx, const ntf_tensor *X, int R, const ntf_opts &o, int precision, int &a, int &b) {
+    const int N = X->order;
+    if (o.merge) {
+        a = o.merge / 16;
+        b = o.merge % 16;
+        if (!(1 <= a && a < b && b <= N - 1))
+            return fail(ctx, NTF_ERR_ARG, "merge %d does not split %d modes into three runs", o.merge, N);
+        return NTF_OK;
     }
-    w.num = (float *)ws_get(ctx, "nwNum", sizeof(float) * (size_t)maxI * s.RP);
-    w.den = (float *)ws_get(ctx, "nwDen", sizeof(float) * (size_t)maxI * s.RP);
-    if (!w.num || !w.den) return fail(ctx, NTF_ERR_OOM, "workspace allocation failed");
+    double best = -1.0;
+    for (int ca = 1; ca <= N - 2; ++ca)
+        for (int cb = ca + 1; cb <= N - 1; ++cb) {
+            double e[3] = {1.0, 1.0, 1.0};
+            for (int m = 0; m < N; ++m) e[m < ca ? 0 : m < cb ? 1 : 2] *= (double)X->dims[m];
+            if (e[0] > 2147483647.0 || e[1] > 2147483647.0 || e[2] > 2147483647.0) continue;
+            const bool tc = precision != NTF_PREC_FP32 && R <= 32 &&
+                            ntf::cp3_tc_eligible(32, (int)e[2], X->values);
+            const double kb = tc ? 128.0 : 64.0;
+            const double cells = e[0] * std::ceil(e[1] / 128.0) * 128.0 * std::ceil(e[2] / kb) * kb;
+            const double cost = cells * (tc ? 1.0 : 8.0);
+            if (best < 0.0 || cost < best) {
+                best = cost;
+                a = ca;
+                b = cb;
+            }
+        }
+    if (best < 0.0) return fail(ctx, NTF_ERR_SHAPE, "no split of the modes fits 32-bit extents");
     return NTF_OK;
 }
 
-ntf::KrArgs kr_args(const NWay &w, const CpDense &s, float *const *L, float *out, double *cs) {
-    ntf::KrArgs k{};
-    for (int m = 0; m < w.M; ++m) {
-        k.L[m] = L[m];
-        k.dims[m] = (int)w.dims[m];
+int nway_setup(ntf_ctx *ctx, const ntf_tensor *X, int R, bool jcomm, bool need_den, int precision,
+               const ntf_opts &o, CpDense &s, NWay &w) {
+    w.N = X->order;
+    int a = 0, b = 0;
+    int rc = nway_split(ctx, X, R, o, precision, a, b);
+    if (rc) return rc;
+    w.gb[0] = 0, w.ge[0] = a, w.gb[1] = a, w.ge[1] = b, w.gb[2] = b, w.ge[2] = w.N;
+    for (int v = 0; v < 3; ++v) {
+        w.dims3[v] = 1;
+        for (int m = w.gb[v]; m < w.ge[v]; ++m) {
+            w.dims[m] = X->dims[m];
+            w.dims3[v] *= X->dims[m];
+            w.view[m] = v;
+        }
     }
-    k.M = w.M;
-    k.rows = (int)w.merged;
+    w.X3 = *X;
+    w.X3.order = 3;
+    w.X3.dims = w.dims3;
+    if ((rc = cp_dense_setup(ctx, &w.X3, R, jcomm, need_den, precision, s))) return rc;
+    const bool chi = jcomm && need_den;
+    int64_t maxI = 1;
+    for (int m = 0; m < w.N; ++m) {
+        const int v = w.view[m];
+        maxI = std::max(maxI, w.dims[m]);
+        if (nway_single(w, v)) {
+            w.P[m] = s.F[v];
+            w.Pt[m] = jcomm ? s.Ft[v] : s.F[v];
+            w.C1P[m] = chi ? s.C1[v] : nullptr;
+            w.C2P[m] = chi ? s.C2[v] : nullptr;
+            continue;
+        }
+        const size_t fb = sizeof(float) * (size_t)w.dims[m] * s.RP;
+        const std::string k = std::to_string(m);
+        w.P[m] = (float *)ws_get(ctx, "nwL" + k, fb);
+        w.Pt[m] = jcomm ? (float *)ws_get(ctx, "nwLt" + k, fb) : w.P[m];
+        w.C1P[m] = chi ? (float *)ws_get(ctx, "nwC1" + k, fb) : nullptr;
+        w.C2P[m] = chi ? (float *)ws_get(ctx, "nwC2" + k, fb) : nullptr;
+        if (!w.P[m] || !w.Pt[m] || (chi && (!w.C1P[m] || !w.C2P[m])))
+            return fail(ctx, NTF_ERR_OOM, "workspace allocation failed");
+    }
+    int64_t maxRun = 1;
+    for (int v = 0; v < 3; ++v)
+        if (!nway_single(w, v)) maxRun = std::max(maxRun, w.dims3[v]);
+    w.num = (float *)ws_get(ctx, "nwNum", sizeof(float) * (size_t)maxI * s.RP);
+    w.den = (float *)ws_get(ctx, "nwDen", sizeof(float) * (size_t)maxI * s.RP);
+    w.sum = (float *)ws_get(ctx, "nwSum", sizeof(float) * (size_t)maxRun * s.RP);
+    if (!w.num || !w.den || !w.sum) return fail(ctx, NTF_ERR_OOM, "workspace allocation failed");
+    return NTF_OK;
+}
+
+// Khatri-Rao product of run v's blocks B[m] (row-major over the run) into out, with FP64
+// column-sum partials into cs (either may be null)
+cudaError_t nway_merge(const NWay &w, const CpDense &s, int v, float *const *B, float *out, double *cs,
+                       cudaStream_t st) {
+    ntf::KrArgs k{};
+    k.M = w.ge[v] - w.gb[v];
+    for (int j = 0; j < k.M; ++j) {
+        k.L[j] = B[w.gb[v] + j];
+        k.dims[j] = (int)w.dims[w.gb[v] + j];
+    }
+    k.rows = (int)w.dims3[v];
     k.RP = s.RP;
     k.out = out;
     k.cs = cs;
-    return k;
+    return ntf::kr_merge(k, st);
 }
 
-// pads the trailing two factors into the view's F[1], F[2] (and, for J-CoMM, the reference
-// copies Ft[1], Ft[2]) with FP64 column-sum partials; the view's mode 1 is left to kr_merge
-int nway_prep_trailing(ntf_ctx *ctx, NWay &w, CpDense &s, float *const *factors, bool ref, cudaStream_t st) {
+// Padded working blocks from the user's factors: the 3-way slots of single-mode runs in one
+// prep launch (with reference / chi copies and column sums), the merged runs' own buffers, then
+// the merged slots (reference slot for J-CoMM, chi slots equal to it at the start).
+int nway_init(ntf_ctx *ctx, NWay &w, CpDense &s, float *const *factors, bool ref, bool chi, cudaStream_t st) {
     ntf::PrepArgs p{};
-    p.rows[0] = 0;  // no row blocks for the merged slot
-    for (int m = 1; m < 3; ++m) {
-        p.src[m] = factors[w.M + m - 1];
-        p.rows[m] = (int)w.dims[w.M + m - 1];
-        p.F[m] = s.F[m];
-        p.Ft[m] = ref ? s.Ft[m] : nullptr;
-        p.cs[m] = s.cs[m];
+    for (int v = 0; v < 3; ++v) {
+        if (!nway_single(w, v)) continue;  // rows 0: no blocks for this slot
+        const int m = w.gb[v];
+        p.src[v] = factors[m];
+        p.rows[v] = (int)w.dims[m];
+        p.F[v] = s.F[v];
+        p.Ft[v] = ref ? s.Ft[v] : nullptr;
+        p.C1[v] = chi ? s.C1[v] : nullptr;
+        p.C2[v] = chi ? s.C2[v] : nullptr;
+        p.cs[v] = s.cs[v];
     }
     p.R = s.R;
     p.RP = s.RP;
     NTF_CUDA(ntf::prep_factors(p, st));
+    for (int m = 0; m < w.N; ++m) {
+        if (nway_single(w, w.view[m])) continue;
+        const int64_t nel = w.dims[m] * s.RP;
+        NTF_CUDA(ntf::pad_factor(factors[m], (int)w.dims[m], s.R, w.Pt[m], s.RP, st));
+        if (ref) NTF_CUDA(ntf::copy_f32(w.Pt[m], w.P[m], nel, st));
+        if (chi) {
+            NTF_CUDA(ntf::copy_f32(w.Pt[m], w.C1P[m], nel, st));
+            NTF_CUDA(ntf::copy_f32(w.Pt[m], w.C2P[m], nel, st));
+        }
+    }
+    for (int v = 0; v < 3; ++v) {
+        if (nway_single(w, v)) continue;
+        float *slot = ref ? s.Ft[v] : s.F[v];
+        NTF_CUDA(nway_merge(w, s, v, w.Pt, slot, s.cs[v], st));
+        if (chi) {
+            NTF_CUDA(ntf::copy_f32(slot, s.C1[v], w.dims3[v] * s.RP, st));
+            NTF_CUDA(ntf::copy_f32(slot, s.C2[v], w.dims3[v] * s.RP, st));
+        }
+    }
     return NTF_OK;
 }
 
-// update of leading mode n from the view's mode-1 partial sums: fold, closed-form KL
-// denominator (product of the column sums of every other current factor) or folded Den, MU
-int nway_leading_update(ntf_ctx *ctx, NWay &w, CpDense &s, int n, float beta, const ntf_opts &o, bool kl,
-                        float *const *Lfold, const float *pre, float *out, float *user, cudaStream_t st) {
+// Update of a mode inside a merged run from the run's 3-way partial sums: Num folded against
+// Lnum, Den folded against Lden or, at beta = 1, the closed form (product of the column sums of
+// every other current block); MU from pre into out, with chi1 / chi2 of the result against ref
+// when those are given, and an unpadded copy into user when given.
+struct RunUpd {
+    float *const *Lnum, *const *Lden;
+    const float *pre;
+    float *out, *user;
+    const float *ref;
+    float *chi1, *chi2;
+};
+
+int nway_run_update(ntf_ctx *ctx, NWay &w, CpDense &s, int n, float beta, const ntf_opts &o, bool kl,
+                    const RunUpd &q, cudaStream_t st) {
+    const int v = w.view[n];
+    const int parts[3] = {s.plan.parts1, s.plan.parts2, s.plan.parts3};
     ntf::FoldArgs f{};
-    f.parts = s.pn[0];
-    f.n_parts = s.plan.parts1;
-    for (int m = 0; m < w.M; ++m) {
-        f.L[m] = Lfold[m];
-        f.dims[m] = (int)w.dims[m];
+    f.parts = s.pn[v];
+    f.n_parts = parts[v];
+    f.M = w.ge[v] - w.gb[v];
+    for (int j = 0; j < f.M; ++j) {
+        f.L[j] = q.Lnum[w.gb[v] + j];
+        f.dims[j] = (int)w.dims[w.gb[v] + j];
     }
-    f.M = w.M;
-    f.n = n;
-    f.rows = (int)w.merged;
+    f.n = n - w.gb[v];
+    f.rows = (int)w.dims3[v];
     f.R = s.R;
     f.RP = s.RP;
     f.out = w.num;
+    f.scratch = w.sum;
     NTF_CUDA(ntf::kr_fold(f, st));
     ntf::MuEpiArgs e{};
     e.pn = w.num;
@@ -687,92 +786,116 @@ int nway_leading_update(ntf_ctx *ctx, NWay &w, CpDense &s, int n, float beta, co
     e.R = s.R;
     if (kl) {
         const float *cf[8];
-        int rows[8], q = 0;
-        for (int m = 0; m < w.M; ++m)
-            if (m != n) { cf[q] = w.L[m]; rows[q] = (int)w.dims[m]; ++q; }
-        cf[q] = s.F[1]; rows[q] = (int)w.dims[w.N - 2]; ++q;
-        cf[q] = s.F[2]; rows[q] = (int)w.dims[w.N - 1]; ++q;
-        NTF_CUDA(ntf::colsum_prod(q, cf, rows, s.RP, s.denc, st));
+        int rows[8], c = 0;
+        for (int m = 0; m < w.N; ++m)
+            if (m != n) {
+                cf[c] = w.P[m];
+                rows[c] = (int)w.dims[m];
+                ++c;
+            }
+        NTF_CUDA(ntf::colsum_prod(c, cf, rows, s.RP, s.denc, st));
         e.den_closed = s.denc;
     } else {
-        f.parts = s.pd[0];
+        f.parts = s.pd[v];
+        for (int j = 0; j < f.M; ++j) f.L[j] = q.Lden[w.gb[v] + j];
         f.out = w.den;
         NTF_CUDA(ntf::kr_fold(f, st));
         e.pd = w.den;
     }
-    e.pre = pre;
-    e.out = out;
+    e.pre = q.pre;
+    e.out = q.out;
+    e.ref = q.ref;
+    e.chi1_out = q.chi1;
+    e.chi2_out = q.chi2;
     e.beta = beta;
     e.gamma = ntf::mu_gamma(beta);
     e.eps = (float)o.eps;
     NTF_CUDA(ntf::mu_epilogue(e, st));
-    if (user) NTF_CUDA(ntf::unpad_factor(out, (int)w.dims[n], s.R, s.RP, user, st));
+    if (q.user) NTF_CUDA(ntf::unpad_factor(q.out, (int)w.dims[n], s.R, s.RP, q.user, st));
     return NTF_OK;
 }
 
+int mode_flag(int v) { return v == 0 ? ntf::PM_M1 : v == 1 ? ntf::PM_M2 : ntf::PM_M3; }
+
+// B-CoMM sweep (Algorithm 1) over the N modes in order on the 3-way view.
 int cp_nway_mu_sweep(ntf_ctx *ctx, const ntf_tensor *X, float beta, int R, float *const *factors, const ntf_opts &o,
                      double *objective_dev, cudaStream_t st) {
-    const int bk = ntf::beta_kind(beta);
-    const bool kl = bk == ntf::BK_KL;
+    const bool kl = ntf::beta_kind(beta) == ntf::BK_KL;
     CpDense s{};
     NWay w{};
-    int rc = nway_setup(ctx, X, R, false, !kl, o.precision, s, w, nullptr, 0, 0);
+    int rc = nway_setup(ctx, X, R, false, !kl, o.precision, o, s, w);
     if (rc) return rc;
-    for (int m = 0; m < w.M; ++m) NTF_CUDA(ntf::pad_factor(factors[m], (int)w.dims[m], R, w.L[m], s.RP, st));
-    if ((rc = nway_prep_trailing(ctx, w, s, factors, false, st))) return rc;
+    if ((rc = nway_init(ctx, w, s, factors, false, false, st))) return rc;
     ntf::Cp3Args a = cp_args(&w.X3, s, o, beta);
     for (int m = 0; m < 3; ++m) a.rec[m] = a.num[m] = a.den[m] = s.F[m];
     for (int n = 0; n < w.N; ++n) {
-        if (n <= w.M) NTF_CUDA(ntf::kr_merge(kr_args(w, s, w.L, s.F[0], s.cs[0]), st));  // current leading blocks
-        if (n < w.M) {
-            const int ms = ntf::PM_M1 | ((n == 0 && objective_dev) ? ntf::PM_OBJ : 0);
-            if ((rc = launch_pass(ctx, s, a, ms, kl ? 0 : 1, st))) return rc;
-            if (n == 0 && objective_dev) NTF_CUDA(ntf::reduce_objective(s.obj, s.plan.grid, 0.0, objective_dev, st));
-            if ((rc = nway_leading_update(ctx, w, s, n, beta, o, kl, w.L, w.L[n], w.L[n], factors[n], st))) return rc;
-        } else {
-            const int k = n - w.M + 1;  // the view's mode 2 or 3
-            if ((rc = launch_pass(ctx, s, a, k == 1 ? ntf::PM_M2 : ntf::PM_M3, kl ? 0 : 1, st))) return rc;
-            ntf::UpdArgs u = upd_args(s, k, beta, o, kl, s.F[k], factors[n]);
+        const int v = w.view[n];
+        const bool obj = n == 0 && objective_dev;
+        if ((rc = launch_pass(ctx, s, a, mode_flag(v) | (obj ? ntf::PM_OBJ : 0), kl ? 0 : 1, st))) return rc;
+        if (obj) NTF_CUDA(ntf::reduce_objective(s.obj, s.plan.grid, 0.0, objective_dev, st));
+        if (nway_single(w, v)) {
+            ntf::UpdArgs u = upd_args(s, v, beta, o, kl, s.F[v], factors[n]);
             NTF_CUDA(ntf::mode_update(u, st));
+        } else {
+            const RunUpd q{w.P, w.P, w.P[n], w.P[n], factors[n], nullptr, nullptr, nullptr};
+            if ((rc = nway_run_update(ctx, w, s, n, beta, o, kl, q, st))) return rc;
+            NTF_CUDA(nway_merge(w, s, v, w.P, s.F[v], s.cs[v], st));
         }
     }
     return NTF_OK;
 }
 
-// J-CoMM at beta = 1 (Section 5.3 with chi1(Z, Zt) = Zt): one pass over X from the reference
-// gives every numerator (the leading ones by folding with the reference leading blocks);
-// Den^(n) = prod_{m != n} colsum of the current blocks.
+// J-CoMM (Algorithm 2) on the 3-way view.  The reference blocks stay in Pt / Ft, the current
+// ones in P / F.  At beta = 1 (chi1(Z, Zt) = Zt) one pass over X from the reference gives every
+// numerator (a merged mode's by folding with the reference blocks of its run) and
+// Den^(n) = prod_{m != n} colsum of the current blocks.  Otherwise every block update takes a
+// pass with Xhat from the reference and Num / Den contracted against chi1 / chi2 of the current
+// blocks (folded inside a merged run, whose slots hold the Khatri-Rao products of its chi blocks).
 int cp_nway_jcomm(ntf_ctx *ctx, const ntf_tensor *X, float beta, int R, float *const *factors, const ntf_opts &o,
                   double *objective_dev, cudaStream_t st) {
-    if (ntf::beta_kind(beta) != ntf::BK_KL)
-        return fail(ctx, NTF_ERR_UNSUPPORTED, "J-CoMM for dense orders N >= 4 is implemented at beta = 1");
+    const bool kl = ntf::beta_kind(beta) == ntf::BK_KL;
     CpDense s{};
     NWay w{};
-    int rc = nway_setup(ctx, X, R, true, false, o.precision, s, w, nullptr, 0, 0);
+    int rc = nway_setup(ctx, X, R, true, !kl, o.precision, o, s, w);
     if (rc) return rc;
-    for (int m = 0; m < w.M; ++m) {
-        NTF_CUDA(ntf::pad_factor(factors[m], (int)w.dims[m], R, w.Lt[m], s.RP, st));
-        NTF_CUDA(ntf::copy_f32(w.Lt[m], w.L[m], w.dims[m] * s.RP, st));
-    }
-    if ((rc = nway_prep_trailing(ctx, w, s, factors, true, st))) return rc;
-    NTF_CUDA(ntf::kr_merge(kr_args(w, s, w.Lt, s.Ft[0], s.cs[0]), st));
+    if ((rc = nway_init(ctx, w, s, factors, true, !kl, st))) return rc;
     ntf::Cp3Args a = cp_args(&w.X3, s, o, beta);
-    for (int m = 0; m < 3; ++m) a.rec[m] = a.num[m] = a.den[m] = s.Ft[m];
-    if ((rc = launch_pass(ctx, s, a, ntf::PM_M1 | ntf::PM_M2 | ntf::PM_M3 | ntf::PM_OBJ, 0, st))) return rc;
-    if (objective_dev) NTF_CUDA(ntf::reduce_objective(s.obj, s.plan.grid, 0.0, objective_dev, st));
+    for (int m = 0; m < 3; ++m) {
+        a.rec[m] = s.Ft[m];
+        a.num[m] = kl ? s.Ft[m] : s.C1[m];
+        a.den[m] = kl ? s.Ft[m] : s.C2[m];
+    }
+    if (kl) {
+        if ((rc = launch_pass(ctx, s, a, ntf::PM_M1 | ntf::PM_M2 | ntf::PM_M3 | ntf::PM_OBJ, 0, st))) return rc;
+        if (objective_dev) NTF_CUDA(ntf::reduce_objective(s.obj, s.plan.grid, 0.0, objective_dev, st));
+    }
     for (int l = 0; l < o.inner_L; ++l) {
         for (int n = 0; n < w.N; ++n) {
+            const int v = w.view[n];
             float *user = l == o.inner_L - 1 ? factors[n] : nullptr;
-            if (n < w.M) {
-                // the trailing current blocks sit in the view's F[1], F[2]: until their first
-                // update they equal the reference (F = Ft after the prep copies)
-                if ((rc = nway_leading_update(ctx, w, s, n, beta, o, true, w.Lt, w.Lt[n], w.L[n], user, st)))
-                    return rc;
-            } else {
-                const int k = n - w.M + 1;
-                if (n == w.M) NTF_CUDA(ntf::kr_merge(kr_args(w, s, w.L, nullptr, s.cs[0]), st));  // current leading
-                ntf::UpdArgs u = upd_args(s, k, beta, o, true, s.Ft[k], user);
+            if (!kl) {
+                const bool obj = l == 0 && n == 0 && objective_dev;
+                if ((rc = launch_pass(ctx, s, a, mode_flag(v) | (obj ? ntf::PM_OBJ : 0), 1, st))) return rc;
+                if (obj) NTF_CUDA(ntf::reduce_objective(s.obj, s.plan.grid, 0.0, objective_dev, st));
+            }
+            if (nway_single(w, v)) {
+                ntf::UpdArgs u = upd_args(s, v, beta, o, kl, s.Ft[v], user);
+                if (!kl) {
+                    u.e.ref = s.Ft[v];
+                    u.e.chi1_out = s.C1[v];
+                    u.e.chi2_out = s.C2[v];
+                }
                 NTF_CUDA(ntf::mode_update(u, st));
+                continue;
+            }
+            const RunUpd q = kl ? RunUpd{w.Pt, w.Pt, w.Pt[n], w.P[n], user, nullptr, nullptr, nullptr}
+                                : RunUpd{w.C1P, w.C2P, w.Pt[n], w.P[n], user, w.Pt[n], w.C1P[n], w.C2P[n]};
+            if ((rc = nway_run_update(ctx, w, s, n, beta, o, kl, q, st))) return rc;
+            if (kl) {
+                NTF_CUDA(nway_merge(w, s, v, w.P, nullptr, s.cs[v], st));  // current column sums
+            } else {
+                NTF_CUDA(nway_merge(w, s, v, w.C1P, s.C1[v], nullptr, st));
+                NTF_CUDA(nway_merge(w, s, v, w.C2P, s.C2[v], nullptr, st));
             }
         }
     }
@@ -783,12 +906,9 @@ int cp_nway_beta_div(ntf_ctx *ctx, const ntf_tensor *X, float beta, int R, const
                      const ntf_opts &o, double *out_dev, cudaStream_t st) {
     CpDense s{};
     NWay w{};
-    int rc = nway_setup(ctx, X, R, false, false, NTF_PREC_FP32, s, w, nullptr, 0, 0);
+    int rc = nway_setup(ctx, X, R, false, false, NTF_PREC_FP32, o, s, w);
     if (rc) return rc;
-    for (int m = 0; m < w.M; ++m) NTF_CUDA(ntf::pad_factor(factors[m], (int)w.dims[m], R, w.L[m], s.RP, st));
-    NTF_CUDA(ntf::pad_factor(factors[w.N - 2], (int)w.dims[w.N - 2], R, s.F[1], s.RP, st));
-    NTF_CUDA(ntf::pad_factor(factors[w.N - 1], (int)w.dims[w.N - 1], R, s.F[2], s.RP, st));
-    NTF_CUDA(ntf::kr_merge(kr_args(w, s, w.L, s.F[0], nullptr), st));
+    if ((rc = nway_init(ctx, w, s, const_cast<float *const *>(factors), false, false, st))) return rc;
     ntf::Cp3Args a = cp_args(&w.X3, s, o, beta);
     for (int m = 0; m < 3; ++m) a.rec[m] = a.num[m] = a.den[m] = s.F[m];
     {
@@ -829,6 +949,7 @@ void ntf_opts_default(ntf_opts *o) {
     o->inner_L = 1;
     o->precision = NTF_PREC_FP32;
     o->autotune = 0;
+    o->merge = 0;
 }
 
 int ntf_ctx_create(ntf_ctx **out, int device) {

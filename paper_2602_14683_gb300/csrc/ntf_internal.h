@@ -254,6 +254,7 @@ struct FoldArgs {
     int dims[8];
     int M, n, rows, R, RP;
     float *out;          // [dims[n]][RP]
+    float *scratch;      // [rows][RP], the summed parts when n_parts > 1
 };
 cudaError_t kr_fold(const FoldArgs &f, cudaStream_t s);
 

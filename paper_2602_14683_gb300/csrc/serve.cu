@@ -82,7 +82,8 @@ size_t estimate_bytes(const ntf_job &j, int sms) {
     const int64_t I = j.dims[0], J = j.dims[1], K = j.dims[2];
     size_t b = 0;
     if (j.model == NTF_CP) {
-        const int RP = rank_pad(j.rank);
+        // tensor-core passes pad the rank to 32
+        const int RP = (j.precision != NTF_PREC_FP32 && j.rank <= 32) ? 32 : rank_pad(j.rank);
         // the tensor-core plan (128-column blocks, four mode-1 partials per row tile) where
         // the job asks for it, else the FP32 plan; the larger of the two when either may run
         const ntf::Cp3Plan p32 = ntf::cp3_plan((int)I, (int)J, (int)K, RP, sms, 64);

@@ -53,6 +53,7 @@ def test_opts_default_without_gpu(lib):
     o = _lib.Opts()
     lib.ntf_opts_default(ctypes.byref(o))
     assert o.eps == 1e-12 and o.eps_x == 1e-12 and o.inner_L == 1 and o.precision == 0
+    assert o.autotune == 0 and o.merge == 0
 
 
 def test_ctx_create_rejects_bad_device(lib):

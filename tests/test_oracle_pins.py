@@ -669,3 +669,43 @@ def test_cp_order4_matches_brute_force_and_permutations(beta):
     for fn in (lambda: oracle.cp_mu_sweep(Xe, A, beta)[0], lambda: oracle.cp_jcomm_outer(Xe, A, beta, L=2)[0]):
         for a, b in zip(fn(), A):
             np.testing.assert_allclose(a, b, rtol=1e-11)
+
+
+@pytest.mark.parametrize("beta", BETAS)
+def test_tucker_order4_matches_brute_force_and_fixed_points(beta):
+    """Order 4 Tucker: the core and factor contractions of P and Q equal brute-force sums over
+    all entries (einsum of the definitions of Xhat, P, Q and the Tucker contractions), a
+    superdiagonal core gives the CP contractions, and exact data is a fixed point of the block
+    sweep and of J-CoMM."""
+    g = np.random.default_rng(41)
+    dims, J = (4, 3, 5, 2), (2, 3, 2, 2)
+    X = g.gamma(3.0, 1.0, size=dims) + 0.05
+    G = g.uniform(0.3, 1.0, size=J)
+    A = [g.uniform(0.2, 1.0, size=(d, j)) for d, j in zip(dims, J)]
+    Xh = np.einsum("abcd,ia,jb,kc,ld->ijkl", G, *A)
+    np.testing.assert_allclose(oracle.tucker_full(dims, G, A), Xh, rtol=1e-13)
+    y = np.maximum(Xh, 1e-12)
+    Xs = np.maximum(X, 1e-12) if beta == 0.0 else X
+    P, Q = Xs * y ** (beta - 2.0), y ** (beta - 1.0)
+    for T in (P, Q):
+        np.testing.assert_allclose(oracle.tucker_core_contr(T, A, J),
+                                   np.einsum("ijkl,ia,jb,kc,ld->abcd", T, *A), rtol=1e-12)
+        subs, csubs = "ijkl", "abcd"
+        for n in range(4):
+            spec = ("ijkl," + csubs + "," + ",".join(subs[m] + csubs[m] for m in range(4) if m != n)
+                    + "->" + subs[n] + csubs[n])
+            want = np.einsum(spec, T, G, *[A[m] for m in range(4) if m != n])
+            np.testing.assert_allclose(oracle.tucker_factor_contr(T, G, A, n), want, rtol=1e-12)
+    R = 2
+    Ac = [g.uniform(0.2, 1.0, size=(d, R)) for d in dims]
+    Gd = np.zeros((R,) * 4)
+    for r in range(R):
+        Gd[r, r, r, r] = 1.0
+    for n in range(4):
+        np.testing.assert_allclose(oracle.tucker_factor_contr(P, Gd, Ac, n), oracle.cp_contr(P, Ac, n), rtol=1e-12)
+    Xe = oracle.tucker_full(dims, G, A)
+    for fn in (lambda: oracle.tucker_mu_sweep(Xe, G, A, beta), lambda: oracle.tucker_jcomm_outer(Xe, G, A, beta, L=2)):
+        G1, A1, _ = fn()
+        np.testing.assert_allclose(G1, G, rtol=1e-10)
+        for a, b in zip(A1, A):
+            np.testing.assert_allclose(a, b, rtol=1e-10)

@@ -272,7 +272,7 @@ def tucker_mu_sweep_extrap(X, beta, core, factors, core_prev, factors_prev, alph
     d = _Desc(X)
     _check_dev(core, torch.float32, "core")
     _check_dev(core_prev, torch.float32, "core_prev")
-    cd = (C.c_int64 * 3)(*core.shape)
+    cd = (C.c_int64 * core.dim())(*core.shape)
     fp = _ptrs(factors, "factors")
     pp = _ptrs(factors_prev, "factors_prev")
     o = make_opts(**opts)
@@ -289,7 +289,7 @@ def tucker_jcomm_outer_extrap(X, beta, core, factors, core_prev, factors_prev, a
     d = _Desc(X)
     _check_dev(core, torch.float32, "core")
     _check_dev(core_prev, torch.float32, "core_prev")
-    cd = (C.c_int64 * 3)(*core.shape)
+    cd = (C.c_int64 * core.dim())(*core.shape)
     fp = _ptrs(factors, "factors")
     pp = _ptrs(factors_prev, "factors_prev")
     o = make_opts(**opts)

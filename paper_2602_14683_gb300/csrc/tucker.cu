@@ -414,6 +414,82 @@ __global__ void extrap_flat_apply_kernel(const float *A, const float *D, int64_t
         E[t] = fmaxf(fmaf(alpha, D[t], A[t]), eps);
 }
 
+// Order N >= 4 on the 3-way kernels (modes cut into three runs of consecutive modes): the
+// factor of a run of several modes is the Kronecker product of the run's factors, rows and
+// columns both row-major over the run (the memory order of X and of the core):
+//   V[(i_a, i_b, ...)][(j_a, j_b, ...)] = prod_m A_m[i_m][j_m], columns >= cols up to ld zero.
+struct KronArgs {
+    const float *L[8];  // the run's factors, I[m] x J[m] row-major
+    int I[8], J[8];
+    int M, rows, cols, ld;
+    float *out;
+};
+
+__global__ void kron_build_kernel(KronArgs k) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)k.rows * k.ld) return;
+    int row = (int)(t / k.ld), c = (int)(t % k.ld);
+    if (c >= k.cols) {
+        k.out[t] = 0.0f;
+        return;
+    }
+    float v = 1.0f;
+    for (int m = k.M - 1; m >= 0; --m) {
+        const int im = row % k.I[m], jm = c % k.J[m];
+        row /= k.I[m];
+        c /= k.J[m];
+        v *= k.L[m][(int64_t)im * k.J[m] + jm];
+    }
+    k.out[t] = v;
+}
+
+// out[i_n][j_n] = sum over the run's other (i, j) index pairs of
+//   S[(i ...)][(j ...)] * prod_{m != n} A_m[i_m][j_m]
+// -- the Tucker factor contraction of mode n from the run's contraction S; one thread per
+// output, FP64 accumulation in a fixed order.
+struct KronFoldArgs {
+    const float *S;  // [rows][ld]
+    int ld;
+    const float *L[8];
+    int I[8], J[8];
+    int M, n;
+    float *out;      // [I[n]][J[n]]
+};
+
+__global__ void kron_fold_kernel(KronFoldArgs f) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)f.I[f.n] * f.J[f.n]) return;
+    const int in = (int)(t / f.J[f.n]), jn = (int)(t % f.J[f.n]);
+    int64_t oi = 1, oj = 1;
+    for (int m = 0; m < f.M; ++m)
+        if (m != f.n) {
+            oi *= f.I[m];
+            oj *= f.J[m];
+        }
+    double acc = 0.0;
+    for (int64_t qi = 0; qi < oi; ++qi)
+        for (int64_t qj = 0; qj < oj; ++qj) {
+            int64_t ri = qi, rj = qj, row = 0, col = 0, mi = 1, mj = 1;
+            float w = 1.0f;
+            for (int m = f.M - 1; m >= 0; --m) {
+                int im = in, jm = jn;
+                if (m != f.n) {
+                    im = (int)(ri % f.I[m]);
+                    ri /= f.I[m];
+                    jm = (int)(rj % f.J[m]);
+                    rj /= f.J[m];
+                    w *= f.L[m][(int64_t)im * f.J[m] + jm];
+                }
+                row += im * mi;
+                col += jm * mj;
+                mi *= f.I[m];
+                mj *= f.J[m];
+            }
+            acc += (double)f.S[row * f.ld + col] * (double)w;
+        }
+    f.out[t] = (float)acc;
+}
+
 __global__ void mu_plain_kernel(const float *pre, const float *num, const float *den, int64_t n, float gamma,
                                 float eps, float *out) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -725,17 +801,30 @@ int mode3_pass(ntf_ctx *ctx, TuckerWs &w, const ntf_tensor *X, const ntf_opts &o
 
 }  // namespace
 
-int tucker_run(ntf_ctx *ctx, const ntf_tensor *X, float beta, const int64_t *core_dims, float *core,
-               float *const *factors, const ntf_opts &o, double *objective_dev, cudaStream_t st, bool jcomm,
-               const TuckerExtrap *xe) {
-    if (!core_dims || !core || !factors) return ctx_fail(ctx, NTF_ERR_ARG, "core_dims, core and factors are required");
-    if (X->order != 3) return ctx_fail(ctx, NTF_ERR_UNSUPPORTED, "Tucker kernels implement order 3");
-    for (int n = 0; n < 3; ++n) {
+// core extents 1..64 and at most the tensor's (order 3: each one is a 3-way block; order N >= 4:
+// the last run's product must also stay <= 64, checked when the cut is chosen)
+static int check_core(ntf_ctx *ctx, const ntf_tensor *X, const int64_t *core_dims, const float *const *factors) {
+    for (int n = 0; n < X->order; ++n) {
         if (!factors[n]) return ctx_fail(ctx, NTF_ERR_ARG, "factor is NULL");
         if (core_dims[n] < 1 || core_dims[n] > 64)
             return ctx_fail(ctx, NTF_ERR_UNSUPPORTED, "core dimensions must lie in 1..64");
         if (core_dims[n] > X->dims[n]) return ctx_fail(ctx, NTF_ERR_SHAPE, "core dimension exceeds tensor dimension");
     }
+    return NTF_OK;
+}
+
+int tucker_nway_run(ntf_ctx *ctx, const ntf_tensor *X, float beta, const int64_t *core_dims, float *core,
+                    float *const *factors, const ntf_opts &o, double *objective_dev, cudaStream_t st, bool jcomm);
+int tucker_nway_beta_div(ntf_ctx *ctx, const ntf_tensor *X, float beta, const int64_t *core_dims, const float *core,
+                         const float *const *factors, const ntf_opts &o, double *out_dev, cudaStream_t st);
+
+int tucker_run(ntf_ctx *ctx, const ntf_tensor *X, float beta, const int64_t *core_dims, float *core,
+               float *const *factors, const ntf_opts &o, double *objective_dev, cudaStream_t st, bool jcomm,
+               const TuckerExtrap *xe) {
+    if (!core_dims || !core || !factors) return ctx_fail(ctx, NTF_ERR_ARG, "core_dims, core and factors are required");
+    if (X->order < 3 || (X->order > 3 && xe)) return ctx_fail(ctx, NTF_ERR_UNSUPPORTED, "Tucker kernels implement order 3");
+    if (int rc0 = check_core(ctx, X, core_dims, factors)) return rc0;
+    if (X->order > 3) return tucker_nway_run(ctx, X, beta, core_dims, core, factors, o, objective_dev, st, jcomm);
     TuckerWs w{};
     int rc = setup(ctx, X, core_dims, jcomm, w, o, beta);
     if (rc) return rc;
@@ -849,13 +938,9 @@ int tucker_run(ntf_ctx *ctx, const ntf_tensor *X, float beta, const int64_t *cor
 int tucker_beta_div(ntf_ctx *ctx, const ntf_tensor *X, float beta, const int64_t *core_dims, const float *core,
                     const float *const *factors, const ntf_opts &o, double *out_dev, cudaStream_t st) {
     if (!core_dims || !core || !factors) return ctx_fail(ctx, NTF_ERR_ARG, "core_dims, core and factors are required");
-    if (X->order != 3) return ctx_fail(ctx, NTF_ERR_UNSUPPORTED, "Tucker kernels implement order 3");
-    for (int n = 0; n < 3; ++n) {
-        if (!factors[n]) return ctx_fail(ctx, NTF_ERR_ARG, "factor is NULL");
-        if (core_dims[n] < 1 || core_dims[n] > 64)
-            return ctx_fail(ctx, NTF_ERR_UNSUPPORTED, "core dimensions must lie in 1..64");
-        if (core_dims[n] > X->dims[n]) return ctx_fail(ctx, NTF_ERR_SHAPE, "core dimension exceeds tensor dimension");
-    }
+    if (X->order < 3) return ctx_fail(ctx, NTF_ERR_UNSUPPORTED, "Tucker kernels implement orders 3..8");
+    if (int rc0 = check_core(ctx, X, core_dims, factors)) return rc0;
+    if (X->order > 3) return tucker_nway_beta_div(ctx, X, beta, core_dims, core, factors, o, out_dev, st);
     TuckerWs w{};
     int rc = setup(ctx, X, core_dims, false, w, o, beta);
     if (rc) return rc;
@@ -956,6 +1041,379 @@ int tucker_run_extrap(ntf_ctx *ctx, const ntf_tensor *X, float beta, const int64
     TK(cudaMemcpyAsync(factors[1], w.cur.A2, sizeof(float) * n2, cudaMemcpyDeviceToDevice, st));
     unpad_cols_kernel<<<nblk(n3), 256, 0, st>>>(w.cur.A3p, w.I3, w.J3, w.RP, factors[2]);
     TK(cudaGetLastError());
+    return NTF_OK;
+}
+
+// ------------------------------------------------------------------ order N >= 4
+// The N modes are cut into three runs of consecutive modes [0, a), [a, b), [b, N); X and the
+// core (both row-major) are then 3-way with the runs' products as extents, and a run of several
+// modes has the Kronecker product of its factors as its 3-way factor.  The core block and
+// every mode alone in its run are the 3-way blocks (same passes, GEMMs and updates); a mode
+// inside a longer run takes the run's 3-way contraction (Num, Den over the merged row and column
+// indices) and folds it against the run's other factors -- the Tucker factor contraction of
+// Section 6.2 over the merged indices -- then the run's Kronecker factor is rebuilt.
+namespace {
+
+struct TNWay {
+    int N;
+    int gb[3], ge[3], view[8];
+    int64_t dims3[3], cdims3[3];
+    int I[8], J[8];
+    ntf_tensor X3;
+    float *A[8], *At[8], *C1[8], *C2[8];  // own blocks of the modes in runs of several modes
+    float *numn, *denn, *S, *Sd;
+};
+
+bool tn_single(const TNWay &t, int v) { return t.ge[v] - t.gb[v] == 1; }
+
+float *slot(Blocks &b, int v) { return v == 0 ? b.A1 : v == 1 ? b.A2 : b.A3p; }
+
+int tn_split(ntf_ctx *ctx, const ntf_tensor *X, const int64_t *cd, const ntf_opts &o, float beta, int &a, int &b) {
+    const int N = X->order;
+    auto fits = [&](int ca, int cb, double *cost) {
+        double e[3] = {1, 1, 1}, c[3] = {1, 1, 1};
+        for (int m = 0; m < N; ++m) {
+            const int v = m < ca ? 0 : m < cb ? 1 : 2;
+            e[v] *= (double)X->dims[m];
+            c[v] *= (double)cd[m];
+        }
+        if (c[2] > 64 || e[0] * e[1] >= 2147483648.0 || e[2] >= 2147483648.0 || c[0] * c[1] * c[2] >= 2147483648.0)
+            return false;
+        const int rp = rank_pad((int)c[2]);
+        const bool tc = o.precision != NTF_PREC_FP32 && beta_kind(beta) != BK_KL && rp == 32 &&
+                        cp3_tc_eligible(32, (int)e[2], X->values);
+        const double tj = rp == 64 ? 64.0 : 128.0;
+        const double pass = e[0] * std::ceil(e[1] / tj) * tj * std::ceil(e[2] / 64.0) * 64.0 * rp * 6.0;
+        const double gemms = 2.0 * e[0] * e[1] * c[2] * (c[0] + 3.0 * c[1]);
+        *cost = pass / (tc ? 8.0 : 1.0) + gemms;
+        return true;
+    };
+    double cost = 0.0, best = -1.0;
+    if (o.merge) {
+        a = o.merge / 16;
+        b = o.merge % 16;
+        if (!(1 <= a && a < b && b <= N - 1))
+            return ctx_fail(ctx, NTF_ERR_ARG, "merge does not split the modes into three runs");
+        if (!fits(a, b, &cost))
+            return ctx_fail(ctx, NTF_ERR_UNSUPPORTED, "the requested cut needs a last-run core extent <= 64");
+        return NTF_OK;
+    }
+    for (int ca = 1; ca <= N - 2; ++ca)
+        for (int cb = ca + 1; cb <= N - 1; ++cb)
+            if (fits(ca, cb, &cost) && (best < 0.0 || cost < best)) {
+                best = cost;
+                a = ca;
+                b = cb;
+            }
+    if (best < 0.0)
+        return ctx_fail(ctx, NTF_ERR_UNSUPPORTED, "no cut of the modes has a last-run core extent <= 64");
+    return NTF_OK;
+}
+
+KronArgs tn_kron(const TNWay &t, int v, float *const *B, float *out, int ld) {
+    KronArgs k{};
+    k.M = t.ge[v] - t.gb[v];
+    for (int j = 0; j < k.M; ++j) {
+        k.L[j] = B[t.gb[v] + j];
+        k.I[j] = t.I[t.gb[v] + j];
+        k.J[j] = t.J[t.gb[v] + j];
+    }
+    k.rows = (int)t.dims3[v];
+    k.cols = (int)t.cdims3[v];
+    k.ld = ld;
+    k.out = out;
+    return k;
+}
+
+int tn_build(ntf_ctx *ctx, const TNWay &t, int v, float *const *B, float *out, int ld, cudaStream_t st) {
+    const KronArgs k = tn_kron(t, v, B, out, ld);
+    kron_build_kernel<<<nblk((int64_t)k.rows * ld), 256, 0, st>>>(k);
+    TK(cudaGetLastError());
+    return NTF_OK;
+}
+
+int tn_fold(ntf_ctx *ctx, const TNWay &t, int n, const float *S, int ld, float *const *B, float *out,
+            cudaStream_t st) {
+    const int v = t.view[n];
+    const KronArgs k = tn_kron(t, v, B, nullptr, ld);
+    KronFoldArgs f{};
+    f.S = S;
+    f.ld = ld;
+    for (int j = 0; j < k.M; ++j) {
+        f.L[j] = k.L[j];
+        f.I[j] = k.I[j];
+        f.J[j] = k.J[j];
+    }
+    f.M = k.M;
+    f.n = n - t.gb[v];
+    f.out = out;
+    kron_fold_kernel<<<nblk((int64_t)t.I[n] * t.J[n]), 256, 0, st>>>(f);
+    TK(cudaGetLastError());
+    return NTF_OK;
+}
+
+int tn_setup(ntf_ctx *ctx, const ntf_tensor *X, float beta, const int64_t *cd, bool jcomm, const ntf_opts &o,
+             TNWay &t, TuckerWs &w) {
+    t.N = X->order;
+    int a = 0, b = 0;
+    int rc = tn_split(ctx, X, cd, o, beta, a, b);
+    if (rc) return rc;
+    t.gb[0] = 0, t.ge[0] = a, t.gb[1] = a, t.ge[1] = b, t.gb[2] = b, t.ge[2] = t.N;
+    for (int v = 0; v < 3; ++v) {
+        t.dims3[v] = t.cdims3[v] = 1;
+        for (int m = t.gb[v]; m < t.ge[v]; ++m) {
+            t.view[m] = v;
+            t.I[m] = (int)X->dims[m];
+            t.J[m] = (int)cd[m];
+            t.dims3[v] *= X->dims[m];
+            t.cdims3[v] *= cd[m];
+        }
+    }
+    t.X3 = *X;
+    t.X3.order = 3;
+    t.X3.dims = t.dims3;
+    if ((rc = setup(ctx, &t.X3, t.cdims3, jcomm, w, o, beta))) return rc;
+    bool ok = true;
+    int64_t mx = 1;
+    static const char *nm[4] = {"tnA", "tnAt", "tnC1", "tnC2"};
+    for (int m = 0; m < t.N; ++m) {
+        t.A[m] = t.At[m] = t.C1[m] = t.C2[m] = nullptr;
+        if (tn_single(t, t.view[m])) continue;
+        const int64_t n = (int64_t)t.I[m] * t.J[m];
+        mx = std::max(mx, n);
+        float **dst[4] = {&t.A[m], &t.At[m], &t.C1[m], &t.C2[m]};
+        for (int q = 0; q < (jcomm ? 4 : 1); ++q) {
+            const std::string name = std::string(nm[q]) + std::to_string(m);
+            *dst[q] = wsf(ctx, name.c_str(), n, ok);
+        }
+    }
+    t.numn = wsf(ctx, "tnNum", mx, ok);
+    t.denn = wsf(ctx, "tnDen", mx, ok);
+    t.S = wsf(ctx, "tnS", t.dims3[2] * w.RP, ok);
+    t.Sd = wsf(ctx, "tnSd", t.dims3[2] * w.RP, ok);
+    if (!ok) return ctx_fail(ctx, NTF_ERR_OOM, "workspace allocation failed");
+    return NTF_OK;
+}
+
+// the user's core and factors into the view blocks (and the runs' own blocks)
+int tn_load(ntf_ctx *ctx, TNWay &t, TuckerWs &w, const float *core, const float *const *factors, cudaStream_t st) {
+    TK(cudaMemcpyAsync(w.cur.G, core, sizeof(float) * t.cdims3[0] * t.cdims3[1] * t.cdims3[2],
+                       cudaMemcpyDeviceToDevice, st));
+    for (int v = 0; v < 3; ++v) {
+        const int ld = v == 2 ? w.RP : (int)t.cdims3[v];
+        if (tn_single(t, v)) {
+            const int m = t.gb[v];
+            if (v < 2) {
+                TK(cudaMemcpyAsync(slot(w.cur, v), factors[m], sizeof(float) * t.I[m] * t.J[m],
+                                   cudaMemcpyDeviceToDevice, st));
+            } else {
+                pad_cols_kernel<<<nblk((int64_t)t.I[m] * w.RP), 256, 0, st>>>(factors[m], t.I[m], t.J[m], w.RP,
+                                                                            w.cur.A3p);
+                TK(cudaGetLastError());
+            }
+            continue;
+        }
+        for (int m = t.gb[v]; m < t.ge[v]; ++m)
+            TK(cudaMemcpyAsync(t.A[m], factors[m], sizeof(float) * t.I[m] * t.J[m], cudaMemcpyDeviceToDevice, st));
+        int rc = tn_build(ctx, t, v, t.A, slot(w.cur, v), ld, st);
+        if (rc) return rc;
+    }
+    return NTF_OK;
+}
+
+int tn_store(ntf_ctx *ctx, TNWay &t, TuckerWs &w, float *core, float *const *factors, cudaStream_t st) {
+    TK(cudaMemcpyAsync(core, w.cur.G, sizeof(float) * t.cdims3[0] * t.cdims3[1] * t.cdims3[2],
+                       cudaMemcpyDeviceToDevice, st));
+    for (int m = 0; m < t.N; ++m) {
+        const int v = t.view[m];
+        const int64_t n = (int64_t)t.I[m] * t.J[m];
+        if (!tn_single(t, v)) {
+            TK(cudaMemcpyAsync(factors[m], t.A[m], sizeof(float) * n, cudaMemcpyDeviceToDevice, st));
+        } else if (v < 2) {
+            TK(cudaMemcpyAsync(factors[m], slot(w.cur, v), sizeof(float) * n, cudaMemcpyDeviceToDevice, st));
+        } else {
+            unpad_cols_kernel<<<nblk(n), 256, 0, st>>>(w.cur.A3p, t.I[m], t.J[m], w.RP, factors[m]);
+            TK(cudaGetLastError());
+        }
+    }
+    return NTF_OK;
+}
+
+// mode n inside a run of several modes: Num / Den folded from the run's contraction (S, Sd with
+// row stride ld) against fold blocks Bn / Bd, MU from pre into out, chi copies when c1 is given
+int tn_run_update(ntf_ctx *ctx, TNWay &t, int n, const float *S, const float *Sd, int ld, float *const *Bn,
+                  float *const *Bd, const float *pre, float *out, float *c1, float *c2, float beta, float eps,
+                  cudaStream_t st) {
+    int rc = tn_fold(ctx, t, n, S, ld, Bn, t.numn, st);
+    if (rc) return rc;
+    if ((rc = tn_fold(ctx, t, n, Sd, ld, Bd, t.denn, st))) return rc;
+    const int64_t cnt = (int64_t)t.I[n] * t.J[n];
+    mu_plain_kernel<<<nblk(cnt), 256, 0, st>>>(pre, t.numn, t.denn, cnt, mu_gamma(beta), eps, out);
+    TK(cudaGetLastError());
+    if (c1) {
+        chi_kernel<<<nblk(cnt), 256, 0, st>>>(out, pre, cnt, beta, c1, c2);
+        TK(cudaGetLastError());
+    }
+    return NTF_OK;
+}
+
+}  // namespace
+
+int tucker_nway_run(ntf_ctx *ctx, const ntf_tensor *X, float beta, const int64_t *core_dims, float *core,
+                    float *const *factors, const ntf_opts &o, double *objective_dev, cudaStream_t st, bool jcomm) {
+    TNWay t{};
+    TuckerWs w{};
+    int rc = tn_setup(ctx, X, beta, core_dims, jcomm, o, t, w);
+    if (rc) return rc;
+    if ((rc = tn_load(ctx, t, w, core, factors, st))) return rc;
+    const float eps = (float)o.eps;
+    const int64_t Jc = t.cdims3[0] * t.cdims3[1] * t.cdims3[2];
+    const int64_t n3p = t.dims3[2] * w.RP;
+    if (!jcomm) {
+        // core block (the pass also yields D_beta of the incoming iterate)
+        if ((rc = build_b3(ctx, w, w.cur, w.Brec, st))) return rc;
+        if ((rc = rows_pass(ctx, w, &t.X3, o, beta, w.Brec, w.cur.A3p, w.cur.A3p, w.cur.A3p, objective_dev != nullptr,
+                            st)))
+            return rc;
+        if (objective_dev) TK(reduce_objective(w.obj, w.obj_n, 0.0, objective_dev, st));
+        if ((rc = contract_from_w(ctx, w, 0, w.cur, w.Wn, w.num, st))) return rc;
+        if ((rc = contract_from_w(ctx, w, 0, w.cur, w.Wd, w.den, st))) return rc;
+        if ((rc = apply_mu(ctx, w, w.cur.G, w.cur.G, Jc, beta, eps, nullptr, nullptr, nullptr, st))) return rc;
+        for (int n = 0; n < t.N; ++n) {
+            const int v = t.view[n];
+            const bool single = tn_single(t, v);
+            if ((rc = build_b3(ctx, w, w.cur, w.Brec, st))) return rc;
+            if (v < 2) {
+                if ((rc = rows_pass(ctx, w, &t.X3, o, beta, w.Brec, w.cur.A3p, w.cur.A3p, w.cur.A3p, false, st)))
+                    return rc;
+                if ((rc = contract_from_w(ctx, w, v + 1, w.cur, w.Wn, w.num, st))) return rc;
+                if ((rc = contract_from_w(ctx, w, v + 1, w.cur, w.Wd, w.den, st))) return rc;
+                if (single) {
+                    float *A = slot(w.cur, v);
+                    if ((rc = apply_mu(ctx, w, A, A, (int64_t)t.I[n] * t.J[n], beta, eps, nullptr, nullptr, nullptr,
+                                       st)))
+                        return rc;
+                    continue;
+                }
+                const int ld = (int)t.cdims3[v];
+                if ((rc = tn_run_update(ctx, t, n, w.num, w.den, ld, t.A, t.A, t.A[n], t.A[n], nullptr, nullptr,
+                                        beta, eps, st)))
+                    return rc;
+                if ((rc = tn_build(ctx, t, v, t.A, slot(w.cur, v), ld, st))) return rc;
+                continue;
+            }
+            if ((rc = mode3_pass(ctx, w, &t.X3, o, beta, w.Brec, w.cur.A3p, w.Brec, w.Brec, false, st))) return rc;
+            if (single) {
+                MuEpiArgs e{};
+                e.pn = w.pn3; e.pd = w.pd3; e.n_parts = w.parts3; e.rows = w.I3; e.RP = w.RP; e.R = w.J3;
+                e.pre = w.cur.A3p; e.out = w.cur.A3p; e.beta = beta; e.gamma = mu_gamma(beta); e.eps = eps;
+                TK(mu_epilogue(e, st));
+                continue;
+            }
+            sum_parts_kernel<<<nblk(n3p), 256, 0, st>>>(w.pn3, w.parts3, n3p, t.S);
+            TK(cudaGetLastError());
+            sum_parts_kernel<<<nblk(n3p), 256, 0, st>>>(w.pd3, w.parts3, n3p, t.Sd);
+            TK(cudaGetLastError());
+            if ((rc = tn_run_update(ctx, t, n, t.S, t.Sd, w.RP, t.A, t.A, t.A[n], t.A[n], nullptr, nullptr, beta, eps,
+                                    st)))
+                return rc;
+            if ((rc = tn_build(ctx, t, 2, t.A, w.cur.A3p, w.RP, st))) return rc;
+        }
+        return tn_store(ctx, t, w, core, factors, st);
+    }
+    // J-CoMM (Algorithm 2): reference, chi1 and chi2 copies of every block
+    if ((rc = copy_blocks(ctx, w, w.cur, w.ref, st))) return rc;
+    if ((rc = copy_blocks(ctx, w, w.cur, w.t1, st))) return rc;
+    if ((rc = copy_blocks(ctx, w, w.cur, w.t2, st))) return rc;
+    for (int m = 0; m < t.N; ++m) {
+        if (tn_single(t, t.view[m])) continue;
+        const size_t bytes = sizeof(float) * t.I[m] * t.J[m];
+        TK(cudaMemcpyAsync(t.At[m], t.A[m], bytes, cudaMemcpyDeviceToDevice, st));
+        TK(cudaMemcpyAsync(t.C1[m], t.A[m], bytes, cudaMemcpyDeviceToDevice, st));
+        TK(cudaMemcpyAsync(t.C2[m], t.A[m], bytes, cudaMemcpyDeviceToDevice, st));
+    }
+    if ((rc = build_b3(ctx, w, w.ref, w.Brec, st))) return rc;
+    for (int l = 0; l < o.inner_L; ++l) {
+        const bool obj = (l == 0) && objective_dev;
+        if ((rc = rows_pass(ctx, w, &t.X3, o, beta, w.Brec, w.ref.A3p, w.t1.A3p, w.t2.A3p, obj, st))) return rc;
+        if (obj) TK(reduce_objective(w.obj, w.obj_n, 0.0, objective_dev, st));
+        if ((rc = contract_from_w(ctx, w, 0, w.t1, w.Wn, w.num, st))) return rc;
+        if ((rc = contract_from_w(ctx, w, 0, w.t2, w.Wd, w.den, st))) return rc;
+        if ((rc = apply_mu(ctx, w, w.ref.G, w.cur.G, Jc, beta, eps, w.ref.G, w.t1.G, w.t2.G, st))) return rc;
+        bool m3_done = false;
+        for (int n = 0; n < t.N; ++n) {
+            const int v = t.view[n];
+            const bool single = tn_single(t, v);
+            if (v < 2) {
+                if ((rc = contract_from_w(ctx, w, v + 1, w.t1, w.Wn, w.num, st))) return rc;
+                if ((rc = contract_from_w(ctx, w, v + 1, w.t2, w.Wd, w.den, st))) return rc;
+                if (single) {
+                    float *At = slot(w.ref, v);
+                    if ((rc = apply_mu(ctx, w, At, slot(w.cur, v), (int64_t)t.I[n] * t.J[n], beta, eps, At,
+                                       slot(w.t1, v), slot(w.t2, v), st)))
+                        return rc;
+                    continue;
+                }
+                const int ld = (int)t.cdims3[v];
+                if ((rc = tn_run_update(ctx, t, n, w.num, w.den, ld, t.C1, t.C2, t.At[n], t.A[n], t.C1[n], t.C2[n],
+                                        beta, eps, st)))
+                    return rc;
+                if ((rc = tn_build(ctx, t, v, t.C1, slot(w.t1, v), ld, st))) return rc;
+                if ((rc = tn_build(ctx, t, v, t.C2, slot(w.t2, v), ld, st))) return rc;
+                continue;
+            }
+            if (!m3_done) {
+                // the mode-3 contraction depends on the core and the first two runs only, which
+                // are final for this sweep: one pass serves every mode of the last run
+                if ((rc = build_b3(ctx, w, w.t1, w.Bn, st))) return rc;
+                if ((rc = build_b3(ctx, w, w.t2, w.Bd, st))) return rc;
+                if ((rc = mode3_pass(ctx, w, &t.X3, o, beta, w.Brec, w.ref.A3p, w.Bn, w.Bd, false, st))) return rc;
+                m3_done = true;
+                if (!single) {
+                    sum_parts_kernel<<<nblk(n3p), 256, 0, st>>>(w.pn3, w.parts3, n3p, t.S);
+                    TK(cudaGetLastError());
+                    sum_parts_kernel<<<nblk(n3p), 256, 0, st>>>(w.pd3, w.parts3, n3p, t.Sd);
+                    TK(cudaGetLastError());
+                }
+            }
+            if (single) {
+                MuEpiArgs e{};
+                e.pn = w.pn3; e.pd = w.pd3; e.n_parts = w.parts3; e.rows = w.I3; e.RP = w.RP; e.R = w.J3;
+                e.pre = w.ref.A3p; e.out = w.cur.A3p; e.ref = w.ref.A3p; e.chi1_out = w.t1.A3p; e.chi2_out = w.t2.A3p;
+                e.beta = beta; e.gamma = mu_gamma(beta); e.eps = eps;
+                TK(mu_epilogue(e, st));
+                continue;
+            }
+            if ((rc = tn_run_update(ctx, t, n, t.S, t.Sd, w.RP, t.C1, t.C2, t.At[n], t.A[n], t.C1[n], t.C2[n], beta,
+                                    eps, st)))
+                return rc;
+            if (n == t.ge[2] - 1) {
+                if ((rc = tn_build(ctx, t, 2, t.C1, w.t1.A3p, w.RP, st))) return rc;
+                if ((rc = tn_build(ctx, t, 2, t.C2, w.t2.A3p, w.RP, st))) return rc;
+            }
+        }
+    }
+    return tn_store(ctx, t, w, core, factors, st);
+}
+
+int tucker_nway_beta_div(ntf_ctx *ctx, const ntf_tensor *X, float beta, const int64_t *core_dims, const float *core,
+                         const float *const *factors, const ntf_opts &o, double *out_dev, cudaStream_t st) {
+    TNWay t{};
+    TuckerWs w{};
+    ntf_opts o32 = o;
+    o32.precision = NTF_PREC_FP32;
+    int rc = tn_setup(ctx, X, beta, core_dims, false, o32, t, w);
+    if (rc) return rc;
+    if ((rc = tn_load(ctx, t, w, core, factors, st))) return rc;
+    if ((rc = build_b3(ctx, w, w.cur, w.Brec, st))) return rc;
+    Cp3Args a = base_args(&t.X3, w, o, beta);
+    a.rrow = w.Brec;
+    for (int m = 0; m < 3; ++m) a.rec[m] = a.num[m] = a.den[m] = w.cur.A3p;
+    a.n_jt = w.plan3.n_jt;
+    a.n_kb = w.plan3.n_kb;
+    a.n_is = w.plan3.n_is;
+    TK(cp3_launch(w.plan3, a, PM_OBJ, 0, st));
+    TK(reduce_objective(w.obj, w.plan3.grid, 0.0, out_dev, st));
     return NTF_OK;
 }
 

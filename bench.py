@@ -43,7 +43,7 @@ def parse():
     p.add_argument("--no-ttt", action="store_true", help="skip the time-to-target runs")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     p.add_argument("--no-other", action="store_true",
-                   help="skip the Tucker 400^3, sparse 3.3M-nonzero and 4-way CP measurements")
+                   help="skip the Tucker 400^3, sparse 3.3M-nonzero and 4-way CP / Tucker measurements")
     p.add_argument("--serve-jobs", type=int, default=48,
                    help="jobs of the serving-mix measurement in the default run (0: skip)")
     p.add_argument("--serve", action="store_true", help="print only the serving-mix line")
@@ -51,9 +51,10 @@ def parse():
     p.add_argument("--profile-n", type=int, default=0,
                    help="profiling driver: three J-CoMM steps and three block-MU sweeps on an n^3, "
                         "R = 32, beta = 1 tensor at --precision, then exit (no measurement)")
-    p.add_argument("--profile-case", default="", choices=["", "tucker", "coo"],
+    p.add_argument("--profile-case", default="", choices=["", "tucker", "coo", "cp4", "tucker4"],
                    help="profiling driver: three block-MM sweeps and three J-CoMM iterations of the Tucker "
-                        "400^3 workload, or three J-CoMM iterations of the sparse 3.3M-nonzero workload")
+                        "400^3 workload, three J-CoMM iterations of the sparse 3.3M-nonzero workload, or "
+                        "the 4-way CP / Tucker measurements with one timed call per configuration")
     return p.parse_args()
 
 
@@ -298,6 +299,50 @@ def run_cp_4way(ntf, ctx, peaks, iters=20, dims=(80, 70, 60, 50), R=10, seed=5):
     return out
 
 
+def run_tucker_4way(ntf, ctx, peaks, iters=10, dims=(80, 70, 60, 50), J=(10, 9, 8, 7), seed=7):
+    """Dense 4-way Tucker 80 x 70 x 60 x 50, core 10 x 9 x 8 x 7 (the shape of the paper's
+    synthetic Tucker experiment): Gamma(2,1) core and factors, model rescaled to mean 10,
+    Poisson noise, init U(0.1, 1).  Times block-MM sweeps (core, then the four factors) and
+    J-CoMM outer iterations (L = 1) at beta in {1/2, 1, 3/2} on the cut the library picks,
+    with a 256 MB write before every timed call (the 67 MB tensor fits in L2)."""
+    import torch
+    import synth
+    dev = torch.device("cuda", torch.cuda.current_device())
+    Xn, _, _ = synth.tucker_dense(dims, J, seed=seed)
+    X = torch.tensor(Xn, dtype=torch.float32, device=dev)
+    G0n, A0n = synth.init_tucker(dims, J, seed=seed + 1)
+    G0 = torch.tensor(G0n, dtype=torch.float32, device=dev)
+    A0 = [torch.tensor(a, dtype=torch.float32, device=dev) for a in A0n]
+    obj = torch.zeros(1, dtype=torch.float64, device=dev)
+    flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)
+    out = {"workload": "dense 4-way Tucker %s, core %s" % ("x".join(map(str, dims)), "x".join(map(str, J))),
+           "l2": "256 MB write between timed iterations", "precision": "fp32"}
+    for beta in (0.5, 1.0, 1.5):
+        for name in ("block_mm", "jcomm"):
+            G, A = G0.clone(), [a.clone() for a in A0]
+
+            def step():
+                if name == "jcomm":
+                    ntf.jcomm_outer(X, beta, A, core=G, objective=obj, ctx=ctx)
+                else:
+                    ntf.tucker_mu_sweep(X, beta, G, A, objective=obj, ctx=ctx)
+            for _ in range(3):
+                step()
+            torch.cuda.synchronize()
+            tot = 0.0
+            for _ in range(iters):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                step()
+                e1.record()
+                torch.cuda.synchronize()
+                tot += e0.elapsed_time(e1)
+            out["%s_b%g_ms" % (name, beta)] = tot / iters
+            out["%s_b%g_objective" % (name, beta)] = obj.item()
+    return out
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -433,6 +478,10 @@ def main():
         ctx, peaks = ntf.default_context(), load_peaks()[0]
         if args.profile_case == "tucker":
             r = run_tucker_c3(ntf, ctx, peaks, iters=0, precisions=(args.precision,))
+        elif args.profile_case == "cp4":
+            r = run_cp_4way(ntf, ctx, peaks, iters=1)
+        elif args.profile_case == "tucker4":
+            r = run_tucker_4way(ntf, ctx, peaks, iters=1)
         else:
             r = run_coo_c4(ntf, ctx, peaks, iters=0)
         print("profile case", args.profile_case, "done")
@@ -662,7 +711,7 @@ def main():
     other = None
     if not args.no_other:
         other = {"tucker_c3": run_tucker_c3(ntf, ctx, peaks), "coo_c4": run_coo_c4(ntf, ctx, peaks),
-                 "cp_4way": run_cp_4way(ntf, ctx, peaks)}
+                 "cp_4way": run_cp_4way(ntf, ctx, peaks), "tucker_4way": run_tucker_4way(ntf, ctx, peaks)}
 
     serving = None
     if args.serve_jobs > 0:

@@ -45,16 +45,20 @@ struct Gemm {
     float *part;          // [splits][batch][M][N] when splits > 1
 };
 
-constexpr int GT = 64;   // output tile edge
 constexpr int GK = 16;   // reduction chunk
 constexpr int GCARRY = 16;  // chunks summed in FP32 before the FP64 carry
 
+// Output tiles of TM x TN (64 x 64, or 256 x 16 for outputs at most 16 columns wide); each of
+// the 256 threads holds a 4 x 4 block of outputs strided by TM / 4 rows and TN / 4 columns.
+template <int TM, int TN>
 __global__ void __launch_bounds__(256) gemm2k_kernel(const Gemm g) {
-    __shared__ float As[GK][GT + 4];
-    __shared__ float Bs[GK][GT + 4];
+    static_assert(TM * TN == 4096, "256 threads x 16 outputs");
+    constexpr int CT = TN / 4;  // thread columns
+    __shared__ float As[GK][TM + 4];
+    __shared__ float Bs[GK][TN + 4];
     const int bt = blockIdx.z % g.batch, sp = blockIdx.z / g.batch;
-    const int m0 = blockIdx.y * GT, n0 = blockIdx.x * GT;
-    const int tid = threadIdx.x, tm = tid / 16, tn = tid % 16;
+    const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
+    const int tid = threadIdx.x, tm = tid / CT, tn = tid % CT;
     const int K = g.K1 * g.K2;
     const int kbeg = sp * g.kchunks * GK, kend = min(K, kbeg + g.kchunks * GK);
     const bool carry = (kend - kbeg + GK - 1) / GK > GCARRY;  // more than one FP32 block
@@ -68,26 +72,32 @@ __global__ void __launch_bounds__(256) gemm2k_kernel(const Gemm g) {
     const float *B = g.B + bt * g.sbb;
     int chunk = 0;
     for (int k0 = kbeg; k0 < kend; k0 += GK) {
-        for (int t = tid; t < GK * GT; t += 256) {
-            const int kk = t / GT, mm = t % GT;
-            const int k = k0 + kk;
-            float va = 0.0f, vb = 0.0f;
-            if (k < kend) {
+        for (int t = tid; t < GK * TM; t += 256) {
+            const int kk = t / TM, mm = t % TM, k = k0 + kk;
+            float va = 0.0f;
+            if (k < kend && m0 + mm < g.M) {
                 const int k1 = g.K2 == 1 ? k : k / g.K2, k2 = k - k1 * g.K2;
-                if (m0 + mm < g.M) va = A[(m0 + mm) * g.sam + k1 * g.sak1 + k2 * g.sak2];
-                if (n0 + mm < g.N) vb = B[k1 * g.sbk1 + k2 * g.sbk2 + (n0 + mm) * g.sbn];
+                va = A[(m0 + mm) * g.sam + k1 * g.sak1 + k2 * g.sak2];
             }
             As[kk][mm] = va;
-            Bs[kk][mm] = vb;
+        }
+        for (int t = tid; t < GK * TN; t += 256) {
+            const int kk = t / TN, nn = t % TN, k = k0 + kk;
+            float vb = 0.0f;
+            if (k < kend && n0 + nn < g.N) {
+                const int k1 = g.K2 == 1 ? k : k / g.K2, k2 = k - k1 * g.K2;
+                vb = B[k1 * g.sbk1 + k2 * g.sbk2 + (n0 + nn) * g.sbn];
+            }
+            Bs[kk][nn] = vb;
         }
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < GK; ++kk) {
             float a[4], b[4];
 #pragma unroll
-            for (int x = 0; x < 4; ++x) a[x] = As[kk][tm + 16 * x];
+            for (int x = 0; x < 4; ++x) a[x] = As[kk][tm + (TM / 4) * x];
 #pragma unroll
-            for (int y = 0; y < 4; ++y) b[y] = Bs[kk][tn + 16 * y];
+            for (int y = 0; y < 4; ++y) b[y] = Bs[kk][tn + CT * y];
 #pragma unroll
             for (int x = 0; x < 4; ++x)
 #pragma unroll
@@ -106,7 +116,7 @@ __global__ void __launch_bounds__(256) gemm2k_kernel(const Gemm g) {
     for (int x = 0; x < 4; ++x)
 #pragma unroll
         for (int y = 0; y < 4; ++y) {
-            const int m = m0 + tm + 16 * x, n = n0 + tn + 16 * y;
+            const int m = m0 + tm + (TM / 4) * x, n = n0 + tn + CT * y;
             if (m < g.M && n < g.N) {
                 const float v = carry ? (float)(tot[x][y] + (double)acc[x][y]) : acc[x][y];
                 if (g.splits > 1) g.part[(((int64_t)sp * g.batch + bt) * g.M + m) * g.N + n] = v;
@@ -129,7 +139,9 @@ __global__ void gemm_split_sum_kernel(const Gemm g) {
 // Splits the reduction when the output tiles alone would leave most SMs idle: about two
 // CTAs per SM, at least four GK-chunks per range.
 static int gemm(ntf_ctx *ctx, Gemm g, cudaStream_t s) {
-    const int tiles = ((g.N + GT - 1) / GT) * ((g.M + GT - 1) / GT) * g.batch;
+    const bool narrow = g.N <= 16;
+    const int TM = narrow ? 256 : 64, TN = narrow ? 16 : 64;
+    const int tiles = ((g.N + TN - 1) / TN) * ((g.M + TM - 1) / TM) * g.batch;
     const int nchunks = (g.K1 * g.K2 + GK - 1) / GK;
     int splits = (2 * ctx_num_sms(ctx) + tiles - 1) / tiles;
     splits = std::max(1, std::min(splits, nchunks / 4));
@@ -139,8 +151,11 @@ static int gemm(ntf_ctx *ctx, Gemm g, cudaStream_t s) {
         g.part = (float *)ctx_ws(ctx, "gemm_split", sizeof(float) * (size_t)g.splits * g.batch * g.M * g.N);
         if (!g.part) return ctx_fail(ctx, NTF_ERR_OOM, "workspace allocation failed");
     }
-    dim3 grid((g.N + GT - 1) / GT, (g.M + GT - 1) / GT, g.batch * g.splits);
-    gemm2k_kernel<<<grid, 256, 0, s>>>(g);
+    dim3 grid((g.N + TN - 1) / TN, (g.M + TM - 1) / TM, g.batch * g.splits);
+    if (narrow)
+        gemm2k_kernel<256, 16><<<grid, 256, 0, s>>>(g);
+    else
+        gemm2k_kernel<64, 64><<<grid, 256, 0, s>>>(g);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess && g.splits > 1) {
         const int64_t total = (int64_t)g.M * g.N * g.batch;
@@ -445,8 +460,8 @@ __global__ void kron_build_kernel(KronArgs k) {
 
 // out[i_n][j_n] = sum over the run's other (i, j) index pairs of
 //   S[(i ...)][(j ...)] * prod_{m != n} A_m[i_m][j_m]
-// -- the Tucker factor contraction of mode n from the run's contraction S; one thread per
-// output, FP64 accumulation in a fixed order.
+// -- the Tucker factor contraction of mode n from the run's contraction S; one block of 256
+// threads per output, the threads striding the pairs with FP64 sums added as a fixed tree.
 struct KronFoldArgs {
     const float *S;  // [rows][ld]
     int ld;
@@ -457,8 +472,8 @@ struct KronFoldArgs {
 };
 
 __global__ void kron_fold_kernel(KronFoldArgs f) {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (int64_t)f.I[f.n] * f.J[f.n]) return;
+    __shared__ double sh[256];
+    const int64_t t = blockIdx.x;  // one block per output
     const int in = (int)(t / f.J[f.n]), jn = (int)(t % f.J[f.n]);
     int64_t oi = 1, oj = 1;
     for (int m = 0; m < f.M; ++m)
@@ -467,27 +482,32 @@ __global__ void kron_fold_kernel(KronFoldArgs f) {
             oj *= f.J[m];
         }
     double acc = 0.0;
-    for (int64_t qi = 0; qi < oi; ++qi)
-        for (int64_t qj = 0; qj < oj; ++qj) {
-            int64_t ri = qi, rj = qj, row = 0, col = 0, mi = 1, mj = 1;
-            float w = 1.0f;
-            for (int m = f.M - 1; m >= 0; --m) {
-                int im = in, jm = jn;
-                if (m != f.n) {
-                    im = (int)(ri % f.I[m]);
-                    ri /= f.I[m];
-                    jm = (int)(rj % f.J[m]);
-                    rj /= f.J[m];
-                    w *= f.L[m][(int64_t)im * f.J[m] + jm];
-                }
-                row += im * mi;
-                col += jm * mj;
-                mi *= f.I[m];
-                mj *= f.J[m];
+    for (int64_t q = threadIdx.x; q < oi * oj; q += blockDim.x) {
+        int64_t ri = q / oj, rj = q % oj, row = 0, col = 0, mi = 1, mj = 1;
+        float w = 1.0f;
+        for (int m = f.M - 1; m >= 0; --m) {
+            int im = in, jm = jn;
+            if (m != f.n) {
+                im = (int)(ri % f.I[m]);
+                ri /= f.I[m];
+                jm = (int)(rj % f.J[m]);
+                rj /= f.J[m];
+                w *= f.L[m][(int64_t)im * f.J[m] + jm];
             }
-            acc += (double)f.S[row * f.ld + col] * (double)w;
+            row += im * mi;
+            col += jm * mj;
+            mi *= f.I[m];
+            mj *= f.J[m];
         }
-    f.out[t] = (float)acc;
+        acc += (double)f.S[row * f.ld + col] * (double)w;
+    }
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int h = 128; h >= 1; h >>= 1) {  // fixed tree
+        if ((int)threadIdx.x < h) sh[threadIdx.x] += sh[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) f.out[t] = (float)sh[0];
 }
 
 __global__ void mu_plain_kernel(const float *pre, const float *num, const float *den, int64_t n, float gamma,
@@ -1147,7 +1167,7 @@ int tn_fold(ntf_ctx *ctx, const TNWay &t, int n, const float *S, int ld, float *
     f.M = k.M;
     f.n = n - t.gb[v];
     f.out = out;
-    kron_fold_kernel<<<nblk((int64_t)t.I[n] * t.J[n]), 256, 0, st>>>(f);
+    kron_fold_kernel<<<(unsigned)((int64_t)t.I[n] * t.J[n]), 256, 0, st>>>(f);
     TK(cudaGetLastError());
     return NTF_OK;
 }

@@ -43,7 +43,8 @@ def parse():
     p.add_argument("--no-ttt", action="store_true", help="skip the time-to-target runs")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     p.add_argument("--no-other", action="store_true",
-                   help="skip the Tucker 400^3, sparse 3.3M-nonzero and 4-way CP / Tucker measurements")
+                   help="skip the Tucker 400^3, sparse 3.3M-nonzero, 4-way CP / Tucker and 5-way Tucker "
+                        "measurements")
     p.add_argument("--serve-jobs", type=int, default=48,
                    help="jobs of the serving-mix measurement in the default run (0: skip)")
     p.add_argument("--serve", action="store_true", help="print only the serving-mix line")
@@ -51,10 +52,11 @@ def parse():
     p.add_argument("--profile-n", type=int, default=0,
                    help="profiling driver: three J-CoMM steps and three block-MU sweeps on an n^3, "
                         "R = 32, beta = 1 tensor at --precision, then exit (no measurement)")
-    p.add_argument("--profile-case", default="", choices=["", "tucker", "coo", "cp4", "tucker4"],
+    p.add_argument("--profile-case", default="", choices=["", "tucker", "coo", "cp4", "tucker4", "tucker5"],
                    help="profiling driver: three block-MM sweeps and three J-CoMM iterations of the Tucker "
                         "400^3 workload, three J-CoMM iterations of the sparse 3.3M-nonzero workload, or "
-                        "the 4-way CP / Tucker measurements with one timed call per configuration")
+                        "the 4-way CP / Tucker or 5-way Tucker measurements with one timed call per "
+                        "configuration")
     return p.parse_args()
 
 
@@ -343,6 +345,55 @@ def run_tucker_4way(ntf, ctx, peaks, iters=10, dims=(80, 70, 60, 50), J=(10, 9, 
     return out
 
 
+def run_tucker_5way(ntf, ctx, peaks, iters=10, dims=(27, 24, 7, 100, 100), J=(10, 10, 5, 10, 10), seed=9):
+    """Dense 5-way Tucker 27 x 24 x 7 x 100 x 100, ranks (10, 10, 5, 10, 10): the shape and ranks of
+    the paper's real-data Tucker fit, on a synthetic stand-in for its count tensor (the dataset is
+    not here): a Tucker intensity with Gamma(0.5, 1) factors and a Gamma(2, 1) core, rescaled so
+    that about 99.4% of the Poisson counts are zero, drawn on the device (seeded); init
+    U(0.1, 1).  Dense contractions, as in the paper.  Times block-MM sweeps and J-CoMM outer
+    iterations (L = 1) at beta in {1/2, 1, 3/2} with precision tf32 (tensor-core passes where
+    beta != 1, FP32 passes at beta = 1) on the cut the library picks; the 181 MB tensor is
+    larger than L2, no flush."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    g = torch.Generator(device=dev).manual_seed(seed)
+    torch.manual_seed(seed)
+    Gt = torch.distributions.Gamma(torch.full(J, 2.0, device=dev), 1.0).sample()
+    At = [torch.distributions.Gamma(torch.full((d, j), 0.5, device=dev), 1.0).sample() for d, j in zip(dims, J)]
+    M = torch.einsum("abcde,ia,jb,kc,ld,me->ijklm", Gt, *At)
+    M *= 0.0062 / M.mean()
+    X = torch.poisson(M).float().contiguous()
+    del M
+    zeros = float((X == 0).float().mean())
+    G0 = torch.rand(J, device=dev, generator=g) * 0.9 + 0.1
+    A0 = [torch.rand((d, j), device=dev, generator=g) * 0.9 + 0.1 for d, j in zip(dims, J)]
+    obj = torch.zeros(1, dtype=torch.float64, device=dev)
+    out = {"workload": "dense 5-way Tucker %s, ranks %s, synthetic counts" % ("x".join(map(str, dims)),
+                                                                            ",".join(map(str, J))),
+           "zero_fraction": zeros, "precision": "tf32", "l2": "inputs larger than L2 (181 MB), no flush"}
+    for beta in (0.5, 1.0, 1.5):
+        for name in ("block_mm", "jcomm"):
+            G, A = G0.clone(), [a.clone() for a in A0]
+
+            def step():
+                if name == "jcomm":
+                    ntf.jcomm_outer(X, beta, A, core=G, objective=obj, ctx=ctx, precision="tf32")
+                else:
+                    ntf.tucker_mu_sweep(X, beta, G, A, objective=obj, ctx=ctx, precision="tf32")
+            for _ in range(3):
+                step()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(iters):
+                step()
+            e1.record()
+            torch.cuda.synchronize()
+            out["%s_b%g_ms" % (name, beta)] = e0.elapsed_time(e1) / max(iters, 1)
+            out["%s_b%g_mean_objective" % (name, beta)] = obj.item() / X.numel()
+    return out
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -482,6 +533,8 @@ def main():
             r = run_cp_4way(ntf, ctx, peaks, iters=1)
         elif args.profile_case == "tucker4":
             r = run_tucker_4way(ntf, ctx, peaks, iters=1)
+        elif args.profile_case == "tucker5":
+            r = run_tucker_5way(ntf, ctx, peaks, iters=1)
         else:
             r = run_coo_c4(ntf, ctx, peaks, iters=0)
         print("profile case", args.profile_case, "done")
@@ -711,7 +764,8 @@ def main():
     other = None
     if not args.no_other:
         other = {"tucker_c3": run_tucker_c3(ntf, ctx, peaks), "coo_c4": run_coo_c4(ntf, ctx, peaks),
-                 "cp_4way": run_cp_4way(ntf, ctx, peaks), "tucker_4way": run_tucker_4way(ntf, ctx, peaks)}
+                 "cp_4way": run_cp_4way(ntf, ctx, peaks), "tucker_4way": run_tucker_4way(ntf, ctx, peaks),
+                 "tucker_5way": run_tucker_5way(ntf, ctx, peaks)}
 
     serving = None
     if args.serve_jobs > 0:

@@ -103,7 +103,7 @@ size_t estimate_bytes(const ntf_job &j, int sms) {
         b += sizeof(double) * (size_t)(ntf::row_blocks((int)I, RP) + ntf::row_blocks((int)J, RP) +
                                        ntf::row_blocks((int)K, RP)) * RP;
     } else {
-        const int RP = rank_pad((int)j.core_dims[2]);
+        const int RP = (j.precision != NTF_PREC_FP32 && j.core_dims[2] <= 32) ? 32 : rank_pad((int)j.core_dims[2]);
         const int64_t Jc = j.core_dims[0] * j.core_dims[1] * j.core_dims[2];
         b += 5 * sizeof(float) * (size_t)(I * J) * RP;  // B3 rec / num / den, W, Wd
         b += 4 * sizeof(float) * (size_t)(4 * Jc + I * j.core_dims[0] + J * j.core_dims[1] + K * RP);

@@ -707,7 +707,12 @@ int setup(ntf_ctx *ctx, const ntf_tensor *X, const int64_t *core_dims, bool jcom
           float beta) {
     w.I1 = (int)X->dims[0]; w.I2 = (int)X->dims[1]; w.I3 = (int)X->dims[2];
     w.J1 = (int)core_dims[0]; w.J2 = (int)core_dims[1]; w.J3 = (int)core_dims[2];
-    w.RP = rank_pad(w.J3);
+    // tensor cores when asked for and the shapes fit them: third core dimension <= 32
+    // (padded to 32), a 16-byte aligned X with I3 % 4 == 0, and beta != 1 (the explicit-rows
+    // kernels carry the denominator side)
+    w.tc = o.precision != NTF_PREC_FP32 && beta_kind(beta) != BK_KL && w.J3 <= 32 &&
+           cp3_tc_eligible(32, w.I3, X->values) && (int64_t)w.I1 * w.I2 < (1ll << 31);
+    w.RP = w.tc ? 32 : rank_pad(w.J3);
     const int64_t IJ = (int64_t)w.I1 * w.I2, Jc = (int64_t)w.J1 * w.J2 * w.J3;
     bool ok = true;
     w.Brec = wsf(ctx, "tkBrec", IJ * w.RP, ok);
@@ -724,11 +729,6 @@ int setup(ntf_ctx *ctx, const ntf_tensor *X, const int64_t *core_dims, bool jcom
     w.num = wsf(ctx, "tkNum", mx, ok);
     w.den = wsf(ctx, "tkDen", mx, ok);
     w.plan3 = cp3_plan(w.I1, w.I2, w.I3, w.RP, ctx_num_sms(ctx));
-    // tensor cores when asked for and the shapes fit them: third core dimension 17..32
-    // (rank padded to 32), a 16-byte aligned X with I3 % 4 == 0, and beta != 1 (the
-    // explicit-rows kernels carry the denominator side)
-    w.tc = o.precision != NTF_PREC_FP32 && beta_kind(beta) != BK_KL &&
-           cp3_tc_eligible(w.RP, w.I3, X->values) && (int64_t)w.I1 * w.I2 < (1ll << 31);
     if (w.tc) {
         w.tplan = cp3_plan(w.I1, w.I2, w.I3, w.RP, ctx_num_sms(ctx), 128);
         w.tplan.s3 = o.precision == NTF_PREC_3XTF32;
@@ -1099,9 +1099,9 @@ int tn_split(ntf_ctx *ctx, const ntf_tensor *X, const int64_t *cd, const ntf_opt
         }
         if (c[2] > 64 || e[0] * e[1] >= 2147483648.0 || e[2] >= 2147483648.0 || c[0] * c[1] * c[2] >= 2147483648.0)
             return false;
-        const int rp = rank_pad((int)c[2]);
-        const bool tc = o.precision != NTF_PREC_FP32 && beta_kind(beta) != BK_KL && rp == 32 &&
+        const bool tc = o.precision != NTF_PREC_FP32 && beta_kind(beta) != BK_KL && c[2] <= 32 &&
                         cp3_tc_eligible(32, (int)e[2], X->values);
+        const int rp = tc ? 32 : rank_pad((int)c[2]);
         const double tj = rp == 64 ? 64.0 : 128.0;
         const double pass = e[0] * std::ceil(e[1] / tj) * tj * std::ceil(e[2] / 64.0) * 64.0 * rp * 6.0;
         const double gemms = 2.0 * e[0] * e[1] * c[2] * (c[0] + 3.0 * c[1]);

@@ -85,6 +85,30 @@ def test_tucker_nway_tc_parity(beta, step):
     _check(Gd, Ad, Gw, Aw, obj, Fw, 1e-3, 2e-4)
 
 
+@pytest.mark.parametrize("beta", [0.5, 1.5])
+def test_tucker_5way_uber_like_tc_parity(beta):
+    """Order 5 with the structure of the paper's Uber Tucker fit (ranks 2,2,3,3,6 here): runs
+    {0,1}, {2,3}, {4}; last core extent 6 padded to 32 for the tensor-core passes; mostly-zero
+    count data."""
+    ntf = _ntf()
+    dims, J = (6, 5, 7, 16, 24), (2, 2, 3, 3, 6)
+    g = np.random.default_rng(80)
+    X = np.float32(g.poisson(0.05, size=dims) * (1 + g.geometric(0.3, size=dims))).astype(np.float64)
+    G0, A0 = synth.init_tucker(dims, J, seed=81)
+    for step in ("sweep", "jcomm"):
+        if step == "sweep":
+            Gw, Aw, Fw = oracle.tucker_mu_sweep(X, G0, A0, beta)
+        else:
+            Gw, Aw, Fw = oracle.tucker_jcomm_outer(X, G0, A0, beta, L=2)
+        Gd, Ad, obj = dev(G0), [dev(a) for a in A0], obj_tensor()
+        if step == "sweep":
+            ntf.tucker_mu_sweep(dev(X), beta, Gd, Ad, objective=obj, merge=(2, 4), precision="tf32")
+        else:
+            ntf.jcomm_outer(dev(X), beta, Ad, core=Gd, objective=obj, inner_L=2, merge=(2, 4), precision="tf32")
+        ntf.default_context().device_status()
+        _check(Gd, Ad, Gw, Aw, obj, Fw, 1e-3, 2e-4)
+
+
 @pytest.mark.parametrize("beta", [0.0, 0.5, 1.0, 1.5, 0.3])
 def test_tucker_nway_beta_div_parity(beta):
     ntf = _ntf()

@@ -2,7 +2,7 @@
 
 The rows pass (W = P A3n, Wd = Q A3d written per 128-column block and summed in block order)
 and the mode-3 pass run on the tensor cores when the precision is "tf32" or "3xtf32", the
-third core dimension pads to 32 (17..32), I3 % 4 == 0 and beta != 1.  Their arithmetic is
+third core dimension is at most 32 (padded to 32), I3 % 4 == 0 and beta != 1.  Their arithmetic is
 that of the CP tensor-core pass (TF32 or split-TF32 reconstruction from the rows of the
 partial tensor B^(3), BF16 contraction operands, FP32 accumulation, FP32 powers, FP64
 objective sum), so the same bars apply: 1e-3 per block after one sweep and 2e-4 on the

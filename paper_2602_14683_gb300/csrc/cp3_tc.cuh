@@ -918,15 +918,12 @@ cudaError_t launch_t(const Cp3Plan &p, const Cp3Args &a, cudaStream_t s) {
 template <int BK, bool S3>
 cudaError_t launch_bk(const Cp3Plan &p, const Cp3Args &a, int ms, cudaStream_t s) {
     if (a.rrow) {  // explicit rows (Tucker): W rows out, or the column contraction
-        if constexpr (BK == BK_KL) {
-            return cudaErrorInvalidValue;
-        } else {
-            switch (ms) {
-                case PM_M1 | PM_M2: return launch_t<PM_M1 | PM_M2, BK, S3, true>(p, a, s);
-                case PM_M1 | PM_M2 | PM_OBJ: return launch_t<PM_M1 | PM_M2 | PM_OBJ, BK, S3, true>(p, a, s);
-                case PM_M3: return launch_t<PM_M3, BK, S3, true>(p, a, s);
-                default: return cudaErrorInvalidValue;
-            }
+        if (p.KB != KBLK) return cudaErrorInvalidValue;
+        switch (ms) {
+            case PM_M1 | PM_M2: return launch_t<PM_M1 | PM_M2, BK, S3, true>(p, a, s);
+            case PM_M1 | PM_M2 | PM_OBJ: return launch_t<PM_M1 | PM_M2 | PM_OBJ, BK, S3, true>(p, a, s);
+            case PM_M3: return launch_t<PM_M3, BK, S3, true>(p, a, s);
+            default: return cudaErrorInvalidValue;
         }
     }
     if constexpr (BK == BK_KL && !S3) {

@@ -526,6 +526,13 @@ __global__ void chi_kernel(const float *z, const float *zt, int64_t n, float bet
     c2[t] = chi2_f(beta, z[t], zt[t]);
 }
 
+// out[p][row][c] = (p == 0 ? v[c] : 0) for p < parts, row < rows, c < RP
+__global__ void bcast_rows_kernel(const float *v, int64_t rows, int RP, int parts, float *out) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)parts * rows * RP) return;
+    out[t] = t < rows * RP ? v[t % RP] : 0.0f;
+}
+
 __global__ void pad_cols_kernel(const float *src, int rows, int cols, int ld, float *dst) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (int64_t)rows * ld) return;
@@ -568,6 +575,7 @@ struct TuckerWs {
     Cp3Plan tplan;
     float *Wpn, *Wpd;
     int parts3, obj_n;
+    float *cs;                // [RP] column sums (closed-form denominators at beta = 1)
     Blocks cur, ref, t1, t2;  // current, reference, chi1 and chi2 transforms
 };
 
@@ -632,13 +640,22 @@ int rows_pass(ntf_ctx *ctx, TuckerWs &w, const ntf_tensor *X, const ntf_opts &o,
         a.p1n = w.Wpn;
         a.p1d = w.Wpd;
         a.err = ctx_status(ctx);
-        TK(cp3_tc_launch(w.tplan, a, PM_M1 | PM_M2 | (obj ? PM_OBJ : 0), 1, st));
+        const bool kl = beta_kind(beta) == BK_KL;
+        TK(cp3_tc_launch(w.tplan, a, PM_M1 | PM_M2 | (obj ? PM_OBJ : 0), kl ? 0 : 1, st));
         // W = sum over the column blocks, in block order
         const int64_t n = (int64_t)w.I1 * w.I2 * w.RP;
         sum_parts_kernel<<<nblk(n), 256, 0, st>>>(w.Wpn, w.tplan.n_kb, n, w.Wn);
         TK(cudaGetLastError());
-        sum_parts_kernel<<<nblk(n), 256, 0, st>>>(w.Wpd, w.tplan.n_kb, n, w.Wd);
-        TK(cudaGetLastError());
+        if (kl) {
+            // Q = 1: Wd[i][j][c] = sum_k d3[k][c], the same for every row
+            const int rows3 = w.I3;
+            TK(colsum_prod(1, &d3, &rows3, w.RP, w.cs, st));
+            bcast_rows_kernel<<<nblk(n), 256, 0, st>>>(w.cs, (int64_t)w.I1 * w.I2, w.RP, 1, w.Wd);
+            TK(cudaGetLastError());
+        } else {
+            sum_parts_kernel<<<nblk(n), 256, 0, st>>>(w.Wpd, w.tplan.n_kb, n, w.Wd);
+            TK(cudaGetLastError());
+        }
         return NTF_OK;
     }
     RowsArgs ra{};
@@ -708,10 +725,10 @@ int setup(ntf_ctx *ctx, const ntf_tensor *X, const int64_t *core_dims, bool jcom
     w.I1 = (int)X->dims[0]; w.I2 = (int)X->dims[1]; w.I3 = (int)X->dims[2];
     w.J1 = (int)core_dims[0]; w.J2 = (int)core_dims[1]; w.J3 = (int)core_dims[2];
     // tensor cores when asked for and the shapes fit them: third core dimension <= 32
-    // (padded to 32), a 16-byte aligned X with I3 % 4 == 0, and beta != 1 (the explicit-rows
-    // kernels carry the denominator side)
-    w.tc = o.precision != NTF_PREC_FP32 && beta_kind(beta) != BK_KL && w.J3 <= 32 &&
-           cp3_tc_eligible(32, w.I3, X->values) && (int64_t)w.I1 * w.I2 < (1ll << 31);
+    // (padded to 32), a 16-byte aligned X with I3 % 4 == 0; at beta = 1 (Q = 1) the passes
+    // carry no denominator side and its sums are column sums (closed_den)
+    w.tc = o.precision != NTF_PREC_FP32 && w.J3 <= 32 && cp3_tc_eligible(32, w.I3, X->values) &&
+           (int64_t)w.I1 * w.I2 < (1ll << 31);
     w.RP = w.tc ? 32 : rank_pad(w.J3);
     const int64_t IJ = (int64_t)w.I1 * w.I2, Jc = (int64_t)w.J1 * w.J2 * w.J3;
     bool ok = true;
@@ -749,6 +766,7 @@ int setup(ntf_ctx *ctx, const ntf_tensor *X, const int64_t *core_dims, bool jcom
     int gmax = std::max(std::max(w.rows_grid, w.plan3.grid), w.tc ? w.tplan.grid : 0);
     w.obj = (double *)ctx_ws(ctx, "tkObj", sizeof(double) * (size_t)gmax);
     if (!w.obj) ok = false;
+    w.cs = wsf(ctx, "tkCs", 64, ok);
     const char *names[4][4] = {{"tkG", "tkA1", "tkA2", "tkA3"}, {"tkGt", "tkA1t", "tkA2t", "tkA3t"},
                                {"tkG1", "tkA11", "tkA21", "tkA31"}, {"tkG2", "tkA12", "tkA22", "tkA32"}};
     Blocks *bs[4] = {&w.cur, &w.ref, &w.t1, &w.t2};
@@ -807,7 +825,17 @@ int mode3_pass(ntf_ctx *ctx, TuckerWs &w, const ntf_tensor *X, const ntf_opts &o
         a.p3n = w.pn3;
         a.p3d = w.pd3;
         a.err = ctx_status(ctx);
-        TK(cp3_tc_launch(w.tplan, a, PM_M3, 1, st));
+        const bool kl = beta_kind(beta) == BK_KL;
+        TK(cp3_tc_launch(w.tplan, a, PM_M3, kl ? 0 : 1, st));
+        if (kl) {
+            // Q = 1: Den3[k][c] = sum over the rows of drow, the same for every k (first part;
+            // the other parts zero)
+            const int rows12 = w.I1 * w.I2;
+            TK(colsum_prod(1, &drow, &rows12, w.RP, w.cs, st));
+            const int64_t n = (int64_t)w.parts3 * w.I3 * w.RP;
+            bcast_rows_kernel<<<nblk(n), 256, 0, st>>>(w.cs, w.I3, w.RP, w.parts3, w.pd3);
+            TK(cudaGetLastError());
+        }
         return NTF_OK;
     }
     a.n_jt = w.plan3.n_jt;
@@ -1099,8 +1127,7 @@ int tn_split(ntf_ctx *ctx, const ntf_tensor *X, const int64_t *cd, const ntf_opt
         }
         if (c[2] > 64 || e[0] * e[1] >= 2147483648.0 || e[2] >= 2147483648.0 || c[0] * c[1] * c[2] >= 2147483648.0)
             return false;
-        const bool tc = o.precision != NTF_PREC_FP32 && beta_kind(beta) != BK_KL && c[2] <= 32 &&
-                        cp3_tc_eligible(32, (int)e[2], X->values);
+        const bool tc = o.precision != NTF_PREC_FP32 && c[2] <= 32 && cp3_tc_eligible(32, (int)e[2], X->values);
         const int rp = tc ? 32 : rank_pad((int)c[2]);
         const double tj = rp == 64 ? 64.0 : 128.0;
         const double pass = e[0] * std::ceil(e[1] / tj) * tj * std::ceil(e[2] / 64.0) * 64.0 * rp * 6.0;

@@ -63,7 +63,7 @@ def test_tucker_nway_jcomm_parity(dims, J, merge, beta, L):
     _check(Gd, Ad, Gw, Aw, obj, Fw, 1e-5, 1e-5)
 
 
-@pytest.mark.parametrize("beta", [0.5, 1.5])
+@pytest.mark.parametrize("beta", [0.5, 1.0, 1.5])
 @pytest.mark.parametrize("step", ["sweep", "jcomm"])
 def test_tucker_nway_tc_parity(beta, step):
     """Last run (modes 3, 4) with core extent 4 x 5 = 20 (padded to 32) and 8 x 12 = 96
@@ -85,7 +85,7 @@ def test_tucker_nway_tc_parity(beta, step):
     _check(Gd, Ad, Gw, Aw, obj, Fw, 1e-3, 2e-4)
 
 
-@pytest.mark.parametrize("beta", [0.5, 1.5])
+@pytest.mark.parametrize("beta", [0.5, 1.0, 1.5])
 def test_tucker_5way_uber_like_tc_parity(beta):
     """Order 5 with the structure of the paper's Uber Tucker fit (ranks 2,2,3,3,6 here): runs
     {0,1}, {2,3}, {4}; last core extent 6 padded to 32 for the tensor-core passes; mostly-zero

@@ -2,7 +2,8 @@
 
 The rows pass (W = P A3n, Wd = Q A3d written per 128-column block and summed in block order)
 and the mode-3 pass run on the tensor cores when the precision is "tf32" or "3xtf32", the
-third core dimension is at most 32 (padded to 32), I3 % 4 == 0 and beta != 1.  Their arithmetic is
+third core dimension is at most 32 (padded to 32) and I3 % 4 == 0 (at beta = 1 the passes carry
+no denominator side: Q = 1 makes those sums column sums).  Their arithmetic is
 that of the CP tensor-core pass (TF32 or split-TF32 reconstruction from the rows of the
 partial tensor B^(3), BF16 contraction operands, FP32 accumulation, FP32 powers, FP64
 objective sum), so the same bars apply: 1e-3 per block after one sweep and 2e-4 on the
@@ -37,7 +38,7 @@ def _check(Gd, Ad, Gw, Aw, obj, Fw, tag):
 
 
 @pytest.mark.parametrize("prec", ["tf32", "3xtf32"])
-@pytest.mark.parametrize("beta", [0.0, 0.5, 1.5, 1.2])
+@pytest.mark.parametrize("beta", [0.0, 0.5, 1.0, 1.5, 1.2])
 @pytest.mark.parametrize("case", range(len(CASES)))
 def test_tucker_tc_sweep_parity(beta, case, prec):
     ntf = _ntf()
@@ -52,7 +53,7 @@ def test_tucker_tc_sweep_parity(beta, case, prec):
 
 
 @pytest.mark.parametrize("prec", ["tf32", "3xtf32"])
-@pytest.mark.parametrize("beta", [0.5, 1.5])
+@pytest.mark.parametrize("beta", [0.5, 1.0, 1.5])
 @pytest.mark.parametrize("L", [1, 2])
 def test_tucker_tc_jcomm_parity(beta, L, prec):
     ntf = _ntf()
@@ -66,19 +67,26 @@ def test_tucker_tc_jcomm_parity(beta, L, prec):
     _check(Gd, Ad, Gw, Aw, obj, Fw, "tucker tc %s jcomm beta=%g L=%d" % (prec, beta, L))
 
 
-def test_tucker_tc_kl_falls_back_to_fp32():
-    """beta = 1 with precision "tf32" runs the FP32 passes: FP32 bar (1e-5)."""
+def test_tucker_tc_kl_runs_on_tensor_cores():
+    """beta = 1 with precision "tf32" runs the tensor-core passes without a denominator side
+    (Q = 1: the Wd rows and the mode-3 denominators are column sums): tensor-core bar against
+    the oracle, and a result that differs from the FP32 passes' (the BF16 contractions ran)."""
     ntf = _ntf()
     dims, J = CASES[0]
     X, _, _ = synth.tucker_dense(dims, J, seed=50)
     G0, A0 = synth.init_tucker(dims, J, seed=51)
     Gw, Aw, Fw = oracle.tucker_mu_sweep(X, G0, A0, 1.0)
-    Gd, Ad, obj = dev(G0), [dev(a) for a in A0], obj_tensor()
-    ntf.tucker_mu_sweep(dev(X), 1.0, Gd, Ad, objective=obj, precision="tf32")
-    assert rel_fro(host(Gd), Gw) <= 1e-5
-    for n in range(3):
-        assert rel_fro(host(Ad[n]), Aw[n]) <= 1e-5, n
-    assert abs(obj.item() - Fw) / Fw <= 1e-5
+    res = {}
+    for prec in ("fp32", "tf32"):
+        Gd, Ad, obj = dev(G0), [dev(a) for a in A0], obj_tensor()
+        ntf.tucker_mu_sweep(dev(X), 1.0, Gd, Ad, objective=obj, precision=prec)
+        ntf.default_context().device_status()
+        res[prec] = (Gd, Ad)
+        if prec == "tf32":
+            _check(Gd, Ad, Gw, Aw, obj, Fw, "tucker tc tf32 sweep beta=1")
+        else:
+            assert rel_fro(host(Gd), Gw) <= 1e-5
+    assert rel_fro(host(res["tf32"][0]), host(res["fp32"][0])) > 1e-7
 
 
 def test_tucker_tc_trajectory_beta15():

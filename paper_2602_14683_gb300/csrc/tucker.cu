@@ -48,14 +48,16 @@ struct Gemm {
 constexpr int GK = 16;   // reduction chunk
 constexpr int GCARRY = 16;  // chunks summed in FP32 before the FP64 carry
 
-// Output tiles of TM x TN (64 x 64, or 256 x 16 for outputs at most 16 columns wide); each of
-// the 256 threads holds a 4 x 4 block of outputs strided by TM / 4 rows and TN / 4 columns.
+// Output tiles of TM x TN (64 x 64; 128 x 32 for outputs at most 32 columns wide, 256 x 16 for at
+// most 16); each of the 256 threads holds a 4 x 4 block of contiguous rows and columns, read from
+// the k-major shared tiles with one 16-byte load each.  Every output sums its k terms in
+// increasing k, so the tile shape does not change any result.
 template <int TM, int TN>
 __global__ void __launch_bounds__(256) gemm2k_kernel(const Gemm g) {
     static_assert(TM * TN == 4096, "256 threads x 16 outputs");
     constexpr int CT = TN / 4;  // thread columns
-    __shared__ float As[GK][TM + 4];
-    __shared__ float Bs[GK][TN + 4];
+    __shared__ __align__(16) float As[GK][TM];
+    __shared__ __align__(16) float Bs[GK][TN];
     const int bt = blockIdx.z % g.batch, sp = blockIdx.z / g.batch;
     const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
     const int tid = threadIdx.x, tm = tid / CT, tn = tid % CT;
@@ -70,34 +72,73 @@ __global__ void __launch_bounds__(256) gemm2k_kernel(const Gemm g) {
         for (int y = 0; y < 4; ++y) acc[x][y] = 0.0f, tot[x][y] = 0.0;
     const float *A = g.A + bt * g.sab;
     const float *B = g.B + bt * g.sbb;
-    int chunk = 0;
-    for (int k0 = kbeg; k0 < kend; k0 += GK) {
-        for (int t = tid; t < GK * TM; t += 256) {
-            const int kk = t / TM, mm = t % TM, k = k0 + kk;
+    // (k1, k2) of k = k0 + kk from k0's quotient and remainder (one division per chunk)
+    auto split = [&](int q0, int r0, int kk, int &k1, int &k2) {
+        if (g.K2 == 1) {
+            k1 = q0 + kk;
+            k2 = 0;
+            return;
+        }
+        k2 = r0 + kk;
+        k1 = q0;
+        if (k2 >= g.K2) {
+            if (g.K2 >= GK) {
+                k2 -= g.K2;
+                k1 += 1;
+            } else {
+                k1 += k2 / g.K2;
+                k2 %= g.K2;
+            }
+        }
+    };
+    // the next chunk's tile elements are loaded into registers while this chunk computes
+    constexpr int NA = GK * TM / 256, NB = GK * TN / 256;
+    float ra[NA], rb[NB];
+    auto load = [&](int k0) {
+        const int q0 = k0 / g.K2, r0 = k0 - q0 * g.K2;
+#pragma unroll
+        for (int e = 0; e < NA; ++e) {
+            const int t = tid + 256 * e, kk = t / TM, mm = t % TM, k = k0 + kk;
             float va = 0.0f;
             if (k < kend && m0 + mm < g.M) {
-                const int k1 = g.K2 == 1 ? k : k / g.K2, k2 = k - k1 * g.K2;
+                int k1, k2;
+                split(q0, r0, kk, k1, k2);
                 va = A[(m0 + mm) * g.sam + k1 * g.sak1 + k2 * g.sak2];
             }
-            As[kk][mm] = va;
+            ra[e] = va;
         }
-        for (int t = tid; t < GK * TN; t += 256) {
-            const int kk = t / TN, nn = t % TN, k = k0 + kk;
+#pragma unroll
+        for (int e = 0; e < NB; ++e) {
+            const int t = tid + 256 * e, kk = t / TN, nn = t % TN, k = k0 + kk;
             float vb = 0.0f;
             if (k < kend && n0 + nn < g.N) {
-                const int k1 = g.K2 == 1 ? k : k / g.K2, k2 = k - k1 * g.K2;
+                int k1, k2;
+                split(q0, r0, kk, k1, k2);
                 vb = B[k1 * g.sbk1 + k2 * g.sbk2 + (n0 + nn) * g.sbn];
             }
-            Bs[kk][nn] = vb;
+            rb[e] = vb;
+        }
+    };
+    if (kbeg < kend) load(kbeg);
+    int chunk = 0;
+    for (int k0 = kbeg; k0 < kend; k0 += GK) {
+#pragma unroll
+        for (int e = 0; e < NA; ++e) {
+            const int t = tid + 256 * e;
+            As[t / TM][t % TM] = ra[e];
+        }
+#pragma unroll
+        for (int e = 0; e < NB; ++e) {
+            const int t = tid + 256 * e;
+            Bs[t / TN][t % TN] = rb[e];
         }
         __syncthreads();
+        if (k0 + GK < kend) load(k0 + GK);
 #pragma unroll
         for (int kk = 0; kk < GK; ++kk) {
-            float a[4], b[4];
-#pragma unroll
-            for (int x = 0; x < 4; ++x) a[x] = As[kk][tm + (TM / 4) * x];
-#pragma unroll
-            for (int y = 0; y < 4; ++y) b[y] = Bs[kk][tn + CT * y];
+            const float4 av = *reinterpret_cast<const float4 *>(&As[kk][4 * tm]);
+            const float4 bv = *reinterpret_cast<const float4 *>(&Bs[kk][4 * tn]);
+            const float a[4] = {av.x, av.y, av.z, av.w}, b[4] = {bv.x, bv.y, bv.z, bv.w};
 #pragma unroll
             for (int x = 0; x < 4; ++x)
 #pragma unroll
@@ -112,17 +153,29 @@ __global__ void __launch_bounds__(256) gemm2k_kernel(const Gemm g) {
                 for (int y = 0; y < 4; ++y) tot[x][y] += (double)acc[x][y], acc[x][y] = 0.0f;
         }
     }
+    // outputs: four consecutive columns as one 16-byte store where the layout allows
+    const int nb = n0 + 4 * tn;
+    const bool vec = nb + 3 < g.N &&
+                     (g.splits > 1 ? (g.N % 4 == 0)
+                                   : (g.scn == 1 && g.scm % 4 == 0 && g.scb % 4 == 0 &&
+                                      (reinterpret_cast<uintptr_t>(g.C) & 15) == 0));
 #pragma unroll
-    for (int x = 0; x < 4; ++x)
+    for (int x = 0; x < 4; ++x) {
+        const int m = m0 + 4 * tm + x;
+        if (m >= g.M) continue;
+        float v[4];
 #pragma unroll
-        for (int y = 0; y < 4; ++y) {
-            const int m = m0 + tm + (TM / 4) * x, n = n0 + tn + CT * y;
-            if (m < g.M && n < g.N) {
-                const float v = carry ? (float)(tot[x][y] + (double)acc[x][y]) : acc[x][y];
-                if (g.splits > 1) g.part[(((int64_t)sp * g.batch + bt) * g.M + m) * g.N + n] = v;
-                else g.C[bt * g.scb + m * g.scm + n * g.scn] = v;
-            }
+        for (int y = 0; y < 4; ++y) v[y] = carry ? (float)(tot[x][y] + (double)acc[x][y]) : acc[x][y];
+        float *dst = g.splits > 1 ? g.part + (((int64_t)sp * g.batch + bt) * g.M + m) * g.N + nb
+                                  : g.C + bt * g.scb + m * g.scm + nb * g.scn;
+        if (vec) {
+            *reinterpret_cast<float4 *>(dst) = make_float4(v[0], v[1], v[2], v[3]);
+        } else {
+#pragma unroll
+            for (int y = 0; y < 4; ++y)
+                if (nb + y < g.N) dst[y * (g.splits > 1 ? 1 : g.scn)] = v[y];
         }
+    }
 }
 
 // C = sum over the reduction ranges, in range order
@@ -139,8 +192,7 @@ __global__ void gemm_split_sum_kernel(const Gemm g) {
 // Splits the reduction when the output tiles alone would leave most SMs idle: about two
 // CTAs per SM, at least four GK-chunks per range.
 static int gemm(ntf_ctx *ctx, Gemm g, cudaStream_t s) {
-    const bool narrow = g.N <= 16;
-    const int TM = narrow ? 256 : 64, TN = narrow ? 16 : 64;
+    const int TN = g.N <= 16 ? 16 : g.N <= 32 ? 32 : 64, TM = 4096 / TN;
     const int tiles = ((g.N + TN - 1) / TN) * ((g.M + TM - 1) / TM) * g.batch;
     const int nchunks = (g.K1 * g.K2 + GK - 1) / GK;
     int splits = (2 * ctx_num_sms(ctx) + tiles - 1) / tiles;
@@ -152,8 +204,10 @@ static int gemm(ntf_ctx *ctx, Gemm g, cudaStream_t s) {
         if (!g.part) return ctx_fail(ctx, NTF_ERR_OOM, "workspace allocation failed");
     }
     dim3 grid((g.N + TN - 1) / TN, (g.M + TM - 1) / TM, g.batch * g.splits);
-    if (narrow)
+    if (TN == 16)
         gemm2k_kernel<256, 16><<<grid, 256, 0, s>>>(g);
+    else if (TN == 32)
+        gemm2k_kernel<128, 32><<<grid, 256, 0, s>>>(g);
     else
         gemm2k_kernel<64, 64><<<grid, 256, 0, s>>>(g);
     cudaError_t e = cudaGetLastError();

@@ -256,14 +256,34 @@ def run_coo_c4(ntf, ctx, peaks, iters=20, R=32, seed=0):
                                "4 passes x 20 B/nnz streamed; factor-row gathers hit L2"}}
 
 
+def flushed_loop_ms(flush, call, iters):
+    """Mean device time of `call` over `iters` back-to-back iterations, each preceded by a
+    write of `flush` (larger than L2) on the same stream and bracketed by its own CUDA events;
+    the host does not wait between iterations, so the intervals hold the call's kernels only
+    (the flush is outside them) and host enqueue time overlaps the previous iteration, as in a
+    loop that a user runs."""
+    import torch
+    ev = []
+    for _ in range(iters):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        call()
+        e1.record()
+        ev.append((e0, e1))
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in ev) / max(iters, 1)
+
+
 def run_cp_4way(ntf, ctx, peaks, iters=20, dims=(80, 70, 60, 50), R=10, seed=5):
     """Dense 4-way CP 80 x 70 x 60 x 50, R = 10 (the shape of the paper's synthetic CP
     experiment): Gamma(2,1) factors x Gamma(10,0.1) noise, init U(0.1, 1).  Times B-CoMM
     sweeps at beta in {1/2, 1, 3/2} and J-CoMM outer iterations (L = 1) at beta = 1, FP32 and
     TF32.  The tensor (67 MB) fits in the 129 MB L2, so a 256 MB buffer is written before
-    every timed iteration and each iteration is timed alone.  Roofline: a B-CoMM sweep makes
-    4 passes over X (leading modes on the merged 3-way view), a J-CoMM iteration at beta = 1
-    one; 4 bytes per entry and pass against the HBM copy bandwidth."""
+    every timed iteration and each iteration is timed by its own events (flushed_loop_ms).
+    Roofline: a B-CoMM sweep makes 4 passes over X (on the 3-way view of the cut the library
+    picks), a J-CoMM iteration at beta = 1 one; 4 bytes per entry and pass against the HBM copy
+    bandwidth."""
     import torch
     import synth
     dev = torch.device("cuda", torch.cuda.current_device())
@@ -283,16 +303,7 @@ def run_cp_4way(ntf, ctx, peaks, iters=20, dims=(80, 70, 60, 50), R=10, seed=5):
             for _ in range(3):
                 fn(X, beta, A, objective=obj, ctx=ctx, precision=prec)
             torch.cuda.synchronize()
-            tot = 0.0
-            for _ in range(iters):
-                flush.zero_()
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record()
-                fn(X, beta, A, objective=obj, ctx=ctx, precision=prec)
-                e1.record()
-                torch.cuda.synchronize()
-                tot += e0.elapsed_time(e1)
-            ms = tot / iters
+            ms = flushed_loop_ms(flush, lambda: fn(X, beta, A, objective=obj, ctx=ctx, precision=prec), iters)
             passes = 1 if name.startswith("jcomm") else len(dims)
             gbs = passes * 4 * entries / (ms / 1e3) / 1e9
             res[name] = {"ms": ms, "objective": obj.item(), "hbm_gbs_algorithmic": gbs,
@@ -306,7 +317,7 @@ def run_tucker_4way(ntf, ctx, peaks, iters=10, dims=(80, 70, 60, 50), J=(10, 9, 
     synthetic Tucker experiment): Gamma(2,1) core and factors, model rescaled to mean 10,
     Poisson noise, init U(0.1, 1).  Times block-MM sweeps (core, then the four factors) and
     J-CoMM outer iterations (L = 1) at beta in {1/2, 1, 3/2} on the cut the library picks,
-    with a 256 MB write before every timed call (the 67 MB tensor fits in L2)."""
+    with a 256 MB write before every timed call (the 67 MB tensor fits in L2; flushed_loop_ms)."""
     import torch
     import synth
     dev = torch.device("cuda", torch.cuda.current_device())
@@ -331,16 +342,7 @@ def run_tucker_4way(ntf, ctx, peaks, iters=10, dims=(80, 70, 60, 50), J=(10, 9, 
             for _ in range(3):
                 step()
             torch.cuda.synchronize()
-            tot = 0.0
-            for _ in range(iters):
-                flush.zero_()
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record()
-                step()
-                e1.record()
-                torch.cuda.synchronize()
-                tot += e0.elapsed_time(e1)
-            out["%s_b%g_ms" % (name, beta)] = tot / iters
+            out["%s_b%g_ms" % (name, beta)] = flushed_loop_ms(flush, step, iters)
             out["%s_b%g_objective" % (name, beta)] = obj.item()
     return out
 

@@ -255,8 +255,8 @@ cudaError_t extrapolate(const ExtrapArgs &x, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// Order N >= 4 on the 3-way kernels: the leading modes 0..M-1 are merged into one mode whose
-// index is the row-major multi-index (last leading mode fastest -- the memory order of X),
+// Order N >= 4 on the 3-way kernels: a run of consecutive modes is merged into one mode whose
+// index is the row-major multi-index (last mode of the run fastest -- the memory order of X),
 // with the Khatri-Rao factor KR[(i_0..i_{M-1})][r] = prod_m L_m[i_m][r].
 __global__ void kr_merge_kernel(KrArgs k) {
     __shared__ double sh[256];
@@ -286,60 +286,74 @@ cudaError_t kr_merge(const KrArgs &k, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// sum[row][r] = sum over the parts, in order, of parts[p][row][r] (FP32)
-__global__ void fold_parts_kernel(const float *parts, int n_parts, int64_t n, float *sum) {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n) return;
-    float v = 0.0f;
-    for (int p = 0; p < n_parts; ++p) v += parts[(int64_t)p * n + t];
-    sum[t] = v;
-}
-
-// out[i_n][r] = sum over the run's other indices (row-major order) of
-//   S[merged index][r] * prod_{m != n} L_m[i_m][r]
-// -- CPContr^(n) of the merged-mode contraction S.  One block per i_n; RP-lane group g of the
-// block takes the other-index positions q = g, g + G, ..., accumulating in FP64, and the groups'
-// sums are added in group order.
-__global__ void kr_fold_kernel(FoldArgs f, const float *S) {
+// One block per row i_n of the mode; RP-lane group g of the block takes the other-index
+// positions q = g, g + G, ... of the fold and the rows g, g + G, ... of the column sums.
+__global__ void run_update_kernel(RunUpdArgs u) {
     __shared__ double sh[256];
-    const int RP = f.RP, G = blockDim.x / RP, t = threadIdx.x, r = t % RP, g = t / RP;
+    __shared__ float num_s[64], den_s[64];
+    const int RP = u.RP, G = blockDim.x / RP, t = threadIdx.x, r = t % RP, g = t / RP;
     const int in = blockIdx.x;
-    int64_t other = 1;
-    for (int m = 0; m < f.M; ++m)
-        if (m != f.n) other *= f.dims[m];
-    double acc = 0.0;
-    for (int64_t q = g; q < other; q += G) {
-        // the other indices from q (row-major over m != n), and the merged row index
-        int64_t rem = q, row = 0, mul = 1;
-        float w = 1.0f;
-        for (int m = f.M - 1; m >= 0; --m) {
-            int im;
-            if (m == f.n) {
-                im = in;
-            } else {
-                im = (int)(rem % f.dims[m]);
-                rem /= f.dims[m];
-                w *= f.L[m][(int64_t)im * RP + r];
-            }
-            row += (int64_t)im * mul;
-            mul *= f.dims[m];
+    if (!u.pd) {
+        double prod = 1.0;
+        for (int k = 0; k < u.ncf; ++k) {
+            double cs = 0.0;
+            for (int i = g; i < u.cf_rows[k]; i += G) cs += (double)u.cf[k][(int64_t)i * RP + r];
+            prod *= group_sum(sh, cs, RP, t);
         }
-        acc += (double)S[row * RP + r] * (double)w;
+        if (t < RP) den_s[t] = (float)prod;
     }
-    const double tot = group_sum(sh, acc, RP, t);
-    if (t < RP) f.out[(int64_t)in * RP + t] = t < f.R ? (float)tot : 0.0f;
+    int64_t other = 1;
+    for (int m = 0; m < u.M; ++m)
+        if (m != u.n) other *= u.dims[m];
+    const int64_t stride = (int64_t)u.rows * RP;
+    for (int side = 0; side < (u.pd ? 2 : 1); ++side) {
+        const float *parts = side ? u.pd : u.pn;
+        const float *const *L = side ? u.Ld : u.Ln;
+        double acc = 0.0;
+        for (int64_t q = g; q < other; q += G) {
+            int64_t rem = q, row = 0, mul = 1;
+            float w = 1.0f;
+            for (int m = u.M - 1; m >= 0; --m) {
+                int im;
+                if (m == u.n) {
+                    im = in;
+                } else {
+                    im = (int)(rem % u.dims[m]);
+                    rem /= u.dims[m];
+                    w *= L[m][(int64_t)im * RP + r];
+                }
+                row += (int64_t)im * mul;
+                mul *= u.dims[m];
+            }
+            float sv = 0.0f;
+            for (int p = 0; p < u.n_parts; ++p) sv += parts[(int64_t)p * stride + row * RP + r];
+            acc += (double)sv * (double)w;
+        }
+        const double tot = group_sum(sh, acc, RP, t);
+        if (t < RP) (side ? den_s : num_s)[t] = (float)tot;
+    }
+    __syncthreads();
+    if (t >= RP) return;
+    const int64_t o = (int64_t)in * RP + t;
+    float v = 0.0f, c1 = 0.0f, c2 = 0.0f;
+    if (t < u.R) {
+        const float ratio = __fdiv_rn(num_s[t], den_s[t]);
+        float m;
+        if (u.gamma == 1.0f) m = ratio;
+        else if (u.gamma == 0.5f) m = sqrtf(ratio);
+        else m = powf(ratio, u.gamma);
+        v = fmaxf(u.pre[o] * m, u.eps);
+        if (u.chi1) c1 = chi1_f(u.beta, v, u.ref[o]);
+        if (u.chi2) c2 = chi2_f(u.beta, v, u.ref[o]);
+        if (u.user) u.user[(int64_t)in * u.R + t] = v;
+    }
+    u.out[o] = v;
+    if (u.chi1) u.chi1[o] = c1;
+    if (u.chi2) u.chi2[o] = c2;
 }
 
-cudaError_t kr_fold(const FoldArgs &f, cudaStream_t s) {
-    const float *S = f.parts;
-    if (f.n_parts > 1) {
-        const int64_t n = (int64_t)f.rows * f.RP;
-        fold_parts_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(f.parts, f.n_parts, n, f.scratch);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-        S = f.scratch;
-    }
-    kr_fold_kernel<<<f.dims[f.n], 256, 0, s>>>(f, S);
+cudaError_t run_update(const RunUpdArgs &u, cudaStream_t s) {
+    run_update_kernel<<<u.dims[u.n], 256, 0, s>>>(u);
     return cudaGetLastError();
 }
 

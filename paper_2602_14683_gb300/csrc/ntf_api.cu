@@ -601,8 +601,6 @@ struct NWay {
     // mode alone in its run, a buffer of its own otherwise (the slot then holds the run's
     // Khatri-Rao product)
     float *P[8], *Pt[8], *C1P[8], *C2P[8];
-    float *num, *den;      // folded Num / Den of a merged mode, [max I_n][RP]
-    float *sum;            // summed partials of a merged run, [max run extent][RP]
 };
 
 bool nway_single(const NWay &w, int v) { return w.ge[v] - w.gb[v] == 1; }
@@ -659,10 +657,8 @@ int nway_setup(ntf_ctx *ctx, const ntf_tensor *X, int R, bool jcomm, bool need_d
     w.X3.dims = w.dims3;
     if ((rc = cp_dense_setup(ctx, &w.X3, R, jcomm, need_den, precision, s))) return rc;
     const bool chi = jcomm && need_den;
-    int64_t maxI = 1;
     for (int m = 0; m < w.N; ++m) {
         const int v = w.view[m];
-        maxI = std::max(maxI, w.dims[m]);
         if (nway_single(w, v)) {
             w.P[m] = s.F[v];
             w.Pt[m] = jcomm ? s.Ft[v] : s.F[v];
@@ -679,13 +675,6 @@ int nway_setup(ntf_ctx *ctx, const ntf_tensor *X, int R, bool jcomm, bool need_d
         if (!w.P[m] || !w.Pt[m] || (chi && (!w.C1P[m] || !w.C2P[m])))
             return fail(ctx, NTF_ERR_OOM, "workspace allocation failed");
     }
-    int64_t maxRun = 1;
-    for (int v = 0; v < 3; ++v)
-        if (!nway_single(w, v)) maxRun = std::max(maxRun, w.dims3[v]);
-    w.num = (float *)ws_get(ctx, "nwNum", sizeof(float) * (size_t)maxI * s.RP);
-    w.den = (float *)ws_get(ctx, "nwDen", sizeof(float) * (size_t)maxI * s.RP);
-    w.sum = (float *)ws_get(ctx, "nwSum", sizeof(float) * (size_t)maxRun * s.RP);
-    if (!w.num || !w.den || !w.sum) return fail(ctx, NTF_ERR_OOM, "workspace allocation failed");
     return NTF_OK;
 }
 
@@ -763,55 +752,37 @@ int nway_run_update(ntf_ctx *ctx, NWay &w, CpDense &s, int n, float beta, const 
                     const RunUpd &q, cudaStream_t st) {
     const int v = w.view[n];
     const int parts[3] = {s.plan.parts1, s.plan.parts2, s.plan.parts3};
-    ntf::FoldArgs f{};
-    f.parts = s.pn[v];
-    f.n_parts = parts[v];
-    f.M = w.ge[v] - w.gb[v];
-    for (int j = 0; j < f.M; ++j) {
-        f.L[j] = q.Lnum[w.gb[v] + j];
-        f.dims[j] = (int)w.dims[w.gb[v] + j];
+    ntf::RunUpdArgs u{};
+    u.pn = s.pn[v];
+    u.pd = kl ? nullptr : s.pd[v];
+    u.n_parts = parts[v];
+    u.rows = (int)w.dims3[v];
+    u.M = w.ge[v] - w.gb[v];
+    for (int j = 0; j < u.M; ++j) {
+        u.Ln[j] = q.Lnum[w.gb[v] + j];
+        u.Ld[j] = q.Lden[w.gb[v] + j];
+        u.dims[j] = (int)w.dims[w.gb[v] + j];
     }
-    f.n = n - w.gb[v];
-    f.rows = (int)w.dims3[v];
-    f.R = s.R;
-    f.RP = s.RP;
-    f.out = w.num;
-    f.scratch = w.sum;
-    NTF_CUDA(ntf::kr_fold(f, st));
-    ntf::MuEpiArgs e{};
-    e.pn = w.num;
-    e.n_parts = 1;
-    e.rows = (int)w.dims[n];
-    e.RP = s.RP;
-    e.R = s.R;
-    if (kl) {
-        const float *cf[8];
-        int rows[8], c = 0;
+    u.n = n - w.gb[v];
+    if (kl)
         for (int m = 0; m < w.N; ++m)
             if (m != n) {
-                cf[c] = w.P[m];
-                rows[c] = (int)w.dims[m];
-                ++c;
+                u.cf[u.ncf] = w.P[m];
+                u.cf_rows[u.ncf] = (int)w.dims[m];
+                ++u.ncf;
             }
-        NTF_CUDA(ntf::colsum_prod(c, cf, rows, s.RP, s.denc, st));
-        e.den_closed = s.denc;
-    } else {
-        f.parts = s.pd[v];
-        for (int j = 0; j < f.M; ++j) f.L[j] = q.Lden[w.gb[v] + j];
-        f.out = w.den;
-        NTF_CUDA(ntf::kr_fold(f, st));
-        e.pd = w.den;
-    }
-    e.pre = q.pre;
-    e.out = q.out;
-    e.ref = q.ref;
-    e.chi1_out = q.chi1;
-    e.chi2_out = q.chi2;
-    e.beta = beta;
-    e.gamma = ntf::mu_gamma(beta);
-    e.eps = (float)o.eps;
-    NTF_CUDA(ntf::mu_epilogue(e, st));
-    if (q.user) NTF_CUDA(ntf::unpad_factor(q.out, (int)w.dims[n], s.R, s.RP, q.user, st));
+    u.pre = q.pre;
+    u.out = q.out;
+    u.ref = q.ref;
+    u.chi1 = q.chi1;
+    u.chi2 = q.chi2;
+    u.user = q.user;
+    u.R = s.R;
+    u.RP = s.RP;
+    u.beta = beta;
+    u.gamma = ntf::mu_gamma(beta);
+    u.eps = (float)o.eps;
+    NTF_CUDA(ntf::run_update(u, st));
     return NTF_OK;
 }
 
@@ -832,11 +803,16 @@ int cp_nway_mu_sweep(ntf_ctx *ctx, const ntf_tensor *X, float beta, int R, float
         const int v = w.view[n];
         const bool obj = n == 0 && objective_dev;
         if ((rc = launch_pass(ctx, s, a, mode_flag(v) | (obj ? ntf::PM_OBJ : 0), kl ? 0 : 1, st))) return rc;
-        if (obj) NTF_CUDA(ntf::reduce_objective(s.obj, s.plan.grid, 0.0, objective_dev, st));
         if (nway_single(w, v)) {
             ntf::UpdArgs u = upd_args(s, v, beta, o, kl, s.F[v], factors[n]);
+            if (obj) {  // the objective sum rides on the update (its own block)
+                u.obj_parts = s.obj;
+                u.obj_n = s.plan.grid;
+                u.obj_out = objective_dev;
+            }
             NTF_CUDA(ntf::mode_update(u, st));
         } else {
+            if (obj) NTF_CUDA(ntf::reduce_objective(s.obj, s.plan.grid, 0.0, objective_dev, st));
             const RunUpd q{w.P, w.P, w.P[n], w.P[n], factors[n], nullptr, nullptr, nullptr};
             if ((rc = nway_run_update(ctx, w, s, n, beta, o, kl, q, st))) return rc;
             NTF_CUDA(nway_merge(w, s, v, w.P, s.F[v], s.cs[v], st));

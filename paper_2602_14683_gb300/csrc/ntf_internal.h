@@ -236,9 +236,9 @@ struct ExtrapArgs {
 };
 cudaError_t extrapolate(const ExtrapArgs &x, cudaStream_t s);
 
-// Order N >= 4 on the 3-way kernels (leading modes 0..M-1 merged): Khatri-Rao factor of the
-// padded leading factors L (rows = prod dims[0..M-1]) with FP64 column-sum partials, and the fold
-// of a merged-mode contraction onto leading mode n.
+// Order N >= 4 on the 3-way kernels (runs of consecutive modes merged): Khatri-Rao factor of a
+// run's padded factors L (rows = prod of the run's dims, row-major) with FP64 column-sum partials,
+// and the update of a mode inside a run from the run's contraction.
 struct KrArgs {
     const float *L[8];
     int dims[8];
@@ -247,16 +247,26 @@ struct KrArgs {
     double *cs;   // column-sum partials [row block][RP] or null
 };
 cudaError_t kr_merge(const KrArgs &k, cudaStream_t s);
-struct FoldArgs {
-    const float *parts;  // [n_parts][rows][RP]
-    int n_parts;
-    const float *L[8];
+// Update of mode n inside a merged run, one launch: Num (and Den unless closed) folded from the
+// run's partials (parts summed in part order in FP32, the fold over the run's other indices in
+// FP64: CPContr^(n) over the merged index); at beta = 1 Den[r] =
+// prod over cf of the column sums (FP64); then out = max(pre * (Num / Den)^gamma, eps) with
+// optional chi1 / chi2 against ref and an unpadded copy into user.
+struct RunUpdArgs {
+    const float *pn, *pd;  // [n_parts][rows][RP]; pd null: closed form from cf
+    int n_parts, rows;
+    const float *Ln[8], *Ld[8];
     int dims[8];
-    int M, n, rows, R, RP;
-    float *out;          // [dims[n]][RP]
-    float *scratch;      // [rows][RP], the summed parts when n_parts > 1
+    int M, n;
+    const float *cf[8];
+    int cf_rows[8];
+    int ncf;
+    const float *pre, *ref;
+    float *out, *chi1, *chi2, *user;
+    int R, RP;
+    float beta, gamma, eps;
 };
-cudaError_t kr_fold(const FoldArgs &f, cudaStream_t s);
+cudaError_t run_update(const RunUpdArgs &u, cudaStream_t s);
 
 struct UpdArgs {
     MuEpiArgs e;

@@ -4,7 +4,7 @@ oracle, which runs the order-N contractions directly.
 Bars as for order 3: FP32 path 1e-5 per factor after one sweep / outer iteration (inner
 L = 1 and 3, beta in {1/2, 1, 3/2}) and on the objective, 1e-4 on a 10-sweep objective trajectory; TF32 tensor-core path 1e-3 per factor and
 2e-4 on the objective.  Shapes give ragged merged-row tiles, a leading mode of size 1, and
-orders 4 to 6.
+orders 4 to 8.
 """
 import numpy as np
 import pytest
@@ -26,6 +26,7 @@ CASES = [
     ((1, 5, 33, 24), 7, "fp32", 1e-5, 1e-5),
     ((4, 3, 5, 30, 20), 6, "fp32", 1e-5, 1e-5),
     ((2, 3, 2, 3, 16, 12), 5, "fp32", 1e-5, 1e-5),
+    ((2, 2, 3, 2, 2, 3, 8, 12), 4, "fp32", 1e-5, 1e-5),
     ((8, 9, 64, 48), 32, "tf32", 1e-3, 2e-4),
     ((6, 7, 40, 52), 10, "tf32", 1e-3, 2e-4),
 ]
@@ -36,7 +37,7 @@ MERGES = [((6, 7, 24, 20), (1, 2)), ((6, 7, 24, 20), (1, 3)), ((6, 7, 24, 20), (
 
 
 @pytest.mark.parametrize("dims,R,prec,tol,tol_obj", CASES)
-@pytest.mark.parametrize("beta", [0.5, 1.0, 1.5])
+@pytest.mark.parametrize("beta", [0.0, 0.5, 1.0, 1.5, 1.2])
 def test_nway_sweep_parity(dims, R, prec, tol, tol_obj, beta):
     ntf = _ntf()
     X, _ = synth.cp_dense(dims, R, seed=len(dims) + R, kind="gamma_noise")

@@ -580,6 +580,33 @@ __global__ void chi_kernel(const float *z, const float *zt, int64_t n, float bet
     c2[t] = chi2_f(beta, z[t], zt[t]);
 }
 
+// Column sums of a [rows][RP] matrix in two launches: CSB blocks each sum a strided set of row
+// groups (FP32 within a thread, FP64 across the block's groups), then one block adds the CSB
+// partials in block order.
+constexpr int CSB = 256;
+
+__global__ void colsum_part_kernel(const float *src, int64_t rows, int RP, double *part) {
+    __shared__ double sh[256];
+    const int G = blockDim.x / RP, t = threadIdx.x, r = t % RP, g = t / RP;
+    float s = 0.0f;
+    for (int64_t i = (int64_t)blockIdx.x * G + g; i < rows; i += (int64_t)gridDim.x * G) s += src[i * RP + r];
+    sh[t] = (double)s;
+    __syncthreads();
+    if (t < RP) {
+        double tot = 0.0;
+        for (int k = 0; k < G; ++k) tot += sh[k * RP + t];
+        part[(int64_t)blockIdx.x * RP + t] = tot;
+    }
+}
+
+__global__ void colsum_final_kernel(const double *part, int nb, int RP, float *out) {
+    const int t = threadIdx.x;
+    if (t >= RP) return;
+    double s = 0.0;
+    for (int b = 0; b < nb; ++b) s += part[(int64_t)b * RP + t];
+    out[t] = (float)s;
+}
+
 // out[p][row][c] = (p == 0 ? v[c] : 0) for p < parts, row < rows, c < RP
 __global__ void bcast_rows_kernel(const float *v, int64_t rows, int RP, int parts, float *out) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -630,6 +657,7 @@ struct TuckerWs {
     float *Wpn, *Wpd;
     int parts3, obj_n;
     float *cs;                // [RP] column sums (closed-form denominators at beta = 1)
+    double *cs_part;          // [CSB][RP] their partials
     Blocks cur, ref, t1, t2;  // current, reference, chi1 and chi2 transforms
 };
 
@@ -679,6 +707,14 @@ Cp3Args base_args(const ntf_tensor *X, const TuckerWs &w, const ntf_opts &o, flo
     return a;
 }
 
+int colsum_rows(ntf_ctx *ctx, TuckerWs &w, const float *src, int64_t rows, cudaStream_t st) {
+    colsum_part_kernel<<<CSB, 256, 0, st>>>(src, rows, w.RP, w.cs_part);
+    TK(cudaGetLastError());
+    colsum_final_kernel<<<1, 64, 0, st>>>(w.cs_part, CSB, w.RP, w.cs);
+    TK(cudaGetLastError());
+    return NTF_OK;
+}
+
 // W (and Wd) from P, Q with third-factor columns n3 / d3; Xhat from rrow, A3rec.
 int rows_pass(ntf_ctx *ctx, TuckerWs &w, const ntf_tensor *X, const ntf_opts &o, float beta, const float *rrow,
               const float *a3rec, const float *n3, const float *d3, bool obj, cudaStream_t st) {
@@ -691,22 +727,26 @@ int rows_pass(ntf_ctx *ctx, TuckerWs &w, const ntf_tensor *X, const ntf_opts &o,
         a.n_jt = w.tplan.n_jt;
         a.n_kb = w.tplan.n_kb;
         a.n_is = w.tplan.n_is;
-        a.p1n = w.Wpn;
-        a.p1d = w.Wpd;
+        // one column block: the pass writes W (and Wd) directly
+        const bool one = w.tplan.n_kb == 1;
+        a.p1n = one ? w.Wn : w.Wpn;
+        a.p1d = one ? w.Wd : w.Wpd;
         a.err = ctx_status(ctx);
         const bool kl = beta_kind(beta) == BK_KL;
         TK(cp3_tc_launch(w.tplan, a, PM_M1 | PM_M2 | (obj ? PM_OBJ : 0), kl ? 0 : 1, st));
         // W = sum over the column blocks, in block order
         const int64_t n = (int64_t)w.I1 * w.I2 * w.RP;
-        sum_parts_kernel<<<nblk(n), 256, 0, st>>>(w.Wpn, w.tplan.n_kb, n, w.Wn);
-        TK(cudaGetLastError());
+        if (!one) {
+            sum_parts_kernel<<<nblk(n), 256, 0, st>>>(w.Wpn, w.tplan.n_kb, n, w.Wn);
+            TK(cudaGetLastError());
+        }
         if (kl) {
             // Q = 1: Wd[i][j][c] = sum_k d3[k][c], the same for every row
-            const int rows3 = w.I3;
-            TK(colsum_prod(1, &d3, &rows3, w.RP, w.cs, st));
+            int rc = colsum_rows(ctx, w, d3, w.I3, st);
+            if (rc) return rc;
             bcast_rows_kernel<<<nblk(n), 256, 0, st>>>(w.cs, (int64_t)w.I1 * w.I2, w.RP, 1, w.Wd);
             TK(cudaGetLastError());
-        } else {
+        } else if (!one) {
             sum_parts_kernel<<<nblk(n), 256, 0, st>>>(w.Wpd, w.tplan.n_kb, n, w.Wd);
             TK(cudaGetLastError());
         }
@@ -821,6 +861,8 @@ int setup(ntf_ctx *ctx, const ntf_tensor *X, const int64_t *core_dims, bool jcom
     w.obj = (double *)ctx_ws(ctx, "tkObj", sizeof(double) * (size_t)gmax);
     if (!w.obj) ok = false;
     w.cs = wsf(ctx, "tkCs", 64, ok);
+    w.cs_part = (double *)ctx_ws(ctx, "tkCsPart", sizeof(double) * CSB * 64);
+    if (!w.cs_part) ok = false;
     const char *names[4][4] = {{"tkG", "tkA1", "tkA2", "tkA3"}, {"tkGt", "tkA1t", "tkA2t", "tkA3t"},
                                {"tkG1", "tkA11", "tkA21", "tkA31"}, {"tkG2", "tkA12", "tkA22", "tkA32"}};
     Blocks *bs[4] = {&w.cur, &w.ref, &w.t1, &w.t2};
@@ -884,8 +926,8 @@ int mode3_pass(ntf_ctx *ctx, TuckerWs &w, const ntf_tensor *X, const ntf_opts &o
         if (kl) {
             // Q = 1: Den3[k][c] = sum over the rows of drow, the same for every k (first part;
             // the other parts zero)
-            const int rows12 = w.I1 * w.I2;
-            TK(colsum_prod(1, &drow, &rows12, w.RP, w.cs, st));
+            int rc = colsum_rows(ctx, w, drow, (int64_t)w.I1 * w.I2, st);
+            if (rc) return rc;
             const int64_t n = (int64_t)w.parts3 * w.I3 * w.RP;
             bcast_rows_kernel<<<nblk(n), 256, 0, st>>>(w.cs, w.I3, w.RP, w.parts3, w.pd3);
             TK(cudaGetLastError());

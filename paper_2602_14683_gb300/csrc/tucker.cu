@@ -48,19 +48,25 @@ struct Gemm {
 constexpr int GK = 16;   // reduction chunk
 constexpr int GCARRY = 16;  // chunks summed in FP32 before the FP64 carry
 
-// Output tiles of TM x TN (64 x 64; 128 x 32 for outputs at most 32 columns wide, 256 x 16 for at
-// most 16); each of the 256 threads holds a 4 x 4 block of contiguous rows and columns, read from
-// the k-major shared tiles with one 16-byte load each.  Every output sums its k terms in
-// increasing k, so the tile shape does not change any result.
-template <int TM, int TN>
+// Output tiles of TM x TN for NBT batches at once (64 x 64; 128 x 32 for outputs at most 32
+// columns wide, 256 x 16 for at most 16; 64 x 16 for four batches of at most 64 x 16 outputs);
+// each of the 256 threads holds a 4 x 4 block of contiguous rows and columns of one batch, read
+// from the k-major shared tiles with one 16-byte load each.  Tile elements are fetched with
+// consecutive threads on the operand's unit-stride index (m or n when that stride is 1, else k),
+// and the next chunk's elements are prefetched into registers while this chunk computes.  Every
+// output sums its k terms in increasing k, so the tile shape does not change any result.
+template <int TM, int TN, int NBT>
 __global__ void __launch_bounds__(256) gemm2k_kernel(const Gemm g) {
-    static_assert(TM * TN == 4096, "256 threads x 16 outputs");
-    constexpr int CT = TN / 4;  // thread columns
-    __shared__ __align__(16) float As[GK][TM];
-    __shared__ __align__(16) float Bs[GK][TN];
-    const int bt = blockIdx.z % g.batch, sp = blockIdx.z / g.batch;
+    static_assert(TM * TN * NBT == 4096, "256 threads x 16 outputs");
+    constexpr int CT = TN / 4, TPB = 256 / NBT;  // thread columns, threads per batch
+    constexpr int LA = TM + 4, LB = TN + 4;       // padded rows (16-byte aligned)
+    __shared__ __align__(16) float As[NBT][GK][LA];
+    __shared__ __align__(16) float Bs[NBT][GK][LB];
+    const int nbg = (g.batch + NBT - 1) / NBT;
+    const int bg = blockIdx.z % nbg, sp = blockIdx.z / nbg;
     const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
-    const int tid = threadIdx.x, tm = tid / CT, tn = tid % CT;
+    const int tid = threadIdx.x, bs = tid / TPB, tl = tid % TPB, tm = tl / CT, tn = tl % CT;
+    const int bt = bg * NBT + bs;  // this thread's batch (outputs only when < batch)
     const int K = g.K1 * g.K2;
     const int kbeg = sp * g.kchunks * GK, kend = min(K, kbeg + g.kchunks * GK);
     const bool carry = (kend - kbeg + GK - 1) / GK > GCARRY;  // more than one FP32 block
@@ -70,8 +76,6 @@ __global__ void __launch_bounds__(256) gemm2k_kernel(const Gemm g) {
     for (int x = 0; x < 4; ++x)
 #pragma unroll
         for (int y = 0; y < 4; ++y) acc[x][y] = 0.0f, tot[x][y] = 0.0;
-    const float *A = g.A + bt * g.sab;
-    const float *B = g.B + bt * g.sbb;
     // (k1, k2) of k = k0 + kk from k0's quotient and remainder (one division per chunk)
     auto split = [&](int q0, int r0, int kk, int &k1, int &k2) {
         if (g.K2 == 1) {
@@ -91,30 +95,47 @@ __global__ void __launch_bounds__(256) gemm2k_kernel(const Gemm g) {
             }
         }
     };
-    // the next chunk's tile elements are loaded into registers while this chunk computes
-    constexpr int NA = GK * TM / 256, NB = GK * TN / 256;
+    const bool a_mfast = g.sam == 1, b_nfast = g.sbn == 1;
+    constexpr int NA = NBT * GK * TM / 256, NB = NBT * GK * TN / 256;
     float ra[NA], rb[NB];
+    // element e of this thread: batch slot, k offset and m (or n) offset within the tile
+    auto a_idx = [&](int e, int &sb, int &kk, int &mm) {
+        const int t = tid + 256 * e;
+        sb = t / (GK * TM);
+        const int u = t % (GK * TM);
+        if (a_mfast) { kk = u / TM; mm = u % TM; } else { mm = u / GK; kk = u % GK; }
+    };
+    auto b_idx = [&](int e, int &sb, int &kk, int &nn) {
+        const int t = tid + 256 * e;
+        sb = t / (GK * TN);
+        const int u = t % (GK * TN);
+        if (b_nfast) { kk = u / TN; nn = u % TN; } else { nn = u / GK; kk = u % GK; }
+    };
     auto load = [&](int k0) {
         const int q0 = k0 / g.K2, r0 = k0 - q0 * g.K2;
 #pragma unroll
         for (int e = 0; e < NA; ++e) {
-            const int t = tid + 256 * e, kk = t / TM, mm = t % TM, k = k0 + kk;
+            int sb, kk, mm;
+            a_idx(e, sb, kk, mm);
+            const int k = k0 + kk, b = bg * NBT + sb;
             float va = 0.0f;
-            if (k < kend && m0 + mm < g.M) {
+            if (k < kend && m0 + mm < g.M && b < g.batch) {
                 int k1, k2;
                 split(q0, r0, kk, k1, k2);
-                va = A[(m0 + mm) * g.sam + k1 * g.sak1 + k2 * g.sak2];
+                va = g.A[b * g.sab + (m0 + mm) * g.sam + k1 * g.sak1 + k2 * g.sak2];
             }
             ra[e] = va;
         }
 #pragma unroll
         for (int e = 0; e < NB; ++e) {
-            const int t = tid + 256 * e, kk = t / TN, nn = t % TN, k = k0 + kk;
+            int sb, kk, nn;
+            b_idx(e, sb, kk, nn);
+            const int k = k0 + kk, b = bg * NBT + sb;
             float vb = 0.0f;
-            if (k < kend && n0 + nn < g.N) {
+            if (k < kend && n0 + nn < g.N && b < g.batch) {
                 int k1, k2;
                 split(q0, r0, kk, k1, k2);
-                vb = B[k1 * g.sbk1 + k2 * g.sbk2 + (n0 + nn) * g.sbn];
+                vb = g.B[b * g.sbb + k1 * g.sbk1 + k2 * g.sbk2 + (n0 + nn) * g.sbn];
             }
             rb[e] = vb;
         }
@@ -124,20 +145,22 @@ __global__ void __launch_bounds__(256) gemm2k_kernel(const Gemm g) {
     for (int k0 = kbeg; k0 < kend; k0 += GK) {
 #pragma unroll
         for (int e = 0; e < NA; ++e) {
-            const int t = tid + 256 * e;
-            As[t / TM][t % TM] = ra[e];
+            int sb, kk, mm;
+            a_idx(e, sb, kk, mm);
+            As[sb][kk][mm] = ra[e];
         }
 #pragma unroll
         for (int e = 0; e < NB; ++e) {
-            const int t = tid + 256 * e;
-            Bs[t / TN][t % TN] = rb[e];
+            int sb, kk, nn;
+            b_idx(e, sb, kk, nn);
+            Bs[sb][kk][nn] = rb[e];
         }
         __syncthreads();
         if (k0 + GK < kend) load(k0 + GK);
 #pragma unroll
         for (int kk = 0; kk < GK; ++kk) {
-            const float4 av = *reinterpret_cast<const float4 *>(&As[kk][4 * tm]);
-            const float4 bv = *reinterpret_cast<const float4 *>(&Bs[kk][4 * tn]);
+            const float4 av = *reinterpret_cast<const float4 *>(&As[bs][kk][4 * tm]);
+            const float4 bv = *reinterpret_cast<const float4 *>(&Bs[bs][kk][4 * tn]);
             const float a[4] = {av.x, av.y, av.z, av.w}, b[4] = {bv.x, bv.y, bv.z, bv.w};
 #pragma unroll
             for (int x = 0; x < 4; ++x)
@@ -153,6 +176,7 @@ __global__ void __launch_bounds__(256) gemm2k_kernel(const Gemm g) {
                 for (int y = 0; y < 4; ++y) tot[x][y] += (double)acc[x][y], acc[x][y] = 0.0f;
         }
     }
+    if (bt >= g.batch) return;
     // outputs: four consecutive columns as one 16-byte store where the layout allows
     const int nb = n0 + 4 * tn;
     const bool vec = nb + 3 < g.N &&
@@ -192,8 +216,12 @@ __global__ void gemm_split_sum_kernel(const Gemm g) {
 // Splits the reduction when the output tiles alone would leave most SMs idle: about two
 // CTAs per SM, at least four GK-chunks per range.
 static int gemm(ntf_ctx *ctx, Gemm g, cudaStream_t s) {
-    const int TN = g.N <= 16 ? 16 : g.N <= 32 ? 32 : 64, TM = 4096 / TN;
-    const int tiles = ((g.N + TN - 1) / TN) * ((g.M + TM - 1) / TM) * g.batch;
+    // tile shape: four batches per CTA for outputs of at most 64 x 16, else by output width
+    const bool multi = g.M <= 64 && g.N <= 16 && g.batch >= 4;
+    const int NBT = multi ? 4 : 1;
+    const int TN = multi ? 16 : g.N <= 16 ? 16 : g.N <= 32 ? 32 : 64, TM = 4096 / (TN * NBT);
+    const int nbg = (g.batch + NBT - 1) / NBT;
+    const int tiles = ((g.N + TN - 1) / TN) * ((g.M + TM - 1) / TM) * nbg;
     const int nchunks = (g.K1 * g.K2 + GK - 1) / GK;
     int splits = (2 * ctx_num_sms(ctx) + tiles - 1) / tiles;
     splits = std::max(1, std::min(splits, nchunks / 4));
@@ -203,13 +231,15 @@ static int gemm(ntf_ctx *ctx, Gemm g, cudaStream_t s) {
         g.part = (float *)ctx_ws(ctx, "gemm_split", sizeof(float) * (size_t)g.splits * g.batch * g.M * g.N);
         if (!g.part) return ctx_fail(ctx, NTF_ERR_OOM, "workspace allocation failed");
     }
-    dim3 grid((g.N + TN - 1) / TN, (g.M + TM - 1) / TM, g.batch * g.splits);
-    if (TN == 16)
-        gemm2k_kernel<256, 16><<<grid, 256, 0, s>>>(g);
+    dim3 grid((g.N + TN - 1) / TN, (g.M + TM - 1) / TM, nbg * g.splits);
+    if (multi)
+        gemm2k_kernel<64, 16, 4><<<grid, 256, 0, s>>>(g);
+    else if (TN == 16)
+        gemm2k_kernel<256, 16, 1><<<grid, 256, 0, s>>>(g);
     else if (TN == 32)
-        gemm2k_kernel<128, 32><<<grid, 256, 0, s>>>(g);
+        gemm2k_kernel<128, 32, 1><<<grid, 256, 0, s>>>(g);
     else
-        gemm2k_kernel<64, 64><<<grid, 256, 0, s>>>(g);
+        gemm2k_kernel<64, 64, 1><<<grid, 256, 0, s>>>(g);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess && g.splits > 1) {
         const int64_t total = (int64_t)g.M * g.N * g.batch;

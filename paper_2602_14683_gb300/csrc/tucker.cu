@@ -612,7 +612,7 @@ __global__ void chi_kernel(const float *z, const float *zt, int64_t n, float bet
 
 // Column sums of a [rows][RP] matrix in two launches: CSB blocks each sum a strided set of row
 // groups (FP32 within a thread, FP64 across the block's groups), then one block adds the CSB
-// partials in block order.
+// partials (lane groups striding the blocks, the groups added in order).
 constexpr int CSB = 256;
 
 __global__ void colsum_part_kernel(const float *src, int64_t rows, int RP, double *part) {
@@ -630,11 +630,17 @@ __global__ void colsum_part_kernel(const float *src, int64_t rows, int RP, doubl
 }
 
 __global__ void colsum_final_kernel(const double *part, int nb, int RP, float *out) {
-    const int t = threadIdx.x;
-    if (t >= RP) return;
+    __shared__ double sh[256];
+    const int G = blockDim.x / RP, t = threadIdx.x, r = t % RP, g = t / RP;
     double s = 0.0;
-    for (int b = 0; b < nb; ++b) s += part[(int64_t)b * RP + t];
-    out[t] = (float)s;
+    for (int b = g; b < nb; b += G) s += part[(int64_t)b * RP + r];
+    sh[t] = s;
+    __syncthreads();
+    if (t < RP) {
+        double tot = 0.0;
+        for (int k = 0; k < G; ++k) tot += sh[k * RP + t];
+        out[t] = (float)tot;
+    }
 }
 
 // out[p][row][c] = (p == 0 ? v[c] : 0) for p < parts, row < rows, c < RP
@@ -740,7 +746,7 @@ Cp3Args base_args(const ntf_tensor *X, const TuckerWs &w, const ntf_opts &o, flo
 int colsum_rows(ntf_ctx *ctx, TuckerWs &w, const float *src, int64_t rows, cudaStream_t st) {
     colsum_part_kernel<<<CSB, 256, 0, st>>>(src, rows, w.RP, w.cs_part);
     TK(cudaGetLastError());
-    colsum_final_kernel<<<1, 64, 0, st>>>(w.cs_part, CSB, w.RP, w.cs);
+    colsum_final_kernel<<<1, 256, 0, st>>>(w.cs_part, CSB, w.RP, w.cs);
     TK(cudaGetLastError());
     return NTF_OK;
 }

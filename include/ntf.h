@@ -24,8 +24,10 @@
  *     message for the last error on that context; it stays valid until the next call.
  *   - beta must lie in [0, 2) (the range of Remark "Exponent gamma(beta)"), else
  *     NTF_ERR_BETA.  Ranks and core dimensions must lie in 1..64, else
- *     NTF_ERR_UNSUPPORTED.  Dense kernels accept order N = 3 (other orders return
- *     NTF_ERR_UNSUPPORTED); COO accepts 2 <= N <= 8.
+ *     NTF_ERR_UNSUPPORTED.  Dense kernels accept orders 3 <= N <= 8 (the extrapolated entries
+ *     and the server order 3 only; other orders return NTF_ERR_UNSUPPORTED); COO accepts
+ *     2 <= N <= 8.  Order N >= 4 runs on the 3-way passes with the modes cut into three runs
+ *     of consecutive modes (ntf_opts.merge), the same memory read as a 3-way tensor.
  *   - Data must be nonnegative and finite; factors and core must be >= eps on entry
  *     (Assumption "Positivity safeguard").  These are preconditions, not checked on the
  *     device.  At beta = 0 the data are floored at eps_x (Remark "The case beta = 0").
@@ -88,11 +90,14 @@ typedef struct {
                       sets the order of the partial sums, so results may differ from a run with
                       another table in the last bits.  Ignored (cost-model plan, nothing cached)
                       while the stream is being captured. */
-    int merge;     /* dense CP of order N >= 4, which runs on the 3-way passes with the modes cut
-                      into three runs of consecutive modes [0, a), [a, b), [b, N) (a run of
-                      several modes is one 3-way mode whose factor is the Khatri-Rao product of
-                      the run's blocks): 0 = the library picks the cut (0); else 16 * a + b,
-                      1 <= a < b <= N - 1 (NTF_ERR_ARG otherwise).  Ignored at N = 3. */
+    int merge;     /* dense CP and Tucker of order N >= 4, which run on the 3-way passes with the
+                      modes cut into three runs of consecutive modes [0, a), [a, b), [b, N) (a run
+                      of several modes is one 3-way mode whose factor is the Khatri-Rao product
+                      (CP) or Kronecker product (Tucker) of the run's blocks): 0 = the library
+                      picks the cut (0); else 16 * a + b, 1 <= a < b <= N - 1 (NTF_ERR_ARG
+                      otherwise; Tucker: NTF_ERR_UNSUPPORTED when the last run's core extent
+                      exceeds 64).  Ignored at N = 3.  Results depend on the cut only through
+                      the order of floating-point sums. */
 } ntf_opts;
 
 /* Fills *o with the defaults shown above. */
@@ -129,7 +134,7 @@ int ntf_device_status(ntf_ctx *ctx, void *stream);
  *   factors:       host array of N device pointers, A^(n) is I_n x rank, updated in place
  *   objective_dev: device double or NULL; receives D_beta(X, Xhat) of the INCOMING
  *                  iterate (before this sweep).
- * Dense (N = 3) and COO (beta = 1 only, else NTF_ERR_UNSUPPORTED) tensors. */
+ * Dense (N = 3..8) and COO (beta = 1 only, else NTF_ERR_UNSUPPORTED) tensors. */
 int ntf_cp_mu_sweep(ntf_ctx *ctx, const ntf_tensor *X, float beta, int rank,
                     float *const *factors, const ntf_opts *opts, double *objective_dev,
                     void *stream);
@@ -178,7 +183,7 @@ int ntf_cp_jcomm_outer_extrap(ntf_ctx *ctx, const ntf_tensor *X, float beta, int
  *   core_dims: host array [N] of J_n; core: device J_1 x ... x J_N, updated in place
  *   factors:   host array of N device pointers, A^(n) is I_n x J_n, updated in place
  *   objective_dev: device double or NULL; D_beta of the incoming iterate.
- * Dense N = 3 only. */
+ * Dense N = 3..8 (N >= 4: the last run of the cut needs a core extent <= 64). */
 int ntf_tucker_mu_sweep(ntf_ctx *ctx, const ntf_tensor *X, float beta, const int64_t *core_dims,
                         float *core, float *const *factors, const ntf_opts *opts,
                         double *objective_dev, void *stream);
@@ -208,7 +213,7 @@ int ntf_tucker_mu_sweep_extrap(ntf_ctx *ctx, const ntf_tensor *X, float beta, co
  * reference factors inside each pass (never stored).
  *   model: NTF_CP (rank_or_0 = R, core arguments NULL) or NTF_TUCKER (rank_or_0 = 0)
  *   objective_ref_dev: device double or NULL; receives D_beta at the reference.
- * CP dense N = 3 (any beta), CP COO (beta = 1), Tucker dense N = 3 (any beta). */
+ * CP dense N = 3..8 (any beta), CP COO (beta = 1), Tucker dense N = 3..8 (any beta). */
 int ntf_jcomm_outer(ntf_ctx *ctx, int model, const ntf_tensor *X, float beta, int rank_or_0,
                     const int64_t *core_dims_or_null, float *core_or_null, float *const *factors,
                     const ntf_opts *opts, double *objective_ref_dev, void *stream);

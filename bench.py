@@ -518,6 +518,24 @@ def run_reference(args):
     return 0
 
 
+# ----------------------------------------------------------------- replicas (N > 1)
+def max_over_ranks(x, world, device):
+    """The largest of every rank's x (one all-reduce; x itself at world = 1).  Every rank
+    solves its own replica, so the job's time is the slowest rank's."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(steps, world, seconds_max):
+    """Whole-job throughput: the steps of all ranks over the slowest rank's time."""
+    return world * steps / seconds_max
+
+
 # ------------------------------------------------------------------------ GPU arm
 def main():
     args = parse()
@@ -574,13 +592,6 @@ def main():
         if world > 1:
             dist.barrier()
 
-    def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
     def timed(fn, steps, warmup):
         for _ in range(warmup):
             fn()
@@ -594,7 +605,7 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
-        return max_over_ranks(e0.elapsed_time(e1) / 1e3)
+        return max_over_ranks(e0.elapsed_time(e1) / 1e3, world, dev)
 
     # ---------------- headline: J-CoMM outer iterations, inputs resident in HBM -------------
     A = [a.clone() for a in A0]
@@ -624,7 +635,7 @@ def main():
         ntf.cp_mu_sweep(X, BETA, B, objective=obj, ctx=ctx, precision=prec, autotune=True)
 
     t_b = timed(bstep, max(5, args.steps // 2), args.warmup)
-    b_rate = world * max(5, args.steps // 2) / t_b
+    b_rate = job_rate(max(5, args.steps // 2), world, t_b)
 
     # ---------------- end to end: host buffers, copies inside the timed region -------------
     Xh = torch.empty(X.shape, dtype=torch.float32).pin_memory()
@@ -773,7 +784,7 @@ def main():
     if args.serve_jobs > 0:
         serving = run_serving(ntf, args.serve_jobs, args.slots)
 
-    value = world * args.steps / t_j
+    value = job_rate(args.steps, world, t_j)
     line = {
         "metric": METRIC, "value": value, "unit": "sweeps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_j / args.steps * 1e3, "higher_is_better": True,
@@ -786,7 +797,7 @@ def main():
         "other_configs": other,
         "roofline": roof,
         "cpu_baseline": cpu,
-        "e2e": {"value": world * e_steps / t_e, "unit": "sweeps/s", "h2d_bytes_per_step": h2d,
+        "e2e": {"value": job_rate(e_steps, world, t_e), "unit": "sweeps/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "clocks": clk,

@@ -49,12 +49,14 @@ constexpr int GK = 16;   // reduction chunk
 constexpr int GCARRY = 16;  // chunks summed in FP32 before the FP64 carry
 
 // Output tiles of TM x TN for NBT batches at once (64 x 64; 128 x 32 for outputs at most 32
-// columns wide, 256 x 16 for at most 16; 64 x 16 for four batches of at most 64 x 16 outputs);
+// columns wide, 256 x 16 for at most 16, 512 x 8 for at most 8; 64 x 16 or 128 x 8 for four
+// batches of at most that many outputs);
 // each of the 256 threads holds a 4 x 4 block of contiguous rows and columns of one batch, read
 // from the k-major shared tiles with one 16-byte load each.  Tile elements are fetched with
 // consecutive threads on the operand's unit-stride index (m or n when that stride is 1, else k),
-// and the next chunk's elements are prefetched into registers while this chunk computes.  Every
-// output sums its k terms in increasing k, so the tile shape does not change any result.
+// and the next chunk's elements are prefetched into registers while this chunk computes.  Within a
+// reduction range every output sums its k terms in increasing k; the number of ranges follows the
+// tile count (gemm()), so a change of tile shape can move results in the last bits.
 template <int TM, int TN, int NBT>
 __global__ void __launch_bounds__(256) gemm2k_kernel(const Gemm g) {
     static_assert(TM * TN * NBT == 4096, "256 threads x 16 outputs");
@@ -96,7 +98,8 @@ __global__ void __launch_bounds__(256) gemm2k_kernel(const Gemm g) {
         }
     };
     const bool a_mfast = g.sam == 1, b_nfast = g.sbn == 1;
-    constexpr int NA = NBT * GK * TM / 256, NB = NBT * GK * TN / 256;
+    constexpr int TOTA = NBT * GK * TM, TOTB = NBT * GK * TN;  // tile elements
+    constexpr int NA = (TOTA + 255) / 256, NB = (TOTB + 255) / 256;
     float ra[NA], rb[NB];
     // element e of this thread: batch slot, k offset and m (or n) offset within the tile
     auto a_idx = [&](int e, int &sb, int &kk, int &mm) {
@@ -119,7 +122,7 @@ __global__ void __launch_bounds__(256) gemm2k_kernel(const Gemm g) {
             a_idx(e, sb, kk, mm);
             const int k = k0 + kk, b = bg * NBT + sb;
             float va = 0.0f;
-            if (k < kend && m0 + mm < g.M && b < g.batch) {
+            if (tid + 256 * e < TOTA && k < kend && m0 + mm < g.M && b < g.batch) {
                 int k1, k2;
                 split(q0, r0, kk, k1, k2);
                 va = g.A[b * g.sab + (m0 + mm) * g.sam + k1 * g.sak1 + k2 * g.sak2];
@@ -132,7 +135,7 @@ __global__ void __launch_bounds__(256) gemm2k_kernel(const Gemm g) {
             b_idx(e, sb, kk, nn);
             const int k = k0 + kk, b = bg * NBT + sb;
             float vb = 0.0f;
-            if (k < kend && n0 + nn < g.N && b < g.batch) {
+            if (tid + 256 * e < TOTB && k < kend && n0 + nn < g.N && b < g.batch) {
                 int k1, k2;
                 split(q0, r0, kk, k1, k2);
                 vb = g.B[b * g.sbb + k1 * g.sbk1 + k2 * g.sbk2 + (n0 + nn) * g.sbn];
@@ -147,13 +150,13 @@ __global__ void __launch_bounds__(256) gemm2k_kernel(const Gemm g) {
         for (int e = 0; e < NA; ++e) {
             int sb, kk, mm;
             a_idx(e, sb, kk, mm);
-            As[sb][kk][mm] = ra[e];
+            if (tid + 256 * e < TOTA) As[sb][kk][mm] = ra[e];
         }
 #pragma unroll
         for (int e = 0; e < NB; ++e) {
             int sb, kk, nn;
             b_idx(e, sb, kk, nn);
-            Bs[sb][kk][nn] = rb[e];
+            if (tid + 256 * e < TOTB) Bs[sb][kk][nn] = rb[e];
         }
         __syncthreads();
         if (k0 + GK < kend) load(k0 + GK);
@@ -216,10 +219,10 @@ __global__ void gemm_split_sum_kernel(const Gemm g) {
 // Splits the reduction when the output tiles alone would leave most SMs idle: about two
 // CTAs per SM, at least four GK-chunks per range.
 static int gemm(ntf_ctx *ctx, Gemm g, cudaStream_t s) {
-    // tile shape: four batches per CTA for outputs of at most 64 x 16, else by output width
-    const bool multi = g.M <= 64 && g.N <= 16 && g.batch >= 4;
+    // tile shape: four batches per CTA for outputs of at most 64 x 16 or 128 x 8, else by width
+    const bool multi = g.batch >= 4 && ((g.M <= 64 && g.N <= 16) || (g.M <= 128 && g.N <= 8));
     const int NBT = multi ? 4 : 1;
-    const int TN = multi ? 16 : g.N <= 16 ? 16 : g.N <= 32 ? 32 : 64, TM = 4096 / (TN * NBT);
+    const int TN = g.N <= 8 ? 8 : g.N <= 16 ? 16 : g.N <= 32 ? 32 : 64, TM = 4096 / (TN * NBT);
     const int nbg = (g.batch + NBT - 1) / NBT;
     const int tiles = ((g.N + TN - 1) / TN) * ((g.M + TM - 1) / TM) * nbg;
     const int nchunks = (g.K1 * g.K2 + GK - 1) / GK;
@@ -232,8 +235,12 @@ static int gemm(ntf_ctx *ctx, Gemm g, cudaStream_t s) {
         if (!g.part) return ctx_fail(ctx, NTF_ERR_OOM, "workspace allocation failed");
     }
     dim3 grid((g.N + TN - 1) / TN, (g.M + TM - 1) / TM, nbg * g.splits);
-    if (multi)
+    if (multi && TN == 8)
+        gemm2k_kernel<128, 8, 4><<<grid, 256, 0, s>>>(g);
+    else if (multi)
         gemm2k_kernel<64, 16, 4><<<grid, 256, 0, s>>>(g);
+    else if (TN == 8)
+        gemm2k_kernel<512, 8, 1><<<grid, 256, 0, s>>>(g);
     else if (TN == 16)
         gemm2k_kernel<256, 16, 1><<<grid, 256, 0, s>>>(g);
     else if (TN == 32)

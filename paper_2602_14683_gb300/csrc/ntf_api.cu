@@ -609,19 +609,24 @@ bool nway_single(const NWay &w, int v) { return w.ge[v] - w.gb[v] == 1; }
 // least, tensor-core eligibility (rank <= 32, last run's extent a multiple of 4) weighing 8x.
 int nway_split(ntf_ctx *ctx, const ntf_tensor *X, int R, const ntf_opts &o, int precision, int &a, int &b) {
     const int N = X->order;
+    auto extents = [&](int ca, int cb, double *e) {  // the runs' extents; false past 32 bits
+        e[0] = e[1] = e[2] = 1.0;
+        for (int m = 0; m < N; ++m) e[m < ca ? 0 : m < cb ? 1 : 2] *= (double)X->dims[m];
+        return e[0] <= 2147483647.0 && e[1] <= 2147483647.0 && e[2] <= 2147483647.0;
+    };
+    double e[3];
     if (o.merge) {
         a = o.merge / 16;
         b = o.merge % 16;
         if (!(1 <= a && a < b && b <= N - 1))
             return fail(ctx, NTF_ERR_ARG, "merge %d does not split %d modes into three runs", o.merge, N);
+        if (!extents(a, b, e)) return fail(ctx, NTF_ERR_SHAPE, "a run of the requested cut exceeds 32-bit extents");
         return NTF_OK;
     }
     double best = -1.0;
     for (int ca = 1; ca <= N - 2; ++ca)
         for (int cb = ca + 1; cb <= N - 1; ++cb) {
-            double e[3] = {1.0, 1.0, 1.0};
-            for (int m = 0; m < N; ++m) e[m < ca ? 0 : m < cb ? 1 : 2] *= (double)X->dims[m];
-            if (e[0] > 2147483647.0 || e[1] > 2147483647.0 || e[2] > 2147483647.0) continue;
+            if (!extents(ca, cb, e)) continue;
             const bool tc = precision != NTF_PREC_FP32 && R <= 32 &&
                             ntf::cp3_tc_eligible(32, (int)e[2], X->values);
             const double kb = tc ? 128.0 : 64.0;

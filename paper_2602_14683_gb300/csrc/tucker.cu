@@ -49,8 +49,8 @@ constexpr int GK = 16;   // reduction chunk
 constexpr int GCARRY = 16;  // chunks summed in FP32 before the FP64 carry
 
 // Output tiles of TM x TN for NBT batches at once (64 x 64; 128 x 32 for outputs at most 32
-// columns wide, 256 x 16 for at most 16, 512 x 8 for at most 8; 64 x 16 or 128 x 8 for four
-// batches of at most that many outputs);
+// columns wide, 256 x 16 for at most 16, 512 x 8 for at most 8; 32 x 32, 64 x 16 or 128 x 8 for
+// four batches of at most that many outputs);
 // each of the 256 threads holds a 4 x 4 block of contiguous rows and columns of one batch, read
 // from the k-major shared tiles with one 16-byte load each.  Tile elements are fetched with
 // consecutive threads on the operand's unit-stride index (m or n when that stride is 1, else k),
@@ -219,8 +219,10 @@ __global__ void gemm_split_sum_kernel(const Gemm g) {
 // Splits the reduction when the output tiles alone would leave most SMs idle: about two
 // CTAs per SM, at least four GK-chunks per range.
 static int gemm(ntf_ctx *ctx, Gemm g, cudaStream_t s) {
-    // tile shape: four batches per CTA for outputs of at most 64 x 16 or 128 x 8, else by width
-    const bool multi = g.batch >= 4 && ((g.M <= 64 && g.N <= 16) || (g.M <= 128 && g.N <= 8));
+    // tile shape: four batches per CTA for outputs of at most 32 x 32, 64 x 16 or 128 x 8, else by
+    // width
+    const bool multi = g.batch >= 4 && ((g.M <= 32 && g.N <= 32) || (g.M <= 64 && g.N <= 16) ||
+                                        (g.M <= 128 && g.N <= 8));
     const int NBT = multi ? 4 : 1;
     const int TN = g.N <= 8 ? 8 : g.N <= 16 ? 16 : g.N <= 32 ? 32 : 64, TM = 4096 / (TN * NBT);
     const int nbg = (g.batch + NBT - 1) / NBT;
@@ -237,8 +239,10 @@ static int gemm(ntf_ctx *ctx, Gemm g, cudaStream_t s) {
     dim3 grid((g.N + TN - 1) / TN, (g.M + TM - 1) / TM, nbg * g.splits);
     if (multi && TN == 8)
         gemm2k_kernel<128, 8, 4><<<grid, 256, 0, s>>>(g);
-    else if (multi)
+    else if (multi && TN == 16)
         gemm2k_kernel<64, 16, 4><<<grid, 256, 0, s>>>(g);
+    else if (multi)
+        gemm2k_kernel<32, 32, 4><<<grid, 256, 0, s>>>(g);
     else if (TN == 8)
         gemm2k_kernel<512, 8, 1><<<grid, 256, 0, s>>>(g);
     else if (TN == 16)

@@ -703,7 +703,8 @@ cudaError_t nway_merge(const NWay &w, const CpDense &s, int v, float *const *B, 
 // Padded working blocks from the user's factors: the 3-way slots of single-mode runs in one
 // prep launch (with reference / chi copies and column sums), the merged runs' own buffers, then
 // the merged slots (reference slot for J-CoMM, chi slots equal to it at the start).
-int nway_init(ntf_ctx *ctx, NWay &w, CpDense &s, float *const *factors, bool ref, bool chi, cudaStream_t st) {
+int nway_init(ntf_ctx *ctx, NWay &w, CpDense &s, const float *const *factors, bool ref, bool chi,
+              cudaStream_t st) {
     ntf::PrepArgs p{};
     for (int v = 0; v < 3; ++v) {
         if (!nway_single(w, v)) continue;  // rows 0: no blocks for this slot
@@ -889,7 +890,7 @@ int cp_nway_beta_div(ntf_ctx *ctx, const ntf_tensor *X, float beta, int R, const
     NWay w{};
     int rc = nway_setup(ctx, X, R, false, false, NTF_PREC_FP32, o, s, w);
     if (rc) return rc;
-    if ((rc = nway_init(ctx, w, s, const_cast<float *const *>(factors), false, false, st))) return rc;
+    if ((rc = nway_init(ctx, w, s, factors, false, false, st))) return rc;
     ntf::Cp3Args a = cp_args(&w.X3, s, o, beta);
     for (int m = 0; m < 3; ++m) a.rec[m] = a.num[m] = a.den[m] = s.F[m];
     {

@@ -61,8 +61,8 @@ def parse():
 
 
 # DRAM bytes (read + write) per tensor entry of the timed tensor-core pass (all numerators +
-# objective, TF32 reconstruction, 256-column blocks), from the ncu capture at 512^3 summarised
-# in profiles/cp3_pass_tc_cp512_r32_beta1_tf32.md; valid only for the kernel sources it was
+# objective, TF32 reconstruction, 256-column blocks), from the ncu capture of that instantiation on
+# the 512^3 tensor (its summary is kept under profiles/); valid only for the kernel sources it was
 # taken on
 TC_CAPTURE = {
     "sources": {"paper_2602_14683_gb300/csrc/cp3_tc.cuh": "7e8d2981dc4e3a8d4628bf64e6737c73b183d6c13195412fa598e7bb8293442b",

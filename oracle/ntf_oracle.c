@@ -13,7 +13,7 @@
  * algorithms state them; no blocking, fusion or reordering is applied beyond the one
  * parallel loop over independent output rows that some functions carry.
  *
- * Readings where the paper is silent (also listed in the design doc):
+ * Readings where the paper is silent:
  *   - eps (parameter floor) and the clip max(Xhat, eps) inside the powers are caller
  *     arguments; the objective uses the same clipped reconstruction.
  *   - eps_x: at beta = 0 the data are floored, X <- max(X, eps_x) (Remark "The case

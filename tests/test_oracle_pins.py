@@ -709,3 +709,43 @@ def test_tucker_order4_matches_brute_force_and_fixed_points(beta):
         np.testing.assert_allclose(G1, G, rtol=1e-10)
         for a, b in zip(A1, A):
             np.testing.assert_allclose(a, b, rtol=1e-10)
+
+
+@pytest.mark.parametrize("beta", [0.5, 1.0, 1.5])
+def test_order5_cp_and_tucker_contractions_brute_force(beta):
+    """Order 5 (the highest order the parity tests use with several merged runs): the CP and
+    Tucker Num/Den of a middle and the last mode equal brute-force einsum sums of the definitions,
+    and a J-CoMM outer iteration keeps exact data fixed."""
+    g = np.random.default_rng(43)
+    dims = (3, 2, 4, 2, 3)
+    subs = "ijklm"
+    X = g.gamma(3.0, 1.0, size=dims) + 0.05
+    R = 2
+    A = [g.uniform(0.2, 1.0, size=(d, R)) for d in dims]
+    Xh = np.einsum("ir,jr,kr,lr,mr->ijklm", *A)
+    P, Q = X * Xh ** (beta - 2.0), Xh ** (beta - 1.0)
+    for n in (2, 4):
+        others = [m for m in range(5) if m != n]
+        spec = subs + "," + ",".join(subs[m] + "r" for m in others) + "->" + subs[n] + "r"
+        _, num, den = oracle.cp_block_update(X, A, n, beta)
+        np.testing.assert_allclose(num, np.einsum(spec, P, *[A[m] for m in others]), rtol=1e-12)
+        np.testing.assert_allclose(den, np.einsum(spec, Q, *[A[m] for m in others]), rtol=1e-12)
+    J = (2, 2, 2, 2, 2)
+    G = g.uniform(0.3, 1.0, size=J)
+    B = [g.uniform(0.2, 1.0, size=(d, j)) for d, j in zip(dims, J)]
+    Th = np.einsum("abcde,ia,jb,kc,ld,me->ijklm", G, *B)
+    PT = X * Th ** (beta - 2.0)
+    csubs = "abcde"
+    for n in (1, 3):
+        spec = (subs + "," + csubs + "," + ",".join(subs[m] + csubs[m] for m in range(5) if m != n)
+                + "->" + subs[n] + csubs[n])
+        want = np.einsum(spec, PT, G, *[B[m] for m in range(5) if m != n])
+        np.testing.assert_allclose(oracle.tucker_factor_contr(PT, G, B, n), want, rtol=1e-12)
+    Xe = oracle.cp_full(dims, A)
+    for a, b in zip(oracle.cp_jcomm_outer(Xe, A, beta, L=2)[0], A):
+        np.testing.assert_allclose(a, b, rtol=1e-10)
+    Te = oracle.tucker_full(dims, G, B)
+    G1, B1, _ = oracle.tucker_jcomm_outer(Te, G, B, beta, L=2)
+    np.testing.assert_allclose(G1, G, rtol=1e-10)
+    for a, b in zip(B1, B):
+        np.testing.assert_allclose(a, b, rtol=1e-10)

@@ -239,6 +239,20 @@ int ntf_beta_div(ntf_ctx *ctx, int model, const ntf_tensor *X, float beta, int r
                  const float *const *factors, const ntf_opts *opts, double *out_dev,
                  void *stream);
 
+/* The cut of a dense order-N (4 <= N <= 8) CP or Tucker problem into the three runs of consecutive
+ * modes [0, a), [a, b), [b, N) that ntf_cp_mu_sweep / ntf_tucker_mu_sweep / ntf_jcomm_outer /
+ * ntf_beta_div use for it (Section 6.1: the contractions over a merged index), as chosen from the
+ * shapes and opts (opts->merge when nonzero, else the library's choice) for a 16-byte-aligned X.
+ * Host-only planning: no context and no device work.
+ *   model: NTF_CP (rank_or_0 = R, core_dims_or_null = NULL) or NTF_TUCKER (rank_or_0 = 0,
+ *          core_dims_or_null = host array [N] of J_n)
+ *   dims:  host array [N]; beta: the divergence (Tucker tensor-core passes depend on it)
+ *   a_out, b_out: the run boundaries.
+ * NTF_ERR_ARG (NULL pointers, bad model or merge), NTF_ERR_UNSUPPORTED (order outside 4..8, rank
+ * or core extents outside 1..64, no cut with a last-run core extent <= 64), NTF_ERR_SHAPE. */
+int ntf_plan_cut(int model, int order, const int64_t *dims, int rank_or_0, const int64_t *core_dims_or_null,
+                 const ntf_opts *opts, float beta, int *a_out, int *b_out);
+
 /* Stable permutation of 0..nnz-1 by key (a COO coordinate array), bit-identical to a
  * stable sort: equal keys keep their input order.  keys: device int32 [nnz] with values
  * in [0, key_range); perm_out: device int32 [nnz].  Used internally to order COO

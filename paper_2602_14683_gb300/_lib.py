@@ -82,6 +82,8 @@ _sig = {
     "ntf_beta_div": (C.c_int, [_P, C.c_int, C.POINTER(Tensor), C.c_float, C.c_int, C.POINTER(C.c_int64), _P,
                                C.POINTER(_P), C.POINTER(Opts), _P, _P]),
     "ntf_coo_stable_perm": (C.c_int, [_P, _P, C.c_int64, C.c_int64, _P, _P]),
+    "ntf_plan_cut": (C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_int64), C.c_int, C.POINTER(C.c_int64),
+                               C.POINTER(Opts), C.c_float, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "ntf_server_create": (C.c_int, [C.POINTER(_P), C.c_int, C.c_int, C.c_size_t]),
     "ntf_server_submit": (C.c_int, [_P, C.POINTER(Job), C.POINTER(C.c_int64)]),
     "ntf_server_poll": (C.c_int, [_P, C.POINTER(Result), C.c_int, C.c_int]),
@@ -338,6 +340,21 @@ def jcomm_outer(X, beta, factors, core=None, objective=None, ctx=None, stream=No
         rc = _lib.ntf_jcomm_outer(ctx.h, NTF_TUCKER, C.byref(d.t), float(beta), 0, cd, core.data_ptr(), fp,
                                   C.byref(o), _out_ptr(objective), _stream(stream))
     ctx.check(rc)
+
+
+def plan_cut(dims, rank=None, core_dims=None, beta=1.0, **opts):
+    """(a, b): the runs [0, a), [a, b), [b, N) an order-N dense CP (rank) or Tucker (core_dims)
+    problem is cut into (host-only planning, no device)."""
+    n = len(dims)
+    d = (C.c_int64 * n)(*dims)
+    cd = (C.c_int64 * n)(*core_dims) if core_dims is not None else None
+    a, b = C.c_int(), C.c_int()
+    o = make_opts(**opts)
+    model = NTF_CP if core_dims is None else NTF_TUCKER
+    rc = _lib.ntf_plan_cut(model, n, d, int(rank or 0), cd, C.byref(o), float(beta), C.byref(a), C.byref(b))
+    if rc != NTF_OK:
+        raise NtfError(rc, "ntf_plan_cut failed")
+    return a.value, b.value
 
 
 def beta_div(X, beta, factors, core=None, out=None, ctx=None, stream=None, **opts):

@@ -1179,6 +1179,34 @@ int ntf_beta_div(ntf_ctx *ctx, int model, const ntf_tensor *X, float beta, int r
     return fail(ctx, NTF_ERR_ARG, "unknown model %d", model);
 }
 
+int ntf_plan_cut(int model, int order, const int64_t *dims, int rank_or_0, const int64_t *core_dims_or_null,
+                 const ntf_opts *opts, float beta, int *a_out, int *b_out) {
+    if (!dims || !a_out || !b_out) return NTF_ERR_ARG;
+    if (order < 4 || order > 8) return NTF_ERR_UNSUPPORTED;
+    for (int n = 0; n < order; ++n)
+        if (dims[n] < 1) return NTF_ERR_SHAPE;
+    const ntf_opts o = resolve_opts(opts);
+    ntf_tensor X{};
+    X.order = order;
+    X.dims = dims;
+    X.kind = NTF_DENSE;
+    X.values = nullptr;  // planning only: a 16-byte-aligned tensor is assumed
+    int a = 0, b = 0, rc;
+    if (model == NTF_CP) {
+        if (rank_or_0 < 1 || rank_or_0 > 64) return NTF_ERR_UNSUPPORTED;
+        rc = nway_split(nullptr, &X, rank_or_0, o, o.precision, a, b);
+    } else if (model == NTF_TUCKER) {
+        if (!core_dims_or_null) return NTF_ERR_ARG;
+        rc = ntf::tucker_plan_cut(&X, core_dims_or_null, o, beta, a, b);
+    } else {
+        return NTF_ERR_ARG;
+    }
+    if (rc) return rc;
+    *a_out = a;
+    *b_out = b;
+    return NTF_OK;
+}
+
 int ntf_coo_stable_perm(ntf_ctx *ctx, const int32_t *keys, int64_t nnz, int64_t key_range, int32_t *perm_out,
                         void *stream) {
     if (!ctx) return NTF_ERR_ARG;

@@ -25,4 +25,6 @@ int tucker_run_extrap(ntf_ctx *ctx, const ntf_tensor *X, float beta, const int64
                       float *const *factors, float *core_prev, float *const *factors_prev, float alpha, float cap,
                       float delta, const ntf_opts &o, double *objective_dev, cudaStream_t st);
 void tucker_release(ntf_ctx *ctx);
+// the cut of an order N >= 4 Tucker problem into three runs (planning only, no device work)
+int tucker_plan_cut(const ntf_tensor *X, const int64_t *core_dims, const ntf_opts &o, float beta, int &a, int &b);
 }  // namespace ntf

@@ -1586,6 +1586,12 @@ int tucker_nway_run(ntf_ctx *ctx, const ntf_tensor *X, float beta, const int64_t
     return tn_store(ctx, t, w, core, factors, st);
 }
 
+int tucker_plan_cut(const ntf_tensor *X, const int64_t *core_dims, const ntf_opts &o, float beta, int &a, int &b) {
+    for (int n = 0; n < X->order; ++n)
+        if (core_dims[n] < 1 || core_dims[n] > 64 || core_dims[n] > X->dims[n]) return NTF_ERR_UNSUPPORTED;
+    return tn_split(nullptr, X, core_dims, o, beta, a, b);
+}
+
 int tucker_nway_beta_div(ntf_ctx *ctx, const ntf_tensor *X, float beta, const int64_t *core_dims, const float *core,
                          const float *const *factors, const ntf_opts &o, double *out_dev, cudaStream_t st) {
     TNWay t{};

@@ -262,7 +262,7 @@ void ntfo_cp_jcomm_outer(int N, const int64_t *dims, const double *X, int R, dou
                          double beta, double eps, double eps_x, int L, int max_blocks,
                          double *F_ref) {
     int64_t cnt = numel(N, dims);
-    double *At[NTFO_MAXN], *C1[NTFO_MAXN], *C2[NTFO_MAXN];
+    double *At[NTFO_MAXN] = {0}, *C1[NTFO_MAXN] = {0}, *C2[NTFO_MAXN] = {0};
     for (int m = 0; m < N; ++m) {
         At[m] = (double *)malloc(sizeof(double) * dims[m] * R);
         C1[m] = (double *)malloc(sizeof(double) * dims[m] * R);

@@ -73,9 +73,12 @@ def test_nway_jcomm_parity(dims, R, prec, tol, tol_obj, L, beta):
 def test_nway_merge_choices(dims, merge, prec, R, tol, tol_obj, beta):
     """Explicit cuts of the modes into the three runs of the 3-way view: B-CoMM sweep and
     J-CoMM with two inner sweeps.  Tensor-core bar 3e-3: these 3-way views have 6 to 48 rows
-    per mode, and the BF16 rounding of a factor operand (u = 2^-9) is shared by every term that
-    uses that row, so it averages over a few rows only (about u / sqrt(rows) per column, two
-    operands, compounded over two inner sweeps), against 150+ rows in the other parity cases."""
+    per mode, and the BF16 rounding of a factor operand (unit roundoff u = 2^-8, 8 significand
+    bits) is shared by every term that uses that row, so it averages over a few rows only:
+    about u / sqrt(rows) = 1.6e-3 per column at 6 rows, sqrt(2) times that (2.3e-3) for the two
+    independently rounded operands of a contraction.  The per-factor Frobenius error averages
+    these per-entry errors over the factor's rows and columns, which keeps it under the 3e-3
+    bar over two inner sweeps; the other parity cases have 150+ rows per mode."""
     ntf = _ntf()
     X, _ = synth.cp_dense(dims, R, seed=sum(merge) + R, kind="gamma_noise")
     A = synth.init_factors(dims, R, seed=R + 7)

@@ -749,3 +749,60 @@ def test_order5_cp_and_tucker_contractions_brute_force(beta):
     np.testing.assert_allclose(G1, G, rtol=1e-10)
     for a, b in zip(B1, B):
         np.testing.assert_allclose(a, b, rtol=1e-10)
+
+
+# ------------------------------------------------------- sampled Num/Den rows (large-problem checker)
+
+def _chi1_def(z, zt, beta):
+    # Section 5.3, "Two transforms": chi_1(Z, Z~) = Z~^(2 - beta) Z^(beta - 1)
+    return zt ** (2.0 - beta) * z ** (beta - 1.0)
+
+
+def _chi2_def(z, zt, beta):
+    # Section 5.3, "Two transforms": chi_2 = Z for beta < 1, Z^beta Z~^(1 - beta) otherwise
+    return z.copy() if beta < 1.0 else z ** beta * zt ** (1.0 - beta)
+
+
+@pytest.mark.parametrize("beta", BETAS)
+@pytest.mark.parametrize("dims", [(5, 4, 3), (3, 4, 2, 3)])
+def test_numden_rows_matches_block_update_and_jcomm_definition(beta, dims):
+    """ntfo_cp_numden_rows (the row-sampled checker of the full-size parity tests and of the CPU
+    baseline) against two things outside it, on every row of every mode:
+      * with one factor set for the reconstruction and both contractions, the Num/Den of
+        ntfo_cp_block_update (Algorithm 1's block, whose contractions are pinned by brute force);
+      * with three distinct factor sets -- the reference A~ for the reconstruction, chi_1(A, A~)
+        for the numerator and chi_2(A, A~) for the denominator -- the J-CoMM Num_J / Den_J of
+        Section 5.3 ("CP inner update"), written here as einsum sums of their definitions.
+    A swapped numerator / denominator factor set, a wrong mode index or a wrong row mapping
+    fails the second check, since all three factor sets differ."""
+    g = np.random.default_rng(53 + len(dims))
+    N, R = len(dims), 3
+    X = g.gamma(3.0, 1.0, size=dims) + 0.05
+    if beta == 0.0:
+        X.flat[::7] = 0.0  # exercises the eps_x floor of the IS case
+    A = [g.uniform(0.2, 1.0, size=(d, R)) for d in dims]
+    At = [g.uniform(0.2, 1.0, size=(d, R)) for d in dims]
+    subs = "ijkl"[:N]
+    # block update: one factor set
+    for n in range(N):
+        rows = np.arange(dims[n])
+        num, den = oracle.cp_numden_rows(X, A, A, A, n, rows, beta)
+        _, num_b, den_b = oracle.cp_block_update(X, A, n, beta)
+        np.testing.assert_allclose(num, num_b, rtol=1e-12)
+        np.testing.assert_allclose(den, den_b, rtol=1e-12)
+    # J-CoMM: reference reconstruction, chi_1 / chi_2 contraction factors
+    B1 = [_chi1_def(a, at, beta) for a, at in zip(A, At)]
+    B2 = [_chi2_def(a, at, beta) for a, at in zip(A, At)]
+    Xt = np.einsum(",".join(s + "r" for s in subs) + "->" + subs, *At)
+    y = np.maximum(Xt, 1e-12)
+    Xs = np.maximum(X, 1e-12) if beta == 0.0 else X
+    Pt, Qt = Xs * y ** (beta - 2.0), y ** (beta - 1.0)
+    for n in range(N):
+        others = [m for m in range(N) if m != n]
+        spec = subs + "," + ",".join(subs[m] + "r" for m in others) + "->" + subs[n] + "r"
+        num_j = np.einsum(spec, Pt, *[B1[m] for m in others])
+        den_j = np.einsum(spec, Qt, *[B2[m] for m in others])
+        rows = np.arange(dims[n])[::-1].copy()  # reversed: output q belongs to rows[q]
+        num, den = oracle.cp_numden_rows(X, At, B1, B2, n, rows, beta)
+        np.testing.assert_allclose(num, num_j[rows], rtol=1e-12)
+        np.testing.assert_allclose(den, den_j[rows], rtol=1e-12)

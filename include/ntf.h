@@ -248,8 +248,14 @@ int ntf_beta_div(ntf_ctx *ctx, int model, const ntf_tensor *X, float beta, int r
  *          core_dims_or_null = host array [N] of J_n)
  *   dims:  host array [N]; beta: the divergence (Tucker tensor-core passes depend on it)
  *   a_out, b_out: the run boundaries.
- * NTF_ERR_ARG (NULL pointers, bad model or merge), NTF_ERR_UNSUPPORTED (order outside 4..8, rank
- * or core extents outside 1..64, no cut with a last-run core extent <= 64), NTF_ERR_SHAPE. */
+ * The cut depends on opts->precision.  ntf_beta_div evaluates the objective on the FP32 passes
+ * whatever opts->precision says, so the cut it uses is the one returned for
+ * opts->precision = NTF_PREC_FP32 (for example CP 80 x 70 x 60 x 50 at R = 10: (1, 2) at
+ * NTF_PREC_TF32 for the sweeps, (1, 3) for ntf_beta_div).
+ * NTF_ERR_ARG (NULL pointers, bad model or merge, eps or eps_x <= 0, inner_L < 1, unknown
+ * precision), NTF_ERR_BETA (beta outside [0, 2)), NTF_ERR_UNSUPPORTED (order outside 4..8, rank
+ * or core extents outside 1..64, no cut with a last-run core extent <= 64), NTF_ERR_SHAPE
+ * (dims outside 1..2^31 - 1, or a run's extent beyond 32 bits). */
 int ntf_plan_cut(int model, int order, const int64_t *dims, int rank_or_0, const int64_t *core_dims_or_null,
                  const ntf_opts *opts, float beta, int *a_out, int *b_out);
 
@@ -313,10 +319,11 @@ int ntf_server_poll(ntf_server *server, ntf_result *out, int max_results, int wa
 void ntf_server_destroy(ntf_server *server);
 
 /* Allocation-free objective for dense CP tensors.  The paper has no counterpart: this is a
- * service for callers that cannot allocate device memory when they call -- code running
- * while a CUDA graph is being captured, or a process whose device memory is reserved up
- * front by another allocator or a fixed budget.  The other entry points grow workspaces
- * with cudaMalloc; this one allocates nothing.  It computes the same value as
+ * service for callers that cannot allocate device memory when they call -- a process whose
+ * device memory is reserved up front by another framework's allocator, or one held to a
+ * fixed device-memory budget, where a cudaMalloc inside the library would fail or take
+ * memory the caller has already given out.  The other entry points grow workspaces with
+ * cudaMalloc; this one allocates nothing.  It computes the same value as
  * ntf_beta_div(ctx, NTF_CP, X, beta, rank, NULL, NULL, factors, opts, out_dev, stream)
  * with opts = {eps, eps_x}, on the current device, asynchronously on `stream`.
  *   - Scratch: a file-scope device array of NTF_NOALLOC_SCRATCH_BYTES that every GPU

@@ -1184,8 +1184,13 @@ int ntf_plan_cut(int model, int order, const int64_t *dims, int rank_or_0, const
     if (!dims || !a_out || !b_out) return NTF_ERR_ARG;
     if (order < 4 || order > 8) return NTF_ERR_UNSUPPORTED;
     for (int n = 0; n < order; ++n)
-        if (dims[n] < 1) return NTF_ERR_SHAPE;
+        if (dims[n] < 1 || dims[n] > (int64_t)0x7fffffff) return NTF_ERR_SHAPE;
     const ntf_opts o = resolve_opts(opts);
+    // the option checks of the calls being planned (check_common), without a context
+    if (!(beta >= 0.0f && beta < 2.0f)) return NTF_ERR_BETA;
+    if (!(o.eps > 0.0) || !(o.eps_x > 0.0) || o.inner_L < 1) return NTF_ERR_ARG;
+    if (o.precision != NTF_PREC_FP32 && o.precision != NTF_PREC_TF32 && o.precision != NTF_PREC_3XTF32)
+        return NTF_ERR_ARG;
     ntf_tensor X{};
     X.order = order;
     X.dims = dims;

@@ -63,3 +63,25 @@ def test_tucker_cut_needs_a_small_last_core_run():
     # the library's own choice avoids that run
     a, b = ntf.plan_cut((6, 5, 9, 9), core_dims=(2, 2, 9, 9))
     assert b == 3
+
+
+def test_objective_cut_is_the_fp32_cut():
+    """ntf_beta_div evaluates the objective on the FP32 passes whatever the precision option says,
+    so its cut is the one planned at fp32; the sweeps at tf32 take the aligned cut."""
+    ntf = _ntf()
+    assert ntf.plan_cut((80, 70, 60, 50), rank=10, precision="tf32") == (1, 2)
+    assert ntf.plan_cut((80, 70, 60, 50), rank=10, precision="fp32") == (1, 3)
+
+
+def test_planning_checks_the_options_of_the_planned_calls():
+    ntf = _ntf()
+    cases = [(dict(dims=(80, 70, 60, 2 ** 31)), -3),          # a dimension beyond 32 bits
+             (dict(precision=7), -1),                          # unknown precision
+             (dict(eps=0.0), -1), (dict(eps_x=-1.0), -1),      # floors must be positive
+             (dict(inner_L=0), -1),
+             (dict(beta=2.0), -2), (dict(beta=-0.5), -2)]      # beta outside [0, 2)
+    for kw, code in cases:
+        dims = kw.pop("dims", (80, 70, 60, 50))
+        with pytest.raises(ntf.NtfError) as e:
+            ntf.plan_cut(dims, rank=10, **kw)
+        assert e.value.code == code, (kw, e.value.code)

@@ -2,42 +2,47 @@
 //
 // Same computation and partial-sum layouts as the FP32 pass (CPContr^(n) of P and Q,
 // Section 6.1; Theorem "CP block multiplicative update"; Xhat never stored).  A CTA owns a
-// tile of 128 rows j, a block of 128 columns k and a range of slabs i, walked as a sequence
-// of 64-column chunks (two per slab).  Warps are specialised: warp 4 CG + 1 streams X
-// chunks into a shared-memory ring by TMA (and PF chunks further ahead into L2 by bulk
-// prefetch); warp 4 CG issues every MMA, in chunk order; warps 0..4 CG - 1 are the epilogue,
-// thread (warp w, lane l) owning tile row 32 (w % 4) + l (its TMEM lane), the column group
-// w / 4 (64 / CG columns) of each chunk and the rank slice w / 4 (32 / CG ranks) of the
-// row-side constants and folds.  The epilogue warps signal per warp, on mbarriers, when an
-// X stage, an X-hat buffer, a P tile or the next slab's R operand is free / ready; the only
-// block-wide wait is one named barrier per slab.
+// tile of 128 rows j, a block of KB columns k (128, or 256 for the KL single-TF32 variants)
+// and a range of slabs i, walked as a sequence of 64-column chunks (KB / 64 per slab).
+// Warps are specialised and hand off through mbarriers only:
+//   warp 17 (producer, one thread): X chunks into a shared-memory ring by TMA (chunks further
+//     ahead into L2 by bulk prefetch) and GEMM1 of every chunk;
+//   warp 16 (issuer, one thread; owns the TMEM allocation): the contractions (GEMM2);
+//   warps 18, 19 (builders): per slab, the GEMM1 rows R = A_i (.) B_j (TF32) and the column
+//     contraction's KRn^T = (A_i (.) B_j)^T (BF16), into rings of NR / NK buffers, one slab
+//     ahead of their use;
+//   warps 0..15 (epilogue): two groups of eight warps that take the chunks in turn (group
+//     g = chunk parity).  Thread (warp w, lane l) owns tile row 32 (w % 4) + l (its TMEM
+//     lane) and the 32 columns 32 ((w / 4) % 2) of its group's chunks; while one group runs
+//     the MUFU-bound powers of a chunk, the other loads, hands off and folds.
 //
 // Per chunk n (slab i, columns k0 + 64 q):
-//   TMA       X chunk (128 x 64 FP32) into a 2- or 3-stage ring, issued that far ahead;
-//   GEMM1     Xhat = R C^T on TF32 operands rounded to nearest, M128 N64 K32, into one of
-//             two TMEM buffers, issued one chunk ahead; with S3 the operands are split into
-//             hi / lo TF32 parts and GEMM1 is hi*lo + lo*hi + hi*hi (about FP32 accuracy);
+//   TMA       X chunk (128 x 64 FP32, two 32-column boxes) into a 2- or 3-stage ring;
+//   GEMM1     Xhat = R C^T on TF32 operands rounded to nearest, M128 N64 K32, into TMEM
+//             buffer n % 2 as soon as that buffer's previous chunk has been read; with S3 the
+//             operands are split into hi / lo TF32 parts (hi*lo + lo*hi + hi*hi);
 //   epilogue  Xhat from TMEM (tcgen05.ld), X from shared memory, P = X Y^(beta-2),
-//             Q = Y^(beta-1) (Y = max(Xhat, eps)) and the objective terms in FP32
-//             registers; P, Q stored once as BF16 tiles [rows][64 cols];
+//             Q = Y^(beta-1) (Y = max(Xhat, eps)) and the objective terms in FP32 registers;
+//             P, Q stored once as BF16 tiles [rows][64 cols] (buffer n % NP);
 //   GEMM2     rows: W[j][r] += sum_k P[j][k] Cn[k][r]   (A = P K-major, B = Cn^T)
 //             cols: N3^T[r][k] += sum_j KRn^T[r][j] P[j][k]  (A = KRn^T with the rank
-//             padded to M = 128, B = the same P tile read MN-major),
-//             BF16 operands, FP32 accumulation in TMEM, overlapping the next epilogue.
-// W and KRn^T are double-buffered per slab: during the second chunk of slab i, mode 1
-// reduces sum_j W[j][r] Bn[j][r] of slab i - 1 over each warp's 32 rows (shuffle
-// reduce-scatter; one partial per 32-row quarter, summed in fixed order later) and mode 2
-// accumulates An[i-1][r] W[j][r] per row, while the contractions of slab i proceed.  Every wait on an mbarrier is bounded;
+//             padded to M = 128, B = the P tile read MN-major; with four P buffers the P
+//             tiles of a chunk pair, adjacent in shared memory, are one N = 128 operand),
+//             BF16 operands, FP32 accumulation in TMEM.
+// W of slab i (double-buffered by slab parity) is folded by both groups, each for 16 of the
+// 32 ranks, early in slab i + 1: mode 1 reduces sum_j W[j][r] Bn[j][r] over each warp's 32
+// rows (shuffle reduce-scatter, one partial per 32-row quarter, summed in fixed order
+// later), mode 2 accumulates An[i][r] W[j][r] per row.  Every wait on an mbarrier is bounded;
 // a wait that runs out raises a shared abort flag that ends the other waits at once; the
-// kernel then sets the context's status word, waits (bounded) for its copies and MMAs,
-// frees its TMEM and returns.
+// kernel then sets the context's status word, waits (bounded) for its copies and MMAs, frees
+// its TMEM and returns.
 //
 // With RX (explicit rows: the Tucker passes of Appendix C), the GEMM1 rows of slab i are
 // rrow[i*J + j] (the mode-3 partial tensor B^(3) of eq. (block_Bn)) instead of A_i (.) B_j,
 // the column contraction's operand is nrow[i*J + j] (and drow) instead of A_i (.) B_j, and
 // the rows contraction W[j][r] of each slab is written out ([column block][I*J][RP]
 // partials, summed over the column blocks afterwards) instead of being folded into modes
-// 1 and 2.  Row values are loaded from global memory two chunks before they are staged.
+// 1 and 2.
 #pragma once
 
 #include <cuda.h>
@@ -54,42 +59,45 @@ constexpr int ROWS = 128;  // tile rows
 constexpr int KBLK = 128;  // columns per CTA block (256 for the KL / single-TF32 variants)
 constexpr int CH = 64;     // columns per chunk
 constexpr int RP = 32;
-constexpr int CG = 4;      // column groups per chunk (epilogue warps = 4 CG)
-constexpr int CW = CH / CG;  // columns per epilogue thread and chunk
-constexpr int RS = RP / CG;  // ranks per epilogue thread in the row-side work
-constexpr int EW = 128 * CG;  // epilogue threads
-constexpr int NT = EW + 64;   // + the MMA issuer warp + the TMA producer warp
-constexpr int PF = 6;         // X chunks prefetched into L2 ahead of the shared-memory ring
-static_assert(CW % 8 == 0 && RS % 4 == 0 && 32 % CW == 0, "column groups");
+constexpr int CW = 32;     // columns per epilogue thread and chunk
+constexpr int EW = 512;    // epilogue threads (two groups of eight warps)
+constexpr int GW = EW / 2; // threads per group
+constexpr int BW = 64;     // builder threads
+constexpr int NT = EW + 64 + BW;  // + the issuer and producer warps + the builders
+constexpr int PF = 6;      // X chunks prefetched into L2 ahead of the shared-memory ring
 
 struct Layout {
     int x, p, q, r, rl, c, cl, cnt, cdt, knt, kdt, misc, total;
     int ns;  // X stages
-    int np;  // P / Q buffers
-    int nk;  // KRn^T / KRd^T buffers (2: slab i + 1's is written while slab i's is read)
+    int np;  // P / Q buffers (2: one per epilogue group; 4: two per group)
+    int nk;  // KRn^T / KRd^T buffers
+    int nr;  // R buffers
 };
 
 // 1024-aligned regions.  The column contraction reads KRn^T as an M = 128 operand whose
 // rows 32..127 are padding: those rows only feed accumulator rows that are never read, so
 // only the 32 real rows are stored (two 4 KB K-atoms per buffer) and the padding reads fall
-// on the 16 KB that follow (the Crec / R tiles), which stay inside the allocation.
+// on the 16 KB or more that follow (the C / R tiles), which stay inside the allocation.
 // kb: columns per CTA block; the C tile is kb x 32 TF32 (128 bytes a column) and the
-// contraction's C^T operand 32 x kb BF16
-__host__ __device__ constexpr int layout_bytes(bool rows, bool m3, bool den, bool s3, int ns, int np, int nk, int kb) {
-    return ns * 32768 + np * 16384 * (den ? 2 : 1) + (s3 ? 2 : 1) * kb * 128 + (s3 ? 2 : 1) * 16384 +
+// contraction's C^T operand 32 x kb BF16.
+__host__ __device__ constexpr int layout_bytes(bool rows, bool m3, bool den, bool s3, int ns, int np, int nk, int nr,
+                                               int kb) {
+    return ns * 32768 + np * 16384 * (den ? 2 : 1) + (s3 ? 2 : 1) * kb * 128 + nr * (s3 ? 2 : 1) * 16384 +
            (rows ? kb * 64 : 0) + ((rows && den) ? kb * 64 : 0) + (m3 ? nk * 8192 : 0) + ((m3 && den) ? nk * 8192 : 0) +
-           4096 + 1024;
+           512 + 1024;
 }
 
 __host__ __device__ constexpr Layout make_layout(bool rows, bool m3, bool den, bool s3, int kb) {
     Layout L{};
-    constexpr int kMax = 232448;  // opt-in shared memory per CTA
+    constexpr int kMax = 231424;  // opt-in shared memory per CTA (227 KB), less 1 KB of margin
     L.ns = 2;
-    L.np = 1;
+    L.np = 2;
     L.nk = 1;
-    if (layout_bytes(rows, m3, den, s3, 2, 2, 1, kb) <= kMax) L.np = 2;
-    if (layout_bytes(rows, m3, den, s3, 2, L.np, 2, kb) <= kMax) L.nk = 2;
-    if (layout_bytes(rows, m3, den, s3, 3, L.np, L.nk, kb) <= kMax) L.ns = 3;
+    L.nr = 1;
+    if (layout_bytes(rows, m3, den, s3, 2, 2, 1, 2, kb) <= kMax) L.nr = 2;
+    if (m3 && layout_bytes(rows, m3, den, s3, 2, 2, 2, L.nr, kb) <= kMax) L.nk = 2;
+    if (layout_bytes(rows, m3, den, s3, 2, 4, L.nk, L.nr, kb) <= kMax) L.np = 4;
+    if (layout_bytes(rows, m3, den, s3, 3, L.np, L.nk, L.nr, kb) <= kMax) L.ns = 3;
     int o = 0;
     L.x = o; o += L.ns * 32768;
     L.p = o; o += L.np * 16384;
@@ -98,11 +106,11 @@ __host__ __device__ constexpr Layout make_layout(bool rows, bool m3, bool den, b
     L.c = o; o += kb * 128;
     L.cl = o; o += s3 ? kb * 128 : 0;
     L.kdt = o; o += (m3 && den) ? L.nk * 8192 : 0;   // padding rows read the R tiles below
-    L.r = o; o += 16384;
-    L.rl = o; o += s3 ? 16384 : 0;
+    L.r = o; o += L.nr * 16384;
+    L.rl = o; o += s3 ? L.nr * 16384 : 0;
     L.cnt = o; o += rows ? kb * 64 : 0;
     L.cdt = o; o += (rows && den) ? kb * 64 : 0;
-    L.misc = o; o += 4096;
+    L.misc = o; o += 512;
     L.total = o + 1024;  // alignment slack of the dynamic base
     return L;
 }
@@ -169,6 +177,21 @@ __device__ __forceinline__ void tmem_ld8(uint32_t addr, float *v) {
     asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
     for (int c = 0; c < 8; ++c) v[c] = __uint_as_float(r[c]);
+}
+// two 16-column loads under one wait
+__device__ __forceinline__ void tmem_ld16x2(uint32_t addr0, uint32_t addr1, float *v) {
+    uint32_t r[32];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                 : "r"(addr0));
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+                 : "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+                   "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                 : "r"(addr1));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+    for (int c = 0; c < 32; ++c) v[c] = __uint_as_float(r[c]);
 }
 template <int N>
 __device__ __forceinline__ void tmem_ld(uint32_t addr, float *v) {
@@ -327,15 +350,26 @@ __device__ __forceinline__ float reduce_scatter(float v[N]) {
     return s;
 }
 
+// eight BF16 values s * v[e] as one 16-byte word
+__device__ __forceinline__ uint4 pack8(const float *v, float s) {
+    __nv_bfloat162 h0 = __floats2bfloat162_rn(s * v[0], s * v[1]), h1 = __floats2bfloat162_rn(s * v[2], s * v[3]);
+    __nv_bfloat162 h2 = __floats2bfloat162_rn(s * v[4], s * v[5]), h3 = __floats2bfloat162_rn(s * v[6], s * v[7]);
+    uint4 u;
+    u.x = *reinterpret_cast<uint32_t *>(&h0); u.y = *reinterpret_cast<uint32_t *>(&h1);
+    u.z = *reinterpret_cast<uint32_t *>(&h2); u.w = *reinterpret_cast<uint32_t *>(&h3);
+    return u;
+}
+
 template <int MS, int BK, bool S3, bool RX, int KB>
 __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUtensorMap xmap, const Cp3Args a) {
     constexpr bool DEN = BK != BK_KL;
     constexpr bool M1 = (MS & PM_M1) != 0, M2 = (MS & PM_M2) != 0, M3 = (MS & PM_M3) != 0;
     constexpr bool OBJ = (MS & PM_OBJ) != 0, RW = M1 || M2;
-    constexpr int CPS = KB / CH;  // chunks per slab
+    constexpr int CPS = KB / CH;  // chunks per slab (2 or 4)
     static_assert(KB == 128 || (KB == 256 && !DEN && !S3 && !RX), "256-column blocks: KL, single TF32");
     constexpr Layout L = make_layout(RW, M3, DEN, S3, KB);
-    constexpr int NP = L.np, NS = L.ns, NK = L.nk;
+    constexpr int NS = L.ns, NP = L.np, NK = L.nk, NR = L.nr;
+    constexpr bool PAIR = M3 && NP == 4;  // column contraction on chunk pairs (N = 128)
     extern __shared__ __align__(1024) uint8_t smraw[];
     uint8_t *sm = (uint8_t *)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
     const float *Xs = (const float *)(sm + L.x);
@@ -349,22 +383,23 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
     __nv_bfloat16 *CdT = (__nv_bfloat16 *)(sm + L.cdt);
     __nv_bfloat16 *KnT = (__nv_bfloat16 *)(sm + L.knt);
     __nv_bfloat16 *KdT = (__nv_bfloat16 *)(sm + L.kdt);
-    // mbarriers, per ring slot s = chunk % NS: chunk_ready (X stage landed and X-hat computed:
-    // the TMA bytes plus the GEMM1 commit), inputs_free (every epilogue warp has read the X
-    // stage and the X-hat buffer); per P buffer: p_full, g2_done (its contractions complete);
-    // r_full (R holds the next slab)
+    // mbarriers.  Per X ring slot (chunk % NS): chunk_ready (the X stage landed and X-hat
+    // computed: the TMA bytes plus the GEMM1 commit), inputs_free (the chunk's group has read
+    // the stage and the X-hat buffer).  Per P buffer (chunk % NP): p_full (the group's eight
+    // warps), g2_done (the contractions that read it are complete).  Per R / KR buffer
+    // (slab % NR, slab % NK): *_full (both builder warps), *_free (the slab's last GEMM1 /
+    // GEMM2 complete).
     uint64_t *bars = (uint64_t *)(sm + L.misc);
-    uint64_t *chunk_ready = bars, *inputs_free = bars + 4, *p_full = bars + 8, *g2_done = bars + 10;
-    uint64_t *r_full = bars + 12;
-    constexpr int NBAR = 13;
-    uint32_t *tslot = (uint32_t *)(sm + L.misc + 128);
-    volatile int *abort_flag = (volatile int *)(sm + L.misc + 136);
-    double *dred = (double *)(sm + L.misc + 192 + 1024);  // [EW / 32]
-    float *srow = (float *)(sm + L.misc + 2048);          // [4 slabs][rec0, num0, den0][32]
+    uint64_t *chunk_ready = bars, *inputs_free = bars + 3, *p_full = bars + 6, *g2_done = bars + 10;
+    uint64_t *r_free = bars + 14, *r_full = bars + 16, *k_free = bars + 18, *k_full = bars + 20;
+    constexpr int NBAR = 22;
+    uint32_t *tslot = (uint32_t *)(sm + L.misc + 192);
+    volatile int *abort_flag = (volatile int *)(sm + L.misc + 200);
+    double *dred = (double *)(sm + L.misc + 256);  // [EW / 32] (128 bytes)
 
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    const bool issuer = warp == EW / 32, producer = warp == EW / 32 + 1, epi = warp < EW / 32;
-    const int quarter = warp & 3, cg = warp >> 2;
+    const bool issuer = warp == EW / 32, producer = warp == EW / 32 + 1, builder = warp >= EW / 32 + 2;
+    const int quarter = warp & 3, half = (warp >> 2) & 1, grp = (warp >> 3) & 1;
     const int row = 32 * quarter + lane;  // tile row = TMEM lane (epilogue warps)
     int b = blockIdx.x;
     const int is = b % a.n_is;
@@ -376,9 +411,11 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
     const int J = a.J, K = a.K;
     const int j0 = jt * ROWS, k0 = kb * KB;
     const int j = j0 + row;
+    const bool epi = warp < EW / 32;
     const bool jv = epi && j < J;
-    const int NC = CPS * (i1 - i0);
-    const int r0 = RS * cg;
+    const int NSL = i1 - i0;  // slabs of this CTA
+    const int NC = CPS * NSL;
+    const int rf = 16 * grp + 8 * half;  // this thread's 8 ranks of the folds
 
     auto wait = [&](uint64_t *bar, uint32_t phase) -> bool {
         const uint32_t ba = su32(bar);
@@ -396,47 +433,37 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
         __syncwarp();
         if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" :: "r"(su32(bar)) : "memory");
     };
-    auto epi_sync = [&]() { asm volatile("bar.sync 1, %0;\n" :: "n"(EW) : "memory"); };
 
-    // ---- per-CTA constants (epilogue threads) ----------------------------------------------
-    float brec[RS], bn[RS], bd[RS];
+    // ---- per-CTA constants (epilogue threads): the row factors of the mode-1 fold ----------
+    float bn[8], bd[8];
 #pragma unroll
-    for (int r = 0; r < RS; ++r) {
-        brec[r] = (jv && !RX) ? __ldg(a.rec[1] + (int64_t)j * RP + r0 + r) : 0.0f;
-        bn[r] = (jv && M1 && !RX) ? __ldg(a.num[1] + (int64_t)j * RP + r0 + r) : 0.0f;
-        bd[r] = (jv && M1 && DEN && !RX) ? __ldg(a.den[1] + (int64_t)j * RP + r0 + r) : 0.0f;
-    }
-    // KRn^T / KRd^T side (mode 3): epilogue thread t owns rank t % 32 and the eight tile rows
-    // 8 (t / 32) .. 8 (t / 32) + 7, so that a slab's KR tile is one 16-byte store per thread
-    const int kr_r = t & 31, kr_j = 8 * (t >> 5);
-    float bk[8], bkd[8];
-#pragma unroll
-    for (int e = 0; e < 8; ++e) {
-        const bool v = M3 && !RX && epi && j0 + kr_j + e < J;
-        bk[e] = v ? __ldg(a.num[1] + (int64_t)(j0 + kr_j + e) * RP + kr_r) : 0.0f;
-        bkd[e] = (v && DEN) ? __ldg(a.den[1] + (int64_t)(j0 + kr_j + e) * RP + kr_r) : 0.0f;
+    for (int r = 0; r < 8; ++r) {
+        bn[r] = (jv && M1 && !RX) ? __ldg(a.num[1] + (int64_t)j * RP + rf + r) : 0.0f;
+        bd[r] = (jv && M1 && DEN && !RX) ? __ldg(a.den[1] + (int64_t)j * RP + rf + r) : 0.0f;
     }
     if (epi) {
+        // C tile (GEMM1 B operand, TF32 hi / lo) and Cn^T / Cd^T (rows contraction B operand)
+        const int cr0 = 8 * (warp >> 2);
 #pragma unroll 1
         for (int cc = row; cc < KB; cc += ROWS) {  // block column cc
             const int kc = k0 + cc;
             const bool kv = kc < K;
 #pragma unroll
-            for (int q = 0; q < RS / 4; ++q) {
+            for (int q = 0; q < 2; ++q) {
                 float h[4], l[4];
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
-                    const float v = kv ? __ldg(a.rec[2] + (int64_t)kc * RP + r0 + 4 * q + e) : 0.0f;
+                    const float v = kv ? __ldg(a.rec[2] + (int64_t)kc * RP + cr0 + 4 * q + e) : 0.0f;
                     h[e] = tf32_rna(v);
                     l[e] = S3 ? tf32_rna(v - h[e]) : 0.0f;
                 }
-                *reinterpret_cast<float4 *>(Cs + swf(cc, r0 + 4 * q)) = make_float4(h[0], h[1], h[2], h[3]);
-                if (S3) *reinterpret_cast<float4 *>(Cl + swf(cc, r0 + 4 * q)) = make_float4(l[0], l[1], l[2], l[3]);
+                *reinterpret_cast<float4 *>(Cs + swf(cc, cr0 + 4 * q)) = make_float4(h[0], h[1], h[2], h[3]);
+                if (S3) *reinterpret_cast<float4 *>(Cl + swf(cc, cr0 + 4 * q)) = make_float4(l[0], l[1], l[2], l[3]);
             }
             if (RW) {
 #pragma unroll
-                for (int r = 0; r < RS; ++r) {
-                    const int rr = r0 + r;
+                for (int r = 0; r < 8; ++r) {
+                    const int rr = cr0 + r;
                     CnT[(cc >> 6) * 2048 + swh(rr, cc & 63)] =
                         __float2bfloat16_rn(kv ? __ldg(a.num[2] + (int64_t)kc * RP + rr) : 0.0f);
                     if (DEN)
@@ -446,95 +473,20 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
             }
         }
     }
-    // Factor rows of slab i for R / KR / folds, in a ring of 4: slot (i + 2) % 4 is written at
-    // the start of slab i, after the barrier there, and its previous slab (i - 2) was last
-    // read by the fold during slab i - 1, before every warp reached that barrier; the first
-    // reader of slab i + 2 (R during slab i + 1) comes after the barrier of slab i + 1.
-    // Slabs i0 .. i0 + 2 are staged before the loop; at the start of slab i (after its
-    // barrier) threads 0..95 store slab i + 2 from a register loaded a slab earlier.
-    auto row_val = [&](int i) -> float {  // thread t < 96: entry t of slab i's staged rows
-        const int f = t >> 5, r = t & 31;
-        const float *src = f == 0 ? a.rec[0] : f == 1 ? a.num[0] : a.den[0];
-        return (f == 2 && !DEN) ? 0.0f : __ldg(src + (int64_t)i * RP + r);
-    };
-    auto stage_rows = [&](int i) {
-        if (t < 96 && !RX) srow[(i & 3) * 96 + t] = row_val(i);
-    };
-    // RX: this thread's entries of the next slabs' explicit rows, loaded ahead
-    float rx[RS], kx[8], kxd[8];
-    auto rx_load = [&](int i) {  // GEMM1 rows of slab i: row `row`, rank slice r0
-#pragma unroll
-        for (int q = 0; q < RS / 4; ++q) {
-            const float4 v = jv ? __ldg(reinterpret_cast<const float4 *>(a.rrow + ((int64_t)i * J + j) * RP + r0) + q)
-                                : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-            rx[4 * q] = v.x; rx[4 * q + 1] = v.y; rx[4 * q + 2] = v.z; rx[4 * q + 3] = v.w;
-        }
-    };
-    auto kx_load = [&](int i) {  // column-contraction rows of slab i: rank kr_r, rows kr_j ..
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            const bool v = epi && j0 + kr_j + e < J;
-            const int64_t o = ((int64_t)i * J + j0 + kr_j + e) * RP + kr_r;
-            kx[e] = v ? __ldg(a.nrow + o) : 0.0f;
-            kxd[e] = (v && DEN) ? __ldg(a.drow + o) : 0.0f;
-        }
-    };
-    auto slab_rows = [&](int i) {  // R (hi/lo) of slab i: row `row`, rank slice r0
-        const float *ar = srow + (i & 3) * 96 + r0;
-#pragma unroll
-        for (int q = 0; q < RS / 4; ++q) {
-            float h[4], l[4];
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const float v = RX ? rx[4 * q + e] : ar[4 * q + e] * brec[4 * q + e];
-                h[e] = tf32_rna(v);
-                l[e] = S3 ? tf32_rna(v - h[e]) : 0.0f;
-            }
-            *reinterpret_cast<float4 *>(Rs + swf(row, r0 + 4 * q)) = make_float4(h[0], h[1], h[2], h[3]);
-            if (S3) *reinterpret_cast<float4 *>(Rl + swf(row, r0 + 4 * q)) = make_float4(l[0], l[1], l[2], l[3]);
-        }
-    };
-    auto pack8 = [](const float *v, float s) {  // eight BF16 values s * v[e] as one uint4
-        __nv_bfloat162 h0 = __floats2bfloat162_rn(s * v[0], s * v[1]), h1 = __floats2bfloat162_rn(s * v[2], s * v[3]);
-        __nv_bfloat162 h2 = __floats2bfloat162_rn(s * v[4], s * v[5]), h3 = __floats2bfloat162_rn(s * v[6], s * v[7]);
-        uint4 u;
-        u.x = *reinterpret_cast<uint32_t *>(&h0); u.y = *reinterpret_cast<uint32_t *>(&h1);
-        u.z = *reinterpret_cast<uint32_t *>(&h2); u.w = *reinterpret_cast<uint32_t *>(&h3);
-        return u;
-    };
-    auto slab_kr = [&](int i) {  // KRn^T / KRd^T of slab i: row kr_r, columns kr_j .. kr_j + 7
-        const float *an = srow + (i & 3) * 96 + 32;
-        const int off = (kr_j >> 6) * 2048 + swh(kr_r, kr_j & 63);
-        *reinterpret_cast<uint4 *>(KnT + ((i - i0) % NK) * 4096 + off) = RX ? pack8(kx, 1.0f) : pack8(bk, an[kr_r]);
-        if (DEN)
-            *reinterpret_cast<uint4 *>(KdT + ((i - i0) % NK) * 4096 + off) = RX ? pack8(kxd, 1.0f) : pack8(bkd, an[32 + kr_r]);
-    };
     if (t == EW) {
         for (int q = 0; q < NBAR; ++q) {
-            const uint32_t cnt = q < 4 ? 2 : q < 10 || q == 12 ? EW / 32 : 1;
+            // chunk_ready: expect_tx + GEMM1 commit; g2_done, r_free, k_free: one commit;
+            // r_full, k_full: the two builder warps; inputs_free, p_full: a group's eight warps
+            const uint32_t cnt = q < 3 ? 2 : (q >= 10 && q < 16) || q == 18 || q == 19 ? 1 : q >= 16 ? 2 : GW / 32;
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" :: "r"(su32(bars + q)), "r"(cnt));
         }
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
         *abort_flag = 0;
     }
-    float rnext = 0.0f;  // slab i0 + 3's staged-row entry (threads t < 96)
-    if (NC > 0) {
-        for (int i = i0; i < i0 + 3 && i < i1; ++i) stage_rows(i);
-        if (t < 96 && i0 + 3 < i1 && !RX) rnext = row_val(i0 + 3);
-    }
     __syncthreads();
     if (issuer) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;\n" :: "r"(su32(tslot)));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
-    } else if (epi && NC > 0) {
-        if (RX) rx_load(i0);
-        slab_rows(i0);
-        if (RX && i0 + 1 < i1) rx_load(i0 + 1);
-        if (M3) {
-            if (RX) kx_load(i0);
-            slab_kr(i0);
-            if (RX && i0 + 1 < i1) kx_load(i0 + 1);
-        }
     }
     fence_async_smem();
     fence_before();
@@ -542,16 +494,16 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
     fence_after();
     const uint32_t tmem = *tslot;
     const uint32_t lane_off = (uint32_t)(32 * quarter) << 16;
-    // TMEM columns: X-hat [2][64] | W, Wd of even / odd slabs [2][32 + 32] | N3 [128] | N3d [128]
+    // TMEM columns: X-hat [2][64] | W, Wd of even / odd slabs [2][32 + 32] | N3 [KB] | N3d [128]
     const uint32_t t_d1 = tmem, t_w = tmem + 128, t_wd = tmem + 160, t_n3 = tmem + 256, t_n3d = tmem + 384;
 
-    float acc2[RS], acc2d[RS];
+    float acc2[8], acc2d[8];
 #pragma unroll
-    for (int r = 0; r < RS; ++r) acc2[r] = acc2d[r] = 0.0f;
+    for (int r = 0; r < 8; ++r) acc2[r] = acc2d[r] = 0.0f;
     double obj_acc = 0.0;
 
     if (producer) {
-        // ---- producer warp: X chunks into the shared-memory ring, PF chunks ahead into L2 ----
+        // ---- producer thread: X chunks into the ring, PF chunks ahead into L2, GEMM1 ------
         if (lane == 0 && NC > 0) {
             auto prefetch_x = [&](int n) {
                 const int i = i0 + n / CPS, x = k0 + CH * (n % CPS);
@@ -559,104 +511,164 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
                 if (x < K) tma_prefetch_2d(&xmap, x, i * J + j0);
                 if (x + 32 < K) tma_prefetch_2d(&xmap, x + 32, i * J + j0);
             };
-            for (int c = NS; c < NS + PF && c < NC; ++c) prefetch_x(c);
-            int xs = 0;        // ring slot of chunk n
-            uint32_t xph = 0;  // parity of its phase, (n / NS) & 1
-            for (int n = 0; n < NC; ++n) {
-                // chunk n - NS used this slot with the other parity
-                if (n >= NS && !wait(inputs_free + xs, xph ^ 1)) break;
+            auto load_x = [&](int n) {
                 const int i = i0 + n / CPS, q = n % CPS;
-                const uint32_t bar = su32(chunk_ready + xs);
-                const uint32_t dst = su32(Xs) + xs * 32768;
+                const uint32_t bar = su32(chunk_ready + n % NS);
+                const uint32_t dst = su32(Xs) + (n % NS) * 32768;
                 expect_tx(bar, 32768);
                 tma_2d(&xmap, dst, bar, k0 + CH * q, i * J + j0);
                 tma_2d(&xmap, dst + 16384, bar, k0 + CH * q + 32, i * J + j0);
-                if (n >= NS && n + PF < NC) prefetch_x(n + PF);
-                if (++xs == NS) {
-                    xs = 0;
-                    xph ^= 1;
+            };
+            // GEMM1 descriptors: A = R rows (K-major, 4 K-steps of 8 TF32), B = C columns
+            const uint32_t id1 = idesc_tf32(CH);
+            const uint64_t dR = sdesc(su32(Rs)), dRl = sdesc(su32(Rl)), dC = sdesc(su32(Cs)), dCl = sdesc(su32(Cl));
+            for (int c = 0; c < NS && c < NC; ++c) load_x(c);
+            for (int c = NS; c < NS + PF && c < NC; ++c) prefetch_x(c);
+            for (int n = 0; n < NC; ++n) {
+                if (n >= 2) {
+                    // chunk n - 2 has been read: X-hat buffer n % 2 and ring slot (n - 2) % NS free
+                    if (!wait(inputs_free + (n - 2) % NS, ((n - 2) / NS) & 1)) break;
+                    const int c = n - 2 + NS;
+                    if (c < NC) load_x(c);
+                    if (c + PF < NC) prefetch_x(c + PF);
                 }
+                const int s = n / CPS, q = n % CPS;
+                if (q == 0 && !wait(r_full + s % NR, (s / NR) & 1)) break;
+                fence_after();
+                const uint32_t d = t_d1 + 64 * (n & 1);
+                const uint32_t ro = (uint32_t)(s % NR) * 1024u;  // 16 KB R buffer, in 16-byte units
+                const uint32_t co = (uint32_t)q * 512u;           // 8 KB of C per chunk
+                if (S3) {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) mma_tf32(d, dRl + ro + 2 * k, dC + co + 2 * k, id1, k > 0);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) mma_tf32(d, dR + ro + 2 * k, dCl + co + 2 * k, id1, 1);
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) mma_tf32(d, dR + ro + 2 * k, dC + co + 2 * k, id1, S3 || k > 0);
+                mma_commit(su32(chunk_ready + n % NS));
+                if (q == CPS - 1) mma_commit(su32(r_free + s % NR));  // R of slab s read once done
             }
         }
         __syncwarp();
     } else if (issuer) {
-        // ---- issuer warp: GEMM1 and the contractions, in chunk order ----------------------
+        // ---- issuer thread: the contractions of every chunk, in chunk order ----------------
         if (lane == 0 && NC > 0) {
-            auto issue_g1 = [&](int n) {
-                const int q = n % CPS;
-                const uint32_t d = t_d1 + 64 * (n & 1);
-                const uint32_t id = idesc_tf32(CH);
-                const uint32_t cb = su32(Cs) + q * 8192, cbl = su32(Cl) + q * 8192;
-                if (S3) {
-#pragma unroll
-                    for (int s = 0; s < 4; ++s) mma_tf32(d, sdesc(su32(Rl) + s * 32), sdesc(cb + s * 32), id, s > 0);
-#pragma unroll
-                    for (int s = 0; s < 4; ++s) mma_tf32(d, sdesc(su32(Rs) + s * 32), sdesc(cbl + s * 32), id, 1);
-                }
-#pragma unroll
-                for (int s = 0; s < 4; ++s) mma_tf32(d, sdesc(su32(Rs) + s * 32), sdesc(cb + s * 32), id, S3 || s > 0);
-                mma_commit(su32(chunk_ready + n % NS));
-            };
-            auto issue_g2 = [&](int n) {
-                const int q = n % CPS, sb = (n / CPS) & 1;
-                const uint32_t kn = su32(KnT) + ((n / CPS) % NK) * 8192, kd = su32(KdT) + ((n / CPS) % NK) * 8192;
-                const uint32_t pb = su32(Ps) + (n % NP) * 16384, qb = su32(Qs) + (n % NP) * 16384;
-                if (RW) {
-                    const uint32_t id = idesc_bf16(RP, false);
-#pragma unroll
-                    for (int s = 0; s < 4; ++s) {
-                        const uint32_t acc = (q > 0 || s > 0) ? 1u : 0u;
-                        mma_bf16(t_w + 64 * sb, sdesc(pb + s * 32), sdesc(su32(CnT) + q * 4096 + s * 32), id, acc);
-                        if (DEN) mma_bf16(t_wd + 64 * sb, sdesc(qb + s * 32), sdesc(su32(CdT) + q * 4096 + s * 32), id, acc);
-                    }
-                }
-                if (M3) {
-                    const uint32_t id = idesc_bf16(CH, true);
-#pragma unroll
-                    for (int s = 0; s < 8; ++s) {
-                        const uint32_t ao = (s >> 2) * 4096 + (s & 3) * 32;
-                        const uint32_t acc = (n >= CPS || s > 0) ? 1u : 0u;
-                        mma_bf16(t_n3 + 64 * q, sdesc(kn + ao), sdesc(pb + s * 2048, 16384, 1024), id, acc);
-                        if (DEN) mma_bf16(t_n3d + 64 * q, sdesc(kd + ao), sdesc(qb + s * 2048, 16384, 1024), id, acc);
-                    }
-                }
-                mma_commit(su32(g2_done + (n % NP)));
-            };
-            fence_after();
-            issue_g1(0);
-            for (int n = 0; n < NC && !*abort_flag; ++n) {
-                const int m = n + 1;
-                if (m < NC) {
-                    bool ok = true;
-                    // X-hat buffer m & 1 was last read by chunk m - 2
-                    if (m >= 2) ok = wait(inputs_free + (m - 2) % NS, ((m - 2) / NS) & 1);
-                    if (ok && m % CPS == 0) ok = wait(r_full, (m / CPS - 1) & 1);
-                    if (!ok) break;
-                    fence_after();
-                    issue_g1(m);
-                }
-                if (!wait(p_full + (n % NP), (n / NP) & 1)) break;
+            const uint32_t idr = idesc_bf16(RP, false), idc = idesc_bf16(PAIR ? 2 * CH : CH, true);
+            const uint64_t dP = sdesc(su32(Ps)), dQ = sdesc(su32(Qs)), dCn = sdesc(su32(CnT)), dCd = sdesc(su32(CdT));
+            const uint64_t dPm = sdesc(su32(Ps), 16384, 1024), dQm = sdesc(su32(Qs), 16384, 1024);
+            const uint64_t dKn = sdesc(su32(KnT)), dKd = sdesc(su32(KdT));
+            for (int n = 0; n < NC; ++n) {
+                const int s = n / CPS, q = n % CPS, pb = n % NP;
+                if (!wait(p_full + pb, (n / NP) & 1)) break;
+                if (M3 && q == 0 && !wait(k_full + s % NK, (s / NK) & 1)) break;
                 fence_after();
-                issue_g2(n);
+                const uint32_t po = (uint32_t)pb * 1024u;  // P / Q buffer (16 KB) in 16-byte units
+                if (RW) {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const uint32_t acc = (q > 0 || k > 0) ? 1u : 0u;
+                        mma_bf16(t_w + 64 * (s & 1), dP + po + 2 * k, dCn + q * 256 + 2 * k, idr, acc);
+                        if (DEN) mma_bf16(t_wd + 64 * (s & 1), dQ + po + 2 * k, dCd + q * 256 + 2 * k, idr, acc);
+                    }
+                }
+                if (M3 && (!PAIR || (n & 1))) {
+                    // one chunk (N = 64), or the pair n - 1, n (N = 128: the two P buffers are
+                    // the operand's two 64-column atoms, 16 KB apart)
+                    const int qq = PAIR ? q - 1 : q;
+                    const uint32_t pp = PAIR ? po - 1024u : po;
+                    const uint32_t ko = (uint32_t)(s % NK) * 512u;
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        const uint32_t ao = ko + (k >> 2) * 256 + (k & 3) * 2;
+                        const uint32_t acc = (s > 0 || k > 0) ? 1u : 0u;
+                        mma_bf16(t_n3 + 64 * qq, dKn + ao, dPm + pp + k * 128, idc, acc);
+                        if (DEN) mma_bf16(t_n3d + 64 * qq, dKd + ao, dQm + pp + k * 128, idc, acc);
+                    }
+                    if (PAIR) mma_commit(su32(g2_done + (n - 1) % NP));
+                }
+                if (!PAIR || (n & 1)) mma_commit(su32(g2_done + pb));
+                if (M3 && q == CPS - 1) mma_commit(su32(k_free + s % NK));  // KR of slab s read once done
             }
         }
         __syncwarp();
+    } else if (builder) {
+        // ---- builder warps: R and KRn^T / KRd^T of every slab, one slab ahead -------------
+        const int bt = t - (EW + 64);
+        for (int s = 0; s < NSL; ++s) {
+            const int i = i0 + s;
+            if (s >= NR && !wait(r_free + s % NR, ((s - NR) / NR) & 1)) break;
+            {
+                // R [128 rows][32 ranks] TF32 (hi / lo): thread bt writes rows bt and bt + 64
+                float *rh = Rs + (s % NR) * 4096, *rl = Rl + (s % NR) * 4096;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int rr = bt + 64 * h, jj = j0 + rr;
+#pragma unroll 2
+                    for (int q = 0; q < 8; ++q) {
+                        float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                        if (jj < J) {
+                            if (RX) {
+                                v = __ldg(reinterpret_cast<const float4 *>(a.rrow + ((int64_t)i * J + jj) * RP) + q);
+                            } else {
+                                const float4 ai = __ldg(reinterpret_cast<const float4 *>(a.rec[0] + (int64_t)i * RP) + q);
+                                const float4 bj = __ldg(reinterpret_cast<const float4 *>(a.rec[1] + (int64_t)jj * RP) + q);
+                                v = make_float4(ai.x * bj.x, ai.y * bj.y, ai.z * bj.z, ai.w * bj.w);
+                            }
+                        }
+                        const float h0 = tf32_rna(v.x), h1 = tf32_rna(v.y), h2 = tf32_rna(v.z), h3 = tf32_rna(v.w);
+                        *reinterpret_cast<float4 *>(rh + swf(rr, 4 * q)) = make_float4(h0, h1, h2, h3);
+                        if (S3)
+                            *reinterpret_cast<float4 *>(rl + swf(rr, 4 * q)) =
+                                make_float4(tf32_rna(v.x - h0), tf32_rna(v.y - h1), tf32_rna(v.z - h2), tf32_rna(v.w - h3));
+                    }
+                }
+            }
+            fence_async_smem();
+            arrive(r_full + s % NR);
+            if (M3) {
+                if (s >= NK && !wait(k_free + s % NK, ((s - NK) / NK) & 1)) break;
+                // KRn^T / KRd^T [32 ranks][128 rows] BF16: thread bt owns rank bt % 32 and the
+                // 64 rows 64 (bt / 32) .., written as eight 16-byte stores each
+                const int kr_r = bt & 31, kr_j = 64 * (bt >> 5);
+                const float an = RX ? 1.0f : __ldg(a.num[0] + (int64_t)i * RP + kr_r);
+                const float ad = (RX || !DEN) ? 1.0f : __ldg(a.den[0] + (int64_t)i * RP + kr_r);
+                __nv_bfloat16 *kn = KnT + (s % NK) * 4096 + (kr_j >> 6) * 2048, *kd = KdT + (s % NK) * 4096 + (kr_j >> 6) * 2048;
+#pragma unroll 1
+                for (int g = 0; g < 8; ++g) {
+                    float vn[8], vd[8];
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        const int jj = j0 + kr_j + 8 * g + e;
+                        const bool v = jj < J;
+                        const int64_t o = RX ? ((int64_t)i * J + jj) * RP + kr_r : (int64_t)jj * RP + kr_r;
+                        vn[e] = v ? __ldg((RX ? a.nrow : a.num[1]) + o) : 0.0f;
+                        vd[e] = (v && DEN) ? __ldg((RX ? a.drow : a.den[1]) + o) : 0.0f;
+                    }
+                    *reinterpret_cast<uint4 *>(kn + swh(kr_r, 8 * g)) = pack8(vn, an);
+                    if (DEN) *reinterpret_cast<uint4 *>(kd + swh(kr_r, 8 * g)) = pack8(vd, ad);
+                }
+                fence_async_smem();
+                arrive(k_full + s % NK);
+            }
+        }
     } else {
         // ---- epilogue warps ---------------------------------------------------------------
-        auto fold = [&](int i) {  // modes 1 and 2 from W of slab i (its contractions complete)
-            const uint32_t wb = 64 * ((i - i0) & 1);
-            float w[RS], wd[RS];
+        auto fold = [&](int s, const float *an, const float *ad) {  // modes 1 and 2 from W of slab offset s
+            const int i = i0 + s;
+            const uint32_t wb = 64 * (s & 1);
+            float w[8], wd[8];
 #pragma unroll
-            for (int r = 0; r < RS; ++r) w[r] = wd[r] = 0.0f;
+            for (int r = 0; r < 8; ++r) w[r] = wd[r] = 0.0f;
             if (!__any_sync(0xffffffffu, *abort_flag != 0)) {  // warp-uniform before tcgen05.ld
-                tmem_ld<RS>(t_w + wb + lane_off + r0, w);
-                if (DEN) tmem_ld<RS>(t_wd + wb + lane_off + r0, wd);
+                tmem_ld8(t_w + wb + lane_off + rf, w);
+                if (DEN) tmem_ld8(t_wd + wb + lane_off + rf, wd);
             }
             if (RX) {  // W rows of slab i for this column block: [kb][i * J + j][RP] partials
                 if (jv && !*abort_flag) {
-                    const int64_t o = (((int64_t)kb * a.I + i) * J + j) * RP + r0;
+                    const int64_t o = (((int64_t)kb * a.I + i) * J + j) * RP + rf;
 #pragma unroll
-                    for (int q = 0; q < RS / 4; ++q) {
+                    for (int q = 0; q < 2; ++q) {
                         reinterpret_cast<float4 *>(a.p1n + o)[q] = make_float4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
                         if (DEN)
                             reinterpret_cast<float4 *>(a.p1d + o)[q] =
@@ -666,121 +678,110 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
                 return;
             }
             if (M2) {
-                const float *an = srow + (i & 3) * 96 + 32 + r0, *ad = an + 32;
 #pragma unroll
-                for (int r = 0; r < RS; ++r) {
+                for (int r = 0; r < 8; ++r) {
                     acc2[r] = fmaf(an[r], w[r], acc2[r]);
                     if (DEN) acc2d[r] = fmaf(ad[r], wd[r], acc2d[r]);
                 }
             }
             if (M1) {
 #pragma unroll
-                for (int r = 0; r < RS; ++r) {
+                for (int r = 0; r < 8; ++r) {
                     w[r] *= bn[r];
                     if (DEN) wd[r] *= bd[r];
                 }
                 // one partial per warp (its 32 rows of the tile), summed later in fixed order
-                const float sr = reduce_scatter<RS>(w);
-                const float sd = DEN ? reduce_scatter<RS>(wd) : 0.0f;
-                if (lane < RS && !*abort_flag) {
-                    const int64_t slot = (((int64_t)(jt * a.n_kb + kb) * 4 + quarter) * a.I + i) * RP + r0 + lane;
+                const float sr = reduce_scatter<8>(w);
+                const float sd = DEN ? reduce_scatter<8>(wd) : 0.0f;
+                if (lane < 8 && !*abort_flag) {
+                    const int64_t slot = (((int64_t)(jt * a.n_kb + kb) * 4 + quarter) * a.I + i) * RP + rf + lane;
                     a.p1n[slot] = sr;
                     if (DEN) a.p1d[slot] = sd;
                 }
             }
         };
+        // W of slab s is folded by group 1 at chunk CPS (s + 1) + 1 and by group 0 at
+        // CPS (s + 1) + 2, after the contractions of the slab's last chunk L = CPS (s + 1) - 1
+        // are complete (the P-buffer wait covers chunk L when NP = 2, else an explicit wait;
+        // the barrier cannot have moved on by two phases, since chunk L + NP's contraction
+        // needs a P tile of this chunk or a later one).  W of slab s is rewritten only by slab
+        // s + 2's first contraction, issued after this chunk's P tile.
+        int fold_next = 0;
+        auto fold_chunk = [&](int s) { return CPS * (s + 1) + 2 - grp; };
         // shared-memory offsets of this thread's X and P / Q entries within a stage / tile
         int xo[CW / 4], po[CW / 8];
 #pragma unroll
-        for (int g = 0; g < CW / 4; ++g) xo[g] = ((CW * cg) >> 5) * 4096 + swf(row, ((CW * cg) & 31) + 4 * g);
+        for (int g = 0; g < CW / 4; ++g) xo[g] = half * 4096 + swf(row, 4 * g);
 #pragma unroll
-        for (int g = 0; g < CW / 8; ++g) po[g] = swh(row, CW * cg + 8 * g);
-        int xs = 0;        // ring slot of chunk n
-        uint32_t xph = 0;  // parity of its phase, (n / NS) & 1
-        for (int n = 0; n < NC; ++n) {
-            const int i = i0 + n / CPS, q = n % CPS;
+        for (int g = 0; g < CW / 8; ++g) po[g] = swh(row, CW * half + 8 * g);
+        float ocarry = 0.0f;  // objective of this thread's last few chunks, FP32
+        int ocount = 0;
+        for (int n = grp; n < NC; n += 2) {
+            const int s = n / CPS, q = n % CPS;
             const int pb = n % NP;
-            if (n >= NP) wait(g2_done + pb, ((n - NP) / NP) & 1);  // P tile pb free again
-            if (q == 0 && n > 0) {
-                // slab boundary: rows of slab i + 2 staged; KRn^T of slab i written into the
-                // buffer last read by the contractions of slab i - NK, which are complete (the
-                // wait above covers chunk n - 1 or n - 2, and MMAs complete in order)
-                if (M3 && NK == 1 && NP == 2) {
-                    wait(g2_done + ((n - 1) % NP), ((n - 1) / NP) & 1);
-                }
-                fence_after();
-                epi_sync();  // rows of slab i + 1 (stored at the previous boundary) visible
-                if (t < 96 && i + 2 < i1) {
-                    if (!RX) srow[((i + 2) & 3) * 96 + t] = rnext;
-                    if (i + 3 < i1 && !RX) rnext = row_val(i + 3);
-                }
-                if (M3) {
-                    slab_kr(i);
-                    if (RX && i + 1 < i1) kx_load(i + 1);
+            const bool fold_now = RW && fold_next < s && fold_chunk(fold_next) <= n;
+            float an[8], ad[8];  // the folded slab's factor row, loaded before the waits
+            if (fold_now && M2 && !RX) {
+#pragma unroll
+                for (int r = 0; r < 8; ++r) {
+                    an[r] = __ldg(a.num[0] + (int64_t)(i0 + fold_next) * RP + rf + r);
+                    ad[r] = DEN ? __ldg(a.den[0] + (int64_t)(i0 + fold_next) * RP + rf + r) : 0.0f;
                 }
             }
-            if (RW && q == 1 && n > CPS) {
-                // fold slab i - 1: its last contraction (chunk n - 2) is complete, as the
-                // P-tile wait above covers chunk n - NP >= n - 2; W of slab i - 1 is rewritten
-                // by slab i + 1, whose contractions start only after this chunk's P tile
+            if (n >= NP) wait(g2_done + pb, ((n - NP) / NP) & 1);  // P tile pb free again
+            if (fold_now) {
+                const int last = CPS * (fold_next + 1) - 1;
+                if (n - NP < last) wait(g2_done + last % NP, (last / NP) & 1);
                 fence_after();
-                fold(i - 1);
+                fold(fold_next++, an, ad);
                 fence_before();
             }
-            const bool ready = __all_sync(0xffffffffu, wait(chunk_ready + xs, xph));
+            const bool ready = __all_sync(0xffffffffu, wait(chunk_ready + n % NS, (n / NS) & 1));
             fence_after();
-            float xh[CW], xv[CW];
+            // the thread's 32 columns as two halves of 16: X-hat of both from TMEM under one
+            // wait, X of each half from shared memory just before its powers
+            float xh[CW], xv[CW / 2];
             if (ready) {  // warp-uniform before tcgen05.ld
-                tmem_ld<CW>(t_d1 + 64 * (n & 1) + lane_off + CW * cg, xh);
+                const uint32_t ta = t_d1 + 64 * (n & 1) + lane_off + CW * half;
+                tmem_ld16x2(ta, ta + 16, xh);
             } else {
 #pragma unroll
                 for (int c = 0; c < CW; ++c) xh[c] = 0.0f;
             }
-            {
-                // the X stage holds two 128 x 32 halves; this group's columns lie in one
-                const float *xa = Xs + xs * 8192;
-#pragma unroll
-                for (int g = 0; g < CW / 4; ++g) {
-                    const float4 v = *reinterpret_cast<const float4 *>(xa + xo[g]);
-                    xv[4 * g] = v.x; xv[4 * g + 1] = v.y; xv[4 * g + 2] = v.z; xv[4 * g + 3] = v.w;
-                }
-            }
-            fence_before();
-            arrive(inputs_free + xs);
-            if (++xs == NS) {
-                xs = 0;
-                xph ^= 1;
-            }
-            if (q == CPS - 1 && n + 1 < NC) {
-                // this chunk's GEMM1 is complete, so R can take slab i + 1 (needed by GEMM1 of
-                // the next chunk, which the issuer starts once every warp has arrived)
-                slab_rows(i + 1);
-                if (RX && i + 2 < i1) rx_load(i + 2);
-                fence_async_smem();
-                arrive(r_full);
-            }
-            __nv_bfloat16 *pa = Ps + pb * 8192;
-            __nv_bfloat16 *qa = Qs + pb * 8192;
-            const int kc = k0 + CH * q + CW * cg;
-            float o1 = 0.0f, o2 = 0.0f;
-            float2 u1 = make_float2(0.0f, 0.0f), u2 = make_float2(0.0f, 0.0f);  // packed KL sums
-            // full strip of a valid row: no per-entry masks
-            auto body = [&](auto full_tag) {
-                constexpr bool FULL = decltype(full_tag)::value;
+            const float *xa = Xs + (n % NS) * 8192;
+            auto load_x = [&](int h) {
 #pragma unroll
                 for (int g = 0; g < CW / 8; ++g) {
+                    const float4 v = *reinterpret_cast<const float4 *>(xa + xo[4 * h + g]);
+                    xv[4 * g] = v.x; xv[4 * g + 1] = v.y; xv[4 * g + 2] = v.z; xv[4 * g + 3] = v.w;
+                }
+            };
+            __nv_bfloat16 *pa = Ps + pb * 8192;
+            __nv_bfloat16 *qa = Qs + pb * 8192;
+            const int kc0 = k0 + CH * q + CW * half;
+            float o1 = 0.0f, o2 = 0.0f;
+            float2 u1 = make_float2(0.0f, 0.0f), u2 = make_float2(0.0f, 0.0f);  // packed KL sums
+            // powers of half h (columns kc0 + 16 h ..); full strip of a valid row: no masks
+            auto body = [&](auto full_tag, int h) {
+                constexpr bool FULL = decltype(full_tag)::value;
+                const int kc = kc0 + 16 * h;
+                const float *xhh = xh + 16 * h;
+#pragma unroll
+                for (int g = 0; g < 2; ++g) {
                     float pv[8], qv[8];
                     if (FULL && BK == BK_KL) {
-                        // the KL point function on pairs of entries
+                        // the KL point function on pairs of entries; P = x / y + 1e-30 keeps
+                        // the logarithm of an x = 0 entry finite (0 * lg2(1e-30) = 0)
 #pragma unroll
                         for (int c = 0; c < 8; c += 2) {
                             const float2 x2 = make_float2(xv[8 * g + c], xv[8 * g + c + 1]);
-                            const float2 y2 = make_float2(fmaxf(xh[8 * g + c], a.eps), fmaxf(xh[8 * g + c + 1], a.eps));
-                            const float2 P2 = mul2(x2, make_float2(mufu_rcp(y2.x), mufu_rcp(y2.y)));
+                            const float2 y2 = make_float2(fmaxf(xhh[8 * g + c], a.eps), fmaxf(xhh[8 * g + c + 1], a.eps));
+                            const float2 P2 = fma2(x2, make_float2(mufu_rcp(y2.x), mufu_rcp(y2.y)),
+                                                   make_float2(1e-30f, 1e-30f));
                             pv[c] = P2.x;
                             pv[c + 1] = P2.y;
                             if (OBJ) {
-                                const float2 l2 = make_float2(mufu_lg2(fmaxf(P2.x, 1e-30f)), mufu_lg2(fmaxf(P2.y, 1e-30f)));
+                                const float2 l2 = make_float2(mufu_lg2(P2.x), mufu_lg2(P2.y));
                                 u1 = fma2(x2, l2, u1);
                                 u2 = add2(u2, sub2(y2, x2));
                             }
@@ -790,7 +791,7 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
                     for (int c = 0; c < 8; ++c) {
                         float x = xv[8 * g + c];
                         if (BK == BK_IS) x = fmaxf(x, a.eps_x);
-                        const float y = fmaxf(xh[8 * g + c], a.eps);
+                        const float y = fmaxf(xhh[8 * g + c], a.eps);
                         if (FULL) {
                             point<BK, OBJ>(a.beta, x, y, pv[c], qv[c], o1, o2);
                         } else {
@@ -802,54 +803,67 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
                             if (OBJ && v) { o1 += e1; o2 += e2; }
                         }
                     }
-                    __nv_bfloat162 h0 = __floats2bfloat162_rn(pv[0], pv[1]), h1 = __floats2bfloat162_rn(pv[2], pv[3]);
-                    __nv_bfloat162 h2 = __floats2bfloat162_rn(pv[4], pv[5]), h3 = __floats2bfloat162_rn(pv[6], pv[7]);
-                    uint4 u;
-                    u.x = *reinterpret_cast<uint32_t *>(&h0); u.y = *reinterpret_cast<uint32_t *>(&h1);
-                    u.z = *reinterpret_cast<uint32_t *>(&h2); u.w = *reinterpret_cast<uint32_t *>(&h3);
-                    *reinterpret_cast<uint4 *>(pa + po[g]) = u;
-                    if (DEN) {
-                        h0 = __floats2bfloat162_rn(qv[0], qv[1]); h1 = __floats2bfloat162_rn(qv[2], qv[3]);
-                        h2 = __floats2bfloat162_rn(qv[4], qv[5]); h3 = __floats2bfloat162_rn(qv[6], qv[7]);
-                        u.x = *reinterpret_cast<uint32_t *>(&h0); u.y = *reinterpret_cast<uint32_t *>(&h1);
-                        u.z = *reinterpret_cast<uint32_t *>(&h2); u.w = *reinterpret_cast<uint32_t *>(&h3);
-                        *reinterpret_cast<uint4 *>(qa + po[g]) = u;
-                    }
+                    *reinterpret_cast<uint4 *>(pa + po[2 * h + g]) = pack8(pv, 1.0f);
+                    if (DEN) *reinterpret_cast<uint4 *>(qa + po[2 * h + g]) = pack8(qv, 1.0f);
                 }
             };
-            if (jv && kc + CW <= K) body(std::true_type{});
-            else body(std::false_type{});
-            if (BK == BK_KL) {
-                o1 += u1.x + u1.y;
-                o2 += u2.x + u2.y;
+            load_x(0);
+            if (jv && kc0 + 16 <= K) body(std::true_type{}, 0);
+            else body(std::false_type{}, 0);
+            load_x(1);
+            fence_before();
+            arrive(inputs_free + n % NS);
+            if (jv && kc0 + 32 <= K) body(std::true_type{}, 1);
+            else body(std::false_type{}, 1);
+            if (OBJ) {
+                if (BK == BK_KL) {
+                    o1 += u1.x + u1.y;
+                    o2 += u2.x + u2.y;
+                }
+                ocarry += obj_combine<BK>(a.beta, o1, o2);
+                if (++ocount == 4) {  // FP64 once per 128 entries of the thread
+                    obj_acc += (double)ocarry;
+                    ocarry = 0.0f;
+                    ocount = 0;
+                }
             }
-            const float objf = OBJ ? obj_combine<BK>(a.beta, o1, o2) : 0.0f;
-            if (OBJ) obj_acc += (double)objf;
             fence_async_smem();
             arrive(p_full + pb);
         }
+        if (OBJ) obj_acc += (double)ocarry;
         if (NC > 0) {
-            wait(g2_done + (NC - 1) % NP, ((NC - 1) / NP) & 1);
+            wait(g2_done + (NC - 1) % NP, ((NC - 1) / NP) & 1);  // every contraction complete
             fence_after();
-            if (RW) fold(i1 - 1);
+            if (RW) {
+                while (fold_next < NSL) {
+                    float an[8], ad[8];
+#pragma unroll
+                    for (int r = 0; r < 8; ++r) {
+                        an[r] = (M2 && !RX) ? __ldg(a.num[0] + (int64_t)(i0 + fold_next) * RP + rf + r) : 0.0f;
+                        ad[r] = (M2 && DEN && !RX) ? __ldg(a.den[0] + (int64_t)(i0 + fold_next) * RP + rf + r) : 0.0f;
+                    }
+                    fold(fold_next++, an, ad);
+                }
+            }
         }
         // ---- CTA outputs ------------------------------------------------------------------
         const bool good = !__any_sync(0xffffffffu, *abort_flag != 0);
         if (M2 && jv && !RX) {
-            const int64_t base = ((int64_t)(kb * a.n_is + is) * J + j) * RP + r0;
+            const int64_t base = ((int64_t)(kb * a.n_is + is) * J + j) * RP + rf;
 #pragma unroll
-            for (int r = 0; r < RS; ++r) {
+            for (int r = 0; r < 8; ++r) {
                 a.p2n[base + r] = acc2[r];
                 if (DEN) a.p2d[base + r] = acc2d[r];
             }
         }
         if (M3 && quarter == 0) {
+            const int cg4 = warp >> 2;
             const int64_t base = (int64_t)(jt * a.n_is + is) * K;
 #pragma unroll 1
-            for (int g = 0; g < KB / (32 * CG); ++g) {
+            for (int g = 0; g < KB / 128; ++g) {
                 float v[32], vd[32];
                 const bool have = good && NC > 0;
-                const int cb = (KB / CG) * cg + 32 * g;
+                const int cb = (KB / 4) * cg4 + 32 * g;
                 if (have) {
                     tmem_ld32(t_n3 + cb, v);
                     if (DEN) tmem_ld32(t_n3d + cb, vd);
@@ -869,7 +883,7 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
             if (lane == 0) dred[warp] = v;
-            epi_sync();
+            asm volatile("bar.sync 1, %0;\n" :: "n"(EW) : "memory");
             if (t == 0) {
                 double s2 = 0.0;
                 for (int w = 0; w < EW / 32; ++w) s2 += dred[w];
@@ -911,6 +925,10 @@ cudaError_t launch_t(const Cp3Plan &p, const Cp3Args &a, cudaStream_t s) {
     auto k = cp3_pass_tc<MS, BK, S3, RX, KB>;
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total);
     if (e != cudaSuccess) return e;
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, k);
+    if (e != cudaSuccess) return e;
+    if (fa.maxThreadsPerBlock < NT) return cudaErrorLaunchOutOfResources;  // registers x NT beyond the SM
     k<<<p.grid, NT, L.total, s>>>(map, a);
     return cudaGetLastError();
 }
@@ -945,7 +963,7 @@ cudaError_t launch_bk(const Cp3Plan &p, const Cp3Args &a, int ms, cudaStream_t s
         case PM_M2: return launch_t<PM_M2, BK, S3, false>(p, a, s);
         case PM_M3: return launch_t<PM_M3, BK, S3, false>(p, a, s);
         case PM_M1 | PM_M2 | PM_M3 | PM_OBJ:
-            if (BK == BK_KL) return launch_t<PM_M1 | PM_M2 | PM_M3 | PM_OBJ, BK_KL, S3, false>(p, a, s);
+            if constexpr (BK == BK_KL) return launch_t<PM_M1 | PM_M2 | PM_M3 | PM_OBJ, BK_KL, S3, false>(p, a, s);
             return cudaErrorInvalidValue;
         default: return cudaErrorInvalidValue;
     }

@@ -361,7 +361,12 @@ int tune_plan(ntf_ctx *ctx, const ntf_tensor *X, CpDense &s, const ntf_opts &o, 
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (rc) return rc == NTF_ERR_CUDA ? fail(ctx, rc, "autotuning launch failed") : rc;
+    if (rc == NTF_ERR_CUDA) {
+        char prev[sizeof(ctx->err)];
+        snprintf(prev, sizeof(prev), "%s", ctx->err);
+        return fail(ctx, rc, "autotuning launch failed: %s", prev);
+    }
+    if (rc) return rc;
     s.plan = ntf::cp3_plan(s.I, s.J, s.K, s.RP, ctx->num_sms, model.KB, best);
     s.plan.s3 = model.s3;
     s.tune.clear();

@@ -281,6 +281,10 @@ int ntf_coo_stable_perm(ntf_ctx *ctx, const int32_t *keys, int64_t nnz, int64_t 
  * The caller owns X, factors and core (device memory) and must keep them alive and
  * untouched until the job's result has been polled; factors and core are updated in
  * place.  Server functions are thread-safe; each job uses the device of the server.
+ * While jobs run, a slot stream may be capturing its job's graph: other threads of the process
+ * must not call cudaDeviceSynchronize (or anything else that synchronizes the whole device)
+ * until ntf_server_poll(..., wait_all = 1) has returned; synchronizing their own streams or
+ * events is fine (the slot streams are non-blocking).
  * --------------------------------------------------------------------------------- */
 typedef struct ntf_server ntf_server;
 

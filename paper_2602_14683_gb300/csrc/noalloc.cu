@@ -2,9 +2,9 @@
 //
 // The regular entry points keep their scratch (padded factor copies, per-CTA partial
 // sums) in workspaces that a context grows with cudaMalloc.  Some callers cannot allocate
-// device memory at call time: code that runs while a CUDA graph is being captured, a
-// serving process whose device memory is carved out up front by another framework's
-// allocator, or an embedded caller with a fixed memory budget.  For them this file keeps
+// device memory at call time: a serving process whose device memory is carved out up
+// front by another framework's allocator, or an embedded caller held to a fixed memory
+// budget, where a cudaMalloc inside the library would fail or take memory already given out.  For them this file keeps
 // the scratch in one file-scope __device__ array of fixed size, which the driver creates
 // when the library's module is loaded on a device and keeps until the process exits.
 #include <mutex>

@@ -1,8 +1,9 @@
 """The allocation-free objective entry point (ntf_cp_beta_div_noalloc) against the regular
 one (ntf_beta_div), through the C ABI.
 
-Who needs it: callers that cannot allocate device memory at call time (a CUDA graph being
-captured, a process whose device memory belongs to another allocator or a fixed budget).
+Who needs it: callers that cannot allocate device memory at call time (a process whose
+device memory belongs to another framework's allocator, or one held to a fixed budget, where
+a cudaMalloc inside the library would fail or take memory already given out).
 The entry point keeps its scratch in a fixed file-scope device array instead of a context
 workspace.  This file is collected last on purpose, and passes alone in a fresh process as
 well as after the other tests.
@@ -38,7 +39,8 @@ def _call(ntf, X, beta, A, out):
 def test_noalloc_matches_regular_entry_point_twice():
     ntf = _ntf()
     import torch
-    cases = [((60, 50, 40), 5, 1.0, 0), ((9, 150, 70), 32, 0.5, 1)]
+    # ranks 5, 32 and 48 (padded to 8, 32 and 64 columns in the scratch array)
+    cases = [((60, 50, 40), 5, 1.0, 0), ((9, 150, 70), 32, 0.5, 1), ((20, 70, 33), 48, 1.5, 2)]
     for dims, R, beta, seed in cases:  # two calls in a row share the scratch array
         X, _ = synth.cp_dense(dims, R, seed=seed, kind="gamma_noise")
         A = synth.init_factors(dims, R, seed=seed + 7)

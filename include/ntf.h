@@ -98,7 +98,20 @@ typedef struct {
                       otherwise; Tucker: NTF_ERR_UNSUPPORTED when the last run's core extent
                       exceeds 64).  Ignored at N = 3.  Results depend on the cut only through
                       the order of floating-point sums. */
+    int cache;     /* J-CoMM at beta != 1, dense 3-way CP on the tensor-core passes: whether the
+                      reference-powered tensors P~ = X (.) X~^(beta-2), Q~ = X~^(beta-1) of an outer
+                      iteration (Section 5.3; Algorithm 2) are kept.  NTF_CACHE_AUTO (0): kept
+                      (with autotune = 1: the choice is timed once per shape and beta class);
+                      NTF_CACHE_NONE: every inner block pass recomputes X~ from the reference;
+                      NTF_CACHE_BF16: the first pass writes the BF16 P~ / Q~ tiles its
+                      contractions consume (2 + 2 bytes per entry of context workspace) and every
+                      later pass of the outer iteration contracts them without reading X.  The
+                      two modes give the same results bit for bit.  Ignored elsewhere. */
 } ntf_opts;
+
+#define NTF_CACHE_AUTO 0
+#define NTF_CACHE_NONE 1
+#define NTF_CACHE_BF16 2
 
 /* Fills *o with the defaults shown above. */
 void ntf_opts_default(ntf_opts *o);
@@ -125,6 +138,15 @@ int ntf_pass_timing(ntf_ctx *ctx, double *total_ms, int64_t *launches);
  * and clears that word, and returns NTF_OK or NTF_ERR_TIMEOUT (the results of the calls
  * since the last check are then invalid). */
 int ntf_device_status(ntf_ctx *ctx, void *stream);
+/* Testing aid for the bounded waits above (the paper has no counterpart).  polls > 0 sets
+ * the number of polls after which a wait of the context's tensor-core passes gives up
+ * (polls <= 0 restores the built-in limit, seconds at worst); with probe != 0, each such
+ * pass first waits on a barrier that nothing arrives on, so that this wait runs out before
+ * the pass has issued any copy or MMA, and the pass then aborts as a real timeout would
+ * (status word set, TMEM freed, no further work issued).  Results of passes run with the
+ * probe on are invalid; ntf_device_status reports NTF_ERR_TIMEOUT for them.
+ * NTF_ERR_ARG for a NULL context. */
+int ntf_debug_wait_limit(ntf_ctx *ctx, int polls, int probe);
 
 /* One B-CoMM sweep for CP (Algorithm 1; Theorem "CP block multiplicative update";
  * CPContr of Section 6.1): for n = 1..N in order, rebuild Xhat from the current

@@ -47,7 +47,7 @@ class Result(C.Structure):
 
 class Opts(C.Structure):
     _fields_ = [("eps", C.c_double), ("eps_x", C.c_double), ("inner_L", C.c_int), ("precision", C.c_int),
-                ("autotune", C.c_int), ("merge", C.c_int)]
+                ("autotune", C.c_int), ("merge", C.c_int), ("cache", C.c_int)]
 
 
 if not os.path.exists(LIB_PATH):
@@ -64,6 +64,7 @@ _sig = {
     "ntf_set_pass_timing": (C.c_int, [_P, C.c_int]),
     "ntf_pass_timing": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "ntf_device_status": (C.c_int, [_P, _P]),
+    "ntf_debug_wait_limit": (C.c_int, [_P, C.c_int, C.c_int]),
     "ntf_cp_mu_sweep": (C.c_int, [_P, C.POINTER(Tensor), C.c_float, C.c_int, C.POINTER(_P), C.POINTER(Opts), _P, _P]),
     "ntf_cp_mu_sweep_extrap": (C.c_int, [_P, C.POINTER(Tensor), C.c_float, C.c_int, C.POINTER(_P), C.POINTER(_P),
                                          C.c_float, C.c_float, C.c_float, C.POINTER(Opts), _P, _P]),
@@ -140,6 +141,11 @@ class Context:
         device-side wait gave up since the last check."""
         self.check(_lib.ntf_device_status(self.h, _stream(stream)))
 
+    def debug_wait_limit(self, polls=0, probe=False):
+        """Testing aid: polls before a bounded wait gives up (0: built-in), and the timeout
+        probe (every tensor-core pass aborts on a wait that runs out before it issues work)."""
+        self.check(_lib.ntf_debug_wait_limit(self.h, int(polls), 1 if probe else 0))
+
     def check(self, rc):
         if rc != NTF_OK:
             raise NtfError(rc, _lib.ntf_last_error(self.h).decode(errors="replace"))
@@ -199,15 +205,20 @@ def _ptrs(tensors, name):
     return (C.c_void_p * len(tensors))(*[t.data_ptr() for t in tensors])
 
 
-def make_opts(eps=1e-12, eps_x=1e-12, inner_L=1, precision="fp32", autotune=False, merge=None):
+CACHE_MODES = {"auto": 0, "none": 1, "bf16": 2}
+
+
+def make_opts(eps=1e-12, eps_x=1e-12, inner_L=1, precision="fp32", autotune=False, merge=None, cache="auto"):
     """merge: None, or (a, b) cutting the modes of an order N >= 4 tensor into the runs
-    [0, a), [a, b), [b, N) of the 3-way view."""
+    [0, a), [a, b), [b, N) of the 3-way view.  cache: "auto", "none" or "bf16" (J-CoMM's
+    reference-powered tensors at beta != 1 on the tensor-core passes)."""
     o = Opts()
     _lib.ntf_opts_default(C.byref(o))
     o.eps, o.eps_x, o.inner_L = float(eps), float(eps_x), int(inner_L)
     o.autotune = 1 if autotune else 0
     o.merge = 0 if merge is None else 16 * int(merge[0]) + int(merge[1])
     o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    o.cache = CACHE_MODES[cache] if isinstance(cache, str) else int(cache)
     return o
 
 

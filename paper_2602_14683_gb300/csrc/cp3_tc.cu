@@ -46,6 +46,18 @@ cudaError_t launch_x_map(const Cp3Args &a, CUtensorMap *map) {
     return cudaSuccess;
 }
 
+cudaError_t cache_map(void *base, const Cp3Args &a, CUtensorMap *map) {
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return cudaErrorNotSupported;
+    const cuuint64_t dims[3] = {(cuuint64_t)a.K, (cuuint64_t)a.J, (cuuint64_t)a.I};
+    const cuuint64_t strides[2] = {(cuuint64_t)a.kp * 2, (cuuint64_t)a.kp * 2 * (cuuint64_t)a.J};
+    const cuuint32_t box[3] = {64, 128, 1}, es[3] = {1, 1, 1};
+    if (enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
+    return cudaSuccess;
+}
+
 }  // namespace tc
 
 bool cp3_tc_eligible(int RP, int K, const float *X) {

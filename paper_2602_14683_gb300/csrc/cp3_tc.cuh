@@ -68,7 +68,7 @@ constexpr int PF = 6;      // X chunks prefetched into L2 ahead of the shared-me
 
 struct Layout {
     int x, p, q, r, rl, c, cl, cnt, cdt, knt, kdt, misc, total;
-    int ns;  // X stages
+    int ns;  // X stages (2)
     int np;  // P / Q buffers (2: one per epilogue group; 4: two per group)
     int nk;  // KRn^T / KRd^T buffers
     int nr;  // R buffers
@@ -97,7 +97,8 @@ __host__ __device__ constexpr Layout make_layout(bool rows, bool m3, bool den, b
     if (layout_bytes(rows, m3, den, s3, 2, 2, 1, 2, kb) <= kMax) L.nr = 2;
     if (m3 && layout_bytes(rows, m3, den, s3, 2, 2, 2, L.nr, kb) <= kMax) L.nk = 2;
     if (layout_bytes(rows, m3, den, s3, 2, 4, L.nk, L.nr, kb) <= kMax) L.np = 4;
-    if (layout_bytes(rows, m3, den, s3, 3, L.np, L.nk, L.nr, kb) <= kMax) L.ns = 3;
+    // two X stages: chunk n uses slot n % 2, so each slot serves one epilogue group, whose parity
+    // wait on it then always follows its own wait on the slot's previous phase
     int o = 0;
     L.x = o; o += L.ns * 32768;
     L.p = o; o += L.np * 16384;
@@ -178,6 +179,20 @@ __device__ __forceinline__ void tmem_ld8(uint32_t addr, float *v) {
 #pragma unroll
     for (int c = 0; c < 8; ++c) v[c] = __uint_as_float(r[c]);
 }
+// a 16-column load whose registers are only read after tmem_ld_wait16 on them: the wait
+// names them as operands, so no use can be scheduled before it
+__device__ __forceinline__ void tmem_ld16_issue(uint32_t addr, uint32_t *r) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                 : "r"(addr));
+}
+__device__ __forceinline__ void tmem_ld_wait16(uint32_t *r) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
+                 :: "memory");
+}
 // two 16-column loads under one wait
 __device__ __forceinline__ void tmem_ld16x2(uint32_t addr0, uint32_t addr1, float *v) {
     uint32_t r[32];
@@ -203,7 +218,7 @@ __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::be
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
 
-constexpr int WAIT_LIMIT = 1 << 26;  // polls (seconds at worst) before a wait gives up
+constexpr int WAIT_LIMIT = 1 << 22;  // polls (a second or so at worst) before a wait gives up
 
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
     for (int it = 0; it < WAIT_LIMIT; ++it) {
@@ -228,6 +243,15 @@ __device__ __forceinline__ int swh(int row, int k) { return row * 64 + ((((k >> 
 __device__ __forceinline__ void tma_2d(const CUtensorMap *map, uint32_t dst, uint32_t bar, int x, int y) {
     asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n"
                  :: "r"(dst), "l"(map), "r"(x), "r"(y), "r"(bar) : "memory");
+}
+// shared -> global tensor store (bulk group); elements outside the tensor are not written
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap *map, uint32_t src, int x, int y, int z) {
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];\n"
+                 :: "l"(map), "r"(x), "r"(y), "r"(z), "r"(src) : "memory");
+}
+__device__ __forceinline__ void tma_3d(const CUtensorMap *map, uint32_t dst, uint32_t bar, int x, int y, int z) {
+    asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];\n"
+                 :: "r"(dst), "l"(map), "r"(x), "r"(y), "r"(z), "r"(bar) : "memory");
 }
 __device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap *map, int x, int y) {
     asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];\n" :: "l"(map), "r"(x), "r"(y) : "memory");
@@ -360,8 +384,10 @@ __device__ __forceinline__ uint4 pack8(const float *v, float s) {
     return u;
 }
 
-template <int MS, int BK, bool S3, bool RX, int KB>
-__global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUtensorMap xmap, const Cp3Args a) {
+template <int MS, int BK, bool S3, bool RX, int KB, bool WC = false>
+__global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUtensorMap xmap,
+                                                      const __grid_constant__ CUtensorMap pcmap,
+                                                      const __grid_constant__ CUtensorMap qcmap, const Cp3Args a) {
     constexpr bool DEN = BK != BK_KL;
     constexpr bool M1 = (MS & PM_M1) != 0, M2 = (MS & PM_M2) != 0, M3 = (MS & PM_M3) != 0;
     constexpr bool OBJ = (MS & PM_OBJ) != 0, RW = M1 || M2;
@@ -392,7 +418,8 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
     uint64_t *bars = (uint64_t *)(sm + L.misc);
     uint64_t *chunk_ready = bars, *inputs_free = bars + 3, *p_full = bars + 6, *g2_done = bars + 10;
     uint64_t *r_free = bars + 14, *r_full = bars + 16, *k_free = bars + 18, *k_full = bars + 20;
-    constexpr int NBAR = 22;
+    uint64_t *probe_bar = bars + 22;  // nothing arrives on it (the timeout probe)
+    constexpr int NBAR = 23;
     uint32_t *tslot = (uint32_t *)(sm + L.misc + 192);
     volatile int *abort_flag = (volatile int *)(sm + L.misc + 200);
     double *dred = (double *)(sm + L.misc + 256);  // [EW / 32] (128 bytes)
@@ -417,9 +444,10 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
     const int NC = CPS * NSL;
     const int rf = 16 * grp + 8 * half;  // this thread's 8 ranks of the folds
 
+    const int wlim = a.wait_limit > 0 ? a.wait_limit : WAIT_LIMIT;
     auto wait = [&](uint64_t *bar, uint32_t phase) -> bool {
         const uint32_t ba = su32(bar);
-        for (int it = 0; it < WAIT_LIMIT; ++it) {
+        for (int it = 0; it < wlim; ++it) {
             uint32_t done;
             asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
                          : "=r"(done) : "r"(ba), "r"(phase) : "memory");
@@ -476,8 +504,9 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
     if (t == EW) {
         for (int q = 0; q < NBAR; ++q) {
             // chunk_ready: expect_tx + GEMM1 commit; g2_done, r_free, k_free: one commit;
-            // r_full, k_full: the two builder warps; inputs_free, p_full: a group's eight warps
-            const uint32_t cnt = q < 3 ? 2 : (q >= 10 && q < 16) || q == 18 || q == 19 ? 1 : q >= 16 ? 2 : GW / 32;
+            // r_full, k_full: the two builder warps; inputs_free, p_full: a group's eight warps;
+            // probe_bar: one (never given)
+            const uint32_t cnt = q < 3 ? 2 : q < 10 ? GW / 32 : q < 16 ? 1 : q < 18 ? 2 : q < 20 ? 1 : q < 22 ? 2 : 1;
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" :: "r"(su32(bars + q)), "r"(cnt));
         }
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
@@ -522,18 +551,24 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
             // GEMM1 descriptors: A = R rows (K-major, 4 K-steps of 8 TF32), B = C columns
             const uint32_t id1 = idesc_tf32(CH);
             const uint64_t dR = sdesc(su32(Rs)), dRl = sdesc(su32(Rl)), dC = sdesc(su32(Cs)), dCl = sdesc(su32(Cl));
-            for (int c = 0; c < NS && c < NC; ++c) load_x(c);
-            for (int c = NS; c < NS + PF && c < NC; ++c) prefetch_x(c);
-            for (int n = 0; n < NC; ++n) {
+            // the timeout probe: one bounded wait that runs out before anything is issued
+            const bool go = !a.timeout_probe || wait(probe_bar, 0);
+            if (go)
+                for (int c = 0; c < NS && c < NC; ++c) load_x(c);
+            if (go)
+                for (int c = NS; c < NS + PF && c < NC; ++c) prefetch_x(c);
+            for (int n = 0; n < NC && go; ++n) {
                 if (n >= 2) {
-                    // chunk n - 2 has been read: X-hat buffer n % 2 and ring slot (n - 2) % NS free
-                    if (!wait(inputs_free + (n - 2) % NS, ((n - 2) / NS) & 1)) break;
+                    // chunk n - 2 has been read: X-hat buffer n % 2 and ring slot (n - 2) % NS
+                    // free; the X chunk first (the longer path), then GEMM1 of chunk n
+                    if (!wait(inputs_free + (n - 2) % NS, ((n - 2) / NS) & 1) || *abort_flag) break;
                     const int c = n - 2 + NS;
                     if (c < NC) load_x(c);
                     if (c + PF < NC) prefetch_x(c + PF);
                 }
                 const int s = n / CPS, q = n % CPS;
                 if (q == 0 && !wait(r_full + s % NR, (s / NR) & 1)) break;
+                if (*abort_flag) break;  // nothing is issued once a wait has given up
                 fence_after();
                 const uint32_t d = t_d1 + 64 * (n & 1);
                 const uint32_t ro = (uint32_t)(s % NR) * 1024u;  // 16 KB R buffer, in 16-byte units
@@ -562,6 +597,7 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
                 const int s = n / CPS, q = n % CPS, pb = n % NP;
                 if (!wait(p_full + pb, (n / NP) & 1)) break;
                 if (M3 && q == 0 && !wait(k_full + s % NK, (s / NK) & 1)) break;
+                if (*abort_flag) break;  // nothing is issued once a wait has given up
                 fence_after();
                 const uint32_t po = (uint32_t)pb * 1024u;  // P / Q buffer (16 KB) in 16-byte units
                 if (RW) {
@@ -587,40 +623,91 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
                     }
                     if (PAIR) mma_commit(su32(g2_done + (n - 1) % NP));
                 }
+                if (WC) {
+                    // the chunk's P~ / Q~ tiles into the cache by TMA; they must be read out of
+                    // shared memory before the buffer's g2_done, which the epilogue waits on
+                    // before it rewrites the buffer
+                    fence_async_smem();
+                    tma_store_3d(&pcmap, su32(Ps) + pb * 16384, k0 + CH * q, j0, i0 + s);
+                    if (DEN) tma_store_3d(&qcmap, su32(Qs) + pb * 16384, k0 + CH * q, j0, i0 + s);
+                    asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+                    asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
+                }
                 if (!PAIR || (n & 1)) mma_commit(su32(g2_done + pb));
                 if (M3 && q == CPS - 1) mma_commit(su32(k_free + s % NK));  // KR of slab s read once done
             }
+            if (WC) asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");  // the cache writes done
         }
         __syncwarp();
     } else if (builder) {
         // ---- builder warps: R and KRn^T / KRd^T of every slab, one slab ahead -------------
-        const int bt = t - (EW + 64);
+        // thread bt owns the tile rows 2 bt and 2 bt + 1 (R rows; KR^T columns); every global
+        // load of a 16-rank half is issued before its first use (one latency per half)
+        const int bt = t - (EW + 64), jr0 = 2 * bt;
+        const bool v0 = j0 + jr0 < J, v1 = j0 + jr0 + 1 < J;
+        const float4 z4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        auto mul4 = [](float4 x, float4 y) { return make_float4(x.x * y.x, x.y * y.y, x.z * y.z, x.w * y.w); };
+        // rank half h of rows j0 + jr0, + 1 of slab i: A_i (.) B_j from the factors f0 / f1, or
+        // the explicit rows xr[i * J + j]
+        auto rows2 = [&](const float *f0, const float *f1, const float *xr, int i, int h, float4 *x0, float4 *x1) {
+            if (RX) {
+                const float4 *p = reinterpret_cast<const float4 *>(xr + ((int64_t)i * J + j0 + jr0) * RP + 16 * h);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    x0[q] = v0 ? __ldg(p + q) : z4;
+                    x1[q] = v1 ? __ldg(p + RP / 4 + q) : z4;
+                }
+            } else {
+                const float4 *pa = reinterpret_cast<const float4 *>(f0 + (int64_t)i * RP + 16 * h);
+                const float4 *pb = reinterpret_cast<const float4 *>(f1 + (int64_t)(j0 + jr0) * RP + 16 * h);
+                float4 av[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    av[q] = __ldg(pa + q);
+                    x0[q] = v0 ? __ldg(pb + q) : z4;
+                    x1[q] = v1 ? __ldg(pb + RP / 4 + q) : z4;
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    x0[q] = mul4(av[q], x0[q]);
+                    x1[q] = mul4(av[q], x1[q]);
+                }
+            }
+        };
+        // KR^T entries (r, jr0) and (r, jr0 + 1) for the 16 ranks of half h, as BF16 pairs
+        auto store_kt = [&](__nv_bfloat16 *kt, int h, const float4 *x0, const float4 *x1) {
+            __nv_bfloat16 *base = kt + (jr0 >> 6) * 2048;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float a0[4] = {x0[q].x, x0[q].y, x0[q].z, x0[q].w}, a1[4] = {x1[q].x, x1[q].y, x1[q].z, x1[q].w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const __nv_bfloat162 pr = __floats2bfloat162_rn(a0[e], a1[e]);
+                    *reinterpret_cast<__nv_bfloat162 *>(base + swh(16 * h + 4 * q + e, jr0 & 63)) = pr;
+                }
+            }
+        };
         for (int s = 0; s < NSL; ++s) {
             const int i = i0 + s;
             if (s >= NR && !wait(r_free + s % NR, ((s - NR) / NR) & 1)) break;
             {
-                // R [128 rows][32 ranks] TF32 (hi / lo): thread bt writes rows bt and bt + 64
+                // R [128 rows][32 ranks] TF32 (hi / lo)
                 float *rh = Rs + (s % NR) * 4096, *rl = Rl + (s % NR) * 4096;
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    const int rr = bt + 64 * h, jj = j0 + rr;
-#pragma unroll 2
-                    for (int q = 0; q < 8; ++q) {
-                        float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-                        if (jj < J) {
-                            if (RX) {
-                                v = __ldg(reinterpret_cast<const float4 *>(a.rrow + ((int64_t)i * J + jj) * RP) + q);
-                            } else {
-                                const float4 ai = __ldg(reinterpret_cast<const float4 *>(a.rec[0] + (int64_t)i * RP) + q);
-                                const float4 bj = __ldg(reinterpret_cast<const float4 *>(a.rec[1] + (int64_t)jj * RP) + q);
-                                v = make_float4(ai.x * bj.x, ai.y * bj.y, ai.z * bj.z, ai.w * bj.w);
-                            }
+                    float4 x0[4], x1[4];
+                    rows2(a.rec[0], a.rec[1], a.rrow, i, h, x0, x1);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+#pragma unroll
+                        for (int e = 0; e < 2; ++e) {
+                            const float4 v = e ? x1[q] : x0[q];
+                            const float h0 = tf32_rna(v.x), h1 = tf32_rna(v.y), h2 = tf32_rna(v.z), h3 = tf32_rna(v.w);
+                            *reinterpret_cast<float4 *>(rh + swf(jr0 + e, 16 * h + 4 * q)) = make_float4(h0, h1, h2, h3);
+                            if (S3)
+                                *reinterpret_cast<float4 *>(rl + swf(jr0 + e, 16 * h + 4 * q)) =
+                                    make_float4(tf32_rna(v.x - h0), tf32_rna(v.y - h1), tf32_rna(v.z - h2), tf32_rna(v.w - h3));
                         }
-                        const float h0 = tf32_rna(v.x), h1 = tf32_rna(v.y), h2 = tf32_rna(v.z), h3 = tf32_rna(v.w);
-                        *reinterpret_cast<float4 *>(rh + swf(rr, 4 * q)) = make_float4(h0, h1, h2, h3);
-                        if (S3)
-                            *reinterpret_cast<float4 *>(rl + swf(rr, 4 * q)) =
-                                make_float4(tf32_rna(v.x - h0), tf32_rna(v.y - h1), tf32_rna(v.z - h2), tf32_rna(v.w - h3));
                     }
                 }
             }
@@ -628,25 +715,16 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
             arrive(r_full + s % NR);
             if (M3) {
                 if (s >= NK && !wait(k_free + s % NK, ((s - NK) / NK) & 1)) break;
-                // KRn^T / KRd^T [32 ranks][128 rows] BF16: thread bt owns rank bt % 32 and the
-                // 64 rows 64 (bt / 32) .., written as eight 16-byte stores each
-                const int kr_r = bt & 31, kr_j = 64 * (bt >> 5);
-                const float an = RX ? 1.0f : __ldg(a.num[0] + (int64_t)i * RP + kr_r);
-                const float ad = (RX || !DEN) ? 1.0f : __ldg(a.den[0] + (int64_t)i * RP + kr_r);
-                __nv_bfloat16 *kn = KnT + (s % NK) * 4096 + (kr_j >> 6) * 2048, *kd = KdT + (s % NK) * 4096 + (kr_j >> 6) * 2048;
-#pragma unroll 1
-                for (int g = 0; g < 8; ++g) {
-                    float vn[8], vd[8];
+                // KRn^T / KRd^T [32 ranks][128 rows] BF16
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) {
-                        const int jj = j0 + kr_j + 8 * g + e;
-                        const bool v = jj < J;
-                        const int64_t o = RX ? ((int64_t)i * J + jj) * RP + kr_r : (int64_t)jj * RP + kr_r;
-                        vn[e] = v ? __ldg((RX ? a.nrow : a.num[1]) + o) : 0.0f;
-                        vd[e] = (v && DEN) ? __ldg((RX ? a.drow : a.den[1]) + o) : 0.0f;
+                for (int h = 0; h < 2; ++h) {
+                    float4 x0[4], x1[4];
+                    rows2(a.num[0], a.num[1], a.nrow, i, h, x0, x1);
+                    store_kt(KnT + (s % NK) * 4096, h, x0, x1);
+                    if (DEN) {
+                        rows2(a.den[0], a.den[1], a.drow, i, h, x0, x1);
+                        store_kt(KdT + (s % NK) * 4096, h, x0, x1);
                     }
-                    *reinterpret_cast<uint4 *>(kn + swh(kr_r, 8 * g)) = pack8(vn, an);
-                    if (DEN) *reinterpret_cast<uint4 *>(kd + swh(kr_r, 8 * g)) = pack8(vd, ad);
                 }
                 fence_async_smem();
                 arrive(k_full + s % NK);
@@ -700,22 +778,26 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
                 }
             }
         };
-        // W of slab s is folded by group 1 at chunk CPS (s + 1) + 1 and by group 0 at
-        // CPS (s + 1) + 2, after the contractions of the slab's last chunk L = CPS (s + 1) - 1
-        // are complete (the P-buffer wait covers chunk L when NP = 2, else an explicit wait;
-        // the barrier cannot have moved on by two phases, since chunk L + NP's contraction
-        // needs a P tile of this chunk or a later one).  W of slab s is rewritten only by slab
-        // s + 2's first contraction, issued after this chunk's P tile.
+        // W of slab s is folded by each group once the contractions of the slab's last chunk
+        // L = CPS (s + 1) - 1 are complete, and before slab s + 2's first contraction rewrites
+        // it (that contraction is issued after the P tile of chunk CPS (s + 2)).  Where that
+        // leaves room, a group folds at its first chunk n >= L + NP, whose own P-buffer wait
+        // (chunk n - NP) covers chunk L; otherwise group 1 folds at L + 2 and group 0 at L + 3
+        // after an explicit wait for chunk L (that barrier cannot have moved on by two phases:
+        // chunk L + NP's contraction needs a P tile of this chunk or a later one).
         int fold_next = 0;
-        auto fold_chunk = [&](int s) { return CPS * (s + 1) + 2 - grp; };
+        auto fold_chunk = [&](int s) {
+            const int last = CPS * (s + 1) - 1;
+            if (last + NP + 1 <= CPS * (s + 2)) return last + NP + ((grp ^ (last + NP)) & 1);
+            return last + 3 - grp;
+        };
         // shared-memory offsets of this thread's X and P / Q entries within a stage / tile
         int xo[CW / 4], po[CW / 8];
 #pragma unroll
         for (int g = 0; g < CW / 4; ++g) xo[g] = half * 4096 + swf(row, 4 * g);
 #pragma unroll
         for (int g = 0; g < CW / 8; ++g) po[g] = swh(row, CW * half + 8 * g);
-        float ocarry = 0.0f;  // objective of this thread's last few chunks, FP32
-        int ocount = 0;
+        float osum = 0.0f, ocomp = 0.0f;  // objective of this thread's chunks: compensated FP32 sum
         for (int n = grp; n < NC; n += 2) {
             const int s = n / CPS, q = n % CPS;
             const int pb = n % NP;
@@ -738,15 +820,18 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
             }
             const bool ready = __all_sync(0xffffffffu, wait(chunk_ready + n % NS, (n / NS) & 1));
             fence_after();
-            // the thread's 32 columns as two halves of 16: X-hat of both from TMEM under one
-            // wait, X of each half from shared memory just before its powers
-            float xh[CW], xv[CW / 2];
+            // the thread's 32 columns as two halves of 16: X-hat of the second half is loaded
+            // from TMEM while the first half's powers run; X of each half from shared memory
+            // just before its powers
+            float xh0[16], xh1[16], xv[CW / 2];
+            uint32_t xr1[16];
+            const uint32_t ta = t_d1 + 64 * (n & 1) + lane_off + CW * half;
             if (ready) {  // warp-uniform before tcgen05.ld
-                const uint32_t ta = t_d1 + 64 * (n & 1) + lane_off + CW * half;
-                tmem_ld16x2(ta, ta + 16, xh);
+                tmem_ld16(ta, xh0);
+                tmem_ld16_issue(ta + 16, xr1);
             } else {
 #pragma unroll
-                for (int c = 0; c < CW; ++c) xh[c] = 0.0f;
+                for (int c = 0; c < 16; ++c) xh0[c] = 0.0f;
             }
             const float *xa = Xs + (n % NS) * 8192;
             auto load_x = [&](int h) {
@@ -765,7 +850,7 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
             auto body = [&](auto full_tag, int h) {
                 constexpr bool FULL = decltype(full_tag)::value;
                 const int kc = kc0 + 16 * h;
-                const float *xhh = xh + 16 * h;
+                const float *xhh = h ? xh1 : xh0;
 #pragma unroll
                 for (int g = 0; g < 2; ++g) {
                     float pv[8], qv[8];
@@ -805,11 +890,15 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
                     }
                     *reinterpret_cast<uint4 *>(pa + po[2 * h + g]) = pack8(pv, 1.0f);
                     if (DEN) *reinterpret_cast<uint4 *>(qa + po[2 * h + g]) = pack8(qv, 1.0f);
+
                 }
             };
             load_x(0);
             if (jv && kc0 + 16 <= K) body(std::true_type{}, 0);
             else body(std::false_type{}, 0);
+            if (ready) tmem_ld_wait16(xr1);
+#pragma unroll
+            for (int c = 0; c < 16; ++c) xh1[c] = ready ? __uint_as_float(xr1[c]) : 0.0f;
             load_x(1);
             fence_before();
             arrive(inputs_free + n % NS);
@@ -820,19 +909,22 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
                     o1 += u1.x + u1.y;
                     o2 += u2.x + u2.y;
                 }
-                ocarry += obj_combine<BK>(a.beta, o1, o2);
-                if (++ocount == 4) {  // FP64 once per 128 entries of the thread
-                    obj_acc += (double)ocarry;
-                    ocarry = 0.0f;
-                    ocount = 0;
-                }
+                const float oy = obj_combine<BK>(a.beta, o1, o2) - ocomp;  // Kahan summation
+                const float ot = osum + oy;
+                ocomp = (ot - osum) - oy;
+                osum = ot;
             }
             fence_async_smem();
             arrive(p_full + pb);
         }
-        if (OBJ) obj_acc += (double)ocarry;
+        if (OBJ) obj_acc = (double)osum - (double)ocomp;
         if (NC > 0) {
-            wait(g2_done + (NC - 1) % NP, ((NC - 1) / NP) & 1);  // every contraction complete
+            // every contraction complete.  A parity wait on a barrier is valid only while the
+            // barrier's previous phase is complete and its next one is not: the last NP chunks
+            // (one per P buffer, none after them) are waited for in increasing order; the
+            // first one's previous phase (chunk NC - 2 NP) is covered by this thread's last
+            // P-buffer wait, each later one's by the wait before it (in-order completion)
+            for (int m = NC - NP > 0 ? NC - NP : 0; m < NC; ++m) wait(g2_done + m % NP, (m / NP) & 1);
             fence_after();
             if (RW) {
                 while (fold_next < NSL) {
@@ -895,9 +987,10 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
     __syncthreads();
     if (*abort_flag && t == EW) {
         // bounded waits (without the abort shortcut) for copies and MMAs still in flight
+        const int clim = wlim < (1 << 20) ? wlim : (1 << 20);
         for (int q = 0; q < NBAR; ++q) {
             for (int ph = 0; ph < 2; ++ph) {
-                for (int it = 0; it < (1 << 20); ++it) {
+                for (int it = 0; it < clim; ++it) {
                     uint32_t done;
                     asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
                                  : "=r"(done) : "r"(su32(bars + q)), "r"(ph) : "memory");
@@ -915,26 +1008,38 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
 }
 
 cudaError_t launch_x_map(const Cp3Args &a, CUtensorMap *map);
+// P~ / Q~ cache as a 3-D BF16 tensor [I][J][K] with row stride kp; boxes of 64 x 128 x 1 with the
+// 128-byte swizzle of the operand buffers (rows past J and columns past K are outside the tensor)
+cudaError_t cache_map(void *base, const Cp3Args &a, CUtensorMap *map);
 
-template <int MS, int BK, bool S3, bool RX, int KB = KBLK>
+template <int MS, int BK, bool S3, bool RX, int KB = KBLK, bool WC = false>
 cudaError_t launch_t(const Cp3Plan &p, const Cp3Args &a, cudaStream_t s) {
     constexpr Layout L = make_layout((MS & (PM_M1 | PM_M2)) != 0, (MS & PM_M3) != 0, BK != BK_KL, S3, KB);
-    CUtensorMap map;
+    CUtensorMap map, pm{}, qm{};
     cudaError_t e = launch_x_map(a, &map);
+    if (e == cudaSuccess && WC) e = cache_map(a.pc, a, &pm);
+    if (e == cudaSuccess && WC && BK != BK_KL) e = cache_map(a.qc, a, &qm);
     if (e != cudaSuccess) return e;
-    auto k = cp3_pass_tc<MS, BK, S3, RX, KB>;
+    auto k = cp3_pass_tc<MS, BK, S3, RX, KB, WC>;
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total);
     if (e != cudaSuccess) return e;
     cudaFuncAttributes fa;
     e = cudaFuncGetAttributes(&fa, k);
     if (e != cudaSuccess) return e;
     if (fa.maxThreadsPerBlock < NT) return cudaErrorLaunchOutOfResources;  // registers x NT beyond the SM
-    k<<<p.grid, NT, L.total, s>>>(map, a);
+    k<<<p.grid, NT, L.total, s>>>(map, pm, qm, a);
     return cudaGetLastError();
 }
 
 template <int BK, bool S3>
 cudaError_t launch_bk(const Cp3Plan &p, const Cp3Args &a, int ms, cudaStream_t s) {
+    if (a.pc) {  // J-CoMM first pass that also writes the P~ / Q~ cache (beta != 1)
+        if constexpr (BK != BK_KL) {
+            if (p.KB == KBLK && ms == (PM_M1 | PM_OBJ)) return launch_t<PM_M1 | PM_OBJ, BK, S3, false, KBLK, true>(p, a, s);
+            if (p.KB == KBLK && ms == PM_M1) return launch_t<PM_M1, BK, S3, false, KBLK, true>(p, a, s);
+        }
+        return cudaErrorInvalidValue;
+    }
     if (a.rrow) {  // explicit rows (Tucker): W rows out, or the column contraction
         if (p.KB != KBLK) return cudaErrorInvalidValue;
         switch (ms) {

@@ -27,6 +27,8 @@ struct ntf_ctx {
     std::vector<cudaEvent_t> ev;  // pairs: ev[2k] start, ev[2k+1] stop
     size_t ev_used = 0;           // pairs in use
     int *status = nullptr;        // device status word (bounded waits that gave up)
+    int wait_limit = 0;           // polls of a bounded wait (0: the kernels' built-in limit)
+    int timeout_probe = 0;        // next tensor-core passes: one wait that runs out, nothing issued
 };
 
 namespace {
@@ -81,6 +83,8 @@ int check_common(ntf_ctx *ctx, const ntf_tensor *X, float beta, const ntf_opts &
     if (o.inner_L < 1) return fail(ctx, NTF_ERR_ARG, "inner_L must be >= 1");
     if (o.precision != NTF_PREC_FP32 && o.precision != NTF_PREC_TF32 && o.precision != NTF_PREC_3XTF32)
         return fail(ctx, NTF_ERR_ARG, "unknown precision %d", o.precision);
+    if (o.cache != NTF_CACHE_AUTO && o.cache != NTF_CACHE_NONE && o.cache != NTF_CACHE_BF16)
+        return fail(ctx, NTF_ERR_ARG, "unknown cache mode %d", o.cache);
     if (X->kind != NTF_DENSE && X->kind != NTF_COO) return fail(ctx, NTF_ERR_ARG, "unknown tensor kind");
     if (X->order < 2 || X->order > 8) return fail(ctx, NTF_ERR_UNSUPPORTED, "order %d not in 2..8", X->order);
     for (int n = 0; n < X->order; ++n)
@@ -133,6 +137,12 @@ struct TuneKey {
 };
 std::mutex g_tune_mu;
 std::map<TuneKey, int> g_tuned;
+// J-CoMM cache choice (beta != 1, tensor-core passes): per shape / precision / beta class, the
+// timed extra cost of the cache-writing first pass and one recomputing / contraction-only pass
+struct CacheTimes {
+    float write_extra_ms, recompute_ms, contract_ms;
+};
+std::map<TuneKey, CacheTimes> g_cache_tuned;
 
 // candidate slab splits: the cost model's, and the splits whose grids come closest to 1..4
 // waves of one CTA per SM from below and above
@@ -260,10 +270,22 @@ int launch_pass(ntf_ctx *ctx, const CpDense &s, const ntf::Cp3Args &a_in, int ms
             return fail(ctx, NTF_ERR_UNSUPPORTED, "pass variant %d/%d has no tensor-core kernel", ms, den);
         ntf::Cp3Args a = a_in;
         a.err = ctx->status;
+        a.wait_limit = ctx->wait_limit;
+        a.timeout_probe = ctx->timeout_probe;
         NTF_CUDA(ntf::cp3_tc_launch(s.plan, a, ms, den, st));
     } else {
         NTF_CUDA(ntf::cp3_launch(s.plan, a_in, ms, den, st));
     }
+    return NTF_OK;
+}
+
+int launch_contract(ntf_ctx *ctx, const CpDense &s, const ntf::Cp3Args &a_in, int ms, cudaStream_t st) {
+    PassTimer t(ctx, st);
+    ntf::Cp3Args a = a_in;
+    a.err = ctx->status;
+    a.wait_limit = ctx->wait_limit;
+    a.timeout_probe = ctx->timeout_probe;
+    NTF_CUDA(ntf::cp3_tc_contract_launch(s.plan, a, ms, st));
     return NTF_OK;
 }
 
@@ -414,6 +436,64 @@ struct JExtrap {
     float alpha, cap, delta;
 };
 
+// Times, once per key, the extra cost of the cache-writing first pass and one mode-2 pass of
+// each kind (the timing launches write only the partial-sum workspaces and the cache, which the
+// real passes overwrite).  Skipped during stream capture (the cache is then used).
+int tune_cache(ntf_ctx *ctx, const CpDense &s, const ntf::Cp3Args &a, const ntf::Cp3Args &c, float beta,
+               CacheTimes &out, cudaStream_t st) {
+    const TuneKey key{ctx->device, s.I, s.J, s.K, s.RP, s.tc, s.plan.s3, ntf::beta_kind(beta), -1};
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_cache_tuned.find(key);
+        if (it != g_cache_tuned.end()) {
+            out = it->second;
+            return NTF_OK;
+        }
+    }
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    NTF_CUDA(cudaStreamIsCapturing(st, &cap));
+    if (cap != cudaStreamCaptureStatusNone) {
+        out = CacheTimes{0.0f, 1.0f, 0.0f};
+        return NTF_OK;
+    }
+    cudaEvent_t ev[2];
+    NTF_CUDA(cudaEventCreate(&ev[0]));
+    if (cudaEventCreate(&ev[1]) != cudaSuccess) {
+        cudaEventDestroy(ev[0]);
+        return fail(ctx, NTF_ERR_CUDA, "event creation failed");
+    }
+    int rc = NTF_OK;
+    float t[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    // 0: first pass without, 1: with the cache outputs; 2: mode-2 recompute; 3: mode-2 contraction
+    for (int v = 0; v < 4 && !rc; ++v) {
+        auto go = [&]() {
+            if (v == 0) return launch_pass(ctx, s, a, ntf::PM_M1 | ntf::PM_OBJ, 1, st);
+            if (v == 1) return launch_pass(ctx, s, c, ntf::PM_M1 | ntf::PM_OBJ, 1, st);
+            if (v == 2) return launch_pass(ctx, s, a, ntf::PM_M2, 1, st);
+            return launch_contract(ctx, s, c, ntf::PM_M2, st);
+        };
+        if ((rc = go())) break;  // untimed
+        if (cudaEventRecord(ev[0], st) != cudaSuccess) { rc = NTF_ERR_CUDA; break; }
+        for (int r = 0; r < 2 && !rc; ++r) rc = go();
+        if (rc) break;
+        if (cudaEventRecord(ev[1], st) != cudaSuccess || cudaEventSynchronize(ev[1]) != cudaSuccess ||
+            cudaEventElapsedTime(&t[v], ev[0], ev[1]) != cudaSuccess)
+            rc = NTF_ERR_CUDA;
+    }
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    if (rc == NTF_ERR_CUDA) {
+        char prev[sizeof(ctx->err)];
+        snprintf(prev, sizeof(prev), "%s", ctx->err);
+        return fail(ctx, rc, "cache autotuning failed: %s", prev);
+    }
+    if (rc) return rc;
+    out = CacheTimes{(t[1] - t[0]) / 2, t[2] / 2, t[3] / 2};
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_cache_tuned[key] = out;
+    return NTF_OK;
+}
+
 int cp_dense_jcomm(ntf_ctx *ctx, const ntf_tensor *X, float beta, int R, float *const *factors,
                    const ntf_opts &o, double *objective_dev, cudaStream_t st, const JExtrap *xe = nullptr) {
     const int bk = ntf::beta_kind(beta);
@@ -503,16 +583,37 @@ int cp_dense_jcomm(ntf_ctx *ctx, const ntf_tensor *X, float beta, int R, float *
         for (int l = 0; l < o.inner_L; ++l)
             for (int n = 0; n < 3; ++n) NTF_CUDA(update(l, n));
     } else {
+        for (int m = 0; m < 3; ++m) {
+            a.rec[m] = s.Ft[m];
+            a.num[m] = s.C1[m];
+            a.den[m] = s.C2[m];
+        }
+        // Reference-powered tensors (Section 5.3): with the cache, the first pass also writes
+        // the BF16 P~ / Q~ its contractions consume and the other 3 L - 1 passes contract them
+        bool cache = s.plan.tc && o.cache != NTF_CACHE_NONE;
+        ntf::Cp3Args c = a;
+        if (cache) {
+            c.kp = (s.K + 7) & ~7;
+            const size_t bytes = sizeof(uint16_t) * (size_t)s.I * s.J * c.kp;
+            c.pc = ws_get(ctx, "cpPc", bytes);
+            c.qc = ws_get(ctx, "cpQc", bytes);
+            if (!c.pc || !c.qc) return fail(ctx, NTF_ERR_OOM, "P~ / Q~ cache allocation failed");
+            if (o.cache == NTF_CACHE_AUTO && o.autotune) {
+                CacheTimes ct{};
+                if ((rc = tune_cache(ctx, s, a, c, beta, ct, st))) return rc;
+                const int later = 3 * o.inner_L - 1;
+                cache = ct.write_extra_ms + later * ct.contract_ms < later * ct.recompute_ms;
+            }
+        }
         for (int l = 0; l < o.inner_L; ++l) {
             for (int n = 0; n < 3; ++n) {
-                for (int m = 0; m < 3; ++m) {
-                    a.rec[m] = s.Ft[m];
-                    a.num[m] = s.C1[m];
-                    a.den[m] = s.C2[m];
-                }
                 int ms = (n == 0 ? ntf::PM_M1 : n == 1 ? ntf::PM_M2 : ntf::PM_M3);
-                if (l == 0 && n == 0) ms |= ntf::PM_OBJ;
-                rc = launch_pass(ctx, s, a, ms, 1, st);
+                if (l == 0 && n == 0) {
+                    if (objective_dev) ms |= ntf::PM_OBJ;
+                    rc = launch_pass(ctx, s, cache ? c : a, ms, 1, st);
+                } else {
+                    rc = cache ? launch_contract(ctx, s, c, ms, st) : launch_pass(ctx, s, a, ms, 1, st);
+                }
                 if (rc) return rc;
                 NTF_CUDA(update(l, n));
             }
@@ -937,6 +1038,7 @@ void ntf_opts_default(ntf_opts *o) {
     o->precision = NTF_PREC_FP32;
     o->autotune = 0;
     o->merge = 0;
+    o->cache = NTF_CACHE_AUTO;
 }
 
 int ntf_ctx_create(ntf_ctx **out, int device) {
@@ -981,6 +1083,13 @@ int64_t ntf_launch_count(const ntf_ctx *c) { return c ? c->launches : 0; }
 int ntf_set_pass_timing(ntf_ctx *c, int enable) {
     if (!c) return NTF_ERR_ARG;
     c->timing = enable != 0;
+    return NTF_OK;
+}
+
+int ntf_debug_wait_limit(ntf_ctx *c, int polls, int probe) {
+    if (!c) return NTF_ERR_ARG;
+    c->wait_limit = polls > 0 ? polls : 0;
+    c->timeout_probe = probe != 0;
     return NTF_OK;
 }
 
@@ -1237,4 +1346,9 @@ int ctx_fail(ntf_ctx *c, int code, const char *msg) { return fail(c, code, "%s",
 void ctx_count(ntf_ctx *c, int n) { c->launches += n; }
 int ctx_num_sms(const ntf_ctx *c) { return c->num_sms; }
 int *ctx_status(ntf_ctx *c) { return c->status; }
+void ctx_wait_opts(ntf_ctx *c, Cp3Args &a) {
+    a.err = c->status;
+    a.wait_limit = c->wait_limit;
+    a.timeout_probe = c->timeout_probe;
+}
 }  // namespace ntf

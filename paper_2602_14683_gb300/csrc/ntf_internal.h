@@ -138,6 +138,12 @@ struct Cp3Args {
     float *p3n, *p3d;      // mode-3 partials [n_jt*n_is][K][RP]
     double *obj;           // per-CTA objective partials [grid]
     int *err;              // device status word: set non-zero when a bounded wait gives up
+    int wait_limit;        // polls before a bounded wait gives up (<= 0: the built-in limit)
+    int timeout_probe;     // 1: one wait on a barrier nothing arrives on, before any copy or MMA
+    // J-CoMM reference-powered tensors P~, Q~ as BF16 [I*J][kp] (kp = K rounded up to 8): the
+    // tensor-core pass writes them when pc is set; the contraction-only pass reads them
+    void *pc, *qc;
+    int kp;
 };
 
 struct Cp3Plan {
@@ -166,6 +172,10 @@ bool cp3_tc_eligible(int RP, int K, const float *X);
 bool cp3_tc_supported(int mode_set, int den, bool rx = false);
 cudaError_t cp3_tc_launch(const Cp3Plan &plan, const Cp3Args &a, int mode_set, int den,
                           cudaStream_t s);
+// Contraction-only pass over the cached BF16 P~ / Q~ (a.pc, a.qc, row stride a.kp) of a J-CoMM
+// outer iteration at beta != 1: mode_set one of PM_M1, PM_M2, PM_M3; same plan, partial-sum
+// layouts and results as the recomputing tensor-core pass.
+cudaError_t cp3_tc_contract_launch(const Cp3Plan &plan, const Cp3Args &a, int mode_set, cudaStream_t s);
 
 // ---------------------------------------------------------------------------------
 // Small kernels (epilogue.cu)

@@ -9,6 +9,7 @@ int ctx_fail(ntf_ctx *c, int code, const char *msg);
 void ctx_count(ntf_ctx *c, int n);
 int ctx_num_sms(const ntf_ctx *c);
 int *ctx_status(ntf_ctx *c);  // device status word of the bounded-wait kernels
+void ctx_wait_opts(ntf_ctx *c, Cp3Args &a);  // status word, wait limit and timeout probe of the context
 
 // previous iterate and weights of an outer-reference extrapolation (J-CoMM)
 struct TuckerExtrap {

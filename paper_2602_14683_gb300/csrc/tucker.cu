@@ -778,7 +778,7 @@ int rows_pass(ntf_ctx *ctx, TuckerWs &w, const ntf_tensor *X, const ntf_opts &o,
         const bool one = w.tplan.n_kb == 1;
         a.p1n = one ? w.Wn : w.Wpn;
         a.p1d = one ? w.Wd : w.Wpd;
-        a.err = ctx_status(ctx);
+        ctx_wait_opts(ctx, a);
         const bool kl = beta_kind(beta) == BK_KL;
         TK(cp3_tc_launch(w.tplan, a, PM_M1 | PM_M2 | (obj ? PM_OBJ : 0), kl ? 0 : 1, st));
         // W = sum over the column blocks, in block order
@@ -967,7 +967,7 @@ int mode3_pass(ntf_ctx *ctx, TuckerWs &w, const ntf_tensor *X, const ntf_opts &o
         a.n_is = w.tplan.n_is;
         a.p3n = w.pn3;
         a.p3d = w.pd3;
-        a.err = ctx_status(ctx);
+        ctx_wait_opts(ctx, a);
         const bool kl = beta_kind(beta) == BK_KL;
         TK(cp3_tc_launch(w.tplan, a, PM_M3, kl ? 0 : 1, st));
         if (kl) {

@@ -29,6 +29,9 @@ METRIC = "J-CoMM time-to-1e-4 rel objective vs FP32 block-MU; sweeps/s; served p
 DIMS = (512, 512, 512)
 RANK = 32
 BETA = 1.0
+# arithmetic of each precision option: FP32 CUDA-core passes, or TF32 (split TF32 for 3xtf32)
+# reconstruction with BF16 contraction operands and FP32 accumulation
+DTYPES = {"fp32": "f32", "tf32": "tf32+bf16", "3xtf32": "3xtf32+bf16"}
 WORKLOAD = ("dense CP 512x512x512 FP32, R=32, beta=1 (KL), J-CoMM outer iteration (L=1); "
             "Gamma(2,1) factors x Gamma(10,0.1) noise, U(0.1,1) init")
 
@@ -45,14 +48,16 @@ def parse():
     p.add_argument("--no-other", action="store_true",
                    help="skip the Tucker 400^3, sparse 3.3M-nonzero, 4-way CP / Tucker and 5-way Tucker "
                         "measurements")
-    p.add_argument("--serve-jobs", type=int, default=48,
+    p.add_argument("--serve-jobs", type=int, default=1000,
                    help="jobs of the serving-mix measurement in the default run (0: skip)")
     p.add_argument("--serve", action="store_true", help="print only the serving-mix line")
     p.add_argument("--slots", type=int, default=16)
+    p.add_argument("--c2-betas", default="0,0.5,1,1.5",
+                   help="betas of the C2 table (block-MU vs J-CoMM L = 1, 3; time to target at each)")
     p.add_argument("--profile-n", type=int, default=0,
                    help="profiling driver: three J-CoMM steps and three block-MU sweeps on an n^3, "
                         "R = 32, beta = 1 tensor at --precision, then exit (no measurement)")
-    p.add_argument("--profile-case", default="", choices=["", "tucker", "coo", "cp4", "tucker4", "tucker5"],
+    p.add_argument("--profile-case", default="", choices=["", "tucker", "coo", "cp4", "tucker4", "tucker5", "jcache"],
                    help="profiling driver: three block-MM sweeps and three J-CoMM iterations of the Tucker "
                         "400^3 workload, three J-CoMM iterations of the sparse 3.3M-nonzero workload, or "
                         "the 4-way CP / Tucker or 5-way Tucker measurements with one timed call per "
@@ -98,68 +103,118 @@ def profile_case(n, prec):
     return 0
 
 
-def run_serving(ntf, n_jobs, slots, seed=0, max_iters=200, rtol=1e-6):
+def profile_jcache(ntf, n=512, beta=1.5, L=3, iters=3):
+    """Small fixed launch sequence for ncu: J-CoMM outer iterations at beta = 3/2 with three inner
+    sweeps and the P~ / Q~ cache on a 512^3, R = 32 tensor (one cache-writing pass and eight
+    contraction-only passes per iteration)."""
+    import torch
+    g = torch.Generator(device="cuda").manual_seed(0)
+    X = torch.rand((n, n, n), device="cuda", generator=g) * 10 + 0.1
+    A = [torch.rand((n, 32), device="cuda", generator=g) * 0.9 + 0.1 for _ in range(3)]
+    obj = torch.zeros(1, dtype=torch.float64, device="cuda")
+    for _ in range(iters):
+        ntf.jcomm_outer(X, beta, A, objective=obj, precision="tf32", inner_L=L, cache="bf16")
+    torch.cuda.synchronize()
+    ntf.default_context().device_status()
+    print("profile case jcache n=%d objective %.6e" % (n, obj.item()))
+    return 0
+
+
+def run_serving(ntf, n_jobs, slots, seed=0, max_iters=200, rtol=1e-6, sweep=(0.5, 1.0, 1.2), sweep_jobs=None):
     """Serving mix (dense 3-way CP / Tucker jobs, dims log-uniform 16..256, rank / core dims
     4..32, beta in {1/2, 1, 3/2}, J-CoMM L = 1, stop at a 1e-6 relative objective change or
-    200 iterations).  A warm-up set of jobs (another seed) runs first, untimed, so that kernel
-    loading and the slots' first workspace allocations stay out of the figures.  Phase 1
-    submits a quarter of the jobs at once (data generated beforehand) to measure the
-    saturation throughput; phase 2 submits the rest as a Poisson stream at 0.8 x that rate.
-    Latency = completion - arrival (host clock)."""
+    200 iterations).  Every job's data and init are drawn on the device BEFORE any timed
+    phase, so the arrival loop only submits.  Phases: an untimed warm-up set (kernel loading,
+    first workspace sizes); a burst submitted at once to measure the saturation throughput;
+    the main run of n_jobs Poisson arrivals at 0.8 x saturation; then a load sweep at
+    0.5 / 1.0 / 1.2 x saturation (sweep_jobs each).  Latency = completion - SCHEDULED arrival
+    (host monotonic clock, the server's own clock), so a submit loop that falls behind its
+    schedule shows up as queueing.  No device-wide synchronisation happens while jobs run
+    (a slot stream may be capturing its graph)."""
     import torch
     import synth
-    jobs = synth.serving_jobs(n_jobs, seed=seed)
-    n1 = max(1, n_jobs // 4)
+    stream = torch.cuda.current_stream()
+    sweep_jobs = sweep_jobs or max(slots * 4, n_jobs // 5)
+
+    def gen(jobs):
+        data = [synth.job_data_torch(j) for j in jobs]
+        stream.synchronize()
+        return data
+
+    def drain(srv, expect):
+        out = []
+        while len(out) < expect:
+            got = srv.poll(wait_all=True, max_results=4096)
+            if not got:
+                break
+            out += got
+        return out
+
+    def submit(srv, j, d):
+        X, G, A = d
+        return srv.submit(X, j["beta"], A, core=G, rtol=rtol, max_iters=max_iters)
+
+    n_sat = max(slots * 4, n_jobs // 8)
+    warm = synth.serving_jobs(2 * slots, seed=seed + 7)
+    burst = synth.serving_jobs(n_sat, seed=seed + 11)
+    main_jobs = synth.serving_jobs(n_jobs, seed=seed)
+    sweeps = {f: synth.serving_jobs(sweep_jobs, seed=seed + 100 + k) for k, f in enumerate(sweep)}
+    d_warm, d_burst, d_main = gen(warm), gen(burst), gen(main_jobs)
+    d_sweep = {f: gen(js) for f, js in sweeps.items()}
     srv = ntf.Server(slots=slots)
-    for j in synth.serving_jobs(2 * slots, seed=seed + 7):
-        X, G, A = synth.job_data_torch(j)
-        srv.submit(X, j["beta"], A, core=G, rtol=rtol, max_iters=max_iters)
-    torch.cuda.synchronize()
-    srv.poll(wait_all=True)
-    data = [synth.job_data_torch(j) for j in jobs[:n1]]
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for j, (X, G, A) in zip(jobs[:n1], data):
-        srv.submit(X, j["beta"], A, core=G, rtol=rtol, max_iters=max_iters)
-    res1 = srv.poll(wait_all=True)
-    sat = n1 / (time.perf_counter() - t0)
-    del data
-    rate = 0.8 * sat
-    g = np.random.default_rng(seed + 1)
-    gaps = g.exponential(1.0 / rate, size=len(jobs) - n1)
-    t1 = time.perf_counter()
-    due = t1
-    for j, gap in zip(jobs[n1:], gaps):
-        X, G, A = synth.job_data_torch(j)
-        torch.cuda.synchronize()
-        due += gap
-        delay = due - time.perf_counter()
-        if delay > 0:
-            time.sleep(delay)
-        srv.submit(X, j["beta"], A, core=G, rtol=rtol, max_iters=max_iters)
-    res2 = srv.poll(wait_all=True)
-    wall = time.perf_counter() - t1
+    for j, d in zip(warm, d_warm):
+        submit(srv, j, d)
+    drain(srv, len(warm))
+    del d_warm
+    # saturation: every job of the burst submitted at once
+    t0 = time.monotonic()
+    for j, d in zip(burst, d_burst):
+        submit(srv, j, d)
+    res_b = drain(srv, len(burst))
+    sat = len(burst) / (max(r["t_done"] for r in res_b) - t0)
+    del d_burst
+
+    def poisson_run(jobs, data, rate, rng_seed):
+        gaps = np.random.default_rng(rng_seed).exponential(1.0 / rate, size=len(jobs))
+        sched = {}
+        start = time.monotonic()
+        due = start
+        lag = 0.0
+        for j, d, gap in zip(jobs, data, gaps):
+            due += gap
+            delay = due - time.monotonic()
+            if delay > 0:
+                time.sleep(delay)
+            lag = max(lag, time.monotonic() - due)
+            sched[submit(srv, j, d)] = due
+        res = drain(srv, len(jobs))
+        lat = np.array([r["t_done"] - sched[r["id"]] for r in res])
+        span = max(r["t_done"] for r in res) - start
+        return res, {"jobs": len(jobs), "offered_per_s": rate, "achieved_per_s": len(res) / span,
+                     "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+                     "max_submit_lag_s": lag, "ok": sum(1 for r in res if r["status"] == 0)}
+
+    res_m, main = poisson_run(main_jobs, d_main, 0.8 * sat, seed + 1)
+    del d_main
+    sweep_out = {}
+    for k, f in enumerate(sweep):
+        _, sweep_out["%gx" % f] = poisson_run(sweeps[f], d_sweep[f], f * sat, seed + 200 + k)
+        del d_sweep[f]
     srv.close()
-    lat = np.array([r["t_done"] - r["t_submit"] for r in res2])
-    its = np.array([r["iterations"] for r in res1 + res2])
-    ok = sum(1 for r in res1 + res2 if r["status"] == 0)
-    return {"jobs": n_jobs, "slots": slots, "saturation_solves_per_s": sat, "poisson_rate_per_s": rate,
-            "solves_per_s": len(res2) / wall, "p50_latency_s": float(np.percentile(lat, 50)) if lat.size else None,
-            "p99_latency_s": float(np.percentile(lat, 99)) if lat.size else None,
-            "mean_iterations": float(its.mean()), "completed_ok": ok,
+    its = np.array([r["iterations"] for r in res_b + res_m])
+    return {"jobs": n_jobs, "slots": slots, "saturation_solves_per_s": sat, "saturation_burst_jobs": len(burst),
+            "poisson_rate_per_s": main["offered_per_s"], "solves_per_s": main["achieved_per_s"],
+            "p50_latency_s": main["p50_latency_s"], "p99_latency_s": main["p99_latency_s"],
+            "max_submit_lag_s": main["max_submit_lag_s"], "completed_ok": main["ok"],
+            "mean_iterations": float(its.mean()), "load_sweep": sweep_out,
+            "latency_from": "scheduled arrival (Poisson), data pre-generated on the device",
             "mix": "dense 3-way CP/Tucker 50/50, dims log-uniform 16..256, rank/core 4..32, beta in {0.5,1,1.5}, "
                    "Poisson-noised low-rank data at mean 10, J-CoMM L=1, stop at 1e-6 rel change or 200 its"}
 
 
-def run_tucker_c3(ntf, ctx, peaks, iters=10, n=400, J=32, beta=1.5, seed=3, precisions=("fp32", "tf32", "3xtf32")):
-    """Dense Tucker 400 x 400 x 400, core 32 x 32 x 32, beta = 3/2: Gamma(2,1) core and
-    factors, model rescaled to mean 10, Poisson noise (drawn on the device, seeded); init
-    U(0.1, 1).  For each precision, times block-MM sweeps (core, then modes 1..3) and J-CoMM
-    outer iterations (L = 1), and reports the objective after the timed sweeps relative to
-    the FP32 CUDA-core path's.  Roofline per sweep: four passes over X (4 bytes per entry
-    each; FP32 path: 2J flops for Xhat and 2J for each of the P and Q contractions per
-    entry, against the derived FP32 FMA peak; tensor-core path: the bytes against the HBM
-    copy bandwidth)."""
+def c3_data(n=400, J=32, seed=3):
+    """C3 inputs: Gamma(2,1) core and factors, model rescaled to mean 10, Poisson noise
+    (drawn on the device, seeded); init U(0.1, 1)."""
     import torch
     torch.manual_seed(seed)
     dev = torch.device("cuda", torch.cuda.current_device())
@@ -172,6 +227,180 @@ def run_tucker_c3(ntf, ctx, peaks, iters=10, n=400, J=32, beta=1.5, seed=3, prec
     g = torch.Generator(device=dev).manual_seed(seed + 1)
     G0 = torch.rand((J, J, J), device=dev, generator=g) * 0.9 + 0.1
     A0 = [torch.rand((n, J), device=dev, generator=g) * 0.9 + 0.1 for _ in range(3)]
+    return X, G0, A0
+
+
+def c3_vs_oracle(ntf, ctx, T=4, beta=1.5, precisions=("fp32", "tf32", "3xtf32")):
+    """C3's accuracy metric: the per-iteration objective error of every precision against the
+    FP64 oracle on the 400^3 Tucker problem.  The GPU runs T block-MM sweeps from the shared
+    init and records the objective of each incoming iterate; the oracle (FP64, mode-n products
+    on the host's cores) runs the same T sweeps from the same FP32 inputs.  Reported:
+    |F_gpu(t) - F_ora(t)| / F_ora(t) for t = 0..T-1 (t = 0: the objective of the init only)."""
+    import torch
+    from oracle import tucker_modeprod as tm
+    X, G0, A0 = c3_data()
+    traj = {}
+    for prec in precisions:
+        G, A = G0.clone(), [a.clone() for a in A0]
+        F = torch.zeros(T, dtype=torch.float64, device=X.device)
+        for t in range(T):
+            ntf.tucker_mu_sweep(X, beta, G, A, objective=F[t:t + 1], ctx=ctx, precision=prec)
+        traj[prec] = F.cpu().numpy()
+    Xh = X.cpu().double()
+    Gh, Ah = G0.cpu().double().numpy(), [a.cpu().double().numpy() for a in A0]
+    del X
+    t0 = time.perf_counter()
+    F_ora = []
+    for t in range(T):
+        Gh, Ah, f = tm.tucker_mu_sweep(Xh, Gh, Ah, beta)
+        F_ora.append(f)
+    sec = time.perf_counter() - t0
+    F_ora = np.array(F_ora)
+    out = {"workload": "dense Tucker 400x400x400, core 32x32x32, beta=1.5, block-MM sweeps from the shared init",
+           "oracle": "FP64 mode-n products (oracle.tucker_modeprod), %d host threads, %.1f s per sweep"
+                     % (torch.get_num_threads(), sec / T),
+           "F_oracle": F_ora.tolist()}
+    for prec, F in traj.items():
+        rel = np.abs(F - F_ora) / F_ora
+        out[prec] = {"rel_err_per_iter": rel.tolist(), "max_rel_err": float(rel.max())}
+    return out
+
+
+def run_cp_c1(ntf, ctx, sweeps=100, dims=(60, 50, 40), R=5, seed=0):
+    """C1, the latency case: dense CP 60 x 50 x 40, R = 5, beta = 1, plain block-MU; X = CP model
+    with U(0.1, 1) factors rescaled to mean 10, Poisson; init U(0.1, 1).  The 100 sweeps are
+    enqueued back to back and timed with CUDA events on the stream (the 0.48 MB tensor stays in
+    L2, as it would in a user's loop); per precision, microseconds per sweep."""
+    import torch
+    import synth
+    dev = torch.device("cuda", torch.cuda.current_device())
+    Xn, _ = synth.cp_dense(dims, R, seed=seed, kind="uniform_poisson")
+    X = torch.tensor(Xn, dtype=torch.float32, device=dev)
+    A0 = [torch.tensor(a, dtype=torch.float32, device=dev) for a in synth.init_factors(dims, R, seed=seed + 1)]
+    obj = torch.zeros(1, dtype=torch.float64, device=dev)
+    out = {"workload": "dense CP 60x50x40, R=5, beta=1, block-MU, 100 sweeps"}
+    for prec in ("fp32", "tf32"):
+        A = [a.clone() for a in A0]
+        for _ in range(5):
+            ntf.cp_mu_sweep(X, 1.0, A, objective=obj, ctx=ctx, precision=prec)
+        A = [a.clone() for a in A0]
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(sweeps):
+            ntf.cp_mu_sweep(X, 1.0, A, objective=obj, ctx=ctx, precision=prec)
+        e1.record()
+        torch.cuda.synchronize()
+        us = e0.elapsed_time(e1) * 1e3 / sweeps
+        out[prec] = {"us_per_sweep": us, "sweeps_per_s": 1e6 / us, "objective_after_100": obj.item()}
+    return out
+
+
+def run_until(ntf, ctx, X, A0, beta, fn, prec, n_max, target, inner_L=1):
+    """Runs fn (a sweep or an outer iteration) from A0 until its objective first reaches
+    `target` (checked every 100 iterations on the device record) or n_max iterations.
+    Returns (objective per iteration, seconds per iteration, [min, max] ms per 100)."""
+    import torch
+    stream = torch.cuda.current_stream()
+    kw = {"inner_L": inner_L} if inner_L != 1 else {}
+    Fr = torch.zeros(n_max, dtype=torch.float64, device=X.device)
+    W_ = [a.clone() for a in A0]
+    for _ in range(3):  # untimed: workspaces sized for this method and precision
+        fn(X, beta, W_, objective=Fr[:1], ctx=ctx, precision=prec, autotune=True, **kw)
+    float(Fr[:2].min())  # the stopping check's reduction kernel loads here, not in the timed region
+    C_ = [a.clone() for a in A0]
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True)]
+    ev[0].record(stream)
+    t = 0
+    while t < n_max:
+        for _ in range(min(100, n_max - t)):
+            fn(X, beta, C_, objective=Fr[t:t + 1], ctx=ctx, precision=prec, autotune=True, **kw)
+            t += 1
+        ev.append(torch.cuda.Event(enable_timing=True))
+        ev[-1].record(stream)
+        if target is not None and float(Fr[:t].min()) <= target:
+            break
+    torch.cuda.synchronize()
+    chunks = [ev[k].elapsed_time(ev[k + 1]) for k in range(len(ev) - 1)]
+    return Fr[:t].cpu().numpy(), ev[0].elapsed_time(ev[-1]) / 1e3 / t, [round(min(chunks), 2), round(max(chunks), 2)]
+
+
+def ttt_summary(runs, fstar):
+    """Iterations and seconds to F*(1 + 1e-4), and to a relative objective change <= 1e-4."""
+    target = fstar * (1 + 1e-4)
+    res = {}
+    for name, (F, per, chunk_ms) in runs.items():
+        hit = np.nonzero(F <= target)[0]
+        rel = np.abs(np.diff(F)) / F[1:]
+        conv = np.nonzero(rel <= 1e-4)[0]
+        res[name] = {"iters": int(hit[0]) if hit.size else None,
+                     "seconds": float(hit[0] * per) if hit.size else None,
+                     "s_per_iter": per, "iters_run": int(F.size),
+                     "iters_rel_change_1e-4": int(conv[0]) + 1 if conv.size else None,
+                     "seconds_rel_change_1e-4": float((conv[0] + 1) * per) if conv.size else None,
+                     "final_rel_gap": float(F[-1] / fstar - 1.0), "ms_per_100_iters_min_max": chunk_ms}
+    return res
+
+
+def run_cp_c2(ntf, ctx, peaks, X, A0, prec, iters=10, betas=(0.0, 0.5, 1.0, 1.5), ttt_betas=(), n_ref=1000):
+    """C2 as stated: dense CP 512^3, R = 32, beta in {0, 1/2, 1, 3/2}; block-MU vs J-CoMM with 1 and
+    3 inner sweeps (at beta != 1 also with every inner pass recomputing X~ instead of contracting
+    the cached P~ / Q~).  Per beta and method: ms per iteration (CUDA events over `iters` iterations,
+    inputs resident, the 537 MB tensor larger than L2), the HBM fraction of the whole iteration
+    (passes over X x 4 bytes per entry; a block-MU sweep makes 3 passes, J-CoMM at beta = 1 one
+    per outer iteration whatever L, at beta != 1 3 L), and, with ttt, the time to F*(1 + 1e-4),
+    F* = the lowest objective of n_ref FP32 block-MU sweeps from the same init."""
+    import torch
+    entries = X.numel()
+    obj = torch.zeros(1, dtype=torch.float64, device=X.device)
+    out = {"workload": "dense CP 512x512x512, R=32, Gamma(2,1) factors x Gamma(10,0.1) noise", "precision": prec}
+    for beta in betas:
+        res = {}
+        runs = [("block_mu", ntf.cp_mu_sweep, 1, None), ("jcomm_L1", ntf.jcomm_outer, 1, "auto"),
+                ("jcomm_L3", ntf.jcomm_outer, 3, "auto")]
+        if beta != 1.0:  # J-CoMM with every inner pass recomputing X~ (no P~ / Q~ cache)
+            runs += [("jcomm_L1_recompute", ntf.jcomm_outer, 1, "none"), ("jcomm_L3_recompute", ntf.jcomm_outer, 3, "none")]
+        for name, fn, L, cache in runs:
+            kw = {"inner_L": L, "cache": cache} if fn is ntf.jcomm_outer else {}
+            A = [a.clone() for a in A0]
+            for _ in range(3):
+                fn(X, beta, A, objective=obj, ctx=ctx, precision=prec, autotune=True, **kw)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(iters):
+                fn(X, beta, A, objective=obj, ctx=ctx, precision=prec, autotune=True, **kw)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / iters
+            passes = 3 if fn is ntf.cp_mu_sweep else (1 if beta == 1.0 else 3 * L)
+            gbs = passes * 4 * entries / (ms / 1e3) / 1e9
+            res[name] = {"ms": ms, "passes": passes, "hbm_frac_of_iteration": gbs / peaks["hbm_gbs"]}
+        if beta in ttt_betas:
+            F_ref, per_ref, ch = run_until(ntf, ctx, X, A0, beta, ntf.cp_mu_sweep, "fp32", n_ref, None)
+            fstar = float(F_ref.min())
+            runs = {"block_mu_fp32": (F_ref, per_ref, ch)}
+            for name, fn, L in (("block_mu_" + prec, ntf.cp_mu_sweep, 1), ("jcomm_L1_" + prec, ntf.jcomm_outer, 1),
+                                ("jcomm_L3_" + prec, ntf.jcomm_outer, 3)):
+                runs[name] = run_until(ntf, ctx, X, A0, beta, fn, prec, 3000, fstar * (1 + 1e-4), inner_L=L)
+            res["time_to_target"] = {"F_star": fstar, **ttt_summary(runs, fstar)}
+        out["beta%g" % beta] = res
+    return out
+
+
+def run_tucker_c3(ntf, ctx, peaks, iters=10, n=400, J=32, beta=1.5, seed=3, precisions=("fp32", "tf32", "3xtf32")):
+    """Dense Tucker 400 x 400 x 400, core 32 x 32 x 32, beta = 3/2: Gamma(2,1) core and
+    factors, model rescaled to mean 10, Poisson noise (drawn on the device, seeded); init
+    U(0.1, 1).  For each precision, times block-MM sweeps (core, then modes 1..3) and J-CoMM
+    outer iterations (L = 1), and reports the objective after the timed sweeps relative to
+    the FP32 CUDA-core path's.  Roofline per sweep: four passes over X (4 bytes per entry
+    each; FP32 path: 2J flops for Xhat and 2J for each of the P and Q contractions per
+    entry, against the derived FP32 FMA peak; tensor-core path: the bytes against the HBM
+    copy bandwidth)."""
+    import torch
+    X, G0, A0 = c3_data(n, J, seed)
+    dev = X.device
     obj = torch.zeros(1, dtype=torch.float64, device=dev)
     entries = n ** 3
     fp32_peak = torch.cuda.get_device_properties(dev).multi_processor_count * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) / 1e6
@@ -248,12 +477,49 @@ def run_coo_c4(ntf, ctx, peaks, iters=20, R=32, seed=0):
     # at beta = 1 every numerator comes from the reference: one pass per mode over that
     # mode's sorted copy of the nonzeros (4 int32 coordinates + 1 FP32 value each)
     byt = len(dims) * 20 * nnz
+    sec = ms / 1e3
+    N = len(dims)
+    # per nonzero and pass: Xhat = sum_r prod of N factor entries (N - 1 multiplies and an add
+    # per rank) and the numerator p * prod_{m != n} A^(m) (N - 1 multiplies and an add per rank):
+    # 2 N R flops; the N - 1 gathered factor rows are R * 4 bytes each
+    flops = N * 2 * N * R * nnz
+    gather = N * (N - 1) * R * 4 * nnz
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak = sms * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    l2 = l2_copy_gbs()
     return {"workload": "sparse COO 183x24x1140x1717, 3.3M nnz, CP R=32, beta=1, J-CoMM L=1",
             "us_per_outer": ms * 1e3, "outer_per_s": 1e3 / ms,
-            "roofline": {"bound": "hbm", "achieved": byt / (ms / 1e3) / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                         "frac": byt / (ms / 1e3) / 1e9 / peaks["hbm_gbs"],
+            "roofline": {"bound": "hbm", "achieved": byt / sec / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": byt / sec / 1e9 / peaks["hbm_gbs"],
                          "of": "whole outer iteration (per-mode sorted copies are cached after the first call): "
-                               "4 passes x 20 B/nnz streamed; factor-row gathers hit L2"}}
+                               "4 passes x 20 B/nnz streamed; factor-row gathers hit L2"},
+            "alu": {"achieved_tflops": flops / sec / 1e12, "peak_tflops": fp32_peak, "frac": flops / sec / 1e12 / fp32_peak,
+                    "of": "2NR flops per nonzero and pass (Xhat and the numerator), N passes; FP32 FMA-pipe peak "
+                          "derived from %d SMs x 128 lanes x 2 x max clock" % sms},
+            "l2_gather": {"achieved_gbs": gather / sec / 1e9, "peak_gbs": l2, "frac": gather / sec / 1e9 / l2,
+                          "of": "(N-1) gathered factor rows of R x 4 bytes per nonzero and pass, N passes, against "
+                                "the L2-resident copy bandwidth measured in this run (32 MB -> 32 MB, best of 20); "
+                                "above 1 when the Zipf-skewed rows are served from L1"}}
+
+
+def l2_copy_gbs():
+    """Copy bandwidth of a 32 MB -> 32 MB copy that stays in the 129 MB L2 (read + write bytes,
+    best of 20 CUDA-event-timed copies): the denominator of the L2-gather fraction."""
+    import torch
+    a = torch.empty(8 << 20, dtype=torch.float32, device="cuda").fill_(1.0)
+    b = torch.empty_like(a)
+    for _ in range(5):
+        b.copy_(a)
+    best = None
+    for _ in range(20):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        b.copy_(a)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    return 2 * a.numel() * 4 / (best / 1e3) / 1e9
 
 
 def flushed_loop_ms(flush, call, iters):
@@ -547,6 +813,8 @@ def main():
         import torch
         import paper_2602_14683_gb300 as ntf
         ctx, peaks = ntf.default_context(), load_peaks()[0]
+        if args.profile_case == "jcache":
+            return profile_jcache(ntf)
         if args.profile_case == "tucker":
             r = run_tucker_c3(ntf, ctx, peaks, iters=0, precisions=(args.precision,))
         elif args.profile_case == "cp4":
@@ -662,42 +930,13 @@ def main():
     h2d = X.numel() * 4 + sum(a.numel() * 4 for a in A0)
     d2h = sum(a.numel() * 4 for a in A0) + 8
 
-    # ---------------- time to F*(1 + 1e-4) ----------------
+    # ---------------- time to F*(1 + 1e-4) at beta = 1, every method ----------------
     ttt = None
     if not args.no_ttt:
         # F* = lowest FP64 objective of 1000 FP32 block-MU sweeps from the shared init; every
         # other method runs from the same init until its objective first reaches F*(1+1e-4)
         # or an iteration cap, recording the objective of each incoming iterate on the device
         # (checked every 100 iterations)
-        n_ref = 1000
-        def run_until(fn, p, n_max, target):
-            Fr = torch.zeros(n_max, dtype=torch.float64, device=dev)
-            W_ = [a.clone() for a in A0]
-            for _ in range(3):  # untimed: workspaces sized for this method and precision
-                fn(X, BETA, W_, objective=Fr[:1], ctx=ctx, precision=p, autotune=True)
-            # the stopping check's reduction kernel is loaded here, not inside the timed region
-            float(Fr[:2].min())
-            C_ = [a.clone() for a in A0]
-            torch.cuda.synchronize()
-            ev = [torch.cuda.Event(enable_timing=True)]
-            ev[0].record(stream)
-            host = 0.0
-            t = 0
-            while t < n_max:
-                h0 = time.perf_counter()
-                for _ in range(min(100, n_max - t)):
-                    fn(X, BETA, C_, objective=Fr[t:t + 1], ctx=ctx, precision=p, autotune=True)
-                    t += 1
-                host += time.perf_counter() - h0
-                ev.append(torch.cuda.Event(enable_timing=True))
-                ev[-1].record(stream)
-                if target is not None and float(Fr[:t].min()) <= target:
-                    break
-            torch.cuda.synchronize()
-            chunks = [ev[k].elapsed_time(ev[k + 1]) for k in range(len(ev) - 1)]
-            run_until.chunk_ms = [round(min(chunks), 2), round(max(chunks), 2)]
-            run_until.host_s = host
-            return Fr[:t].cpu().numpy(), ev[0].elapsed_time(ev[-1]) / 1e3 / t
         class Extrap:
             # extrapolated sweeps / outer iterations with the Nesterov-type weights, one state
             # per factor list
@@ -712,11 +951,9 @@ def main():
                 self.fn(X, beta, A, self.prev[k], next(self.w[k]), objective=objective, ctx=ctx,
                         precision=precision, autotune=autotune)
 
-        F_ref, per_ref = run_until(ntf.cp_mu_sweep, "fp32", n_ref, None)
+        F_ref, per_ref, ch = run_until(ntf, ctx, X, A0, BETA, ntf.cp_mu_sweep, "fp32", 1000, None)
         fstar = float(F_ref.min())
-        target = fstar * (1 + 1e-4)
-        runs = {"block_mu_fp32": (F_ref, per_ref)}
-        diag = {"block_mu_fp32": (run_until.chunk_ms, run_until.host_s)}
+        runs = {"block_mu_fp32": (F_ref, per_ref, ch)}
         for name, fn, p, cap in (("jcomm_" + prec, ntf.jcomm_outer, prec, 5000),
                                  ("jcomm_3xtf32", ntf.jcomm_outer, "3xtf32", 5000),
                                  ("block_mu_" + prec, ntf.cp_mu_sweep, prec, 2000),
@@ -724,22 +961,16 @@ def main():
                                  ("jcomm_extrap_" + prec, Extrap(ntf.cp_jcomm_outer_extrap), prec, 2000),
                                  ("jcomm_fp32", ntf.jcomm_outer, "fp32", 2000)):
             if name not in runs:
-                runs[name] = run_until(fn, p, cap, target)
-                diag[name] = (run_until.chunk_ms, run_until.host_s)
-        res = {}
-        for name, (F, per) in runs.items():
-            hit = np.nonzero(F <= target)[0]
-            rel = np.abs(np.diff(F)) / F[1:]
-            conv = np.nonzero(rel <= 1e-4)[0]
-            res[name] = {"iters": int(hit[0]) if hit.size else None,
-                         "seconds": float(hit[0] * per) if hit.size else None,
-                         "s_per_iter": per, "iters_run": int(F.size),
-                         "iters_rel_change_1e-4": int(conv[0]) + 1 if conv.size else None,
-                         "seconds_rel_change_1e-4": float((conv[0] + 1) * per) if conv.size else None,
-                         "final_rel_gap": float(F[-1] / fstar - 1.0),
-                         "ms_per_100_iters_min_max": diag[name][0], "host_enqueue_s": diag[name][1]}
+                runs[name] = run_until(ntf, ctx, X, A0, BETA, fn, p, cap, fstar * (1 + 1e-4))
         ttt = {"target": "F*(1+1e-4)", "F_star": fstar,
-               "F_star_from": "lowest objective of %d FP32 block-MU sweeps" % n_ref, **res}
+               "F_star_from": "lowest objective of 1000 FP32 block-MU sweeps", **ttt_summary(runs, fstar)}
+
+    # ---------------- C2 as stated: every beta, block-MU vs J-CoMM L = 1, 3 ----------------
+    c2_betas = tuple(float(b) for b in args.c2_betas.split(",")) if args.c2_betas else ()
+    # beta = 1's time to target is the every-method run above
+    c2 = run_cp_c2(ntf, ctx, peaks, X, A0, prec, betas=c2_betas,
+                   ttt_betas=() if args.no_ttt else tuple(b for b in c2_betas if b != BETA))
+    c1 = run_cp_c1(ntf, ctx)
 
     # ---------------- roofline of the dominant kernel (the fused pass) ----------------
     entries = DIMS[0] * DIMS[1] * DIMS[2]
@@ -773,6 +1004,11 @@ def main():
         cores = os.cpu_count() or 1
         sec, desc = oracle_step_sample(X_np.astype(np.float64), A_np, cores, 12.0)
         cpu = {"value": 1.0 / sec, "unit": "sweeps/s", "cores": cores, "kind": "oracle", "sample": desc}
+    # C3's metric needs the oracle too: the per-iteration objective error of each precision
+    # against FP64 (same leg: rank 0, N = 1)
+    c3_ora = None
+    if rank == 0 and world == 1 and not args.no_cpu and not args.no_other:
+        c3_ora = c3_vs_oracle(ntf, ctx)
 
     other = None
     if not args.no_other:
@@ -788,11 +1024,14 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": "sweeps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_j / args.steps * 1e3, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[prec], "data": "synthetic",
         "config": {"workload": WORKLOAD, "precision": prec, "method": "J-CoMM L=1", "plan": "autotuned slab split",
                    "l2": "inputs larger than L2 (537 MB tensor), no flush", "parallelism": "replicas"},
         "block_mu_sweeps_per_s": b_rate,
         "time_to_target": ttt,
+        "c1_latency": c1,
+        "c2_table": c2,
+        "c3_objective_error_vs_oracle": c3_ora,
         "serving": serving,
         "other_configs": other,
         "roofline": roof,
@@ -804,9 +1043,54 @@ def main():
     }
     if rank == 0:
         print(json.dumps(line))
+        sys.stdout.flush()
+        sys.stderr.write(summary(line) + "\n")
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def summary(line):
+    """Compact text of the figures beyond the headline, for readers of the log's tail."""
+    out = ["SUMMARY %s %.1f %s, pass frac %.3f of HBM (%s)" % (line["config"]["precision"], line["value"], line["unit"],
+           line["roofline"]["frac"], line["roofline"]["unit"])]
+    t = line.get("time_to_target")
+    if t:
+        out.append("TTT beta=1 F*(1+1e-4): " + ", ".join(
+            "%s %s s (%s it)" % (k, None if v["seconds"] is None else round(v["seconds"], 3), v["iters"])
+            for k, v in t.items() if isinstance(v, dict)))
+    c2 = line.get("c2_table") or {}
+    for b, r in c2.items():
+        if not isinstance(r, dict) or "block_mu" not in r:
+            continue
+        row = "C2 %s ms: block %.3f, J L1 %.3f, J L3 %.3f" % (b, r["block_mu"]["ms"], r["jcomm_L1"]["ms"], r["jcomm_L3"]["ms"])
+        if "time_to_target" in r:
+            row += "; TTT s: " + ", ".join("%s %s" % (k, None if v["seconds"] is None else round(v["seconds"], 3))
+                                           for k, v in r["time_to_target"].items() if isinstance(v, dict))
+        out.append(row)
+    c1 = line.get("c1_latency")
+    if c1:
+        out.append("C1 us/sweep: fp32 %.1f, tf32 %.1f" % (c1["fp32"]["us_per_sweep"], c1["tf32"]["us_per_sweep"]))
+    c3 = line.get("c3_objective_error_vs_oracle")
+    if c3:
+        out.append("C3 max rel obj err vs FP64 oracle: " + ", ".join(
+            "%s %.2e" % (k, v["max_rel_err"]) for k, v in c3.items() if isinstance(v, dict)))
+    o = line.get("other_configs") or {}
+    if o.get("tucker_c3"):
+        tc = o["tucker_c3"]
+        out.append("C3 ms block/jcomm: " + ", ".join("%s %.3f/%.3f" % (p, tc[p]["block_mm_ms"], tc[p]["jcomm_ms"])
+                                                  for p in ("fp32", "tf32", "3xtf32") if p in tc))
+    if o.get("coo_c4"):
+        c4 = o["coo_c4"]
+        out.append("C4 us/outer %.1f; frac hbm %.3f alu %.3f l2 %.3f" % (c4["us_per_outer"], c4["roofline"]["frac"],
+                                                                        c4["alu"]["frac"], c4["l2_gather"]["frac"]))
+    sv = line.get("serving")
+    if sv:
+        out.append("C5 %d jobs: sat %.1f/s, at 0.8x: %.1f/s p50 %.3f s p99 %.3f s; sweep " % (
+            sv["jobs"], sv["saturation_solves_per_s"], sv["solves_per_s"], sv["p50_latency_s"], sv["p99_latency_s"]) +
+            ", ".join("%s %.1f/%.1f p99 %.3f" % (k, v["achieved_per_s"], v["offered_per_s"], v["p99_latency_s"])
+                      for k, v in sv["load_sweep"].items()))
+    return "\n".join(out)
 
 
 if __name__ == "__main__":

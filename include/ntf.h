@@ -290,10 +290,14 @@ int ntf_coo_stable_perm(ntf_ctx *ctx, const int32_t *keys, int64_t nnz, int64_t 
 
 /* ---------------------------------------------------------------------------------
  * Continuous-batching server for many small dense 3-way jobs (CP or Tucker).
- * The server owns `slots` execution slots (a context and a stream each) and a scheduler
- * thread.  Submitted jobs queue FIFO; the head is admitted into a free slot when its
- * estimated workspace fits the device-memory budget (a job larger than the budget runs
- * alone).  An admitted job runs one iteration eagerly (sizing its slot's workspaces), then
+ * A scheduler thread admits submitted jobs into two lanes, each in FIFO order.  Dense CP
+ * jobs with precision NTF_PREC_FP32 join a batch (ntf_batch_* below) whose arena is half of
+ * the memory budget: they are admitted when their workspace fits the arena and share every
+ * launch of an iteration with the other resident jobs of their class, a few iterations per
+ * graph launch.  All other jobs (and a CP job larger than the whole arena) use the slot lane:
+ * the server owns `slots` execution slots (a context and a stream each); the lane's head is
+ * admitted into a free slot when its estimated workspace fits the other half of the budget
+ * (a job larger than the budget runs alone).  An admitted job runs one iteration eagerly (sizing its slot's workspaces), then
  * the rest of the job as one CUDA graph launch: a conditional WHILE node over one captured
  * iteration of its method followed by a one-thread kernel that applies the stopping test on
  * the device to the FP64 objective of the iteration's incoming iterate (Section 3.2): stop
@@ -343,6 +347,47 @@ int ntf_server_submit(ntf_server *server, const ntf_job *job, int64_t *id_out);
 int ntf_server_poll(ntf_server *server, ntf_result *out, int max_results, int wait_all);
 /* Stops the scheduler (queued jobs are dropped), waits for running work, frees slots. */
 void ntf_server_destroy(ntf_server *server);
+
+/* ---------------------------------------------------------------------------------
+ * Launches shared by many small dense 3-way CP jobs (FP32 passes).
+ * A batch keeps resident jobs -- the ntf_job requests above with model NTF_CP and precision
+ * NTF_PREC_FP32, J-CoMM (Algorithm 2, inner_L = 1) or block MM (Algorithm 1) -- in classes
+ * by rank padding (8, 16, 32, 64) and iteration shape (J-CoMM at beta = 1: one pass with
+ * all numerators; beta = 1 block MM: three passes with closed-form denominators; beta != 1:
+ * three passes with numerators and denominators).  One iteration of a class is one launch
+ * per step for ALL its jobs: a persistent grid walks a device-resident work table in which
+ * each job owns the work items of its own single-job launch, so every job computes exactly
+ * what ntf_jcomm_outer / ntf_cp_mu_sweep compute for it on the FP32 path (the same bits),
+ * whatever else is resident.  ntf_batch_tick runs up to `iters` iterations of every class as
+ * one graph launch per class (a conditional WHILE node over the captured iteration and a
+ * device stopping test: |F_{t-1} - F_t| / F_{t-1} <= rtol on the FP64 objective of the
+ * incoming iterate, or the iteration cap); classes run concurrently on their own streams.
+ * Between launches the batch retires stopped jobs and admits new ones (continuous batching
+ * at iteration granularity).  Workspaces come from one device arena of mem_budget_bytes
+ * allocated at creation (0: a quarter of the free device memory): ntf_batch_add returns
+ * NTF_ERR_OOM when the job does not fit now (retry after a tick has retired jobs) or when
+ * `capacity` jobs are resident; NTF_ERR_UNSUPPORTED for Tucker or tensor-core requests.
+ * The caller owns X and the factors (device memory), keeps them alive and untouched until
+ * the job's result has been returned, and finds the factors updated in place.  A batch is
+ * driven by one host thread; its calls are not thread-safe.
+ * --------------------------------------------------------------------------------- */
+typedef struct ntf_batch ntf_batch;
+int ntf_batch_create(ntf_batch **batch, int device, int capacity, size_t mem_budget_bytes);
+/* Makes the job resident (it joins the next launch of its class); id_out (may be NULL)
+ * receives its id.  job->X and job->factors must stay valid while it is resident. */
+int ntf_batch_add(ntf_batch *batch, const ntf_job *job, int64_t *id_out);
+/* For every class whose previous launch has finished (with wait != 0: after waiting for
+ * it): moves the stopped jobs' results to the result list and frees their workspaces; then,
+ * if the class still holds jobs, launches up to `iters` (>= 1) more iterations of all of
+ * them.  Asynchronous apart from the wait.  Returns the number of resident jobs (>= 0; with
+ * wait != 0, 0 means every job has finished) or a negative ntf_status.  A failed launch
+ * ends all jobs of its class with NTF_ERR_CUDA. */
+int ntf_batch_tick(ntf_batch *batch, int iters, int wait);
+/* Moves up to max_results finished results (oldest first) into out; returns how many. */
+int ntf_batch_results(ntf_batch *batch, ntf_result *out, int max_results);
+int ntf_batch_resident(const ntf_batch *batch);
+/* Waits for running launches, then frees the batch (resident jobs are dropped). */
+void ntf_batch_destroy(ntf_batch *batch);
 
 /* Allocation-free objective for dense CP tensors.  The paper has no counterpart: this is a
  * service for callers that cannot allocate device memory when they call -- a process whose

@@ -7,5 +7,5 @@ thin Python binding.  Build the library with ``paper_2602_14683_gb300.build.buil
 from ._lib import (  # noqa: F401
     Context, Coo, NtfError, beta_div, coo_stable_perm, cp_beta_div_noalloc, cp_mu_sweep, cp_mu_sweep_extrap,
     cp_jcomm_outer_extrap, default_context, jcomm_outer, nesterov_weights,
-    make_opts, plan_cut, raw_library, tucker_jcomm_outer_extrap, tucker_mu_sweep, tucker_mu_sweep_extrap, Server, LIB_PATH, EXPORTED,
+    make_opts, plan_cut, raw_library, tucker_jcomm_outer_extrap, tucker_mu_sweep, tucker_mu_sweep_extrap, Batch, Server, LIB_PATH, EXPORTED,
 )

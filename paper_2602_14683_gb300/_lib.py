@@ -89,6 +89,12 @@ _sig = {
     "ntf_server_submit": (C.c_int, [_P, C.POINTER(Job), C.POINTER(C.c_int64)]),
     "ntf_server_poll": (C.c_int, [_P, C.POINTER(Result), C.c_int, C.c_int]),
     "ntf_server_destroy": (None, [_P]),
+    "ntf_batch_create": (C.c_int, [C.POINTER(_P), C.c_int, C.c_int, C.c_size_t]),
+    "ntf_batch_add": (C.c_int, [_P, C.POINTER(Job), C.POINTER(C.c_int64)]),
+    "ntf_batch_tick": (C.c_int, [_P, C.c_int, C.c_int]),
+    "ntf_batch_results": (C.c_int, [_P, C.POINTER(Result), C.c_int]),
+    "ntf_batch_resident": (C.c_int, [_P]),
+    "ntf_batch_destroy": (None, [_P]),
     "ntf_cp_beta_div_noalloc": (C.c_int, [C.POINTER(Tensor), C.c_float, C.c_int, C.POINTER(_P), C.c_double,
                                           C.c_double, _P, _P]),
 }
@@ -408,6 +414,92 @@ def cp_beta_div_noalloc(X, beta, factors, out, eps=1e-12, eps_x=1e-12, stream=No
                                         float(eps_x), _out_ptr(out), _stream(stream))
 
 
+def _job(X, beta, factors, core, method, rtol, max_iters, precision, eps):
+    _check_dev(X, torch.float32, "X")
+    for f in factors:
+        _check_dev(f, torch.float32, "factors")
+    j = Job()
+    j.model = NTF_CP if core is None else NTF_TUCKER
+    j.method = {"jcomm": 0, "block": 1}[method]
+    j.precision = PRECISIONS[precision]
+    for n in range(3):
+        j.dims[n] = X.shape[n]
+    if core is None:
+        j.rank = factors[0].shape[1]
+    else:
+        _check_dev(core, torch.float32, "core")
+        for n in range(3):
+            j.core_dims[n] = core.shape[n]
+        j.core = core.data_ptr()
+    j.beta, j.eps, j.rtol, j.max_iters = float(beta), float(eps), float(rtol), int(max_iters)
+    j.X = X.data_ptr()
+    for n in range(3):
+        j.factors[n] = factors[n].data_ptr()
+    return j
+
+
+def _results(buf, n):
+    return [dict(id=buf[q].id, status=buf[q].status, iterations=buf[q].iterations, objective=buf[q].objective,
+                 t_submit=buf[q].t_submit, t_admit=buf[q].t_admit, t_done=buf[q].t_done) for q in range(n)]
+
+
+class Batch:
+    """Launches shared by many small dense CP jobs (ntf_batch_*): add jobs made of CUDA
+    tensors, tick, collect results.  Keeps every resident job's tensors alive until its
+    result has been collected."""
+
+    def __init__(self, device=0, capacity=1024, mem_budget_bytes=0):
+        h = _P()
+        rc = _lib.ntf_batch_create(C.byref(h), int(device), int(capacity), int(mem_budget_bytes))
+        if rc != NTF_OK:
+            raise NtfError(rc, "ntf_batch_create failed")
+        self.h = h
+        self._live = {}
+
+    def add(self, X, beta, factors, method="jcomm", rtol=1e-6, max_iters=200, eps=1e-12):
+        """Makes a job resident; returns its id, or None when it does not fit now."""
+        j = _job(X, beta, factors, None, method, rtol, max_iters, "fp32", eps)
+        jid = C.c_int64()
+        rc = _lib.ntf_batch_add(self.h, C.byref(j), C.byref(jid))
+        if rc == -4:
+            return None
+        if rc != NTF_OK:
+            raise NtfError(rc, "ntf_batch_add failed")
+        self._live[jid.value] = (X, factors)
+        return jid.value
+
+    def tick(self, iters=8, wait=True):
+        rc = _lib.ntf_batch_tick(self.h, int(iters), 1 if wait else 0)
+        if rc < 0:
+            raise NtfError(rc, "ntf_batch_tick failed")
+        return rc
+
+    def results(self, max_results=4096):
+        buf = (Result * max_results)()
+        out = _results(buf, _lib.ntf_batch_results(self.h, buf, max_results))
+        for r in out:
+            self._live.pop(r["id"], None)
+        return out
+
+    def run(self, iters=8):
+        """Ticks until every resident job has finished; returns all results."""
+        out = []
+        while self.tick(iters, wait=True) > 0:
+            out += self.results()
+        return out + self.results()
+
+    def close(self):
+        if self.h:
+            _lib.ntf_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Server:
     """Continuous-batching server (ntf_server_*): submit jobs made of CUDA tensors, poll
     results.  Keeps every submitted job's tensors alive until its result is polled."""
@@ -422,26 +514,7 @@ class Server:
 
     def submit(self, X, beta, factors, core=None, method="jcomm", rtol=1e-6, max_iters=200, precision="fp32",
                eps=1e-12):
-        _check_dev(X, torch.float32, "X")
-        for f in factors:
-            _check_dev(f, torch.float32, "factors")
-        j = Job()
-        j.model = NTF_CP if core is None else NTF_TUCKER
-        j.method = {"jcomm": 0, "block": 1}[method]
-        j.precision = PRECISIONS[precision]
-        for n in range(3):
-            j.dims[n] = X.shape[n]
-        if core is None:
-            j.rank = factors[0].shape[1]
-        else:
-            _check_dev(core, torch.float32, "core")
-            for n in range(3):
-                j.core_dims[n] = core.shape[n]
-            j.core = core.data_ptr()
-        j.beta, j.eps, j.rtol, j.max_iters = float(beta), float(eps), float(rtol), int(max_iters)
-        j.X = X.data_ptr()
-        for n in range(3):
-            j.factors[n] = factors[n].data_ptr()
+        j = _job(X, beta, factors, core, method, rtol, max_iters, precision, eps)
         jid = C.c_int64()
         rc = _lib.ntf_server_submit(self.h, C.byref(j), C.byref(jid))
         if rc != NTF_OK:
@@ -452,12 +525,11 @@ class Server:
     def poll(self, wait_all=False, max_results=4096):
         buf = (Result * max_results)()
         n = _lib.ntf_server_poll(self.h, buf, max_results, 1 if wait_all else 0)
-        out = []
-        for q in range(n):
-            r = buf[q]
-            self._live.pop(r.id, None)
-            out.append(dict(id=r.id, status=r.status, iterations=r.iterations, objective=r.objective,
-                            t_submit=r.t_submit, t_admit=r.t_admit, t_done=r.t_done))
+        if n < 0:
+            raise NtfError(n, "ntf_server_poll failed")
+        out = _results(buf, n)
+        for r in out:
+            self._live.pop(r["id"], None)
         return out
 
     def close(self):

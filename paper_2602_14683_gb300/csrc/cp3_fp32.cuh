@@ -140,12 +140,15 @@ __device__ __forceinline__ void load_x_tile(const Cp3Args &a, float *xs, int i, 
     }
 }
 
+// The pass over one CTA's share (work item `blk` of the plan's grid): the kernel below runs
+// item blockIdx.x; the batched kernel runs the items of many jobs' plans in one launch.
 template <int RP, bool DEN, int MS>
-__global__ void __launch_bounds__(NT, 1) cp3_pass_fp32(const Cp3Args a) {
+__device__ __forceinline__ void cp3_fp32_body(const Cp3Args &a, const int blk) {
     using G = Geo<RP>;
     constexpr int TJ = G::TJ, RW = G::RW, RG = G::RG, TS = G::TS, RS = G::RS, TT = G::TT;
     constexpr bool M1 = (MS & PM_M1) != 0, M2 = (MS & PM_M2) != 0, M3 = (MS & PM_M3) != 0;
     constexpr bool OBJ = (MS & PM_OBJ) != 0;
+    constexpr bool NOX = (MS & PM_NOX) != 0;  // X == 0, not read; denominator side only
     constexpr bool ROWS = M1 || M2;
     constexpr Layout L = layout<RP, DEN, MS>();
 
@@ -168,7 +171,7 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_fp32(const Cp3Args a) {
     const int tr = tid >> 3, tc = tid & 7;
     const int slice = tid >> 6, gc = (tid & 63) >> 3, gr = tid & 7;
 
-    int b = blockIdx.x;
+    int b = blk;
     const int is = b % a.n_is;
     b /= a.n_is;
     const int kb = b % a.n_kb;
@@ -220,7 +223,7 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_fp32(const Cp3Args a) {
             for (int q = 0; q < RG; ++q) acc3[ch][c][q] = acc3d[ch][c][q] = 0.0f;
     double obj_acc = 0.0;
 
-    if (i0 < i1) load_x_tile<TJ>(a, xs0, i0, j0, k0);
+    if (!NOX && i0 < i1) load_x_tile<TJ>(a, xs0, i0, j0, k0);
     cp_async_commit();
 
     int buf = 0;
@@ -260,7 +263,7 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_fp32(const Cp3Args a) {
             {
                 int ni = (ch + 1 < NCH) ? i : i + 1;
                 int nch = (ch + 1 < NCH) ? ch + 1 : 0;
-                if (ni < i1) load_x_tile<TJ>(a, xs0 + (buf ^ 1) * TJ * XS, ni, j0, k0 + nch * KC);
+                if (!NOX && ni < i1) load_x_tile<TJ>(a, xs0 + (buf ^ 1) * TJ * XS, ni, j0, k0 + nch * KC);
                 cp_async_commit();
             }
             cp_async_wait<1>();
@@ -296,15 +299,15 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_fp32(const Cp3Args a) {
                 for (int c = 0; c < 4; ++c) {
                     const int col = tc + 8 * c;
                     const bool v = rv && (kc + col) < K;
-                    float xv = xs[row * XS + col];
-                    if (a.bkind == BK_IS) xv = fmaxf(xv, a.eps_x);
+                    float xv = NOX ? 0.0f : xs[row * XS + col];
+                    if (!NOX && a.bkind == BK_IS) xv = fmaxf(xv, a.eps_x);
                     const float y = fmaxf(xh[x][c], a.eps);
                     float P = 0.0f, Q = 0.0f;
                     if (M1 || M2 || M3) pq_powers(a.bkind, a.beta, xv, y, P, Q);
                     if (!v) { P = 0.0f; Q = 0.0f; }
                     if (OBJ && v) objf += dbeta_stable(a.bkind, a.beta, xv, y);
                     if (M1 || M2 || M3) {
-                        ps[row * XS + col] = P;
+                        if (!NOX) ps[row * XS + col] = P;
                         if (DEN) qs[row * XS + col] = Q;
                     }
                 }
@@ -321,19 +324,19 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_fp32(const Cp3Args a) {
                     float p[RW][4], qv[RW][4];
 #pragma unroll
                     for (int x = 0; x < RW; ++x) {
-                        VecLd<4>::ld(ps + (tr * RW + x) * XS + c4 * 4, p[x]);
+                        if (!NOX) VecLd<4>::ld(ps + (tr * RW + x) * XS + c4 * 4, p[x]);
                         if (DEN) VecLd<4>::ld(qs + (tr * RW + x) * XS + c4 * 4, qv[x]);
                     }
 #pragma unroll
                     for (int cq = 0; cq < 4; ++cq) {
                         float cv[RG], dv[RG];
-                        VecLd<RG>::ld(cnc + (c4 * 4 + cq) * RS, cv);
+                        if (!NOX) VecLd<RG>::ld(cnc + (c4 * 4 + cq) * RS, cv);
                         if (DEN) VecLd<RG>::ld(cdc + (c4 * 4 + cq) * RS, dv);
 #pragma unroll
                         for (int x = 0; x < RW; ++x)
 #pragma unroll
                             for (int q = 0; q < RG; ++q) {
-                                W[x][q] = fmaf(p[x][cq], cv[q], W[x][q]);
+                                if (!NOX) W[x][q] = fmaf(p[x][cq], cv[q], W[x][q]);
                                 if (DEN) Wd[x][q] = fmaf(qv[x][cq], dv[q], Wd[x][q]);
                             }
                     }
@@ -345,8 +348,10 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_fp32(const Cp3Args a) {
                 for (int rr = 0; rr < TS; ++rr) {
                     const int row = slice * TS + rr;
                     float p[4], qv[4], kv[RG], kd[RG];
-                    VecLd<4>::ld(ps + row * XS + gc * 4, p);
-                    VecLd<RG>::ld(krn + row * RS + gr * RG, kv);
+                    if (!NOX) {
+                        VecLd<4>::ld(ps + row * XS + gc * 4, p);
+                        VecLd<RG>::ld(krn + row * RS + gr * RG, kv);
+                    }
                     if (DEN) {
                         VecLd<4>::ld(qs + row * XS + gc * 4, qv);
                         VecLd<RG>::ld(krd + row * RS + gr * RG, kd);
@@ -355,7 +360,7 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_fp32(const Cp3Args a) {
                     for (int c = 0; c < 4; ++c)
 #pragma unroll
                         for (int q = 0; q < RG; ++q) {
-                            acc3[ch][c][q] = fmaf(p[c], kv[q], acc3[ch][c][q]);
+                            if (!NOX) acc3[ch][c][q] = fmaf(p[c], kv[q], acc3[ch][c][q]);
                             if (DEN) acc3d[ch][c][q] = fmaf(qv[c], kd[q], acc3d[ch][c][q]);
                         }
                 }
@@ -369,14 +374,14 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_fp32(const Cp3Args a) {
             float an[RG], ad[RG];
 #pragma unroll
             for (int q = 0; q < RG; ++q) {
-                an[q] = a.num[0][(int64_t)i * RP + tc * RG + q];
+                an[q] = NOX ? 0.0f : a.num[0][(int64_t)i * RP + tc * RG + q];
                 ad[q] = DEN ? a.den[0][(int64_t)i * RP + tc * RG + q] : 0.0f;
             }
 #pragma unroll
             for (int x = 0; x < RW; ++x)
 #pragma unroll
                 for (int q = 0; q < RG; ++q) {
-                    acc2[x][q] = fmaf(an[q], W[x][q], acc2[x][q]);
+                    if (!NOX) acc2[x][q] = fmaf(an[q], W[x][q], acc2[x][q]);
                     if (DEN) acc2d[x][q] = fmaf(ad[q], Wd[x][q], acc2d[x][q]);
                 }
         }
@@ -388,12 +393,14 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_fp32(const Cp3Args a) {
                 sd[q] = 0.0f;
 #pragma unroll
                 for (int x = 0; x < RW; ++x) {
-                    s[q] = fmaf(W[x][q], bn[(tr * RW + x) * RS + tc * RG + q], s[q]);
+                    if (!NOX) s[q] = fmaf(W[x][q], bn[(tr * RW + x) * RS + tc * RG + q], s[q]);
                     if (DEN) sd[q] = fmaf(Wd[x][q], bd[(tr * RW + x) * RS + tc * RG + q], sd[q]);
                 }
                 // lanes with the same tc: lane = (tr & 3) * 8 + tc
-                s[q] += __shfl_xor_sync(0xffffffffu, s[q], 8);
-                s[q] += __shfl_xor_sync(0xffffffffu, s[q], 16);
+                if (!NOX) {
+                    s[q] += __shfl_xor_sync(0xffffffffu, s[q], 8);
+                    s[q] += __shfl_xor_sync(0xffffffffu, s[q], 16);
+                }
                 if (DEN) {
                     sd[q] += __shfl_xor_sync(0xffffffffu, sd[q], 8);
                     sd[q] += __shfl_xor_sync(0xffffffffu, sd[q], 16);
@@ -403,7 +410,7 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_fp32(const Cp3Args a) {
             if (lane < 8) {
 #pragma unroll
                 for (int q = 0; q < RG; ++q) {
-                    red[warp * RP + lane * RG + q] = s[q];
+                    if (!NOX) red[warp * RP + lane * RG + q] = s[q];
                     if (DEN) red[8 * RP + warp * RP + lane * RG + q] = sd[q];
                 }
             }
@@ -412,11 +419,11 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_fp32(const Cp3Args a) {
                 float t = 0.0f, td = 0.0f;
 #pragma unroll
                 for (int w = 0; w < 8; ++w) {
-                    t += red[w * RP + tid];
+                    if (!NOX) t += red[w * RP + tid];
                     if (DEN) td += red[8 * RP + w * RP + tid];
                 }
                 const int64_t slot = ((int64_t)(jt * a.n_kb + kb) * a.I + i) * RP + tid;
-                a.p1n[slot] = t;
+                if (!NOX) a.p1n[slot] = t;
                 if (DEN) a.p1d[slot] = td;
             }
             __syncthreads();
@@ -439,7 +446,7 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_fp32(const Cp3Args a) {
             if (j < J) {
 #pragma unroll
                 for (int q = 0; q < RG; ++q) {
-                    a.p2n[(base + j) * RP + tc * RG + q] = acc2[x][q];
+                    if (!NOX) a.p2n[(base + j) * RP + tc * RG + q] = acc2[x][q];
                     if (DEN) a.p2d[(base + j) * RP + tc * RG + q] = acc2d[x][q];
                 }
             }
@@ -450,7 +457,7 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_fp32(const Cp3Args a) {
         // order through shared memory, then store the column block
         float *acc_s = xs0;  // KB x RP floats, fits in the X double buffer
         __syncthreads();
-        for (int pass = 0; pass < (DEN ? 2 : 1); ++pass) {
+        for (int pass = NOX ? 1 : 0; pass < (DEN ? 2 : 1); ++pass) {
             for (int sl = 0; sl < 4; ++sl) {
                 if (slice == sl) {
 #pragma unroll
@@ -487,8 +494,30 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_fp32(const Cp3Args a) {
         if (tid == 0) {
             double t = 0.0;
             for (int w = 0; w < 8; ++w) t += dred[w];
-            a.obj[blockIdx.x] = t;
+            a.obj[blk] = t;
         }
+    }
+}
+
+template <int RP, bool DEN, int MS>
+__global__ void __launch_bounds__(NT, 1) cp3_pass_fp32(const Cp3Args a) {
+    cp3_fp32_body<RP, DEN, MS>(a, blockIdx.x);
+}
+
+// Many jobs' passes in one launch: a persistent grid walks the items of the work table (job j
+// owns items [pfx[j], pfx[j+1]) of its own plan), skipping jobs that have stopped.  Each item
+// does exactly the arithmetic of the single-job kernel, so a job's partial sums do not depend
+// on the other jobs of the table.
+template <int RP, bool DEN, int MS>
+__global__ void __launch_bounds__(NT, 1) cp3_pass_fp32_batched(const BatchTable<Cp3Args> t) {
+    const int n = *t.n;
+    const int total = n > 0 ? t.pfx[n] : 0;
+    for (int item = blockIdx.x; item < total; item += gridDim.x) {
+        const int j = batch_job_of(t.pfx, n, item);
+        if (t.state[j].done) continue;  // uniform over the CTA
+        const Cp3Args a = t.args[j];
+        cp3_fp32_body<RP, DEN, MS>(a, item - t.pfx[j]);
+        __syncthreads();
     }
 }
 
@@ -512,6 +541,10 @@ cudaError_t launch_rp(const Cp3Plan &p, const Cp3Args &a, int ms, int den, cudaS
             case PM_M1 | PM_OBJ: return launch_one<RP, true, PM_M1 | PM_OBJ>(p, a, s);
             case PM_M2: return launch_one<RP, true, PM_M2>(p, a, s);
             case PM_M3: return launch_one<RP, true, PM_M3>(p, a, s);
+            case PM_M1 | PM_NOX: return launch_one<RP, true, PM_M1 | PM_NOX>(p, a, s);
+            case PM_M1 | PM_OBJ | PM_NOX: return launch_one<RP, true, PM_M1 | PM_OBJ | PM_NOX>(p, a, s);
+            case PM_M2 | PM_NOX: return launch_one<RP, true, PM_M2 | PM_NOX>(p, a, s);
+            case PM_M3 | PM_NOX: return launch_one<RP, true, PM_M3 | PM_NOX>(p, a, s);
             default: return cudaErrorInvalidValue;
         }
     }
@@ -523,6 +556,48 @@ cudaError_t launch_rp(const Cp3Plan &p, const Cp3Args &a, int ms, int den, cudaS
         case PM_M1 | PM_M2 | PM_M3 | PM_OBJ:
             return launch_one<RP, false, PM_M1 | PM_M2 | PM_M3 | PM_OBJ>(p, a, s);
         case PM_OBJ: return launch_one<RP, false, PM_OBJ>(p, a, s);
+        case PM_OBJ | PM_NOX: return launch_one<RP, false, PM_OBJ | PM_NOX>(p, a, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int RP, bool DEN, int MS>
+cudaError_t launch_batched_one(const BatchTable<Cp3Args> &t, int grid, cudaStream_t s) {
+    constexpr Layout L = layout<RP, DEN, MS>();
+    const size_t bytes = (size_t)L.end * sizeof(float);
+    auto k = cp3_pass_fp32_batched<RP, DEN, MS>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    if (grid <= 0) {  // persistent grid: every CTA that fits on the device at once
+        int per_sm = 0, dev = 0, sms = 0;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, NT, bytes)) != cudaSuccess) return e;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        if (per_sm < 1) return cudaErrorInvalidConfiguration;
+        grid = per_sm * sms;
+    }
+    k<<<grid, NT, bytes, s>>>(t);
+    return cudaGetLastError();
+}
+
+// The pass variants of the batched iterations: the first pass of an iteration (mode 1 with
+// the objective), modes 2 and 3, and the KL J-CoMM pass (all numerators and the objective).
+template <int RP>
+cudaError_t launch_batched_rp(const BatchTable<Cp3Args> &t, int ms, int den, int grid, cudaStream_t s) {
+    if (den) {
+        switch (ms) {
+            case PM_M1 | PM_OBJ: return launch_batched_one<RP, true, PM_M1 | PM_OBJ>(t, grid, s);
+            case PM_M2: return launch_batched_one<RP, true, PM_M2>(t, grid, s);
+            case PM_M3: return launch_batched_one<RP, true, PM_M3>(t, grid, s);
+            default: return cudaErrorInvalidValue;
+        }
+    }
+    switch (ms) {
+        case PM_M1 | PM_OBJ: return launch_batched_one<RP, false, PM_M1 | PM_OBJ>(t, grid, s);
+        case PM_M2: return launch_batched_one<RP, false, PM_M2>(t, grid, s);
+        case PM_M3: return launch_batched_one<RP, false, PM_M3>(t, grid, s);
+        case PM_M1 | PM_M2 | PM_M3 | PM_OBJ:
+            return launch_batched_one<RP, false, PM_M1 | PM_M2 | PM_M3 | PM_OBJ>(t, grid, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -6,4 +6,7 @@ namespace ntf {
 cudaError_t cp3_launch_fp32_r32(const Cp3Plan &p, const Cp3Args &a, int ms, int den, cudaStream_t s) {
     return fp32::launch_rp<32>(p, a, ms, den, s);
 }
+cudaError_t cp3_batched_fp32_r32(const BatchTable<Cp3Args> &t, int ms, int den, int grid, cudaStream_t s) {
+    return fp32::launch_batched_rp<32>(t, ms, den, grid, s);
+}
 }  // namespace ntf

@@ -7,6 +7,10 @@ cudaError_t cp3_launch_fp32_r8(const Cp3Plan &, const Cp3Args &, int, int, cudaS
 cudaError_t cp3_launch_fp32_r16(const Cp3Plan &, const Cp3Args &, int, int, cudaStream_t);
 cudaError_t cp3_launch_fp32_r32(const Cp3Plan &, const Cp3Args &, int, int, cudaStream_t);
 cudaError_t cp3_launch_fp32_r64(const Cp3Plan &, const Cp3Args &, int, int, cudaStream_t);
+cudaError_t cp3_batched_fp32_r8(const BatchTable<Cp3Args> &, int, int, int, cudaStream_t);
+cudaError_t cp3_batched_fp32_r16(const BatchTable<Cp3Args> &, int, int, int, cudaStream_t);
+cudaError_t cp3_batched_fp32_r32(const BatchTable<Cp3Args> &, int, int, int, cudaStream_t);
+cudaError_t cp3_batched_fp32_r64(const BatchTable<Cp3Args> &, int, int, int, cudaStream_t);
 
 // Row tiles of TJ rows (128; 64 at RP = 64), column blocks of 64 columns, and the slab
 // axis split so that the grid quantises well onto the SMs (one resident CTA per SM):
@@ -50,6 +54,16 @@ cudaError_t cp3_launch(const Cp3Plan &p, const Cp3Args &a, int ms, int den, cuda
         case 16: return cp3_launch_fp32_r16(p, a, ms, den, s);
         case 32: return cp3_launch_fp32_r32(p, a, ms, den, s);
         case 64: return cp3_launch_fp32_r64(p, a, ms, den, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t cp3_batched_launch(int RP, const BatchTable<Cp3Args> &t, int ms, int den, int grid, cudaStream_t s) {
+    switch (RP) {
+        case 8: return cp3_batched_fp32_r8(t, ms, den, grid, s);
+        case 16: return cp3_batched_fp32_r16(t, ms, den, grid, s);
+        case 32: return cp3_batched_fp32_r32(t, ms, den, grid, s);
+        case 64: return cp3_batched_fp32_r64(t, ms, den, grid, s);
         default: return cudaErrorInvalidValue;
     }
 }

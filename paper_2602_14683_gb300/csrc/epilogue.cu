@@ -143,9 +143,9 @@ __device__ __forceinline__ double group_sum(double *sh, double v, int RP, int t)
     return tot;
 }
 
-__global__ void prep_kernel(PrepArgs p) {
+__device__ __forceinline__ void prep_body(const PrepArgs &p, const int blk) {
     __shared__ double sh[256];
-    int b = blockIdx.x, m = 0;
+    int b = blk, m = 0;
     while (m < 2 && b >= row_blocks(p.rows[m], p.RP)) {
         b -= row_blocks(p.rows[m], p.RP);
         ++m;
@@ -168,6 +168,8 @@ __global__ void prep_kernel(PrepArgs p) {
         if (t < RP) p.cs[m][(int64_t)b * RP + t] = tot;
     }
 }
+
+__global__ void prep_kernel(PrepArgs p) { prep_body(p, blockIdx.x); }
 
 // Extrapolation (Section "Going beyond: Majorization-Minimization with Extrapolation"):
 // for each factor, D = pad([A - Aprev]_+) and FP64 partial sums of D^2 per row block (the
@@ -307,6 +309,10 @@ __global__ void run_update_kernel(RunUpdArgs u) {
         if (m != u.n) other *= u.dims[m];
     const int64_t stride = (int64_t)u.rows * RP;
     for (int side = 0; side < (u.pd ? 2 : 1); ++side) {
+        if (side == 0 && u.num_rows) {  // the numerator is given (uniform over the block)
+            if (t < RP) num_s[t] = u.num_rows[(int64_t)in * RP + t];
+            continue;
+        }
         const float *parts = side ? u.pd : u.pn;
         const float *const *L = side ? u.Ld : u.Ln;
         double acc = 0.0;
@@ -357,9 +363,14 @@ cudaError_t run_update(const RunUpdArgs &u, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t prep_factors(const PrepArgs &p, cudaStream_t s) {
+int prep_items(const PrepArgs &p) {
     int blocks = 0;
     for (int m = 0; m < 3; ++m) blocks += row_blocks(p.rows[m], p.RP);
+    return blocks;
+}
+
+cudaError_t prep_factors(const PrepArgs &p, cudaStream_t s) {
+    const int blocks = prep_items(p);
     if (blocks == 0) return cudaSuccess;
     prep_kernel<<<blocks, 256, 0, s>>>(p);
     return cudaGetLastError();
@@ -369,13 +380,13 @@ cudaError_t prep_factors(const PrepArgs &p, cudaStream_t s) {
 // that only sums the objective partials, so that this reduction is off the critical path.
 // A thread's loads of the column-sum partials and of its first row's partial sums are all
 // issued before the first barrier.
-__global__ void mode_update_kernel(UpdArgs u) {
+__device__ __forceinline__ void mode_update_body(const UpdArgs &u, const int blk) {
     __shared__ double sh[256];
     __shared__ float den_s[64];
     const MuEpiArgs &e = u.e;
     const int RP = e.RP, G = blockDim.x / RP, t = threadIdx.x, r = t % RP, g = t / RP;
     const int nrb = row_blocks(e.rows, RP);
-    if ((int)blockIdx.x == nrb) {  // the objective block: same order as reduce_obj_kernel
+    if (blk == nrb) {  // the objective block: same order as reduce_obj_kernel
         double v = 0.0;
         for (int k = t; k < u.obj_n; k += blockDim.x) v += u.obj_parts[k];
 #pragma unroll
@@ -390,7 +401,7 @@ __global__ void mode_update_kernel(UpdArgs u) {
         return;
     }
     const int rpb = rows_per_block(e.rows, RP);
-    const int ibeg = blockIdx.x * rpb, iend = min(e.rows, ibeg + rpb);
+    const int ibeg = blk * rpb, iend = min(e.rows, ibeg + rpb);
     const int64_t stride = (int64_t)e.rows * RP;
     // partials in batches of 16, each batch added as a fixed tree and the batch sums in order
     // (a fixed order for every run); 32 loads are in flight at once
@@ -481,12 +492,52 @@ __global__ void mode_update_kernel(UpdArgs u) {
     }
     if (u.cs_out) {
         const double tot = group_sum(sh, cs, RP, t);
-        if (t < RP) u.cs_out[(int64_t)blockIdx.x * RP + t] = tot;
+        if (t < RP) u.cs_out[(int64_t)blk * RP + t] = tot;
     }
 }
 
+__global__ void mode_update_kernel(UpdArgs u) { mode_update_body(u, blockIdx.x); }
+
+int mode_update_items(const UpdArgs &u) { return row_blocks(u.e.rows, u.e.RP) + (u.obj_out ? 1 : 0); }
+
 cudaError_t mode_update(const UpdArgs &u, cudaStream_t s) {
-    mode_update_kernel<<<row_blocks(u.e.rows, u.e.RP) + (u.obj_out ? 1 : 0), 256, 0, s>>>(u);
+    mode_update_kernel<<<mode_update_items(u), 256, 0, s>>>(u);
+    return cudaGetLastError();
+}
+
+// Batched forms: a persistent grid walks the work items of every resident job that has not
+// stopped; each item is the block of the single-job launch with the same index.
+__global__ void prep_batched_kernel(const BatchTable<PrepArgs> t) {
+    const int n = *t.n;
+    const int total = n > 0 ? t.pfx[n] : 0;
+    for (int item = blockIdx.x; item < total; item += gridDim.x) {
+        const int j = batch_job_of(t.pfx, n, item);
+        if (t.state[j].done) continue;
+        const PrepArgs p = t.args[j];
+        prep_body(p, item - t.pfx[j]);
+        __syncthreads();
+    }
+}
+
+__global__ void mode_update_batched_kernel(const BatchTable<UpdArgs> t) {
+    const int n = *t.n;
+    const int total = n > 0 ? t.pfx[n] : 0;
+    for (int item = blockIdx.x; item < total; item += gridDim.x) {
+        const int j = batch_job_of(t.pfx, n, item);
+        if (t.state[j].done) continue;
+        const UpdArgs u = t.args[j];
+        mode_update_body(u, item - t.pfx[j]);
+        __syncthreads();
+    }
+}
+
+cudaError_t prep_batched(const BatchTable<PrepArgs> &t, int grid, cudaStream_t s) {
+    prep_batched_kernel<<<grid, 256, 0, s>>>(t);
+    return cudaGetLastError();
+}
+
+cudaError_t mode_update_batched(const BatchTable<UpdArgs> &t, int grid, cudaStream_t s) {
+    mode_update_batched_kernel<<<grid, 256, 0, s>>>(t);
     return cudaGetLastError();
 }
 
@@ -508,6 +559,32 @@ __global__ void reduce_obj_kernel(const double *parts, int n, double *out) {
 
 cudaError_t reduce_objective(const double *parts, int n, double, double *out, cudaStream_t s) {
     reduce_obj_kernel<<<1, 256, 0, s>>>(parts, n, out);
+    return cudaGetLastError();
+}
+
+// Two partial-sum arrays, each summed as reduce_obj_kernel does, then added (a first).
+__global__ void reduce_obj2_kernel(const double *a, int na, const double *b, int nb, double *out) {
+    __shared__ double sh[32];
+    double tot[2];
+    for (int k = 0; k < 2; ++k) {
+        const double *p = k ? b : a;
+        const int n = k ? nb : na;
+        double s = 0.0;
+        for (int t = threadIdx.x; t < n; t += blockDim.x) s += p[t];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+        __syncthreads();
+        tot[k] = 0.0;
+        if (threadIdx.x == 0)
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot[k] += sh[w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = tot[0] + tot[1];
+}
+
+cudaError_t reduce_objective2(const double *a, int na, const double *b, int nb, double *out, cudaStream_t s) {
+    reduce_obj2_kernel<<<1, 256, 0, s>>>(a, na, b, nb, out);
     return cudaGetLastError();
 }
 

@@ -117,7 +117,10 @@ __device__ __forceinline__ float chi2_f(float beta, float z, float zt) {
 // ---------------------------------------------------------------------------------
 // Dense 3-way CP pass (the fused reconstruct -> powers -> contract kernel)
 // ---------------------------------------------------------------------------------
-enum PassMode : int { PM_M1 = 1, PM_M2 = 2, PM_M3 = 4, PM_OBJ = 8 };
+// PM_NOX (FP32 pass only): the entries of X are taken as 0 and X is not read -- the dense part
+// of a sparse tensor's update (Section 6.3): only the denominator side (Q = Xhat^(beta-1)
+// against the den factors) is contracted, and the objective term is d_beta(0 | Xhat).
+enum PassMode : int { PM_M1 = 1, PM_M2 = 2, PM_M3 = 4, PM_OBJ = 8, PM_NOX = 16 };
 
 struct Cp3Args {
     const float *X;
@@ -145,6 +148,55 @@ struct Cp3Args {
     void *pc, *qc;
     int kp;
 };
+
+// ---------------------------------------------------------------------------------
+// Jobs that run many iterations on the device (serving slots and batched launches)
+// ---------------------------------------------------------------------------------
+// Stopping state of one job, updated on the device after every iteration.
+struct JobState {
+    double F_prev, F_last;  // objectives of the last two iterations' incoming iterates
+    double rtol;
+    int iters, max_iters, done, pad;
+};
+
+#ifdef __CUDACC__
+// One more iteration done: its incoming iterate's objective is *F.  Stop when t > 1 and
+// |F_{t-1} - F_t| / F_{t-1} <= rtol (Section 3.2's objective, relative change), or at
+// t = max_iters.
+__device__ __forceinline__ void job_step(JobState *s, const double *F) {
+    s->iters += 1;
+    s->F_prev = s->F_last;
+    s->F_last = *F;
+    const double a = s->F_prev, b = s->F_last;
+    const bool conv = s->iters > 1 && a > 0.0 && (a - b) / a <= s->rtol && (b - a) / a <= s->rtol;
+    s->done = (conv || s->iters >= s->max_iters) ? 1 : 0;
+}
+#endif
+
+// Work table of one step of a batched iteration: resident job j owns the step's work items
+// [pfx[j], pfx[j+1]) (its own launch grid for that step) and the arguments args[j]; a
+// persistent grid walks all items in one launch and skips the jobs whose state says done.
+// Every pointer is device memory; n and the tables change between launches, never during one.
+template <class A>
+struct BatchTable {
+    const int *n;           // number of resident jobs
+    const int *pfx;         // [n + 1] item prefix (pfx[0] = 0)
+    const A *args;          // [n]
+    const JobState *state;  // [n]
+};
+
+#ifdef __CUDACC__
+// The job that owns work item `item` (pfx non-decreasing, pfx[0] = 0 <= item < pfx[n]).
+__device__ __forceinline__ int batch_job_of(const int *pfx, int n, int item) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (pfx[mid] <= item) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+#endif
 
 struct Cp3Plan {
     int tc;  // 1: tensor-core (tcgen05) pass, else FP32 CUDA-core pass
@@ -176,6 +228,12 @@ cudaError_t cp3_tc_launch(const Cp3Plan &plan, const Cp3Args &a, int mode_set, i
 // outer iteration at beta != 1: mode_set one of PM_M1, PM_M2, PM_M3; same plan, partial-sum
 // layouts and results as the recomputing tensor-core pass.
 cudaError_t cp3_tc_contract_launch(const Cp3Plan &plan, const Cp3Args &a, int mode_set, cudaStream_t s);
+
+// Batched FP32 pass over the work table (every job of the table padded to rank RP): mode_set
+// PM_M1 | PM_OBJ, PM_M2 or PM_M3 (den 0 or 1), or PM_M1 | PM_M2 | PM_M3 | PM_OBJ (den 0).
+// grid <= 0: a persistent grid of every CTA that fits on the current device at once.
+cudaError_t cp3_batched_launch(int RP, const BatchTable<Cp3Args> &t, int mode_set, int den, int grid,
+                               cudaStream_t s);
 
 // ---------------------------------------------------------------------------------
 // Small kernels (epilogue.cu)
@@ -264,6 +322,7 @@ cudaError_t kr_merge(const KrArgs &k, cudaStream_t s);
 // optional chi1 / chi2 against ref and an unpadded copy into user.
 struct RunUpdArgs {
     const float *pn, *pd;  // [n_parts][rows][RP]; pd null: closed form from cf
+    const float *num_rows; // when set: Num^(n) itself, [dims[n]][RP] (pn and Ln unused)
     int n_parts, rows;
     const float *Ln[8], *Ld[8];
     int dims[8];
@@ -290,8 +349,17 @@ struct UpdArgs {
     double *obj_out;
 };
 cudaError_t mode_update(const UpdArgs &u, cudaStream_t s);
+// The same two kernels over a batched work table (items: row blocks of each job's factors for
+// prep; row blocks of mode u.e's factor, plus the objective block when obj_out is set, for the
+// update), on a persistent grid of `grid` CTAs.
+int prep_items(const PrepArgs &p);
+int mode_update_items(const UpdArgs &u);
+cudaError_t prep_batched(const BatchTable<PrepArgs> &t, int grid, cudaStream_t s);
+cudaError_t mode_update_batched(const BatchTable<UpdArgs> &t, int grid, cudaStream_t s);
 cudaError_t reduce_objective(const double *parts, int n, double add_const_unused, double *out,
                              cudaStream_t s);
+// *out = (fixed-order sum of a[0..na)) + (fixed-order sum of b[0..nb)).
+cudaError_t reduce_objective2(const double *a, int na, const double *b, int nb, double *out, cudaStream_t s);
 cudaError_t copy_f32(const float *src, float *dst, int64_t n, cudaStream_t s);
 
 }  // namespace ntf

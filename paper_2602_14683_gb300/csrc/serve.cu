@@ -1,5 +1,9 @@
 // Continuous-batching server for many small factorization jobs.
 //
+// Dense CP jobs on the FP32 path go to a batch (batch.cu): resident jobs of a class share
+// every launch of an iteration, the batch runs a few iterations per graph launch, and jobs
+// join and leave it between launches, admitted by the memory of the batch's arena.  Every
+// other job (Tucker, tensor-core precisions, a CP job larger than the arena) runs in a slot:
 // A server owns `slots` execution slots, each an ntf context (its own workspaces) and a
 // CUDA stream.  Jobs wait in a FIFO queue; a scheduler thread admits the head of the queue
 // into a free slot when the slot's estimated workspace fits the device-memory budget, runs
@@ -22,6 +26,7 @@
 #include <vector>
 
 #include "../../include/ntf.h"
+#include "ntf_batch.h"
 #include "ntf_internal.h"
 
 namespace {
@@ -30,12 +35,11 @@ using Clock = std::chrono::steady_clock;
 
 double now_s() { return std::chrono::duration<double>(Clock::now().time_since_epoch()).count(); }
 
-// Stopping state of one job, updated on the device after every iteration.
-struct JobState {
-    double F_prev, F_last;  // objectives of the last two iterations' incoming iterates
-    double rtol;
-    int iters, max_iters, done, pad;
-};
+using ntf::JobState;
+using ntf::job_step;
+
+// iterations of every batched job per graph launch of its class (the admission granularity)
+constexpr int kBatchIters = 4;
 
 struct Slot {
     ntf_ctx *ctx = nullptr;
@@ -52,16 +56,6 @@ struct Slot {
     size_t bytes = 0;
 };
 
-// One more iteration done: its incoming iterate's objective is *F.  Same test as a host
-// loop would apply: stop when t > 1 and |F_{t-1} - F_t| / F_{t-1} <= rtol, or t = max_iters.
-__device__ void job_step(JobState *s, const double *F) {
-    s->iters += 1;
-    s->F_prev = s->F_last;
-    s->F_last = *F;
-    const double a = s->F_prev, b = s->F_last;
-    const bool conv = s->iters > 1 && a > 0.0 && (a - b) / a <= s->rtol && (b - a) / a <= s->rtol;
-    s->done = (conv || s->iters >= s->max_iters) ? 1 : 0;
-}
 __global__ void job_check_kernel(JobState *s, const double *F) { job_step(s, F); }
 __global__ void job_check_loop_kernel(JobState *s, const double *F, cudaGraphConditionalHandle h) {
     job_step(s, F);
@@ -72,6 +66,7 @@ struct Pending {
     ntf_job job;
     int64_t id;
     double t_submit;
+    bool slot_lane;  // a batch-lane job that does not fit the batch's empty arena
 };
 
 int rank_pad(int R) { return R <= 8 ? 8 : R <= 16 ? 16 : R <= 32 ? 32 : 64; }
@@ -118,7 +113,8 @@ size_t estimate_bytes(const ntf_job &j, int sms) {
 
 struct ntf_server {
     int device = 0, sms = 1;
-    size_t budget = 0, used = 0;
+    size_t budget = 0, used = 0;  // slot lane: budget and estimated use
+    ntf_batch *batch = nullptr;   // batched lane (dense CP, FP32)
     std::vector<Slot> slots;
     std::deque<Pending> pending;
     std::vector<ntf_result> done;
@@ -229,23 +225,82 @@ int admit(Slot &s) {
     return NTF_OK;
 }
 
+bool batch_lane(const ntf_server *sv, const Pending &p) {
+    return sv->batch && !p.slot_lane && p.job.model == NTF_CP && p.job.precision == NTF_PREC_FP32;
+}
+
+// Batched-lane admissions, in queue order: each CP job joins the batch if its workspace fits
+// the arena now (a job that does not fit an empty arena goes to the slot lane instead); the
+// first one that does not fit stops the lane's admissions until jobs retire.
+void admit_batched(ntf_server *sv) {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    for (auto it = sv->pending.begin(); it != sv->pending.end();) {
+        if (!batch_lane(sv, *it)) {
+            ++it;
+            continue;
+        }
+        const int rc = ntf::batch_add(sv->batch, &it->job, it->id, it->t_submit);
+        if (rc == NTF_ERR_OOM) {
+            if (ntf_batch_resident(sv->batch) == 0) {
+                it->slot_lane = true;
+                ++it;
+                continue;
+            }
+            break;
+        }
+        if (rc) {
+            ntf_result r{};
+            r.id = it->id;
+            r.status = rc;
+            r.t_submit = it->t_submit;
+            r.t_admit = r.t_done = now_s();
+            sv->done.push_back(r);
+            sv->cv_done.notify_all();
+        } else {
+            ++sv->active;
+        }
+        it = sv->pending.erase(it);
+    }
+}
+
+// Launches the batch's next iterations where the previous launch has finished and moves
+// the finished jobs' results to the server's list.  Returns the number of resident jobs.
+int drive_batch(ntf_server *sv) {
+    if (!sv->batch) return 0;
+    const int res = ntf::batch_tick(sv->batch, kBatchIters, 0);
+    ntf_result buf[256];
+    for (;;) {
+        const int n = ntf_batch_results(sv->batch, buf, 256);
+        if (n <= 0) break;
+        std::lock_guard<std::mutex> lk(sv->mu);
+        for (int q = 0; q < n; ++q) sv->done.push_back(buf[q]);
+        sv->active -= n;
+        sv->cv_done.notify_all();
+    }
+    return res > 0 ? res : 0;
+}
+
 void worker_loop(ntf_server *sv) {
     cudaSetDevice(sv->device);
     for (;;) {
-        // admissions (FIFO: the head waits until a slot and the memory budget allow it)
+        admit_batched(sv);
+        // slot-lane admissions (FIFO over the slot lane's jobs: the first waits until a slot
+        // and the memory budget allow it)
         for (;;) {
             Pending p;
             int slot = -1;
             {
                 std::unique_lock<std::mutex> lk(sv->mu);
                 if (sv->stop) return;
-                if (sv->pending.empty()) break;
-                const size_t need = estimate_bytes(sv->pending.front().job, sv->sms);
+                auto head = sv->pending.begin();
+                while (head != sv->pending.end() && batch_lane(sv, *head)) ++head;
+                if (head == sv->pending.end()) break;
+                const size_t need = estimate_bytes(head->job, sv->sms);
                 for (size_t q = 0; q < sv->slots.size(); ++q)
                     if (!sv->slots[q].busy) { slot = (int)q; break; }
                 if (slot < 0 || (sv->used + need > sv->budget && sv->active > 0)) break;
-                p = sv->pending.front();
-                sv->pending.pop_front();
+                p = *head;
+                sv->pending.erase(head);
                 sv->used += need;
                 ++sv->active;
                 sv->slots[slot].bytes = need;
@@ -259,8 +314,9 @@ void worker_loop(ntf_server *sv) {
             const int rc = admit(s);
             if (rc) finish(sv, s, rc);
         }
+        // the batch's next launches and its finished jobs
+        bool any = drive_batch(sv) > 0;
         // completion of active slots (each runs its whole job as one graph launch)
-        bool any = false;
         for (auto &s : sv->slots) {
             if (!s.busy) continue;
             any = true;
@@ -303,7 +359,14 @@ int ntf_server_create(ntf_server **out, int device, int slots, size_t mem_budget
         cudaMemGetInfo(&fr, &tot);
         mem_budget_bytes = fr / 2;
     }
-    sv->budget = mem_budget_bytes;
+    // half of the budget is the batch's arena (allocated now), half the slots' estimate
+    const size_t arena = mem_budget_bytes / 2;
+    sv->budget = mem_budget_bytes - arena;
+    if (ntf_batch_create(&sv->batch, device, 4096, arena) != NTF_OK) {
+        sv->batch = nullptr;
+        delete sv;
+        return NTF_ERR_CUDA;
+    }
     sv->slots.resize(slots);
     for (auto &s : sv->slots) {
         if (ntf_ctx_create(&s.ctx, device) != NTF_OK || cudaStreamCreateWithFlags(&s.st, cudaStreamNonBlocking) != cudaSuccess ||
@@ -332,7 +395,7 @@ int ntf_server_submit(ntf_server *sv, const ntf_job *job, int64_t *id_out) {
         if (job->dims[n] < 1) return NTF_ERR_SHAPE;
     std::lock_guard<std::mutex> lk(sv->mu);
     const int64_t id = sv->next_id++;
-    sv->pending.push_back({*job, id, now_s()});
+    sv->pending.push_back({*job, id, now_s(), false});
     if (id_out) *id_out = id;
     sv->cv.notify_all();
     return NTF_OK;
@@ -359,6 +422,7 @@ void ntf_server_destroy(ntf_server *sv) {
     sv->cv.notify_all();
     if (sv->worker.joinable()) sv->worker.join();
     cudaSetDevice(sv->device);
+    if (sv->batch) ntf_batch_destroy(sv->batch);
     for (auto &s : sv->slots) {
         if (s.st) cudaStreamSynchronize(s.st);
         if (s.exec) cudaGraphExecDestroy(s.exec);

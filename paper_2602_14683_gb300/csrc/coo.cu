@@ -1,6 +1,7 @@
-// Sparse COO tensors under KL (beta = 1), Section 6.3 ("For sparse tensors"): numerators
-// are sums over the stored entries only, and Q == 1 makes every denominator the product
-// of column sums of the other factors.
+// Sparse COO tensors, Section 6.3 ("For sparse tensors"): numerators are sums over the
+// stored entries only.  Under KL (beta = 1), Q == 1 makes every denominator the product of
+// column sums of the other factors; at other beta the denominators come from a dense pass
+// that reads no X (ntf_api.cu), and this file supplies the stored-entry numerators.
 //
 // Preprocessing (once per tensor, cached by coordinate pointers and sizes):
 //   * per mode n a stable permutation pi_n ordering the entries by i_n (LSD radix sort
@@ -153,6 +154,8 @@ struct CooPassArgs {
     const int32_t *unit_beg, *unit_end;
     int n_units;
     float eps;
+    int bkind;     // beta class (BK_KL: p = x / Xhat)
+    float beta;
     float *part;   // [n_units][RP]
     double *obj;   // per-warp objective partials or null
 };
@@ -186,18 +189,30 @@ __global__ void __launch_bounds__(256) coo_pass_kernel(const CooPassArgs a) {
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         const float x = __ldg(a.sval + t);
         const float y = fmaxf(s, a.eps);
-        const float p = __fdiv_rn(x, y);
+        float p;
+        if (a.bkind == BK_KL) {
+            p = __fdiv_rn(x, y);
+        } else {  // P = x Xhat^(beta - 2) (Section 4.1); Q is the dense pass's
+            float q;
+            pq_powers(a.bkind, a.beta, x, y, p, q);
+        }
 #pragma unroll
         for (int g = 0; g < RG; ++g) acc[g] = fmaf(p, zex[g], acc[g]);
         if (a.obj && lane == 0 && x > 0.0f) {
-            // x log(x / y) - x, the stored-entry part of d_1 (the + y part is summed in closed form)
-            const float r = __fdiv_rn(y, x);
             float d;
-            if (r > 1e-4f && r < 1e4f) {
-                const float tt = r - 1.0f;
-                d = x * (tt - log1pf(tt)) - y;
+            if (a.bkind == BK_KL) {
+                // x log(x / y) - x, the stored-entry part of d_1 (the + y part is summed in closed form)
+                const float r = __fdiv_rn(y, x);
+                if (r > 1e-4f && r < 1e4f) {
+                    const float tt = r - 1.0f;
+                    d = x * (tt - log1pf(tt)) - y;
+                } else {
+                    d = x * (logf(x) - logf(y)) - x;
+                }
             } else {
-                d = x * (logf(x) - logf(y)) - x;
+                // d_beta(x | y) - d_beta(0 | y): the dense pass adds d_beta(0 | y) = y^beta / beta
+                // over every entry, stored or not
+                d = dbeta_stable(a.bkind, a.beta, x, y) - dbeta_stable(a.bkind, a.beta, 0.0f, y);
             }
             objf += d;
         }
@@ -512,7 +527,7 @@ int get_cache(ntf_ctx *ctx, const ntf_tensor *X, CooCache *&out, cudaStream_t st
 }
 
 int launch_coo_pass(ntf_ctx *ctx, const CooCache &c, int n, int RP, const float *const *rec, const float *const *num,
-                    float eps, float *part, double *obj, cudaStream_t st) {
+                    float eps, float *part, double *obj, cudaStream_t st, int bkind = BK_KL, float beta = 1.0f) {
     const ModeData &d = c.md[n];
     if (d.n_units == 0) return NTF_OK;
     CooPassArgs a{};
@@ -527,11 +542,14 @@ int launch_coo_pass(ntf_ctx *ctx, const CooCache &c, int n, int RP, const float 
     a.unit_end = d.unit_end;
     a.n_units = d.n_units;
     a.eps = eps;
+    a.bkind = bkind;
+    a.beta = beta;
     a.part = part;
     a.obj = obj;
     const unsigned grid = (unsigned)((d.n_units + 7) / 8);
     bool same = true;  // the rank-32 kernel reads one set of factors for both roles
     for (int m = 0; m < c.N; ++m) same = same && rec[m] == num[m];
+    same = same && bkind == BK_KL;  // the rank-32 kernel computes p = x / Xhat
     if (RP == 32 && same && c.N <= 4) coo_pass32_kernel<4><<<grid, 256, 0, st>>>(a);
     else if (RP == 32 && same) coo_pass32_kernel<8><<<grid, 256, 0, st>>>(a);
     else if (RP == 32) coo_pass_kernel<1><<<grid, 256, 0, st>>>(a);
@@ -662,6 +680,28 @@ int coo_kl_sweep(ntf_ctx *ctx, const ntf_tensor *X, int R, float *const *factors
     }
     // the pointer/row tables above are read by kernels in flight; they live in the
     // context's workspace, so later calls may overwrite them only after this stream work
+    return NTF_OK;
+}
+
+int coo_num_rows(ntf_ctx *ctx, const ntf_tensor *X, int n, int RP, const float *const *rec, const float *const *num,
+                 float beta, float eps, float *out, double **obj_parts, int *n_obj, cudaStream_t st) {
+    CooCache *c = nullptr;
+    int rc = get_cache(ctx, X, c, st);
+    if (rc) return rc;
+    if (RP != 32 && RP != 64) return ctx_fail(ctx, NTF_ERR_UNSUPPORTED, "COO passes pad the rank to 32 or 64");
+    float *part = (float *)ctx_ws(ctx, "cooPart", sizeof(float) * (size_t)(c->max_units + 1) * RP);
+    float *gpart = (float *)ctx_ws(ctx, "cooGpart", sizeof(float) * (size_t)(c->max_groups + 1) * RP);
+    double *objp = (double *)ctx_ws(ctx, "cooObjP", sizeof(double) * (size_t)(c->max_units + 1));
+    if (!part || !gpart || !objp) return ctx_fail(ctx, NTF_ERR_OOM, "COO workspace allocation failed");
+    const bool want_obj = obj_parts != nullptr;
+    if (want_obj && c->md[n].n_units == 0) CK(cudaMemsetAsync(objp, 0, sizeof(double), st));
+    rc = launch_coo_pass(ctx, *c, n, RP, rec, num, eps, part, want_obj ? objp : nullptr, st, beta_kind(beta), beta);
+    if (rc) return rc;
+    if (want_obj) {
+        *obj_parts = objp;
+        *n_obj = c->md[n].n_units > 0 ? c->md[n].n_units : 1;
+    }
+    if (out) return row_sums(ctx, *c, n, RP, part, gpart, out, st);
     return NTF_OK;
 }
 

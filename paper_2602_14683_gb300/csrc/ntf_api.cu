@@ -160,7 +160,7 @@ std::vector<int> tune_candidates(const ntf::Cp3Plan &model, int I, int sms) {
 }
 
 int cp_dense_setup(ntf_ctx *ctx, const ntf_tensor *X, int R, bool jcomm, bool need_den, int precision,
-                   CpDense &s, const ntf_opts *tune_opts = nullptr, int tune_bk = 0, int tune_ms = 0) {
+                   CpDense &s, const ntf_opts *tune_opts = nullptr, int tune_bk = 0, int tune_ms = 0, int min_rp = 0) {
     s.I = (int)X->dims[0];
     s.J = (int)X->dims[1];
     s.K = (int)X->dims[2];
@@ -168,7 +168,7 @@ int cp_dense_setup(ntf_ctx *ctx, const ntf_tensor *X, int R, bool jcomm, bool ne
     // tensor-core passes where the request asks for them and the shapes allow (rank padded
     // to 32, rows of X 16-byte aligned for TMA); FP32 CUDA-core passes otherwise
     const bool tc = precision != NTF_PREC_FP32 && R <= 32 && ntf::cp3_tc_eligible(32, s.K, X->values);
-    s.RP = tc ? 32 : rank_pad(R);
+    s.RP = tc ? 32 : std::max(rank_pad(R), min_rp);
     s.tc = tc;
     // 256-column blocks where the tensor memory allows them (KL: no denominator accumulators;
     // single TF32: no low-part C tile)
@@ -749,7 +749,7 @@ int nway_split(ntf_ctx *ctx, const ntf_tensor *X, int R, const ntf_opts &o, int 
 }
 
 int nway_setup(ntf_ctx *ctx, const ntf_tensor *X, int R, bool jcomm, bool need_den, int precision,
-               const ntf_opts &o, CpDense &s, NWay &w) {
+               const ntf_opts &o, CpDense &s, NWay &w, int min_rp = 0) {
     w.N = X->order;
     int a = 0, b = 0;
     int rc = nway_split(ctx, X, R, o, precision, a, b);
@@ -766,7 +766,7 @@ int nway_setup(ntf_ctx *ctx, const ntf_tensor *X, int R, bool jcomm, bool need_d
     w.X3 = *X;
     w.X3.order = 3;
     w.X3.dims = w.dims3;
-    if ((rc = cp_dense_setup(ctx, &w.X3, R, jcomm, need_den, precision, s))) return rc;
+    if ((rc = cp_dense_setup(ctx, &w.X3, R, jcomm, need_den, precision, s, nullptr, 0, 0, min_rp))) return rc;
     const bool chi = jcomm && need_den;
     for (int m = 0; m < w.N; ++m) {
         const int v = w.view[m];
@@ -861,12 +861,13 @@ struct RunUpd {
 };
 
 int nway_run_update(ntf_ctx *ctx, NWay &w, CpDense &s, int n, float beta, const ntf_opts &o, bool kl,
-                    const RunUpd &q, cudaStream_t st) {
+                    const RunUpd &q, cudaStream_t st, const float *num_rows = nullptr) {
     const int v = w.view[n];
     const int parts[3] = {s.plan.parts1, s.plan.parts2, s.plan.parts3};
     ntf::RunUpdArgs u{};
     u.pn = s.pn[v];
     u.pd = kl ? nullptr : s.pd[v];
+    u.num_rows = num_rows;
     u.n_parts = parts[v];
     u.rows = (int)w.dims3[v];
     u.M = w.ge[v] - w.gb[v];
@@ -1007,6 +1008,106 @@ int cp_nway_beta_div(ntf_ctx *ctx, const ntf_tensor *X, float beta, int R, const
     return NTF_OK;
 }
 
+// ------------------------------------------------- sparse COO tensors at beta != 1
+// Section 6.3: P = X (.) Xhat^(beta-2) vanishes where X does, so Num^(n) is a sum over the
+// stored entries (a COO pass, coo.cu); Q = Xhat^(beta-1) does not, so Den^(n) contracts it over
+// the whole index space: a dense pass that reads no X (PM_NOX), on the N modes cut into three
+// runs as for dense tensors of order N.  The objective splits the same way: the stored entries
+// contribute d_beta(x | y) - d_beta(0 | y) and the dense pass sum_i d_beta(0 | y_i).  beta = 0
+// is excluded: d_0(x | y) needs x > 0 everywhere, which a tensor with unstored zeros is not.
+int coo_beta_check(ntf_ctx *ctx, const ntf_tensor *X, float beta) {
+    if (ntf::beta_kind(beta) == ntf::BK_IS)
+        return fail(ctx, NTF_ERR_UNSUPPORTED, "beta = 0 needs positive data; a COO tensor has unstored zeros");
+    if (X->order < 3) return fail(ctx, NTF_ERR_UNSUPPORTED, "COO tensors at beta != 1 need order >= 3");
+    return NTF_OK;
+}
+
+int cp_coo_beta_setup(ntf_ctx *ctx, const ntf_tensor *X, int R, bool jcomm, const ntf_opts &o, CpDense &s, NWay &w) {
+    ntf_tensor Xv = *X;  // the index space of X, cut into three runs like a dense tensor
+    Xv.kind = NTF_DENSE;
+    ntf_opts od = o;
+    od.precision = NTF_PREC_FP32;
+    return nway_setup(ctx, &Xv, R, jcomm, true, NTF_PREC_FP32, od, s, w, R <= 32 ? 32 : 64);
+}
+
+// B-CoMM sweep (Algorithm 1; jcomm = false) or J-CoMM outer iteration (Algorithm 2).
+int cp_coo_beta(ntf_ctx *ctx, const ntf_tensor *X, float beta, int R, float *const *factors, const ntf_opts &o,
+                double *objective_dev, cudaStream_t st, bool jcomm) {
+    int rc = coo_beta_check(ctx, X, beta);
+    if (rc) return rc;
+    CpDense s{};
+    NWay w{};
+    if ((rc = cp_coo_beta_setup(ctx, X, R, jcomm, o, s, w))) return rc;
+    if ((rc = nway_init(ctx, w, s, factors, jcomm, jcomm, st))) return rc;
+    int64_t maxdim = 1;
+    for (int m = 0; m < w.N; ++m) maxdim = std::max(maxdim, w.dims[m]);
+    float *num = (float *)ws_get(ctx, "coobNum", sizeof(float) * (size_t)maxdim * s.RP);
+    if (!num) return fail(ctx, NTF_ERR_OOM, "workspace allocation failed");
+    ntf::Cp3Args a = cp_args(&w.X3, s, o, beta);
+    a.X = nullptr;
+    a.vec16 = 0;
+    for (int m = 0; m < 3; ++m) {
+        a.rec[m] = jcomm ? s.Ft[m] : s.F[m];
+        a.num[m] = a.den[m] = jcomm ? s.C2[m] : s.F[m];
+    }
+    // per-mode blocks for the stored-entry pass: Xhat from rec, Num against chi_1 (J-CoMM)
+    float *const *rec = jcomm ? w.Pt : w.P;
+    float *const *nf = jcomm ? w.C1P : w.P;
+    const int L = jcomm ? o.inner_L : 1;
+    for (int l = 0; l < L; ++l) {
+        for (int n = 0; n < w.N; ++n) {
+            const int v = w.view[n];
+            const bool obj = l == 0 && n == 0 && objective_dev;
+            {
+                PassTimer t(ctx, st);
+                NTF_CUDA(ntf::cp3_launch(s.plan, a, mode_flag(v) | ntf::PM_NOX | (obj ? ntf::PM_OBJ : 0), 1, st));
+            }
+            double *objp = nullptr;
+            int nobj = 0;
+            if ((rc = ntf::coo_num_rows(ctx, X, n, s.RP, rec, nf, beta, (float)o.eps, num, obj ? &objp : nullptr,
+                                        &nobj, st)))
+                return rc;
+            if (obj) NTF_CUDA(ntf::reduce_objective2(objp, nobj, s.obj, s.plan.grid, objective_dev, st));
+            float *user = l == L - 1 ? factors[n] : nullptr;
+            const RunUpd q = jcomm ? RunUpd{w.C1P, w.C2P, w.Pt[n], w.P[n], user, w.Pt[n], w.C1P[n], w.C2P[n]}
+                                   : RunUpd{w.P, w.P, w.P[n], w.P[n], user, nullptr, nullptr, nullptr};
+            if ((rc = nway_run_update(ctx, w, s, n, beta, o, false, q, st, num))) return rc;
+            if (!nway_single(w, v)) {  // the run's 3-way slots follow its updated blocks
+                if (jcomm) {
+                    NTF_CUDA(nway_merge(w, s, v, w.C1P, s.C1[v], nullptr, st));
+                    NTF_CUDA(nway_merge(w, s, v, w.C2P, s.C2[v], nullptr, st));
+                } else {
+                    NTF_CUDA(nway_merge(w, s, v, w.P, s.F[v], nullptr, st));
+                }
+            }
+        }
+    }
+    return NTF_OK;
+}
+
+int cp_coo_beta_div(ntf_ctx *ctx, const ntf_tensor *X, float beta, int R, const float *const *factors,
+                    const ntf_opts &o, double *out_dev, cudaStream_t st) {
+    int rc = coo_beta_check(ctx, X, beta);
+    if (rc) return rc;
+    CpDense s{};
+    NWay w{};
+    if ((rc = cp_coo_beta_setup(ctx, X, R, false, o, s, w))) return rc;
+    if ((rc = nway_init(ctx, w, s, factors, false, false, st))) return rc;
+    ntf::Cp3Args a = cp_args(&w.X3, s, o, beta);
+    a.X = nullptr;
+    a.vec16 = 0;
+    for (int m = 0; m < 3; ++m) a.rec[m] = a.num[m] = a.den[m] = s.F[m];
+    {
+        PassTimer t(ctx, st);
+        NTF_CUDA(ntf::cp3_launch(s.plan, a, ntf::PM_OBJ | ntf::PM_NOX, 0, st));
+    }
+    double *objp = nullptr;
+    int nobj = 0;
+    if ((rc = ntf::coo_num_rows(ctx, X, 0, s.RP, w.P, w.P, beta, (float)o.eps, nullptr, &objp, &nobj, st))) return rc;
+    NTF_CUDA(ntf::reduce_objective2(objp, nobj, s.obj, s.plan.grid, out_dev, st));
+    return NTF_OK;
+}
+
 int cp_dense_beta_div(ntf_ctx *ctx, const ntf_tensor *X, float beta, int R, const float *const *factors,
                       const ntf_opts &o, double *out_dev, cudaStream_t st) {
     CpDense s{};
@@ -1141,7 +1242,7 @@ int ntf_cp_mu_sweep(ntf_ctx *ctx, const ntf_tensor *X, float beta, int rank, flo
     cudaStream_t st = (cudaStream_t)stream;
     if (X->kind == NTF_COO) {
         if (ntf::beta_kind(beta) != ntf::BK_KL)
-            return fail(ctx, NTF_ERR_UNSUPPORTED, "COO tensors are implemented for beta = 1 only");
+            return cp_coo_beta(ctx, X, beta, rank, factors, o, objective_dev, st, /*jcomm=*/false);
         return ntf::coo_kl_sweep(ctx, X, rank, factors, o, objective_dev, st, /*jcomm=*/false);
     }
     if (X->order > 3) return cp_nway_mu_sweep(ctx, X, beta, rank, factors, o, objective_dev, st);
@@ -1251,7 +1352,7 @@ int ntf_jcomm_outer(ntf_ctx *ctx, int model, const ntf_tensor *X, float beta, in
         if (rc) return rc;
         if (X->kind == NTF_COO) {
             if (ntf::beta_kind(beta) != ntf::BK_KL)
-                return fail(ctx, NTF_ERR_UNSUPPORTED, "COO tensors are implemented for beta = 1 only");
+                return cp_coo_beta(ctx, X, beta, rank_or_0, factors, o, objective_ref_dev, st, /*jcomm=*/true);
             return ntf::coo_kl_sweep(ctx, X, rank_or_0, factors, o, objective_ref_dev, st, /*jcomm=*/true);
         }
         if (X->order > 3) return cp_nway_jcomm(ctx, X, beta, rank_or_0, factors, o, objective_ref_dev, st);
@@ -1280,7 +1381,7 @@ int ntf_beta_div(ntf_ctx *ctx, int model, const ntf_tensor *X, float beta, int r
         if (rc) return rc;
         if (X->kind == NTF_COO) {
             if (ntf::beta_kind(beta) != ntf::BK_KL)
-                return fail(ctx, NTF_ERR_UNSUPPORTED, "COO tensors are implemented for beta = 1 only");
+                return cp_coo_beta_div(ctx, X, beta, rank_or_0, factors, o, out_dev, st);
             return ntf::coo_kl_objective(ctx, X, rank_or_0, factors, o, out_dev, st);
         }
         if (X->order > 3) return cp_nway_beta_div(ctx, X, beta, rank_or_0, factors, o, out_dev, st);

@@ -72,7 +72,7 @@ def test_coo_block_mu_parity(R):
     assert abs(obj.item() - Fw) / abs(Fw) <= TOL
 
 
-def test_coo_objective_and_non_kl_rejected():
+def test_coo_objective_and_is_rejected():
     ntf = _ntf()
     dims, idx, vals = _small_coo(21)
     A = synth.init_factors(dims, 6, seed=5)
@@ -80,8 +80,8 @@ def test_coo_objective_and_non_kl_rejected():
     X = _coo_dev(dims, idx, vals)
     got = ntf.beta_div(X, 1.0, [dev(a) for a in A]).item()
     assert abs(got - want) / abs(want) <= TOL
-    with pytest.raises(ntf.NtfError) as e:
-        ntf.jcomm_outer(X, 1.5, [dev(a) for a in A])
+    with pytest.raises(ntf.NtfError) as e:  # beta = 0 needs x > 0 everywhere
+        ntf.jcomm_outer(X, 0.0, [dev(a) for a in A])
     assert e.value.code == -8
 
 

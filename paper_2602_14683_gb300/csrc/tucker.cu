@@ -34,17 +34,6 @@ namespace ntf {
 // range, products are summed in FP32 over blocks of GCARRY * GK terms and the blocks in
 // FP64; a range of one block never touches FP64 (a slow pipe on this part).
 // ----------------------------------------------------------------------------------
-struct Gemm {
-    const float *A, *B;
-    float *C;
-    int M, N, K1, K2, batch;
-    int64_t sab, sam, sak1, sak2;
-    int64_t sbb, sbk1, sbk2, sbn;
-    int64_t scb, scm, scn;
-    int splits, kchunks;  // reduction ranges and GK-chunks per range (set by gemm())
-    float *part;          // [splits][batch][M][N] when splits > 1
-};
-
 constexpr int GK = 16;   // reduction chunk
 constexpr int GCARRY = 16;  // chunks summed in FP32 before the FP64 carry
 
@@ -210,15 +199,59 @@ __global__ void gemm_split_sum_kernel(const Gemm g) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t mn = (int64_t)g.M * g.N, total = mn * g.batch;
     if (t >= total) return;
-    double v = 0.0;
-    for (int sp = 0; sp < g.splits; ++sp) v += (double)g.part[(int64_t)sp * total + t];
+    double v = 0.0;  // the ranges in order; their loads eight at a time
+    for (int sp0 = 0; sp0 < g.splits; sp0 += 8) {
+        float x[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) x[q] = sp0 + q < g.splits ? g.part[(int64_t)(sp0 + q) * total + t] : 0.0f;
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            if (sp0 + q < g.splits) v += (double)x[q];
+    }
     const int bt = (int)(t / mn), m = (int)((t % mn) / g.N), n = (int)(t % g.N);
     g.C[bt * g.scb + m * g.scm + n * g.scn] = (float)v;
 }
 
 // Splits the reduction when the output tiles alone would leave most SMs idle: about two
-// CTAs per SM, at least four GK-chunks per range.
-static int gemm(ntf_ctx *ctx, Gemm g, cudaStream_t s) {
+// CTAs per SM, at least four GK-chunks per range (two 32-index chunks on the tensor cores).
+// mode: 0 FP32 CUDA cores, 1 tcgen05 on TF32 operands, 2 tcgen05 on split (3xTF32) operands.
+static int gemm(ntf_ctx *ctx, Gemm g, cudaStream_t s, int mode = 0) {
+    // tensor-core tile width: the widest that still gives two CTAs per SM, else 32 columns
+    int ntt = 32;
+    for (int w = 256; w >= 64; w >>= 1) {
+        if (g.N <= w / 2) continue;
+        const int64_t tl = (int64_t)((g.N + w - 1) / w) * ((g.M + 127) / 128) * g.batch;
+        if (tl >= 2 * ctx_num_sms(ctx)) {
+            ntt = w;
+            break;
+        }
+    }
+    const int64_t tiles_tc = (int64_t)((g.N + ntt - 1) / ntt) * ((g.M + 127) / 128) * g.batch;
+    const int nchunks_tc = (g.K1 * g.K2 + 31) / 32;
+    int splits_tc = (int)std::min<int64_t>((2 * ctx_num_sms(ctx) + tiles_tc - 1) / tiles_tc, 1 << 20);
+    splits_tc = std::max(1, std::min(splits_tc, nchunks_tc / 2));
+    // grid limits of the tensor-core form (batch x splits on the z dimension): else FP32
+    if ((int64_t)g.batch * splits_tc > 65535 || g.N > 65535 * 256) mode = 0;
+    if (mode) {
+        const int nchunks = std::max(1, nchunks_tc);
+        g.kchunks = std::max(1, (nchunks + splits_tc - 1) / splits_tc);
+        g.splits = std::max(1, (nchunks + g.kchunks - 1) / g.kchunks);
+        g.err = ctx_status(ctx);
+        if (g.splits > 1) {
+            g.part = (float *)ctx_ws(ctx, "gemm_split", sizeof(float) * (size_t)g.splits * g.batch * g.M * g.N);
+            if (!g.part) return ctx_fail(ctx, NTF_ERR_OOM, "workspace allocation failed");
+        }
+        cudaError_t e = gemm_tc_launch(g, mode == 2, ntt, s);
+        if (e == cudaSuccess && g.splits > 1) {
+            const int64_t total = (int64_t)g.M * g.N * g.batch;
+            gemm_split_sum_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(g);
+            e = cudaGetLastError();
+            ctx_count(ctx, 1);
+        }
+        if (e != cudaSuccess) return ctx_fail(ctx, NTF_ERR_CUDA, cudaGetErrorString(e));
+        ctx_count(ctx, 1);
+        return NTF_OK;
+    }
     // tile shape: four batches per CTA for outputs of at most 32 x 32, 64 x 16 or 128 x 8, else by
     // width
     const bool multi = g.batch >= 4 && ((g.M <= 32 && g.N <= 32) || (g.M <= 64 && g.N <= 16) ||
@@ -706,6 +739,7 @@ struct TuckerWs {
     float *cs;                // [RP] column sums (closed-form denominators at beta = 1)
     double *cs_part;          // [CSB][RP] their partials
     Blocks cur, ref, t1, t2;  // current, reference, chi1 and chi2 transforms
+    int gemm_mode;            // small contractions: 0 FP32, 1 TF32 tensor cores, 2 3xTF32 tensor cores
 };
 
 #define TK(call)                                                                   \
@@ -730,14 +764,14 @@ int build_b3(ntf_ctx *ctx, TuckerWs &w, const Blocks &b, float *out, cudaStream_
     g.A = b.A1; g.B = b.G; g.C = w.GA1;
     g.M = w.I1; g.N = w.J2 * w.J3; g.K1 = w.J1; g.K2 = 1; g.batch = 1;
     g.sam = w.J1; g.sak1 = 1; g.sbk1 = (int64_t)w.J2 * w.J3; g.sbn = 1; g.scm = (int64_t)w.J2 * w.J3; g.scn = 1;
-    { const int rc_ = gemm(ctx, g, st); if (rc_) return rc_; }
+    { const int rc_ = gemm(ctx, g, st, w.gemm_mode); if (rc_) return rc_; }
     Gemm h{};
     h.A = b.A2; h.B = w.GA1; h.C = out;
     h.M = w.I2; h.N = w.J3; h.K1 = w.J2; h.K2 = 1; h.batch = w.I1;
     h.sab = 0; h.sam = w.J2; h.sak1 = 1;
     h.sbb = (int64_t)w.J2 * w.J3; h.sbk1 = w.J3; h.sbn = 1;
     h.scb = (int64_t)w.I2 * w.RP; h.scm = w.RP; h.scn = 1;
-    { const int rc_ = gemm(ctx, h, st); if (rc_) return rc_; }
+    { const int rc_ = gemm(ctx, h, st, w.gemm_mode); if (rc_) return rc_; }
     return NTF_OK;
 }
 
@@ -822,13 +856,13 @@ int contract_from_w(ntf_ctx *ctx, TuckerWs &w, int block, const Blocks &b, const
         g.sam = 1; g.sak1 = w.J2;
         g.sbb = (int64_t)w.I2 * w.RP; g.sbk1 = w.RP; g.sbn = 1;
         g.scb = (int64_t)w.J2 * w.J3; g.scm = w.J3; g.scn = 1;
-        { const int rc_ = gemm(ctx, g, st); if (rc_) return rc_; }
+        { const int rc_ = gemm(ctx, g, st, w.gemm_mode); if (rc_) return rc_; }
         Gemm h{};
         h.A = b.A1; h.B = w.Y; h.C = out;
         h.M = w.J1; h.N = w.J2 * w.J3; h.K1 = w.I1; h.K2 = 1; h.batch = 1;
         h.sam = 1; h.sak1 = w.J1; h.sbk1 = (int64_t)w.J2 * w.J3; h.sbn = 1;
         h.scm = (int64_t)w.J2 * w.J3; h.scn = 1;
-        { const int rc_ = gemm(ctx, h, st); if (rc_) return rc_; }
+        { const int rc_ = gemm(ctx, h, st, w.gemm_mode); if (rc_) return rc_; }
     } else if (block == 1) {  // H[j][a][c] = sum_b A2[j,b] G[a,b,c]; Num1 = sum_{j,c} W H
         Gemm g{};
         g.A = b.A2; g.B = b.G; g.C = w.H;
@@ -836,27 +870,27 @@ int contract_from_w(ntf_ctx *ctx, TuckerWs &w, int block, const Blocks &b, const
         g.sam = w.J2; g.sak1 = 1;
         g.sbb = (int64_t)w.J2 * w.J3; g.sbk1 = w.J3; g.sbn = 1;
         g.scb = w.J3; g.scm = (int64_t)w.J1 * w.J3; g.scn = 1;
-        { const int rc_ = gemm(ctx, g, st); if (rc_) return rc_; }
+        { const int rc_ = gemm(ctx, g, st, w.gemm_mode); if (rc_) return rc_; }
         Gemm h{};
         h.A = W; h.B = w.H; h.C = out;
         h.M = w.I1; h.N = w.J1; h.K1 = w.I2; h.K2 = w.J3; h.batch = 1;
         h.sam = (int64_t)w.I2 * w.RP; h.sak1 = w.RP; h.sak2 = 1;
         h.sbk1 = (int64_t)w.J1 * w.J3; h.sbk2 = 1; h.sbn = w.J3;
         h.scm = w.J1; h.scn = 1;
-        { const int rc_ = gemm(ctx, h, st); if (rc_) return rc_; }
+        { const int rc_ = gemm(ctx, h, st, w.gemm_mode); if (rc_) return rc_; }
     } else {  // GA1[i][b][c] = sum_a A1[i,a] G[a,b,c]; Num2 = sum_{i,c} W GA1
         Gemm g{};
         g.A = b.A1; g.B = b.G; g.C = w.GA1;
         g.M = w.I1; g.N = w.J2 * w.J3; g.K1 = w.J1; g.K2 = 1; g.batch = 1;
         g.sam = w.J1; g.sak1 = 1; g.sbk1 = (int64_t)w.J2 * w.J3; g.sbn = 1; g.scm = (int64_t)w.J2 * w.J3; g.scn = 1;
-        { const int rc_ = gemm(ctx, g, st); if (rc_) return rc_; }
+        { const int rc_ = gemm(ctx, g, st, w.gemm_mode); if (rc_) return rc_; }
         Gemm h{};
         h.A = W; h.B = w.GA1; h.C = out;
         h.M = w.I2; h.N = w.J2; h.K1 = w.I1; h.K2 = w.J3; h.batch = 1;
         h.sam = w.RP; h.sak1 = (int64_t)w.I2 * w.RP; h.sak2 = 1;
         h.sbk1 = (int64_t)w.J2 * w.J3; h.sbk2 = 1; h.sbn = w.J3;
         h.scm = w.J2; h.scn = 1;
-        { const int rc_ = gemm(ctx, h, st); if (rc_) return rc_; }
+        { const int rc_ = gemm(ctx, h, st, w.gemm_mode); if (rc_) return rc_; }
     }
     return NTF_OK;
 }
@@ -871,6 +905,8 @@ int setup(ntf_ctx *ctx, const ntf_tensor *X, const int64_t *core_dims, bool jcom
     w.tc = o.precision != NTF_PREC_FP32 && w.J3 <= 32 && cp3_tc_eligible(32, w.I3, X->values) &&
            (int64_t)w.I1 * w.I2 < (1ll << 31);
     w.RP = w.tc ? 32 : rank_pad(w.J3);
+    // the small contractions follow the passes: tensor cores when the passes use them
+    w.gemm_mode = !w.tc ? 0 : o.precision == NTF_PREC_3XTF32 ? 2 : 1;
     const int64_t IJ = (int64_t)w.I1 * w.I2, Jc = (int64_t)w.J1 * w.J2 * w.J3;
     bool ok = true;
     w.Brec = wsf(ctx, "tkBrec", IJ * w.RP, ok);

@@ -1,0 +1,286 @@
+// The small contractions of the Tucker updates on the 5th-generation tensor cores (tcgen05).
+//
+// The partial tensor B^(3) = G x_1 A^(1) x_2 A^(2) (eq. (block_Bn)), the core contractions of
+// eq. (block_core_num_den) and the factor contractions of eqs. (block_factor_num/den) are all
+// strided batched products C[bt] = sum_k A(bt, m, k) B(bt, k, n) (the Gemm of ntf_tucker.h).
+// Here one CTA of four warps computes a 128 x NTT tile of one batch over one reduction range:
+//   * per chunk of 32 reduction indices, the threads gather the A and B tiles with plain loads
+//     (any strides), round them to TF32 (and, for 3xTF32, the remainders too) and store them into
+//     128-byte-swizzled K-major tiles (one 128-byte row per m or n) of a two-stage ring in shared
+//     memory.  An operand whose rows are contiguous (unit m or n stride) is read with consecutive
+//     lanes on consecutive rows, any other with consecutive lanes on consecutive reduction
+//     indices, so that a warp's load touches as few lines as the layout allows; the loads of
+//     chunk c + 1 are issued into registers before chunk c's MMAs;
+//   * thread 0 issues the chunk's tcgen05.mma.kind::tf32 (M 128, N NTT, K 8 four times; with the
+//     split hi*hi + hi*lo + lo*hi) into one TMEM accumulator and commits to the stage's mbarrier,
+//     which the threads wait on before they refill that stage two chunks later;
+//   * after the last chunk each warp reads its 32 TMEM lanes (rows), transposes them through
+//     shared memory and stores whole rows (consecutive lanes on consecutive columns).
+// Every wait is bounded; a wait that runs out sets the context's status word, and the kernel then
+// writes nothing, waits (bounded) for its MMAs and frees its TMEM.
+#include "cp3_tc.cuh"
+#include "ntf_tucker.h"
+
+namespace ntf {
+namespace tgemm {
+
+using tc::fence_after;
+using tc::fence_async_smem;
+using tc::fence_before;
+using tc::idesc_tf32;
+using tc::mbar_wait;
+using tc::mma_commit;
+using tc::mma_tf32;
+using tc::sdesc;
+using tc::su32;
+using tc::swf;
+using tc::tf32_rna;
+using tc::tmem_ld32;
+
+constexpr int NTH = 128;
+constexpr int KC = 32;  // reduction indices per chunk: one 128-byte TF32 row of each tile
+
+template <int NTT, bool S3>
+struct Geo {
+    static constexpr int ABYTES = 128 * KC * 4;  // 16 KB
+    static constexpr int BBYTES = NTT * KC * 4;  // NTT rows of 128 bytes
+    static constexpr int STAGE = (ABYTES + BBYTES) * (S3 ? 2 : 1);
+    static constexpr int SMEM = 2 * STAGE + 64 + 1024;  // + barriers, TMEM slot, flags; + alignment slack
+};
+
+// One operand tile (NR rows x 32 reduction indices k0 .. k0 + 31) of a chunk: element (row r,
+// index kk) = base[r srow + k1 sk1 + k2 sk2] with k0 + kk = k1 K2 + k2, zero outside rows < nrow or
+// indices < kend.  Each thread holds NR / 4 elements: with unit row stride (rowmode) thread t takes
+// row t % NR (consecutive lanes, consecutive rows) and a run of consecutive indices; otherwise its
+// lane is the index and the warps take rows in turn.  load_tile issues the global loads into
+// registers (a chunk ahead of its use), store_tile rounds them to TF32 and writes the swizzled
+// K-major tiles hi (and lo).
+template <int NR>
+struct TileMap {
+    static constexpr int TPR = NR >= NTH ? 1 : NTH / NR;  // rowmode: threads per row
+    static constexpr int RK = KC / TPR;                  // rowmode: indices per thread and row
+    static constexpr int RPT = NR >= NTH ? NR / NTH : 1;  // rowmode: rows per thread
+    static constexpr int PER = NR / 4;                   // elements per thread (both modes)
+};
+
+template <int NR>
+__device__ __forceinline__ void load_tile(float (&v)[NR / 4], bool rowmode, const float *base, int64_t srow,
+                                          int64_t sk1, int64_t sk2, int K2, int k0, int kend, int nrow, int t) {
+    using T = TileMap<NR>;
+    if (rowmode) {
+#pragma unroll
+        for (int p = 0; p < T::RPT; ++p) {
+            const int r = NR >= NTH ? t + NTH * p : t % NR;
+            const int kk0 = NR >= NTH ? 0 : (t / NR) * T::RK;
+            int k = k0 + kk0, k1 = K2 == 1 ? k : k / K2, k2 = k - k1 * K2;
+            const bool rv = r < nrow;
+#pragma unroll
+            for (int q = 0; q < T::RK; ++q) {
+                v[p * T::RK + q] = (rv && k + q < kend) ? __ldg(base + r + (int64_t)k1 * sk1 + (int64_t)k2 * sk2) : 0.0f;
+                if (++k2 == K2) {
+                    k2 = 0;
+                    ++k1;
+                }
+            }
+        }
+    } else {
+        const int lane = t & 31, warp = t >> 5;
+        const int k = k0 + lane;
+        const bool kv = k < kend;
+        int k1 = 0, k2 = 0;
+        if (kv) {
+            k1 = K2 == 1 ? k : k / K2;
+            k2 = k - k1 * K2;
+        }
+        const float *p = base + (int64_t)k1 * sk1 + (int64_t)k2 * sk2;
+#pragma unroll
+        for (int i = 0; i < T::PER; ++i) {
+            const int r = 4 * i + warp;
+            v[i] = (kv && r < nrow) ? __ldg(p + (int64_t)r * srow) : 0.0f;
+        }
+    }
+}
+
+template <int NR, bool S3>
+__device__ __forceinline__ void store_tile(const float (&v)[NR / 4], bool rowmode, float *hi, float *lo, int t) {
+    using T = TileMap<NR>;
+    if (rowmode) {
+#pragma unroll
+        for (int p = 0; p < T::RPT; ++p) {
+            const int r = NR >= NTH ? t + NTH * p : t % NR;
+            const int kk0 = NR >= NTH ? 0 : (t / NR) * T::RK;
+#pragma unroll
+            for (int q = 0; q < T::RK; ++q) {
+                const float x = v[p * T::RK + q], h = tf32_rna(x);
+                hi[swf(r, kk0 + q)] = h;
+                if (S3) lo[swf(r, kk0 + q)] = tf32_rna(x - h);
+            }
+        }
+    } else {
+        const int lane = t & 31, warp = t >> 5;
+#pragma unroll
+        for (int i = 0; i < T::PER; ++i) {
+            const int r = 4 * i + warp;
+            const float x = v[i], h = tf32_rna(x);
+            hi[swf(r, lane)] = h;
+            if (S3) lo[swf(r, lane)] = tf32_rna(x - h);
+        }
+    }
+}
+
+template <int NTT, bool S3>
+__global__ void __launch_bounds__(NTH, 1) gemm_tc_kernel(const Gemm g) {
+    using G = Geo<NTT, S3>;
+    extern __shared__ uint8_t smraw[];
+    uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + 2 * G::STAGE);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2);
+    int *abort_flag = reinterpret_cast<int *>(tslot + 1);
+    int *last_issued = abort_flag + 1;
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int n0 = blockIdx.x * NTT, m0 = blockIdx.y * 128;
+    const int bt = blockIdx.z % g.batch, sp = blockIdx.z / g.batch;
+    const int K = g.K1 * g.K2;
+    const int kbeg = sp * g.kchunks * KC, kend = min(K, kbeg + g.kchunks * KC);
+    const int nch = kend > kbeg ? (kend - kbeg + KC - 1) / KC : 0;
+
+    if (t == 0) {
+        for (int q = 0; q < 2; ++q) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" :: "r"(su32(bars + q)));
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
+        *abort_flag = 0;
+        *last_issued = -1;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" :: "r"(su32(tslot)), "n"(NTT));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tslot;
+    const uint32_t id = idesc_tf32(NTT);
+    const int64_t abase = (int64_t)bt * g.sab, bbase = (int64_t)bt * g.sbb;
+
+    const float *Abase = g.A + abase + (int64_t)m0 * g.sam, *Bbase = g.B + bbase + (int64_t)n0 * g.sbn;
+    const bool arow = g.sam == 1, brow = g.sbn == 1;
+    float va[32], vb[NTT / 4];  // the next chunk's operands, loaded a chunk ahead
+    if (nch > 0) {
+        load_tile<128>(va, arow, Abase, g.sam, g.sak1, g.sak2, g.K2, kbeg, kend, g.M - m0, t);
+        load_tile<NTT>(vb, brow, Bbase, g.sbn, g.sbk1, g.sbk2, g.K2, kbeg, kend, g.N - n0, t);
+    }
+    for (int c = 0; c < nch; ++c) {
+        const int s = c & 1;
+        uint8_t *st = sm + s * G::STAGE;
+        float *Ah = reinterpret_cast<float *>(st), *Bh = reinterpret_cast<float *>(st + G::ABYTES);
+        float *Al = reinterpret_cast<float *>(st + G::ABYTES + G::BBYTES);
+        float *Bl = reinterpret_cast<float *>(st + 2 * G::ABYTES + G::BBYTES);
+        // the MMAs of chunk c - 2 read this stage
+        if (c >= 2 && !mbar_wait(su32(bars + s), ((c - 2) >> 1) & 1)) *abort_flag = 1;
+        store_tile<128, S3>(va, arow, Ah, Al, t);
+        store_tile<NTT, S3>(vb, brow, Bh, Bl, t);
+        if (c + 1 < nch) {  // in flight while this chunk is handed to the tensor cores
+            const int k0 = kbeg + (c + 1) * KC;
+            load_tile<128>(va, arow, Abase, g.sam, g.sak1, g.sak2, g.K2, k0, kend, g.M - m0, t);
+            load_tile<NTT>(vb, brow, Bbase, g.sbn, g.sbk1, g.sbk2, g.K2, k0, kend, g.N - n0, t);
+        }
+        fence_async_smem();
+        fence_before();
+        __syncthreads();
+        if (*abort_flag) break;  // uniform: read after the barrier
+        if (t == 0) {
+            fence_after();
+            const uint64_t da = sdesc(su32(Ah)), db = sdesc(su32(Bh));
+            if (S3) {
+                const uint64_t dal = sdesc(su32(Al)), dbl = sdesc(su32(Bl));
+#pragma unroll
+                for (int q = 0; q < 4; ++q) mma_tf32(tmem, dal + 2 * q, db + 2 * q, id, (c > 0 || q > 0) ? 1u : 0u);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) mma_tf32(tmem, da + 2 * q, dbl + 2 * q, id, 1u);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) mma_tf32(tmem, da + 2 * q, db + 2 * q, id, (S3 || c > 0 || q > 0) ? 1u : 0u);
+            mma_commit(su32(bars + s));
+            *last_issued = c;
+        }
+    }
+    __syncthreads();
+    // the last chunk's commit covers every MMA issued before it
+    const int li = *last_issued;
+    if (li >= 0 && !*abort_flag && !mbar_wait(su32(bars + (li & 1)), (li >> 1) & 1)) *abort_flag = 1;
+    __syncthreads();
+    fence_after();
+    const bool aborted = *abort_flag != 0;
+    if (!aborted) {
+        // warp w holds TMEM lanes 32 w .. 32 w + 31 (rows m0 + 32 w + lane); each 32-column block
+        // goes through a 32 x 33 staging tile of the warp's own (the operand ring is free now), and
+        // the warp then stores its rows one at a time, lane = column
+        float *stg = reinterpret_cast<float *>(sm) + warp * 32 * 33;
+        const int64_t sn = g.splits > 1 ? 1 : g.scn;
+#pragma unroll 1
+        for (int j = 0; j < NTT / 32; ++j) {
+            float v[32];
+            if (li >= 0) {
+                tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + 32 * j, v);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 32; ++q) v[q] = 0.0f;  // empty reduction range
+            }
+#pragma unroll
+            for (int q = 0; q < 32; ++q) stg[lane * 33 + q] = v[q];
+            __syncwarp();
+            const int n = n0 + 32 * j + lane;
+#pragma unroll 4
+            for (int i = 0; i < 32; ++i) {
+                const int m = m0 + 32 * warp + i;
+                if (m < g.M && n < g.N) {
+                    float *dst = g.splits > 1 ? g.part + (((int64_t)sp * g.batch + bt) * g.M + m) * g.N
+                                              : g.C + (int64_t)bt * g.scb + (int64_t)m * g.scm;
+                    dst[(int64_t)n * sn] = stg[i * 33 + lane];
+                }
+            }
+            __syncwarp();
+        }
+    } else if (t == 0) {
+        if (g.err) atomicExch(g.err, 1);
+        if (li >= 0) {  // bounded wait for the MMAs still in flight before the TMEM is freed
+            for (int it = 0; it < (1 << 20); ++it) {
+                uint32_t done;
+                asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                             : "=r"(done) : "r"(su32(bars + (li & 1))), "r"((li >> 1) & 1) : "memory");
+                if (done) break;
+            }
+        }
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" :: "r"(tmem), "n"(NTT));
+    }
+}
+
+template <int NTT, bool S3>
+cudaError_t launch_t(const Gemm &g, cudaStream_t s) {
+    using G = Geo<NTT, S3>;
+    auto k = gemm_tc_kernel<NTT, S3>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
+    if (e != cudaSuccess) return e;
+    const dim3 grid((unsigned)((g.N + NTT - 1) / NTT), (unsigned)((g.M + 127) / 128), (unsigned)(g.batch * g.splits));
+    k<<<grid, NTH, G::SMEM, s>>>(g);
+    return cudaGetLastError();
+}
+
+}  // namespace tgemm
+
+cudaError_t gemm_tc_launch(const Gemm &g, bool s3, int ntt, cudaStream_t s) {
+    if (g.M < 1 || g.N < 1 || g.batch < 1 || g.splits < 1 || g.kchunks < 1) return cudaErrorInvalidValue;
+    switch (ntt) {
+        case 32: return s3 ? tgemm::launch_t<32, true>(g, s) : tgemm::launch_t<32, false>(g, s);
+        case 64: return s3 ? tgemm::launch_t<64, true>(g, s) : tgemm::launch_t<64, false>(g, s);
+        case 128: return s3 ? tgemm::launch_t<128, true>(g, s) : tgemm::launch_t<128, false>(g, s);
+        case 256: return s3 ? tgemm::launch_t<256, true>(g, s) : tgemm::launch_t<256, false>(g, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace ntf

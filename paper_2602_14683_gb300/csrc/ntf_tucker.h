@@ -28,6 +28,9 @@ struct Gemm {
     int splits, kchunks;  // reduction ranges and chunks per range (set by the launcher)
     float *part;          // [splits][batch][M][N] when splits > 1
     int *err;             // tensor-core form: status word set when a bounded wait gives up
+    int nin;              // > 0: the batch is folded into n (A shared by all batches, sab = 0): N counts
+                          // batch x nin columns, column b nin + n stands for (batch b, column n), and
+                          // batch is 1; B and C then step by sbb / scb from one batch block to the next
 };
 // Tensor-core form of the same product (tucker_gemm_tc.cu): tcgen05 kind::tf32 MMAs on operands
 // rounded to TF32 (s3: split into high and low TF32 parts, three products, about FP32 accuracy),

@@ -194,63 +194,97 @@ __global__ void __launch_bounds__(256) gemm2k_kernel(const Gemm g) {
     }
 }
 
-// C = sum over the reduction ranges, in range order
+// C = sum over the reduction ranges: four consecutive threads per output each add a quarter of
+// the ranges in range order (loads eight at a time), and the four quarter sums are added in
+// quarter order; in FP64 for the FP32 GEMM (its accuracy carry), in FP32 for the tensor-core one
+// (TF32 operands; a few ranges, and the GB300 FP64 pipe, conversions included, is slow).  With the
+// batch folded into the columns (g.nin > 0), column b nin + n goes to batch block b of C.
+template <typename T>
 __global__ void gemm_split_sum_kernel(const Gemm g) {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t t = gt >> 2;
+    const int qid = (int)(gt & 3);
     const int64_t mn = (int64_t)g.M * g.N, total = mn * g.batch;
-    if (t >= total) return;
-    double v = 0.0;  // the ranges in order; their loads eight at a time
-    for (int sp0 = 0; sp0 < g.splits; sp0 += 8) {
-        float x[8];
+    const int per = (g.splits + 3) / 4, s0 = qid * per, s1 = min(g.splits, s0 + per);
+    T v = 0;
+    if (t < total) {
+        for (int sp0 = s0; sp0 < s1; sp0 += 8) {
+            float x[8];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) x[q] = sp0 + q < g.splits ? g.part[(int64_t)(sp0 + q) * total + t] : 0.0f;
+            for (int q = 0; q < 8; ++q) x[q] = sp0 + q < s1 ? g.part[(int64_t)(sp0 + q) * total + t] : 0.0f;
 #pragma unroll
-        for (int q = 0; q < 8; ++q)
-            if (sp0 + q < g.splits) v += (double)x[q];
+            for (int q = 0; q < 8; ++q)
+                if (sp0 + q < s1) v += (T)x[q];
+        }
     }
+    const T v1 = __shfl_down_sync(0xffffffffu, v, 1), v2 = __shfl_down_sync(0xffffffffu, v, 2),
+            v3 = __shfl_down_sync(0xffffffffu, v, 3);
+    if (qid != 0 || t >= total) return;
+    const T tot = ((v + v1) + v2) + v3;
     const int bt = (int)(t / mn), m = (int)((t % mn) / g.N), n = (int)(t % g.N);
-    g.C[bt * g.scb + m * g.scm + n * g.scn] = (float)v;
+    int64_t c;
+    if (g.nin > 0) {
+        const int b = n / g.nin;
+        c = (int64_t)m * g.scm + (int64_t)b * g.scb + (int64_t)(n - b * g.nin) * g.scn;
+    } else {
+        c = (int64_t)bt * g.scb + (int64_t)m * g.scm + (int64_t)n * g.scn;
+    }
+    g.C[c] = (float)tot;
+}
+
+static cudaError_t split_sum(const Gemm &g, cudaStream_t s, bool fp64) {
+    const int64_t total = (int64_t)g.M * g.N * g.batch;
+    const unsigned blocks = (unsigned)((4 * total + 255) / 256);
+    if (fp64) gemm_split_sum_kernel<double><<<blocks, 256, 0, s>>>(g);
+    else gemm_split_sum_kernel<float><<<blocks, 256, 0, s>>>(g);
+    return cudaGetLastError();
 }
 
 // Splits the reduction when the output tiles alone would leave most SMs idle: about two
 // CTAs per SM, at least four GK-chunks per range (two 32-index chunks on the tensor cores).
 // mode: 0 FP32 CUDA cores, 1 tcgen05 on TF32 operands, 2 tcgen05 on split (3xTF32) operands.
 static int gemm(ntf_ctx *ctx, Gemm g, cudaStream_t s, int mode = 0) {
-    // tensor-core tile width: the widest that still gives two CTAs per SM, else 32 columns
-    int ntt = 32;
-    for (int w = 256; w >= 64; w >>= 1) {
-        if (g.N <= w / 2) continue;
-        const int64_t tl = (int64_t)((g.N + w - 1) / w) * ((g.M + 127) / 128) * g.batch;
-        if (tl >= 2 * ctx_num_sms(ctx)) {
-            ntt = w;
-            break;
-        }
-    }
-    const int64_t tiles_tc = (int64_t)((g.N + ntt - 1) / ntt) * ((g.M + 127) / 128) * g.batch;
-    const int nchunks_tc = (g.K1 * g.K2 + 31) / 32;
-    int splits_tc = (int)std::min<int64_t>((2 * ctx_num_sms(ctx) + tiles_tc - 1) / tiles_tc, 1 << 20);
-    splits_tc = std::max(1, std::min(splits_tc, nchunks_tc / 2));
-    // grid limits of the tensor-core form (batch x splits on the z dimension): else FP32
-    if ((int64_t)g.batch * splits_tc > 65535 || g.N > 65535 * 256) mode = 0;
     if (mode) {
-        const int nchunks = std::max(1, nchunks_tc);
-        g.kchunks = std::max(1, (nchunks + splits_tc - 1) / splits_tc);
-        g.splits = std::max(1, (nchunks + g.kchunks - 1) / g.kchunks);
-        g.err = ctx_status(ctx);
-        if (g.splits > 1) {
-            g.part = (float *)ctx_ws(ctx, "gemm_split", sizeof(float) * (size_t)g.splits * g.batch * g.M * g.N);
-            if (!g.part) return ctx_fail(ctx, NTF_ERR_OOM, "workspace allocation failed");
+        // tensor cores: an A shared by every batch (sab = 0) serves several batches per tile, with
+        // the batch folded into the columns (the B^(3) build, Y = A2^T W, H); then the widest tile
+        // whose split plan still gives about two CTAs per SM (else 32 columns)
+        Gemm f = g;
+        if (g.sab == 0 && g.batch > 1 && g.N < 256 && (int64_t)g.N * g.batch < (1ll << 30)) {
+            f.nin = g.N;
+            f.N = g.N * g.batch;
+            f.batch = 1;
         }
-        cudaError_t e = gemm_tc_launch(g, mode == 2, ntt, s);
-        if (e == cudaSuccess && g.splits > 1) {
-            const int64_t total = (int64_t)g.M * g.N * g.batch;
-            gemm_split_sum_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(g);
-            e = cudaGetLastError();
+        const int nchunks = std::max(1, (f.K1 * f.K2 + 31) / 32);
+        const int64_t want = 2 * (int64_t)ctx_num_sms(ctx);
+        int ntt = 32, splits = 1;
+        for (int w = 256; w >= 32; w >>= 1) {
+            if (w > 32 && f.N <= w / 2) continue;
+            const int64_t tiles = (int64_t)((f.N + w - 1) / w) * ((f.M + 127) / 128) * f.batch;
+            const int sp = (int)std::max<int64_t>(1, std::min<int64_t>((want + tiles - 1) / tiles, nchunks / 2));
+            if (tiles * sp >= want || w == 32) {
+                ntt = w;
+                splits = sp;
+                break;
+            }
+        }
+        f.kchunks = std::max(1, (nchunks + splits - 1) / splits);
+        f.splits = std::max(1, (nchunks + f.kchunks - 1) / f.kchunks);
+        // the grid's z extent is batch x splits; past it, the CUDA-core kernel below
+        if ((int64_t)f.batch * f.splits <= 65535 && (f.M + 127) / 128 <= 65535) {
+            f.err = ctx_status(ctx);
+            if (f.splits > 1) {
+                f.part = (float *)ctx_ws(ctx, "gemm_split", sizeof(float) * (size_t)f.splits * f.batch * f.M * f.N);
+                if (!f.part) return ctx_fail(ctx, NTF_ERR_OOM, "workspace allocation failed");
+            }
+            cudaError_t e = gemm_tc_launch(f, mode == 2, ntt, s);
+            if (e == cudaSuccess && f.splits > 1) {
+                e = split_sum(f, s, false);
+                ctx_count(ctx, 1);
+            }
+            if (e != cudaSuccess) return ctx_fail(ctx, NTF_ERR_CUDA, cudaGetErrorString(e));
             ctx_count(ctx, 1);
+            return NTF_OK;
         }
-        if (e != cudaSuccess) return ctx_fail(ctx, NTF_ERR_CUDA, cudaGetErrorString(e));
-        ctx_count(ctx, 1);
-        return NTF_OK;
     }
     // tile shape: four batches per CTA for outputs of at most 32 x 32, 64 x 16 or 128 x 8, else by
     // width
@@ -286,9 +320,7 @@ static int gemm(ntf_ctx *ctx, Gemm g, cudaStream_t s, int mode = 0) {
         gemm2k_kernel<64, 64, 1><<<grid, 256, 0, s>>>(g);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess && g.splits > 1) {
-        const int64_t total = (int64_t)g.M * g.N * g.batch;
-        gemm_split_sum_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(g);
-        e = cudaGetLastError();
+        e = split_sum(g, s, true);
         ctx_count(ctx, 1);
     }
     if (e != cudaSuccess) return ctx_fail(ctx, NTF_ERR_CUDA, cudaGetErrorString(e));

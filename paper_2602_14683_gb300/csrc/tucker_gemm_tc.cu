@@ -63,9 +63,20 @@ struct TileMap {
     static constexpr int PER = NR / 4;                   // elements per thread (both modes)
 };
 
+// Offset of tile row r (global row row0 + r): (row / nin) sblk + (row % nin) srow when the batch
+// is folded into the rows (nin > 0), else row srow.
+__device__ __forceinline__ int64_t row_off(int row, int64_t srow, int nin, int64_t sblk) {
+    if (nin > 0) {
+        const int b = row / nin;
+        return (int64_t)b * sblk + (int64_t)(row - b * nin) * srow;
+    }
+    return (int64_t)row * srow;
+}
+
 template <int NR>
-__device__ __forceinline__ void load_tile(float (&v)[NR / 4], bool rowmode, const float *base, int64_t srow,
-                                          int64_t sk1, int64_t sk2, int K2, int k0, int kend, int nrow, int t) {
+__device__ __forceinline__ void load_tile(float (&v)[NR / 4], bool rowmode, const float *base, int row0, int64_t srow,
+                                          int nin, int64_t sblk, int64_t sk1, int64_t sk2, int K2, int k0, int kend,
+                                          int nrow, int t) {
     using T = TileMap<NR>;
     if (rowmode) {
 #pragma unroll
@@ -74,9 +85,10 @@ __device__ __forceinline__ void load_tile(float (&v)[NR / 4], bool rowmode, cons
             const int kk0 = NR >= NTH ? 0 : (t / NR) * T::RK;
             int k = k0 + kk0, k1 = K2 == 1 ? k : k / K2, k2 = k - k1 * K2;
             const bool rv = r < nrow;
+            const float *br = base + (rv ? row_off(row0 + r, srow, nin, sblk) : 0);
 #pragma unroll
             for (int q = 0; q < T::RK; ++q) {
-                v[p * T::RK + q] = (rv && k + q < kend) ? __ldg(base + r + (int64_t)k1 * sk1 + (int64_t)k2 * sk2) : 0.0f;
+                v[p * T::RK + q] = (rv && k + q < kend) ? __ldg(br + (int64_t)k1 * sk1 + (int64_t)k2 * sk2) : 0.0f;
                 if (++k2 == K2) {
                     k2 = 0;
                     ++k1;
@@ -96,7 +108,7 @@ __device__ __forceinline__ void load_tile(float (&v)[NR / 4], bool rowmode, cons
 #pragma unroll
         for (int i = 0; i < T::PER; ++i) {
             const int r = 4 * i + warp;
-            v[i] = (kv && r < nrow) ? __ldg(p + (int64_t)r * srow) : 0.0f;
+            v[i] = (kv && r < nrow) ? __ldg(p + row_off(row0 + r, srow, nin, sblk)) : 0.0f;
         }
     }
 }
@@ -161,12 +173,12 @@ __global__ void __launch_bounds__(NTH, 1) gemm_tc_kernel(const Gemm g) {
     const uint32_t id = idesc_tf32(NTT);
     const int64_t abase = (int64_t)bt * g.sab, bbase = (int64_t)bt * g.sbb;
 
-    const float *Abase = g.A + abase + (int64_t)m0 * g.sam, *Bbase = g.B + bbase + (int64_t)n0 * g.sbn;
+    const float *Abase = g.A + abase, *Bbase = g.B + bbase;
     const bool arow = g.sam == 1, brow = g.sbn == 1;
     float va[32], vb[NTT / 4];  // the next chunk's operands, loaded a chunk ahead
     if (nch > 0) {
-        load_tile<128>(va, arow, Abase, g.sam, g.sak1, g.sak2, g.K2, kbeg, kend, g.M - m0, t);
-        load_tile<NTT>(vb, brow, Bbase, g.sbn, g.sbk1, g.sbk2, g.K2, kbeg, kend, g.N - n0, t);
+        load_tile<128>(va, arow, Abase, m0, g.sam, 0, 0, g.sak1, g.sak2, g.K2, kbeg, kend, g.M - m0, t);
+        load_tile<NTT>(vb, brow, Bbase, n0, g.sbn, g.nin, g.sbb, g.sbk1, g.sbk2, g.K2, kbeg, kend, g.N - n0, t);
     }
     for (int c = 0; c < nch; ++c) {
         const int s = c & 1;
@@ -180,8 +192,8 @@ __global__ void __launch_bounds__(NTH, 1) gemm_tc_kernel(const Gemm g) {
         store_tile<NTT, S3>(vb, brow, Bh, Bl, t);
         if (c + 1 < nch) {  // in flight while this chunk is handed to the tensor cores
             const int k0 = kbeg + (c + 1) * KC;
-            load_tile<128>(va, arow, Abase, g.sam, g.sak1, g.sak2, g.K2, k0, kend, g.M - m0, t);
-            load_tile<NTT>(vb, brow, Bbase, g.sbn, g.sbk1, g.sbk2, g.K2, k0, kend, g.N - n0, t);
+            load_tile<128>(va, arow, Abase, m0, g.sam, 0, 0, g.sak1, g.sak2, g.K2, k0, kend, g.M - m0, t);
+            load_tile<NTT>(vb, brow, Bbase, n0, g.sbn, g.nin, g.sbb, g.sbk1, g.sbk2, g.K2, k0, kend, g.N - n0, t);
         }
         fence_async_smem();
         fence_before();
@@ -229,13 +241,15 @@ __global__ void __launch_bounds__(NTH, 1) gemm_tc_kernel(const Gemm g) {
             for (int q = 0; q < 32; ++q) stg[lane * 33 + q] = v[q];
             __syncwarp();
             const int n = n0 + 32 * j + lane;
+            // this lane's column: its offset in C (batch block and column when folded)
+            const int64_t cn = g.splits > 1 ? (int64_t)n : row_off(n, sn, g.nin, g.scb);
 #pragma unroll 4
             for (int i = 0; i < 32; ++i) {
                 const int m = m0 + 32 * warp + i;
                 if (m < g.M && n < g.N) {
                     float *dst = g.splits > 1 ? g.part + (((int64_t)sp * g.batch + bt) * g.M + m) * g.N
                                               : g.C + (int64_t)bt * g.scb + (int64_t)m * g.scm;
-                    dst[(int64_t)n * sn] = stg[i * 33 + lane];
+                    dst[cn] = stg[i * 33 + lane];
                 }
             }
             __syncwarp();

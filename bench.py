@@ -487,7 +487,32 @@ def run_coo_c4(ntf, ctx, peaks, iters=20, R=32, seed=0):
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     fp32_peak = sms * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     l2 = l2_copy_gbs()
+    # beta = 3/2 on the same tensor (Section 6.3): stored-entry numerators, and every denominator a
+    # pass over the whole 8.6e9-entry index space that reads no X (2R flops for Xhat and 2R for the
+    # contraction per index entry, one pass per mode)
+    beta_other = None
+    if iters > 0:
+        B = [a.clone() for a in A0]
+        ntf.jcomm_outer(X, 1.5, B, objective=obj, ctx=ctx)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(2):
+            ntf.jcomm_outer(X, 1.5, B, objective=obj, ctx=ctx)
+        e1.record()
+        torch.cuda.synchronize()
+        ms15 = e0.elapsed_time(e1) / 2
+        cells = 1
+        for d in dims:
+            cells *= d
+        dflops = N * cells * 4 * R
+        beta_other = {"beta": 1.5, "ms_per_outer": ms15,
+                      "dense_pass": {"achieved_tflops": dflops / (ms15 / 1e3) / 1e12, "peak_tflops": fp32_peak,
+                                     "frac": dflops / (ms15 / 1e3) / 1e12 / fp32_peak,
+                                     "of": "N X-free FP32 passes over the %d index entries, 4R flops each (the "
+                                           "denominators and the objective's dense part), over the whole outer "
+                                           "iteration (the stored-entry passes included)" % cells}}
     return {"workload": "sparse COO 183x24x1140x1717, 3.3M nnz, CP R=32, beta=1, J-CoMM L=1",
+            "beta_1p5_jcomm": beta_other,
             "us_per_outer": ms * 1e3, "outer_per_s": 1e3 / ms,
             "roofline": {"bound": "hbm", "achieved": byt / sec / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                          "frac": byt / sec / 1e9 / peaks["hbm_gbs"],
@@ -500,6 +525,47 @@ def run_coo_c4(ntf, ctx, peaks, iters=20, R=32, seed=0):
                           "of": "(N-1) gathered factor rows of R x 4 bytes per nonzero and pass, N passes, against "
                                 "the L2-resident copy bandwidth measured in this run (32 MB -> 32 MB, best of 20); "
                                 "above 1 when the Zipf-skewed rows are served from L1"}}
+
+
+def run_batch_cp(ntf, n_jobs=256, alone=16, seed=5):
+    """Launches shared by many small jobs (ntf_batch_*): dense CP jobs with dims log-uniform in
+    16..64, ranks 4..32, beta in {1/2, 1, 3/2}, J-CoMM L = 1, stop at a 1e-6 relative objective
+    change or 200 iterations, FP32 passes.  Every job resident in one batch (one launch per step
+    and class for all of them, eight iterations per graph launch) against the first `alone` jobs
+    solved one at a time by the same batch; wall time from the first add to the last result,
+    data already on the device."""
+    import torch
+    import synth
+    jobs = [j for j in synth.serving_jobs(6 * n_jobs, seed=seed, dim_lo=16, dim_hi=64) if j["model"] == "cp"][:n_jobs]
+    data = [synth.job_data_torch(j) for j in jobs]
+    torch.cuda.synchronize()
+    bt = ntf.Batch(capacity=len(jobs), mem_budget_bytes=2 << 30)
+
+    def solve(sel):
+        facs = [[a.clone() for a in data[q][2]] for q in sel]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for q, f in zip(sel, facs):
+            if bt.add(data[q][0], jobs[q]["beta"], f) is None:
+                raise RuntimeError("batch arena too small")
+        res = bt.run(iters=8)
+        return res, time.perf_counter() - t0
+
+    solve(list(range(min(8, len(jobs)))))  # warm-up (kernel loading)
+    res, sec = solve(list(range(len(jobs))))
+    t_alone, its_alone = 0.0, 0
+    for q in range(min(alone, len(jobs))):
+        r, s = solve([q])
+        t_alone += s
+        its_alone += r[0]["iterations"]
+    bt.close()
+    its = sum(r["iterations"] for r in res)
+    return {"workload": "%d dense CP jobs, dims log-uniform 16..64, rank 4..32, beta in {0.5,1,1.5}, J-CoMM L=1, "
+                        "stop at 1e-6 or 200 its, FP32" % len(jobs),
+            "batched": {"jobs": len(res), "seconds": sec, "solves_per_s": len(res) / sec, "iterations": its,
+                        "iterations_per_s": its / sec, "ok": sum(1 for r in res if r["status"] == 0)},
+            "one_at_a_time": {"jobs": min(alone, len(jobs)), "seconds": t_alone,
+                              "solves_per_s": min(alone, len(jobs)) / t_alone, "iterations_per_s": its_alone / t_alone}}
 
 
 def l2_copy_gbs():
@@ -1014,7 +1080,7 @@ def main():
     if not args.no_other:
         other = {"tucker_c3": run_tucker_c3(ntf, ctx, peaks), "coo_c4": run_coo_c4(ntf, ctx, peaks),
                  "cp_4way": run_cp_4way(ntf, ctx, peaks), "tucker_4way": run_tucker_4way(ntf, ctx, peaks),
-                 "tucker_5way": run_tucker_5way(ntf, ctx, peaks)}
+                 "tucker_5way": run_tucker_5way(ntf, ctx, peaks), "batch_cp": run_batch_cp(ntf)}
 
     serving = None
     if args.serve_jobs > 0:
@@ -1084,6 +1150,13 @@ def summary(line):
         c4 = o["coo_c4"]
         out.append("C4 us/outer %.1f; frac hbm %.3f alu %.3f l2 %.3f" % (c4["us_per_outer"], c4["roofline"]["frac"],
                                                                         c4["alu"]["frac"], c4["l2_gather"]["frac"]))
+        if c4.get("beta_1p5_jcomm"):
+            out.append("C4 shape at beta=1.5: %.1f ms/outer (dense X-free passes %.3f of FP32 peak)" % (
+                c4["beta_1p5_jcomm"]["ms_per_outer"], c4["beta_1p5_jcomm"]["dense_pass"]["frac"]))
+    if o.get("batch_cp"):
+        bc = o["batch_cp"]
+        out.append("batched small CP jobs: %.1f solves/s (%d jobs), one at a time %.1f solves/s" % (
+            bc["batched"]["solves_per_s"], bc["batched"]["jobs"], bc["one_at_a_time"]["solves_per_s"]))
     sv = line.get("serving")
     if sv:
         out.append("C5 %d jobs: sat %.1f/s, at 0.8x: %.1f/s p50 %.3f s p99 %.3f s; sweep " % (

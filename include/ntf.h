@@ -63,7 +63,10 @@ enum { NTF_CP = 0, NTF_TUCKER = 1 };
  * cores (dense CP, rank padded to 32): the reconstruction Xhat on TF32 operands rounded to
  * nearest (one MMA pass), the Num / Den contractions on BF16 operands, FP32 accumulation.
  * 3XTF32: the same, with the reconstruction split into high and low TF32 parts (three MMA
- * passes, about FP32 accuracy for Xhat and the objective).  The beta-powers are always
+ * passes, about FP32 accuracy for Xhat and the objective).  Dense Tucker on the tensor cores
+ * (third core dimension <= 32): the passes over X as for CP, and the small contractions of
+ * Appendix C (the partial tensor B^(3), the core and factor products) as tcgen05 GEMMs on TF32
+ * operands (split high / low with 3XTF32), FP32 accumulation.  The beta-powers are always
  * FP32 and the objective is accumulated in FP64. */
 enum { NTF_PREC_FP32 = 0, NTF_PREC_TF32 = 1, NTF_PREC_3XTF32 = 2 };
 
@@ -81,15 +84,18 @@ typedef struct {
     double eps_x;  /* data floor used only at beta = 0 (1e-12) */
     int inner_L;   /* J-CoMM inner sweeps per outer iteration, >= 1 (1) */
     int precision; /* NTF_PREC_FP32 (default), NTF_PREC_TF32 or NTF_PREC_3XTF32 */
-    int autotune;  /* dense CP: 1 = pick the pass's slab split by timing (0).  On the first call
-                      for a given shape, rank padding, precision, beta class and pass variant in
-                      this process, the call times the pass it is about to run under a few grid
-                      plans (about one to four waves of CTAs, plus the cost model's choice) on its
-                      own stream, synchronizing that stream, and keeps the fastest in a
-                      process-wide table that every later call and context reuses.  The split
-                      sets the order of the partial sums, so results may differ from a run with
-                      another table in the last bits.  Ignored (cost-model plan, nothing cached)
-                      while the stream is being captured. */
+    int autotune;  /* 1 = pick launch plans by timing (0).  Dense CP: the pass's slab split; on the
+                      first call for a given shape, rank padding, precision, beta class and pass
+                      variant in this process, the call times the pass it is about to run under a
+                      few grid plans (about one to four waves of CTAs, plus the cost model's choice).
+                      Tucker on the tensor cores: every contraction's tile width and reduction split
+                      (each width with its rule's split, and the rule's width with half and twice
+                      its split), on the first call for that product's shape and strides.  The
+                      timing runs on the call's own stream, synchronizing it, and the fastest plan
+                      goes to a process-wide table that every later call and context reuses.  A plan
+                      sets the order of partial sums, so results may differ from a run with another
+                      table in the last bits.  Ignored (rule's plan, nothing cached) while the
+                      stream is being captured. */
     int merge;     /* dense CP and Tucker of order N >= 4, which run on the 3-way passes with the
                       modes cut into three runs of consecutive modes [0, a), [a, b), [b, N) (a run
                       of several modes is one 3-way mode whose factor is the Khatri-Rao product
@@ -156,7 +162,11 @@ int ntf_debug_wait_limit(ntf_ctx *ctx, int polls, int probe);
  *   factors:       host array of N device pointers, A^(n) is I_n x rank, updated in place
  *   objective_dev: device double or NULL; receives D_beta(X, Xhat) of the INCOMING
  *                  iterate (before this sweep).
- * Dense (N = 3..8) and COO (beta = 1 only, else NTF_ERR_UNSUPPORTED) tensors. */
+ * Dense (N = 3..8) and COO tensors.  COO (Section 6.3): Num^(n) runs over the stored entries
+ * (P vanishes where X does); at beta = 1 Den^(n) is the closed form, at other beta it contracts
+ * Xhat^(beta-1) over the whole index space in a pass that reads no X (FP32, N >= 3; the modes cut
+ * into three runs as for dense tensors).  COO at beta = 0 (d_0 needs X > 0 everywhere) and COO of
+ * order 2 at beta != 1 return NTF_ERR_UNSUPPORTED. */
 int ntf_cp_mu_sweep(ntf_ctx *ctx, const ntf_tensor *X, float beta, int rank,
                     float *const *factors, const ntf_opts *opts, double *objective_dev,
                     void *stream);
@@ -205,7 +215,9 @@ int ntf_cp_jcomm_outer_extrap(ntf_ctx *ctx, const ntf_tensor *X, float beta, int
  *   core_dims: host array [N] of J_n; core: device J_1 x ... x J_N, updated in place
  *   factors:   host array of N device pointers, A^(n) is I_n x J_n, updated in place
  *   objective_dev: device double or NULL; D_beta of the incoming iterate.
- * Dense N = 3..8 (N >= 4: the last run of the cut needs a core extent <= 64). */
+ * Dense N = 3..8 (N >= 4: the last run of the cut needs a core extent <= 64), and COO of order 3
+ * at beta = 1 (Section 6.3: numerators over the stored entries, closed-form denominators; FP32
+ * passes whatever the precision); other COO Tucker requests return NTF_ERR_UNSUPPORTED. */
 int ntf_tucker_mu_sweep(ntf_ctx *ctx, const ntf_tensor *X, float beta, const int64_t *core_dims,
                         float *core, float *const *factors, const ntf_opts *opts,
                         double *objective_dev, void *stream);
@@ -235,7 +247,8 @@ int ntf_tucker_mu_sweep_extrap(ntf_ctx *ctx, const ntf_tensor *X, float beta, co
  * reference factors inside each pass (never stored).
  *   model: NTF_CP (rank_or_0 = R, core arguments NULL) or NTF_TUCKER (rank_or_0 = 0)
  *   objective_ref_dev: device double or NULL; receives D_beta at the reference.
- * CP dense N = 3..8 (any beta), CP COO (beta = 1), Tucker dense N = 3..8 (any beta). */
+ * CP dense N = 3..8 (any beta), CP COO (as ntf_cp_mu_sweep), Tucker dense N = 3..8 (any beta),
+ * Tucker COO (order 3, beta = 1). */
 int ntf_jcomm_outer(ntf_ctx *ctx, int model, const ntf_tensor *X, float beta, int rank_or_0,
                     const int64_t *core_dims_or_null, float *core_or_null, float *const *factors,
                     const ntf_opts *opts, double *objective_ref_dev, void *stream);
@@ -254,8 +267,11 @@ int ntf_tucker_jcomm_outer_extrap(ntf_ctx *ctx, const ntf_tensor *X, float beta,
 
 /* D_beta(X, Xhat) = sum_i d_beta(X_i | max(Xhat_i, eps)) (Section 3.2, Definition
  * "beta-divergence") in FP64, written to *out_dev.  Per-entry terms use stable forms
- * in FP32 (log1p/expm1) and are summed in FP64.  For COO (beta = 1 only) the unstored
- * entries contribute prod_n colsum(A^(n)) in closed form. */
+ * in FP32 (log1p/expm1) and are summed in FP64.  For COO the unstored entries (x = 0) add
+ * d_beta(0 | Xhat) = Xhat^beta / beta: at beta = 1 the closed form sum of Xhat (CP:
+ * sum_r prod_n colsum(A^(n))_r; Tucker, order 3: the same from B^(3) and A^(3)), at other beta
+ * (CP) a pass over the whole index space that reads no X; COO requests as ntf_cp_mu_sweep /
+ * ntf_tucker_mu_sweep. */
 int ntf_beta_div(ntf_ctx *ctx, int model, const ntf_tensor *X, float beta, int rank_or_0,
                  const int64_t *core_dims_or_null, const float *core_or_null,
                  const float *const *factors, const ntf_opts *opts, double *out_dev,

@@ -705,6 +705,22 @@ int coo_num_rows(ntf_ctx *ctx, const ntf_tensor *X, int n, int RP, const float *
     return NTF_OK;
 }
 
+int coo_kl_objective_total(ntf_ctx *ctx, const ntf_tensor *X, const float *const *F, int R, int RP,
+                           const double *parts, int n_parts, double *out_dev, cudaStream_t st) {
+    const int N = X->order;
+    const float **fptr = (const float **)ctx_ws(ctx, "cooFptr", sizeof(float *) * 8);
+    int *frows = (int *)ctx_ws(ctx, "cooFrows", sizeof(int) * 8);
+    if (!fptr || !frows) return ctx_fail(ctx, NTF_ERR_OOM, "COO workspace allocation failed");
+    CK(cudaMemcpyAsync(fptr, F, sizeof(float *) * N, cudaMemcpyHostToDevice, st));
+    int rows[8];
+    for (int m = 0; m < N; ++m) rows[m] = (int)X->dims[m];
+    CK(cudaMemcpyAsync(frows, rows, sizeof(int) * N, cudaMemcpyHostToDevice, st));
+    coo_obj_finish_kernel<<<1, 1024, 0, st>>>(parts, n_parts, fptr, frows, N, R, RP, out_dev);
+    CK(cudaGetLastError());
+    ctx_count(ctx, 1);
+    return NTF_OK;
+}
+
 int coo_kl_objective(ntf_ctx *ctx, const ntf_tensor *X, int R, const float *const *factors, const ntf_opts &o,
                      double *out_dev, cudaStream_t st) {
     CooCache *c = nullptr;

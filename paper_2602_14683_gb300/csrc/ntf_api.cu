@@ -1108,6 +1108,16 @@ int cp_coo_beta_div(ntf_ctx *ctx, const ntf_tensor *X, float beta, int R, const 
     return NTF_OK;
 }
 
+// Tucker on a COO tensor: order 3 at beta = 1, where Q = 1 keeps every denominator a closed form and
+// the stored entries alone give the numerators and the objective's data terms (Section 6.3).  Other
+// orders and beta values would need a dense X-free Tucker rows pass, which is not built.
+int tucker_kind_check(ntf_ctx *ctx, const ntf_tensor *X, float beta) {
+    if (X->kind == NTF_DENSE) return NTF_OK;
+    if (X->order != 3) return fail(ctx, NTF_ERR_UNSUPPORTED, "COO Tucker is implemented for order 3");
+    if (ntf::beta_kind(beta) != ntf::BK_KL) return fail(ctx, NTF_ERR_UNSUPPORTED, "COO Tucker is implemented for beta = 1");
+    return NTF_OK;
+}
+
 int cp_dense_beta_div(ntf_ctx *ctx, const ntf_tensor *X, float beta, int R, const float *const *factors,
                       const ntf_opts &o, double *out_dev, cudaStream_t st) {
     CpDense s{};
@@ -1296,7 +1306,7 @@ int ntf_tucker_mu_sweep(ntf_ctx *ctx, const ntf_tensor *X, float beta, const int
     ntf_opts o = resolve_opts(opts);
     int rc = check_common(ctx, X, beta, o);
     if (rc) return rc;
-    if (X->kind != NTF_DENSE) return fail(ctx, NTF_ERR_UNSUPPORTED, "Tucker is implemented for dense tensors");
+    if ((rc = tucker_kind_check(ctx, X, beta))) return rc;
     cudaSetDevice(ctx->device);
     ctx->err[0] = 0;
     return ntf::tucker_run(ctx, X, beta, core_dims, core, factors, o, objective_dev, (cudaStream_t)stream,
@@ -1359,7 +1369,7 @@ int ntf_jcomm_outer(ntf_ctx *ctx, int model, const ntf_tensor *X, float beta, in
         return cp_dense_jcomm(ctx, X, beta, rank_or_0, factors, o, objective_ref_dev, st);
     }
     if (model == NTF_TUCKER) {
-        if (X->kind != NTF_DENSE) return fail(ctx, NTF_ERR_UNSUPPORTED, "Tucker is implemented for dense tensors");
+        if ((rc = tucker_kind_check(ctx, X, beta))) return rc;
         return ntf::tucker_run(ctx, X, beta, core_dims_or_null, core_or_null, factors, o, objective_ref_dev, st,
                                /*jcomm=*/true);
     }
@@ -1388,7 +1398,7 @@ int ntf_beta_div(ntf_ctx *ctx, int model, const ntf_tensor *X, float beta, int r
         return cp_dense_beta_div(ctx, X, beta, rank_or_0, factors, o, out_dev, st);
     }
     if (model == NTF_TUCKER) {
-        if (X->kind != NTF_DENSE) return fail(ctx, NTF_ERR_UNSUPPORTED, "Tucker is implemented for dense tensors");
+        if ((rc = tucker_kind_check(ctx, X, beta))) return rc;
         return ntf::tucker_beta_div(ctx, X, beta, core_dims_or_null, core_or_null, factors, o, out_dev, st);
     }
     return fail(ctx, NTF_ERR_ARG, "unknown model %d", model);

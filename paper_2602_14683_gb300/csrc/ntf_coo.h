@@ -15,6 +15,11 @@ int coo_kl_objective(ntf_ctx *ctx, const ntf_tensor *X, int R, const float *cons
 // form at beta = 1), returned in *obj_parts (context workspace) with their count in *n_obj.
 int coo_num_rows(ntf_ctx *ctx, const ntf_tensor *X, int n, int RP, const float *const *rec, const float *const *num,
                  float beta, float eps, float *out, double **obj_parts, int *n_obj, cudaStream_t st);
+// The KL objective of a COO tensor from the stored-entry partials of coo_num_rows (parts, n_parts)
+// plus the closed-form dense part sum_{r < R} prod_n colsum(F[n])_r (F: padded blocks, RP columns,
+// X->dims[n] rows), into *out_dev.  The pointer table it reads lives in the context's workspace.
+int coo_kl_objective_total(ntf_ctx *ctx, const ntf_tensor *X, const float *const *F, int R, int RP,
+                           const double *parts, int n_parts, double *out_dev, cudaStream_t st);
 int coo_stable_perm(ntf_ctx *ctx, const int32_t *keys, int64_t nnz, int64_t key_range, int32_t *perm_out,
                     cudaStream_t st);
 void coo_release(ntf_ctx *ctx);

@@ -18,9 +18,14 @@
 // on the third factor only, one rows pass serves the core and modes 1 and 2 of an inner
 // sweep, so an inner sweep reads X twice instead of four times.
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
 #include <string>
 
 #include "cp3_fp32.cuh"
+#include "ntf_coo.h"
 #include "ntf_tucker.h"
 
 namespace ntf {
@@ -240,10 +245,56 @@ static cudaError_t split_sum(const Gemm &g, cudaStream_t s, bool fp64) {
     return cudaGetLastError();
 }
 
+// Tensor-core plans timed by the autotuner: process-wide, keyed by device, shape, strides and
+// arithmetic; the value is (tile width, reduction ranges).
+struct GemmKey {
+    int dev, M, N, K1, K2, batch, mode;
+    int64_t sab, sam, sak1, sak2, sbb, sbk1, sbk2, sbn;
+    bool operator<(const GemmKey &o) const {
+        return std::tie(dev, M, N, K1, K2, batch, mode, sab, sam, sak1, sak2, sbb, sbk1, sbk2, sbn) <
+               std::tie(o.dev, o.M, o.N, o.K1, o.K2, o.batch, o.mode, o.sab, o.sam, o.sak1, o.sak2, o.sbb, o.sbk1,
+                        o.sbk2, o.sbn);
+    }
+};
+std::mutex g_gemm_mu;
+std::map<GemmKey, std::pair<int, int>> g_gemm_tuned;
+
+// reduction ranges for a tile width: enough CTAs for about two per SM, at least two chunks each
+static int tc_splits(const Gemm &f, int w, int sms) {
+    const int nchunks = std::max(1, (f.K1 * f.K2 + 31) / 32);
+    const int64_t want = 2 * (int64_t)sms;
+    const int64_t tiles = (int64_t)((f.N + w - 1) / w) * ((f.M + 127) / 128) * f.batch;
+    return (int)std::max<int64_t>(1, std::min<int64_t>((want + tiles - 1) / tiles, nchunks / 2));
+}
+
+// One tensor-core product with the given plan (launch, and the range sum when split).
+static int gemm_tc_run(ntf_ctx *ctx, Gemm f, int ntt, int splits, int mode, cudaStream_t s) {
+    const int nchunks = std::max(1, (f.K1 * f.K2 + 31) / 32);
+    f.kchunks = std::max(1, (nchunks + splits - 1) / splits);
+    f.splits = std::max(1, (nchunks + f.kchunks - 1) / f.kchunks);
+    if ((int64_t)f.batch * f.splits > 65535 || (f.M + 127) / 128 > 65535) return NTF_ERR_UNSUPPORTED;
+    f.err = ctx_status(ctx);
+    if (f.splits > 1) {
+        f.part = (float *)ctx_ws(ctx, "gemm_split", sizeof(float) * (size_t)f.splits * f.batch * f.M * f.N);
+        if (!f.part) return ctx_fail(ctx, NTF_ERR_OOM, "workspace allocation failed");
+    }
+    cudaError_t e = gemm_tc_launch(f, mode == 2, ntt, s);
+    if (e == cudaSuccess && f.splits > 1) {
+        e = split_sum(f, s, false);
+        ctx_count(ctx, 1);
+    }
+    if (e != cudaSuccess) return ctx_fail(ctx, NTF_ERR_CUDA, cudaGetErrorString(e));
+    ctx_count(ctx, 1);
+    return NTF_OK;
+}
+
 // Splits the reduction when the output tiles alone would leave most SMs idle: about two
 // CTAs per SM, at least four GK-chunks per range (two 32-index chunks on the tensor cores).
 // mode: 0 FP32 CUDA cores, 1 tcgen05 on TF32 operands, 2 tcgen05 on split (3xTF32) operands.
-static int gemm(ntf_ctx *ctx, Gemm g, cudaStream_t s, int mode = 0) {
+// tune (tensor cores): on the first call for a shape, time every tile width with its rule's
+// ranges, and the rule's width with half and twice its ranges, and keep the fastest for the
+// process (not while the stream is being captured: the rule's plan then).
+static int gemm(ntf_ctx *ctx, Gemm g, cudaStream_t s, int mode = 0, bool tune = false) {
     if (mode) {
         // tensor cores: an A shared by every batch (sab = 0) serves several batches per tile, with
         // the batch folded into the columns (the B^(3) build, Y = A2^T W, H); then the widest tile
@@ -254,37 +305,81 @@ static int gemm(ntf_ctx *ctx, Gemm g, cudaStream_t s, int mode = 0) {
             f.N = g.N * g.batch;
             f.batch = 1;
         }
-        const int nchunks = std::max(1, (f.K1 * f.K2 + 31) / 32);
-        const int64_t want = 2 * (int64_t)ctx_num_sms(ctx);
+        const int sms = ctx_num_sms(ctx);
+        const int64_t want = 2 * (int64_t)sms;
         int ntt = 32, splits = 1;
         for (int w = 256; w >= 32; w >>= 1) {
             if (w > 32 && f.N <= w / 2) continue;
             const int64_t tiles = (int64_t)((f.N + w - 1) / w) * ((f.M + 127) / 128) * f.batch;
-            const int sp = (int)std::max<int64_t>(1, std::min<int64_t>((want + tiles - 1) / tiles, nchunks / 2));
+            const int sp = tc_splits(f, w, sms);
             if (tiles * sp >= want || w == 32) {
                 ntt = w;
                 splits = sp;
                 break;
             }
         }
-        f.kchunks = std::max(1, (nchunks + splits - 1) / splits);
-        f.splits = std::max(1, (nchunks + f.kchunks - 1) / f.kchunks);
-        // the grid's z extent is batch x splits; past it, the CUDA-core kernel below
-        if ((int64_t)f.batch * f.splits <= 65535 && (f.M + 127) / 128 <= 65535) {
-            f.err = ctx_status(ctx);
-            if (f.splits > 1) {
-                f.part = (float *)ctx_ws(ctx, "gemm_split", sizeof(float) * (size_t)f.splits * f.batch * f.M * f.N);
-                if (!f.part) return ctx_fail(ctx, NTF_ERR_OOM, "workspace allocation failed");
+        if (tune) {
+            int dev = 0;
+            cudaGetDevice(&dev);
+            const GemmKey key{dev, f.M, f.N, f.K1, f.K2, f.batch, mode, f.sab, f.sam, f.sak1, f.sak2, f.sbb, f.sbk1,
+                              f.sbk2, f.sbn};
+            bool found = false;
+            {
+                std::lock_guard<std::mutex> lk(g_gemm_mu);
+                auto it = g_gemm_tuned.find(key);
+                if (it != g_gemm_tuned.end()) {
+                    ntt = it->second.first;
+                    splits = it->second.second;
+                    found = true;
+                }
             }
-            cudaError_t e = gemm_tc_launch(f, mode == 2, ntt, s);
-            if (e == cudaSuccess && f.splits > 1) {
-                e = split_sum(f, s, false);
-                ctx_count(ctx, 1);
+            cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+            if (!found && cudaStreamIsCapturing(s, &cap) == cudaSuccess && cap == cudaStreamCaptureStatusNone) {
+                std::vector<std::pair<int, int>> cand;
+                for (int w = 256; w >= 32; w >>= 1)
+                    if (w == 32 || f.N > w / 2) cand.push_back({w, tc_splits(f, w, sms)});
+                cand.push_back({ntt, std::max(1, splits / 2)});
+                cand.push_back({ntt, splits * 2});
+                cudaEvent_t e0, e1;
+                if (cudaEventCreate(&e0) != cudaSuccess) return ctx_fail(ctx, NTF_ERR_CUDA, "event creation failed");
+                if (cudaEventCreate(&e1) != cudaSuccess) {
+                    cudaEventDestroy(e0);
+                    return ctx_fail(ctx, NTF_ERR_CUDA, "event creation failed");
+                }
+                float best = -1.0f;
+                int rc = NTF_OK;
+                for (const auto &c : cand) {
+                    int r = gemm_tc_run(ctx, f, c.first, c.second, mode, s);  // untimed: code and caches
+                    if (r == NTF_ERR_UNSUPPORTED) continue;
+                    if (!r && cudaEventRecord(e0, s) != cudaSuccess) r = NTF_ERR_CUDA;
+                    if (r) {
+                        rc = r;
+                        break;
+                    }
+                    for (int q = 0; q < 2 && !r; ++q) r = gemm_tc_run(ctx, f, c.first, c.second, mode, s);
+                    float ms = 0.0f;
+                    if (r || cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                        rc = r ? r : NTF_ERR_CUDA;
+                        break;
+                    }
+                    if (best < 0.0f || ms < best) {
+                        best = ms;
+                        ntt = c.first;
+                        splits = c.second;
+                    }
+                }
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                if (rc == NTF_ERR_CUDA) return ctx_fail(ctx, rc, "autotuning a contraction failed");
+                if (rc) return rc;
+                std::lock_guard<std::mutex> lk(g_gemm_mu);
+                g_gemm_tuned[key] = {ntt, splits};
             }
-            if (e != cudaSuccess) return ctx_fail(ctx, NTF_ERR_CUDA, cudaGetErrorString(e));
-            ctx_count(ctx, 1);
-            return NTF_OK;
         }
+        const int r = gemm_tc_run(ctx, f, ntt, splits, mode, s);
+        if (r != NTF_ERR_UNSUPPORTED) return r;
+        // past the grid's z extent (batch x splits): the CUDA-core kernel below
     }
     // tile shape: four batches per CTA for outputs of at most 32 x 32, 64 x 16 or 128 x 8, else by
     // width
@@ -726,6 +821,12 @@ __global__ void bcast_rows_kernel(const float *v, int64_t rows, int RP, int part
     out[t] = t < rows * RP ? v[t % RP] : 0.0f;
 }
 
+// row index of the (i, j) pair of a stored entry in the I1*I2 x I3 view of a 3-way COO tensor
+__global__ void pair_index_kernel(const int32_t *i, const int32_t *j, int64_t nnz, int I2, int32_t *out) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < nnz) out[t] = i[t] * I2 + j[t];
+}
+
 __global__ void pad_cols_kernel(const float *src, int rows, int cols, int ld, float *dst) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (int64_t)rows * ld) return;
@@ -772,7 +873,28 @@ struct TuckerWs {
     double *cs_part;          // [CSB][RP] their partials
     Blocks cur, ref, t1, t2;  // current, reference, chi1 and chi2 transforms
     int gemm_mode;            // small contractions: 0 FP32, 1 TF32 tensor cores, 2 3xTF32 tensor cores
+    bool gemm_tune;           // time the tensor-core contraction plans (ntf_opts.autotune)
+    // sparse (COO) X at beta = 1: the stored entries as a 2-way COO tensor with rows (i, j) -> i I2 + j
+    // and columns k, on which Xhat[(i, j), k] = sum_c B3[(i, j), c] A3[k, c] is a 2-way CP model
+    bool coo;
+    ntf_tensor X2;
+    int64_t dims2[2];
+    const int32_t *idx2[2];
 };
+
+// The source COO tensor of each context's 2-way view: the view's row indices live in the
+// context's workspace, and the COO orders built for the view are cached by that pointer, so a
+// different source tensor rebuilds both.
+struct CooSrc {
+    const void *idx[3], *vals;
+    int64_t nnz, dims[3];
+    bool operator==(const CooSrc &o) const {
+        return idx[0] == o.idx[0] && idx[1] == o.idx[1] && idx[2] == o.idx[2] && vals == o.vals && nnz == o.nnz &&
+               dims[0] == o.dims[0] && dims[1] == o.dims[1] && dims[2] == o.dims[2];
+    }
+};
+std::mutex g_coo_src_mu;
+std::map<const ntf_ctx *, CooSrc> g_coo_src;
 
 #define TK(call)                                                                   \
     do {                                                                           \
@@ -796,14 +918,14 @@ int build_b3(ntf_ctx *ctx, TuckerWs &w, const Blocks &b, float *out, cudaStream_
     g.A = b.A1; g.B = b.G; g.C = w.GA1;
     g.M = w.I1; g.N = w.J2 * w.J3; g.K1 = w.J1; g.K2 = 1; g.batch = 1;
     g.sam = w.J1; g.sak1 = 1; g.sbk1 = (int64_t)w.J2 * w.J3; g.sbn = 1; g.scm = (int64_t)w.J2 * w.J3; g.scn = 1;
-    { const int rc_ = gemm(ctx, g, st, w.gemm_mode); if (rc_) return rc_; }
+    { const int rc_ = gemm(ctx, g, st, w.gemm_mode, w.gemm_tune); if (rc_) return rc_; }
     Gemm h{};
     h.A = b.A2; h.B = w.GA1; h.C = out;
     h.M = w.I2; h.N = w.J3; h.K1 = w.J2; h.K2 = 1; h.batch = w.I1;
     h.sab = 0; h.sam = w.J2; h.sak1 = 1;
     h.sbb = (int64_t)w.J2 * w.J3; h.sbk1 = w.J3; h.sbn = 1;
     h.scb = (int64_t)w.I2 * w.RP; h.scm = w.RP; h.scn = 1;
-    { const int rc_ = gemm(ctx, h, st, w.gemm_mode); if (rc_) return rc_; }
+    { const int rc_ = gemm(ctx, h, st, w.gemm_mode, w.gemm_tune); if (rc_) return rc_; }
     return NTF_OK;
 }
 
@@ -831,6 +953,23 @@ int colsum_rows(ntf_ctx *ctx, TuckerWs &w, const float *src, int64_t rows, cudaS
 // W (and Wd) from P, Q with third-factor columns n3 / d3; Xhat from rrow, A3rec.
 int rows_pass(ntf_ctx *ctx, TuckerWs &w, const ntf_tensor *X, const ntf_opts &o, float beta, const float *rrow,
               const float *a3rec, const float *n3, const float *d3, bool obj, cudaStream_t st) {
+    if (w.coo) {
+        // W over the stored entries: the 2-way view's rows contraction, W[(i, j)][c] = sum_k P A3n[k][c]
+        // (Section 6.3: P vanishes where X does); with obj the whole KL objective (stored entries +
+        // sum of Xhat = sum_c colsum(B3)_c colsum(A3)_c) into w.obj[0]
+        const float *rec[2] = {rrow, a3rec}, *num[2] = {rrow, n3};
+        double *objp = nullptr;
+        int nobj = 0;
+        int rc = coo_num_rows(ctx, &w.X2, 0, w.RP, rec, num, 1.0f, (float)o.eps, w.Wn, obj ? &objp : nullptr, &nobj, st);
+        if (rc) return rc;
+        if (obj && (rc = coo_kl_objective_total(ctx, &w.X2, rec, w.J3, w.RP, objp, nobj, w.obj, st))) return rc;
+        // Q = 1: Wd[(i, j)][c] = sum_k d3[k][c] for every row
+        if ((rc = colsum_rows(ctx, w, d3, w.I3, st))) return rc;
+        const int64_t n = (int64_t)w.I1 * w.I2 * w.RP;
+        bcast_rows_kernel<<<nblk(n), 256, 0, st>>>(w.cs, (int64_t)w.I1 * w.I2, w.RP, 1, w.Wd);
+        TK(cudaGetLastError());
+        return NTF_OK;
+    }
     if (w.tc) {
         Cp3Args a = base_args(X, w, o, beta);
         a.rrow = rrow;
@@ -888,13 +1027,13 @@ int contract_from_w(ntf_ctx *ctx, TuckerWs &w, int block, const Blocks &b, const
         g.sam = 1; g.sak1 = w.J2;
         g.sbb = (int64_t)w.I2 * w.RP; g.sbk1 = w.RP; g.sbn = 1;
         g.scb = (int64_t)w.J2 * w.J3; g.scm = w.J3; g.scn = 1;
-        { const int rc_ = gemm(ctx, g, st, w.gemm_mode); if (rc_) return rc_; }
+        { const int rc_ = gemm(ctx, g, st, w.gemm_mode, w.gemm_tune); if (rc_) return rc_; }
         Gemm h{};
         h.A = b.A1; h.B = w.Y; h.C = out;
         h.M = w.J1; h.N = w.J2 * w.J3; h.K1 = w.I1; h.K2 = 1; h.batch = 1;
         h.sam = 1; h.sak1 = w.J1; h.sbk1 = (int64_t)w.J2 * w.J3; h.sbn = 1;
         h.scm = (int64_t)w.J2 * w.J3; h.scn = 1;
-        { const int rc_ = gemm(ctx, h, st, w.gemm_mode); if (rc_) return rc_; }
+        { const int rc_ = gemm(ctx, h, st, w.gemm_mode, w.gemm_tune); if (rc_) return rc_; }
     } else if (block == 1) {  // H[j][a][c] = sum_b A2[j,b] G[a,b,c]; Num1 = sum_{j,c} W H
         Gemm g{};
         g.A = b.A2; g.B = b.G; g.C = w.H;
@@ -902,33 +1041,33 @@ int contract_from_w(ntf_ctx *ctx, TuckerWs &w, int block, const Blocks &b, const
         g.sam = w.J2; g.sak1 = 1;
         g.sbb = (int64_t)w.J2 * w.J3; g.sbk1 = w.J3; g.sbn = 1;
         g.scb = w.J3; g.scm = (int64_t)w.J1 * w.J3; g.scn = 1;
-        { const int rc_ = gemm(ctx, g, st, w.gemm_mode); if (rc_) return rc_; }
+        { const int rc_ = gemm(ctx, g, st, w.gemm_mode, w.gemm_tune); if (rc_) return rc_; }
         Gemm h{};
         h.A = W; h.B = w.H; h.C = out;
         h.M = w.I1; h.N = w.J1; h.K1 = w.I2; h.K2 = w.J3; h.batch = 1;
         h.sam = (int64_t)w.I2 * w.RP; h.sak1 = w.RP; h.sak2 = 1;
         h.sbk1 = (int64_t)w.J1 * w.J3; h.sbk2 = 1; h.sbn = w.J3;
         h.scm = w.J1; h.scn = 1;
-        { const int rc_ = gemm(ctx, h, st, w.gemm_mode); if (rc_) return rc_; }
+        { const int rc_ = gemm(ctx, h, st, w.gemm_mode, w.gemm_tune); if (rc_) return rc_; }
     } else {  // GA1[i][b][c] = sum_a A1[i,a] G[a,b,c]; Num2 = sum_{i,c} W GA1
         Gemm g{};
         g.A = b.A1; g.B = b.G; g.C = w.GA1;
         g.M = w.I1; g.N = w.J2 * w.J3; g.K1 = w.J1; g.K2 = 1; g.batch = 1;
         g.sam = w.J1; g.sak1 = 1; g.sbk1 = (int64_t)w.J2 * w.J3; g.sbn = 1; g.scm = (int64_t)w.J2 * w.J3; g.scn = 1;
-        { const int rc_ = gemm(ctx, g, st, w.gemm_mode); if (rc_) return rc_; }
+        { const int rc_ = gemm(ctx, g, st, w.gemm_mode, w.gemm_tune); if (rc_) return rc_; }
         Gemm h{};
         h.A = W; h.B = w.GA1; h.C = out;
         h.M = w.I2; h.N = w.J2; h.K1 = w.I1; h.K2 = w.J3; h.batch = 1;
         h.sam = w.RP; h.sak1 = (int64_t)w.I2 * w.RP; h.sak2 = 1;
         h.sbk1 = (int64_t)w.J2 * w.J3; h.sbk2 = 1; h.sbn = w.J3;
         h.scm = w.J2; h.scn = 1;
-        { const int rc_ = gemm(ctx, h, st, w.gemm_mode); if (rc_) return rc_; }
+        { const int rc_ = gemm(ctx, h, st, w.gemm_mode, w.gemm_tune); if (rc_) return rc_; }
     }
     return NTF_OK;
 }
 
 int setup(ntf_ctx *ctx, const ntf_tensor *X, const int64_t *core_dims, bool jcomm, TuckerWs &w, const ntf_opts &o,
-          float beta) {
+          float beta, cudaStream_t st_setup = nullptr) {
     w.I1 = (int)X->dims[0]; w.I2 = (int)X->dims[1]; w.I3 = (int)X->dims[2];
     w.J1 = (int)core_dims[0]; w.J2 = (int)core_dims[1]; w.J3 = (int)core_dims[2];
     // tensor cores when asked for and the shapes fit them: third core dimension <= 32
@@ -936,9 +1075,12 @@ int setup(ntf_ctx *ctx, const ntf_tensor *X, const int64_t *core_dims, bool jcom
     // carry no denominator side and its sums are column sums (closed_den)
     w.tc = o.precision != NTF_PREC_FP32 && w.J3 <= 32 && cp3_tc_eligible(32, w.I3, X->values) &&
            (int64_t)w.I1 * w.I2 < (1ll << 31);
-    w.RP = w.tc ? 32 : rank_pad(w.J3);
+    w.coo = X->kind == NTF_COO;
+    if (w.coo) w.tc = false;  // the stored-entry passes run on CUDA cores; their rows are 32 or 64 wide
+    w.RP = w.tc ? 32 : w.coo ? (w.J3 <= 32 ? 32 : 64) : rank_pad(w.J3);
     // the small contractions follow the passes: tensor cores when the passes use them
     w.gemm_mode = !w.tc ? 0 : o.precision == NTF_PREC_3XTF32 ? 2 : 1;
+    w.gemm_tune = o.autotune != 0;
     const int64_t IJ = (int64_t)w.I1 * w.I2, Jc = (int64_t)w.J1 * w.J2 * w.J3;
     bool ok = true;
     w.Brec = wsf(ctx, "tkBrec", IJ * w.RP, ok);
@@ -961,7 +1103,7 @@ int setup(ntf_ctx *ctx, const ntf_tensor *X, const int64_t *core_dims, bool jcom
         w.Wpn = wsf(ctx, "tkWpn", (int64_t)w.tplan.n_kb * IJ * w.RP, ok);
         w.Wpd = wsf(ctx, "tkWpd", (int64_t)w.tplan.n_kb * IJ * w.RP, ok);
     }
-    w.parts3 = w.tc ? w.tplan.parts3 : w.plan3.parts3;
+    w.parts3 = w.coo ? 1 : w.tc ? w.tplan.parts3 : w.plan3.parts3;
     w.pn3 = wsf(ctx, "tkPn3", (int64_t)w.parts3 * w.I3 * w.RP, ok);
     w.pd3 = wsf(ctx, "tkPd3", (int64_t)w.parts3 * w.I3 * w.RP, ok);
     // rows pass grid: row tiles x slab splits, about one wave per SM
@@ -971,7 +1113,7 @@ int setup(ntf_ctx *ctx, const ntf_tensor *X, const int64_t *core_dims, bool jcom
     if (is > w.I1) is = w.I1;
     w.rows_is = is;
     w.rows_grid = n_jt * is;
-    w.obj_n = w.tc ? w.tplan.grid : w.rows_grid;
+    w.obj_n = w.coo ? 1 : w.tc ? w.tplan.grid : w.rows_grid;
     int gmax = std::max(std::max(w.rows_grid, w.plan3.grid), w.tc ? w.tplan.grid : 0);
     w.obj = (double *)ctx_ws(ctx, "tkObj", sizeof(double) * (size_t)gmax);
     if (!w.obj) ok = false;
@@ -988,6 +1130,34 @@ int setup(ntf_ctx *ctx, const ntf_tensor *X, const int64_t *core_dims, bool jcom
         bs[q]->A3p = wsf(ctx, names[q][3], (int64_t)w.I3 * w.RP, ok);
     }
     if (!ok) return ctx_fail(ctx, NTF_ERR_OOM, "Tucker workspace allocation failed");
+    if (w.coo) {
+        if ((int64_t)w.I1 * w.I2 >= (1ll << 31)) return ctx_fail(ctx, NTF_ERR_SHAPE, "I1 * I2 exceeds 32-bit indices");
+        int32_t *rows = (int32_t *)ctx_ws(ctx, "tkCooRows", sizeof(int32_t) * (size_t)(X->nnz + 1));
+        if (!rows) return ctx_fail(ctx, NTF_ERR_OOM, "Tucker workspace allocation failed");
+        w.dims2[0] = (int64_t)w.I1 * w.I2;
+        w.dims2[1] = w.I3;
+        w.idx2[0] = rows;
+        w.idx2[1] = X->idx[2];
+        w.X2 = *X;
+        w.X2.order = 2;
+        w.X2.dims = w.dims2;
+        w.X2.idx = w.idx2;
+        const CooSrc src{{X->idx[0], X->idx[1], X->idx[2]}, X->values, X->nnz, {X->dims[0], X->dims[1], X->dims[2]}};
+        bool same;
+        {
+            std::lock_guard<std::mutex> lk(g_coo_src_mu);
+            auto it = g_coo_src.find(ctx);
+            same = it != g_coo_src.end() && it->second == src;
+            g_coo_src[ctx] = src;
+        }
+        if (!same) {  // a new source tensor: its pair rows, and the view's orders rebuilt on first use
+            coo_release(ctx);
+            if (X->nnz > 0) {
+                pair_index_kernel<<<nblk(X->nnz), 256, 0, st_setup>>>(X->idx[0], X->idx[1], X->nnz, w.I2, rows);
+                TK(cudaGetLastError());
+            }
+        }
+    }
     return NTF_OK;
 }
 
@@ -1024,6 +1194,18 @@ int apply_mu(ntf_ctx *ctx, TuckerWs &w, const float *pre, float *out, int64_t n,
 
 int mode3_pass(ntf_ctx *ctx, TuckerWs &w, const ntf_tensor *X, const ntf_opts &o, float beta, const float *rrow,
                const float *a3rec, const float *nrow, const float *drow, bool obj, cudaStream_t st) {
+    if (w.coo) {
+        // Num3[k][c] = sum over the stored entries of P nrow[(i, j)][c]; Q = 1: Den3[k][c] = the
+        // column sums of drow over all (i, j), the same for every k
+        const float *rec[2] = {rrow, a3rec}, *num[2] = {nrow, a3rec};
+        int rc = coo_num_rows(ctx, &w.X2, 1, w.RP, rec, num, 1.0f, (float)o.eps, w.pn3, nullptr, nullptr, st);
+        if (rc) return rc;
+        if ((rc = colsum_rows(ctx, w, drow, (int64_t)w.I1 * w.I2, st))) return rc;
+        const int64_t n = (int64_t)w.I3 * w.RP;
+        bcast_rows_kernel<<<nblk(n), 256, 0, st>>>(w.cs, w.I3, w.RP, 1, w.pd3);
+        TK(cudaGetLastError());
+        return NTF_OK;
+    }
     Cp3Args a = base_args(X, w, o, beta);
     a.rrow = rrow;
     a.nrow = nrow;
@@ -1085,7 +1267,7 @@ int tucker_run(ntf_ctx *ctx, const ntf_tensor *X, float beta, const int64_t *cor
     if (int rc0 = check_core(ctx, X, core_dims, factors)) return rc0;
     if (X->order > 3) return tucker_nway_run(ctx, X, beta, core_dims, core, factors, o, objective_dev, st, jcomm);
     TuckerWs w{};
-    int rc = setup(ctx, X, core_dims, jcomm, w, o, beta);
+    int rc = setup(ctx, X, core_dims, jcomm, w, o, beta, st);
     if (rc) return rc;
     const float eps = (float)o.eps;
     const int64_t Jc = (int64_t)w.J1 * w.J2 * w.J3;
@@ -1201,10 +1383,17 @@ int tucker_beta_div(ntf_ctx *ctx, const ntf_tensor *X, float beta, const int64_t
     if (int rc0 = check_core(ctx, X, core_dims, factors)) return rc0;
     if (X->order > 3) return tucker_nway_beta_div(ctx, X, beta, core_dims, core, factors, o, out_dev, st);
     TuckerWs w{};
-    int rc = setup(ctx, X, core_dims, false, w, o, beta);
+    int rc = setup(ctx, X, core_dims, false, w, o, beta, st);
     if (rc) return rc;
     if ((rc = load_blocks(ctx, w, core, factors, w.cur, st))) return rc;
     if ((rc = build_b3(ctx, w, w.cur, w.Brec, st))) return rc;
+    if (w.coo) {  // stored-entry part from the 2-way view's pass, the dense part in closed form
+        const float *rec[2] = {w.Brec, w.cur.A3p};
+        double *objp = nullptr;
+        int nobj = 0;
+        if ((rc = coo_num_rows(ctx, &w.X2, 0, w.RP, rec, rec, 1.0f, (float)o.eps, nullptr, &objp, &nobj, st))) return rc;
+        return coo_kl_objective_total(ctx, &w.X2, rec, w.J3, w.RP, objp, nobj, out_dev, st);
+    }
     Cp3Args a = base_args(X, w, o, beta);
     a.rrow = w.Brec;
     for (int m = 0; m < 3; ++m) a.rec[m] = a.num[m] = a.den[m] = w.cur.A3p;
@@ -1235,7 +1424,7 @@ int tucker_run_extrap(ntf_ctx *ctx, const ntf_tensor *X, float beta, const int64
         if (core_dims[n] > X->dims[n]) return ctx_fail(ctx, NTF_ERR_SHAPE, "core dimension exceeds tensor dimension");
     }
     TuckerWs w{};
-    int rc = setup(ctx, X, core_dims, false, w, o, beta);
+    int rc = setup(ctx, X, core_dims, false, w, o, beta, st);
     if (rc) return rc;
     const float eps = (float)o.eps;
     const int64_t Jc = (int64_t)w.J1 * w.J2 * w.J3;

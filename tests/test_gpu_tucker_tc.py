@@ -67,6 +67,31 @@ def test_tucker_tc_jcomm_parity(beta, L, prec):
     _check(Gd, Ad, Gw, Aw, obj, Fw, "tucker tc %s jcomm beta=%g L=%d" % (prec, beta, L))
 
 
+@pytest.mark.parametrize("prec", ["tf32", "3xtf32"])
+@pytest.mark.parametrize("method", ["block", "jcomm"])
+def test_tucker_tc_autotuned_contractions(prec, method):
+    """Contraction plans timed by the autotuner (tile width and reduction split per product):
+    the first call tunes, the second reuses the table; both against the oracle at the
+    tensor-core bars."""
+    ntf = _ntf()
+    dims, J = CASES[1]
+    X, _, _ = synth.tucker_dense(dims, J, seed=44)
+    G0, A0 = synth.init_tucker(dims, J, seed=45)
+    if method == "block":
+        Gw, Aw, Fw = oracle.tucker_mu_sweep(X, G0, A0, 1.5)
+    else:
+        Gw, Aw, Fw = oracle.tucker_jcomm_outer(X, G0, A0, 1.5)
+    Xd = dev(X)
+    for rep in range(2):
+        Gd, Ad, obj = dev(G0), [dev(a) for a in A0], obj_tensor()
+        if method == "block":
+            ntf.tucker_mu_sweep(Xd, 1.5, Gd, Ad, objective=obj, precision=prec, autotune=True)
+        else:
+            ntf.jcomm_outer(Xd, 1.5, Ad, core=Gd, objective=obj, precision=prec, autotune=True)
+        ntf.default_context().device_status()
+        _check(Gd, Ad, Gw, Aw, obj, Fw, "tucker tc %s %s autotuned call %d" % (prec, method, rep))
+
+
 def test_tucker_tc_kl_runs_on_tensor_cores():
     """beta = 1 with precision "tf32" runs the tensor-core passes without a denominator side
     (Q = 1: the Wd rows and the mode-3 denominators are column sums): tensor-core bar against

@@ -1,6 +1,6 @@
 // Fused dense 3-way CP pass on CUDA cores (FP32 FMA), the parity path.
 //
-// One CTA (256 threads) owns a row tile of TJ rows j in [j0, j0+TJ), a column block of
+// One CTA (256 threads) owns a row tile of TJ = 64 rows j in [j0, j0+TJ), a column block of
 // KB = 64 columns k in [k0, k0+KB) and a slab range i in [i0, i1).  For each i it walks
 // the column block in chunks of KC = 32 columns:
 //   GEMM1  Xhat[j][k] = sum_r Arec[i][r] Brec[j][r] Crec[k][r]        (reduction over R)
@@ -27,9 +27,13 @@ constexpr int KB = 64;
 constexpr int NCH = KB / KC;
 constexpr int XS = KC + 4;
 
+// Tiles of 64 rows: at RP <= 32 the shared-memory layout then stays under 100 KB and two CTAs
+// (16 warps) share an SM, which the latency-bound loops below need more than the longer register
+// tiles that 128-row tiles allow
 template <int RP>
 struct Geo {
-    static constexpr int TJ = (RP == 64) ? 64 : 128;
+    static constexpr int TJ = 64;
+    static constexpr int MINB = (RP == 64) ? 1 : 2;  // resident CTAs per SM the launch bounds ask for
     static constexpr int RW = TJ / 32;  // rows per thread in GEMM1 / rows-GEMM2
     static constexpr int RG = RP / 8;   // rank columns per thread in the GEMM2s
     static constexpr int TS = TJ / 4;   // rows per slice in the cols-GEMM2
@@ -500,7 +504,7 @@ __device__ __forceinline__ void cp3_fp32_body(const Cp3Args &a, const int blk) {
 }
 
 template <int RP, bool DEN, int MS>
-__global__ void __launch_bounds__(NT, 1) cp3_pass_fp32(const Cp3Args a) {
+__global__ void __launch_bounds__(NT, Geo<RP>::MINB) cp3_pass_fp32(const Cp3Args a) {
     cp3_fp32_body<RP, DEN, MS>(a, blockIdx.x);
 }
 
@@ -509,7 +513,7 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_fp32(const Cp3Args a) {
 // does exactly the arithmetic of the single-job kernel, so a job's partial sums do not depend
 // on the other jobs of the table.
 template <int RP, bool DEN, int MS>
-__global__ void __launch_bounds__(NT, 1) cp3_pass_fp32_batched(const BatchTable<Cp3Args> t) {
+__global__ void __launch_bounds__(NT, Geo<RP>::MINB) cp3_pass_fp32_batched(const BatchTable<Cp3Args> t) {
     const int n = *t.n;
     const int total = n > 0 ? t.pfx[n] : 0;
     for (int item = blockIdx.x; item < total; item += gridDim.x) {

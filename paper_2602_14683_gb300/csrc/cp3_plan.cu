@@ -12,7 +12,7 @@ cudaError_t cp3_batched_fp32_r16(const BatchTable<Cp3Args> &, int, int, int, cud
 cudaError_t cp3_batched_fp32_r32(const BatchTable<Cp3Args> &, int, int, int, cudaStream_t);
 cudaError_t cp3_batched_fp32_r64(const BatchTable<Cp3Args> &, int, int, int, cudaStream_t);
 
-// Row tiles of TJ rows (128; 64 at RP = 64), column blocks of 64 columns, and the slab
+// Row tiles of TJ rows (128 on the tensor cores, 64 on the FP32 pass), column blocks of KB columns, and the slab
 // axis split so that the grid quantises well onto the SMs (one resident CTA per SM):
 // the split minimises waves * (ceil(I / n_is) + c0), where c0 = 4 slab-equivalents is
 // the per-CTA cost of staging factor blocks and writing partial sums; ties go to fewer
@@ -21,7 +21,7 @@ Cp3Plan cp3_plan(int I, int J, int K, int RP, int num_sms, int kb, int force_is)
     Cp3Plan p{};
     p.tc = kb >= 128;
     p.RP = RP;
-    p.TJ = (RP == 64) ? 64 : 128;
+    p.TJ = p.tc ? 128 : 64;
     p.KB = kb;
     p.n_jt = (J + p.TJ - 1) / p.TJ;
     p.n_kb = (K + p.KB - 1) / p.KB;

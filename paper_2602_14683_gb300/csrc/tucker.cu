@@ -435,7 +435,7 @@ struct RowsArgs {
 };
 
 template <int RP, bool DEN, bool OBJ>
-__global__ void __launch_bounds__(fp32::NT, 1) tucker_rows_kernel(const RowsArgs ra) {
+__global__ void __launch_bounds__(fp32::NT, fp32::Geo<RP>::MINB) tucker_rows_kernel(const RowsArgs ra) {
     using namespace fp32;
     using G = Geo<RP>;
     constexpr int TJ = G::TJ, RW = G::RW, RG = G::RG, RS = G::RS, TT = G::TT;
@@ -1106,10 +1106,11 @@ int setup(ntf_ctx *ctx, const ntf_tensor *X, const int64_t *core_dims, bool jcom
     w.parts3 = w.coo ? 1 : w.tc ? w.tplan.parts3 : w.plan3.parts3;
     w.pn3 = wsf(ctx, "tkPn3", (int64_t)w.parts3 * w.I3 * w.RP, ok);
     w.pd3 = wsf(ctx, "tkPd3", (int64_t)w.parts3 * w.I3 * w.RP, ok);
-    // rows pass grid: row tiles x slab splits, about one wave per SM
-    const int TJ = (w.RP == 64) ? 64 : 128;
+    // the FP32 rows kernel's tile (fp32::Geo) and about one wave of its resident CTAs (two per SM
+    // at RP <= 32)
+    const int TJ = 64, per_sm = w.RP == 64 ? 1 : 2;
     const int n_jt = (w.I2 + TJ - 1) / TJ;
-    int is = (ctx_num_sms(ctx) + n_jt - 1) / n_jt;
+    int is = (per_sm * ctx_num_sms(ctx) + n_jt - 1) / n_jt;
     if (is > w.I1) is = w.I1;
     w.rows_is = is;
     w.rows_grid = n_jt * is;

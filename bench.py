@@ -489,28 +489,33 @@ def run_coo_c4(ntf, ctx, peaks, iters=20, R=32, seed=0):
     l2 = l2_copy_gbs()
     # beta = 3/2 on the same tensor (Section 6.3): stored-entry numerators, and every denominator a
     # pass over the whole 8.6e9-entry index space that reads no X (2R flops for Xhat and 2R for the
-    # contraction per index entry, one pass per mode)
+    # contraction per index entry, one pass per mode), on the tensor cores and on the FP32 pipe
     beta_other = None
     if iters > 0:
-        B = [a.clone() for a in A0]
-        ntf.jcomm_outer(X, 1.5, B, objective=obj, ctx=ctx)
-        torch.cuda.synchronize()
-        e0.record()
-        for _ in range(2):
-            ntf.jcomm_outer(X, 1.5, B, objective=obj, ctx=ctx)
-        e1.record()
-        torch.cuda.synchronize()
-        ms15 = e0.elapsed_time(e1) / 2
         cells = 1
         for d in dims:
             cells *= d
         dflops = N * cells * 4 * R
-        beta_other = {"beta": 1.5, "ms_per_outer": ms15,
-                      "dense_pass": {"achieved_tflops": dflops / (ms15 / 1e3) / 1e12, "peak_tflops": fp32_peak,
-                                     "frac": dflops / (ms15 / 1e3) / 1e12 / fp32_peak,
-                                     "of": "N X-free FP32 passes over the %d index entries, 4R flops each (the "
-                                           "denominators and the objective's dense part), over the whole outer "
-                                           "iteration (the stored-entry passes included)" % cells}}
+        beta_other = {"beta": 1.5}
+        for prec in ("tf32", "fp32"):
+            B = [a.clone() for a in A0]
+            ntf.jcomm_outer(X, 1.5, B, objective=obj, ctx=ctx, precision=prec)
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(2):
+                ntf.jcomm_outer(X, 1.5, B, objective=obj, ctx=ctx, precision=prec)
+            e1.record()
+            torch.cuda.synchronize()
+            ms15 = e0.elapsed_time(e1) / 2
+            peak, pname = (peaks["bf16_tflops"], "measured dense bf16 tensor peak (burst)") if prec == "tf32" else \
+                (fp32_peak, "derived FP32 FMA-pipe peak")
+            beta_other[prec] = {"ms_per_outer": ms15, "objective": obj.item(),
+                                "dense_pass": {"achieved_tflops": dflops / (ms15 / 1e3) / 1e12, "peak_tflops": peak,
+                                               "frac": dflops / (ms15 / 1e3) / 1e12 / peak,
+                                               "of": "N X-free passes over the %d index entries, 4R flops each "
+                                                     "(the denominators and the objective's dense part), over the "
+                                                     "whole outer iteration (the stored-entry passes included), "
+                                                     "against the %s" % (cells, pname)}}
     return {"workload": "sparse COO 183x24x1140x1717, 3.3M nnz, CP R=32, beta=1, J-CoMM L=1",
             "beta_1p5_jcomm": beta_other,
             "us_per_outer": ms * 1e3, "outer_per_s": 1e3 / ms,
@@ -1151,8 +1156,9 @@ def summary(line):
         out.append("C4 us/outer %.1f; frac hbm %.3f alu %.3f l2 %.3f" % (c4["us_per_outer"], c4["roofline"]["frac"],
                                                                         c4["alu"]["frac"], c4["l2_gather"]["frac"]))
         if c4.get("beta_1p5_jcomm"):
-            out.append("C4 shape at beta=1.5: %.1f ms/outer (dense X-free passes %.3f of FP32 peak)" % (
-                c4["beta_1p5_jcomm"]["ms_per_outer"], c4["beta_1p5_jcomm"]["dense_pass"]["frac"]))
+            b15 = c4["beta_1p5_jcomm"]
+            out.append("C4 shape at beta=1.5: %.1f ms/outer on tensor cores, %.1f ms on the FP32 pipe" % (
+                b15["tf32"]["ms_per_outer"], b15["fp32"]["ms_per_outer"]))
     if o.get("batch_cp"):
         bc = o["batch_cp"]
         out.append("batched small CP jobs: %.1f solves/s (%d jobs), one at a time %.1f solves/s" % (

@@ -65,6 +65,10 @@ bool cp3_tc_eligible(int RP, int K, const float *X) {
 }
 
 bool cp3_tc_supported(int ms, int den, bool rx) {
+    if (ms & PM_NOX) {
+        const int m = ms & ~PM_NOX;
+        return !rx && den && (m == PM_M1 || m == (PM_M1 | PM_OBJ) || m == PM_M2 || m == PM_M3);
+    }
     if (rx) return ms == (PM_M1 | PM_M2) || ms == (PM_M1 | PM_M2 | PM_OBJ) || ms == PM_M3;
     switch (ms) {
         case PM_M1: case PM_M1 | PM_OBJ: case PM_M2: case PM_M3: return true;

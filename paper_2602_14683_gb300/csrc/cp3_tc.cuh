@@ -391,6 +391,11 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
     constexpr bool DEN = BK != BK_KL;
     constexpr bool M1 = (MS & PM_M1) != 0, M2 = (MS & PM_M2) != 0, M3 = (MS & PM_M3) != 0;
     constexpr bool OBJ = (MS & PM_OBJ) != 0, RW = M1 || M2;
+    // X-free pass (the dense part of a sparse tensor's update, Section 6.3): every entry is x = 0,
+    // so no X chunk is copied (the producer's arrival takes the copy's place on chunk_ready), P
+    // vanishes and Q = Xhat^(beta - 1) and the objective term d_beta(0 | Xhat) remain
+    constexpr bool NX = (MS & PM_NOX) != 0;
+    static_assert(!NX || (DEN && !RX && !WC), "the X-free pass is the denominator side of a CP pass");
     constexpr int CPS = KB / CH;  // chunks per slab (2 or 4)
     static_assert(KB == 128 || (KB == 256 && !DEN && !S3 && !RX), "256-column blocks: KL, single TF32");
     constexpr Layout L = make_layout(RW, M3, DEN, S3, KB);
@@ -535,6 +540,7 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
         // ---- producer thread: X chunks into the ring, PF chunks ahead into L2, GEMM1 ------
         if (lane == 0 && NC > 0) {
             auto prefetch_x = [&](int n) {
+                if (NX) return;
                 const int i = i0 + n / CPS, x = k0 + CH * (n % CPS);
                 // only boxes that start inside the tensor (a ragged block's last chunk may not)
                 if (x < K) tma_prefetch_2d(&xmap, x, i * J + j0);
@@ -544,6 +550,10 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
                 const int i = i0 + n / CPS, q = n % CPS;
                 const uint32_t bar = su32(chunk_ready + n % NS);
                 const uint32_t dst = su32(Xs) + (n % NS) * 32768;
+                if (NX) {  // nothing to copy: the arrival alone
+                    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" :: "r"(bar) : "memory");
+                    return;
+                }
                 expect_tx(bar, 32768);
                 tma_2d(&xmap, dst, bar, k0 + CH * q, i * J + j0);
                 tma_2d(&xmap, dst + 16384, bar, k0 + CH * q + 32, i * J + j0);
@@ -837,7 +847,8 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
             auto load_x = [&](int h) {
 #pragma unroll
                 for (int g = 0; g < CW / 8; ++g) {
-                    const float4 v = *reinterpret_cast<const float4 *>(xa + xo[4 * h + g]);
+                    const float4 v = NX ? make_float4(0.0f, 0.0f, 0.0f, 0.0f)
+                                        : *reinterpret_cast<const float4 *>(xa + xo[4 * h + g]);
                     xv[4 * g] = v.x; xv[4 * g + 1] = v.y; xv[4 * g + 2] = v.z; xv[4 * g + 3] = v.w;
                 }
             };
@@ -1015,8 +1026,8 @@ cudaError_t cache_map(void *base, const Cp3Args &a, CUtensorMap *map);
 template <int MS, int BK, bool S3, bool RX, int KB = KBLK, bool WC = false>
 cudaError_t launch_t(const Cp3Plan &p, const Cp3Args &a, cudaStream_t s) {
     constexpr Layout L = make_layout((MS & (PM_M1 | PM_M2)) != 0, (MS & PM_M3) != 0, BK != BK_KL, S3, KB);
-    CUtensorMap map, pm{}, qm{};
-    cudaError_t e = launch_x_map(a, &map);
+    CUtensorMap map{}, pm{}, qm{};
+    cudaError_t e = (MS & PM_NOX) ? cudaSuccess : launch_x_map(a, &map);  // the X-free pass reads no X
     if (e == cudaSuccess && WC) e = cache_map(a.pc, a, &pm);
     if (e == cudaSuccess && WC && BK != BK_KL) e = cache_map(a.qc, a, &qm);
     if (e != cudaSuccess) return e;
@@ -1037,6 +1048,19 @@ cudaError_t launch_bk(const Cp3Plan &p, const Cp3Args &a, int ms, cudaStream_t s
         if constexpr (BK != BK_KL) {
             if (p.KB == KBLK && ms == (PM_M1 | PM_OBJ)) return launch_t<PM_M1 | PM_OBJ, BK, S3, false, KBLK, true>(p, a, s);
             if (p.KB == KBLK && ms == PM_M1) return launch_t<PM_M1, BK, S3, false, KBLK, true>(p, a, s);
+        }
+        return cudaErrorInvalidValue;
+    }
+    if (ms & PM_NOX) {  // X-free denominator passes of a sparse tensor at beta != 1
+        if constexpr (BK != BK_KL) {
+            if (p.KB != KBLK) return cudaErrorInvalidValue;
+            switch (ms) {
+                case PM_M1 | PM_NOX: return launch_t<PM_M1 | PM_NOX, BK, S3, false>(p, a, s);
+                case PM_M1 | PM_OBJ | PM_NOX: return launch_t<PM_M1 | PM_OBJ | PM_NOX, BK, S3, false>(p, a, s);
+                case PM_M2 | PM_NOX: return launch_t<PM_M2 | PM_NOX, BK, S3, false>(p, a, s);
+                case PM_M3 | PM_NOX: return launch_t<PM_M3 | PM_NOX, BK, S3, false>(p, a, s);
+                default: break;
+            }
         }
         return cudaErrorInvalidValue;
     }

@@ -160,14 +160,16 @@ std::vector<int> tune_candidates(const ntf::Cp3Plan &model, int I, int sms) {
 }
 
 int cp_dense_setup(ntf_ctx *ctx, const ntf_tensor *X, int R, bool jcomm, bool need_den, int precision,
-                   CpDense &s, const ntf_opts *tune_opts = nullptr, int tune_bk = 0, int tune_ms = 0, int min_rp = 0) {
+                   CpDense &s, const ntf_opts *tune_opts = nullptr, int tune_bk = 0, int tune_ms = 0, int min_rp = 0,
+                   bool nox = false) {
     s.I = (int)X->dims[0];
     s.J = (int)X->dims[1];
     s.K = (int)X->dims[2];
     s.R = R;
     // tensor-core passes where the request asks for them and the shapes allow (rank padded
     // to 32, rows of X 16-byte aligned for TMA); FP32 CUDA-core passes otherwise
-    const bool tc = precision != NTF_PREC_FP32 && R <= 32 && ntf::cp3_tc_eligible(32, s.K, X->values);
+    // (an X-free pass reads no X, so neither K's alignment nor X's matters to it)
+    const bool tc = precision != NTF_PREC_FP32 && R <= 32 && (nox || ntf::cp3_tc_eligible(32, s.K, X->values));
     s.RP = tc ? 32 : std::max(rank_pad(R), min_rp);
     s.tc = tc;
     // 256-column blocks where the tensor memory allows them (KL: no denominator accumulators;
@@ -713,7 +715,8 @@ bool nway_single(const NWay &w, int v) { return w.ge[v] - w.gb[v] == 1; }
 
 // Run boundaries: opts->merge when given, else the split whose padded 3-way tile work is
 // least, tensor-core eligibility (rank <= 32, last run's extent a multiple of 4) weighing 8x.
-int nway_split(ntf_ctx *ctx, const ntf_tensor *X, int R, const ntf_opts &o, int precision, int &a, int &b) {
+int nway_split(ntf_ctx *ctx, const ntf_tensor *X, int R, const ntf_opts &o, int precision, int &a, int &b,
+               bool nox = false) {
     const int N = X->order;
     auto extents = [&](int ca, int cb, double *e) {  // the runs' extents; false past 32 bits
         e[0] = e[1] = e[2] = 1.0;
@@ -734,7 +737,7 @@ int nway_split(ntf_ctx *ctx, const ntf_tensor *X, int R, const ntf_opts &o, int 
         for (int cb = ca + 1; cb <= N - 1; ++cb) {
             if (!extents(ca, cb, e)) continue;
             const bool tc = precision != NTF_PREC_FP32 && R <= 32 &&
-                            ntf::cp3_tc_eligible(32, (int)e[2], X->values);
+                            (nox || ntf::cp3_tc_eligible(32, (int)e[2], X->values));
             const double kb = tc ? 128.0 : 64.0;
             const double cells = e[0] * std::ceil(e[1] / 128.0) * 128.0 * std::ceil(e[2] / kb) * kb;
             const double cost = cells * (tc ? 1.0 : 8.0);
@@ -749,10 +752,10 @@ int nway_split(ntf_ctx *ctx, const ntf_tensor *X, int R, const ntf_opts &o, int 
 }
 
 int nway_setup(ntf_ctx *ctx, const ntf_tensor *X, int R, bool jcomm, bool need_den, int precision,
-               const ntf_opts &o, CpDense &s, NWay &w, int min_rp = 0) {
+               const ntf_opts &o, CpDense &s, NWay &w, int min_rp = 0, bool nox = false) {
     w.N = X->order;
     int a = 0, b = 0;
-    int rc = nway_split(ctx, X, R, o, precision, a, b);
+    int rc = nway_split(ctx, X, R, o, precision, a, b, nox);
     if (rc) return rc;
     w.gb[0] = 0, w.ge[0] = a, w.gb[1] = a, w.ge[1] = b, w.gb[2] = b, w.ge[2] = w.N;
     for (int v = 0; v < 3; ++v) {
@@ -766,7 +769,7 @@ int nway_setup(ntf_ctx *ctx, const ntf_tensor *X, int R, bool jcomm, bool need_d
     w.X3 = *X;
     w.X3.order = 3;
     w.X3.dims = w.dims3;
-    if ((rc = cp_dense_setup(ctx, &w.X3, R, jcomm, need_den, precision, s, nullptr, 0, 0, min_rp))) return rc;
+    if ((rc = cp_dense_setup(ctx, &w.X3, R, jcomm, need_den, precision, s, nullptr, 0, 0, min_rp, nox))) return rc;
     const bool chi = jcomm && need_den;
     for (int m = 0; m < w.N; ++m) {
         const int v = w.view[m];
@@ -1022,12 +1025,15 @@ int coo_beta_check(ntf_ctx *ctx, const ntf_tensor *X, float beta) {
     return NTF_OK;
 }
 
-int cp_coo_beta_setup(ntf_ctx *ctx, const ntf_tensor *X, int R, bool jcomm, const ntf_opts &o, CpDense &s, NWay &w) {
+// precision: NTF_PREC_FP32 for the FP32 X-free pass, else the tensor-core one (R <= 32; TF32
+// reconstruction, BF16 contraction of Q, as for dense tensors)
+int cp_coo_beta_setup(ntf_ctx *ctx, const ntf_tensor *X, int R, bool jcomm, const ntf_opts &o, int precision,
+                      CpDense &s, NWay &w) {
     ntf_tensor Xv = *X;  // the index space of X, cut into three runs like a dense tensor
     Xv.kind = NTF_DENSE;
     ntf_opts od = o;
-    od.precision = NTF_PREC_FP32;
-    return nway_setup(ctx, &Xv, R, jcomm, true, NTF_PREC_FP32, od, s, w, R <= 32 ? 32 : 64);
+    od.precision = precision;
+    return nway_setup(ctx, &Xv, R, jcomm, true, precision, od, s, w, R <= 32 ? 32 : 64, /*nox=*/true);
 }
 
 // B-CoMM sweep (Algorithm 1; jcomm = false) or J-CoMM outer iteration (Algorithm 2).
@@ -1037,7 +1043,7 @@ int cp_coo_beta(ntf_ctx *ctx, const ntf_tensor *X, float beta, int R, float *con
     if (rc) return rc;
     CpDense s{};
     NWay w{};
-    if ((rc = cp_coo_beta_setup(ctx, X, R, jcomm, o, s, w))) return rc;
+    if ((rc = cp_coo_beta_setup(ctx, X, R, jcomm, o, o.precision, s, w))) return rc;
     if ((rc = nway_init(ctx, w, s, factors, jcomm, jcomm, st))) return rc;
     int64_t maxdim = 1;
     for (int m = 0; m < w.N; ++m) maxdim = std::max(maxdim, w.dims[m]);
@@ -1058,10 +1064,7 @@ int cp_coo_beta(ntf_ctx *ctx, const ntf_tensor *X, float beta, int R, float *con
         for (int n = 0; n < w.N; ++n) {
             const int v = w.view[n];
             const bool obj = l == 0 && n == 0 && objective_dev;
-            {
-                PassTimer t(ctx, st);
-                NTF_CUDA(ntf::cp3_launch(s.plan, a, mode_flag(v) | ntf::PM_NOX | (obj ? ntf::PM_OBJ : 0), 1, st));
-            }
+            if ((rc = launch_pass(ctx, s, a, mode_flag(v) | ntf::PM_NOX | (obj ? ntf::PM_OBJ : 0), 1, st))) return rc;
             double *objp = nullptr;
             int nobj = 0;
             if ((rc = ntf::coo_num_rows(ctx, X, n, s.RP, rec, nf, beta, (float)o.eps, num, obj ? &objp : nullptr,
@@ -1091,7 +1094,7 @@ int cp_coo_beta_div(ntf_ctx *ctx, const ntf_tensor *X, float beta, int R, const 
     if (rc) return rc;
     CpDense s{};
     NWay w{};
-    if ((rc = cp_coo_beta_setup(ctx, X, R, false, o, s, w))) return rc;
+    if ((rc = cp_coo_beta_setup(ctx, X, R, false, o, NTF_PREC_FP32, s, w))) return rc;
     if ((rc = nway_init(ctx, w, s, factors, false, false, st))) return rc;
     ntf::Cp3Args a = cp_args(&w.X3, s, o, beta);
     a.X = nullptr;

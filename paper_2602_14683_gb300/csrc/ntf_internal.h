@@ -117,7 +117,7 @@ __device__ __forceinline__ float chi2_f(float beta, float z, float zt) {
 // ---------------------------------------------------------------------------------
 // Dense 3-way CP pass (the fused reconstruct -> powers -> contract kernel)
 // ---------------------------------------------------------------------------------
-// PM_NOX (FP32 pass only): the entries of X are taken as 0 and X is not read -- the dense part
+// PM_NOX (FP32 pass; tensor-core pass at beta != 1): the entries of X are taken as 0 and X is not read -- the dense part
 // of a sparse tensor's update (Section 6.3): only the denominator side (Q = Xhat^(beta-1)
 // against the den factors) is contracted, and the objective term is d_beta(0 | Xhat).
 enum PassMode : int { PM_M1 = 1, PM_M2 = 2, PM_M3 = 4, PM_OBJ = 8, PM_NOX = 16 };

@@ -123,3 +123,33 @@ def test_coo_beta_rejections():
     with pytest.raises(ntf.NtfError) as e:
         ntf.cp_mu_sweep(X2c, 1.5, A2)
     assert e.value.code == -8
+
+
+TOL_TC, TOL_TC_OBJ = 1e-3, 2e-4
+
+
+@pytest.mark.parametrize("prec", ["tf32", "3xtf32"])
+@pytest.mark.parametrize("method", ["block", "jcomm"])
+@pytest.mark.parametrize("beta", [0.5, 1.5, 1.2])
+@pytest.mark.parametrize("dims,R", [((13, 17, 23), 5), ((9, 6, 31, 41), 7), ((11, 150, 131), 20)])
+def test_coo_beta_tensor_core_dense_pass(dims, R, beta, method, prec):
+    """The X-free denominator pass on the tensor cores (TF32 reconstruction, BF16 contraction of
+    Q; no X is read, so the last extent need not be a multiple of 4): the tensor-core bars of the
+    dense passes, 1e-3 per factor and 2e-4 on the objective."""
+    ntf = _ntf()
+    X, idx, vals = _sparse(5 * len(dims) + R, dims)
+    A = synth.init_factors(dims, R, seed=R + 9)
+    if method == "block":
+        want, Fw = oracle.cp_mu_sweep(X, A, beta)
+    else:
+        want, Fw = oracle.cp_jcomm_outer(X, A, beta, L=2)
+    Ad, obj = [dev(a) for a in A], obj_tensor()
+    Xc = _coo_dev(dims, idx, vals)
+    if method == "block":
+        ntf.cp_mu_sweep(Xc, beta, Ad, objective=obj, precision=prec)
+    else:
+        ntf.jcomm_outer(Xc, beta, Ad, objective=obj, inner_L=2, precision=prec)
+    ntf.default_context().device_status()
+    errs = [rel_fro(host(Ad[n]), want[n]) for n in range(len(dims))]
+    assert max(errs) <= TOL_TC, errs
+    assert abs(obj.item() - Fw) / Fw <= TOL_TC_OBJ

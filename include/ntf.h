@@ -216,8 +216,9 @@ int ntf_cp_jcomm_outer_extrap(ntf_ctx *ctx, const ntf_tensor *X, float beta, int
  *   factors:   host array of N device pointers, A^(n) is I_n x J_n, updated in place
  *   objective_dev: device double or NULL; D_beta of the incoming iterate.
  * Dense N = 3..8 (N >= 4: the last run of the cut needs a core extent <= 64), and COO of order 3
- * at beta = 1 (Section 6.3: numerators over the stored entries, closed-form denominators; FP32
- * passes whatever the precision); other COO Tucker requests return NTF_ERR_UNSUPPORTED. */
+ * at beta != 0 (Section 6.3: numerators over the stored entries; denominators in closed form at
+ * beta = 1, else from X-free passes over the whole index space; FP32 passes whatever the
+ * precision); other COO Tucker requests return NTF_ERR_UNSUPPORTED. */
 int ntf_tucker_mu_sweep(ntf_ctx *ctx, const ntf_tensor *X, float beta, const int64_t *core_dims,
                         float *core, float *const *factors, const ntf_opts *opts,
                         double *objective_dev, void *stream);
@@ -248,7 +249,7 @@ int ntf_tucker_mu_sweep_extrap(ntf_ctx *ctx, const ntf_tensor *X, float beta, co
  *   model: NTF_CP (rank_or_0 = R, core arguments NULL) or NTF_TUCKER (rank_or_0 = 0)
  *   objective_ref_dev: device double or NULL; receives D_beta at the reference.
  * CP dense N = 3..8 (any beta), CP COO (as ntf_cp_mu_sweep), Tucker dense N = 3..8 (any beta),
- * Tucker COO (order 3, beta = 1). */
+ * Tucker COO (order 3, beta != 0). */
 int ntf_jcomm_outer(ntf_ctx *ctx, int model, const ntf_tensor *X, float beta, int rank_or_0,
                     const int64_t *core_dims_or_null, float *core_or_null, float *const *factors,
                     const ntf_opts *opts, double *objective_ref_dev, void *stream);
@@ -270,7 +271,7 @@ int ntf_tucker_jcomm_outer_extrap(ntf_ctx *ctx, const ntf_tensor *X, float beta,
  * in FP32 (log1p/expm1) and are summed in FP64.  For COO the unstored entries (x = 0) add
  * d_beta(0 | Xhat) = Xhat^beta / beta: at beta = 1 the closed form sum of Xhat (CP:
  * sum_r prod_n colsum(A^(n))_r; Tucker, order 3: the same from B^(3) and A^(3)), at other beta
- * (CP) a pass over the whole index space that reads no X; COO requests as ntf_cp_mu_sweep /
+ * a pass over the whole index space that reads no X; COO requests as ntf_cp_mu_sweep /
  * ntf_tucker_mu_sweep. */
 int ntf_beta_div(ntf_ctx *ctx, int model, const ntf_tensor *X, float beta, int rank_or_0,
                  const int64_t *core_dims_or_null, const float *core_or_null,

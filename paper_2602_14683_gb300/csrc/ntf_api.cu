@@ -1111,13 +1111,14 @@ int cp_coo_beta_div(ntf_ctx *ctx, const ntf_tensor *X, float beta, int R, const 
     return NTF_OK;
 }
 
-// Tucker on a COO tensor: order 3 at beta = 1, where Q = 1 keeps every denominator a closed form and
-// the stored entries alone give the numerators and the objective's data terms (Section 6.3).  Other
-// orders and beta values would need a dense X-free Tucker rows pass, which is not built.
+// Tucker on a COO tensor, order 3 (Section 6.3): the numerators over the stored entries; at beta = 1
+// Q = 1 keeps every denominator a closed form, at other beta the denominators come from X-free dense
+// passes.  beta = 0 is excluded (d_0 needs X > 0 everywhere), and so are orders >= 4.
 int tucker_kind_check(ntf_ctx *ctx, const ntf_tensor *X, float beta) {
     if (X->kind == NTF_DENSE) return NTF_OK;
     if (X->order != 3) return fail(ctx, NTF_ERR_UNSUPPORTED, "COO Tucker is implemented for order 3");
-    if (ntf::beta_kind(beta) != ntf::BK_KL) return fail(ctx, NTF_ERR_UNSUPPORTED, "COO Tucker is implemented for beta = 1");
+    if (ntf::beta_kind(beta) == ntf::BK_IS)
+        return fail(ctx, NTF_ERR_UNSUPPORTED, "beta = 0 needs positive data; a COO tensor has unstored zeros");
     return NTF_OK;
 }
 

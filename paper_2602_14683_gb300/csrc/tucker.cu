@@ -434,7 +434,10 @@ struct RowsArgs {
     int n_is;
 };
 
-template <int RP, bool DEN, bool OBJ>
+// NOX (the dense part of a sparse tensor's update at beta != 1, Section 6.3): every entry is x = 0,
+// no X tile is staged, and only Wd (Q against the den columns) and the objective terms
+// d_beta(0 | Xhat) are computed.
+template <int RP, bool DEN, bool OBJ, bool NOX = false>
 __global__ void __launch_bounds__(fp32::NT, fp32::Geo<RP>::MINB) tucker_rows_kernel(const RowsArgs ra) {
     using namespace fp32;
     using G = Geo<RP>;
@@ -458,7 +461,7 @@ __global__ void __launch_bounds__(fp32::NT, fp32::Geo<RP>::MINB) tucker_rows_ker
 
     auto stage = [&](int buf, int i, int q) {
         const int kc = q * KC;
-        load_x_tile<TJ>(a, xs0 + buf * TJ * XS, i, j0, kc);
+        if (!NOX) load_x_tile<TJ>(a, xs0 + buf * TJ * XS, i, j0, kc);
         float *ct = ct0 + buf * RP * KC;
         for (int t = tid; t < RP * KC; t += NT) {
             const int r = t / KC, c = t % KC, k = kc + c;
@@ -528,14 +531,14 @@ __global__ void __launch_bounds__(fp32::NT, fp32::Geo<RP>::MINB) tucker_rows_ker
             for (int c = 0; c < 4; ++c) {
                 const int col = tc + 8 * c;
                 const bool v = rv && (kc + col) < K;
-                float xv = xs[row * XS + col];
-                if (a.bkind == BK_IS) xv = fmaxf(xv, a.eps_x);
+                float xv = NOX ? 0.0f : xs[row * XS + col];
+                if (!NOX && a.bkind == BK_IS) xv = fmaxf(xv, a.eps_x);
                 const float y = fmaxf(xh[x][c], a.eps);
                 float P, Q;
                 pq_powers(a.bkind, a.beta, xv, y, P, Q);
                 if (!v) { P = 0.0f; Q = 0.0f; }
                 if (OBJ && v) objf += dbeta_stable(a.bkind, a.beta, xv, y);
-                ps[row * XS + col] = P;
+                if (!NOX) ps[row * XS + col] = P;
                 if (DEN) qs[row * XS + col] = Q;
             }
         }
@@ -546,19 +549,19 @@ __global__ void __launch_bounds__(fp32::NT, fp32::Geo<RP>::MINB) tucker_rows_ker
             float p[RW][4], qv[RW][4];
 #pragma unroll
             for (int x = 0; x < RW; ++x) {
-                VecLd<4>::ld(ps + (tr * RW + x) * XS + c4 * 4, p[x]);
+                if (!NOX) VecLd<4>::ld(ps + (tr * RW + x) * XS + c4 * 4, p[x]);
                 if (DEN) VecLd<4>::ld(qs + (tr * RW + x) * XS + c4 * 4, qv[x]);
             }
 #pragma unroll
             for (int cq = 0; cq < 4; ++cq) {
                 float cv[RG], dv[RG];
-                VecLd<RG>::ld(cn + (c4 * 4 + cq) * RS + tc * RG, cv);
+                if (!NOX) VecLd<RG>::ld(cn + (c4 * 4 + cq) * RS + tc * RG, cv);
                 if (DEN) VecLd<RG>::ld(cd + (c4 * 4 + cq) * RS + tc * RG, dv);
 #pragma unroll
                 for (int x = 0; x < RW; ++x)
 #pragma unroll
                     for (int y = 0; y < RG; ++y) {
-                        W[x][y] = fmaf(p[x][cq], cv[y], W[x][y]);
+                        if (!NOX) W[x][y] = fmaf(p[x][cq], cv[y], W[x][y]);
                         if (DEN) Wd[x][y] = fmaf(qv[x][cq], dv[y], Wd[x][y]);
                     }
             }
@@ -571,7 +574,7 @@ __global__ void __launch_bounds__(fp32::NT, fp32::Geo<RP>::MINB) tucker_rows_ker
                 if (j0 + row < J) {
 #pragma unroll
                     for (int y = 0; y < RG; ++y) {
-                        ra.Wn[(rb + row) * RP + tc * RG + y] = W[x][y];
+                        if (!NOX) ra.Wn[(rb + row) * RP + tc * RG + y] = W[x][y];
                         if (DEN) ra.Wd[(rb + row) * RP + tc * RG + y] = Wd[x][y];
                     }
                 }
@@ -596,14 +599,14 @@ __global__ void __launch_bounds__(fp32::NT, fp32::Geo<RP>::MINB) tucker_rows_ker
     }
 }
 
-template <int RP, bool DEN, bool OBJ>
+template <int RP, bool DEN, bool OBJ, bool NOX = false>
 static cudaError_t rows_launch_t(const RowsArgs &ra, int grid, cudaStream_t s) {
     using namespace fp32;
     using G = Geo<RP>;
     const size_t floats = 2 * G::TJ * XS + G::TJ * XS + (DEN ? G::TJ * XS : 0) + RP * G::TT + 2 * RP * KC +
                           2 * KC * G::RS + (DEN ? 2 * KC * G::RS : 0) + 2 * 32;
     const size_t bytes = floats * sizeof(float);
-    auto k = tucker_rows_kernel<RP, DEN, OBJ>;
+    auto k = tucker_rows_kernel<RP, DEN, OBJ, NOX>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
     k<<<grid, NT, bytes, s>>>(ra);
@@ -611,16 +614,17 @@ static cudaError_t rows_launch_t(const RowsArgs &ra, int grid, cudaStream_t s) {
 }
 
 template <int RP>
-static cudaError_t rows_launch_rp(const RowsArgs &ra, int grid, bool obj, cudaStream_t s) {
+static cudaError_t rows_launch_rp(const RowsArgs &ra, int grid, bool obj, cudaStream_t s, bool nox) {
+    if (nox) return obj ? rows_launch_t<RP, true, true, true>(ra, grid, s) : rows_launch_t<RP, true, false, true>(ra, grid, s);
     return obj ? rows_launch_t<RP, true, true>(ra, grid, s) : rows_launch_t<RP, true, false>(ra, grid, s);
 }
 
-static cudaError_t rows_launch(int RP, const RowsArgs &ra, int grid, bool obj, cudaStream_t s) {
+static cudaError_t rows_launch(int RP, const RowsArgs &ra, int grid, bool obj, cudaStream_t s, bool nox = false) {
     switch (RP) {
-        case 8: return rows_launch_rp<8>(ra, grid, obj, s);
-        case 16: return rows_launch_rp<16>(ra, grid, obj, s);
-        case 32: return rows_launch_rp<32>(ra, grid, obj, s);
-        case 64: return rows_launch_rp<64>(ra, grid, obj, s);
+        case 8: return rows_launch_rp<8>(ra, grid, obj, s, nox);
+        case 16: return rows_launch_rp<16>(ra, grid, obj, s, nox);
+        case 32: return rows_launch_rp<32>(ra, grid, obj, s, nox);
+        case 64: return rows_launch_rp<64>(ra, grid, obj, s, nox);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -880,6 +884,8 @@ struct TuckerWs {
     ntf_tensor X2;
     int64_t dims2[2];
     const int32_t *idx2[2];
+    float *pd3x;     // beta != 1: the X-free mode-3 pass's Den3 partials [plan3.parts3][I3][RP]
+    double *obj_tot; // the sparse objective (stored + dense parts), one value
 };
 
 // The source COO tensor of each context's 2-way view: the view's row indices live in the
@@ -960,14 +966,35 @@ int rows_pass(ntf_ctx *ctx, TuckerWs &w, const ntf_tensor *X, const ntf_opts &o,
         const float *rec[2] = {rrow, a3rec}, *num[2] = {rrow, n3};
         double *objp = nullptr;
         int nobj = 0;
-        int rc = coo_num_rows(ctx, &w.X2, 0, w.RP, rec, num, 1.0f, (float)o.eps, w.Wn, obj ? &objp : nullptr, &nobj, st);
+        int rc = coo_num_rows(ctx, &w.X2, 0, w.RP, rec, num, beta, (float)o.eps, w.Wn, obj ? &objp : nullptr, &nobj, st);
         if (rc) return rc;
-        if (obj && (rc = coo_kl_objective_total(ctx, &w.X2, rec, w.J3, w.RP, objp, nobj, w.obj, st))) return rc;
-        // Q = 1: Wd[(i, j)][c] = sum_k d3[k][c] for every row
-        if ((rc = colsum_rows(ctx, w, d3, w.I3, st))) return rc;
-        const int64_t n = (int64_t)w.I1 * w.I2 * w.RP;
-        bcast_rows_kernel<<<nblk(n), 256, 0, st>>>(w.cs, (int64_t)w.I1 * w.I2, w.RP, 1, w.Wd);
-        TK(cudaGetLastError());
+        if (beta_kind(beta) == BK_KL) {
+            if (obj && (rc = coo_kl_objective_total(ctx, &w.X2, rec, w.J3, w.RP, objp, nobj, w.obj, st))) return rc;
+            // Q = 1: Wd[(i, j)][c] = sum_k d3[k][c] for every row
+            if ((rc = colsum_rows(ctx, w, d3, w.I3, st))) return rc;
+            const int64_t n = (int64_t)w.I1 * w.I2 * w.RP;
+            bcast_rows_kernel<<<nblk(n), 256, 0, st>>>(w.cs, (int64_t)w.I1 * w.I2, w.RP, 1, w.Wd);
+            TK(cudaGetLastError());
+            return NTF_OK;
+        }
+        // Q = Xhat^(beta - 1) is dense: Wd over the whole index space from the X-free rows pass,
+        // which also sums the objective's dense part d_beta(0 | Xhat) (rows_grid partials)
+        RowsArgs ra{};
+        ra.a = base_args(X, w, o, beta);
+        ra.a.X = nullptr;
+        ra.a.vec16 = 0;
+        ra.a.rrow = rrow;
+        ra.a.rec[2] = a3rec;
+        ra.a.num[2] = d3;
+        ra.a.den[2] = d3;
+        ra.Wn = w.Wd;  // not written by the X-free pass
+        ra.Wd = w.Wd;
+        ra.n_is = w.rows_is;
+        TK(rows_launch(w.RP, ra, w.rows_grid, obj, st, /*nox=*/true));
+        if (obj) {  // stored-entry part + dense part, as one partial for the caller's sum
+            TK(reduce_objective2(objp, nobj, w.obj, w.rows_grid, w.obj_tot, st));
+            TK(cudaMemcpyAsync(w.obj, w.obj_tot, sizeof(double), cudaMemcpyDeviceToDevice, st));
+        }
         return NTF_OK;
     }
     if (w.tc) {
@@ -1133,6 +1160,10 @@ int setup(ntf_ctx *ctx, const ntf_tensor *X, const int64_t *core_dims, bool jcom
     if (!ok) return ctx_fail(ctx, NTF_ERR_OOM, "Tucker workspace allocation failed");
     if (w.coo) {
         if ((int64_t)w.I1 * w.I2 >= (1ll << 31)) return ctx_fail(ctx, NTF_ERR_SHAPE, "I1 * I2 exceeds 32-bit indices");
+        bool ok2 = true;
+        w.pd3x = beta_kind(beta) == BK_KL ? nullptr : wsf(ctx, "tkPd3x", (int64_t)w.plan3.parts3 * w.I3 * w.RP, ok2);
+        w.obj_tot = (double *)ctx_ws(ctx, "tkObjTot", sizeof(double));
+        if (!ok2 || !w.obj_tot) return ctx_fail(ctx, NTF_ERR_OOM, "Tucker workspace allocation failed");
         int32_t *rows = (int32_t *)ctx_ws(ctx, "tkCooRows", sizeof(int32_t) * (size_t)(X->nnz + 1));
         if (!rows) return ctx_fail(ctx, NTF_ERR_OOM, "Tucker workspace allocation failed");
         w.dims2[0] = (int64_t)w.I1 * w.I2;
@@ -1199,11 +1230,32 @@ int mode3_pass(ntf_ctx *ctx, TuckerWs &w, const ntf_tensor *X, const ntf_opts &o
         // Num3[k][c] = sum over the stored entries of P nrow[(i, j)][c]; Q = 1: Den3[k][c] = the
         // column sums of drow over all (i, j), the same for every k
         const float *rec[2] = {rrow, a3rec}, *num[2] = {nrow, a3rec};
-        int rc = coo_num_rows(ctx, &w.X2, 1, w.RP, rec, num, 1.0f, (float)o.eps, w.pn3, nullptr, nullptr, st);
+        int rc = coo_num_rows(ctx, &w.X2, 1, w.RP, rec, num, beta, (float)o.eps, w.pn3, nullptr, nullptr, st);
         if (rc) return rc;
-        if ((rc = colsum_rows(ctx, w, drow, (int64_t)w.I1 * w.I2, st))) return rc;
+        if (beta_kind(beta) == BK_KL) {
+            if ((rc = colsum_rows(ctx, w, drow, (int64_t)w.I1 * w.I2, st))) return rc;
+            const int64_t n = (int64_t)w.I3 * w.RP;
+            bcast_rows_kernel<<<nblk(n), 256, 0, st>>>(w.cs, w.I3, w.RP, 1, w.pd3);
+            TK(cudaGetLastError());
+            return NTF_OK;
+        }
+        // Den3 over the whole index space: the X-free FP32 pass in mode 3 with explicit rows, its
+        // partials then summed (in part order) into the single part the update reads
+        Cp3Args a = base_args(X, w, o, beta);
+        a.X = nullptr;
+        a.vec16 = 0;
+        a.rrow = rrow;
+        a.nrow = drow;
+        a.drow = drow;
+        for (int m = 0; m < 3; ++m) a.rec[m] = a.num[m] = a.den[m] = a3rec;
+        a.n_jt = w.plan3.n_jt;
+        a.n_kb = w.plan3.n_kb;
+        a.n_is = w.plan3.n_is;
+        a.p3n = w.pd3x;  // not written by the X-free pass
+        a.p3d = w.pd3x;
+        TK(cp3_launch(w.plan3, a, PM_M3 | PM_NOX, 1, st));
         const int64_t n = (int64_t)w.I3 * w.RP;
-        bcast_rows_kernel<<<nblk(n), 256, 0, st>>>(w.cs, w.I3, w.RP, 1, w.pd3);
+        sum_parts_kernel<<<nblk(n), 256, 0, st>>>(w.pd3x, w.plan3.parts3, n, w.pd3);
         TK(cudaGetLastError());
         return NTF_OK;
     }
@@ -1388,12 +1440,23 @@ int tucker_beta_div(ntf_ctx *ctx, const ntf_tensor *X, float beta, const int64_t
     if (rc) return rc;
     if ((rc = load_blocks(ctx, w, core, factors, w.cur, st))) return rc;
     if ((rc = build_b3(ctx, w, w.cur, w.Brec, st))) return rc;
-    if (w.coo) {  // stored-entry part from the 2-way view's pass, the dense part in closed form
-        const float *rec[2] = {w.Brec, w.cur.A3p};
+    if (w.coo) {  // stored-entry part from the 2-way view's pass; the dense part in closed form (KL)
+        const float *rec[2] = {w.Brec, w.cur.A3p};  // or from an X-free objective pass (other beta)
         double *objp = nullptr;
         int nobj = 0;
-        if ((rc = coo_num_rows(ctx, &w.X2, 0, w.RP, rec, rec, 1.0f, (float)o.eps, nullptr, &objp, &nobj, st))) return rc;
-        return coo_kl_objective_total(ctx, &w.X2, rec, w.J3, w.RP, objp, nobj, out_dev, st);
+        if ((rc = coo_num_rows(ctx, &w.X2, 0, w.RP, rec, rec, beta, (float)o.eps, nullptr, &objp, &nobj, st))) return rc;
+        if (beta_kind(beta) == BK_KL) return coo_kl_objective_total(ctx, &w.X2, rec, w.J3, w.RP, objp, nobj, out_dev, st);
+        Cp3Args a = base_args(X, w, o, beta);
+        a.X = nullptr;
+        a.vec16 = 0;
+        a.rrow = w.Brec;
+        for (int m = 0; m < 3; ++m) a.rec[m] = a.num[m] = a.den[m] = w.cur.A3p;
+        a.n_jt = w.plan3.n_jt;
+        a.n_kb = w.plan3.n_kb;
+        a.n_is = w.plan3.n_is;
+        TK(cp3_launch(w.plan3, a, PM_OBJ | PM_NOX, 0, st));
+        TK(reduce_objective2(objp, nobj, w.obj, w.plan3.grid, out_dev, st));
+        return NTF_OK;
     }
     Cp3Args a = base_args(X, w, o, beta);
     a.rrow = w.Brec;

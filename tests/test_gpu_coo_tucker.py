@@ -1,8 +1,9 @@
-"""Sparse COO Tucker (order 3, KL) against the FP64 oracle on the densified tensor.
+"""Sparse COO Tucker (order 3) against the FP64 oracle on the densified tensor.
 
-At beta = 1, P = X / Xhat vanishes where X does and Q = 1 (Section 6.3), so the numerators are
-sums over the stored entries and every denominator is a closed form of column sums.  The
-library runs the stored entries as a 2-way COO tensor with rows (i, j) -> i I2 + j on which
+P = X Xhat^(beta-2) vanishes where X does (Section 6.3), so the numerators are sums over the
+stored entries; at beta = 1 (Q = 1) every denominator is a closed form of column sums, at other
+beta the denominators contract Q over the whole index space in X-free passes.  The library runs
+the stored entries as a 2-way COO tensor with rows (i, j) -> i I2 + j on which
 Xhat = B^(3) A3^T (eq. (block_Bn)); the oracle runs the dense Tucker updates with the zeros
 written out, so an entry that the sparse path misses or counts twice shows.  Bars: 1e-5 per
 block and on the objective (FP32 one-sweep bar), 1e-4 on a 10-iteration trajectory.  Shapes have
@@ -51,42 +52,44 @@ def _check(Gd, Ad, Gw, Aw, obj, Fw, tag):
     assert eo <= TOL, (tag, eo)
 
 
+@pytest.mark.parametrize("beta", [1.0, 0.5, 1.5])
 @pytest.mark.parametrize("dims,J", CASES)
-def test_coo_tucker_block_sweep(dims, J):
+def test_coo_tucker_block_sweep(dims, J, beta):
     ntf = _ntf()
     X, idx, vals = _sparse(sum(dims), dims)
     G0, A0 = synth.init_tucker(dims, J, seed=3)
-    Gw, Aw, Fw = oracle.tucker_mu_sweep(X, G0, A0, 1.0)
+    Gw, Aw, Fw = oracle.tucker_mu_sweep(X, G0, A0, beta)
     Gd, Ad, obj = dev(G0), [dev(a) for a in A0], obj_tensor()
-    ntf.tucker_mu_sweep(_coo_dev(dims, idx, vals), 1.0, Gd, Ad, objective=obj)
+    ntf.tucker_mu_sweep(_coo_dev(dims, idx, vals), beta, Gd, Ad, objective=obj)
     ntf.default_context().device_status()
     _check(Gd, Ad, Gw, Aw, obj, Fw, "block")
 
 
+@pytest.mark.parametrize("beta", [1.0, 0.5, 1.5])
 @pytest.mark.parametrize("dims,J", CASES)
 @pytest.mark.parametrize("L", [1, 2])
-def test_coo_tucker_jcomm(dims, J, L):
+def test_coo_tucker_jcomm(dims, J, L, beta):
     ntf = _ntf()
     X, idx, vals = _sparse(2 * sum(dims) + L, dims)
     G0, A0 = synth.init_tucker(dims, J, seed=4)
-    Gw, Aw, Fw = oracle.tucker_jcomm_outer(X, G0, A0, 1.0, L=L)
+    Gw, Aw, Fw = oracle.tucker_jcomm_outer(X, G0, A0, beta, L=L)
     Gd, Ad, obj = dev(G0), [dev(a) for a in A0], obj_tensor()
-    ntf.jcomm_outer(_coo_dev(dims, idx, vals), 1.0, Ad, core=Gd, objective=obj, inner_L=L)
+    ntf.jcomm_outer(_coo_dev(dims, idx, vals), beta, Ad, core=Gd, objective=obj, inner_L=L)
     ntf.default_context().device_status()
     _check(Gd, Ad, Gw, Aw, obj, Fw, "jcomm L=%d" % L)
 
 
 def test_coo_tucker_objective_and_new_source():
-    """The objective of two different tensors of the same sizes in turn (the second call must not
-    reuse the first tensor's cached orders), each against the oracle."""
+    """The objective of different tensors of the same sizes in turn (a call must not reuse another
+    tensor's cached orders), at beta = 1 and other beta, each against the oracle."""
     ntf = _ntf()
     dims, J = CASES[0]
     G0, A0 = synth.init_tucker(dims, J, seed=5)
-    for seed in (11, 12, 11):
+    for seed, beta in ((11, 1.0), (12, 1.0), (11, 1.0), (13, 1.5), (14, 0.5), (13, 1.2)):
         X, idx, vals = _sparse(seed, dims)
-        got = ntf.beta_div(_coo_dev(dims, idx, vals), 1.0, [dev(a) for a in A0], core=dev(G0)).item()
-        want = oracle.tucker_objective(X, G0, A0, 1.0)
-        assert abs(got - want) / want <= TOL, (seed, got, want)
+        got = ntf.beta_div(_coo_dev(dims, idx, vals), beta, [dev(a) for a in A0], core=dev(G0)).item()
+        want = oracle.tucker_objective(X, G0, A0, beta)
+        assert abs(got - want) / want <= TOL, (seed, beta, got, want)
 
 
 def test_coo_tucker_trajectory_10_iterations():
@@ -110,10 +113,9 @@ def test_coo_tucker_rejections():
     X, idx, vals = _sparse(31, dims)
     G0, A0 = synth.init_tucker(dims, J, seed=7)
     Xc = _coo_dev(dims, idx, vals)
-    for beta in (0.5, 1.5):
-        with pytest.raises(ntf.NtfError) as e:
-            ntf.tucker_mu_sweep(Xc, beta, dev(G0), [dev(a) for a in A0])
-        assert e.value.code == -8
+    with pytest.raises(ntf.NtfError) as e:  # beta = 0 needs x > 0 everywhere
+        ntf.tucker_mu_sweep(Xc, 0.0, dev(G0), [dev(a) for a in A0])
+    assert e.value.code == -8
     d4 = dims + (3,)
     X4 = np.zeros(d4)
     X4[0, 0, 0, 0] = 1.0

@@ -117,3 +117,34 @@ def test_iteration_caps_match_alone():
             for n in range(3):
                 assert rel_fro(host(Ad[n]), host(A1[n])) <= 1e-6, (cap, q, n)
     srv.close()
+
+
+def test_cp_jobs_larger_than_the_batch_arena_run_in_slots():
+    """With a memory budget whose batch arena (half of it) holds no CP job, the CP jobs fall back
+    to the slot lane (each job alone there when it exceeds the slots' half too) and still give the
+    alone results; Tucker jobs share the slots."""
+    ntf = _ntf()
+    import torch
+    rtol, max_iters = 1e-6, 15
+    jobs = _jobs(6, seed=13)
+    alone = [_alone(ntf, j, d, rtol, max_iters) for j, d in jobs]
+    torch.cuda.synchronize()
+    srv = ntf.Server(slots=2, mem_budget_bytes=64 << 10)
+    mixed = {}
+    for q, (j, (X, G, A)) in enumerate(jobs):
+        Xd = dev(X)
+        Ad = [dev(a) for a in A]
+        Gd = dev(G) if G is not None else None
+        mixed[srv.submit(Xd, j["beta"], Ad, core=Gd, rtol=rtol, max_iters=max_iters)] = (q, Ad, Gd)
+    res = srv.poll(wait_all=True)
+    srv.close()
+    assert len(res) == len(jobs)
+    for r in res:
+        q, Ad, Gd = mixed[r["id"]]
+        A1, G1, iters, F = alone[q]
+        assert r["status"] == 0 and r["iterations"] == iters, (q, r, iters)
+        assert abs(r["objective"] - F) <= 1e-6 * abs(F)
+        for n in range(3):
+            assert rel_fro(host(Ad[n]), host(A1[n])) <= 1e-6, (q, n)
+        if Gd is not None:
+            assert rel_fro(host(Gd), host(G1)) <= 1e-6, q

@@ -397,7 +397,10 @@ __global__ void __launch_bounds__(NT, 1) cp3_pass_tc(const __grid_constant__ CUt
     constexpr bool NX = (MS & PM_NOX) != 0;
     static_assert(!NX || (DEN && !RX && !WC), "the X-free pass is the denominator side of a CP pass");
     constexpr int CPS = KB / CH;  // chunks per slab (2 or 4)
-    static_assert(KB == 128 || (KB == 256 && !DEN && !S3 && !RX), "256-column blocks: KL, single TF32");
+    // 256-column blocks: single TF32, and either the KL CP passes or the explicit-rows W pass (no
+    // column contraction: its N3 / N3d tensor-memory columns are free)
+    static_assert(KB == 128 || (KB == 256 && !S3 && ((!DEN && !RX) || (RX && !M3))),
+                  "256-column blocks: single TF32, KL CP passes or the explicit-rows W pass");
     constexpr Layout L = make_layout(RW, M3, DEN, S3, KB);
     constexpr int NS = L.ns, NP = L.np, NK = L.nk, NR = L.nr;
     constexpr bool PAIR = M3 && NP == 4;  // column contraction on chunk pairs (N = 128)
@@ -1065,6 +1068,15 @@ cudaError_t launch_bk(const Cp3Plan &p, const Cp3Args &a, int ms, cudaStream_t s
         return cudaErrorInvalidValue;
     }
     if (a.rrow) {  // explicit rows (Tucker): W rows out, or the column contraction
+        if constexpr (!S3) {
+            if (p.KB == 256) {
+                switch (ms) {
+                    case PM_M1 | PM_M2: return launch_t<PM_M1 | PM_M2, BK, S3, true, 256>(p, a, s);
+                    case PM_M1 | PM_M2 | PM_OBJ: return launch_t<PM_M1 | PM_M2 | PM_OBJ, BK, S3, true, 256>(p, a, s);
+                    default: return cudaErrorInvalidValue;
+                }
+            }
+        }
         if (p.KB != KBLK) return cudaErrorInvalidValue;
         switch (ms) {
             case PM_M1 | PM_M2: return launch_t<PM_M1 | PM_M2, BK, S3, true>(p, a, s);

@@ -870,7 +870,8 @@ struct TuckerWs {
     // tensor-core passes (TF32 / 3xTF32 reconstruction, BF16 contractions): plan, W partials
     // per 128-column block [n_kb][I1*I2][RP], and the partial counts of the passes in use
     bool tc;
-    Cp3Plan tplan;
+    Cp3Plan tplan;   // rows pass (W, Wd): 256-column blocks with single TF32, else 128
+    Cp3Plan tplan3;  // mode-3 pass: 128-column blocks
     float *Wpn, *Wpd;
     int parts3, obj_n;
     float *cs;                // [RP] column sums (closed-form denominators at beta = 1)
@@ -1125,12 +1126,17 @@ int setup(ntf_ctx *ctx, const ntf_tensor *X, const int64_t *core_dims, bool jcom
     w.den = wsf(ctx, "tkDen", mx, ok);
     w.plan3 = cp3_plan(w.I1, w.I2, w.I3, w.RP, ctx_num_sms(ctx));
     if (w.tc) {
-        w.tplan = cp3_plan(w.I1, w.I2, w.I3, w.RP, ctx_num_sms(ctx), 128);
+        // the rows pass carries no column contraction, so with single TF32 operands its tensor
+        // memory and shared memory allow 256-column blocks: half as many W partials to add
+        const int kb_rows = o.precision == NTF_PREC_TF32 ? 256 : 128;
+        w.tplan = cp3_plan(w.I1, w.I2, w.I3, w.RP, ctx_num_sms(ctx), kb_rows);
         w.tplan.s3 = o.precision == NTF_PREC_3XTF32;
+        w.tplan3 = cp3_plan(w.I1, w.I2, w.I3, w.RP, ctx_num_sms(ctx), 128);
+        w.tplan3.s3 = w.tplan.s3;
         w.Wpn = wsf(ctx, "tkWpn", (int64_t)w.tplan.n_kb * IJ * w.RP, ok);
         w.Wpd = wsf(ctx, "tkWpd", (int64_t)w.tplan.n_kb * IJ * w.RP, ok);
     }
-    w.parts3 = w.coo ? 1 : w.tc ? w.tplan.parts3 : w.plan3.parts3;
+    w.parts3 = w.coo ? 1 : w.tc ? w.tplan3.parts3 : w.plan3.parts3;
     w.pn3 = wsf(ctx, "tkPn3", (int64_t)w.parts3 * w.I3 * w.RP, ok);
     w.pd3 = wsf(ctx, "tkPd3", (int64_t)w.parts3 * w.I3 * w.RP, ok);
     // the FP32 rows kernel's tile (fp32::Geo) and about one wave of its resident CTAs (two per SM
@@ -1142,7 +1148,7 @@ int setup(ntf_ctx *ctx, const ntf_tensor *X, const int64_t *core_dims, bool jcom
     w.rows_is = is;
     w.rows_grid = n_jt * is;
     w.obj_n = w.coo ? 1 : w.tc ? w.tplan.grid : w.rows_grid;
-    int gmax = std::max(std::max(w.rows_grid, w.plan3.grid), w.tc ? w.tplan.grid : 0);
+    int gmax = std::max(std::max(w.rows_grid, w.plan3.grid), w.tc ? std::max(w.tplan.grid, w.tplan3.grid) : 0);
     w.obj = (double *)ctx_ws(ctx, "tkObj", sizeof(double) * (size_t)gmax);
     if (!w.obj) ok = false;
     w.cs = wsf(ctx, "tkCs", 64, ok);
@@ -1265,14 +1271,14 @@ int mode3_pass(ntf_ctx *ctx, TuckerWs &w, const ntf_tensor *X, const ntf_opts &o
     a.drow = drow;
     for (int m = 0; m < 3; ++m) a.rec[m] = a.num[m] = a.den[m] = a3rec;
     if (w.tc) {
-        a.n_jt = w.tplan.n_jt;
-        a.n_kb = w.tplan.n_kb;
-        a.n_is = w.tplan.n_is;
+        a.n_jt = w.tplan3.n_jt;
+        a.n_kb = w.tplan3.n_kb;
+        a.n_is = w.tplan3.n_is;
         a.p3n = w.pn3;
         a.p3d = w.pd3;
         ctx_wait_opts(ctx, a);
         const bool kl = beta_kind(beta) == BK_KL;
-        TK(cp3_tc_launch(w.tplan, a, PM_M3, kl ? 0 : 1, st));
+        TK(cp3_tc_launch(w.tplan3, a, PM_M3, kl ? 0 : 1, st));
         if (kl) {
             // Q = 1: Den3[k][c] = sum over the rows of drow, the same for every k (first part;
             // the other parts zero)

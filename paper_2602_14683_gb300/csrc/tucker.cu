@@ -648,6 +648,23 @@ __global__ void sum_parts_kernel(const float *parts, int n_parts, int64_t n, flo
     out[t] = acc;
 }
 
+// The same sum, four consecutive elements per thread (n4 = n / 4 float4 groups, 16-byte
+// aligned arrays); blockIdx.y picks one of two independent sums (W and Wd in one launch).
+__global__ void sum_parts4_kernel(const float *pa, float *oa, const float *pb, float *ob, int n_parts, int64_t n4) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n4) return;
+    const float4 *parts = reinterpret_cast<const float4 *>(blockIdx.y ? pb : pa);
+    float4 acc = parts[t];
+    for (int p = 1; p < n_parts; ++p) {
+        const float4 v = parts[(int64_t)p * n4 + t];
+        acc.x += v.x;
+        acc.y += v.y;
+        acc.z += v.z;
+        acc.w += v.w;
+    }
+    reinterpret_cast<float4 *>(blockIdx.y ? ob : oa)[t] = acc;
+}
+
 // Extrapolation of one flat block (Section "Going beyond: Majorization-Minimization with
 // Extrapolation"): D = [A - Aprev]_+ and FP64 partial sums of D^2 per CTA, Aprev <- A; then
 // E = max(A + alpha D, eps), alpha = min(alpha_nes, cap / (||D||_F + delta)), every CTA
@@ -872,6 +889,10 @@ struct TuckerWs {
     bool tc;
     Cp3Plan tplan;   // rows pass (W, Wd): 256-column blocks with single TF32, else 128
     Cp3Plan tplan3;  // mode-3 pass: 128-column blocks
+    // the passes' view of X as tI slabs of tJ rows: with explicit rows only the row index
+    // i I2 + j matters, so when 128 divides I1 I2 the rows are cut into slabs of exactly 128
+    // (no ragged row tile); otherwise (I1, I2)
+    int tI, tJ;
     float *Wpn, *Wpd;
     int parts3, obj_n;
     float *cs;                // [RP] column sums (closed-form denominators at beta = 1)
@@ -1000,6 +1021,8 @@ int rows_pass(ntf_ctx *ctx, TuckerWs &w, const ntf_tensor *X, const ntf_opts &o,
     }
     if (w.tc) {
         Cp3Args a = base_args(X, w, o, beta);
+        a.I = w.tI;
+        a.J = w.tJ;
         a.rrow = rrow;
         a.rec[2] = a3rec;
         a.num[2] = n3;
@@ -1014,10 +1037,11 @@ int rows_pass(ntf_ctx *ctx, TuckerWs &w, const ntf_tensor *X, const ntf_opts &o,
         ctx_wait_opts(ctx, a);
         const bool kl = beta_kind(beta) == BK_KL;
         TK(cp3_tc_launch(w.tplan, a, PM_M1 | PM_M2 | (obj ? PM_OBJ : 0), kl ? 0 : 1, st));
-        // W = sum over the column blocks, in block order
+        // W (and Wd) = sum over the column blocks, in block order
         const int64_t n = (int64_t)w.I1 * w.I2 * w.RP;
         if (!one) {
-            sum_parts_kernel<<<nblk(n), 256, 0, st>>>(w.Wpn, w.tplan.n_kb, n, w.Wn);
+            const dim3 grid(nblk(n / 4), kl ? 1 : 2);
+            sum_parts4_kernel<<<grid, 256, 0, st>>>(w.Wpn, w.Wn, w.Wpd, w.Wd, w.tplan.n_kb, n / 4);
             TK(cudaGetLastError());
         }
         if (kl) {
@@ -1025,9 +1049,6 @@ int rows_pass(ntf_ctx *ctx, TuckerWs &w, const ntf_tensor *X, const ntf_opts &o,
             int rc = colsum_rows(ctx, w, d3, w.I3, st);
             if (rc) return rc;
             bcast_rows_kernel<<<nblk(n), 256, 0, st>>>(w.cs, (int64_t)w.I1 * w.I2, w.RP, 1, w.Wd);
-            TK(cudaGetLastError());
-        } else if (!one) {
-            sum_parts_kernel<<<nblk(n), 256, 0, st>>>(w.Wpd, w.tplan.n_kb, n, w.Wd);
             TK(cudaGetLastError());
         }
         return NTF_OK;
@@ -1045,9 +1066,11 @@ int rows_pass(ntf_ctx *ctx, TuckerWs &w, const ntf_tensor *X, const ntf_opts &o,
     return NTF_OK;
 }
 
-// Num1 / Num2 / Pcore from W with the (possibly transformed) blocks b
+// Num1 / Num2 / Pcore from W with the (possibly transformed) blocks b; with same_blocks the
+// W-free factor (H of block 1, GA1 of block 2) of the previous call, made from the same b, is
+// reused
 int contract_from_w(ntf_ctx *ctx, TuckerWs &w, int block, const Blocks &b, const float *W, float *out,
-                    cudaStream_t st) {
+                    cudaStream_t st, bool same_blocks = false) {
     if (block == 0) {  // core: Y[i][b][c] = sum_j A2[j,b] W[i,j,c]; Pcore = sum_i A1[i,a] Y[i]
         Gemm g{};
         g.A = b.A2; g.B = W; g.C = w.Y;
@@ -1069,7 +1092,7 @@ int contract_from_w(ntf_ctx *ctx, TuckerWs &w, int block, const Blocks &b, const
         g.sam = w.J2; g.sak1 = 1;
         g.sbb = (int64_t)w.J2 * w.J3; g.sbk1 = w.J3; g.sbn = 1;
         g.scb = w.J3; g.scm = (int64_t)w.J1 * w.J3; g.scn = 1;
-        { const int rc_ = gemm(ctx, g, st, w.gemm_mode, w.gemm_tune); if (rc_) return rc_; }
+        if (!same_blocks) { const int rc_ = gemm(ctx, g, st, w.gemm_mode, w.gemm_tune); if (rc_) return rc_; }
         Gemm h{};
         h.A = W; h.B = w.H; h.C = out;
         h.M = w.I1; h.N = w.J1; h.K1 = w.I2; h.K2 = w.J3; h.batch = 1;
@@ -1082,7 +1105,7 @@ int contract_from_w(ntf_ctx *ctx, TuckerWs &w, int block, const Blocks &b, const
         g.A = b.A1; g.B = b.G; g.C = w.GA1;
         g.M = w.I1; g.N = w.J2 * w.J3; g.K1 = w.J1; g.K2 = 1; g.batch = 1;
         g.sam = w.J1; g.sak1 = 1; g.sbk1 = (int64_t)w.J2 * w.J3; g.sbn = 1; g.scm = (int64_t)w.J2 * w.J3; g.scn = 1;
-        { const int rc_ = gemm(ctx, g, st, w.gemm_mode, w.gemm_tune); if (rc_) return rc_; }
+        if (!same_blocks) { const int rc_ = gemm(ctx, g, st, w.gemm_mode, w.gemm_tune); if (rc_) return rc_; }
         Gemm h{};
         h.A = W; h.B = w.GA1; h.C = out;
         h.M = w.I2; h.N = w.J2; h.K1 = w.I1; h.K2 = w.J3; h.batch = 1;
@@ -1129,9 +1152,13 @@ int setup(ntf_ctx *ctx, const ntf_tensor *X, const int64_t *core_dims, bool jcom
         // the rows pass carries no column contraction, so with single TF32 operands its tensor
         // memory and shared memory allow 256-column blocks: half as many W partials to add
         const int kb_rows = o.precision == NTF_PREC_TF32 ? 256 : 128;
-        w.tplan = cp3_plan(w.I1, w.I2, w.I3, w.RP, ctx_num_sms(ctx), kb_rows);
+        const int TR = 128;  // row tile of the tensor-core passes
+        const bool flat = IJ % TR == 0;
+        w.tI = flat ? (int)(IJ / TR) : w.I1;
+        w.tJ = flat ? TR : w.I2;
+        w.tplan = cp3_plan(w.tI, w.tJ, w.I3, w.RP, ctx_num_sms(ctx), kb_rows);
         w.tplan.s3 = o.precision == NTF_PREC_3XTF32;
-        w.tplan3 = cp3_plan(w.I1, w.I2, w.I3, w.RP, ctx_num_sms(ctx), 128);
+        w.tplan3 = cp3_plan(w.tI, w.tJ, w.I3, w.RP, ctx_num_sms(ctx), 128);
         w.tplan3.s3 = w.tplan.s3;
         w.Wpn = wsf(ctx, "tkWpn", (int64_t)w.tplan.n_kb * IJ * w.RP, ok);
         w.Wpd = wsf(ctx, "tkWpd", (int64_t)w.tplan.n_kb * IJ * w.RP, ok);
@@ -1271,6 +1298,8 @@ int mode3_pass(ntf_ctx *ctx, TuckerWs &w, const ntf_tensor *X, const ntf_opts &o
     a.drow = drow;
     for (int m = 0; m < 3; ++m) a.rec[m] = a.num[m] = a.den[m] = a3rec;
     if (w.tc) {
+        a.I = w.tI;
+        a.J = w.tJ;
         a.n_jt = w.tplan3.n_jt;
         a.n_kb = w.tplan3.n_kb;
         a.n_is = w.tplan3.n_is;
@@ -1378,7 +1407,7 @@ int tucker_run(ntf_ctx *ctx, const ntf_tensor *X, float beta, const int64_t *cor
             if ((rc = build_b3(ctx, w, w.cur, w.Brec, st))) return rc;
             if ((rc = rows_pass(ctx, w, X, o, beta, w.Brec, w.cur.A3p, w.cur.A3p, w.cur.A3p, false, st))) return rc;
             if ((rc = contract_from_w(ctx, w, blk, w.cur, w.Wn, w.num, st))) return rc;
-            if ((rc = contract_from_w(ctx, w, blk, w.cur, w.Wd, w.den, st))) return rc;
+            if ((rc = contract_from_w(ctx, w, blk, w.cur, w.Wd, w.den, st, /*same_blocks=*/true))) return rc;
             float *A = blk == 1 ? w.cur.A1 : w.cur.A2;
             if ((rc = apply_mu(ctx, w, A, A, blk == 1 ? n1 : n2, beta, eps, nullptr, nullptr, nullptr, st))) return rc;
         }
@@ -1541,7 +1570,7 @@ int tucker_run_extrap(ntf_ctx *ctx, const ntf_tensor *X, float beta, const int64
         if ((rc = build_b3(ctx, w, b, w.Brec, st))) return rc;
         if ((rc = rows_pass(ctx, w, X, o, beta, w.Brec, w.cur.A3p, w.cur.A3p, w.cur.A3p, false, st))) return rc;
         if ((rc = contract_from_w(ctx, w, blk, w.cur, w.Wn, w.num, st))) return rc;
-        if ((rc = contract_from_w(ctx, w, blk, w.cur, w.Wd, w.den, st))) return rc;
+        if ((rc = contract_from_w(ctx, w, blk, w.cur, w.Wd, w.den, st, /*same_blocks=*/true))) return rc;
         if ((rc = apply_mu(ctx, w, Ah, A, blk == 1 ? n1 : n2, beta, eps, nullptr, nullptr, nullptr, st))) return rc;
     }
     // mode 3: extrapolated on the unpadded block, then padded
@@ -1804,7 +1833,7 @@ int tucker_nway_run(ntf_ctx *ctx, const ntf_tensor *X, float beta, const int64_t
                 if ((rc = rows_pass(ctx, w, &t.X3, o, beta, w.Brec, w.cur.A3p, w.cur.A3p, w.cur.A3p, false, st)))
                     return rc;
                 if ((rc = contract_from_w(ctx, w, v + 1, w.cur, w.Wn, w.num, st))) return rc;
-                if ((rc = contract_from_w(ctx, w, v + 1, w.cur, w.Wd, w.den, st))) return rc;
+                if ((rc = contract_from_w(ctx, w, v + 1, w.cur, w.Wd, w.den, st, /*same_blocks=*/true))) return rc;
                 if (single) {
                     float *A = slot(w.cur, v);
                     if ((rc = apply_mu(ctx, w, A, A, (int64_t)t.I[n] * t.J[n], beta, eps, nullptr, nullptr, nullptr,

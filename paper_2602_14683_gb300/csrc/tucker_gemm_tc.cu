@@ -9,8 +9,10 @@
 //     128-byte-swizzled K-major tiles (one 128-byte row per m or n) of a two-stage ring in shared
 //     memory.  An operand whose rows are contiguous (unit m or n stride) is read with consecutive
 //     lanes on consecutive rows, any other with consecutive lanes on consecutive reduction
-//     indices, so that a warp's load touches as few lines as the layout allows; the loads of
-//     chunk c + 1 are issued into registers before chunk c's MMAs;
+//     indices (on 32-column tiles, four consecutive indices per lane with 16-byte loads and
+//     shared stores when the layout is aligned for it), so that a warp's load touches as few
+//     lines as the layout allows; the loads of chunk c + 1 are issued into registers before
+//     chunk c's MMAs;
 //   * thread 0 issues the chunk's tcgen05.mma.kind::tf32 (M 128, N NTT, K 8 four times; with the
 //     split hi*hi + hi*lo + lo*hi) into one TMEM accumulator and commits to the stage's mbarrier,
 //     which the threads wait on before they refill that stage two chunks later;
@@ -52,7 +54,8 @@ struct Geo {
 // index kk) = base[r srow + k1 sk1 + k2 sk2] with k0 + kk = k1 K2 + k2, zero outside rows < nrow or
 // indices < kend.  Each thread holds NR / 4 elements: with unit row stride (rowmode) thread t takes
 // row t % NR (consecutive lanes, consecutive rows) and a run of consecutive indices; otherwise its
-// lane is the index and the warps take rows in turn.  load_tile issues the global loads into
+// lane is the index and the warps take rows in turn (mode 0), or (mode 2) each group of eight
+// lanes takes one row, four consecutive indices per lane.  load_tile issues the global loads into
 // registers (a chunk ahead of its use), store_tile rounds them to TF32 and writes the swizzled
 // K-major tiles hi (and lo).
 template <int NR>
@@ -73,11 +76,29 @@ __device__ __forceinline__ int64_t row_off(int row, int64_t srow, int nin, int64
     return (int64_t)row * srow;
 }
 
-template <int NR>
-__device__ __forceinline__ void load_tile(float (&v)[NR / 4], bool rowmode, const float *base, int row0, int64_t srow,
+template <int NR, bool V>
+__device__ __forceinline__ void load_tile(float (&v)[NR / 4], int mode, const float *base, int row0, int64_t srow,
                                           int nin, int64_t sblk, int64_t sk1, int64_t sk2, int K2, int k0, int kend,
                                           int nrow, int t) {
     using T = TileMap<NR>;
+    if (V && mode == 2) {  // eight lanes per row, four consecutive indices each, four rows per warp load
+        const int lane = t & 31, warp = t >> 5;
+        const int k = k0 + 4 * (lane & 7);
+        const bool kv = k < kend;
+        const int64_t ko = kv ? (K2 == 1 ? (int64_t)k * sk1 : (int64_t)(k / K2) * sk1 + (int64_t)(k % K2) * sk2) : 0;
+#pragma unroll
+        for (int s = 0; s < NR / 16; ++s) {
+            const int r = 16 * s + 4 * warp + (lane >> 3);
+            float4 x = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            if (kv && r < nrow) x = __ldg(reinterpret_cast<const float4 *>(base + row_off(row0 + r, srow, nin, sblk) + ko));
+            v[4 * s] = x.x;
+            v[4 * s + 1] = x.y;
+            v[4 * s + 2] = x.z;
+            v[4 * s + 3] = x.w;
+        }
+        return;
+    }
+    const bool rowmode = mode == 1;
     if (rowmode) {
 #pragma unroll
         for (int p = 0; p < T::RPT; ++p) {
@@ -113,9 +134,27 @@ __device__ __forceinline__ void load_tile(float (&v)[NR / 4], bool rowmode, cons
     }
 }
 
-template <int NR, bool S3>
-__device__ __forceinline__ void store_tile(const float (&v)[NR / 4], bool rowmode, float *hi, float *lo, int t) {
+template <int NR, bool S3, bool V>
+__device__ __forceinline__ void store_tile(const float (&v)[NR / 4], int mode, float *hi, float *lo, int t) {
     using T = TileMap<NR>;
+    if (V && mode == 2) {
+        const int lane = t & 31, warp = t >> 5;
+        const int kk = 4 * (lane & 7);
+#pragma unroll
+        for (int s = 0; s < NR / 16; ++s) {
+            const int r = 16 * s + 4 * warp + (lane >> 3);
+            float h[4], l[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                h[e] = tf32_rna(v[4 * s + e]);
+                l[e] = S3 ? tf32_rna(v[4 * s + e] - h[e]) : 0.0f;
+            }
+            *reinterpret_cast<float4 *>(hi + swf(r, kk)) = make_float4(h[0], h[1], h[2], h[3]);
+            if (S3) *reinterpret_cast<float4 *>(lo + swf(r, kk)) = make_float4(l[0], l[1], l[2], l[3]);
+        }
+        return;
+    }
+    const bool rowmode = mode == 1;
     if (rowmode) {
 #pragma unroll
         for (int p = 0; p < T::RPT; ++p) {
@@ -140,7 +179,7 @@ __device__ __forceinline__ void store_tile(const float (&v)[NR / 4], bool rowmod
     }
 }
 
-template <int NTT, bool S3>
+template <int NTT, bool S3, bool V>
 __global__ void __launch_bounds__(NTH, 1) gemm_tc_kernel(const Gemm g) {
     using G = Geo<NTT, S3>;
     extern __shared__ uint8_t smraw[];
@@ -174,11 +213,14 @@ __global__ void __launch_bounds__(NTH, 1) gemm_tc_kernel(const Gemm g) {
     const int64_t abase = (int64_t)bt * g.sab, bbase = (int64_t)bt * g.sbb;
 
     const float *Abase = g.A + abase, *Bbase = g.B + bbase;
-    const bool arow = g.sam == 1, brow = g.sbn == 1;
+    // operand modes: rows contiguous (1); else one index per lane (0), or with V (the launcher has
+    // checked the alignment) runs of four indices per lane (2)
+    const int arow = g.sam == 1 ? 1 : V ? 2 : 0;
+    const int brow = g.sbn == 1 ? 1 : V ? 2 : 0;
     float va[32], vb[NTT / 4];  // the next chunk's operands, loaded a chunk ahead
     if (nch > 0) {
-        load_tile<128>(va, arow, Abase, m0, g.sam, 0, 0, g.sak1, g.sak2, g.K2, kbeg, kend, g.M - m0, t);
-        load_tile<NTT>(vb, brow, Bbase, n0, g.sbn, g.nin, g.sbb, g.sbk1, g.sbk2, g.K2, kbeg, kend, g.N - n0, t);
+        load_tile<128, V>(va, arow, Abase, m0, g.sam, 0, 0, g.sak1, g.sak2, g.K2, kbeg, kend, g.M - m0, t);
+        load_tile<NTT, V>(vb, brow, Bbase, n0, g.sbn, g.nin, g.sbb, g.sbk1, g.sbk2, g.K2, kbeg, kend, g.N - n0, t);
     }
     for (int c = 0; c < nch; ++c) {
         const int s = c & 1;
@@ -188,12 +230,12 @@ __global__ void __launch_bounds__(NTH, 1) gemm_tc_kernel(const Gemm g) {
         float *Bl = reinterpret_cast<float *>(st + 2 * G::ABYTES + G::BBYTES);
         // the MMAs of chunk c - 2 read this stage
         if (c >= 2 && !mbar_wait(su32(bars + s), ((c - 2) >> 1) & 1)) *abort_flag = 1;
-        store_tile<128, S3>(va, arow, Ah, Al, t);
-        store_tile<NTT, S3>(vb, brow, Bh, Bl, t);
+        store_tile<128, S3, V>(va, arow, Ah, Al, t);
+        store_tile<NTT, S3, V>(vb, brow, Bh, Bl, t);
         if (c + 1 < nch) {  // in flight while this chunk is handed to the tensor cores
             const int k0 = kbeg + (c + 1) * KC;
-            load_tile<128>(va, arow, Abase, m0, g.sam, 0, 0, g.sak1, g.sak2, g.K2, k0, kend, g.M - m0, t);
-            load_tile<NTT>(vb, brow, Bbase, n0, g.sbn, g.nin, g.sbb, g.sbk1, g.sbk2, g.K2, k0, kend, g.N - n0, t);
+            load_tile<128, V>(va, arow, Abase, m0, g.sam, 0, 0, g.sak1, g.sak2, g.K2, k0, kend, g.M - m0, t);
+            load_tile<NTT, V>(vb, brow, Bbase, n0, g.sbn, g.nin, g.sbb, g.sbk1, g.sbk2, g.K2, k0, kend, g.N - n0, t);
         }
         fence_async_smem();
         fence_before();
@@ -273,10 +315,10 @@ __global__ void __launch_bounds__(NTH, 1) gemm_tc_kernel(const Gemm g) {
     }
 }
 
-template <int NTT, bool S3>
+template <int NTT, bool S3, bool V = false>
 cudaError_t launch_t(const Gemm &g, cudaStream_t s) {
     using G = Geo<NTT, S3>;
-    auto k = gemm_tc_kernel<NTT, S3>;
+    auto k = gemm_tc_kernel<NTT, S3, V>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
     if (e != cudaSuccess) return e;
     const dim3 grid((unsigned)((g.N + NTT - 1) / NTT), (unsigned)((g.M + 127) / 128), (unsigned)(g.batch * g.splits));
@@ -284,10 +326,29 @@ cudaError_t launch_t(const Gemm &g, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// Runs of four reduction indices per lane (16-byte loads and shared stores) for an operand whose
+// rows are not contiguous: the runs, the row, batch and fold offsets and the base all 16-byte
+// aligned, K % 4 == 0 (a run is then either inside the range or past its end).  Operands with
+// contiguous rows keep their own mapping.
+static bool vec_ok(const float *p, int64_t sbat, int64_t srow, int nin, int64_t sblk, int64_t sk1, int64_t sk2,
+                   int K2, int K) {
+    if (srow == 1) return true;
+    const bool runs = (K2 == 1 && sk1 == 1) || (sk2 == 1 && K2 % 4 == 0 && sk1 % 4 == 0);
+    return runs && K % 4 == 0 && srow % 4 == 0 && sbat % 4 == 0 && (nin == 0 || sblk % 4 == 0) &&
+           (reinterpret_cast<uintptr_t>(p) & 15) == 0;
+}
+
 }  // namespace tgemm
 
 cudaError_t gemm_tc_launch(const Gemm &g, bool s3, int ntt, cudaStream_t s) {
     if (g.M < 1 || g.N < 1 || g.batch < 1 || g.splits < 1 || g.kchunks < 1) return cudaErrorInvalidValue;
+    const int K = g.K1 * g.K2;
+    // the 16-byte form only for 32-column tiles (the long-reduction factor contractions): in the
+    // wider tiles its extra registers cost a resident CTA per SM
+    const bool v = ntt == 32 && (g.sam != 1 || g.sbn != 1) &&
+                   tgemm::vec_ok(g.A, g.sab, g.sam, 0, 0, g.sak1, g.sak2, g.K2, K) &&
+                   tgemm::vec_ok(g.B, g.sbb, g.sbn, g.nin, g.sbb, g.sbk1, g.sbk2, g.K2, K);
+    if (v) return s3 ? tgemm::launch_t<32, true, true>(g, s) : tgemm::launch_t<32, false, true>(g, s);
     switch (ntt) {
         case 32: return s3 ? tgemm::launch_t<32, true>(g, s) : tgemm::launch_t<32, false>(g, s);
         case 64: return s3 ? tgemm::launch_t<64, true>(g, s) : tgemm::launch_t<64, false>(g, s);

@@ -8,7 +8,8 @@ that of the CP tensor-core pass (TF32 or split-TF32 reconstruction from the rows
 partial tensor B^(3), BF16 contraction operands, FP32 accumulation, FP32 powers, FP64
 objective sum), so the same bars apply: 1e-3 per block after one sweep and 2e-4 on the
 objective (the derivation is in test_gpu_tc.py).  Shapes span several 128-row tiles and
-128-column blocks with ragged tails.
+128-column blocks with ragged tails.  When 128 divides I1 I2 the passes cut the rows i I2 + j into
+slabs of exactly 128 that straddle the i boundaries (the third case: I2 = 96 < 128, I1 I2 = 9 x 128).
 """
 import numpy as np
 import pytest
@@ -21,7 +22,7 @@ pytestmark = pytest.mark.gpu
 TOL_TC = 1e-3
 TOL_TC_OBJ = 2e-4
 
-CASES = [((6, 140, 132), (3, 4, 20)), ((5, 131, 264), (4, 3, 32))]
+CASES = [((6, 140, 132), (3, 4, 20)), ((5, 131, 264), (4, 3, 32)), ((12, 96, 200), (4, 5, 28))]
 
 
 def _ntf():
@@ -54,17 +55,17 @@ def test_tucker_tc_sweep_parity(beta, case, prec):
 
 @pytest.mark.parametrize("prec", ["tf32", "3xtf32"])
 @pytest.mark.parametrize("beta", [0.5, 1.0, 1.5])
-@pytest.mark.parametrize("L", [1, 2])
-def test_tucker_tc_jcomm_parity(beta, L, prec):
+@pytest.mark.parametrize("L,case", [(1, 1), (2, 1), (2, 2)])
+def test_tucker_tc_jcomm_parity(beta, L, case, prec):
     ntf = _ntf()
-    dims, J = CASES[1]
+    dims, J = CASES[case]
     X, _, _ = synth.tucker_dense(dims, J, seed=40)
     G0, A0 = synth.init_tucker(dims, J, seed=41)
     Gw, Aw, Fw = oracle.tucker_jcomm_outer(X, G0, A0, beta, L=L)
     Gd, Ad, obj = dev(G0), [dev(a) for a in A0], obj_tensor()
     ntf.jcomm_outer(dev(X), beta, Ad, core=Gd, objective=obj, inner_L=L, precision=prec)
     ntf.default_context().device_status()
-    _check(Gd, Ad, Gw, Aw, obj, Fw, "tucker tc %s jcomm beta=%g L=%d" % (prec, beta, L))
+    _check(Gd, Ad, Gw, Aw, obj, Fw, "tucker tc %s jcomm beta=%g L=%d %s" % (prec, beta, L, dims))
 
 
 @pytest.mark.parametrize("prec", ["tf32", "3xtf32"])

@@ -17,7 +17,8 @@ void ctx_wait_opts(ntf_ctx *c, Cp3Args &a);  // status word, wait limit and time
 //   A(bt, m, k1, k2) = A[bt sab + m sam + k1 sak1 + k2 sak2], B(bt, k1, k2, n) = B[bt sbb + k1 sbk1 +
 //   k2 sbk2 + n sbn], C at bt scb + m scm + n scn.
 // The reduction index k = k1 K2 + k2 may be cut into `splits` contiguous ranges of `kchunks`
-// chunks each; every range's sum then goes to `part` and the ranges are added in order (FP64).
+// chunks each; every range's sum then goes to `part` and the ranges are added in order (FP64 for
+// the CUDA-core form, FP32 for the tensor-core one).
 struct Gemm {
     const float *A, *B;
     float *C;
@@ -31,6 +32,9 @@ struct Gemm {
     int nin;              // > 0: the batch is folded into n (A shared by all batches, sab = 0): N counts
                           // batch x nin columns, column b nin + n stands for (batch b, column n), and
                           // batch is 1; B and C then step by sbb / scb from one batch block to the next
+    int mfold;            // > 0 (tensor-core form only, 32-column tiles, scm = 1, nin = 0): row m of A and C
+    int64_t samb, scmb;   // is (m / mfold) samb + (m % mfold) sam and (m / mfold) scmb + (m % mfold) scm (a
+                          // second index folded into the rows); the range partials are then [splits][n][m]
 };
 // Tensor-core form of the same product (tucker_gemm_tc.cu): tcgen05 kind::tf32 MMAs on operands
 // rounded to TF32 (s3: split into high and low TF32 parts, three products, about FP32 accuracy),

@@ -203,43 +203,67 @@ __global__ void __launch_bounds__(256) gemm2k_kernel(const Gemm g) {
 // the ranges in range order (loads eight at a time), and the four quarter sums are added in
 // quarter order; in FP64 for the FP32 GEMM (its accuracy carry), in FP32 for the tensor-core one
 // (TF32 operands; a few ranges, and the GB300 FP64 pipe, conversions included, is slow).  With the
-// batch folded into the columns (g.nin > 0), column b nin + n goes to batch block b of C.
+// batch folded into the columns (g.nin > 0), column b nin + n goes to batch block b of C; with a
+// second index folded into the rows (g.mfold > 0) the partials are [n][m].  A bounded grid strides
+// over the outputs (eight per warp and step, warp-uniform loop).
 template <typename T>
 __global__ void gemm_split_sum_kernel(const Gemm g) {
-    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t t = gt >> 2;
-    const int qid = (int)(gt & 3);
-    const int64_t mn = (int64_t)g.M * g.N, total = mn * g.batch;
+    const int64_t total = (int64_t)g.M * g.N * g.batch;
+    const int qid = threadIdx.x & 3;
+    const int64_t step = ((int64_t)gridDim.x * blockDim.x) >> 2;
     const int per = (g.splits + 3) / 4, s0 = qid * per, s1 = min(g.splits, s0 + per);
-    T v = 0;
-    if (t < total) {
-        for (int sp0 = s0; sp0 < s1; sp0 += 8) {
-            float x[8];
+    const int64_t first = ((int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) >> 2;  // the warp's first output
+    for (int64_t w0 = first; w0 < total; w0 += step) {
+        const int64_t t = w0 + ((threadIdx.x & 31) >> 2);
+        const bool live = t < total;
+        T v = 0;
+        if (live) {
+            for (int sp0 = s0; sp0 < s1; sp0 += 8) {
+                float x[8];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) x[q] = sp0 + q < s1 ? g.part[(int64_t)(sp0 + q) * total + t] : 0.0f;
+                for (int q = 0; q < 8; ++q) x[q] = sp0 + q < s1 ? g.part[(int64_t)(sp0 + q) * total + t] : 0.0f;
 #pragma unroll
-            for (int q = 0; q < 8; ++q)
-                if (sp0 + q < s1) v += (T)x[q];
+                for (int q = 0; q < 8; ++q)
+                    if (sp0 + q < s1) v += (T)x[q];
+            }
         }
+        const T v1 = __shfl_down_sync(0xffffffffu, v, 1), v2 = __shfl_down_sync(0xffffffffu, v, 2),
+                v3 = __shfl_down_sync(0xffffffffu, v, 3);
+        if (qid != 0 || !live) continue;
+        const T tot = ((v + v1) + v2) + v3;
+        // output t: [batch][M][N] order, or [batch][N][M] for the row-folded form (its partials'
+        // order, m contiguous in C)
+        const int inner = g.mfold > 0 ? g.M : g.N, outer = g.mfold > 0 ? g.N : g.M;
+        int64_t q;
+        int r;
+        if (total < (1ll << 31)) {  // 32-bit index arithmetic
+            q = (int)t / inner;
+            r = (int)t - (int)q * inner;
+        } else {
+            q = t / inner;
+            r = (int)(t - q * inner);
+        }
+        const int bt = (int)(q / outer), o = (int)(q - (int64_t)bt * outer);
+        const int m = g.mfold > 0 ? r : o, n = g.mfold > 0 ? o : r;
+        int64_t mo = (int64_t)m * g.scm;  // row m's offset (second index folded into the rows: mfold > 0)
+        if (g.mfold > 0) {
+            const int f = m / g.mfold;
+            mo = (int64_t)f * g.scmb + (int64_t)(m - f * g.mfold) * g.scm;
+        }
+        int64_t c;
+        if (g.nin > 0) {
+            const int b = n / g.nin;
+            c = mo + (int64_t)b * g.scb + (int64_t)(n - b * g.nin) * g.scn;
+        } else {
+            c = (int64_t)bt * g.scb + mo + (int64_t)n * g.scn;
+        }
+        g.C[c] = (float)tot;
     }
-    const T v1 = __shfl_down_sync(0xffffffffu, v, 1), v2 = __shfl_down_sync(0xffffffffu, v, 2),
-            v3 = __shfl_down_sync(0xffffffffu, v, 3);
-    if (qid != 0 || t >= total) return;
-    const T tot = ((v + v1) + v2) + v3;
-    const int bt = (int)(t / mn), m = (int)((t % mn) / g.N), n = (int)(t % g.N);
-    int64_t c;
-    if (g.nin > 0) {
-        const int b = n / g.nin;
-        c = (int64_t)m * g.scm + (int64_t)b * g.scb + (int64_t)(n - b * g.nin) * g.scn;
-    } else {
-        c = (int64_t)bt * g.scb + (int64_t)m * g.scm + (int64_t)n * g.scn;
-    }
-    g.C[c] = (float)tot;
 }
 
-static cudaError_t split_sum(const Gemm &g, cudaStream_t s, bool fp64) {
+static cudaError_t split_sum(const Gemm &g, cudaStream_t s, bool fp64, int sms) {
     const int64_t total = (int64_t)g.M * g.N * g.batch;
-    const unsigned blocks = (unsigned)((4 * total + 255) / 256);
+    const unsigned blocks = (unsigned)std::min<int64_t>((4 * total + 255) / 256, 8 * (int64_t)sms);
     if (fp64) gemm_split_sum_kernel<double><<<blocks, 256, 0, s>>>(g);
     else gemm_split_sum_kernel<float><<<blocks, 256, 0, s>>>(g);
     return cudaGetLastError();
@@ -248,23 +272,24 @@ static cudaError_t split_sum(const Gemm &g, cudaStream_t s, bool fp64) {
 // Tensor-core plans timed by the autotuner: process-wide, keyed by device, shape, strides and
 // arithmetic; the value is (tile width, reduction ranges).
 struct GemmKey {
-    int dev, M, N, K1, K2, batch, mode;
-    int64_t sab, sam, sak1, sak2, sbb, sbk1, sbk2, sbn;
+    int dev, M, N, K1, K2, batch, mode, mfold;
+    int64_t sab, sam, samb, sak1, sak2, sbb, sbk1, sbk2, sbn;
     bool operator<(const GemmKey &o) const {
-        return std::tie(dev, M, N, K1, K2, batch, mode, sab, sam, sak1, sak2, sbb, sbk1, sbk2, sbn) <
-               std::tie(o.dev, o.M, o.N, o.K1, o.K2, o.batch, o.mode, o.sab, o.sam, o.sak1, o.sak2, o.sbb, o.sbk1,
-                        o.sbk2, o.sbn);
+        return std::tie(dev, M, N, K1, K2, batch, mode, mfold, sab, sam, samb, sak1, sak2, sbb, sbk1, sbk2, sbn) <
+               std::tie(o.dev, o.M, o.N, o.K1, o.K2, o.batch, o.mode, o.mfold, o.sab, o.sam, o.samb, o.sak1, o.sak2,
+                        o.sbb, o.sbk1, o.sbk2, o.sbn);
     }
 };
 std::mutex g_gemm_mu;
 std::map<GemmKey, std::pair<int, int>> g_gemm_tuned;
 
-// reduction ranges for a tile width: enough CTAs for about two per SM, at least two chunks each
+// reduction ranges for a tile width: up to about two CTAs per SM (rounded down, so that the
+// CTAs fit one wave), at least two chunks each
 static int tc_splits(const Gemm &f, int w, int sms) {
     const int nchunks = std::max(1, (f.K1 * f.K2 + 31) / 32);
     const int64_t want = 2 * (int64_t)sms;
     const int64_t tiles = (int64_t)((f.N + w - 1) / w) * ((f.M + 127) / 128) * f.batch;
-    return (int)std::max<int64_t>(1, std::min<int64_t>((want + tiles - 1) / tiles, nchunks / 2));
+    return (int)std::max<int64_t>(1, std::min<int64_t>(want / tiles, nchunks / 2));
 }
 
 // One tensor-core product with the given plan (launch, and the range sum when split).
@@ -280,7 +305,7 @@ static int gemm_tc_run(ntf_ctx *ctx, Gemm f, int ntt, int splits, int mode, cuda
     }
     cudaError_t e = gemm_tc_launch(f, mode == 2, ntt, s);
     if (e == cudaSuccess && f.splits > 1) {
-        e = split_sum(f, s, false);
+        e = split_sum(f, s, false, ctx_num_sms(ctx));
         ctx_count(ctx, 1);
     }
     if (e != cudaSuccess) return ctx_fail(ctx, NTF_ERR_CUDA, cudaGetErrorString(e));
@@ -321,8 +346,8 @@ static int gemm(ntf_ctx *ctx, Gemm g, cudaStream_t s, int mode = 0, bool tune = 
         if (tune) {
             int dev = 0;
             cudaGetDevice(&dev);
-            const GemmKey key{dev, f.M, f.N, f.K1, f.K2, f.batch, mode, f.sab, f.sam, f.sak1, f.sak2, f.sbb, f.sbk1,
-                              f.sbk2, f.sbn};
+            const GemmKey key{dev,   f.M,   f.N,    f.K1,  f.K2,  f.batch, mode,  f.mfold, f.sab,
+                              f.sam, f.samb, f.sak1, f.sak2, f.sbb, f.sbk1,  f.sbk2, f.sbn};
             bool found = false;
             {
                 std::lock_guard<std::mutex> lk(g_gemm_mu);
@@ -381,6 +406,7 @@ static int gemm(ntf_ctx *ctx, Gemm g, cudaStream_t s, int mode = 0, bool tune = 
         if (r != NTF_ERR_UNSUPPORTED) return r;
         // past the grid's z extent (batch x splits): the CUDA-core kernel below
     }
+    if (g.mfold > 0) return ctx_fail(ctx, NTF_ERR_UNSUPPORTED, "row-folded contraction past the tensor-core grid");
     // tile shape: four batches per CTA for outputs of at most 32 x 32, 64 x 16 or 128 x 8, else by
     // width
     const bool multi = g.batch >= 4 && ((g.M <= 32 && g.N <= 32) || (g.M <= 64 && g.N <= 16) ||
@@ -415,7 +441,7 @@ static int gemm(ntf_ctx *ctx, Gemm g, cudaStream_t s, int mode = 0, bool tune = 
         gemm2k_kernel<64, 64, 1><<<grid, 256, 0, s>>>(g);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess && g.splits > 1) {
-        e = split_sum(g, s, true);
+        e = split_sum(g, s, true, ctx_num_sms(ctx));
         ctx_count(ctx, 1);
     }
     if (e != cudaSuccess) return ctx_fail(ctx, NTF_ERR_CUDA, cudaGetErrorString(e));
@@ -1073,11 +1099,21 @@ int contract_from_w(ntf_ctx *ctx, TuckerWs &w, int block, const Blocks &b, const
                     cudaStream_t st, bool same_blocks = false) {
     if (block == 0) {  // core: Y[i][b][c] = sum_j A2[j,b] W[i,j,c]; Pcore = sum_i A1[i,a] Y[i]
         Gemm g{};
-        g.A = b.A2; g.B = W; g.C = w.Y;
-        g.M = w.J2; g.N = w.J3; g.K1 = w.I2; g.K2 = 1; g.batch = w.I1;
-        g.sam = 1; g.sak1 = w.J2;
-        g.sbb = (int64_t)w.I2 * w.RP; g.sbk1 = w.RP; g.sbn = 1;
-        g.scb = (int64_t)w.J2 * w.J3; g.scm = w.J3; g.scn = 1;
+        if (w.gemm_mode) {
+            // tensor cores: W is the 128-row operand, rows (i, c) folded (m = i J3 + c), so that no
+            // tile row is padding (J2 alone fills a quarter of one)
+            g.A = W; g.B = b.A2; g.C = w.Y;
+            g.M = w.I1 * w.J3; g.N = w.J2; g.K1 = w.I2; g.K2 = 1; g.batch = 1;
+            g.mfold = w.J3; g.sam = 1; g.samb = (int64_t)w.I2 * w.RP; g.sak1 = w.RP;
+            g.sbk1 = w.J2; g.sbn = 1;
+            g.scm = 1; g.scmb = (int64_t)w.J2 * w.J3; g.scn = w.J3;
+        } else {
+            g.A = b.A2; g.B = W; g.C = w.Y;
+            g.M = w.J2; g.N = w.J3; g.K1 = w.I2; g.K2 = 1; g.batch = w.I1;
+            g.sam = 1; g.sak1 = w.J2;
+            g.sbb = (int64_t)w.I2 * w.RP; g.sbk1 = w.RP; g.sbn = 1;
+            g.scb = (int64_t)w.J2 * w.J3; g.scm = w.J3; g.scn = 1;
+        }
         { const int rc_ = gemm(ctx, g, st, w.gemm_mode, w.gemm_tune); if (rc_) return rc_; }
         Gemm h{};
         h.A = b.A1; h.B = w.Y; h.C = out;

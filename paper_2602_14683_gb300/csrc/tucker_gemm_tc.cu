@@ -17,7 +17,9 @@
 //     split hi*hi + hi*lo + lo*hi) into one TMEM accumulator and commits to the stage's mbarrier,
 //     which the threads wait on before they refill that stage two chunks later;
 //   * after the last chunk each warp reads its 32 TMEM lanes (rows), transposes them through
-//     shared memory and stores whole rows (consecutive lanes on consecutive columns).
+//     shared memory and stores whole rows (consecutive lanes on consecutive columns); with a
+//     second index folded into the rows (C's rows contiguous, its columns not) each thread stores
+//     its own row instead.
 // Every wait is bounded; a wait that runs out sets the context's status word, and the kernel then
 // writes nothing, waits (bounded) for its MMAs and frees its TMEM.
 #include "cp3_tc.cuh"
@@ -179,7 +181,10 @@ __device__ __forceinline__ void store_tile(const float (&v)[NR / 4], int mode, f
     }
 }
 
-template <int NTT, bool S3, bool V>
+// RF: rows folded (g.mfold > 0) in A and C; each thread then stores its own row of C (or, over
+// several reduction ranges, of the transposed partials [range][n][m]), so that a warp's store of
+// one column covers 32 consecutive rows.
+template <int NTT, bool S3, bool V, bool RF>
 __global__ void __launch_bounds__(NTH, 1) gemm_tc_kernel(const Gemm g) {
     using G = Geo<NTT, S3>;
     extern __shared__ uint8_t smraw[];
@@ -219,7 +224,7 @@ __global__ void __launch_bounds__(NTH, 1) gemm_tc_kernel(const Gemm g) {
     const int brow = g.sbn == 1 ? 1 : V ? 2 : 0;
     float va[32], vb[NTT / 4];  // the next chunk's operands, loaded a chunk ahead
     if (nch > 0) {
-        load_tile<128, V>(va, arow, Abase, m0, g.sam, 0, 0, g.sak1, g.sak2, g.K2, kbeg, kend, g.M - m0, t);
+        load_tile<128, V>(va, arow, Abase, m0, g.sam, RF ? g.mfold : 0, g.samb, g.sak1, g.sak2, g.K2, kbeg, kend, g.M - m0, t);
         load_tile<NTT, V>(vb, brow, Bbase, n0, g.sbn, g.nin, g.sbb, g.sbk1, g.sbk2, g.K2, kbeg, kend, g.N - n0, t);
     }
     for (int c = 0; c < nch; ++c) {
@@ -234,7 +239,7 @@ __global__ void __launch_bounds__(NTH, 1) gemm_tc_kernel(const Gemm g) {
         store_tile<NTT, S3, V>(vb, brow, Bh, Bl, t);
         if (c + 1 < nch) {  // in flight while this chunk is handed to the tensor cores
             const int k0 = kbeg + (c + 1) * KC;
-            load_tile<128, V>(va, arow, Abase, m0, g.sam, 0, 0, g.sak1, g.sak2, g.K2, k0, kend, g.M - m0, t);
+            load_tile<128, V>(va, arow, Abase, m0, g.sam, RF ? g.mfold : 0, g.samb, g.sak1, g.sak2, g.K2, k0, kend, g.M - m0, t);
             load_tile<NTT, V>(vb, brow, Bbase, n0, g.sbn, g.nin, g.sbb, g.sbk1, g.sbk2, g.K2, k0, kend, g.N - n0, t);
         }
         fence_async_smem();
@@ -264,7 +269,32 @@ __global__ void __launch_bounds__(NTH, 1) gemm_tc_kernel(const Gemm g) {
     __syncthreads();
     fence_after();
     const bool aborted = *abort_flag != 0;
-    if (!aborted) {
+    if (RF && !aborted) {
+        // each thread stores its own row (TMEM lane): C's row m (scm = 1 within a fold block), or
+        // row m of the range's transposed partial [n][m]
+        const int m = m0 + 32 * warp + lane;
+        const bool part = g.splits > 1;
+        float *base = part ? g.part + ((int64_t)sp * g.batch + bt) * g.M * g.N : g.C;
+        const int64_t ro = part ? (int64_t)m : (int64_t)bt * g.scb + row_off(m, 1, g.mfold, g.scmb);
+        const int64_t cs = part ? (int64_t)g.M : g.scn;
+#pragma unroll 1
+        for (int j = 0; j < NTT / 32; ++j) {
+            float v[32];
+            if (li >= 0) {
+                tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + 32 * j, v);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 32; ++q) v[q] = 0.0f;  // empty reduction range
+            }
+            if (m < g.M) {
+#pragma unroll
+                for (int q = 0; q < 32; ++q) {
+                    const int n = n0 + 32 * j + q;
+                    if (n < g.N) base[ro + (int64_t)n * cs] = v[q];
+                }
+            }
+        }
+    } else if (!aborted) {
         // warp w holds TMEM lanes 32 w .. 32 w + 31 (rows m0 + 32 w + lane); each 32-column block
         // goes through a 32 x 33 staging tile of the warp's own (the operand ring is free now), and
         // the warp then stores its rows one at a time, lane = column
@@ -315,10 +345,10 @@ __global__ void __launch_bounds__(NTH, 1) gemm_tc_kernel(const Gemm g) {
     }
 }
 
-template <int NTT, bool S3, bool V = false>
+template <int NTT, bool S3, bool V = false, bool RF = false>
 cudaError_t launch_t(const Gemm &g, cudaStream_t s) {
     using G = Geo<NTT, S3>;
-    auto k = gemm_tc_kernel<NTT, S3, V>;
+    auto k = gemm_tc_kernel<NTT, S3, V, RF>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
     if (e != cudaSuccess) return e;
     const dim3 grid((unsigned)((g.N + NTT - 1) / NTT), (unsigned)((g.M + 127) / 128), (unsigned)(g.batch * g.splits));
@@ -343,10 +373,14 @@ static bool vec_ok(const float *p, int64_t sbat, int64_t srow, int nin, int64_t 
 cudaError_t gemm_tc_launch(const Gemm &g, bool s3, int ntt, cudaStream_t s) {
     if (g.M < 1 || g.N < 1 || g.batch < 1 || g.splits < 1 || g.kchunks < 1) return cudaErrorInvalidValue;
     const int K = g.K1 * g.K2;
+    if (g.mfold > 0) {  // rows folded: 32-column tiles, C's rows contiguous within a fold block
+        if (ntt != 32 || g.scm != 1 || g.nin != 0) return cudaErrorInvalidValue;
+        return s3 ? tgemm::launch_t<32, true, false, true>(g, s) : tgemm::launch_t<32, false, false, true>(g, s);
+    }
     // the 16-byte form only for 32-column tiles (the long-reduction factor contractions): in the
     // wider tiles its extra registers cost a resident CTA per SM
     const bool v = ntt == 32 && (g.sam != 1 || g.sbn != 1) &&
-                   tgemm::vec_ok(g.A, g.sab, g.sam, 0, 0, g.sak1, g.sak2, g.K2, K) &&
+                   tgemm::vec_ok(g.A, g.sab, g.sam, g.mfold, g.samb, g.sak1, g.sak2, g.K2, K) &&
                    tgemm::vec_ok(g.B, g.sbb, g.sbn, g.nin, g.sbb, g.sbk1, g.sbk2, g.K2, K);
     if (v) return s3 ? tgemm::launch_t<32, true, true>(g, s) : tgemm::launch_t<32, false, true>(g, s);
     switch (ntt) {

@@ -90,31 +90,41 @@ cudaError_t colsum_prod(int nf, const float *const *f, const int *rows, int RP, 
 // multiplicative update"; Section 5.3 "CP inner update" with pre = reference block):
 //   out = max(pre * (Num / Den)^gamma, eps)
 __global__ void mu_epilogue_kernel(MuEpiArgs e) {
-    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (int64_t)e.rows * e.RP) return;
-    const int r = (int)(t % e.RP);
+    // four consecutive threads per output: each adds a quarter of the parts in part order, and the
+    // quarter sums are added in quarter order (lane 0 of the four then applies the update)
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t t = gt >> 2;
+    const int q = (int)(gt & 3);
+    const int64_t n = (int64_t)e.rows * e.RP;
+    const bool live = t < n;
+    const int r = live ? (int)(t % e.RP) : 0;
+    const bool used = live && r < e.R;
+    const int per = (e.n_parts + 3) / 4, p0 = q * per, p1 = min(e.n_parts, p0 + per);
+    auto psum = [&](const float *src) {
+        float acc = 0.0f;
+        if (used) {
+            for (int pb = p0; pb < p1; pb += 8) {
+                float v[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) v[k] = pb + k < p1 ? src[(int64_t)(pb + k) * n + t] : 0.0f;
+#pragma unroll
+                for (int k = 0; k < 8; ++k)
+                    if (pb + k < p1) acc += v[k];
+            }
+        }
+        const float a1 = __shfl_down_sync(0xffffffffu, acc, 1), a2 = __shfl_down_sync(0xffffffffu, acc, 2),
+                    a3 = __shfl_down_sync(0xffffffffu, acc, 3);
+        return ((acc + a1) + a2) + a3;
+    };
+    const float num = psum(e.pn);
+    const float den = e.den_closed ? (used ? e.den_closed[r] : 1.0f) : psum(e.pd);
+    if (q != 0 || !live) return;
     if (r >= e.R) {
         e.out[t] = 0.0f;
         if (e.chi1_out) e.chi1_out[t] = 0.0f;
         if (e.chi2_out) e.chi2_out[t] = 0.0f;
         return;
     }
-    const int64_t stride = (int64_t)e.rows * e.RP;
-    // partial sums added in part order; sixteen loads are issued before their adds
-    auto psum = [&](const float *src) {
-        float acc = 0.0f;
-        for (int p0 = 0; p0 < e.n_parts; p0 += 16) {
-            float v[16];
-#pragma unroll
-            for (int k = 0; k < 16; ++k) v[k] = p0 + k < e.n_parts ? src[(p0 + k) * stride + t] : 0.0f;
-#pragma unroll
-            for (int k = 0; k < 16; ++k)
-                if (p0 + k < e.n_parts) acc += v[k];
-        }
-        return acc;
-    };
-    const float num = psum(e.pn);
-    const float den = e.den_closed ? e.den_closed[r] : psum(e.pd);
     const float ratio = __fdiv_rn(num, den);
     float m;
     if (e.gamma == 1.0f) m = ratio;
@@ -128,7 +138,7 @@ __global__ void mu_epilogue_kernel(MuEpiArgs e) {
 
 cudaError_t mu_epilogue(const MuEpiArgs &e, cudaStream_t s) {
     int64_t n = (int64_t)e.rows * e.RP;
-    mu_epilogue_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(e);
+    mu_epilogue_kernel<<<(unsigned)((4 * n + 255) / 256), 256, 0, s>>>(e);
     return cudaGetLastError();
 }
 

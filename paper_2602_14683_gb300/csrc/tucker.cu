@@ -199,22 +199,23 @@ __global__ void __launch_bounds__(256) gemm2k_kernel(const Gemm g) {
     }
 }
 
-// C = sum over the reduction ranges: four consecutive threads per output each add a quarter of
-// the ranges in range order (loads eight at a time), and the four quarter sums are added in
-// quarter order; in FP64 for the FP32 GEMM (its accuracy carry), in FP32 for the tensor-core one
+// C = sum over the reduction ranges.  With L = 4 (many ranges) four consecutive threads per output
+// each add a quarter of the ranges in range order (loads eight at a time) and the four quarter
+// sums are added in quarter order; with L = 1 (at most eight ranges) one thread adds them all in
+// range order.  In FP64 for the FP32 GEMM (its accuracy carry), in FP32 for the tensor-core one
 // (TF32 operands; a few ranges, and the GB300 FP64 pipe, conversions included, is slow).  With the
 // batch folded into the columns (g.nin > 0), column b nin + n goes to batch block b of C; with a
 // second index folded into the rows (g.mfold > 0) the partials are [n][m].  A bounded grid strides
-// over the outputs (eight per warp and step, warp-uniform loop).
-template <typename T>
+// over the outputs (32 / L per warp and step, warp-uniform loop).
+template <typename T, int L>
 __global__ void gemm_split_sum_kernel(const Gemm g) {
     const int64_t total = (int64_t)g.M * g.N * g.batch;
-    const int qid = threadIdx.x & 3;
-    const int64_t step = ((int64_t)gridDim.x * blockDim.x) >> 2;
-    const int per = (g.splits + 3) / 4, s0 = qid * per, s1 = min(g.splits, s0 + per);
-    const int64_t first = ((int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) >> 2;  // the warp's first output
+    const int qid = L == 1 ? 0 : (int)(threadIdx.x & 3);
+    const int64_t step = ((int64_t)gridDim.x * blockDim.x) / L;
+    const int per = (g.splits + L - 1) / L, s0 = qid * per, s1 = min(g.splits, s0 + per);
+    const int64_t first = ((int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) / L;  // the warp's first output
     for (int64_t w0 = first; w0 < total; w0 += step) {
-        const int64_t t = w0 + ((threadIdx.x & 31) >> 2);
+        const int64_t t = w0 + (threadIdx.x & 31) / L;
         const bool live = t < total;
         T v = 0;
         if (live) {
@@ -227,23 +228,28 @@ __global__ void gemm_split_sum_kernel(const Gemm g) {
                     if (sp0 + q < s1) v += (T)x[q];
             }
         }
-        const T v1 = __shfl_down_sync(0xffffffffu, v, 1), v2 = __shfl_down_sync(0xffffffffu, v, 2),
-                v3 = __shfl_down_sync(0xffffffffu, v, 3);
+        T tot = v;
+        if (L == 4) {
+            const T v1 = __shfl_down_sync(0xffffffffu, v, 1), v2 = __shfl_down_sync(0xffffffffu, v, 2),
+                    v3 = __shfl_down_sync(0xffffffffu, v, 3);
+            tot = ((v + v1) + v2) + v3;
+        }
         if (qid != 0 || !live) continue;
-        const T tot = ((v + v1) + v2) + v3;
         // output t: [batch][M][N] order, or [batch][N][M] for the row-folded form (its partials'
         // order, m contiguous in C)
         const int inner = g.mfold > 0 ? g.M : g.N, outer = g.mfold > 0 ? g.N : g.M;
-        int64_t q;
-        int r;
+        int bt, o, r;
         if (total < (1ll << 31)) {  // 32-bit index arithmetic
-            q = (int)t / inner;
-            r = (int)t - (int)q * inner;
+            const int ti = (int)t, q = ti / inner;
+            r = ti - q * inner;
+            bt = q / outer;
+            o = q - bt * outer;
         } else {
-            q = t / inner;
+            const int64_t q = t / inner;
             r = (int)(t - q * inner);
+            bt = (int)(q / outer);
+            o = (int)(q - (int64_t)bt * outer);
         }
-        const int bt = (int)(q / outer), o = (int)(q - (int64_t)bt * outer);
         const int m = g.mfold > 0 ? r : o, n = g.mfold > 0 ? o : r;
         int64_t mo = (int64_t)m * g.scm;  // row m's offset (second index folded into the rows: mfold > 0)
         if (g.mfold > 0) {
@@ -263,9 +269,15 @@ __global__ void gemm_split_sum_kernel(const Gemm g) {
 
 static cudaError_t split_sum(const Gemm &g, cudaStream_t s, bool fp64, int sms) {
     const int64_t total = (int64_t)g.M * g.N * g.batch;
-    const unsigned blocks = (unsigned)std::min<int64_t>((4 * total + 255) / 256, 8 * (int64_t)sms);
-    if (fp64) gemm_split_sum_kernel<double><<<blocks, 256, 0, s>>>(g);
-    else gemm_split_sum_kernel<float><<<blocks, 256, 0, s>>>(g);
+    const int L = g.splits <= 8 ? 1 : 4;
+    const unsigned blocks = (unsigned)std::min<int64_t>((L * total + 255) / 256, 8 * (int64_t)sms);
+    if (fp64) {
+        if (L == 1) gemm_split_sum_kernel<double, 1><<<blocks, 256, 0, s>>>(g);
+        else gemm_split_sum_kernel<double, 4><<<blocks, 256, 0, s>>>(g);
+    } else {
+        if (L == 1) gemm_split_sum_kernel<float, 1><<<blocks, 256, 0, s>>>(g);
+        else gemm_split_sum_kernel<float, 4><<<blocks, 256, 0, s>>>(g);
+    }
     return cudaGetLastError();
 }
 

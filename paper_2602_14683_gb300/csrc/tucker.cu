@@ -978,13 +978,15 @@ float *wsf(ntf_ctx *ctx, const char *name, int64_t n, bool &ok) {
 }
 
 // B3[i][j][c] = sum_b A2[j,b] sum_a A1[i,a] G[a,b,c], padded to RP columns (pad kept 0)
-int build_b3(ntf_ctx *ctx, TuckerWs &w, const Blocks &b, float *out, cudaStream_t st) {
-    TK(cudaMemsetAsync(out, 0, sizeof(float) * (size_t)w.I1 * w.I2 * w.RP, st));
+// B3 = (A1 x_1 G) x_2 A2 into out; with ga1_ready, w.GA1 already holds A1 x_1 G of these blocks
+int build_b3(ntf_ctx *ctx, TuckerWs &w, const Blocks &b, float *out, cudaStream_t st, bool ga1_ready = false) {
+    // the product writes columns c < J3 of every row; padding columns (J3 < RP) must read zero
+    if (w.J3 < w.RP) TK(cudaMemsetAsync(out, 0, sizeof(float) * (size_t)w.I1 * w.I2 * w.RP, st));
     Gemm g{};
     g.A = b.A1; g.B = b.G; g.C = w.GA1;
     g.M = w.I1; g.N = w.J2 * w.J3; g.K1 = w.J1; g.K2 = 1; g.batch = 1;
     g.sam = w.J1; g.sak1 = 1; g.sbk1 = (int64_t)w.J2 * w.J3; g.sbn = 1; g.scm = (int64_t)w.J2 * w.J3; g.scn = 1;
-    { const int rc_ = gemm(ctx, g, st, w.gemm_mode, w.gemm_tune); if (rc_) return rc_; }
+    if (!ga1_ready) { const int rc_ = gemm(ctx, g, st, w.gemm_mode, w.gemm_tune); if (rc_) return rc_; }
     Gemm h{};
     h.A = b.A2; h.B = w.GA1; h.C = out;
     h.M = w.I2; h.N = w.J3; h.K1 = w.J2; h.K2 = 1; h.batch = w.I1;
@@ -1450,17 +1452,17 @@ int tucker_run(ntf_ctx *ctx, const ntf_tensor *X, float beta, const int64_t *cor
         if ((rc = contract_from_w(ctx, w, 0, w.cur, w.Wn, w.num, st))) return rc;
         if ((rc = contract_from_w(ctx, w, 0, w.cur, w.Wd, w.den, st))) return rc;
         if ((rc = apply_mu(ctx, w, w.cur.G, w.cur.G, Jc, beta, eps, nullptr, nullptr, nullptr, st))) return rc;
-        // ---- modes 1 and 2 ----
+        // ---- modes 1 and 2 (block 2's GA1 = A1 x_1 G is the one the B3 build just made) ----
         for (int blk = 1; blk <= 2; ++blk) {
             if ((rc = build_b3(ctx, w, w.cur, w.Brec, st))) return rc;
             if ((rc = rows_pass(ctx, w, X, o, beta, w.Brec, w.cur.A3p, w.cur.A3p, w.cur.A3p, false, st))) return rc;
-            if ((rc = contract_from_w(ctx, w, blk, w.cur, w.Wn, w.num, st))) return rc;
+            if ((rc = contract_from_w(ctx, w, blk, w.cur, w.Wn, w.num, st, /*same_blocks=*/blk == 2))) return rc;
             if ((rc = contract_from_w(ctx, w, blk, w.cur, w.Wd, w.den, st, /*same_blocks=*/true))) return rc;
             float *A = blk == 1 ? w.cur.A1 : w.cur.A2;
             if ((rc = apply_mu(ctx, w, A, A, blk == 1 ? n1 : n2, beta, eps, nullptr, nullptr, nullptr, st))) return rc;
         }
-        // ---- mode 3 ----
-        if ((rc = build_b3(ctx, w, w.cur, w.Brec, st))) return rc;
+        // ---- mode 3 (A1 and G unchanged since block 2: GA1 still holds their product) ----
+        if ((rc = build_b3(ctx, w, w.cur, w.Brec, st, /*ga1_ready=*/true))) return rc;
         if ((rc = mode3_pass(ctx, w, X, o, beta, w.Brec, w.cur.A3p, w.Brec, w.Brec, false, st))) return rc;
         MuEpiArgs e{};
         e.pn = w.pn3; e.pd = w.pd3; e.n_parts = w.parts3; e.rows = w.I3; e.RP = w.RP; e.R = w.J3;
@@ -1491,9 +1493,10 @@ int tucker_run(ntf_ctx *ctx, const ntf_tensor *X, float beta, const int64_t *cor
                 float *c2 = blk == 1 ? w.t2.A1 : w.t2.A2;
                 if ((rc = apply_mu(ctx, w, At, A, blk == 1 ? n1 : n2, beta, eps, At, c1, c2, st))) return rc;
             }
-            // mode 3: rows of the transformed partial tensors
+            // mode 3: rows of the transformed partial tensors (the chi2 side first: GA1 still holds
+            // A1 x_1 G of the chi2 blocks from block 2, whose update changed only A2)
+            if ((rc = build_b3(ctx, w, w.t2, w.Bd, st, /*ga1_ready=*/true))) return rc;
             if ((rc = build_b3(ctx, w, w.t1, w.Bn, st))) return rc;
-            if ((rc = build_b3(ctx, w, w.t2, w.Bd, st))) return rc;
             if ((rc = mode3_pass(ctx, w, X, o, beta, w.Brec, w.ref.A3p, w.Bn, w.Bd, false, st))) return rc;
             MuEpiArgs e{};
             e.pn = w.pn3; e.pd = w.pd3; e.n_parts = w.parts3; e.rows = w.I3; e.RP = w.RP; e.R = w.J3;

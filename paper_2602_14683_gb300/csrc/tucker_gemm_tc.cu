@@ -313,16 +313,15 @@ __global__ void __launch_bounds__(NTH, 1) gemm_tc_kernel(const Gemm g) {
             for (int q = 0; q < 32; ++q) stg[lane * 33 + q] = v[q];
             __syncwarp();
             const int n = n0 + 32 * j + lane;
-            // this lane's column: its offset in C (batch block and column when folded)
-            const int64_t cn = g.splits > 1 ? (int64_t)n : row_off(n, sn, g.nin, g.scb);
+            if (n < g.N) {
+                // this lane's column: its offset in C (batch block and column when folded); the
+                // warp's rows then follow at a fixed stride
+                const int mw = m0 + 32 * warp, mcnt = min(32, g.M - mw);
+                float *dst = g.splits > 1 ? g.part + (((int64_t)sp * g.batch + bt) * g.M + mw) * g.N + n
+                                          : g.C + (int64_t)bt * g.scb + (int64_t)mw * g.scm + row_off(n, sn, g.nin, g.scb);
+                const int64_t rstep = g.splits > 1 ? (int64_t)g.N : g.scm;
 #pragma unroll 4
-            for (int i = 0; i < 32; ++i) {
-                const int m = m0 + 32 * warp + i;
-                if (m < g.M && n < g.N) {
-                    float *dst = g.splits > 1 ? g.part + (((int64_t)sp * g.batch + bt) * g.M + m) * g.N
-                                              : g.C + (int64_t)bt * g.scb + (int64_t)m * g.scm;
-                    dst[cn] = stg[i * 33 + lane];
-                }
+                for (int i = 0; i < mcnt; ++i, dst += rstep) *dst = stg[i * 33 + lane];
             }
             __syncwarp();
         }

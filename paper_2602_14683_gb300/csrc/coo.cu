@@ -341,8 +341,14 @@ __global__ void coo_row_reduce_kernel(const float *gpart, const int32_t *row_gro
 // CTA of 1024 threads in a fixed order: thread (s, r) sums the rows i = s mod 32 of rank r
 // for each factor, the 32 slices are added in order, and the products over ranks r < R
 // are added in rank order after the stored-entry partials.
-__global__ void __launch_bounds__(1024) coo_obj_finish_kernel(const double *parts, int n, const float *const *F,
-                                                              const int *rows, int N, int R, int RP, double *out) {
+// the padded factors and their row counts, passed by value (no host-to-device copy per call)
+struct CooFactorSet {
+    const float *f[8];
+    int rows[8];
+};
+
+__global__ void __launch_bounds__(1024) coo_obj_finish_kernel(const double *parts, int n, const CooFactorSet fs,
+                                                              int N, int R, int RP, double *out) {
     __shared__ double sh[1024];
     __shared__ double prod[64];
     const int t = threadIdx.x, r = t % 32, sl = t / 32;
@@ -368,11 +374,12 @@ __global__ void __launch_bounds__(1024) coo_obj_finish_kernel(const double *part
         double pr = 1.0;
         for (int m = 0; m < N; ++m) {
             double c = 0.0;
-            const float *f = F[m] + rb + r;
-            for (int i0 = sl; i0 < rows[m]; i0 += 8 * 32) {
+            const float *f = fs.f[m] + rb + r;
+            const int rows = fs.rows[m];
+            for (int i0 = sl; i0 < rows; i0 += 8 * 32) {
                 float v[8];
 #pragma unroll
-                for (int k = 0; k < 8; ++k) v[k] = i0 + 32 * k < rows[m] ? f[(int64_t)(i0 + 32 * k) * RP] : 0.0f;
+                for (int k = 0; k < 8; ++k) v[k] = i0 + 32 * k < rows ? f[(int64_t)(i0 + 32 * k) * RP] : 0.0f;
 #pragma unroll
                 for (int k = 0; k < 8; ++k) c += (double)v[k];
             }
@@ -393,6 +400,18 @@ __global__ void __launch_bounds__(1024) coo_obj_finish_kernel(const double *part
         for (int q = 0; q < R; ++q) tot += prod[q];
         *out = tot;
     }
+}
+
+// the fixed-order objective total: stored-entry partials plus the dense part from the factors
+static cudaError_t obj_finish(const double *parts, int n, const float *const *F, const int64_t *dims, int N, int R,
+                              int RP, double *out, cudaStream_t st) {
+    CooFactorSet fs{};
+    for (int m = 0; m < N; ++m) {
+        fs.f[m] = F[m];
+        fs.rows[m] = (int)dims[m];
+    }
+    coo_obj_finish_kernel<<<1, 1024, 0, st>>>(parts, n, fs, N, R, RP, out);
+    return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------- cache & driver
@@ -600,9 +619,7 @@ int coo_kl_sweep(ntf_ctx *ctx, const ntf_tensor *X, int R, float *const *factors
     for (int m = 0; m < N; ++m) maxdim = X->dims[m] > maxdim ? X->dims[m] : maxdim;
     float *num = (float *)ctx_ws(ctx, "cooNum", sizeof(float) * (size_t)maxdim * RP);
     float *denc = (float *)ctx_ws(ctx, "cooDenc", sizeof(float) * 64);
-    const float **fptr = (const float **)ctx_ws(ctx, "cooFptr", sizeof(float *) * 8);
-    int *frows = (int *)ctx_ws(ctx, "cooFrows", sizeof(int) * 8);
-    if (!part || !objp || !num || !denc || !fptr || !frows) return ctx_fail(ctx, NTF_ERR_OOM, "COO workspace allocation failed");
+    if (!part || !objp || !num || !denc) return ctx_fail(ctx, NTF_ERR_OOM, "COO workspace allocation failed");
 
     // objective of the incoming (= reference) iterate, from the mode-1 pass
     const bool want_obj = objective_dev != nullptr;
@@ -617,12 +634,7 @@ int coo_kl_sweep(ntf_ctx *ctx, const ntf_tensor *X, int R, float *const *factors
             rc = launch_coo_pass(ctx, *c, n, RP, Ft, Ft, (float)o.eps, part, (n == 0 && want_obj) ? objp : nullptr, st);
             if (rc) return rc;
             if (n == 0 && want_obj) {
-                CK(cudaMemcpyAsync(fptr, Ft, sizeof(float *) * N, cudaMemcpyHostToDevice, st));
-                int rows[8];
-                for (int m = 0; m < N; ++m) rows[m] = (int)X->dims[m];
-                CK(cudaMemcpyAsync(frows, rows, sizeof(int) * N, cudaMemcpyHostToDevice, st));
-                coo_obj_finish_kernel<<<1, 1024, 0, st>>>(objp, c->md[0].n_units, fptr, frows, N, R, RP, objective_dev);
-                CK(cudaGetLastError());
+                CK(obj_finish(objp, c->md[0].n_units, Ft, X->dims, N, R, RP, objective_dev, st));
                 ctx_count(ctx, 1);
             }
             rc = row_sums(ctx, *c, n, RP, part, gpart, buf, st);
@@ -640,12 +652,7 @@ int coo_kl_sweep(ntf_ctx *ctx, const ntf_tensor *X, int R, float *const *factors
                 rc = launch_coo_pass(ctx, *c, n, RP, F, F, (float)o.eps, part, obj ? objp : nullptr, st);
                 if (rc) return rc;
                 if (obj) {
-                    CK(cudaMemcpyAsync(fptr, F, sizeof(float *) * N, cudaMemcpyHostToDevice, st));
-                    int rows[8];
-                    for (int m = 0; m < N; ++m) rows[m] = (int)X->dims[m];
-                    CK(cudaMemcpyAsync(frows, rows, sizeof(int) * N, cudaMemcpyHostToDevice, st));
-                    coo_obj_finish_kernel<<<1, 1024, 0, st>>>(objp, c->md[0].n_units, fptr, frows, N, R, RP, objective_dev);
-                    CK(cudaGetLastError());
+                    CK(obj_finish(objp, c->md[0].n_units, F, X->dims, N, R, RP, objective_dev, st));
                     ctx_count(ctx, 1);
                 }
                 rc = row_sums(ctx, *c, n, RP, part, gpart, num, st);
@@ -708,15 +715,7 @@ int coo_num_rows(ntf_ctx *ctx, const ntf_tensor *X, int n, int RP, const float *
 int coo_kl_objective_total(ntf_ctx *ctx, const ntf_tensor *X, const float *const *F, int R, int RP,
                            const double *parts, int n_parts, double *out_dev, cudaStream_t st) {
     const int N = X->order;
-    const float **fptr = (const float **)ctx_ws(ctx, "cooFptr", sizeof(float *) * 8);
-    int *frows = (int *)ctx_ws(ctx, "cooFrows", sizeof(int) * 8);
-    if (!fptr || !frows) return ctx_fail(ctx, NTF_ERR_OOM, "COO workspace allocation failed");
-    CK(cudaMemcpyAsync(fptr, F, sizeof(float *) * N, cudaMemcpyHostToDevice, st));
-    int rows[8];
-    for (int m = 0; m < N; ++m) rows[m] = (int)X->dims[m];
-    CK(cudaMemcpyAsync(frows, rows, sizeof(int) * N, cudaMemcpyHostToDevice, st));
-    coo_obj_finish_kernel<<<1, 1024, 0, st>>>(parts, n_parts, fptr, frows, N, R, RP, out_dev);
-    CK(cudaGetLastError());
+    CK(obj_finish(parts, n_parts, F, X->dims, N, R, RP, out_dev, st));
     ctx_count(ctx, 1);
     return NTF_OK;
 }
@@ -737,17 +736,10 @@ int coo_kl_objective(ntf_ctx *ctx, const ntf_tensor *X, int R, const float *cons
     }
     float *part = (float *)ctx_ws(ctx, "cooPart", sizeof(float) * (size_t)(c->max_units + 1) * RP);
     double *objp = (double *)ctx_ws(ctx, "cooObjP", sizeof(double) * (size_t)(c->max_units + 1));
-    const float **fptr = (const float **)ctx_ws(ctx, "cooFptr", sizeof(float *) * 8);
-    int *frows = (int *)ctx_ws(ctx, "cooFrows", sizeof(int) * 8);
-    if (!part || !objp || !fptr || !frows) return ctx_fail(ctx, NTF_ERR_OOM, "COO workspace allocation failed");
+    if (!part || !objp) return ctx_fail(ctx, NTF_ERR_OOM, "COO workspace allocation failed");
     rc = launch_coo_pass(ctx, *c, 0, RP, F, F, (float)o.eps, part, objp, st);
     if (rc) return rc;
-    CK(cudaMemcpyAsync(fptr, F, sizeof(float *) * N, cudaMemcpyHostToDevice, st));
-    int rows[8];
-    for (int m = 0; m < N; ++m) rows[m] = (int)X->dims[m];
-    CK(cudaMemcpyAsync(frows, rows, sizeof(int) * N, cudaMemcpyHostToDevice, st));
-    coo_obj_finish_kernel<<<1, 1024, 0, st>>>(objp, c->md[0].n_units, fptr, frows, N, R, RP, out_dev);
-    CK(cudaGetLastError());
+    CK(obj_finish(objp, c->md[0].n_units, F, X->dims, N, R, RP, out_dev, st));
     ctx_count(ctx, 1);
     return NTF_OK;
 }

@@ -1113,9 +1113,9 @@ int contract_from_w(ntf_ctx *ctx, TuckerWs &w, int block, const Blocks &b, const
                     cudaStream_t st, bool same_blocks = false) {
     if (block == 0) {  // core: Y[i][b][c] = sum_j A2[j,b] W[i,j,c]; Pcore = sum_i A1[i,a] Y[i]
         Gemm g{};
-        if (w.gemm_mode) {
-            // tensor cores: W is the 128-row operand, rows (i, c) folded (m = i J3 + c), so that no
-            // tile row is padding (J2 alone fills a quarter of one)
+        // tensor cores: W is the 128-row operand, rows (i, c) folded (m = i J3 + c), so that no tile
+        // row is padding (J2 alone fills a quarter of one), while its row tiles fit the grid
+        if (w.gemm_mode && ((int64_t)w.I1 * w.J3 + 127) / 128 <= 65535) {
             g.A = W; g.B = b.A2; g.C = w.Y;
             g.M = w.I1 * w.J3; g.N = w.J2; g.K1 = w.I2; g.K2 = 1; g.batch = 1;
             g.mfold = w.J3; g.sam = 1; g.samb = (int64_t)w.I2 * w.RP; g.sak1 = w.RP;

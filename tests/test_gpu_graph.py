@@ -74,3 +74,25 @@ def test_tucker_graph_replay_bit_exact(prec):
     for a, b in zip(be, bg):
         assert np.array_equal(host(a), host(b))
     assert oe.item() == og.item()
+
+
+@pytest.mark.parametrize("beta", [1.0, 1.5])
+def test_coo_graph_replay_bit_exact(beta):
+    """Sparse COO J-CoMM (the orders are built by the first, eager call; the objective's factor
+    set is a kernel argument, so the captured calls copy nothing from the host)."""
+    import torch
+    ntf = _ntf()
+    g = np.random.default_rng(9)
+    dims, R = (9, 6, 31, 40), 5
+    X = np.where(g.uniform(size=dims) < 0.15, 1.0 + g.geometric(0.3, size=dims) - 1.0, 0.0)
+    idx = np.nonzero(X)
+    Xc = ntf.Coo(dims, [torch.tensor(i.astype(np.int32), device="cuda") for i in idx],
+                 torch.tensor(X[idx].astype(np.float32), device="cuda"))
+    A0 = [dev(a) for a in synth.init_factors(dims, R, seed=10)]
+
+    def call(A, obj):
+        ntf.jcomm_outer(Xc, beta, A, objective=obj)
+    (be, oe), (bg, og) = _replay_vs_eager(call, A0)
+    for a, b in zip(be, bg):
+        assert np.array_equal(host(a), host(b))
+    assert oe.item() == og.item()

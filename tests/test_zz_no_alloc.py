@@ -55,6 +55,29 @@ def test_noalloc_matches_regular_entry_point_twice():
     torch.cuda.synchronize()
 
 
+def test_noalloc_call_captured_in_a_cuda_graph():
+    """One eager call first (which loads the kernels), then a second call captured into a CUDA
+    graph and replayed: the replay writes the objective the regular entry point computes."""
+    ntf = _ntf()
+    import torch
+    dims, R, beta = (60, 50, 40), 5, 1.5
+    X, _ = synth.cp_dense(dims, R, seed=11, kind="gamma_noise")
+    Xd = dev(X)
+    Ad = [dev(a) for a in synth.init_factors(dims, R, seed=12)]
+    out, out_g = obj_tensor(), obj_tensor()
+    assert _call(ntf, Xd, beta, Ad, out) == 0
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        rc = _call(ntf, Xd, beta, Ad, out_g)
+    assert rc == 0
+    g.replay()
+    torch.cuda.synchronize()
+    want = ntf.beta_div(Xd, beta, Ad).item()
+    assert abs(out_g.item() - want) <= TOL * abs(want), (out_g.item(), want)
+    assert out_g.item() == out.item()  # the same kernels on the same inputs
+
+
 def test_noalloc_rejects_oversized_problem_before_any_work():
     ntf = _ntf()
     import torch

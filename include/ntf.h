@@ -18,6 +18,12 @@
  *     the legacy default stream).  Factors are updated in place when the call's work on
  *     the stream completes.  Objective outputs are FP64 device scalars written on the
  *     same stream.
+ *   - Once a call's workspaces exist (after one call of the same kind, shapes and
+ *     options on the context, and before any larger one), a repeated call makes no
+ *     allocation, no host synchronisation and no host-to-device copy: it may be captured
+ *     on a capturing `stream` into a CUDA graph and replayed, and the replays give
+ *     bit-identical results to eager calls (the first sparse call per tensor, which builds
+ *     the mode orders, must be made outside capture).
  *   - Return value: NTF_OK (0) or a negative ntf_status.  On error nothing has been
  *     launched that modifies caller buffers, except NTF_ERR_CUDA (a launch failed; the
  *     caller's buffers are in an unspecified state).  ntf_last_error(ctx) returns a

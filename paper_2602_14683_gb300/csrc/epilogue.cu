@@ -308,8 +308,17 @@ __global__ void run_update_kernel(RunUpdArgs u) {
     if (!u.pd) {
         double prod = 1.0;
         for (int k = 0; k < u.ncf; ++k) {
+            // rows i = g, g + G, ... added in order, eight loads issued before their adds
+            const int nr = u.cf_rows[k];
             double cs = 0.0;
-            for (int i = g; i < u.cf_rows[k]; i += G) cs += (double)u.cf[k][(int64_t)i * RP + r];
+            for (int i0 = g; i0 < nr; i0 += 8 * G) {
+                float x[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) x[j] = i0 + j * G < nr ? u.cf[k][(int64_t)(i0 + j * G) * RP + r] : 0.0f;
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    if (i0 + j * G < nr) cs += (double)x[j];
+            }
             prod *= group_sum(sh, cs, RP, t);
         }
         if (t < RP) den_s[t] = (float)prod;
@@ -326,24 +335,54 @@ __global__ void run_update_kernel(RunUpdArgs u) {
         const float *parts = side ? u.pd : u.pn;
         const float *const *L = side ? u.Ld : u.Ln;
         double acc = 0.0;
-        for (int64_t q = g; q < other; q += G) {
-            int64_t rem = q, row = 0, mul = 1;
-            float w = 1.0f;
-            for (int m = u.M - 1; m >= 0; --m) {
-                int im;
-                if (m == u.n) {
-                    im = in;
-                } else {
-                    im = (int)(rem % u.dims[m]);
-                    rem /= u.dims[m];
-                    w *= L[m][(int64_t)im * RP + r];
+        // the thread's rows q = g, g + G, ... of the other merged modes, four per step: their merged
+        // row, Khatri-Rao weight and partials are all loaded before any of them is added; each
+        // partial sum and acc keep the order of one row at a time, parts in order (the merged
+        // run has fewer than 2^31 rows: 32-bit index arithmetic)
+        const int oth = (int)other;
+        for (int q0 = g; q0 < oth; q0 += 4 * G) {
+            int rowq[4];
+            float wq[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int q = q0 + j * G;
+                int rem = q < oth ? q : 0, row = 0, mul = 1;
+                float w = 1.0f;
+                for (int m = u.M - 1; m >= 0; --m) {
+                    int im;
+                    if (m == u.n) {
+                        im = in;
+                    } else {
+                        const int d = u.dims[m], nx = rem / d;
+                        im = rem - nx * d;
+                        rem = nx;
+                        w *= L[m][(int64_t)im * RP + r];
+                    }
+                    row += im * mul;
+                    mul *= u.dims[m];
                 }
-                row += (int64_t)im * mul;
-                mul *= u.dims[m];
+                rowq[j] = row;
+                wq[j] = w;
             }
-            float sv = 0.0f;
-            for (int p = 0; p < u.n_parts; ++p) sv += parts[(int64_t)p * stride + row * RP + r];
-            acc += (double)sv * (double)w;
+            float sv[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+            for (int p0 = 0; p0 < u.n_parts; p0 += 8) {
+                float x[4][8];
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+#pragma unroll
+                    for (int k = 0; k < 8; ++k)
+                        x[j][k] = (q0 + j * G < oth && p0 + k < u.n_parts)
+                                      ? parts[(int64_t)(p0 + k) * stride + (int64_t)rowq[j] * RP + r]
+                                      : 0.0f;
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+#pragma unroll
+                    for (int k = 0; k < 8; ++k)
+                        if (p0 + k < u.n_parts) sv[j] += x[j][k];
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (q0 + j * G < oth) acc += (double)sv[j] * (double)wq[j];
         }
         const double tot = group_sum(sh, acc, RP, t);
         if (t < RP) (side ? den_s : num_s)[t] = (float)tot;
@@ -434,15 +473,18 @@ __device__ __forceinline__ void mode_update_body(const UpdArgs &u, const int blk
     };
     auto psum = [&](const float *src, int64_t o, float *first) {  // first: loaded batch 0 or null
         float acc = 0.0f;
-        for (int p0 = 0; p0 < e.n_parts; p0 += 32) {
-            float v[32];
+        for (int p0 = 0; p0 < e.n_parts; p0 += 64) {  // two batches of loads in flight
+            float v[32], v2[32];
             if (p0 == 0 && first) {
 #pragma unroll
                 for (int k = 0; k < 32; ++k) v[k] = first[k];
             } else {
                 load32(src, o, p0, v);
             }
+            const bool two = p0 + 32 < e.n_parts;
+            if (two) load32(src, o, p0 + 32, v2);
             acc = add32(p0, v, acc);
+            if (two) acc = add32(p0 + 32, v2, acc);
         }
         return acc;
     };

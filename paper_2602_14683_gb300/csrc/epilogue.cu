@@ -473,18 +473,15 @@ __device__ __forceinline__ void mode_update_body(const UpdArgs &u, const int blk
     };
     auto psum = [&](const float *src, int64_t o, float *first) {  // first: loaded batch 0 or null
         float acc = 0.0f;
-        for (int p0 = 0; p0 < e.n_parts; p0 += 64) {  // two batches of loads in flight
-            float v[32], v2[32];
+        for (int p0 = 0; p0 < e.n_parts; p0 += 32) {
+            float v[32];
             if (p0 == 0 && first) {
 #pragma unroll
                 for (int k = 0; k < 32; ++k) v[k] = first[k];
             } else {
                 load32(src, o, p0, v);
             }
-            const bool two = p0 + 32 < e.n_parts;
-            if (two) load32(src, o, p0 + 32, v2);
             acc = add32(p0, v, acc);
-            if (two) acc = add32(p0 + 32, v2, acc);
         }
         return acc;
     };
